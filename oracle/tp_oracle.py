@@ -1,0 +1,517 @@
+"""FP64 CPU oracle for the tangent-point surface-flow hot path.
+
+TEST INFRASTRUCTURE ONLY. This module is the plain, slow, obviously correct
+restatement of what the GPU library computes. Only the tests, the smoke
+check and the benchmark's CPU-baseline leg may import it; the library never
+does, and it never imports the library.
+
+Every function cites the passage of "Repulsive Surfaces" (Yu, Brakensiek,
+Schumacher, Crane 2021) it follows. Equations are numbered in order of
+appearance: Eq. 9 discrete kernel, Eq. 10 discrete energy, Eq. 11 pairwise
+L^sigma entries, Eq. 12/13 high/low-order summands, Eq. 14 saddle problem,
+Eq. 15 projection saddle problem, Eq. 16 Barnes-Hut energy, Eq. 17 Schur
+complement, Eq. 18 projected direction, Eq. 19 Schur correction.
+
+Conventions: positions f are float64 [nv,3]; faces int [nf,3] counter-
+clockwise; all arithmetic is float64; pair sums run over ordered pairs
+S != T (the diagonal term is 0/0 and is excluded, as in the (1 - delta_ST)
+factor of the kernel matrices of §5.1).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+CHUNK = 256
+
+
+# ---------------------------------------------------------------------------
+# §3.1 face geometry
+# ---------------------------------------------------------------------------
+
+def face_geometry(f, faces):
+    """Barycenter X_S, unit normal N_S and area a_S of every face (§3.1:
+    barycenters and areas of Eq. 9/10; the normal projector is P_S = N_S N_S^T,
+    §2.1)."""
+    fi, fj, fk = f[faces[:, 0]], f[faces[:, 1]], f[faces[:, 2]]
+    X = (fi + fj + fk) / 3.0
+    n = np.cross(fj - fi, fk - fi)
+    nn = np.linalg.norm(n, axis=1)
+    return X, n / nn[:, None], 0.5 * nn
+
+
+def sobolev_s(p, n=2):
+    """Sobolev order s = 2 - n/p of the energy (§2.3)."""
+    return 2.0 - n / p
+
+
+# ---------------------------------------------------------------------------
+# §3.1 discrete energy, Eq. 9 and Eq. 10
+# ---------------------------------------------------------------------------
+
+def tp_kernel(X, N, Y, p):
+    """K_p(X, P; Y) = |P (X - Y)|^p / |X - Y|^{2p} with P = N N^T (Eq. 9, and
+    its rewriting in §4.1). Broadcasts over leading axes."""
+    d = X - Y
+    r2 = np.sum(d * d, axis=-1)
+    u = np.abs(np.sum(N * d, axis=-1))
+    return u ** p / r2 ** p
+
+
+def energy_rows(f, faces, p=6.0, targets=None):
+    """Row sums E_S = sum_{T != S} K(S,T) a_S a_T of Eq. 10 for the given
+    target faces (all by default)."""
+    X, N, a = face_geometry(f, faces)
+    nf = len(faces)
+    targets = np.arange(nf) if targets is None else np.asarray(targets)
+    out = np.empty(len(targets))
+    for c0 in range(0, len(targets), CHUNK):
+        S = targets[c0:c0 + CHUNK]
+        d = X[S, None, :] - X[None, :, :]
+        r2 = np.sum(d * d, axis=-1)
+        self_pair = S[:, None] == np.arange(nf)[None, :]
+        r2 = np.where(self_pair, 1.0, r2)
+        u = np.abs(np.einsum("sk,stk->st", N[S], d))
+        K = np.where(self_pair, 0.0, u ** p / r2 ** p)
+        out[c0:c0 + CHUNK] = a[S] * (K @ a)
+    return out
+
+
+def energy(f, faces, p=6.0):
+    """Discrete tangent-point energy, Eq. 10, ordered pairs S != T."""
+    return float(np.sum(energy_rows(f, faces, p)))
+
+
+# ---------------------------------------------------------------------------
+# §3.1 differential (chain rule through X_S, N_S, a_S)
+# ---------------------------------------------------------------------------
+
+def face_adjoints(f, faces, p=6.0, rows=None):
+    """Per-face partial derivatives of Eq. 10 with respect to the face data:
+    gX = dE/dX_S, gN = dE/dN_S (N_S treated as a free vector), ga = dE/da_S.
+
+    Face S enters Eq. 10 twice: as the first argument of K(S,T) (its
+    barycenter, normal and area) and as the second argument of K(T,S) (its
+    barycenter and area). With d = X_S - X_T, u = N.d and
+    K = |u|^p / |d|^{2p}:
+        dK/dd = p |u|^{p-2} u |d|^{-2p} N - 2 p K d / |d|^2,
+        dK/dN = p |u|^{p-2} u |d|^{-2p} d.
+    """
+    X, N, a = face_geometry(f, faces)
+    nf = len(faces)
+    rows = np.arange(nf) if rows is None else np.asarray(rows)
+    gX = np.zeros((len(rows), 3))
+    gN = np.zeros((len(rows), 3))
+    ga = np.zeros(len(rows))
+    for c0 in range(0, len(rows), CHUNK):
+        S = rows[c0:c0 + CHUNK]
+        d = X[S, None, :] - X[None, :, :]                 # d_ST = X_S - X_T
+        r2 = np.sum(d * d, axis=-1)
+        self_pair = S[:, None] == np.arange(nf)[None, :]
+        r2 = np.where(self_pair, 1.0, r2)
+        w = np.where(self_pair, 0.0, 1.0)
+        uS = np.einsum("sk,stk->st", N[S], d)             # N_S . d_ST
+        uT = np.einsum("tk,stk->st", N, d)                # N_T . d_ST
+        r2p = r2 ** p
+        KST = w * np.abs(uS) ** p / r2p
+        KTS = w * np.abs(uT) ** p / r2p
+        cS = w * p * np.abs(uS) ** (p - 2.0) * uS / r2p   # p|u|^{p-2}u/|d|^{2p}
+        cT = w * p * np.abs(uT) ** (p - 2.0) * uT / r2p
+        aT = a[None, :]
+        # forward role: E_ST = K(S,T) a_S a_T, derivative wrt X_S is +dK/dd
+        fwd = cS[..., None] * N[S][:, None, :] - (2.0 * p * KST / r2)[..., None] * d
+        # reverse role: E_TS = K(T,S) a_T a_S with d_TS = -d_ST and normal N_T;
+        # derivative wrt X_S is -dK/dd(d_TS) = cT N_T - 2p K(T,S) d_ST/|d|^2
+        rev = cT[..., None] * N[None, :, :] - (2.0 * p * KTS / r2)[..., None] * d
+        gX[c0:c0 + CHUNK] = a[S][:, None] * np.einsum("st,stk->sk", aT, fwd + rev)
+        gN[c0:c0 + CHUNK] = a[S][:, None] * np.einsum("st,stk->sk", aT * cS, d)
+        ga[c0:c0 + CHUNK] = (KST + KTS) @ a
+    return gX, gN, ga
+
+
+def faces_to_vertices(f, faces, gX, gN, ga, rows=None):
+    """Chain rule from face adjoints to vertex positions (§3.1).
+
+    X = (f_i+f_j+f_k)/3; n = (f_j-f_i) x (f_k-f_i); a = |n|/2; N = n/|n|.
+    dN = (I - N N^T) dn / |n|, da = N.dn / 2, so gN.dN + ga da = w.dn with
+    w = (I - N N^T) gN / |n| + ga N / 2, and dn = de1 x e2 + e1 x de2.
+    Returns the per-face corner gradients [nf,3,3] (rows: corners i,j,k).
+    """
+    F = faces if rows is None else faces[rows]
+    fi, fj, fk = f[F[:, 0]], f[F[:, 1]], f[F[:, 2]]
+    e1, e2 = fj - fi, fk - fi
+    n = np.cross(e1, e2)
+    nn = np.linalg.norm(n, axis=1)
+    N = n / nn[:, None]
+    tang = gN - np.sum(gN * N, axis=1, keepdims=True) * N
+    w = tang / nn[:, None] + 0.5 * ga[:, None] * N
+    gj = np.cross(e2, w)
+    gk = np.cross(w, e1)
+    gi = -(gj + gk)
+    third = gX / 3.0
+    return np.stack([gi + third, gj + third, gk + third], axis=1)
+
+
+def differential(f, faces, p=6.0):
+    """dE/df of Eq. 10, shape [nv,3]."""
+    gX, gN, ga = face_adjoints(f, faces, p)
+    corner = faces_to_vertices(f, faces, gX, gN, ga)
+    out = np.zeros_like(f)
+    for c in range(3):
+        np.add.at(out, faces[:, c], corner[:, c])
+    return out
+
+
+def differential_at_vertices(f, faces, verts, p=6.0):
+    """dE/df_v for a sample of vertices v, computed from the adjoints of the
+    faces incident to v only (for checks at sizes where the full sum is too
+    slow)."""
+    verts = np.asarray(verts)
+    out = np.zeros((len(verts), 3))
+    inc = [np.nonzero(np.any(faces == v, axis=1))[0] for v in verts]
+    rows = np.unique(np.concatenate(inc))
+    gX, gN, ga = face_adjoints(f, faces, p, rows)
+    corner = faces_to_vertices(f, faces, gX, gN, ga, rows)
+    pos = {int(r): i for i, r in enumerate(rows)}
+    for vi, v in enumerate(verts):
+        for S in inc[vi]:
+            c = int(np.nonzero(faces[S] == v)[0][0])
+            out[vi] += corner[pos[int(S)], c]
+    return out
+
+
+# ---------------------------------------------------------------------------
+# §3.2 discrete inner product: hat averages, discrete derivative D
+# ---------------------------------------------------------------------------
+
+def hat_average_matrix(faces, nv):
+    """F x V sparse matrix of bar-phi_i(S) = 1/3 if i is a vertex of S (§3.2)."""
+    nf = len(faces)
+    rows = np.repeat(np.arange(nf), 3)
+    return sp.csr_matrix((np.full(3 * nf, 1.0 / 3.0), (rows, faces.reshape(-1))),
+                         shape=(nf, nv))
+
+
+def hat_gradients(f, faces):
+    """Gradient of the hat function of each corner inside each face (the
+    discrete derivative D of §3.2.1, read as the piecewise-linear gradient):
+    grad phi_i |_S = N_S x e_i / (2 a_S), e_i the edge opposite corner i taken
+    counter-clockwise. Returns [nf, 3 corners, 3]."""
+    fi, fj, fk = f[faces[:, 0]], f[faces[:, 1]], f[faces[:, 2]]
+    X, N, a = face_geometry(f, faces)
+    e = np.stack([fk - fj, fi - fk, fj - fi], axis=1)
+    return np.cross(N[:, None, :], e) / (2.0 * a)[:, None, None]
+
+
+def D_apply(f, faces, v):
+    """(D v)(S) = sum_{i in S} v_i grad phi_i|_S; v [nv,k] -> [nf,3,k]."""
+    G = hat_gradients(f, faces)
+    return np.einsum("sci,sck->sik", G, v[faces])
+
+
+def D_transpose(f, faces, z, nv):
+    """D^T: per-face 3-vectors z [nf,3,k] -> vertices [nv,k]."""
+    G = hat_gradients(f, faces)
+    out = np.zeros((nv, z.shape[2]))
+    for c in range(3):
+        np.add.at(out, faces[:, c], np.einsum("si,sik->sk", G[:, c, :], z))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Algorithm 1 / Eq. 11-13: pairwise assembly of L^sigma, B, B0 (small meshes)
+# ---------------------------------------------------------------------------
+
+def assemble_pairwise(f, faces, kind, sigma, p=6.0):
+    """Dense |V|x|V| matrix by the pair loop of Algorithm 1 over ordered
+    distinct face pairs, with the summand of Eq. 11 (kind='L'), Eq. 12
+    ('B', vector-valued D phi differences) or Eq. 13 ('B0', extra factor
+    K_{f,2}(S,T)). The kernel denominator is |X_S - X_T|^{2 sigma + 2}."""
+    nv, nf = len(f), len(faces)
+    X, N, a = face_geometry(f, faces)
+    G = hat_gradients(f, faces)
+    M = np.zeros((nv, nv))
+    S, T = np.nonzero(~np.eye(nf, dtype=bool))
+    d = X[S] - X[T]
+    r2 = np.sum(d * d, axis=1)
+    w = a[S] * a[T] / r2 ** (sigma + 1.0)
+    if kind == "B0":
+        w = w * tp_kernel(X[S], N[S], X[T], 2.0)
+    idx = np.concatenate([faces[S], faces[T]], axis=1)          # [npairs, 6]
+    if kind in ("L", "B0"):
+        c = np.concatenate([np.full((len(S), 3), 1.0 / 3.0),
+                            np.full((len(S), 3), -1.0 / 3.0)], axis=1)
+        val = w[:, None, None] * c[:, :, None] * c[:, None, :]
+    elif kind == "B":
+        c = np.concatenate([G[S], -G[T]], axis=1)                # [npairs, 6, 3]
+        val = w[:, None, None] * np.einsum("pak,pbk->pab", c, c)
+    else:
+        raise ValueError(kind)
+    np.add.at(M, (np.repeat(idx, 6, axis=1).reshape(-1), np.tile(idx, (1, 6)).reshape(-1)),
+              val.reshape(-1))
+    return M
+
+
+# ---------------------------------------------------------------------------
+# §5.1.1-5.1.3 and Appendix A: kernel-matrix form of the operators
+# ---------------------------------------------------------------------------
+
+def _kernel_rows(X, N, S, kind, expo):
+    """Rows S of a kernel matrix H_ST = (1 - delta_ST) h(X_S, P_S; X_T, P_T)
+    with |d|^{-expo} singular part; kind 'plain' or 'low' (the symmetrised
+    k_2 factor of §5.1.3)."""
+    nf = len(X)
+    d = X[S, None, :] - X[None, :, :]
+    r2 = np.sum(d * d, axis=-1)
+    self_pair = S[:, None] == np.arange(nf)[None, :]
+    r2 = np.where(self_pair, 1.0, r2)
+    h = r2 ** (-0.5 * expo)
+    if kind == "low":
+        uS = np.einsum("sk,stk->st", N[S], d)
+        uT = np.einsum("tk,stk->st", N, d)
+        h = h * (uS * uS + uT * uT) / (2.0 * r2 * r2)
+    return np.where(self_pair, 0.0, h)
+
+
+def kernel_apply(X, N, a, W, kind, expo):
+    """z = [diag(diag(a)^-1 H a) - H] W for a per-face block W [nf, m]."""
+    nf = len(X)
+    z = np.empty_like(W)
+    for c0 in range(0, nf, CHUNK):
+        S = np.arange(c0, min(nf, c0 + CHUNK))
+        H = _kernel_rows(X, N, S, kind, expo)
+        r = (H @ a) / a[S]
+        z[S] = r[:, None] * W[S] - H @ W
+    return z
+
+
+def apply_operator(f, faces, v, op, p=6.0):
+    """y = O v for v [nv,k] (each column separately, i.e. O_3 on k columns).
+
+    op 'B'    high-order term, §5.1.2: 2 V^T [..] V v, V = diag(a) D,
+              kernel |d|^{-2s};
+    op 'B0'   low-order term, §5.1.3 (read with the face-average map U):
+              kernel (k_2(X,P;Y) + k_2(Y,Q;X)) / (2 |d|^{2s});
+    op 'A'    B + B0 (§2.4);
+    op 'L'    L^{2-s} of the preconditioner (§5.2), §5.1.1 with
+              sigma = 2 - s, kernel |d|^{-(2 sigma + 2)}.
+    """
+    nv = len(f)
+    X, N, a = face_geometry(f, faces)
+    s = sobolev_s(p)
+    Ubar = hat_average_matrix(faces, nv)
+    y = np.zeros_like(v)
+    if op in ("B", "A"):
+        W = a[:, None, None] * D_apply(f, faces, v)                 # V v, [nf,3,k]
+        nk = v.shape[1]
+        z = kernel_apply(X, N, a, W.reshape(len(faces), 3 * nk), "plain", 2.0 * s)
+        y += 2.0 * D_transpose(f, faces, a[:, None, None] * z.reshape(-1, 3, nk), nv)
+    if op in ("B0", "A"):
+        W = a[:, None] * (Ubar @ v)                                 # U v
+        z = kernel_apply(X, N, a, W, "low", 2.0 * s)
+        y += 2.0 * (Ubar.T @ (a[:, None] * z))
+    if op == "L":
+        sigma = 2.0 - s
+        W = a[:, None] * (Ubar @ v)
+        z = kernel_apply(X, N, a, W, "plain", 2.0 * sigma + 2.0)
+        y += 2.0 * (Ubar.T @ (a[:, None] * z))
+    return y
+
+
+def operator_matrix(f, faces, op, p=6.0):
+    """Dense |V|x|V| matrix of apply_operator (columns = applies to unit
+    vectors), for small meshes."""
+    nv = len(f)
+    return apply_operator(f, faces, np.eye(nv), op, p)
+
+
+# ---------------------------------------------------------------------------
+# §5.2 preconditioner: cotan Laplacian, Poisson solves, L^{2-s}
+# ---------------------------------------------------------------------------
+
+def cotan_laplacian(f, faces):
+    """Weak (stiffness) cotan Laplacian C of the mesh (§5.2): C_ij =
+    -1/2 (cot alpha_ij + cot beta_ij) for edges, C_ii = -sum_j C_ij."""
+    nv = len(f)
+    I, J, W = [], [], []
+    for c in range(3):
+        i, j, k = faces[:, c], faces[:, (c + 1) % 3], faces[:, (c + 2) % 3]
+        u, w = f[i] - f[k], f[j] - f[k]
+        cot = np.sum(u * w, axis=1) / np.linalg.norm(np.cross(u, w), axis=1)
+        I += [i, j]
+        J += [j, i]
+        W += [-0.5 * cot, -0.5 * cot]
+    I, J, W = np.concatenate(I), np.concatenate(J), np.concatenate(W)
+    off = sp.csr_matrix((W, (I, J)), shape=(nv, nv))
+    diag = -np.asarray(off.sum(axis=1)).ravel()
+    return (off + sp.diags(diag)).tocsr()
+
+
+def project_mean_zero(b):
+    """Remove the constant component of each column (the nullspace of C and
+    of the fractional operators)."""
+    return b - b.mean(axis=0, keepdims=True)
+
+
+def poisson_solve(C, b):
+    """Solve C z = b in the mean-zero subspace (exact sparse direct solve:
+    the system with the first vertex's row and column removed, then the
+    mean removed). b [nv,k]."""
+    b = project_mean_zero(b)
+    Cr = C[1:, 1:].tocsc()
+    z = np.zeros_like(b)
+    lu = spla.splu(Cr)
+    for c in range(b.shape[1]):
+        z[1:, c] = lu.solve(b[1:, c])
+    return project_mean_zero(z)
+
+
+def precond_apply(f, faces, b, p=6.0):
+    """Preconditioner of §5.2: C^+ L^{2-s} C^+ b (the two integer Laplacians
+    are the cotan stiffness matrix; all vectors kept mean-zero)."""
+    C = cotan_laplacian(f, faces)
+    z = poisson_solve(C, b)
+    z = project_mean_zero(apply_operator(f, faces, z, "L", p))
+    return poisson_solve(C, z)
+
+
+# ---------------------------------------------------------------------------
+# §7.1 constraints
+# ---------------------------------------------------------------------------
+
+def total_area(f, faces):
+    """sum_T a_f(T) (§7.1.3)."""
+    return float(np.sum(face_geometry(f, faces)[2]))
+
+
+def area_gradient(f, faces):
+    """d(total area)/df_i = 1/2 sum_{S ni i} N_S x e_i (§7.1.3)."""
+    fi, fj, fk = f[faces[:, 0]], f[faces[:, 1]], f[faces[:, 2]]
+    N = face_geometry(f, faces)[1]
+    out = np.zeros_like(f)
+    for c, e in enumerate((fk - fj, fi - fk, fj - fi)):
+        np.add.at(out, faces[:, c], 0.5 * np.cross(N, e))
+    return out
+
+
+def total_volume(f, faces):
+    """(1/6) sum_{ijk} f_i . (f_j x f_k) (§7.1.4)."""
+    fi, fj, fk = f[faces[:, 0]], f[faces[:, 1]], f[faces[:, 2]]
+    return float(np.sum(fi * np.cross(fj, fk)) / 6.0)
+
+
+def volume_gradient(f, faces):
+    """d(volume)/df_i = (1/6) sum_{(i,j,k) in F} f_j x f_k (§7.1.4)."""
+    out = np.zeros_like(f)
+    for c in range(3):
+        i, j, k = faces[:, c], faces[:, (c + 1) % 3], faces[:, (c + 2) % 3]
+        np.add.at(out, i, np.cross(f[j], f[k]) / 6.0)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# §3.3 and §5.3: constrained descent direction, line search, projection
+# ---------------------------------------------------------------------------
+
+def _constraint_rows(f, faces, use_area, use_volume):
+    rows = []
+    if use_area:
+        rows.append(area_gradient(f, faces).reshape(-1))
+    if use_volume:
+        rows.append(volume_gradient(f, faces).reshape(-1))
+    return np.array(rows).reshape(len(rows), -1)
+
+
+def _barycenter_rows(nv):
+    """Jacobian of the fixed-barycenter constraint read as |V| copies of I_3
+    (§7.1.1), one row per coordinate, in the [nv,3] row-major ordering."""
+    J = np.zeros((3, 3 * nv))
+    for c in range(3):
+        J[c, c::3] = 1.0
+    return J
+
+
+def saddle_matrix(f, faces, use_area=True, use_volume=True, p=6.0):
+    """[A_3 dPhi^T; dPhi 0] of Eq. 14 with the barycenter rows (§7.1.1) plus
+    area and volume rows; A_3 = A (x) I_3 on the [nv,3] ordering."""
+    nv = len(f)
+    A = operator_matrix(f, faces, "A", p)
+    A3 = np.kron(A, np.eye(3))
+    J = np.concatenate([_barycenter_rows(nv),
+                        _constraint_rows(f, faces, use_area, use_volume)], axis=0)
+    m = J.shape[0]
+    M = np.zeros((3 * nv + m, 3 * nv + m))
+    M[:3 * nv, :3 * nv] = A3
+    M[:3 * nv, 3 * nv:] = J.T
+    M[3 * nv:, :3 * nv] = J
+    return M, J
+
+
+def descent_direction(f, faces, use_area=True, use_volume=True, p=6.0):
+    """x of Eq. 14: [A_3 dPhi^T; dPhi 0][x; lambda] = [-dE; 0], solved
+    densely. Returns (x [nv,3], g = dE [nv,3])."""
+    nv = len(f)
+    g = differential(f, faces, p)
+    M, J = saddle_matrix(f, faces, use_area, use_volume, p)
+    rhs = np.zeros(M.shape[0])
+    rhs[:3 * nv] = -g.reshape(-1)
+    sol = np.linalg.solve(M, rhs)
+    return sol[:3 * nv].reshape(nv, 3), g
+
+
+def schur_direction(f, faces, use_area=True, use_volume=True, p=6.0):
+    """The same direction via the Schur complement of §5.3 (Eq. 17, Eq. 18)
+    with A_3^{-1} applied in the mean-zero subspace (where the barycenter
+    rows are satisfied), g = dE, Z = A_3^{-1} dPhi^T:
+        x = -(A^{-1} g - Z (dPhi Z)^{-1} dPhi A^{-1} g)."""
+    nv = len(f)
+    g = differential(f, faces, p)
+    A = operator_matrix(f, faces, "A", p)
+    P = np.eye(nv) - np.full((nv, nv), 1.0 / nv)
+    Ainv = np.linalg.pinv(P @ A @ P)
+    Ainv3 = lambda w: (Ainv @ project_mean_zero(w.reshape(nv, 3))).reshape(-1)
+    J = _constraint_rows(f, faces, use_area, use_volume)
+    Ag = Ainv3(g.reshape(-1))
+    Z = np.stack([Ainv3(row) for row in J], axis=1)
+    S = J @ Z                                   # -(M/A), Eq. 17
+    x = -(Ag - Z @ np.linalg.solve(S, J @ Ag))
+    return x.reshape(nv, 3), Z, S
+
+
+def constraint_values(f, faces, A0, V0, use_area=True, use_volume=True):
+    vals = []
+    if use_area:
+        vals.append(total_area(f, faces) - A0)
+    if use_volume:
+        vals.append(total_volume(f, faces) - V0)
+    return np.array(vals)
+
+
+def precond_step(f, faces, A0, V0, use_area=True, use_volume=True, p=6.0,
+                 tau0=1.0, armijo_c=1e-4, shrink=0.5, ls_max=30, fixed_tau=None):
+    """One constrained descent step (§3, steps 1-5; §5.4 with exact solves):
+    direction by Eq. 14, Armijo backtracking from tau0 (E(f + tau x) <=
+    E(f) + c tau dE.x), then one corrective projection by Eq. 15 with the
+    constraint Jacobian taken at f and Phi evaluated at f + tau x.
+    Returns dict(f_new, x, tau, E0, E1, h)."""
+    nv = len(f)
+    x, g = descent_direction(f, faces, use_area, use_volume, p)
+    E0 = energy(f, faces, p)
+    slope = float(np.sum(g * x))
+    if fixed_tau is not None:
+        tau = fixed_tau
+    else:
+        tau = tau0
+        for _ in range(ls_max):
+            if energy(f + tau * x, faces, p) <= E0 + armijo_c * tau * slope:
+                break
+            tau *= shrink
+    f1 = f + tau * x
+    M, J = saddle_matrix(f, faces, use_area, use_volume, p)
+    rhs = np.zeros(M.shape[0])
+    phi = constraint_values(f1, faces, A0, V0, use_area, use_volume)
+    rhs[3 * nv + 3:] = -phi
+    h = np.linalg.solve(M, rhs)[:3 * nv].reshape(nv, 3)
+    f2 = f1 + h
+    return dict(f_new=f2, x=x, tau=tau, E0=E0, E1=energy(f2, faces, p), h=h, slope=slope)
