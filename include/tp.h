@@ -1,0 +1,212 @@
+/*
+ * tp.h -- C ABI of the GB300 tangent-point surface-flow library (libtpsurf).
+ *
+ * The library evaluates the hot path of "Repulsive Surfaces" (Yu,
+ * Brakensiek, Schumacher, Crane 2021) on one GPU:
+ *   - the discrete tangent-point energy E (§3.1, Eq. 9-10) and its
+ *     differential dE (§3.1, chain rule),
+ *   - the forward application of the fractional operators B, B0, A = B + B0
+ *     (§3.2, §5.1.2-5.1.3, Appendix A) and L^{2-s} (§5.1.1, §5.2),
+ *   - Barnes-Hut approximations of E and dE over a GPU-built BVH (§4),
+ *   - the cotan-Laplacian Poisson solves of the preconditioner by CG (§5.2),
+ *   - the constrained preconditioned descent step (§3.3, §5.3, §5.4).
+ *
+ * Conventions shared by every call:
+ *   - Return value: TP_OK (0) or one of the TP_ERR_* codes. On error the
+ *     outputs are unspecified and tp_last_error() (thread-local) describes it.
+ *   - Positions are float64 [nv][3] row-major (x,y,z per vertex); faces are
+ *     int32 [nf][3], counter-clockwise, 0-based, every face non-degenerate.
+ *   - Vertex vectors v, y, b, z with k columns are float64 [nv][k] row-major.
+ *   - ptr_kind says whether the array arguments of a call are host memory
+ *     (TP_PTR_HOST; copied synchronously on `stream`) or device memory of
+ *     the mesh's GPU (TP_PTR_DEVICE; must stay valid until `stream` has
+ *     passed the call).
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream). Calls that
+ *     return host scalars synchronise `stream` before returning.
+ *   - The caller owns every array it passes; the library owns the state of a
+ *     tp_mesh (positions, face tables, BVH, CSR Laplacian, workspaces) and
+ *     frees it in tp_mesh_destroy. A tp_mesh must be used by one host thread
+ *     at a time.
+ */
+#ifndef TP_H
+#define TP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define TP_OK                 0
+#define TP_ERR_INVALID_ARG    1  /* null pointer, bad size, index out of range, bad enum */
+#define TP_ERR_DEGENERATE     2  /* zero-area face or non-finite position */
+#define TP_ERR_OOM            3  /* device allocation failed */
+#define TP_ERR_NOT_CONVERGED  4  /* CG or Krylov solver hit its iteration cap */
+#define TP_ERR_TIMEOUT        5  /* a bounded device-side wait gave up */
+#define TP_ERR_CUDA           6  /* any other CUDA runtime error */
+
+/* ptr_kind */
+#define TP_PTR_HOST   0
+#define TP_PTR_DEVICE 1
+
+/* precision of the pair terms */
+#define TP_PREC_FP32  0  /* FP32 pair terms, compensated FP32 sums, FP64 final reduction */
+#define TP_PREC_FP64  1  /* plain FP64 pair terms */
+
+/* operators of fractional_apply */
+#define TP_OP_A   0  /* A = B + B0, the H^s inner product (§2.4, §5.1.2-5.1.3) */
+#define TP_OP_B   1  /* high-order term B, kernel |d|^{-2s} (§5.1.2)            */
+#define TP_OP_B0  2  /* low-order term B0, kernel (k2(S;T)+k2(T;S))/(2|d|^{2s}) (§5.1.3) */
+#define TP_OP_L   3  /* L^{2-s} of the preconditioner, kernel |d|^{-(6-2s)} (§5.1.1, §5.2) */
+
+/* Barnes-Hut differential modes (§4.2) */
+#define TP_BH_DIFF_FULL     0  /* forward terms plus node-level reverse terms pushed to faces */
+#define TP_BH_DIFF_LITERAL  1  /* only the terms in which the face is the target S */
+
+/* constraint flags (the barycenter constraint of §7.1.1 is always on) */
+#define TP_CONSTRAINT_AREA    1  /* total area, §7.1.3 */
+#define TP_CONSTRAINT_VOLUME  2  /* total signed volume, §7.1.4 */
+
+typedef struct tp_params {
+    double p;             /* tangent-point exponent p (numerator |P d|^p, denominator |d|^{2p}); paper default 6 (§2.1) */
+    double theta;         /* Barnes-Hut separation theta; 0 = exact all-pairs sums (§4.1) */
+    int    leaf_size;     /* BVH leaf size l, 1..32; paper default 8 (§4.1) */
+    int    precision;     /* TP_PREC_FP32 or TP_PREC_FP64 */
+    int    bh_diff_mode;  /* TP_BH_DIFF_FULL or TP_BH_DIFF_LITERAL */
+    int    bh_apply;      /* 1 = Barnes-Hut traversal also for fractional_apply when theta > 0 */
+    double krylov_tol;    /* relative residual of the outer GMRES solves */
+    int    krylov_max;    /* iteration cap of one GMRES solve (all restarts) */
+    int    gmres_restart; /* restart length m */
+    double cg_tol;        /* relative residual of the Poisson CG solves */
+    int    cg_max;        /* iteration cap of one CG solve */
+    double armijo_c;      /* sufficient-decrease constant of the line search */
+    double armijo_shrink; /* step shrink factor */
+    double tau0;          /* initial step */
+    int    ls_max;        /* maximum line-search trials */
+    int    fixed_tau;     /* 1 = take tau0 without line search */
+    int    proj_iters;    /* corrective projections per step (§3.3.2: one suffices; repeats allowed) */
+} tp_params;
+
+typedef struct tp_constraints {
+    int    flags;   /* TP_CONSTRAINT_AREA | TP_CONSTRAINT_VOLUME */
+    double A0;      /* target total area   */
+    double V0;      /* target total volume */
+} tp_constraints;
+
+typedef struct tp_step_report {
+    double E_before;       /* E(f) */
+    double E_after;        /* E(f_new) */
+    double tau;            /* accepted step */
+    double slope;          /* dE . x (negative for a descent direction) */
+    double phi_before[2];  /* constraint values at f + tau x (area, volume) */
+    double phi_after[2];   /* constraint values at f_new */
+    int    krylov_iters;   /* total GMRES iterations of the step */
+    int    cg_iters;       /* total CG iterations of the step */
+    int    ls_trials;      /* energy evaluations of the line search */
+    int    status;         /* TP_OK or the first non-fatal solver status */
+    double pair_interactions; /* (target, source) terms evaluated during the step */
+} tp_step_report;
+
+/* Per-kernel statistics of a mesh (tp_profile_read). `units` is the
+ * algorithmic work of the launches: pair interactions for the pair and
+ * Barnes-Hut kernels, bytes of matrix and vector traffic for CG. */
+typedef struct tp_kernel_stat {
+    char      name[32];
+    long long launches;
+    double    ms;        /* summed CUDA-event durations (0 unless profiling is on) */
+    double    units;
+} tp_kernel_stat;
+
+typedef struct tp_mesh tp_mesh;
+
+/* Fill *p with the defaults: p=6, theta=0, leaf_size=8, FP32 pairs,
+ * full BH differential, krylov_tol=1e-6, krylov_max=200, restart 30,
+ * cg_tol=1e-10, cg_max=20000, Armijo c=1e-4, shrink 0.5, tau0=1, ls_max=30,
+ * proj_iters=1. */
+void tp_params_default(tp_params* p);
+
+/* Create a mesh on CUDA device `device` from nv positions and nf faces.
+ * Validates the face indices (TP_ERR_INVALID_ARG) and the geometry
+ * (TP_ERR_DEGENERATE). Allocates all device state of the mesh. */
+int tp_mesh_create(int device, int nv, int nf, const double* pos,
+                   const int32_t* faces, int ptr_kind, void* stream,
+                   tp_mesh** out);
+
+/* Replace the positions (same topology) and refresh the face tables. */
+int tp_mesh_set_positions(tp_mesh* m, const double* pos, int ptr_kind, void* stream);
+
+/* Copy the current positions (float64 [nv][3]) out. */
+int tp_mesh_get_positions(tp_mesh* m, double* pos, int ptr_kind, void* stream);
+
+/* Free every device resource of the mesh. Accepts NULL. */
+int tp_mesh_destroy(tp_mesh* m);
+
+/* Device bytes a mesh of this size holds, for admission control. */
+size_t tp_mesh_footprint_bytes(int nv, int nf, const tp_params* p);
+
+/* Discrete tangent-point energy E (§3.1, Eq. 10; ordered pairs S != T),
+ * or its Barnes-Hut approximation (§4.1, Eq. 16) when theta > 0.
+ * *E_out is a host double. */
+int tp_energy(tp_mesh* m, const tp_params* p, double* E_out, void* stream);
+
+/* Row sums E_S = sum_{T != S} K(S,T) a_S a_T of Eq. 10 (or of Eq. 16 when
+ * theta > 0) for n target faces `targets` (int32); rows is float64 [n]. */
+int tp_energy_rows(tp_mesh* m, const tp_params* p, const int32_t* targets, int n,
+                   double* rows, int ptr_kind, void* stream);
+
+/* Differential dE/df (float64 [nv][3]) of Eq. 10 by the chain rule through
+ * the face barycenters, normals and areas (§3.1); with theta > 0 the
+ * Barnes-Hut derivative of §4.2 (mode bh_diff_mode). E_out (host, may be
+ * NULL) receives the energy of the same pass. */
+int tp_differential(tp_mesh* m, const tp_params* p, double* dE, int ptr_kind,
+                    double* E_out, void* stream);
+
+/* y = O v for op in TP_OP_* and k columns (1 <= k <= 9), each column
+ * separately (the vector operator O_3 of §3.2.1 for k = 3), through the
+ * kernel-matrix form of §5.1.1-5.1.3 and Appendix A:
+ *   O v = 2 W^T [diag(diag(a)^-1 H a) - H] W v,
+ * W = diag(a) D (op B) or the area-weighted face average (ops B0, L). */
+int fractional_apply(tp_mesh* m, const tp_params* p, int op, const double* v,
+                     int k, double* y, int ptr_kind, void* stream);
+
+/* z = C^+ b: Jacobi-preconditioned CG on the cotan stiffness matrix C of
+ * the current positions (§5.2), k columns (1 <= k <= 9), right-hand side
+ * and solution projected to zero mean. *iters_out (host, may be NULL)
+ * receives the iteration count. TP_ERR_NOT_CONVERGED if cg_max is hit. */
+int cotan_solve(tp_mesh* m, const tp_params* p, const double* b, int k, double* z,
+                int ptr_kind, void* stream, int* iters_out);
+
+/* z = C^+ L^{2-s} C^+ b, the preconditioner of §5.2, k columns. */
+int precond_apply(tp_mesh* m, const tp_params* p, const double* b, int k,
+                  double* z, int ptr_kind, void* stream);
+
+/* One constrained descent step (§5.4): dE, the Schur-complement solution
+ * of the saddle problem (Eq. 14, 17, 18) with GMRES on A_3 preconditioned
+ * by precond_apply, Armijo line search, and proj_iters corrective
+ * projections (Eq. 15, 19) with the constraint Jacobian of the start of the
+ * step. Updates the mesh positions in place. rep may be NULL. */
+int precond_step(tp_mesh* m, const tp_params* p, const tp_constraints* c,
+                 tp_step_report* rep, void* stream);
+
+/* Turn per-launch CUDA-event timing of the pair, Barnes-Hut and CG kernels
+ * of this mesh on (1) or off (0). Events are recorded on the launching
+ * stream; launches and units are counted whether or not timing is on. */
+int tp_profile_enable(tp_mesh* m, int on);
+
+/* Copy up to `max` per-kernel statistics (accumulated since the last read)
+ * into out, set *n to the number written, and reset them. Synchronises
+ * with the recorded events. */
+int tp_profile_read(tp_mesh* m, tp_kernel_stat* out, int max, int* n);
+
+/* Number of CUDA kernels this library has launched in this process. */
+unsigned long long tp_launch_count(void);
+
+/* Thread-local description of the last error of this thread ("" if none). */
+const char* tp_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TP_H */

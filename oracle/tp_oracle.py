@@ -489,11 +489,12 @@ def constraint_values(f, faces, A0, V0, use_area=True, use_volume=True):
 
 
 def precond_step(f, faces, A0, V0, use_area=True, use_volume=True, p=6.0,
-                 tau0=1.0, armijo_c=1e-4, shrink=0.5, ls_max=30, fixed_tau=None):
+                 tau0=1.0, armijo_c=1e-4, shrink=0.5, ls_max=30, fixed_tau=None, proj_iters=1):
     """One constrained descent step (§3, steps 1-5; §5.4 with exact solves):
     direction by Eq. 14, Armijo backtracking from tau0 (E(f + tau x) <=
-    E(f) + c tau dE.x), then one corrective projection by Eq. 15 with the
-    constraint Jacobian taken at f and Phi evaluated at f + tau x.
+    E(f) + c tau dE.x), then corrective projections by Eq. 15 with the
+    left-hand side of Eq. 14 (Jacobian at f) and Phi at the current point;
+    §3.3.2 says one suffices and allows repeats (proj_iters).
     Returns dict(f_new, x, tau, E0, E1, h)."""
     nv = len(f)
     x, g = descent_direction(f, faces, use_area, use_volume, p)
@@ -509,9 +510,50 @@ def precond_step(f, faces, A0, V0, use_area=True, use_volume=True, p=6.0,
             tau *= shrink
     f1 = f + tau * x
     M, J = saddle_matrix(f, faces, use_area, use_volume, p)
-    rhs = np.zeros(M.shape[0])
-    phi = constraint_values(f1, faces, A0, V0, use_area, use_volume)
-    rhs[3 * nv + 3:] = -phi
-    h = np.linalg.solve(M, rhs)[:3 * nv].reshape(nv, 3)
-    f2 = f1 + h
+    f2 = f1
+    h = np.zeros_like(f)
+    for _ in range(proj_iters):
+        rhs = np.zeros(M.shape[0])
+        rhs[3 * nv + 3:] = -constraint_values(f2, faces, A0, V0, use_area, use_volume)
+        dh = np.linalg.solve(M, rhs)[:3 * nv].reshape(nv, 3)
+        f2 = f2 + dh
+        h = h + dh
     return dict(f_new=f2, x=x, tau=tau, E0=E0, E1=energy(f2, faces, p), h=h, slope=slope)
+
+
+def apply_operator_at_vertices(f, faces, v, op, verts, p=6.0):
+    """Rows y[verts] of apply_operator, with the kernel-matrix rows computed
+    only for the faces incident to those vertices (for checks at sizes where
+    the full product is too slow). Same formulas as apply_operator."""
+    nv = len(f)
+    verts = np.asarray(verts)
+    X, N, a = face_geometry(f, faces)
+    s = sobolev_s(p)
+    G = hat_gradients(f, faces)
+    vbar = (v[faces[:, 0]] + v[faces[:, 1]] + v[faces[:, 2]]) / 3.0        # [nf,k]
+    inc = [np.nonzero(np.any(faces == u, axis=1))[0] for u in verts]
+    rows = np.unique(np.concatenate(inc))
+    pos = {int(r): i for i, r in enumerate(rows)}
+    zV = zU = None
+    if op in ("B", "A"):
+        W = a[:, None, None] * D_apply(f, faces, v)
+        Wf = W.reshape(len(faces), -1)
+        H = _kernel_rows(X, N, rows, "plain", 2.0 * s)
+        zV = (((H @ a) / a[rows])[:, None] * Wf[rows] - H @ Wf).reshape(len(rows), 3, -1)
+    if op in ("B0", "A", "L"):
+        W = a[:, None] * vbar
+        if op == "L":
+            H = _kernel_rows(X, N, rows, "plain", 2.0 * (2.0 - s) + 2.0)
+        else:
+            H = _kernel_rows(X, N, rows, "low", 2.0 * s)
+        zU = ((H @ a) / a[rows])[:, None] * W[rows] - H @ W
+    out = np.zeros((len(verts), v.shape[1]))
+    for vi, u in enumerate(verts):
+        for S in inc[vi]:
+            c = int(np.nonzero(faces[S] == u)[0][0])
+            r = pos[int(S)]
+            if zV is not None:
+                out[vi] += 2.0 * a[S] * np.einsum("i,ik->k", G[S, c], zV[r])
+            if zU is not None:
+                out[vi] += 2.0 * a[S] * zU[r] / 3.0
+    return out

@@ -1,0 +1,376 @@
+"""Python binding of libtpsurf, the GB300 tangent-point surface-flow library.
+
+A thin ctypes layer over the C ABI of include/tp.h: the functions have the
+same names and do argument marshalling only. Every step of the computation
+runs in the library's CUDA kernels; there is no CPU or PyTorch fallback, and
+importing this package fails loudly when the compiled library is missing.
+
+Arrays may be numpy arrays or CPU tensors (host memory) or CUDA tensors
+(device memory of the mesh's GPU). Results come back in the same kind of
+memory as the input; CUDA work is queued on torch's current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "TP_OK", "TP_OP_A", "TP_OP_B", "TP_OP_B0", "TP_OP_L", "TP_PREC_FP32", "TP_PREC_FP64",
+    "TP_CONSTRAINT_AREA", "TP_CONSTRAINT_VOLUME", "TP_BH_DIFF_FULL", "TP_BH_DIFF_LITERAL",
+    "TpError", "tp_params", "tp_constraints", "tp_step_report", "params", "Mesh",
+    "tp_mesh_create", "tp_mesh_set_positions", "tp_mesh_get_positions", "tp_mesh_destroy",
+    "tp_mesh_footprint_bytes", "tp_energy", "tp_energy_rows", "tp_differential",
+    "fractional_apply", "cotan_solve", "precond_apply", "precond_step", "TangentPointEnergy",
+    "lib_path", "lib", "tp_kernel_stat", "tp_profile_enable", "tp_profile_read", "tp_launch_count",
+]
+
+TP_OK, TP_ERR_INVALID_ARG, TP_ERR_DEGENERATE, TP_ERR_OOM = 0, 1, 2, 3
+TP_ERR_NOT_CONVERGED, TP_ERR_TIMEOUT, TP_ERR_CUDA = 4, 5, 6
+TP_PTR_HOST, TP_PTR_DEVICE = 0, 1
+TP_PREC_FP32, TP_PREC_FP64 = 0, 1
+TP_OP_A, TP_OP_B, TP_OP_B0, TP_OP_L = 0, 1, 2, 3
+TP_BH_DIFF_FULL, TP_BH_DIFF_LITERAL = 0, 1
+TP_CONSTRAINT_AREA, TP_CONSTRAINT_VOLUME = 1, 2
+_OPS = {"A": TP_OP_A, "B": TP_OP_B, "B0": TP_OP_B0, "L": TP_OP_L}
+
+
+class TpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"tp status {code}: {msg}")
+        self.code = code
+
+
+class tp_params(ctypes.Structure):
+    _fields_ = [
+        ("p", ctypes.c_double), ("theta", ctypes.c_double), ("leaf_size", ctypes.c_int),
+        ("precision", ctypes.c_int), ("bh_diff_mode", ctypes.c_int), ("bh_apply", ctypes.c_int),
+        ("krylov_tol", ctypes.c_double), ("krylov_max", ctypes.c_int), ("gmres_restart", ctypes.c_int),
+        ("cg_tol", ctypes.c_double), ("cg_max", ctypes.c_int), ("armijo_c", ctypes.c_double),
+        ("armijo_shrink", ctypes.c_double), ("tau0", ctypes.c_double), ("ls_max", ctypes.c_int),
+        ("fixed_tau", ctypes.c_int), ("proj_iters", ctypes.c_int),
+    ]
+
+
+class tp_constraints(ctypes.Structure):
+    _fields_ = [("flags", ctypes.c_int), ("A0", ctypes.c_double), ("V0", ctypes.c_double)]
+
+
+class tp_step_report(ctypes.Structure):
+    _fields_ = [
+        ("E_before", ctypes.c_double), ("E_after", ctypes.c_double), ("tau", ctypes.c_double),
+        ("slope", ctypes.c_double), ("phi_before", ctypes.c_double * 2),
+        ("phi_after", ctypes.c_double * 2), ("krylov_iters", ctypes.c_int),
+        ("cg_iters", ctypes.c_int), ("ls_trials", ctypes.c_int), ("status", ctypes.c_int),
+        ("pair_interactions", ctypes.c_double),
+    ]
+
+
+class tp_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double),
+                ("units", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """The loaded libtpsurf (ctypes.CDLL); raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        raise ImportError(f"libtpsurf.so is not built ({path}); run "
+                          "python -c 'import __graft_entry__ as g; g.build()'")
+    L = ctypes.CDLL(path)
+    c_int, c_double, vp, c_size = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+    P = ctypes.POINTER
+    sig = {
+        "tp_params_default": (None, [P(tp_params)]),
+        "tp_mesh_create": (c_int, [c_int, c_int, c_int, vp, vp, c_int, vp, P(vp)]),
+        "tp_mesh_set_positions": (c_int, [vp, vp, c_int, vp]),
+        "tp_mesh_get_positions": (c_int, [vp, vp, c_int, vp]),
+        "tp_mesh_destroy": (c_int, [vp]),
+        "tp_mesh_footprint_bytes": (c_size, [c_int, c_int, P(tp_params)]),
+        "tp_energy": (c_int, [vp, P(tp_params), P(c_double), vp]),
+        "tp_energy_rows": (c_int, [vp, P(tp_params), vp, c_int, vp, c_int, vp]),
+        "tp_differential": (c_int, [vp, P(tp_params), vp, c_int, P(c_double), vp]),
+        "fractional_apply": (c_int, [vp, P(tp_params), c_int, vp, c_int, vp, c_int, vp]),
+        "cotan_solve": (c_int, [vp, P(tp_params), vp, c_int, vp, c_int, vp, P(c_int)]),
+        "precond_apply": (c_int, [vp, P(tp_params), vp, c_int, vp, c_int, vp]),
+        "precond_step": (c_int, [vp, P(tp_params), P(tp_constraints), P(tp_step_report), vp]),
+        "tp_last_error": (ctypes.c_char_p, []),
+        "tp_profile_enable": (c_int, [vp, c_int]),
+        "tp_profile_read": (c_int, [vp, P(tp_kernel_stat), c_int, P(c_int)]),
+        "tp_launch_count": (ctypes.c_ulonglong, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(code):
+    if code != TP_OK:
+        raise TpError(code, lib().tp_last_error().decode())
+
+
+def params(**overrides) -> tp_params:
+    """tp_params with the library defaults and the given fields replaced."""
+    p = tp_params()
+    lib().tp_params_default(ctypes.byref(p))
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(f"tp_params has no field {k}")
+        setattr(p, k, v)
+    return p
+
+
+# ---------------------------------------------------------------------------
+# array marshalling
+# ---------------------------------------------------------------------------
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and x.is_cuda
+
+
+def _stream_ptr(x=None):
+    if x is None or not _is_cuda(x):
+        try:
+            torch = _torch()
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return ctypes.c_void_p(0)
+    return ctypes.c_void_p(_torch().cuda.current_stream(x.device).cuda_stream)
+
+
+def _as_buffer(x, dtype):
+    """(pointer, kind, keepalive) of a contiguous array of the given numpy dtype."""
+    if _is_cuda(x):
+        torch = _torch()
+        tdt = {np.float64: torch.float64, np.int32: torch.int32}[dtype]
+        t = x.to(tdt).contiguous()
+        return ctypes.c_void_p(t.data_ptr()), TP_PTR_DEVICE, t
+    if hasattr(x, "numpy"):
+        x = x.detach().cpu().numpy()
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return ctypes.c_void_p(a.ctypes.data), TP_PTR_HOST, a
+
+
+def _empty_like_kind(ref, shape, dtype=np.float64):
+    if _is_cuda(ref):
+        torch = _torch()
+        t = torch.empty(shape, dtype=torch.float64, device=ref.device)
+        return t, ctypes.c_void_p(t.data_ptr()), TP_PTR_DEVICE
+    a = np.empty(shape, dtype=dtype)
+    return a, ctypes.c_void_p(a.ctypes.data), TP_PTR_HOST
+
+
+# ---------------------------------------------------------------------------
+# C ABI, same names
+# ---------------------------------------------------------------------------
+
+class Mesh:
+    """Owns a tp_mesh handle (positions, face tables, BVH, Laplacian on the GPU)."""
+
+    def __init__(self, positions, faces, device: int = 0):
+        self.handle = tp_mesh_create(positions, faces, device)
+        self.nv = int(np.shape(positions)[0])
+        self.nf = int(np.shape(faces)[0])
+        self.device = device
+
+    def set_positions(self, positions):
+        tp_mesh_set_positions(self, positions)
+
+    def get_positions(self, like=None):
+        return tp_mesh_get_positions(self, like)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().tp_mesh_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def tp_mesh_create(positions, faces, device: int = 0):
+    pp, pk, keep_p = _as_buffer(positions, np.float64)
+    fp, fk, keep_f = _as_buffer(faces, np.int32)
+    if pk != fk:
+        raise ValueError("positions and faces must both be host or both be device arrays")
+    h = ctypes.c_void_p()
+    nv, nf = int(np.shape(positions)[0]), int(np.shape(faces)[0])
+    _check(lib().tp_mesh_create(device, nv, nf, pp, fp, pk, _stream_ptr(positions), ctypes.byref(h)))
+    return h
+
+
+def tp_mesh_set_positions(mesh: Mesh, positions):
+    pp, pk, keep = _as_buffer(positions, np.float64)
+    _check(lib().tp_mesh_set_positions(mesh.handle, pp, pk, _stream_ptr(positions)))
+
+
+def tp_mesh_get_positions(mesh: Mesh, like=None):
+    out, ptr, kind = _empty_like_kind(like, (mesh.nv, 3))
+    _check(lib().tp_mesh_get_positions(mesh.handle, ptr, kind, _stream_ptr(like)))
+    return out
+
+
+def tp_mesh_destroy(mesh: Mesh):
+    mesh.close()
+
+
+def tp_mesh_footprint_bytes(nv: int, nf: int, p: tp_params | None = None) -> int:
+    p = p or params()
+    return int(lib().tp_mesh_footprint_bytes(nv, nf, ctypes.byref(p)))
+
+
+def tp_energy(mesh: Mesh, p: tp_params | None = None) -> float:
+    p = p or params()
+    E = ctypes.c_double()
+    _check(lib().tp_energy(mesh.handle, ctypes.byref(p), ctypes.byref(E), _stream_ptr()))
+    return E.value
+
+
+def tp_energy_rows(mesh: Mesh, targets, p: tp_params | None = None):
+    p = p or params()
+    tp_, tk, keep = _as_buffer(targets, np.int32)
+    n = int(np.shape(targets)[0])
+    out, ptr, kind = _empty_like_kind(targets, (n,))
+    _check(lib().tp_energy_rows(mesh.handle, ctypes.byref(p), tp_, n, ptr, kind, _stream_ptr(targets)))
+    return out
+
+
+def tp_differential(mesh: Mesh, p: tp_params | None = None, like=None):
+    """(dE [nv,3], E); dE in the memory kind of `like` (host by default)."""
+    p = p or params()
+    out, ptr, kind = _empty_like_kind(like, (mesh.nv, 3))
+    E = ctypes.c_double()
+    _check(lib().tp_differential(mesh.handle, ctypes.byref(p), ptr, kind, ctypes.byref(E), _stream_ptr(like)))
+    return out, E.value
+
+
+def fractional_apply(mesh: Mesh, op, v, p: tp_params | None = None):
+    p = p or params()
+    op = _OPS.get(op, op)
+    vp, vk, keep = _as_buffer(v, np.float64)
+    k = 1 if len(np.shape(v)) == 1 else int(np.shape(v)[1])
+    out, ptr, kind = _empty_like_kind(v, tuple(np.shape(v)))
+    _check(lib().fractional_apply(mesh.handle, ctypes.byref(p), int(op), vp, k, ptr, vk, _stream_ptr(v)))
+    return out
+
+
+def cotan_solve(mesh: Mesh, b, p: tp_params | None = None):
+    p = p or params()
+    bp, bk, keep = _as_buffer(b, np.float64)
+    k = 1 if len(np.shape(b)) == 1 else int(np.shape(b)[1])
+    out, ptr, kind = _empty_like_kind(b, tuple(np.shape(b)))
+    it = ctypes.c_int()
+    _check(lib().cotan_solve(mesh.handle, ctypes.byref(p), bp, k, ptr, bk, _stream_ptr(b), ctypes.byref(it)))
+    return out, it.value
+
+
+def precond_apply(mesh: Mesh, b, p: tp_params | None = None):
+    p = p or params()
+    bp, bk, keep = _as_buffer(b, np.float64)
+    k = 1 if len(np.shape(b)) == 1 else int(np.shape(b)[1])
+    out, ptr, kind = _empty_like_kind(b, tuple(np.shape(b)))
+    _check(lib().precond_apply(mesh.handle, ctypes.byref(p), bp, k, ptr, bk, _stream_ptr(b)))
+    return out
+
+
+def precond_step(mesh: Mesh, constraints: tp_constraints, p: tp_params | None = None) -> dict:
+    p = p or params()
+    rep = tp_step_report()
+    _check(lib().precond_step(mesh.handle, ctypes.byref(p), ctypes.byref(constraints), ctypes.byref(rep),
+                              _stream_ptr()))
+    return {
+        "E_before": rep.E_before, "E_after": rep.E_after, "tau": rep.tau, "slope": rep.slope,
+        "phi_before": list(rep.phi_before), "phi_after": list(rep.phi_after),
+        "krylov_iters": rep.krylov_iters, "cg_iters": rep.cg_iters, "ls_trials": rep.ls_trials,
+        "status": rep.status, "pair_interactions": rep.pair_interactions,
+    }
+
+
+def tp_profile_enable(mesh: Mesh, on: bool = True):
+    _check(lib().tp_profile_enable(mesh.handle, 1 if on else 0))
+
+
+def tp_profile_read(mesh: Mesh) -> dict:
+    """{kernel: {launches, ms, units}} accumulated since the last read (then reset)."""
+    buf = (tp_kernel_stat * 32)()
+    n = ctypes.c_int()
+    _check(lib().tp_profile_read(mesh.handle, buf, 32, ctypes.byref(n)))
+    return {buf[i].name.decode(): {"launches": buf[i].launches, "ms": buf[i].ms, "units": buf[i].units}
+            for i in range(n.value)}
+
+
+def tp_launch_count() -> int:
+    return int(lib().tp_launch_count())
+
+
+# ---------------------------------------------------------------------------
+# autograd: E with the hand-written dE as its backward
+# ---------------------------------------------------------------------------
+
+def _make_autograd():
+    torch = _torch()
+
+    class _TangentPointEnergy(torch.autograd.Function):
+        """E(f) of Eq. 10 (or its Barnes-Hut approximation); its backward is
+        the library's differential kernel. f is a float64 CUDA tensor [nv,3]."""
+
+        @staticmethod
+        def forward(ctx, positions, mesh, p):
+            f = positions.detach().contiguous()
+            tp_mesh_set_positions(mesh, f)
+            ctx.save_for_backward(f)
+            ctx.mesh, ctx.p = mesh, p
+            return positions.new_tensor(tp_energy(mesh, p))
+
+        @staticmethod
+        def backward(ctx, grad_out):
+            (f,) = ctx.saved_tensors
+            tp_mesh_set_positions(ctx.mesh, f)
+            dE, _ = tp_differential(ctx.mesh, ctx.p, like=f)
+            return grad_out * dE, None, None
+
+    return _TangentPointEnergy
+
+
+class _Lazy:
+    _fn = None
+
+    def apply(self, positions, mesh, p=None):
+        if _Lazy._fn is None:
+            _Lazy._fn = _make_autograd()
+        return _Lazy._fn.apply(positions, mesh, p or params())
+
+
+TangentPointEnergy = _Lazy()

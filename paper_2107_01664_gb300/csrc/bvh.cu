@@ -1,0 +1,714 @@
+// Barnes-Hut approximation of the energy (§4.1, Eq. 16) and its
+// differential (§4.2) over a BVH built on the GPU.
+//
+// Tree. Faces are sorted by the 30-bit Morton code of their barycenter
+// (ties broken by face index, so the order is unique); runs of `leaf_size`
+// consecutive faces form the leaves, and an implicit binary tree over the
+// leaves splits every range of n leaves into ceil(n/2) + floor(n/2). Nodes
+// are numbered in pre-order, so the left child of node i is i + 1 and the
+// first node after the subtree of i (its escape index) is i + 2n - 1: the
+// traversal needs no stack. The shape depends only on (nf, leaf_size) and
+// is built once per mesh; the Morton order and the node data (area a_I,
+// area-weighted barycenter X_I, bounding box of the faces' vertices, radius
+// r_I from X_I) are rebuilt bottom-up whenever the positions change.
+//
+// Admissibility of node I for target face S (read with the separation
+// parameter theta, which the printed inequality omits):
+//     max(r_S, r_I)^2 < theta^2 dist(box_S, box_I)^2,
+// box_S the bounding box of triangle S and r_S its radius from X_S. An
+// admissible node contributes K(X_S, P_S; X_I) a_S a_I; a leaf that is not
+// admissible is summed exactly over its faces (T != S); otherwise the
+// traversal descends. theta = 0 never admits a node, which gives the exact
+// all-pairs sum.
+//
+// Differential ("full" mode): the exact derivative of the Barnes-Hut energy
+// with the admissible sets held fixed. The target side is accumulated in
+// registers. The source side is scattered with FP64 atomics into per-node
+// accumulators G_I = sum_S -a_S a_I dK/dd, Q_I = sum_S a_S K (far field) and
+// per-face accumulators (near field), then pushed down to the faces through
+// X_I = sum a_T X_T / a_I and a_I = sum a_T. "Literal" mode keeps only the
+// target-side terms, the formula printed in §4.2.
+#include <cub/device/device_radix_sort.cuh>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "tp_internal.cuh"
+
+namespace tp {
+
+struct NodeShape {  // fixed per mesh
+    int first, count, skip, leaf;
+};
+
+// ---------------------------------------------------------------------------
+// host: implicit tree shape
+// ---------------------------------------------------------------------------
+
+static void shape_rec(std::vector<NodeShape>& out, std::vector<int>& depth, std::vector<int>& left,
+                      int id, int lo, int hi, int d, int leaf, int nf) {
+    int n = hi - lo;
+    NodeShape s;
+    s.first = lo * leaf;
+    s.count = std::min(hi * leaf, nf) - lo * leaf;
+    s.skip = id + 2 * n - 1;
+    s.leaf = n == 1;
+    out[id] = s;
+    depth[id] = d;
+    if (n == 1) {
+        left[id] = -1;
+        return;
+    }
+    int nl = (n + 1) / 2;
+    left[id] = id + 1;
+    shape_rec(out, depth, left, id + 1, lo, lo + nl, d + 1, leaf, nf);
+    shape_rec(out, depth, left, id + 2 * nl, lo + nl, hi, d + 1, leaf, nf);
+}
+
+struct BvhHost {
+    int leaf = 0, nleaf = 0, nnodes = 0, maxdepth = 0;
+    std::vector<int> level_off;  // nodes sorted by depth: offsets per depth
+};
+
+// device arrays in m->bvh_tmp: [shape int4 nnodes][right child int][level order int]
+static int bvh_shape(tp_mesh* m, int leaf, BvhHost& h) {
+    h.leaf = leaf;
+    h.nleaf = (m->nf + leaf - 1) / leaf;
+    h.nnodes = 2 * h.nleaf - 1;
+    std::vector<NodeShape> sh(h.nnodes);
+    std::vector<int> depth(h.nnodes), left(h.nnodes);
+    shape_rec(sh, depth, left, 0, 0, h.nleaf, 0, leaf, m->nf);
+    h.maxdepth = *std::max_element(depth.begin(), depth.end());
+    std::vector<int> order(h.nnodes);
+    for (int i = 0; i < h.nnodes; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return depth[a] < depth[b]; });
+    h.level_off.assign(h.maxdepth + 2, 0);
+    for (int i = 0; i < h.nnodes; ++i) h.level_off[depth[i] + 1]++;
+    for (int d = 0; d <= h.maxdepth; ++d) h.level_off[d + 1] += h.level_off[d];
+    // right child = first node after the left subtree = escape index of the left child
+    std::vector<int> right(h.nnodes, -1);
+    for (int i = 0; i < h.nnodes; ++i)
+        if (!sh[i].leaf) right[i] = sh[i + 1].skip;
+    size_t bytes = sizeof(NodeShape) * h.nnodes + sizeof(int) * 2 * (size_t)h.nnodes;
+    TP_TRY(ensure(m->bvh_tmp, bytes));
+    char* base = m->bvh_tmp.as<char>();
+    TP_CUDA(cudaMemcpy(base, sh.data(), sizeof(NodeShape) * h.nnodes, cudaMemcpyHostToDevice));
+    TP_CUDA(cudaMemcpy(base + sizeof(NodeShape) * h.nnodes, right.data(), sizeof(int) * h.nnodes,
+                       cudaMemcpyHostToDevice));
+    TP_CUDA(cudaMemcpy(base + sizeof(NodeShape) * h.nnodes + sizeof(int) * h.nnodes, order.data(),
+                       sizeof(int) * h.nnodes, cudaMemcpyHostToDevice));
+    return TP_OK;
+}
+
+
+// ---------------------------------------------------------------------------
+// device: Morton codes, sort, face boxes, node aggregates
+// ---------------------------------------------------------------------------
+
+__global__ void k_bbox_partial(const d4* __restrict__ X, int nf, double* __restrict__ part) {
+    __shared__ double lo[3][256], hi[3][256];
+    double l[3] = {1e300, 1e300, 1e300}, h[3] = {-1e300, -1e300, -1e300};
+    for (int i = blockIdx.x * 256 + threadIdx.x; i < nf; i += gridDim.x * 256) {
+        d4 x = X[i];
+        double v[3] = {x.x, x.y, x.z};
+        for (int c = 0; c < 3; ++c) {
+            l[c] = fmin(l[c], v[c]);
+            h[c] = fmax(h[c], v[c]);
+        }
+    }
+    for (int c = 0; c < 3; ++c) {
+        lo[c][threadIdx.x] = l[c];
+        hi[c][threadIdx.x] = h[c];
+    }
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int c = 0; c < 3; ++c) {
+                lo[c][threadIdx.x] = fmin(lo[c][threadIdx.x], lo[c][threadIdx.x + w]);
+                hi[c][threadIdx.x] = fmax(hi[c][threadIdx.x], hi[c][threadIdx.x + w]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 3; ++c) {
+            part[6 * blockIdx.x + c] = lo[c][0];
+            part[6 * blockIdx.x + 3 + c] = hi[c][0];
+        }
+}
+
+__global__ void k_bbox_final(double* __restrict__ part, int nblk) {
+    if (threadIdx.x != 0) return;
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int b = 0; b < nblk; ++b)
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = fmin(lo[c], part[6 * b + c]);
+            hi[c] = fmax(hi[c], part[6 * b + 3 + c]);
+        }
+    for (int c = 0; c < 3; ++c) {
+        part[6 * 1024 + c] = lo[c];
+        part[6 * 1024 + 3 + c] = hi[c];
+    }
+}
+
+__device__ __forceinline__ unsigned spread10(unsigned v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// 30-bit Morton code of the FP64 barycenter, cell = floor((x - lo) / ext * 1024)
+__global__ void k_morton(const d4* __restrict__ X, int nf, const double* __restrict__ bb,
+                         unsigned long long* __restrict__ keys) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    const double lo[3] = {bb[0], bb[1], bb[2]}, hi[3] = {bb[3], bb[4], bb[5]};
+    d4 x = X[i];
+    double v[3] = {x.x, x.y, x.z};
+    unsigned q[3];
+    for (int c = 0; c < 3; ++c) {
+        double ext = hi[c] - lo[c];
+        double t = ext > 0.0 ? __dmul_rn(__dsub_rn(v[c], lo[c]), 1024.0 / ext) : 0.0;
+        int qi = (int)floor(t);
+        q[c] = (unsigned)(qi < 0 ? 0 : (qi > 1023 ? 1023 : qi));
+    }
+    unsigned code = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+    keys[i] = ((unsigned long long)code << 32) | (unsigned)i;
+}
+
+// sorted face tables, face boxes and radii
+struct FaceBox {
+    float lox, loy, loz, r2;
+    float hix, hiy, hiz, a;
+};
+
+__global__ void k_sorted_faces(const unsigned long long* __restrict__ keys, int nf,
+                               const double* __restrict__ pos, const int* __restrict__ faces,
+                               const double* __restrict__ center, const d4* __restrict__ f64a,
+                               const float4* __restrict__ f32a, const float4* __restrict__ f32b,
+                               int* __restrict__ perm, float4* __restrict__ sa, float4* __restrict__ sb,
+                               FaceBox* __restrict__ box) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    int S = (int)(keys[i] & 0xffffffffull);
+    perm[i] = S;
+    sa[i] = f32a[S];
+    sb[i] = f32b[S];
+    d4 X = f64a[S];
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, r2 = 0.0;
+    for (int cr = 0; cr < 3; ++cr) {
+        int v = faces[3 * S + cr];
+        double p[3] = {pos[3 * v] - center[0], pos[3 * v + 1] - center[1], pos[3 * v + 2] - center[2]};
+        double dx = p[0] - X.x, dy = p[1] - X.y, dz = p[2] - X.z;
+        r2 = fmax(r2, dx * dx + dy * dy + dz * dz);
+        for (int c = 0; c < 3; ++c) {
+            lo[c] = fmin(lo[c], p[c]);
+            hi[c] = fmax(hi[c], p[c]);
+        }
+    }
+    box[i] = FaceBox{(float)lo[0], (float)lo[1], (float)lo[2], (float)r2,
+                     (float)hi[0], (float)hi[1], (float)hi[2], (float)X.w};
+}
+
+// node aggregates, one depth level per launch (deepest first)
+__global__ void k_nodes_level(const NodeShape* __restrict__ shape, const int* __restrict__ right,
+                              const int* __restrict__ order, int n0, int n1,
+                              const int* __restrict__ perm, const double* __restrict__ pos,
+                              const int* __restrict__ faces, const double* __restrict__ center,
+                              const d4* __restrict__ f64a, const FaceBox* __restrict__ fbox,
+                              BvhNode* __restrict__ node, d4* __restrict__ node64) {
+    int k = n0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n1) return;
+    int id = order[k];
+    NodeShape s = shape[id];
+    double a = 0.0, X[3] = {0, 0, 0}, lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300},
+           r = 0.0;
+    if (s.leaf) {
+        for (int i = s.first; i < s.first + s.count; ++i) {
+            d4 f = f64a[perm[i]];
+            a += f.w;
+            X[0] += f.w * f.x;
+            X[1] += f.w * f.y;
+            X[2] += f.w * f.z;
+        }
+        for (int c = 0; c < 3; ++c) X[c] /= a;
+        for (int i = s.first; i < s.first + s.count; ++i) {
+            int S = perm[i];
+            FaceBox b = fbox[i];
+            lo[0] = fmin(lo[0], (double)b.lox); lo[1] = fmin(lo[1], (double)b.loy); lo[2] = fmin(lo[2], (double)b.loz);
+            hi[0] = fmax(hi[0], (double)b.hix); hi[1] = fmax(hi[1], (double)b.hiy); hi[2] = fmax(hi[2], (double)b.hiz);
+            for (int cr = 0; cr < 3; ++cr) {
+                int v = faces[3 * S + cr];
+                double dx = pos[3 * v] - center[0] - X[0], dy = pos[3 * v + 1] - center[1] - X[1],
+                       dz = pos[3 * v + 2] - center[2] - X[2];
+                r = fmax(r, sqrt(dx * dx + dy * dy + dz * dz));
+            }
+        }
+    } else {
+        int L = id + 1, R = right[id];
+        d4 xl = node64[L], xr = node64[R];
+        a = xl.w + xr.w;
+        X[0] = (xl.w * xl.x + xr.w * xr.x) / a;
+        X[1] = (xl.w * xl.y + xr.w * xr.y) / a;
+        X[2] = (xl.w * xl.z + xr.w * xr.z) / a;
+        BvhNode nl = node[L], nr = node[R];
+        lo[0] = fmin(nl.lox, nr.lox); lo[1] = fmin(nl.loy, nr.loy); lo[2] = fmin(nl.loz, nr.loz);
+        hi[0] = fmax(nl.hix, nr.hix); hi[1] = fmax(nl.hiy, nr.hiy); hi[2] = fmax(nl.hiz, nr.hiz);
+        double rl = sqrt((double)nl.r2), rr = sqrt((double)nr.r2);
+        double dl = sqrt((xl.x - X[0]) * (xl.x - X[0]) + (xl.y - X[1]) * (xl.y - X[1]) + (xl.z - X[2]) * (xl.z - X[2]));
+        double dr = sqrt((xr.x - X[0]) * (xr.x - X[0]) + (xr.y - X[1]) * (xr.y - X[1]) + (xr.z - X[2]) * (xr.z - X[2]));
+        r = fmax(dl + rl, dr + rr);
+    }
+    node64[id] = d4{X[0], X[1], X[2], a};
+    BvhNode o;
+    o.cx = (float)X[0]; o.cy = (float)X[1]; o.cz = (float)X[2]; o.a = (float)a;
+    o.lox = (float)lo[0]; o.loy = (float)lo[1]; o.loz = (float)lo[2]; o.r2 = (float)(r * r);
+    o.hix = (float)hi[0]; o.hiy = (float)hi[1]; o.hiz = (float)hi[2]; o.pad = 0.f;
+    o.first = s.first; o.count = s.count; o.skip = s.skip; o.leaf = s.leaf;
+    node[id] = o;
+}
+
+int bvh_build(tp_mesh* m, const tp_params* p, cudaStream_t st) {
+    if (m->bvh_shape_leaf != p->leaf_size) {
+        BvhHost h;
+        TP_TRY(bvh_shape(m, p->leaf_size, h));
+        m->bvh_shape_leaf = h.leaf;
+        m->bvh_maxdepth = h.maxdepth;
+        m->bvh_nodes = h.nnodes;
+        m->bvh_level_off = h.level_off;
+        m->bvh_valid = false;
+    }
+    if (m->bvh_valid) return TP_OK;
+    BvhHost h;
+    h.leaf = m->bvh_shape_leaf;
+    h.nnodes = m->bvh_nodes;
+    h.maxdepth = m->bvh_maxdepth;
+    h.level_off = m->bvh_level_off;
+    const int nf = m->nf;
+    m->bvh_nodes = h.nnodes;
+    m->bvh_leaf = h.leaf;
+    // buffers
+    size_t sort_bytes = 0;
+    cub::DeviceRadixSort::SortKeys((void*)nullptr, sort_bytes, (unsigned long long*)nullptr,
+                                   (unsigned long long*)nullptr, nf, 0, 62);
+    TP_TRY(ensure(m->bvh_keys, sizeof(unsigned long long) * 2 * (size_t)nf + sizeof(double) * 6 * 1025));
+    TP_TRY(ensure(m->bvh_sortws, sort_bytes + 256));
+    TP_TRY(ensure(m->bvh_perm, sizeof(int) * (size_t)nf + sizeof(FaceBox) * (size_t)nf));
+    TP_TRY(ensure(m->bvh_f32a, sizeof(float4) * (size_t)nf));
+    TP_TRY(ensure(m->bvh_f32b, sizeof(float4) * (size_t)nf));
+    TP_TRY(ensure(m->bvh_node, sizeof(BvhNode) * (size_t)h.nnodes + sizeof(d4) * (size_t)h.nnodes));
+    unsigned long long* kin = m->bvh_keys.as<unsigned long long>();
+    unsigned long long* kout = kin + nf;
+    double* bpart = (double*)(kout + nf);
+    int* perm = m->bvh_perm.as<int>();
+    FaceBox* fbox = (FaceBox*)(perm + nf);
+    BvhNode* node = m->bvh_node.as<BvhNode>();
+    d4* node64 = (d4*)(node + h.nnodes);
+    const NodeShape* shape = m->bvh_tmp.as<NodeShape>();
+    const int* right = (const int*)(shape + h.nnodes);
+    const int* order = right + h.nnodes;
+
+    ProfScope ps(m, PK_BVH_BUILD, (double)nf, st);
+    int nblk = std::min(1024, (nf + 255) / 256);
+    k_bbox_partial<<<nblk, 256, 0, st>>>(m->f64a.as<d4>(), nf, bpart);
+    TP_LAUNCH_CHECK();
+    k_bbox_final<<<1, 32, 0, st>>>(bpart, nblk);
+    TP_LAUNCH_CHECK();
+    k_morton<<<(nf + 255) / 256, 256, 0, st>>>(m->f64a.as<d4>(), nf, bpart + 6 * 1024, kin);
+    TP_LAUNCH_CHECK();
+    TP_CUDA(cub::DeviceRadixSort::SortKeys(m->bvh_sortws.ptr, sort_bytes, kin, kout, nf, 0, 62, st));
+    k_sorted_faces<<<(nf + 255) / 256, 256, 0, st>>>(kout, nf, m->pos.as<double>(), m->faces.as<int>(),
+                                                     m->center.as<double>(), m->f64a.as<d4>(),
+                                                     m->f32a.as<float4>(), m->f32b.as<float4>(), perm,
+                                                     m->bvh_f32a.as<float4>(), m->bvh_f32b.as<float4>(), fbox);
+    TP_LAUNCH_CHECK();
+    for (int d = h.maxdepth; d >= 0; --d) {
+        int n0 = h.level_off[d], n1 = h.level_off[d + 1];
+        k_nodes_level<<<(n1 - n0 + 127) / 128, 128, 0, st>>>(shape, right, order, n0, n1, perm,
+                                                             m->pos.as<double>(), m->faces.as<int>(),
+                                                             m->center.as<double>(), m->f64a.as<d4>(), fbox,
+                                                             node, node64);
+        TP_LAUNCH_CHECK();
+    }
+    m->bvh_valid = true;
+    return TP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// traversal
+// ---------------------------------------------------------------------------
+
+// squared distance between two boxes; max(0, ...) per axis, fixed op order
+__device__ __forceinline__ float box_dist2(float alx, float aly, float alz, float ahx, float ahy, float ahz,
+                                           const BvhNode& n) {
+    float gx = fmaxf(fmaxf(__fsub_rn(n.lox, ahx), __fsub_rn(alx, n.hix)), 0.f);
+    float gy = fmaxf(fmaxf(__fsub_rn(n.loy, ahy), __fsub_rn(aly, n.hiy)), 0.f);
+    float gz = fmaxf(fmaxf(__fsub_rn(n.loz, ahz), __fsub_rn(alz, n.hiz)), 0.f);
+    return __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
+}
+
+__device__ __forceinline__ float frcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float fpow(float x, float y) {
+    float l, r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(l) : "f"(x));
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(y * l));
+    return r;
+}
+
+struct KahanF {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {
+        float y = x - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+// energy rows: thread per target (sorted position i, or target list)
+template <bool P6>
+__global__ void __launch_bounds__(128)
+k_bh_energy(const BvhNode* __restrict__ node, int nnodes, const float4* __restrict__ sa,
+            const float4* __restrict__ sb, const FaceBox* __restrict__ fbox, const int* __restrict__ perm,
+            const int* __restrict__ inv_targets /* sorted positions of a target list, or null */, int nt,
+            float theta2, float halfp, const d4* __restrict__ f64a, double* __restrict__ rows,
+            unsigned long long* __restrict__ count) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const int i = inv_targets ? inv_targets[t] : t;
+    float4 A = sa[i], B = sb[i];
+    FaceBox fb = fbox[i];
+    float acc = 0.f;
+    KahanF sum;
+    int nint = 0, run = 0;
+    int id = 0;
+    while (id < nnodes) {
+        BvhNode n = node[id];
+        float d2 = box_dist2(fb.lox, fb.loy, fb.loz, fb.hix, fb.hiy, fb.hiz, n);
+        float mr2 = fmaxf(fb.r2, n.r2);
+        if (mr2 < __fmul_rn(theta2, d2)) {
+            float dx = A.x - n.cx, dy = A.y - n.cy, dz = A.z - n.cz;
+            float r2 = dx * dx + dy * dy + dz * dz;
+            float u = B.x * dx + B.y * dy + B.z * dz;
+            float ir2 = frcp(fmaxf(r2, 1e-18f));
+            float q = u * u * (ir2 * ir2);
+            float K = P6 ? q * q * q : fpow(q, halfp);
+            acc = fmaf(K, n.a, acc);
+            ++nint;
+            if (++run == 32) { sum.add(acc); acc = 0.f; run = 0; }
+            id = n.skip;
+        } else if (n.leaf) {
+            for (int j = n.first; j < n.first + n.count; ++j) {
+                if (j == i) continue;
+                float4 s = sa[j];
+                float dx = A.x - s.x, dy = A.y - s.y, dz = A.z - s.z;
+                float r2 = dx * dx + dy * dy + dz * dz;
+                float u = B.x * dx + B.y * dy + B.z * dz;
+                float ir2 = frcp(fmaxf(r2, 1e-18f));
+                float q = u * u * (ir2 * ir2);
+                float K = P6 ? q * q * q : fpow(q, halfp);
+                acc = fmaf(K, s.w, acc);
+                ++nint;
+            }
+            sum.add(acc);
+            acc = 0.f;
+            run = 0;
+            id = n.skip;
+        } else {
+            id = id + 1;
+        }
+    }
+    sum.add(acc);
+    rows[t] = f64a[perm[i]].w * sum.value();
+    if (count) atomicAdd(count, (unsigned long long)nint);
+}
+
+// device counters of Barnes-Hut interactions: [0] energy, [1] differential
+int bh_counter(tp_mesh* m, cudaStream_t st) {
+    if (m->bhcount.ptr) return TP_OK;
+    TP_TRY(ensure(m->bhcount, 2 * sizeof(unsigned long long)));
+    TP_CUDA(cudaMemsetAsync(m->bhcount.ptr, 0, 2 * sizeof(unsigned long long), st));
+    return TP_OK;
+}
+
+int bh_counts_read(tp_mesh* m, unsigned long long out[2], bool reset, cudaStream_t st) {
+    out[0] = out[1] = 0;
+    if (!m->bhcount.ptr) return TP_OK;
+    TP_CUDA(cudaMemcpyAsync(out, m->bhcount.ptr, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    TP_CUDA(cudaStreamSynchronize(st));
+    if (reset) TP_CUDA(cudaMemsetAsync(m->bhcount.ptr, 0, 2 * sizeof(unsigned long long), st));
+    return TP_OK;
+}
+
+// inverse permutation (face -> sorted position) for target lists
+__global__ void k_inv_perm(const int* __restrict__ perm, int nf, int* __restrict__ inv) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nf) inv[perm[i]] = i;
+}
+__global__ void k_map_targets(const int* __restrict__ tl, int nt, const int* __restrict__ inv, int* __restrict__ out) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < nt) out[t] = inv[tl[t]];
+}
+// rows in sorted order -> rows in face order
+__global__ void k_unsort_rows(const double* __restrict__ rs, const int* __restrict__ perm, int nf,
+                              double* __restrict__ rows) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nf) rows[perm[i]] = rs[i];
+}
+
+int energy_rows_bh(tp_mesh* m, const tp_params* p, const int32_t* tl, int nt, double* rows, cudaStream_t st) {
+    TP_TRY(bvh_build(m, p, st));
+    const int nf = m->nf;
+    int* perm = m->bvh_perm.as<int>();
+    FaceBox* fbox = (FaceBox*)(perm + nf);
+    float theta2 = (float)(p->theta * p->theta);
+    float halfp = (float)(0.5 * p->p);
+    const int* map = nullptr;
+    double* out = rows;
+    TP_TRY(ensure(m->tmpv[6], sizeof(double) * 64 + sizeof(int) * 2 * (size_t)nf + sizeof(double) * nf));
+    char* base = m->tmpv[6].as<char>() + sizeof(double) * 64;
+    int* inv = (int*)base;
+    int* mapped = inv + nf;
+    double* rs = (double*)(mapped + nf);
+    if (tl) {
+        k_inv_perm<<<(nf + 255) / 256, 256, 0, st>>>(perm, nf, inv);
+        k_map_targets<<<(nt + 255) / 256, 256, 0, st>>>(tl, nt, inv, mapped);
+        TP_LAUNCH_CHECK();
+        map = mapped;
+    } else {
+        out = rs;  // sorted order, unsorted afterwards
+    }
+    TP_TRY(bh_counter(m, st));
+    {
+        ProfScope ps(m, PK_BH_ENERGY, 0.0, st);
+        unsigned long long* cnt = m->bhcount.as<unsigned long long>();
+        if (p->p == 6.0)
+            k_bh_energy<true><<<(nt + 127) / 128, 128, 0, st>>>(m->bvh_node.as<BvhNode>(), m->bvh_nodes,
+                                                               m->bvh_f32a.as<float4>(), m->bvh_f32b.as<float4>(),
+                                                               fbox, perm, map, nt, theta2, halfp,
+                                                               m->f64a.as<d4>(), out, cnt);
+        else
+            k_bh_energy<false><<<(nt + 127) / 128, 128, 0, st>>>(m->bvh_node.as<BvhNode>(), m->bvh_nodes,
+                                                                m->bvh_f32a.as<float4>(), m->bvh_f32b.as<float4>(),
+                                                                fbox, perm, map, nt, theta2, halfp,
+                                                                m->f64a.as<d4>(), out, cnt);
+        TP_LAUNCH_CHECK();
+    }
+    if (!tl) {
+        k_unsort_rows<<<(nf + 255) / 256, 256, 0, st>>>(rs, perm, nf, rows);
+        TP_LAUNCH_CHECK();
+    }
+    return TP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// differential
+// ---------------------------------------------------------------------------
+
+// target-side accumulators: 0 sum a c | 1-3 sum a c d | 4-6 sum a K d/|d|^2 | 7 sum a K
+// reverse scatter: node accumulators nacc[id*4 + 0..2] = G, [3] = Q; faces facc[i*4 ...]
+template <bool P6, bool FULL>
+__global__ void __launch_bounds__(128)
+k_bh_diff(const BvhNode* __restrict__ node, int nnodes, const float4* __restrict__ sa,
+          const float4* __restrict__ sb, const FaceBox* __restrict__ fbox, int nf, float theta2, float hm1,
+          float p, double* __restrict__ tacc /* [nf][8] sorted */, double* __restrict__ nacc,
+          double* __restrict__ facc, unsigned long long* __restrict__ count) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    float4 A = sa[i], B = sb[i];
+    FaceBox fb = fbox[i];
+    const float aS = A.w;
+    KahanF acc[8];
+    float pt[8];
+    for (int k = 0; k < 8; ++k) pt[k] = 0.f;
+    int run = 0, nint = 0;
+    auto flush = [&]() {
+        for (int k = 0; k < 8; ++k) {
+            acc[k].add(pt[k]);
+            pt[k] = 0.f;
+        }
+        run = 0;
+    };
+    // one interaction with a source of barycenter (sx,sy,sz), weight w; returns the
+    // source-side derivative (G: -a_S w dK/dd, Q: a_S K)
+    auto interact = [&](float sx, float sy, float sz, float w, float* G, float& Q) {
+        float dx = A.x - sx, dy = A.y - sy, dz = A.z - sz;
+        float r2 = dx * dx + dy * dy + dz * dz;
+        float u = B.x * dx + B.y * dy + B.z * dz;
+        float ir2 = frcp(fmaxf(r2, 1e-18f));
+        float ir4 = ir2 * ir2;
+        float q = u * u * ir4;
+        float mq = P6 ? q * q : fpow(q, hm1);
+        float K = mq * q;
+        float c = mq * u * ir4;  // |u|^{p-2} u / |d|^{2p}
+        float wc = w * c, wK = w * K, wKd = wK * ir2;
+        pt[0] += wc;
+        pt[1] = fmaf(wc, dx, pt[1]);
+        pt[2] = fmaf(wc, dy, pt[2]);
+        pt[3] = fmaf(wc, dz, pt[3]);
+        pt[4] = fmaf(wKd, dx, pt[4]);
+        pt[5] = fmaf(wKd, dy, pt[5]);
+        pt[6] = fmaf(wKd, dz, pt[6]);
+        pt[7] += wK;
+        // dK/dd = p c N - 2p K d/|d|^2 ; source side gets -a_S w dK/dd
+        float s1 = -aS * p * wc, s2 = 2.f * aS * p * wKd;
+        G[0] = s1 * B.x + s2 * dx;
+        G[1] = s1 * B.y + s2 * dy;
+        G[2] = s1 * B.z + s2 * dz;
+        Q = aS * K;
+    };
+    int id = 0;
+    while (id < nnodes) {
+        BvhNode n = node[id];
+        float d2 = box_dist2(fb.lox, fb.loy, fb.loz, fb.hix, fb.hiy, fb.hiz, n);
+        float mr2 = fmaxf(fb.r2, n.r2);
+        if (mr2 < __fmul_rn(theta2, d2)) {
+            float G[3], Q;
+            interact(n.cx, n.cy, n.cz, n.a, G, Q);
+            ++nint;
+            if (FULL) {
+                atomicAdd(nacc + 4 * id + 0, (double)G[0]);
+                atomicAdd(nacc + 4 * id + 1, (double)G[1]);
+                atomicAdd(nacc + 4 * id + 2, (double)G[2]);
+                atomicAdd(nacc + 4 * id + 3, (double)Q);
+            }
+            if (++run == 32) flush();
+            id = n.skip;
+        } else if (n.leaf) {
+            for (int j = n.first; j < n.first + n.count; ++j) {
+                if (j == i) continue;
+                float4 s = sa[j];
+                float G[3], Q;
+                interact(s.x, s.y, s.z, s.w, G, Q);
+                ++nint;
+                if (FULL) {
+                    atomicAdd(facc + 4 * j + 0, (double)G[0]);
+                    atomicAdd(facc + 4 * j + 1, (double)G[1]);
+                    atomicAdd(facc + 4 * j + 2, (double)G[2]);
+                    atomicAdd(facc + 4 * j + 3, (double)Q);
+                }
+            }
+            flush();
+            id = n.skip;
+        } else {
+            id = id + 1;
+        }
+    }
+    flush();
+    for (int k = 0; k < 8; ++k) tacc[(size_t)i * 8 + k] = acc[k].value();
+    atomicAdd(count, (unsigned long long)nint);
+}
+
+// per node: g1 = G/a_I, q = Q - G.X_I/a_I (FP64 node data)
+__global__ void k_node_push_terms(double* __restrict__ nacc, const d4* __restrict__ node64, int nnodes) {
+    int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= nnodes) return;
+    d4 X = node64[id];
+    double G[3] = {nacc[4 * id], nacc[4 * id + 1], nacc[4 * id + 2]};
+    double Q = nacc[4 * id + 3];
+    nacc[4 * id + 0] = G[0] / X.w;
+    nacc[4 * id + 1] = G[1] / X.w;
+    nacc[4 * id + 2] = G[2] / X.w;
+    nacc[4 * id + 3] = Q - (G[0] * X.x + G[1] * X.y + G[2] * X.z) / X.w;
+}
+
+// per sorted face i: walk root -> leaf of i summing the node terms, then
+// assemble the FP64 face adjoints (face order) from target and source sides
+__global__ void k_bh_diff_combine(const NodeShape* __restrict__ shape, const int* __restrict__ right, int nnodes,
+                                  int leaf, const int* __restrict__ perm, int nf, const double* __restrict__ tacc,
+                                  const double* __restrict__ nacc, const double* __restrict__ facc,
+                                  const d4* __restrict__ f64a, const d4* __restrict__ f64b, double p, int full,
+                                  double* __restrict__ adj, double* __restrict__ erow) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    int S = perm[i];
+    d4 X = f64a[S], N = f64b[S];
+    double a = X.w;
+    const double* t = tacc + (size_t)i * 8;
+    double gX[3], gN[3], ga;
+    double NS[3] = {N.x, N.y, N.z};
+    for (int c = 0; c < 3; ++c) {
+        gX[c] = a * (p * t[0] * NS[c] - 2.0 * p * t[4 + c]);
+        gN[c] = a * p * t[1 + c];
+    }
+    ga = t[7];
+    if (erow) erow[S] = a * t[7];
+    if (full) {
+        double g1[3] = {0, 0, 0}, q = 0.0;
+        int lf = i / leaf;
+        int id = 0;
+        for (;;) {
+            for (int c = 0; c < 3; ++c) g1[c] += nacc[4 * id + c];
+            q += nacc[4 * id + 3];
+            NodeShape s = shape[id];
+            if (s.leaf) break;
+            int L = id + 1;
+            NodeShape sl = shape[L];
+            int lfirst = sl.first / leaf, lcount = (sl.skip - L + 1) / 2;
+            id = (lf >= lfirst && lf < lfirst + lcount) ? L : right[id];
+        }
+        double Xv[3] = {X.x, X.y, X.z};
+        for (int c = 0; c < 3; ++c) gX[c] += a * g1[c] + facc[4 * i + c];
+        ga += q + g1[0] * Xv[0] + g1[1] * Xv[1] + g1[2] * Xv[2] + facc[4 * i + 3];
+    }
+    for (int c = 0; c < 3; ++c) {
+        adj[7 * S + c] = gX[c];
+        adj[7 * S + 3 + c] = gN[c];
+    }
+    adj[7 * S + 6] = ga;
+}
+
+int diff_adjoints_bh(tp_mesh* m, const tp_params* p, double* adj, double* erow, cudaStream_t st) {
+    TP_TRY(bvh_build(m, p, st));
+    const int nf = m->nf, nn = m->bvh_nodes;
+    int* perm = m->bvh_perm.as<int>();
+    FaceBox* fbox = (FaceBox*)(perm + nf);
+    BvhNode* node = m->bvh_node.as<BvhNode>();
+    d4* node64 = (d4*)(node + nn);
+    TP_TRY(ensure(m->part, sizeof(double) * ((size_t)8 * nf + 4 * (size_t)nn + 4 * (size_t)nf)));
+    double* tacc = m->part.as<double>();
+    double* nacc = tacc + (size_t)8 * nf;
+    double* facc = nacc + (size_t)4 * nn;
+    TP_CUDA(cudaMemsetAsync(nacc, 0, sizeof(double) * (4 * (size_t)nn + 4 * (size_t)nf), st));
+    const bool full = p->bh_diff_mode == TP_BH_DIFF_FULL;
+    float theta2 = (float)(p->theta * p->theta);
+    float hm1 = (float)(0.5 * p->p - 1.0);
+    const float4* sa = m->bvh_f32a.as<float4>();
+    const float4* sb = m->bvh_f32b.as<float4>();
+    dim3 g((nf + 127) / 128);
+    TP_TRY(bh_counter(m, st));
+    {
+        ProfScope ps(m, PK_BH_DIFF, 0.0, st);
+        unsigned long long* cnt = m->bhcount.as<unsigned long long>() + 1;
+        const float pf = (float)p->p;
+        if (p->p == 6.0) {
+            if (full) k_bh_diff<true, true><<<g, 128, 0, st>>>(node, nn, sa, sb, fbox, nf, theta2, hm1, pf, tacc, nacc, facc, cnt);
+            else k_bh_diff<true, false><<<g, 128, 0, st>>>(node, nn, sa, sb, fbox, nf, theta2, hm1, pf, tacc, nacc, facc, cnt);
+        } else {
+            if (full) k_bh_diff<false, true><<<g, 128, 0, st>>>(node, nn, sa, sb, fbox, nf, theta2, hm1, pf, tacc, nacc, facc, cnt);
+            else k_bh_diff<false, false><<<g, 128, 0, st>>>(node, nn, sa, sb, fbox, nf, theta2, hm1, pf, tacc, nacc, facc, cnt);
+        }
+        TP_LAUNCH_CHECK();
+    }
+    if (full) {
+        k_node_push_terms<<<(nn + 255) / 256, 256, 0, st>>>(nacc, node64, nn);
+        TP_LAUNCH_CHECK();
+    }
+    const NodeShape* shape = m->bvh_tmp.as<NodeShape>();
+    const int* right = (const int*)(shape + nn);
+    k_bh_diff_combine<<<(nf + 255) / 256, 256, 0, st>>>(shape, right, nn, m->bvh_leaf, perm, nf, tacc, nacc, facc,
+                                                        m->f64a.as<d4>(), m->f64b.as<d4>(), p->p, full ? 1 : 0,
+                                                        adj, erow);
+    TP_LAUNCH_CHECK();
+    return TP_OK;
+}
+
+}  // namespace tp

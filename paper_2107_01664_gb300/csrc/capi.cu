@@ -1,0 +1,387 @@
+// The extern "C" entry points declared in include/tp.h: argument checks,
+// device selection, staging of host arrays, and dispatch to the kernels.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "tp_internal.cuh"
+
+using namespace tp;
+
+namespace {
+
+// selects the mesh's device for the duration of a call and restores the
+// caller's current device afterwards
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int check_params(const tp_params* p) {
+    if (!p) return fail(TP_ERR_INVALID_ARG, "params is NULL");
+    if (!(p->p > 2.0) || !std::isfinite(p->p)) return fail(TP_ERR_INVALID_ARG, "p must be > 2");
+    if (!(p->theta >= 0.0) || !std::isfinite(p->theta))
+        return fail(TP_ERR_INVALID_ARG, "theta must be finite and >= 0");
+    if (p->leaf_size < 1 || p->leaf_size > 32) return fail(TP_ERR_INVALID_ARG, "leaf_size must be in 1..32");
+    if (p->precision != TP_PREC_FP32 && p->precision != TP_PREC_FP64)
+        return fail(TP_ERR_INVALID_ARG, "unknown precision");
+    if (p->theta > 0.0 && p->precision != TP_PREC_FP32)
+        return fail(TP_ERR_INVALID_ARG, "Barnes-Hut (theta > 0) runs in TP_PREC_FP32 only");
+    return TP_OK;
+}
+
+int check_mesh(const tp_mesh* m) {
+    if (!m) return fail(TP_ERR_INVALID_ARG, "mesh is NULL");
+    return TP_OK;
+}
+
+int check_kind(int ptr_kind) {
+    if (ptr_kind != TP_PTR_HOST && ptr_kind != TP_PTR_DEVICE)
+        return fail(TP_ERR_INVALID_ARG, "ptr_kind must be TP_PTR_HOST or TP_PTR_DEVICE");
+    return TP_OK;
+}
+
+// returns a device pointer holding `bytes` of `src` (staged through `buf`
+// when src is host memory)
+int stage_in(Buf& buf, const void* src, size_t bytes, int ptr_kind, cudaStream_t st, const void** out) {
+    if (ptr_kind == TP_PTR_DEVICE) {
+        *out = src;
+        return TP_OK;
+    }
+    TP_TRY(ensure(buf, bytes));
+    TP_TRY(copy_in(buf.ptr, src, bytes, TP_PTR_HOST, st));
+    *out = buf.ptr;
+    return TP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void tp_params_default(tp_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->p = 6.0;
+    p->theta = 0.0;
+    p->leaf_size = 8;
+    p->precision = TP_PREC_FP32;
+    p->bh_diff_mode = TP_BH_DIFF_FULL;
+    p->bh_apply = 0;
+    p->krylov_tol = 1e-6;
+    p->krylov_max = 200;
+    p->gmres_restart = 30;
+    p->cg_tol = 1e-10;
+    p->cg_max = 20000;
+    p->armijo_c = 1e-4;
+    p->armijo_shrink = 0.5;
+    p->tau0 = 1.0;
+    p->ls_max = 30;
+    p->fixed_tau = 0;
+    p->proj_iters = 1;
+}
+
+const char* tp_last_error(void) { return tp::last_error(); }
+
+int tp_mesh_create(int device, int nv, int nf, const double* pos, const int32_t* faces, int ptr_kind,
+                   void* stream, tp_mesh** out) {
+    set_error("");
+    if (!out || !pos || !faces) return fail(TP_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    TP_TRY(check_kind(ptr_kind));
+    if (nv < 3 || nf < 1) return fail(TP_ERR_INVALID_ARG, "need nv >= 3 and nf >= 1");
+    if ((long long)nf * 3 > (1LL << 30)) return fail(TP_ERR_INVALID_ARG, "too many faces");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(TP_ERR_INVALID_ARG, "no such CUDA device");
+    DeviceGuard g(device);
+    if (!g.ok) return fail(TP_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    // faces on the host for validation and the incidence structures
+    std::vector<int> F(3 * (size_t)nf);
+    if (ptr_kind == TP_PTR_HOST)
+        std::memcpy(F.data(), faces, sizeof(int) * 3 * (size_t)nf);
+    else {
+        TP_CUDA(cudaMemcpyAsync(F.data(), faces, sizeof(int) * 3 * (size_t)nf, cudaMemcpyDeviceToHost, st));
+        TP_CUDA(cudaStreamSynchronize(st));
+    }
+    for (int S = 0; S < nf; ++S) {
+        int a = F[3 * S], b = F[3 * S + 1], c = F[3 * S + 2];
+        if (a < 0 || b < 0 || c < 0 || a >= nv || b >= nv || c >= nv)
+            return fail(TP_ERR_INVALID_ARG, "face " + std::to_string(S) + " has a vertex index out of range");
+        if (a == b || b == c || a == c)
+            return fail(TP_ERR_INVALID_ARG, "face " + std::to_string(S) + " repeats a vertex");
+    }
+    // vertex -> (face*3+corner) incidence, sorted by face
+    std::vector<int> vptr(nv + 1, 0), vidx(3 * (size_t)nf);
+    for (int e = 0; e < 3 * nf; ++e) vptr[F[e] + 1]++;
+    for (int v = 0; v < nv; ++v) vptr[v + 1] += vptr[v];
+    {
+        std::vector<int> fill(vptr.begin(), vptr.end() - 1);
+        for (int e = 0; e < 3 * nf; ++e) vidx[fill[F[e]]++] = e;
+    }
+    tp_mesh* m = new tp_mesh();
+    m->device = device;
+    m->nv = nv;
+    m->nf = nf;
+    auto bail = [&](int code) {
+        tp_mesh_destroy(m);
+        return code;
+    };
+    int s = TP_OK;
+    if ((s = ensure(m->faces, sizeof(int) * 3 * (size_t)nf)) ||
+        (s = ensure(m->vf_ptr, sizeof(int) * (nv + 1))) || (s = ensure(m->vf_idx, sizeof(int) * 3 * (size_t)nf)) ||
+        (s = ensure(m->pos, sizeof(double) * 3 * (size_t)nv)) || (s = ensure(m->center, sizeof(double) * 4)) ||
+        (s = ensure(m->errflag, sizeof(int) * 4)) || (s = ensure(m->f32a, sizeof(float4) * (size_t)nf)) ||
+        (s = ensure(m->f32b, sizeof(float4) * (size_t)nf)) || (s = ensure(m->f64a, sizeof(d4) * (size_t)nf)) ||
+        (s = ensure(m->f64b, sizeof(d4) * (size_t)nf)) || (s = ensure(m->fgrad, sizeof(double) * 9 * (size_t)nf)))
+        return bail(s);
+    if (cudaMemcpy(m->faces.ptr, F.data(), sizeof(int) * 3 * (size_t)nf, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m->vf_ptr.ptr, vptr.data(), sizeof(int) * (nv + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(m->vf_idx.ptr, vidx.data(), sizeof(int) * 3 * (size_t)nf, cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(fail(TP_ERR_CUDA, "copying the topology failed"));
+    if ((s = laplacian_setup(m))) return bail(s);
+    if ((s = copy_in(m->pos.ptr, pos, sizeof(double) * 3 * (size_t)nv, ptr_kind, st))) return bail(s);
+    if ((s = refresh_geometry(m, st))) return bail(s);
+    *out = m;
+    return TP_OK;
+}
+
+int tp_mesh_set_positions(tp_mesh* m, const double* pos, int ptr_kind, void* stream) {
+    set_error("");
+    TP_TRY(check_mesh(m));
+    TP_TRY(check_kind(ptr_kind));
+    if (!pos) return fail(TP_ERR_INVALID_ARG, "pos is NULL");
+    DeviceGuard g(m->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    TP_TRY(copy_in(m->pos.ptr, pos, sizeof(double) * 3 * (size_t)m->nv, ptr_kind, st));
+    return refresh_geometry(m, st);
+}
+
+int tp_mesh_get_positions(tp_mesh* m, double* pos, int ptr_kind, void* stream) {
+    set_error("");
+    TP_TRY(check_mesh(m));
+    TP_TRY(check_kind(ptr_kind));
+    if (!pos) return fail(TP_ERR_INVALID_ARG, "pos is NULL");
+    DeviceGuard g(m->device);
+    return copy_out(pos, m->pos.ptr, sizeof(double) * 3 * (size_t)m->nv, ptr_kind, (cudaStream_t)stream);
+}
+
+int tp_mesh_destroy(tp_mesh* m) {
+    if (!m) return TP_OK;
+    DeviceGuard g(m->device);
+    Buf* all[] = {&m->faces, &m->vf_ptr, &m->vf_idx, &m->pos, &m->center, &m->errflag, &m->f32a, &m->f32b,
+                  &m->f64a, &m->f64b, &m->fgrad, &m->rowptr, &m->col, &m->cotsrc, &m->diagpos, &m->val,
+                  &m->dinv, &m->bvh_node, &m->bvh_perm, &m->bvh_keys, &m->bvh_tmp, &m->bvh_sortws,
+                  &m->bvh_f32a, &m->bvh_f32b, &m->bvh_nodeP, &m->part, &m->part2, &m->scal, &m->corner,
+                  &m->wv64, &m->wv32, &m->io_in, &m->io_out, &m->adj, &m->erow, &m->tlist, &m->rowsum,
+                  &m->kry};
+    for (Buf* b : all) release(*b);
+    release(m->bhcount);
+    prof_release(m);
+    for (auto& b : m->tmpv) release(b);
+    for (auto& b : m->stepv) release(b);
+    for (auto& b : m->prec) release(b);
+    delete m;
+    return TP_OK;
+}
+
+size_t tp_mesh_footprint_bytes(int nv, int nf, const tp_params* p) {
+    if (nv < 0 || nf < 0) return 0;
+    const int restart = p ? std::max(1, std::min(60, p->gmres_restart)) : 30;
+    size_t F = (size_t)nf, V = (size_t)nv;
+    size_t geom = F * (12 + 4 + 16 + 16 + 32 + 32 + 72) + V * (24 + 4);
+    size_t lap = (7 * V + F) * (4 + 8 + 8) + V * 16;
+    size_t bvh = F * (4 + 8 + 16 + 16 + 16) + F * 64;
+    size_t nsplit = 16;
+    size_t pairs = nsplit * F * 14 * 8 + F * (96 + 72 + 72 + 56 + 8);
+    size_t krylov = (size_t)(2 * restart + 1) * 3 * V * 8;
+    size_t vecs = 24 * 3 * V * 8;
+    return geom + lap + bvh + pairs + krylov + vecs;
+}
+
+int tp_energy(tp_mesh* m, const tp_params* p, double* E_out, void* stream) {
+    set_error("");
+    TP_TRY(check_mesh(m));
+    TP_TRY(check_params(p));
+    if (!E_out) return fail(TP_ERR_INVALID_ARG, "E_out is NULL");
+    DeviceGuard g(m->device);
+    return energy_value(m, p, E_out, (cudaStream_t)stream);
+}
+
+int tp_energy_rows(tp_mesh* m, const tp_params* p, const int32_t* targets, int n, double* rows, int ptr_kind,
+                   void* stream) {
+    set_error("");
+    TP_TRY(check_mesh(m));
+    TP_TRY(check_params(p));
+    TP_TRY(check_kind(ptr_kind));
+    if (n < 0 || (n > 0 && (!targets || !rows))) return fail(TP_ERR_INVALID_ARG, "bad targets/rows");
+    if (n == 0) return TP_OK;
+    DeviceGuard g(m->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (ptr_kind == TP_PTR_HOST)
+        for (int i = 0; i < n; ++i)
+            if (targets[i] < 0 || targets[i] >= m->nf) return fail(TP_ERR_INVALID_ARG, "target index out of range");
+    const void* tl = nullptr;
+    TP_TRY(stage_in(m->tlist, targets, sizeof(int) * (size_t)n, ptr_kind, st, &tl));
+    TP_TRY(ensure(m->io_out, sizeof(double) * (size_t)n));
+    double* out = ptr_kind == TP_PTR_DEVICE ? rows : m->io_out.as<double>();
+    if (p->theta > 0.0)
+        TP_TRY(energy_rows_bh(m, p, (const int32_t*)tl, n, out, st));
+    else
+        TP_TRY(energy_rows_direct(m, p, (const int32_t*)tl, n, out, st));
+    if (ptr_kind == TP_PTR_HOST) TP_TRY(copy_out(rows, out, sizeof(double) * (size_t)n, TP_PTR_HOST, st));
+    return TP_OK;
+}
+
+int tp_differential(tp_mesh* m, const tp_params* p, double* dE, int ptr_kind, double* E_out, void* stream) {
+    set_error("");
+    TP_TRY(check_mesh(m));
+    TP_TRY(check_params(p));
+    TP_TRY(check_kind(ptr_kind));
+    if (!dE) return fail(TP_ERR_INVALID_ARG, "dE is NULL");
+    DeviceGuard g(m->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t bytes = sizeof(double) * 3 * (size_t)m->nv;
+    TP_TRY(ensure(m->io_out, bytes));
+    double* out = ptr_kind == TP_PTR_DEVICE ? dE : m->io_out.as<double>();
+    TP_TRY(differential_dev(m, p, out, E_out, st));
+    if (ptr_kind == TP_PTR_HOST) TP_TRY(copy_out(dE, out, bytes, TP_PTR_HOST, st));
+    return TP_OK;
+}
+
+int fractional_apply(tp_mesh* m, const tp_params* p, int op, const double* v, int k, double* y, int ptr_kind,
+                     void* stream) {
+    set_error("");
+    TP_TRY(check_mesh(m));
+    TP_TRY(check_params(p));
+    TP_TRY(check_kind(ptr_kind));
+    if (op < TP_OP_A || op > TP_OP_L) return fail(TP_ERR_INVALID_ARG, "unknown operator");
+    if (k < 1 || k > 9) return fail(TP_ERR_INVALID_ARG, "k must be in 1..9");
+    if (!v || !y) return fail(TP_ERR_INVALID_ARG, "NULL vector");
+    DeviceGuard g(m->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t bytes = sizeof(double) * (size_t)m->nv * k;
+    const void* vin = nullptr;
+    TP_TRY(stage_in(m->io_in, v, bytes, ptr_kind, st, &vin));
+    TP_TRY(ensure(m->io_out, bytes));
+    double* out = ptr_kind == TP_PTR_DEVICE ? y : m->io_out.as<double>();
+    TP_TRY(apply_direct(m, p, op, (const double*)vin, k, out, st));
+    if (ptr_kind == TP_PTR_HOST) TP_TRY(copy_out(y, out, bytes, TP_PTR_HOST, st));
+    return TP_OK;
+}
+
+int cotan_solve(tp_mesh* m, const tp_params* p, const double* b, int k, double* z, int ptr_kind, void* stream,
+                int* iters_out) {
+    set_error("");
+    TP_TRY(check_mesh(m));
+    TP_TRY(check_params(p));
+    TP_TRY(check_kind(ptr_kind));
+    if (k < 1 || k > 9) return fail(TP_ERR_INVALID_ARG, "k must be in 1..9");
+    if (!b || !z) return fail(TP_ERR_INVALID_ARG, "NULL vector");
+    DeviceGuard g(m->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t bytes = sizeof(double) * (size_t)m->nv * k;
+    const void* bin = nullptr;
+    TP_TRY(stage_in(m->io_in, b, bytes, ptr_kind, st, &bin));
+    TP_TRY(ensure(m->io_out, bytes));
+    double* out = ptr_kind == TP_PTR_DEVICE ? z : m->io_out.as<double>();
+    int it = 0;
+    int s = cg_solve(m, p, (const double*)bin, k, out, st, &it);
+    if (iters_out) *iters_out = it;
+    if (s != TP_OK) return s;
+    if (ptr_kind == TP_PTR_HOST) TP_TRY(copy_out(z, out, bytes, TP_PTR_HOST, st));
+    return TP_OK;
+}
+
+int precond_apply(tp_mesh* m, const tp_params* p, const double* b, int k, double* z, int ptr_kind, void* stream) {
+    set_error("");
+    TP_TRY(check_mesh(m));
+    TP_TRY(check_params(p));
+    TP_TRY(check_kind(ptr_kind));
+    if (k < 1 || k > 9) return fail(TP_ERR_INVALID_ARG, "k must be in 1..9");
+    if (!b || !z) return fail(TP_ERR_INVALID_ARG, "NULL vector");
+    DeviceGuard g(m->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t bytes = sizeof(double) * (size_t)m->nv * k;
+    const void* bin = nullptr;
+    TP_TRY(stage_in(m->io_in, b, bytes, ptr_kind, st, &bin));
+    TP_TRY(ensure(m->io_out, bytes));
+    double* out = ptr_kind == TP_PTR_DEVICE ? z : m->io_out.as<double>();
+    TP_TRY(precond_apply_dev(m, p, (const double*)bin, k, out, st, nullptr));
+    if (ptr_kind == TP_PTR_HOST) TP_TRY(copy_out(z, out, bytes, TP_PTR_HOST, st));
+    return TP_OK;
+}
+
+int precond_step(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp_step_report* rep, void* stream) {
+    set_error("");
+    TP_TRY(check_mesh(m));
+    TP_TRY(check_params(p));
+    if (!c) return fail(TP_ERR_INVALID_ARG, "constraints is NULL");
+    if (c->flags & ~(TP_CONSTRAINT_AREA | TP_CONSTRAINT_VOLUME))
+        return fail(TP_ERR_INVALID_ARG, "unknown constraint flag");
+    if (p->krylov_max < 1 || p->cg_max < 1 || p->ls_max < 1 || p->proj_iters < 0 || p->proj_iters > 100 ||
+        !(p->armijo_shrink > 0.0 && p->armijo_shrink < 1.0))
+        return fail(TP_ERR_INVALID_ARG, "bad solver parameters");
+    DeviceGuard g(m->device);
+    return precond_step_dev(m, p, c, rep, (cudaStream_t)stream);
+}
+
+int tp_profile_enable(tp_mesh* m, int on) {
+    set_error("");
+    TP_TRY(check_mesh(m));
+    m->prof.on = on != 0;
+    return TP_OK;
+}
+
+int tp_profile_read(tp_mesh* m, tp_kernel_stat* out, int max, int* n) {
+    set_error("");
+    TP_TRY(check_mesh(m));
+    if (!n || (max > 0 && !out)) return fail(TP_ERR_INVALID_ARG, "NULL output");
+    DeviceGuard g(m->device);
+    static const char* names[PK_COUNT] = {"energy_direct", "diff_direct", "apply_A", "apply_B", "apply_B0",
+                                          "apply_L", "bh_energy", "bh_diff", "bvh_build", "cg"};
+    Profiler& P = m->prof;
+    for (auto& pe : P.pending) {
+        float ms = 0.f;
+        TP_CUDA(cudaEventSynchronize(pe.second.second));
+        TP_CUDA(cudaEventElapsedTime(&ms, pe.second.first, pe.second.second));
+        P.ms[pe.first] += ms;
+        P.pool.push_back(pe.second.first);
+        P.pool.push_back(pe.second.second);
+    }
+    P.pending.clear();
+    unsigned long long bh[2];
+    TP_TRY(bh_counts_read(m, bh, true, nullptr));
+    P.units[PK_BH_ENERGY] += (double)bh[0];
+    P.units[PK_BH_DIFF] += (double)bh[1];
+    int k = 0;
+    for (int i = 0; i < PK_COUNT && k < max; ++i) {
+        if (P.launches[i] == 0) continue;
+        std::memset(out[k].name, 0, sizeof(out[k].name));
+        std::strncpy(out[k].name, names[i], sizeof(out[k].name) - 1);
+        out[k].launches = P.launches[i];
+        out[k].ms = P.ms[i];
+        out[k].units = P.units[i];
+        ++k;
+    }
+    *n = k;
+    for (int i = 0; i < PK_COUNT; ++i) {
+        P.launches[i] = 0;
+        P.ms[i] = 0.0;
+        P.units[i] = 0.0;
+    }
+    return TP_OK;
+}
+
+unsigned long long tp_launch_count(void) { return tp::launch_count(); }
+
+}  // extern "C"

@@ -1,0 +1,276 @@
+// Mesh state: face geometry (X_S, N_S, a_S and hat gradients), the
+// face-corner -> vertex gather, copies and deterministic FP64 sums.
+#include <cmath>
+#include <cstring>
+
+#include "tp_internal.cuh"
+
+namespace tp {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+const char* last_error() { return g_last_error.c_str(); }
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int ensure(Buf& b, size_t bytes) {
+    if (bytes <= b.bytes && b.ptr) return TP_OK;
+    if (b.ptr) cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+    size_t want = bytes < 256 ? 256 : bytes;
+    cudaError_t e = cudaMalloc(&b.ptr, want);
+    if (e != cudaSuccess) {
+        b.ptr = nullptr;
+        cudaGetLastError();
+        return fail(TP_ERR_OOM, std::string("cudaMalloc(") + std::to_string(want) +
+                                    "): " + cudaGetErrorString(e));
+    }
+    b.bytes = want;
+    return TP_OK;
+}
+
+void release(Buf& b) {
+    if (b.ptr) cudaFree(b.ptr);
+    b.ptr = nullptr;
+    b.bytes = 0;
+}
+
+int sm_count() {
+    static int cached[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return 132;
+    if (!cached[dev]) {
+        int n = 0;
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        cached[dev] = n > 0 ? n : 132;
+    }
+    return cached[dev];
+}
+
+int copy_in(void* dst, const void* src, size_t bytes, int ptr_kind, cudaStream_t st) {
+    if (bytes == 0) return TP_OK;
+    TP_CUDA(cudaMemcpyAsync(dst, src, bytes,
+                            ptr_kind == TP_PTR_HOST ? cudaMemcpyHostToDevice
+                                                    : cudaMemcpyDeviceToDevice,
+                            st));
+    return TP_OK;
+}
+
+int copy_out(void* dst, const void* src, size_t bytes, int ptr_kind, cudaStream_t st) {
+    if (bytes == 0) return TP_OK;
+    TP_CUDA(cudaMemcpyAsync(dst, src, bytes,
+                            ptr_kind == TP_PTR_HOST ? cudaMemcpyDeviceToHost
+                                                    : cudaMemcpyDeviceToDevice,
+                            st));
+    if (ptr_kind == TP_PTR_HOST) TP_CUDA(cudaStreamSynchronize(st));
+    return TP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// deterministic column sums of a row-major [n][k] FP64 array (k <= 64)
+// ---------------------------------------------------------------------------
+
+static constexpr int kSumThreads = 256;
+
+__global__ void k_colsum_partial(const double* __restrict__ x, long n, int k, int rows_per_block,
+                                 double* __restrict__ part) {
+    __shared__ double sh[kSumThreads];
+    long r0 = (long)blockIdx.x * rows_per_block;
+    long r1 = r0 + rows_per_block < n ? r0 + rows_per_block : n;
+    for (int c = 0; c < k; ++c) {
+        double s = 0.0;
+        for (long r = r0 + threadIdx.x; r < r1; r += kSumThreads) s += x[r * k + c];
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = kSumThreads / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[(long)blockIdx.x * k + c] = sh[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_colsum_final(const double* __restrict__ part, int nblk, int k, double scale,
+                               double* __restrict__ out) {
+    __shared__ double sh[kSumThreads];
+    for (int c = 0; c < k; ++c) {
+        double s = 0.0;
+        for (int b = threadIdx.x; b < nblk; b += kSumThreads) s += part[(long)b * k + c];
+        sh[threadIdx.x] = s;
+        __syncthreads();
+        for (int w = kSumThreads / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) out[c] = sh[0] * scale;
+        __syncthreads();
+    }
+}
+
+// column sums (times `scale`) of x [n][k] into out_dev [k]; uses m->part2
+int colsum(tp_mesh* m, const double* x, long n, int k, double scale, double* out_dev,
+                  cudaStream_t st) {
+    int nblk = (int)((n + 4095) / 4096);
+    if (nblk < 1) nblk = 1;
+    if (nblk > 1024) nblk = 1024;
+    int rpb = (int)((n + nblk - 1) / nblk);
+    if (rpb < 1) rpb = 1;
+    TP_TRY(ensure(m->part2, sizeof(double) * (size_t)nblk * k));
+    k_colsum_partial<<<nblk, kSumThreads, 0, st>>>(x, n, k, rpb, m->part2.as<double>());
+    TP_LAUNCH_CHECK();
+    k_colsum_final<<<1, kSumThreads, 0, st>>>(m->part2.as<double>(), nblk, k, scale, out_dev);
+    TP_LAUNCH_CHECK();
+    return TP_OK;
+}
+
+int sum_f64(const double* x, int n, double* out_dev, tp_mesh* m, cudaStream_t st) {
+    return colsum(m, x, n, 1, 1.0, out_dev, st);
+}
+
+// ---------------------------------------------------------------------------
+// face geometry, §3.1 / §3.2.1
+// ---------------------------------------------------------------------------
+
+__global__ void k_face_geom(const double* __restrict__ pos, const int* __restrict__ faces, int nf,
+                            const double* __restrict__ center, float4* __restrict__ f32a,
+                            float4* __restrict__ f32b, d4* __restrict__ f64a, d4* __restrict__ f64b,
+                            double* __restrict__ fgrad, int* __restrict__ err) {
+    int S = blockIdx.x * blockDim.x + threadIdx.x;
+    if (S >= nf) return;
+    int i = faces[3 * S], j = faces[3 * S + 1], k = faces[3 * S + 2];
+    double pi[3], pj[3], pk[3];
+    for (int c = 0; c < 3; ++c) {
+        pi[c] = pos[3 * i + c];
+        pj[c] = pos[3 * j + c];
+        pk[c] = pos[3 * k + c];
+    }
+    double e1[3] = {pj[0] - pi[0], pj[1] - pi[1], pj[2] - pi[2]};
+    double e2[3] = {pk[0] - pi[0], pk[1] - pi[1], pk[2] - pi[2]};
+    double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                   e1[0] * e2[1] - e1[1] * e2[0]};
+    double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    bool ok = nn > 0.0 && isfinite(nn);
+    for (int c = 0; c < 3; ++c) ok = ok && isfinite(pi[c]) && isfinite(pj[c]) && isfinite(pk[c]);
+    if (!ok) {
+        atomicOr(err, 1);
+        nn = 1.0;
+    }
+    double a = 0.5 * nn;
+    double N[3] = {n[0] / nn, n[1] / nn, n[2] / nn};
+    double X[3];
+    for (int c = 0; c < 3; ++c) X[c] = (pi[c] + pj[c] + pk[c]) / 3.0 - center[c];
+    f64a[S] = d4{X[0], X[1], X[2], a};
+    f64b[S] = d4{N[0], N[1], N[2], 0.0};
+    f32a[S] = make_float4((float)X[0], (float)X[1], (float)X[2], (float)a);
+    f32b[S] = make_float4((float)N[0], (float)N[1], (float)N[2], 0.0f);
+    // hat gradients: grad phi_c = N x e_c / (2a), e_c the edge opposite corner c
+    const double* P[3] = {pi, pj, pk};
+    for (int c = 0; c < 3; ++c) {
+        const double* p1 = P[(c + 1) % 3];
+        const double* p2 = P[(c + 2) % 3];
+        double e[3] = {p2[0] - p1[0], p2[1] - p1[1], p2[2] - p1[2]};
+        double g[3] = {N[1] * e[2] - N[2] * e[1], N[2] * e[0] - N[0] * e[2],
+                       N[0] * e[1] - N[1] * e[0]};
+        for (int q = 0; q < 3; ++q) fgrad[9 * S + 3 * c + q] = g[q] / (2.0 * a);
+    }
+}
+
+int refresh_geometry(tp_mesh* m, cudaStream_t st) {
+    // reference frame: mean vertex position (FP64), so that the FP32 face
+    // table holds barycenters relative to the mesh
+    TP_TRY(colsum(m, m->pos.as<double>(), m->nv, 3, 1.0 / m->nv, m->center.as<double>(), st));
+    TP_CUDA(cudaMemsetAsync(m->errflag.ptr, 0, sizeof(int) * 4, st));
+    int nb = (m->nf + 255) / 256;
+    k_face_geom<<<nb, 256, 0, st>>>(m->pos.as<double>(), m->faces.as<int>(), m->nf,
+                                    m->center.as<double>(), m->f32a.as<float4>(),
+                                    m->f32b.as<float4>(), m->f64a.as<d4>(), m->f64b.as<d4>(),
+                                    m->fgrad.as<double>(), m->errflag.as<int>());
+    TP_LAUNCH_CHECK();
+    int err = 0;
+    TP_CUDA(cudaMemcpyAsync(&err, m->errflag.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TP_CUDA(cudaStreamSynchronize(st));
+    m->lap_valid = false;
+    m->bvh_valid = false;
+    if (err) return fail(TP_ERR_DEGENERATE, "zero-area face or non-finite position");
+    return TP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// face corners -> vertices (deterministic CSR gather, no atomics)
+// ---------------------------------------------------------------------------
+
+__global__ void k_gather(const double* __restrict__ corner, const int* __restrict__ vf_ptr,
+                         const int* __restrict__ vf_idx, int nv, int k, double* __restrict__ y) {
+    int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= nv) return;
+    int e0 = vf_ptr[v], e1 = vf_ptr[v + 1];
+    for (int c = 0; c < k; ++c) {
+        double s = 0.0;
+        for (int e = e0; e < e1; ++e) s += corner[(long)vf_idx[e] * k + c];
+        y[(long)v * k + c] = s;
+    }
+}
+
+int corners_to_vertices(tp_mesh* m, const double* corner, int k, double* y, cudaStream_t st) {
+    int nb = (m->nv + 255) / 256;
+    k_gather<<<nb, 256, 0, st>>>(corner, m->vf_ptr.as<int>(), m->vf_idx.as<int>(), m->nv, k, y);
+    TP_LAUNCH_CHECK();
+    return TP_OK;
+}
+
+}  // namespace tp
+
+// ---------------------------------------------------------------------------
+// launch counting and per-mesh kernel statistics
+// ---------------------------------------------------------------------------
+
+#include <atomic>
+
+namespace tp {
+
+static std::atomic<unsigned long long> g_launches{0};
+
+void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(); }
+
+ProfScope::ProfScope(tp_mesh* m_, int key_, double units, cudaStream_t st_) : m(m_), key(key_), st(st_) {
+    Profiler& P = m->prof;
+    P.launches[key] += 1;
+    P.units[key] += units;
+    if (!P.on) return;
+    for (cudaEvent_t* e : {&e0, &e1}) {
+        if (!P.pool.empty()) {
+            *e = P.pool.back();
+            P.pool.pop_back();
+        } else if (cudaEventCreate(e) != cudaSuccess) {
+            *e = nullptr;
+        }
+    }
+    if (e0) cudaEventRecord(e0, st);
+}
+
+ProfScope::~ProfScope() {
+    if (!e0 || !e1) return;
+    cudaEventRecord(e1, st);
+    m->prof.pending.push_back({key, {e0, e1}});
+}
+
+void prof_release(tp_mesh* m) {
+    Profiler& P = m->prof;
+    for (auto& pe : P.pending) {
+        cudaEventDestroy(pe.second.first);
+        cudaEventDestroy(pe.second.second);
+    }
+    for (auto e : P.pool) cudaEventDestroy(e);
+    P.pending.clear();
+    P.pool.clear();
+}
+
+}  // namespace tp

@@ -1,0 +1,643 @@
+// Direct all-pairs kernels of the hot path (N-body tiles):
+//   energy rows of Eq. 10 (§3.1),
+//   face adjoints of the differential of Eq. 10 (§3.1, both roles of a face),
+//   kernel-matrix products of §5.1.1-5.1.3 / Appendix A for A, B, B0, L^{2-s}.
+//
+// Every thread owns TT target faces held in registers; a block of NT
+// threads streams tiles of NT source faces through shared memory. The grid
+// is (target blocks) x (source splits) so that small meshes still fill the
+// GPU; each (block, split) writes per-target partial sums that a combine
+// kernel adds in a fixed order (deterministic results). In the FP32 path
+// the pair terms are FP32, each run of CH consecutive sources is summed in
+// FP32 and the runs are added with Kahan compensation; partials and the
+// final per-face combination are FP64. The FP64 path runs the same kernels
+// with double arithmetic.
+#include <cmath>
+
+#include "tp_internal.cuh"
+
+namespace tp {
+
+constexpr int NT = 128;  // threads per block = sources per shared-memory tile
+constexpr int CH = 32;   // sources per FP32 run before the compensated add
+
+template <typename T> struct V4T;
+template <> struct V4T<float> { using type = float4; };
+template <> struct V4T<double> { using type = d4; };
+
+template <typename T> __device__ __forceinline__ typename V4T<T>::type v4zero();
+template <> __device__ __forceinline__ float4 v4zero<float>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+template <> __device__ __forceinline__ d4 v4zero<double>() { return d4{0.0, 0.0, 0.0, 0.0}; }
+
+// ---- elementary functions (FP32: single MUFU instructions) --------------
+
+__device__ __forceinline__ float rcp_(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ double rcp_(double x) { return 1.0 / x; }
+
+__device__ __forceinline__ float lg2_(float x) {
+    float r;
+    asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ex2_(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+// x^y for x >= 0 (x = 0 gives 0 for y > 0)
+__device__ __forceinline__ float pow_(float x, float y) { return ex2_(y * lg2_(x)); }
+__device__ __forceinline__ double pow_(double x, double y) { return pow(x, y); }
+
+// smallest |d|^2 treated as a real pair; the self pair has d = 0 exactly
+template <typename T> __device__ __forceinline__ T tiny_r2();
+template <> __device__ __forceinline__ float tiny_r2<float>() { return 1e-18f; }
+template <> __device__ __forceinline__ double tiny_r2<double>() { return 1e-150; }
+
+// ---- compensated accumulators -------------------------------------------
+
+template <typename T> struct Acc;
+template <> struct Acc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float x) {  // Kahan
+        float y = x - c;
+        float t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+template <> struct Acc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+// ---- launch geometry ------------------------------------------------------
+
+struct Grid {
+    int bx, nsplit, tiles_per_split;
+};
+
+static Grid make_grid(int nt, int nf, int tt) {
+    Grid g;
+    g.bx = (nt + NT * tt - 1) / (NT * tt);
+    if (g.bx < 1) g.bx = 1;
+    int ntiles = (nf + NT - 1) / NT;
+    int want = sm_count() * 8;  // blocks in flight for a full GPU
+    int ns = (want + g.bx - 1) / g.bx;
+    if (ns < 1) ns = 1;
+    if (ns > ntiles) ns = ntiles;
+    g.tiles_per_split = (ntiles + ns - 1) / ns;
+    g.nsplit = (ntiles + g.tiles_per_split - 1) / g.tiles_per_split;
+    return g;
+}
+
+// ===========================================================================
+// energy rows, Eq. 10: sum_{T != S} K(S,T) a_T  (times a_S in the combine)
+// ===========================================================================
+
+template <typename T, bool P6, int TT>
+__global__ void __launch_bounds__(NT)
+k_energy(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::type* __restrict__ fb,
+         int nf, const int* __restrict__ tlist, int nt, int tiles_per_split, T halfp,
+         double* __restrict__ part) {
+    using V4 = typename V4T<T>::type;
+    __shared__ V4 sh[NT];
+    T tx[TT], ty[TT], tz[TT], nx[TT], ny[TT], nz[TT];
+    int tid[TT];
+#pragma unroll
+    for (int j = 0; j < TT; ++j) {
+        int t = blockIdx.x * NT * TT + j * NT + threadIdx.x;
+        tid[j] = t;
+        if (t < nt) {
+            int S = tlist ? tlist[t] : t;
+            V4 A = fa[S], B = fb[S];
+            tx[j] = A.x; ty[j] = A.y; tz[j] = A.z;
+            nx[j] = B.x; ny[j] = B.y; nz[j] = B.z;
+        } else {  // idle slot: zero normal gives zero terms
+            tx[j] = ty[j] = tz[j] = T(0);
+            nx[j] = ny[j] = nz[j] = T(0);
+        }
+    }
+    Acc<T> acc[TT];
+    const int ntiles = (nf + NT - 1) / NT;
+    const int k0 = blockIdx.y * tiles_per_split;
+    const int k1 = min(k0 + tiles_per_split, ntiles);
+    for (int tile = k0; tile < k1; ++tile) {
+        int src = tile * NT + threadIdx.x;
+        __syncthreads();
+        sh[threadIdx.x] = src < nf ? fa[src] : v4zero<T>();  // zero area pads the tail
+        __syncthreads();
+        for (int c = 0; c < NT; c += CH) {
+            T pt[TT];
+#pragma unroll
+            for (int j = 0; j < TT; ++j) pt[j] = T(0);
+#pragma unroll 8
+            for (int q = 0; q < CH; ++q) {
+                V4 s = sh[c + q];
+#pragma unroll
+                for (int j = 0; j < TT; ++j) {
+                    T dx = tx[j] - s.x, dy = ty[j] - s.y, dz = tz[j] - s.z;
+                    T r2 = dx * dx + dy * dy + dz * dz;
+                    T u = nx[j] * dx + ny[j] * dy + nz[j] * dz;
+                    T ir2 = rcp_(fmax(r2, tiny_r2<T>()));
+                    T qq = u * u * (ir2 * ir2);      // (N.d)^2 / |d|^4
+                    T K = P6 ? qq * qq * qq : pow_(qq, halfp);
+                    pt[j] = fma(K, s.w, pt[j]);
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < TT; ++j) acc[j].add(pt[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < TT; ++j)
+        if (tid[j] < nt) part[(size_t)blockIdx.y * nt + tid[j]] = acc[j].value();
+}
+
+__global__ void k_energy_combine(const double* __restrict__ part, int nsplit, int nt,
+                                 const int* __restrict__ tlist, const d4* __restrict__ f64a,
+                                 double* __restrict__ rows) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    int S = tlist ? tlist[t] : t;
+    double s = 0.0;
+    for (int k = 0; k < nsplit; ++k) s += part[(size_t)k * nt + t];
+    rows[t] = f64a[S].w * s;
+}
+
+template <typename T>
+static int launch_energy(tp_mesh* m, const tp_params* p, const int32_t* tl, int nt, double* rows,
+                         cudaStream_t st) {
+    using V4 = typename V4T<T>::type;
+    constexpr int TT = 2;
+    Grid g = make_grid(nt, m->nf, TT);
+    TP_TRY(ensure(m->part, sizeof(double) * (size_t)g.nsplit * nt));
+    const V4* fa = (const V4*)(sizeof(T) == 4 ? m->f32a.ptr : m->f64a.ptr);
+    const V4* fb = (const V4*)(sizeof(T) == 4 ? m->f32b.ptr : m->f64b.ptr);
+    dim3 grid(g.bx, g.nsplit);
+    const double units = (double)nt * (m->nf - 1);
+    m->pairs += units;
+    {
+        ProfScope ps(m, PK_ENERGY, units, st);
+        if (p->p == 6.0)
+            k_energy<T, true, TT><<<grid, NT, 0, st>>>(fa, fb, m->nf, tl, nt, g.tiles_per_split,
+                                                       T(3), m->part.as<double>());
+        else
+            k_energy<T, false, TT><<<grid, NT, 0, st>>>(fa, fb, m->nf, tl, nt, g.tiles_per_split,
+                                                        T(0.5 * p->p), m->part.as<double>());
+        TP_LAUNCH_CHECK();
+    }
+    k_energy_combine<<<(nt + 255) / 256, 256, 0, st>>>(m->part.as<double>(), g.nsplit, nt, tl,
+                                                       m->f64a.as<d4>(), rows);
+    TP_LAUNCH_CHECK();
+    return TP_OK;
+}
+
+int energy_rows_direct(tp_mesh* m, const tp_params* p, const int32_t* tl, int nt, double* rows,
+                       cudaStream_t st) {
+    if (nt == 0) return TP_OK;
+    return p->precision == TP_PREC_FP64 ? launch_energy<double>(m, p, tl, nt, rows, st)
+                                        : launch_energy<float>(m, p, tl, nt, rows, st);
+}
+
+// ===========================================================================
+// differential of Eq. 10: face adjoints in both roles of each face
+//   with d = X_S - X_T, u_S = N_S.d, u_T = N_T.d, q = u^2/|d|^4,
+//   K = q^{p/2}, c = q^{p/2-1} u / |d|^4  (= |u|^{p-2} u / |d|^{2p}):
+//   dE/dX_S = a_S sum_T a_T [p c_S N_S + p c_T N_T - 2p (K_ST + K_TS) d/|d|^2]
+//   dE/dN_S = a_S sum_T a_T p c_S d
+//   dE/da_S = sum_T a_T (K_ST + K_TS)
+// accumulators: 0 sum a c_S | 1-3 sum a c_S d | 4-6 sum a c_T N_T |
+//               7-9 sum a (K_ST+K_TS) d/|d|^2 | 10 sum a (K_ST+K_TS) | 11 sum a K_ST
+// ===========================================================================
+
+constexpr int NADJ = 12;
+
+template <typename T, bool P6, int TT>
+__global__ void __launch_bounds__(NT)
+k_diff(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::type* __restrict__ fb,
+       int nf, int tiles_per_split, T hm1, double* __restrict__ part) {
+    using V4 = typename V4T<T>::type;
+    __shared__ V4 sa[NT];
+    __shared__ V4 sb[NT];
+    const int nt = nf;
+    T tx[TT], ty[TT], tz[TT], nx[TT], ny[TT], nz[TT];
+    int tid[TT];
+#pragma unroll
+    for (int j = 0; j < TT; ++j) {
+        int t = blockIdx.x * NT * TT + j * NT + threadIdx.x;
+        tid[j] = t;
+        if (t < nt) {
+            V4 A = fa[t], B = fb[t];
+            tx[j] = A.x; ty[j] = A.y; tz[j] = A.z;
+            nx[j] = B.x; ny[j] = B.y; nz[j] = B.z;
+        } else {
+            tx[j] = ty[j] = tz[j] = T(0);
+            nx[j] = ny[j] = nz[j] = T(0);
+        }
+    }
+    Acc<T> acc[TT][NADJ];
+    const int ntiles = (nf + NT - 1) / NT;
+    const int k0 = blockIdx.y * tiles_per_split;
+    const int k1 = min(k0 + tiles_per_split, ntiles);
+    for (int tile = k0; tile < k1; ++tile) {
+        int src = tile * NT + threadIdx.x;
+        __syncthreads();
+        sa[threadIdx.x] = src < nf ? fa[src] : v4zero<T>();
+        sb[threadIdx.x] = src < nf ? fb[src] : v4zero<T>();
+        __syncthreads();
+        for (int c = 0; c < NT; c += CH) {
+            T pt[TT][NADJ];
+#pragma unroll
+            for (int j = 0; j < TT; ++j)
+#pragma unroll
+                for (int i = 0; i < NADJ; ++i) pt[j][i] = T(0);
+#pragma unroll 4
+            for (int q = 0; q < CH; ++q) {
+                V4 s = sa[c + q];
+                V4 n = sb[c + q];
+#pragma unroll
+                for (int j = 0; j < TT; ++j) {
+                    T dx = tx[j] - s.x, dy = ty[j] - s.y, dz = tz[j] - s.z;
+                    T r2 = dx * dx + dy * dy + dz * dz;
+                    T uS = nx[j] * dx + ny[j] * dy + nz[j] * dz;
+                    T uT = n.x * dx + n.y * dy + n.z * dz;
+                    T ir2 = rcp_(fmax(r2, tiny_r2<T>()));
+                    T ir4 = ir2 * ir2;
+                    T qS = uS * uS * ir4, qT = uT * uT * ir4;
+                    T mS = P6 ? qS * qS : pow_(qS, hm1);
+                    T mT = P6 ? qT * qT : pow_(qT, hm1);
+                    T KS = mS * qS, KT = mT * qT;
+                    T at = s.w;
+                    T w = at * (mS * uS * ir4);
+                    T v = at * (mT * uT * ir4);
+                    T kS = at * KS;
+                    T ks = fma(at, KT, kS);
+                    T kd = ks * ir2;
+                    pt[j][0] += w;
+                    pt[j][1] = fma(w, dx, pt[j][1]);
+                    pt[j][2] = fma(w, dy, pt[j][2]);
+                    pt[j][3] = fma(w, dz, pt[j][3]);
+                    pt[j][4] = fma(v, n.x, pt[j][4]);
+                    pt[j][5] = fma(v, n.y, pt[j][5]);
+                    pt[j][6] = fma(v, n.z, pt[j][6]);
+                    pt[j][7] = fma(kd, dx, pt[j][7]);
+                    pt[j][8] = fma(kd, dy, pt[j][8]);
+                    pt[j][9] = fma(kd, dz, pt[j][9]);
+                    pt[j][10] += ks;
+                    pt[j][11] += kS;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < TT; ++j)
+#pragma unroll
+                for (int i = 0; i < NADJ; ++i) acc[j][i].add(pt[j][i]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < TT; ++j)
+        if (tid[j] < nt)
+#pragma unroll
+            for (int i = 0; i < NADJ; ++i)
+                part[((size_t)blockIdx.y * NADJ + i) * nt + tid[j]] = acc[j][i].value();
+}
+
+// adj[S*7 + 0..2] = dE/dX_S, [3..5] = dE/dN_S, [6] = dE/da_S; erow[S] = energy row
+__global__ void k_diff_combine(const double* __restrict__ part, int nsplit, int nf, double p,
+                               const d4* __restrict__ f64a, const d4* __restrict__ f64b,
+                               double* __restrict__ adj, double* __restrict__ erow) {
+    int S = blockIdx.x * blockDim.x + threadIdx.x;
+    if (S >= nf) return;
+    double s[NADJ];
+    for (int i = 0; i < NADJ; ++i) s[i] = 0.0;
+    for (int k = 0; k < nsplit; ++k)
+        for (int i = 0; i < NADJ; ++i) s[i] += part[((size_t)k * NADJ + i) * nf + S];
+    double a = f64a[S].w;
+    d4 N = f64b[S];
+    double NS[3] = {N.x, N.y, N.z};
+    for (int c = 0; c < 3; ++c) {
+        adj[7 * S + c] = a * (p * (s[0] * NS[c] + s[4 + c]) - 2.0 * p * s[7 + c]);
+        adj[7 * S + 3 + c] = a * p * s[1 + c];
+    }
+    adj[7 * S + 6] = s[10];
+    if (erow) erow[S] = a * s[11];
+}
+
+template <typename T>
+static int launch_diff(tp_mesh* m, const tp_params* p, double* adj, double* erow, cudaStream_t st) {
+    using V4 = typename V4T<T>::type;
+    constexpr int TT = 1;
+    Grid g = make_grid(m->nf, m->nf, TT);
+    TP_TRY(ensure(m->part, sizeof(double) * (size_t)g.nsplit * NADJ * m->nf));
+    const V4* fa = (const V4*)(sizeof(T) == 4 ? m->f32a.ptr : m->f64a.ptr);
+    const V4* fb = (const V4*)(sizeof(T) == 4 ? m->f32b.ptr : m->f64b.ptr);
+    dim3 grid(g.bx, g.nsplit);
+    const double units = (double)m->nf * (m->nf - 1);
+    m->pairs += units;
+    {
+        ProfScope ps(m, PK_DIFF, units, st);
+        if (p->p == 6.0)
+            k_diff<T, true, TT><<<grid, NT, 0, st>>>(fa, fb, m->nf, g.tiles_per_split, T(2),
+                                                     m->part.as<double>());
+        else
+            k_diff<T, false, TT><<<grid, NT, 0, st>>>(fa, fb, m->nf, g.tiles_per_split,
+                                                      T(0.5 * p->p - 1.0), m->part.as<double>());
+        TP_LAUNCH_CHECK();
+    }
+    k_diff_combine<<<(m->nf + 255) / 256, 256, 0, st>>>(m->part.as<double>(), g.nsplit, m->nf,
+                                                        p->p, m->f64a.as<d4>(), m->f64b.as<d4>(),
+                                                        adj, erow);
+    TP_LAUNCH_CHECK();
+    return TP_OK;
+}
+
+int diff_adjoints_direct(tp_mesh* m, const tp_params* p, double* adj, double* erow,
+                         cudaStream_t st) {
+    return p->precision == TP_PREC_FP64 ? launch_diff<double>(m, p, adj, erow, st)
+                                        : launch_diff<float>(m, p, adj, erow, st);
+}
+
+// chain rule from (gX, gN, ga) of a face to its corners (§3.1):
+//   X = (f_i+f_j+f_k)/3, n = (f_j-f_i) x (f_k-f_i), a = |n|/2, N = n/|n|;
+//   w = (I - N N^T) gN / |n| + ga N / 2;  g_j = e2 x w, g_k = w x e1,
+//   g_i = -(g_j + g_k), plus gX/3 on each corner.
+__global__ void k_adj_to_corner(const double* __restrict__ pos, const int* __restrict__ faces,
+                                int nf, const double* __restrict__ adj, double* __restrict__ corner) {
+    int S = blockIdx.x * blockDim.x + threadIdx.x;
+    if (S >= nf) return;
+    int i = faces[3 * S], j = faces[3 * S + 1], k = faces[3 * S + 2];
+    double e1[3], e2[3];
+    for (int c = 0; c < 3; ++c) {
+        e1[c] = pos[3 * j + c] - pos[3 * i + c];
+        e2[c] = pos[3 * k + c] - pos[3 * i + c];
+    }
+    double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2],
+                   e1[0] * e2[1] - e1[1] * e2[0]};
+    double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    double N[3] = {n[0] / nn, n[1] / nn, n[2] / nn};
+    const double* g = adj + 7 * S;
+    double gNn = g[3] * N[0] + g[4] * N[1] + g[5] * N[2];
+    double w[3];
+    for (int c = 0; c < 3; ++c) w[c] = (g[3 + c] - gNn * N[c]) / nn + 0.5 * g[6] * N[c];
+    double gj[3] = {e2[1] * w[2] - e2[2] * w[1], e2[2] * w[0] - e2[0] * w[2],
+                    e2[0] * w[1] - e2[1] * w[0]};
+    double gk[3] = {w[1] * e1[2] - w[2] * e1[1], w[2] * e1[0] - w[0] * e1[2],
+                    w[0] * e1[1] - w[1] * e1[0]};
+    for (int c = 0; c < 3; ++c) {
+        double third = g[c] / 3.0;
+        corner[9 * S + c] = -(gj[c] + gk[c]) + third;
+        corner[9 * S + 3 + c] = gj[c] + third;
+        corner[9 * S + 6 + c] = gk[c] + third;
+    }
+}
+
+int adjoints_to_dE(tp_mesh* m, const double* adj, double* dE, cudaStream_t st) {
+    TP_TRY(ensure(m->corner, sizeof(double) * 9 * (size_t)m->nf));
+    k_adj_to_corner<<<(m->nf + 255) / 256, 256, 0, st>>>(m->pos.as<double>(), m->faces.as<int>(),
+                                                         m->nf, adj, m->corner.as<double>());
+    TP_LAUNCH_CHECK();
+    return corners_to_vertices(m, m->corner.as<double>(), 3, dE, st);
+}
+
+// ===========================================================================
+// kernel-matrix products, §5.1.1-5.1.3 and Appendix A, 3 columns per pass
+//   B : W_V = diag(a) D v (3x3 per face), h = |d|^{-2s}
+//   B0: W_U = diag(a) avg v (3 per face), h = (k2(S;T)+k2(T;S)) / (2|d|^{2s})
+//   L : W_U,                               h = |d|^{-2(3-s)}   (sigma = 2 - s)
+// per target: r = sum_T h a_T and (H W)_S = sum_T h W_T.
+// ===========================================================================
+
+constexpr int KC = 3;  // columns per pass
+
+template <int OP> struct OpLayout;
+template <> struct OpLayout<TP_OP_A> { static constexpr int NW = 12, NW4 = 3, NA = 14; };
+template <> struct OpLayout<TP_OP_B> { static constexpr int NW = 9, NW4 = 3, NA = 10; };
+template <> struct OpLayout<TP_OP_B0> { static constexpr int NW = 3, NW4 = 1, NA = 4; };
+template <> struct OpLayout<TP_OP_L> { static constexpr int NW = 3, NW4 = 1, NA = 4; };
+
+// per-face W (FP64 [nf][12]: W_V (q*3+c), then W_U (c)) and its padded copy
+// in the pair precision, for columns col0..col0+2 of v [nv][k]
+template <typename T>
+__global__ void k_face_W(const double* __restrict__ v, int k, int col0, const int* __restrict__ faces,
+                         int nf, const d4* __restrict__ f64a, const double* __restrict__ fgrad,
+                         int op, double* __restrict__ W64, typename V4T<T>::type* __restrict__ Wp,
+                         int nw4) {
+    int S = blockIdx.x * blockDim.x + threadIdx.x;
+    if (S >= nf) return;
+    double a = f64a[S].w;
+    double val[3][KC];
+    for (int cr = 0; cr < 3; ++cr) {
+        int vi = faces[3 * S + cr];
+        for (int c = 0; c < KC; ++c) val[cr][c] = (col0 + c < k) ? v[(size_t)vi * k + col0 + c] : 0.0;
+    }
+    double w[12];
+    for (int q = 0; q < 3; ++q)
+        for (int c = 0; c < KC; ++c) {
+            double g = 0.0;
+            for (int cr = 0; cr < 3; ++cr) g += val[cr][c] * fgrad[9 * S + 3 * cr + q];
+            w[q * KC + c] = a * g;
+        }
+    for (int c = 0; c < KC; ++c) w[9 + c] = a * (val[0][c] + val[1][c] + val[2][c]) / 3.0;
+    for (int i = 0; i < 12; ++i) W64[12 * (size_t)S + i] = w[i];
+    // pair-precision copy in the operator's layout
+    T buf[12];
+    int n = 0;
+    if (op == TP_OP_A || op == TP_OP_B)
+        for (int i = 0; i < 9; ++i) buf[n++] = (T)w[i];
+    if (op == TP_OP_A || op == TP_OP_B0 || op == TP_OP_L)
+        for (int c = 0; c < 3; ++c) buf[n++] = (T)w[9 + c];
+    while (n < 4 * nw4) buf[n++] = T(0);
+    T* out = reinterpret_cast<T*>(Wp) + (size_t)S * 4 * nw4;
+    for (int i = 0; i < 4 * nw4; ++i) out[i] = buf[i];
+}
+
+template <typename T, int OP>
+__global__ void __launch_bounds__(NT)
+k_apply(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::type* __restrict__ fb,
+        const typename V4T<T>::type* __restrict__ Wp, int nf, int tiles_per_split, T s_exp,
+        T l_exp, double* __restrict__ part) {
+    using V4 = typename V4T<T>::type;
+    using L = OpLayout<OP>;
+    constexpr bool LOW = (OP == TP_OP_A || OP == TP_OP_B0);
+    constexpr bool HIGH = (OP == TP_OP_A || OP == TP_OP_B);
+    __shared__ V4 sa[NT];
+    __shared__ V4 sb[LOW ? NT : 1];
+    __shared__ V4 sw[NT * L::NW4];
+    const int t = blockIdx.x * NT + threadIdx.x;
+    T tx = 0, ty = 0, tz = 0, nx = 0, ny = 0, nz = 0;
+    if (t < nf) {
+        V4 A = fa[t];
+        tx = A.x; ty = A.y; tz = A.z;
+        if (LOW) {
+            V4 B = fb[t];
+            nx = B.x; ny = B.y; nz = B.z;
+        }
+    }
+    Acc<T> acc[L::NA];
+    const int ntiles = (nf + NT - 1) / NT;
+    const int k0 = blockIdx.y * tiles_per_split;
+    const int k1 = min(k0 + tiles_per_split, ntiles);
+    for (int tile = k0; tile < k1; ++tile) {
+        int src = tile * NT + threadIdx.x;
+        __syncthreads();
+        sa[threadIdx.x] = src < nf ? fa[src] : v4zero<T>();
+        if (LOW) sb[threadIdx.x] = src < nf ? fb[src] : v4zero<T>();
+        for (int i = threadIdx.x; i < NT * L::NW4; i += NT) {
+            int f = tile * NT + i / L::NW4;
+            sw[i] = f < nf ? Wp[(size_t)tile * NT * L::NW4 + i] : v4zero<T>();
+        }
+        __syncthreads();
+        for (int c = 0; c < NT; c += CH) {
+            T pt[L::NA];
+#pragma unroll
+            for (int i = 0; i < L::NA; ++i) pt[i] = T(0);
+#pragma unroll 2
+            for (int q = 0; q < CH; ++q) {
+                const int j = c + q;
+                V4 s = sa[j];
+                T dx = tx - s.x, dy = ty - s.y, dz = tz - s.z;
+                T r2 = dx * dx + dy * dy + dz * dz;
+                bool valid = r2 > T(0);
+                T r2c = fmax(r2, tiny_r2<T>());
+                T wv[4 * L::NW4];
+#pragma unroll
+                for (int i = 0; i < L::NW4; ++i) {
+                    V4 x = sw[j * L::NW4 + i];
+                    wv[4 * i] = x.x; wv[4 * i + 1] = x.y; wv[4 * i + 2] = x.z; wv[4 * i + 3] = x.w;
+                }
+                if (OP == TP_OP_L) {
+                    T h = valid ? pow_(r2c, -l_exp) : T(0);
+                    pt[0] = fma(h, s.w, pt[0]);
+#pragma unroll
+                    for (int i = 0; i < 3; ++i) pt[1 + i] = fma(h, wv[i], pt[1 + i]);
+                } else {
+                    T hB = valid ? pow_(r2c, -s_exp) : T(0);
+                    int o = 0;
+                    if (HIGH) {
+                        pt[0] = fma(hB, s.w, pt[0]);
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) pt[1 + i] = fma(hB, wv[i], pt[1 + i]);
+                        o = 10;
+                    }
+                    if (LOW) {
+                        V4 n = sb[j];
+                        T uS = nx * dx + ny * dy + nz * dz;
+                        T uT = n.x * dx + n.y * dy + n.z * dz;
+                        T ir2 = rcp_(r2c);
+                        T h0 = T(0.5) * (uS * uS + uT * uT) * (ir2 * ir2) * hB;
+                        const int wo = HIGH ? 9 : 0;
+                        pt[o] = fma(h0, s.w, pt[o]);
+#pragma unroll
+                        for (int i = 0; i < 3; ++i) pt[o + 1 + i] = fma(h0, wv[wo + i], pt[o + 1 + i]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < L::NA; ++i) acc[i].add(pt[i]);
+        }
+    }
+    if (t < nf)
+#pragma unroll
+        for (int i = 0; i < L::NA; ++i) part[((size_t)blockIdx.y * L::NA + i) * nf + t] = acc[i].value();
+}
+
+// per face: z = (r/a) W_S - (H W)_S in FP64, then the corner values of the
+// transposed map: 2 a_S grad phi_c . zV (B) and 2 a_S zU / 3 (B0, L)
+__global__ void k_apply_combine(const double* __restrict__ part, int nsplit, int nf, int op, int na,
+                                const d4* __restrict__ f64a, const double* __restrict__ fgrad,
+                                const double* __restrict__ W64, int k, int col0,
+                                double* __restrict__ corner) {
+    int S = blockIdx.x * blockDim.x + threadIdx.x;
+    if (S >= nf) return;
+    double s[14];
+    for (int i = 0; i < na; ++i) {
+        double x = 0.0;
+        for (int sp = 0; sp < nsplit; ++sp) x += part[((size_t)sp * na + i) * nf + S];
+        s[i] = x;
+    }
+    double a = f64a[S].w;
+    const double* W = W64 + 12 * (size_t)S;
+    double zV[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, zU[3] = {0, 0, 0};
+    int o = 0;
+    if (op == TP_OP_A || op == TP_OP_B) {
+        double r = s[0] / a;
+        for (int i = 0; i < 9; ++i) zV[i] = r * W[i] - s[1 + i];
+        o = 10;
+    }
+    if (op != TP_OP_B) {
+        double r = s[o] / a;
+        for (int c = 0; c < 3; ++c) zU[c] = r * W[9 + c] - s[o + 1 + c];
+    }
+    for (int cr = 0; cr < 3; ++cr)
+        for (int c = 0; c < KC && col0 + c < k; ++c) {
+            double g = 0.0;
+            for (int q = 0; q < 3; ++q) g += fgrad[9 * S + 3 * cr + q] * zV[q * KC + c];
+            corner[((size_t)S * 3 + cr) * k + col0 + c] = 2.0 * a * (g + zU[c] / 3.0);
+        }
+}
+
+template <typename T, int OP>
+static int launch_apply_op(tp_mesh* m, const tp_params* p, const double* v, int k, double* y,
+                           cudaStream_t st) {
+    using V4 = typename V4T<T>::type;
+    using L = OpLayout<OP>;
+    const int nf = m->nf;
+    const double s = 2.0 - 2.0 / p->p;       // Sobolev order, §2.3
+    const double l_exp = 3.0 - s;            // |d|^{-(2 sigma + 2)} = r2^{-(sigma+1)}, sigma = 2 - s
+    Grid g = make_grid(nf, nf, 1);
+    TP_TRY(ensure(m->part, sizeof(double) * (size_t)g.nsplit * L::NA * nf));
+    TP_TRY(ensure(m->wv64, sizeof(double) * 12 * (size_t)nf));
+    TP_TRY(ensure(m->wv32, sizeof(V4) * L::NW4 * (size_t)nf));
+    TP_TRY(ensure(m->corner, sizeof(double) * 3 * (size_t)nf * k));
+    const V4* fa = (const V4*)(sizeof(T) == 4 ? m->f32a.ptr : m->f64a.ptr);
+    const V4* fb = (const V4*)(sizeof(T) == 4 ? m->f32b.ptr : m->f64b.ptr);
+    for (int col0 = 0; col0 < k; col0 += KC) {
+        k_face_W<T><<<(nf + 255) / 256, 256, 0, st>>>(v, k, col0, m->faces.as<int>(), nf,
+                                                      m->f64a.as<d4>(), m->fgrad.as<double>(), OP,
+                                                      m->wv64.as<double>(), m->wv32.as<V4>(), L::NW4);
+        TP_LAUNCH_CHECK();
+        dim3 grid(g.bx, g.nsplit);
+        {
+            const double units = (double)nf * (nf - 1);
+            m->pairs += units;
+            constexpr int key = OP == TP_OP_A ? PK_APPLY_A : OP == TP_OP_B ? PK_APPLY_B
+                              : OP == TP_OP_B0 ? PK_APPLY_B0 : PK_APPLY_L;
+            ProfScope ps(m, key, units, st);
+            k_apply<T, OP><<<grid, NT, 0, st>>>(fa, fb, m->wv32.as<V4>(), nf, g.tiles_per_split, T(s),
+                                                T(l_exp), m->part.as<double>());
+        }
+        TP_LAUNCH_CHECK();
+        k_apply_combine<<<(nf + 255) / 256, 256, 0, st>>>(m->part.as<double>(), g.nsplit, nf, OP,
+                                                          L::NA, m->f64a.as<d4>(),
+                                                          m->fgrad.as<double>(),
+                                                          m->wv64.as<double>(), k, col0,
+                                                          m->corner.as<double>());
+        TP_LAUNCH_CHECK();
+    }
+    return corners_to_vertices(m, m->corner.as<double>(), k, y, st);
+}
+
+template <typename T>
+static int launch_apply(tp_mesh* m, const tp_params* p, int op, const double* v, int k, double* y,
+                        cudaStream_t st) {
+    switch (op) {
+        case TP_OP_A: return launch_apply_op<T, TP_OP_A>(m, p, v, k, y, st);
+        case TP_OP_B: return launch_apply_op<T, TP_OP_B>(m, p, v, k, y, st);
+        case TP_OP_B0: return launch_apply_op<T, TP_OP_B0>(m, p, v, k, y, st);
+        case TP_OP_L: return launch_apply_op<T, TP_OP_L>(m, p, v, k, y, st);
+    }
+    return fail(TP_ERR_INVALID_ARG, "unknown operator");
+}
+
+int apply_direct(tp_mesh* m, const tp_params* p, int op, const double* v, int k, double* y,
+                 cudaStream_t st) {
+    return p->precision == TP_PREC_FP64 ? launch_apply<double>(m, p, op, v, k, y, st)
+                                        : launch_apply<float>(m, p, op, v, k, y, st);
+}
+
+}  // namespace tp

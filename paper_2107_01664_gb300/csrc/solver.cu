@@ -1,0 +1,412 @@
+// Device-resident orchestration of the descent step (§5.4):
+//   energy and differential (direct or Barnes-Hut),
+//   the preconditioner C^+ L^{2-s} C^+ (§5.2),
+//   flexible GMRES on A_3 in the mean-zero subspace (§5, §5.4 step 3a),
+//   the Schur-complement direction and correction (§5.3, Eq. 17-19),
+//   Armijo line search and the corrective projection (§3.3.2).
+// All solver vectors are FP64 [nv][3] on the device; only the small
+// Hessenberg / Schur systems live on the host.
+#include <cmath>
+#include <vector>
+
+#include "tp_internal.cuh"
+
+namespace tp {
+
+// ---------------------------------------------------------------------------
+// energy / differential dispatch
+// ---------------------------------------------------------------------------
+
+int energy_value(tp_mesh* m, const tp_params* p, double* E_host, cudaStream_t st) {
+    TP_TRY(ensure(m->erow, sizeof(double) * m->nf));
+    TP_TRY(ensure(m->rowsum, sizeof(double) * 8));
+    if (p->theta > 0.0)
+        TP_TRY(energy_rows_bh(m, p, nullptr, m->nf, m->erow.as<double>(), st));
+    else
+        TP_TRY(energy_rows_direct(m, p, nullptr, m->nf, m->erow.as<double>(), st));
+    TP_TRY(sum_f64(m->erow.as<double>(), m->nf, m->rowsum.as<double>(), m, st));
+    TP_CUDA(cudaMemcpyAsync(E_host, m->rowsum.ptr, sizeof(double), cudaMemcpyDeviceToHost, st));
+    TP_CUDA(cudaStreamSynchronize(st));
+    return TP_OK;
+}
+
+int differential_dev(tp_mesh* m, const tp_params* p, double* dE, double* E_host, cudaStream_t st) {
+    TP_TRY(ensure(m->adj, sizeof(double) * 7 * (size_t)m->nf));
+    TP_TRY(ensure(m->erow, sizeof(double) * m->nf));
+    if (p->theta > 0.0)
+        TP_TRY(diff_adjoints_bh(m, p, m->adj.as<double>(), m->erow.as<double>(), st));
+    else
+        TP_TRY(diff_adjoints_direct(m, p, m->adj.as<double>(), m->erow.as<double>(), st));
+    TP_TRY(adjoints_to_dE(m, m->adj.as<double>(), dE, st));
+    if (E_host) {
+        TP_TRY(ensure(m->rowsum, sizeof(double) * 8));
+        TP_TRY(sum_f64(m->erow.as<double>(), m->nf, m->rowsum.as<double>(), m, st));
+        TP_CUDA(cudaMemcpyAsync(E_host, m->rowsum.ptr, sizeof(double), cudaMemcpyDeviceToHost, st));
+        TP_CUDA(cudaStreamSynchronize(st));
+    }
+    return TP_OK;
+}
+
+// y = A v for the GMRES operator (mean-zero output)
+static int apply_A(tp_mesh* m, const tp_params* p, const double* v, double* y, cudaStream_t st) {
+    TP_TRY(apply_direct(m, p, TP_OP_A, v, 3, y, st));
+    return project_mean_zero(m, y, 3, st);
+}
+
+// z = C^+ L^{2-s} C^+ b (§5.2); b, z [nv][k] device
+int precond_apply_dev(tp_mesh* m, const tp_params* p, const double* b, int k, double* z,
+                      cudaStream_t st, int* cg_iters) {
+    const size_t n = (size_t)m->nv * k;
+    TP_TRY(ensure(m->prec[0], sizeof(double) * n));
+    TP_TRY(ensure(m->prec[1], sizeof(double) * n));
+    int it1 = 0, it2 = 0;
+    TP_TRY(cg_solve(m, p, b, k, m->prec[0].as<double>(), st, &it1));
+    TP_TRY(apply_direct(m, p, TP_OP_L, m->prec[0].as<double>(), k, m->prec[1].as<double>(), st));
+    TP_TRY(project_mean_zero(m, m->prec[1].as<double>(), k, st));
+    TP_TRY(cg_solve(m, p, m->prec[1].as<double>(), k, z, st, &it2));
+    if (cg_iters) *cg_iters += it1 + it2;
+    return TP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// flexible GMRES(m), right preconditioning, on the mean-zero subspace
+// ---------------------------------------------------------------------------
+
+struct KrylovStats {
+    int iters = 0, cg_iters = 0;
+    double rel_res = 0.0;
+};
+
+static int fgmres(tp_mesh* m, const tp_params* p, const double* b, double* x, cudaStream_t st,
+                  KrylovStats* ks) {
+    const int mr = p->gmres_restart < 1 ? 1 : (p->gmres_restart > 60 ? 60 : p->gmres_restart);
+    const size_t n = (size_t)m->nv * 3;
+    TP_TRY(ensure(m->kry, sizeof(double) * n * (2 * mr + 1)));
+    TP_TRY(ensure(m->tmpv[5], sizeof(double) * n));
+    double* Vb = m->kry.as<double>();
+    auto Vv = [&](int j) { return Vb + (size_t)j * n; };
+    auto Zv = [&](int j) { return Vb + (size_t)(mr + 1 + j) * n; };
+    double* w = m->tmpv[5].as<double>();
+
+    TP_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
+    // r0 = b (projected)
+    TP_CUDA(cudaMemcpyAsync(Vv(0), b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    TP_TRY(project_mean_zero(m, Vv(0), 3, st));
+    double bn2;
+    {
+        const double* xs[1] = {Vv(0)};
+        TP_TRY(dots(m, xs, Vv(0), 1, n, &bn2, st));
+    }
+    const double bnorm = std::sqrt(bn2);
+    ks->rel_res = 0.0;
+    if (bnorm == 0.0) return TP_OK;
+    double beta = bnorm;
+    int total = 0;
+    std::vector<double> H((mr + 1) * mr), cs(mr), sn(mr), g(mr + 1), y(mr);
+    bool converged = false;
+    while (!converged && total < p->krylov_max) {
+        {
+            double sc = 1.0 / beta;
+            const double* xs[1] = {Vv(0)};
+            TP_TRY(lincomb(Vv(0), xs, &sc, 1, n, 0.0, st));
+        }
+        std::fill(g.begin(), g.end(), 0.0);
+        g[0] = beta;
+        int j = 0;
+        for (; j < mr && total < p->krylov_max; ++j) {
+            TP_TRY(precond_apply_dev(m, p, Vv(j), 3, Zv(j), st, &ks->cg_iters));
+            TP_TRY(apply_A(m, p, Zv(j), w, st));
+            // classical Gram-Schmidt, twice
+            std::vector<const double*> basis(j + 1);
+            for (int i = 0; i <= j; ++i) basis[i] = Vv(i);
+            std::vector<double> h(j + 1), h2(j + 1);
+            TP_TRY(dots(m, basis.data(), w, j + 1, n, h.data(), st));
+            std::vector<double> neg(j + 1);
+            for (int i = 0; i <= j; ++i) neg[i] = -h[i];
+            TP_TRY(lincomb(w, basis.data(), neg.data(), j + 1, n, 1.0, st));
+            TP_TRY(dots(m, basis.data(), w, j + 1, n, h2.data(), st));
+            for (int i = 0; i <= j; ++i) neg[i] = -h2[i];
+            TP_TRY(lincomb(w, basis.data(), neg.data(), j + 1, n, 1.0, st));
+            for (int i = 0; i <= j; ++i) H[i * mr + j] = h[i] + h2[i];
+            double wn2;
+            {
+                const double* xs[1] = {w};
+                TP_TRY(dots(m, xs, w, 1, n, &wn2, st));
+            }
+            double hn = std::sqrt(wn2);
+            H[(j + 1) * mr + j] = hn;
+            if (hn > 0.0) {
+                double sc = 1.0 / hn;
+                const double* xs[1] = {w};
+                TP_TRY(lincomb(Vv(j + 1), xs, &sc, 1, n, 0.0, st));
+            }
+            // Givens rotations
+            for (int i = 0; i < j; ++i) {
+                double a = H[i * mr + j], c = H[(i + 1) * mr + j];
+                H[i * mr + j] = cs[i] * a + sn[i] * c;
+                H[(i + 1) * mr + j] = -sn[i] * a + cs[i] * c;
+            }
+            double a = H[j * mr + j], c = H[(j + 1) * mr + j];
+            double r = std::hypot(a, c);
+            cs[j] = r > 0.0 ? a / r : 1.0;
+            sn[j] = r > 0.0 ? c / r : 0.0;
+            H[j * mr + j] = r;
+            H[(j + 1) * mr + j] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            ++total;
+            ks->rel_res = std::fabs(g[j + 1]) / bnorm;
+            if (ks->rel_res <= p->krylov_tol || hn == 0.0) {
+                ++j;
+                converged = true;
+                break;
+            }
+        }
+        // x += Z y, with H y = g (upper triangular, size j)
+        for (int i = j - 1; i >= 0; --i) {
+            double s = g[i];
+            for (int l = i + 1; l < j; ++l) s -= H[i * mr + l] * y[l];
+            y[i] = H[i * mr + i] != 0.0 ? s / H[i * mr + i] : 0.0;
+        }
+        std::vector<const double*> zs(j);
+        for (int i = 0; i < j; ++i) zs[i] = Zv(i);
+        TP_TRY(lincomb(x, zs.data(), y.data(), j, n, 1.0, st));
+        if (converged) break;
+        // restart from the true residual r = b - A x
+        TP_TRY(apply_A(m, p, x, w, st));
+        {
+            const double* xs[2] = {b, w};
+            double cf[2] = {1.0, -1.0};
+            TP_TRY(lincomb(Vv(0), xs, cf, 2, n, 0.0, st));
+        }
+        TP_TRY(project_mean_zero(m, Vv(0), 3, st));
+        double rn2;
+        {
+            const double* xs[1] = {Vv(0)};
+            TP_TRY(dots(m, xs, Vv(0), 1, n, &rn2, st));
+        }
+        beta = std::sqrt(rn2);
+        ks->rel_res = beta / bnorm;
+        if (ks->rel_res <= p->krylov_tol) converged = true;
+    }
+    ks->iters += total;
+    TP_TRY(project_mean_zero(m, x, 3, st));
+    if (!converged)
+        return fail(TP_ERR_NOT_CONVERGED, "gmres: relative residual " + std::to_string(ks->rel_res) +
+                                              " after " + std::to_string(total) + " iterations");
+    return TP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// constraints (§7.1.3 area, §7.1.4 volume): values and gradients
+// ---------------------------------------------------------------------------
+
+// per face: area, volume term; per corner: area and volume gradients
+__global__ void k_constraint_terms(const double* __restrict__ pos, const int* __restrict__ faces, int nf,
+                                   double* __restrict__ fterm /* [nf][2] */,
+                                   double* __restrict__ cga /* [nf*3][3] */,
+                                   double* __restrict__ cgv /* [nf*3][3] */) {
+    int S = blockIdx.x * blockDim.x + threadIdx.x;
+    if (S >= nf) return;
+    int id[3] = {faces[3 * S], faces[3 * S + 1], faces[3 * S + 2]};
+    double P[3][3];
+    for (int c = 0; c < 3; ++c)
+        for (int q = 0; q < 3; ++q) P[c][q] = pos[3 * id[c] + q];
+    double e1[3], e2[3];
+    for (int q = 0; q < 3; ++q) {
+        e1[q] = P[1][q] - P[0][q];
+        e2[q] = P[2][q] - P[0][q];
+    }
+    double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    double N[3] = {n[0] / nn, n[1] / nn, n[2] / nn};
+    const double* a = P[0];
+    const double* b = P[1];
+    const double* c = P[2];
+    double bxc[3] = {b[1] * c[2] - b[2] * c[1], b[2] * c[0] - b[0] * c[2], b[0] * c[1] - b[1] * c[0]};
+    fterm[2 * S] = 0.5 * nn;
+    fterm[2 * S + 1] = (a[0] * bxc[0] + a[1] * bxc[1] + a[2] * bxc[2]) / 6.0;
+    for (int cr = 0; cr < 3; ++cr) {
+        const double* pj = P[(cr + 1) % 3];
+        const double* pk = P[(cr + 2) % 3];
+        double e[3] = {pk[0] - pj[0], pk[1] - pj[1], pk[2] - pj[2]};
+        double ga[3] = {N[1] * e[2] - N[2] * e[1], N[2] * e[0] - N[0] * e[2], N[0] * e[1] - N[1] * e[0]};
+        double gv[3] = {pj[1] * pk[2] - pj[2] * pk[1], pj[2] * pk[0] - pj[0] * pk[2],
+                        pj[0] * pk[1] - pj[1] * pk[0]};
+        for (int q = 0; q < 3; ++q) {
+            cga[(3 * S + cr) * 3 + q] = 0.5 * ga[q];
+            cgv[(3 * S + cr) * 3 + q] = gv[q] / 6.0;
+        }
+    }
+}
+
+// values [area, volume] to host; gradients (if gA/gV non-null) to device [nv][3]
+static int constraints_eval(tp_mesh* m, const double* pos, double vals[2], double* gA, double* gV,
+                            cudaStream_t st) {
+    const int nf = m->nf;
+    TP_TRY(ensure(m->tmpv[7], sizeof(double) * 2 * (size_t)nf));
+    TP_TRY(ensure(m->corner, sizeof(double) * 18 * (size_t)nf));
+    TP_TRY(ensure(m->rowsum, sizeof(double) * 8));
+    double* ft = m->tmpv[7].as<double>();
+    double* cga = m->corner.as<double>();
+    double* cgv = cga + 9 * (size_t)nf;
+    k_constraint_terms<<<(nf + 255) / 256, 256, 0, st>>>(pos, m->faces.as<int>(), nf, ft, cga, cgv);
+    TP_LAUNCH_CHECK();
+    TP_TRY(colsum(m, ft, nf, 2, 1.0, m->rowsum.as<double>(), st));
+    TP_CUDA(cudaMemcpyAsync(vals, m->rowsum.ptr, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (gA) TP_TRY(corners_to_vertices(m, cga, 3, gA, st));
+    if (gV) TP_TRY(corners_to_vertices(m, cgv, 3, gV, st));
+    TP_CUDA(cudaStreamSynchronize(st));
+    return TP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// one constrained descent step
+// ---------------------------------------------------------------------------
+
+static int set_positions_dev(tp_mesh* m, const double* src, cudaStream_t st) {
+    if (src != m->pos.as<double>())
+        TP_CUDA(cudaMemcpyAsync(m->pos.ptr, src, sizeof(double) * 3 * (size_t)m->nv,
+                                cudaMemcpyDeviceToDevice, st));
+    return refresh_geometry(m, st);
+}
+
+int precond_step_dev(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp_step_report* rep,
+                     cudaStream_t st) {
+    const size_t n = (size_t)m->nv * 3;
+    for (int i = 0; i < 8; ++i) TP_TRY(ensure(m->stepv[i], sizeof(double) * n));
+    double* f0 = m->stepv[0].as<double>();   // positions at the start
+    double* g = m->stepv[1].as<double>();    // dE
+    double* Ag = m->stepv[2].as<double>();   // A^-1 g
+    double* J[2] = {m->stepv[3].as<double>(), m->stepv[4].as<double>()};   // dPhi rows
+    double* Z[2] = {m->stepv[5].as<double>(), m->stepv[6].as<double>()};   // A^-1 dPhi^T
+    double* x = m->stepv[7].as<double>();    // direction
+    tp_step_report r{};
+    r.status = TP_OK;
+    const double pairs0 = m->pairs;
+    unsigned long long bh0[2];
+    TP_TRY(bh_counts_read(m, bh0, false, st));
+    TP_CUDA(cudaMemcpyAsync(f0, m->pos.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+
+    // 1. differential
+    double E0 = 0.0;
+    TP_TRY(differential_dev(m, p, g, &E0, st));
+    r.E_before = E0;
+    // 2. constraint Jacobian rows at f
+    int use[2] = {(c->flags & TP_CONSTRAINT_AREA) ? 1 : 0, (c->flags & TP_CONSTRAINT_VOLUME) ? 1 : 0};
+    double phi0[2];
+    TP_TRY(constraints_eval(m, f0, phi0, J[0], J[1], st));
+    int nc = 0;
+    double* Jr[2];
+    double* Zr[2];
+    for (int i = 0; i < 2; ++i)
+        if (use[i]) {
+            Jr[nc] = J[i];
+            Zr[nc] = Z[i];
+            ++nc;
+        }
+    // 3. k+1 solves with A_3 (Eq. 17, 18)
+    KrylovStats ks;
+    int st_solve = fgmres(m, p, g, Ag, st, &ks);
+    if (st_solve != TP_OK && st_solve != TP_ERR_NOT_CONVERGED) return st_solve;
+    if (st_solve != TP_OK) r.status = st_solve;
+    for (int i = 0; i < nc; ++i) {
+        st_solve = fgmres(m, p, Jr[i], Zr[i], st, &ks);
+        if (st_solve != TP_OK && st_solve != TP_ERR_NOT_CONVERGED) return st_solve;
+        if (st_solve != TP_OK) r.status = st_solve;
+    }
+    // 4. Schur complement S = dPhi Z (= -(M/A)), x = -(Ag - Z S^-1 dPhi Ag)
+    double Sm[2][2] = {{0, 0}, {0, 0}}, JAg[2] = {0, 0};
+    for (int i = 0; i < nc; ++i) {
+        std::vector<const double*> zs(Zr, Zr + nc);
+        double out[2];
+        TP_TRY(dots(m, zs.data(), Jr[i], nc, n, out, st));
+        for (int j = 0; j < nc; ++j) Sm[i][j] = out[j];
+        const double* a1[1] = {Ag};
+        TP_TRY(dots(m, a1, Jr[i], 1, n, &JAg[i], st));
+    }
+    double lam[2] = {0, 0};
+    auto solve_small = [&](const double rhs[2], double out[2]) {
+        if (nc == 1) {
+            out[0] = rhs[0] / Sm[0][0];
+        } else if (nc == 2) {
+            double det = Sm[0][0] * Sm[1][1] - Sm[0][1] * Sm[1][0];
+            out[0] = (Sm[1][1] * rhs[0] - Sm[0][1] * rhs[1]) / det;
+            out[1] = (-Sm[1][0] * rhs[0] + Sm[0][0] * rhs[1]) / det;
+        }
+    };
+    solve_small(JAg, lam);
+    {
+        std::vector<const double*> xs;
+        std::vector<double> cf;
+        xs.push_back(Ag);
+        cf.push_back(-1.0);
+        for (int i = 0; i < nc; ++i) {
+            xs.push_back(Zr[i]);
+            cf.push_back(lam[i]);
+        }
+        TP_TRY(lincomb(x, xs.data(), cf.data(), (int)xs.size(), n, 0.0, st));
+    }
+    {
+        const double* a1[1] = {g};
+        TP_TRY(dots(m, a1, x, 1, n, &r.slope, st));
+    }
+    // 5. Armijo line search on E(f + tau x)
+    double tau = p->tau0;
+    double* ftrial = m->pos.as<double>();
+    int trials = 0;
+    double E1 = E0;
+    for (;;) {
+        const double* xs[2] = {f0, x};
+        double cf[2] = {1.0, tau};
+        TP_TRY(lincomb(ftrial, xs, cf, 2, n, 0.0, st));
+        int gs = refresh_geometry(m, st);
+        ++trials;
+        if (gs == TP_OK) {
+            TP_TRY(energy_value(m, p, &E1, st));
+            if (p->fixed_tau || E1 <= E0 + p->armijo_c * tau * r.slope) break;
+        } else if (gs != TP_ERR_DEGENERATE) {
+            return gs;
+        }
+        if (trials >= p->ls_max) break;
+        tau *= p->armijo_shrink;
+    }
+    r.tau = tau;
+    r.ls_trials = trials;
+    // 6. corrective projection (Eq. 15 / 19): h = -Z S^-1 Phi(f_k), Z and S
+    //    of the start of the step, repeated proj_iters times
+    double phi1[2];
+    TP_TRY(constraints_eval(m, m->pos.as<double>(), phi1, nullptr, nullptr, st));
+    r.phi_before[0] = use[0] ? phi1[0] - c->A0 : 0.0;
+    r.phi_before[1] = use[1] ? phi1[1] - c->V0 : 0.0;
+    for (int it = 0; it < p->proj_iters && nc > 0; ++it) {
+        if (it > 0) {
+            TP_TRY(refresh_geometry(m, st));
+            TP_TRY(constraints_eval(m, m->pos.as<double>(), phi1, nullptr, nullptr, st));
+        }
+        double res[2] = {0, 0};
+        int ci = 0;
+        if (use[0]) res[ci++] = phi1[0] - c->A0;
+        if (use[1]) res[ci++] = phi1[1] - c->V0;
+        double mu[2] = {0, 0};
+        solve_small(res, mu);
+        std::vector<double> cf(nc);
+        for (int i = 0; i < nc; ++i) cf[i] = -mu[i];
+        TP_TRY(lincomb(m->pos.as<double>(), (const double* const*)Zr, cf.data(), nc, n, 1.0, st));
+    }
+    TP_TRY(set_positions_dev(m, m->pos.as<double>(), st));
+    double phi2[2];
+    TP_TRY(constraints_eval(m, m->pos.as<double>(), phi2, nullptr, nullptr, st));
+    r.phi_after[0] = use[0] ? phi2[0] - c->A0 : 0.0;
+    r.phi_after[1] = use[1] ? phi2[1] - c->V0 : 0.0;
+    TP_TRY(energy_value(m, p, &r.E_after, st));
+    r.krylov_iters = ks.iters;
+    r.cg_iters = ks.cg_iters;
+    unsigned long long bh1[2];
+    TP_TRY(bh_counts_read(m, bh1, false, st));
+    r.pair_interactions = (m->pairs - pairs0) + (double)(bh1[0] - bh0[0]) + (double)(bh1[1] - bh0[1]);
+    if (rep) *rep = r;
+    return TP_OK;
+}
+
+}  // namespace tp

@@ -1,0 +1,201 @@
+// Internal declarations shared by the translation units of libtpsurf.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "tp.h"
+
+// ---------------------------------------------------------------------------
+// error handling
+// ---------------------------------------------------------------------------
+
+namespace tp {
+
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+#define TP_CUDA(call)                                                              \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess)                                                     \
+            return ::tp::fail(e_ == cudaErrorMemoryAllocation ? TP_ERR_OOM         \
+                                                              : TP_ERR_CUDA,       \
+                              std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define TP_TRY(call)                 \
+    do {                             \
+        int s_ = (call);             \
+        if (s_ != TP_OK) return s_;  \
+    } while (0)
+
+// every launch site of the library calls TP_LAUNCH_CHECK once per launch
+void count_launches(unsigned long long n);
+#define TP_LAUNCH_CHECK()            \
+    do {                             \
+        ::tp::count_launches(1);     \
+        TP_CUDA(cudaGetLastError()); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// device buffers (grow-only)
+// ---------------------------------------------------------------------------
+
+struct Buf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+int ensure(Buf& b, size_t bytes);
+void release(Buf& b);
+
+// 32-byte FP64 quadruple used for face tables of the FP64 path
+struct alignas(32) d4 {
+    double x, y, z, w;
+};
+
+// number of SMs of the current device (cached per device)
+int sm_count();
+
+// ---------------------------------------------------------------------------
+// Barnes-Hut tree (implicit, Morton-ordered; built on the device)
+// ---------------------------------------------------------------------------
+
+struct BvhNode {          // 64 bytes, FP32 (pair path)
+    float cx, cy, cz, a;  // area-weighted barycenter (relative frame), total area
+    float lox, loy, loz, r2;   // AABB of the barycenters' faces (lower), squared radius
+    float hix, hiy, hiz, pad;  // AABB (upper)
+    int first, count, skip, leaf;  // face range in Morton order, escape index, leaf flag
+};
+
+// ---------------------------------------------------------------------------
+// per-mesh kernel statistics (CUDA events on the launching stream)
+// ---------------------------------------------------------------------------
+
+enum ProfKey { PK_ENERGY = 0, PK_DIFF, PK_APPLY_A, PK_APPLY_B, PK_APPLY_B0, PK_APPLY_L, PK_BH_ENERGY,
+               PK_BH_DIFF, PK_BVH_BUILD, PK_CG, PK_COUNT };
+
+struct Profiler {
+    bool on = false;
+    long long launches[PK_COUNT] = {};
+    double ms[PK_COUNT] = {};
+    double units[PK_COUNT] = {};
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+};
+
+}  // namespace tp
+
+struct tp_mesh {
+    int device = 0;
+    int nv = 0, nf = 0;
+    // topology (fixed for the life of the mesh)
+    tp::Buf faces;      // int32 [nf*3]
+    tp::Buf vf_ptr;     // int32 [nv+1]  vertex -> incident (face*3+corner)
+    tp::Buf vf_idx;     // int32 [3*nf]
+    // positions
+    tp::Buf pos;        // double [nv*3]
+    tp::Buf center;     // double [4]    reference frame of the FP32 face table
+    tp::Buf errflag;    // int [4]
+    // face tables
+    tp::Buf f32a;       // float4 [nf]   X - c, a
+    tp::Buf f32b;       // float4 [nf]   N, 0
+    tp::Buf f64a;       // d4 [nf]       X - c, a
+    tp::Buf f64b;       // d4 [nf]       N, 0
+    tp::Buf fgrad;      // double [nf*9] gradients of the three hat functions
+    // cotan Laplacian (pattern fixed, values per positions)
+    int nnz = 0;
+    tp::Buf rowptr, col, cotsrc, diagpos, val, dinv;
+    bool lap_valid = false;
+    // Barnes-Hut tree (rebuilt per positions on demand)
+    int bvh_nodes = 0, bvh_leaf = 0;
+    int bvh_shape_leaf = 0, bvh_maxdepth = 0;
+    std::vector<int> bvh_level_off;
+    bool bvh_valid = false;
+    tp::Buf bvh_node, bvh_perm, bvh_keys, bvh_tmp, bvh_sortws;
+    tp::Buf bvh_f32a, bvh_f32b;   // face tables permuted to Morton order
+    tp::Buf bvh_nodeP;            // float [nodes*8] node-average projector (upper triangle) for B0
+    // workspaces
+    tp::Buf part, part2, scal, corner, wv64, wv32, tmpv[8];
+    tp::Buf io_in, io_out, adj, erow, tlist, rowsum;
+    tp::Buf kry;        // FGMRES bases V and Z
+    tp::Buf stepv[8];   // vectors of the constrained step
+    tp::Buf prec[3];    // preconditioner temporaries
+    tp::Buf bhcount;    // device counter of Barnes-Hut interactions
+    tp::Profiler prof;
+    double pairs = 0.0; // pair interactions evaluated (host-known part)
+};
+
+namespace tp {
+
+// -------- mesh.cu ----------------------------------------------------------
+int refresh_geometry(tp_mesh* m, cudaStream_t st);   // face tables from m->pos
+int corners_to_vertices(tp_mesh* m, const double* corner, int k, double* y, cudaStream_t st);
+int copy_in(void* dst, const void* src, size_t bytes, int ptr_kind, cudaStream_t st);
+int copy_out(void* dst, const void* src, size_t bytes, int ptr_kind, cudaStream_t st);
+int sum_f64(const double* x, int n, double* out_dev, tp_mesh* m, cudaStream_t st);
+int colsum(tp_mesh* m, const double* x, long n, int k, double scale, double* out_dev, cudaStream_t st);
+const char* last_error();
+// profiling: wrap a launch (or a group of launches) of kernel class `key`
+// processing `units` of algorithmic work
+struct ProfScope {
+    tp_mesh* m;
+    int key;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaStream_t st;
+    ProfScope(tp_mesh* m, int key, double units, cudaStream_t st);
+    ~ProfScope();
+};
+void prof_release(tp_mesh* m);
+unsigned long long launch_count();
+
+// -------- pairs.cu ---------------------------------------------------------
+// per-target rows of Eq. 10 (targets == nullptr: all faces), written to rows_dev [nt]
+int energy_rows_direct(tp_mesh* m, const tp_params* p, const int32_t* targets_dev, int nt,
+                       double* rows_dev, cudaStream_t st);
+// face adjoints gX,gN,ga (FP64 [nf*7]) and energy rows
+int diff_adjoints_direct(tp_mesh* m, const tp_params* p, double* adj_dev, double* erow_dev,
+                         cudaStream_t st);
+// adjoints -> per-face corner gradients [nf*3*3] -> dE [nv*3]
+int adjoints_to_dE(tp_mesh* m, const double* adj_dev, double* dE_dev, cudaStream_t st);
+// y = O v (device, [nv*k]); direct all pairs
+int apply_direct(tp_mesh* m, const tp_params* p, int op, const double* v_dev, int k,
+                 double* y_dev, cudaStream_t st);
+
+// -------- bvh.cu -----------------------------------------------------------
+int bvh_build(tp_mesh* m, const tp_params* p, cudaStream_t st);
+int energy_rows_bh(tp_mesh* m, const tp_params* p, const int32_t* targets_dev, int nt,
+                   double* rows_dev, cudaStream_t st);
+int diff_adjoints_bh(tp_mesh* m, const tp_params* p, double* adj_dev, double* erow_dev,
+                     cudaStream_t st);
+int bh_counter(tp_mesh* m, cudaStream_t st);
+int bh_counts_read(tp_mesh* m, unsigned long long out[2], bool reset, cudaStream_t st);
+
+// -------- cg.cu ------------------------------------------------------------
+int laplacian_setup(tp_mesh* m);                        // CSR pattern (host, once)
+int laplacian_values(tp_mesh* m, cudaStream_t st);      // cotan values for current positions
+int cg_solve(tp_mesh* m, const tp_params* p, const double* b_dev, int k, double* z_dev,
+             cudaStream_t st, int* iters);
+// vector helpers (device, FP64, deterministic)
+int project_mean_zero(tp_mesh* m, double* x_dev, int k, cudaStream_t st);
+int dots(tp_mesh* m, const double* const* xs, const double* y, int nvec, size_t n,
+         double* out_host, cudaStream_t st);
+int axpy(double* y, const double* x, double a, size_t n, cudaStream_t st);
+int lincomb(double* y, const double* const* xs, const double* coef_host, int nvec, size_t n,
+            double beta, cudaStream_t st);
+
+// -------- solver.cu --------------------------------------------------------
+int energy_value(tp_mesh* m, const tp_params* p, double* E_host, cudaStream_t st);
+int differential_dev(tp_mesh* m, const tp_params* p, double* dE_dev, double* E_host,
+                     cudaStream_t st);
+int precond_apply_dev(tp_mesh* m, const tp_params* p, const double* b, int k, double* z,
+                      cudaStream_t st, int* cg_iters);
+int precond_step_dev(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp_step_report* rep,
+                     cudaStream_t st);
+
+}  // namespace tp

@@ -1,0 +1,277 @@
+"""GPU parity of the direct (all-pairs) path against the FP64 oracle, through
+the C ABI: energy, energy rows, differential, operator applies, the cotan
+Poisson solve, the preconditioner and the constrained step.
+
+Tolerances: the FP32 pair path must agree with the oracle to 1e-5 (relative
+for E, 2-norm relative for vectors); the FP64 path to 1e-10. Sizes cover a
+single partial tile (4, 8 faces), several tiles with a ragged tail (182, 320
+faces), exact multiples of the 128-face tile (1280), and the full 20,000-face
+torus in the launch configuration of the benchmark (sampled outputs).
+"""
+import numpy as np
+import pytest
+
+from oracle import tp_oracle as O
+from synth import small_mesh, vertex_vectors, workload
+
+pytestmark = pytest.mark.gpu
+
+TOL32, TOL64 = 1e-5, 1e-10
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def dev(x, dtype=None):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(x), device="cuda:0", dtype=dtype)
+
+
+MESHES = ["tetra", "octa", "torus13x7", "ico2", "ico3"]
+
+
+@pytest.fixture(scope="module")
+def meshes(lib):
+    import torch
+    out = {}
+    for name in MESHES:
+        V, F = small_mesh(name, seed=21)
+        out[name] = (V, F, lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)))
+    yield out
+    for v in out.values():
+        v[2].close()
+
+
+@pytest.mark.parametrize("name", MESHES)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_energy(lib, meshes, name, prec):
+    V, F, m = meshes[name]
+    E = lib.tp_energy(m, lib.params(precision=prec))
+    assert rel(E, O.energy(V, F)) <= (TOL32 if prec == 0 else TOL64)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("p", [4.5, 3.0])
+def test_energy_generic_exponent(lib, meshes, prec, p):
+    V, F, m = meshes["ico2"]
+    E = lib.tp_energy(m, lib.params(precision=prec, p=p))
+    assert rel(E, O.energy(V, F, p)) <= (TOL32 if prec == 0 else TOL64)
+
+
+def test_energy_closed_forms(lib, meshes):
+    # tetrahedron and octahedron closed forms (hand-derived, see the oracle pins)
+    assert rel(lib.tp_energy(meshes["tetra"][2], lib.params(precision=1)), 60.75) < 1e-13
+    assert rel(lib.tp_energy(meshes["octa"][2], lib.params(precision=1)), 56 * 27 / 64 * 0.75) < 1e-13
+
+
+def test_energy_rows_targets(lib, meshes):
+    V, F, m = meshes["ico3"]
+    tg = np.array([0, 5, 1279, 640, 5, 77], dtype=np.int32)
+    rows = lib.tp_energy_rows(m, tg, lib.params())
+    assert rel(rows, O.energy_rows(V, F, 6.0, tg)) <= TOL32
+    rows_d = lib.tp_energy_rows(m, dev(tg), lib.params(precision=1))
+    assert rel(rows_d.cpu().numpy(), O.energy_rows(V, F, 6.0, tg)) <= TOL64
+
+
+@pytest.mark.parametrize("name", MESHES)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_differential(lib, meshes, name, prec):
+    V, F, m = meshes[name]
+    g, E = lib.tp_differential(m, lib.params(precision=prec))
+    tol = TOL32 if prec == 0 else TOL64
+    assert rel(g, O.differential(V, F)) <= tol
+    assert rel(E, O.energy(V, F)) <= tol
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_differential_generic_exponent(lib, meshes, prec):
+    V, F, m = meshes["torus13x7"]
+    g, _ = lib.tp_differential(m, lib.params(precision=prec, p=4.5))
+    assert rel(g, O.differential(V, F, 4.5)) <= (TOL32 if prec == 0 else TOL64)
+
+
+@pytest.mark.parametrize("name", ["torus13x7", "ico2", "ico3"])
+@pytest.mark.parametrize("op", ["A", "B", "B0", "L"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_operator_apply(lib, meshes, name, op, prec):
+    V, F, m = meshes[name]
+    u = vertex_vectors(len(V), 3, 101)
+    y = lib.fractional_apply(m, op, u, lib.params(precision=prec))
+    assert rel(y, O.apply_operator(V, F, u, op)) <= (TOL32 if prec == 0 else TOL64)
+
+
+@pytest.mark.parametrize("k", [1, 2, 5])
+def test_operator_apply_columns(lib, meshes, k):
+    V, F, m = meshes["ico2"]
+    u = vertex_vectors(len(V), k, 7)
+    y = lib.fractional_apply(m, "A", dev(u), lib.params())
+    assert rel(y.cpu().numpy(), O.apply_operator(V, F, u, "A")) <= TOL32
+
+
+def test_operator_constant_nullspace_and_symmetry(lib, meshes):
+    V, F, m = meshes["ico3"]
+    p = lib.params(precision=1)
+    one = np.ones((len(V), 1))
+    y = lib.fractional_apply(m, "A", one, p)
+    scale = np.abs(lib.fractional_apply(m, "A", vertex_vectors(len(V), 1, 3), p)).max()
+    assert np.abs(y).max() < 1e-10 * scale
+    a, b = vertex_vectors(len(V), 1, 4), vertex_vectors(len(V), 1, 5)
+    assert rel(float(a[:, 0] @ lib.fractional_apply(m, "A", b, p)[:, 0]),
+               float(b[:, 0] @ lib.fractional_apply(m, "A", a, p)[:, 0])) < 1e-10
+
+
+@pytest.mark.parametrize("name", ["torus13x7", "ico3"])
+def test_cotan_solve(lib, meshes, name):
+    V, F, m = meshes[name]
+    b = O.project_mean_zero(vertex_vectors(len(V), 3, 9))
+    z, it = lib.cotan_solve(m, b, lib.params(cg_tol=1e-12))
+    ref = O.poisson_solve(O.cotan_laplacian(V, F), b)
+    assert rel(z, ref) <= 1e-9
+    assert it > 0
+
+
+def test_cotan_solve_not_converged_is_reported(lib, meshes):
+    V, F, m = meshes["ico3"]
+    b = O.project_mean_zero(vertex_vectors(len(V), 1, 9))
+    with pytest.raises(lib.TpError) as e:
+        lib.cotan_solve(m, b, lib.params(cg_tol=1e-14, cg_max=3))
+    assert e.value.code == lib.TP_ERR_NOT_CONVERGED
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_precond_apply(lib, meshes, prec):
+    V, F, m = meshes["ico3"]
+    b = O.project_mean_zero(vertex_vectors(len(V), 3, 11))
+    z = lib.precond_apply(m, b, lib.params(precision=prec, cg_tol=1e-12))
+    assert rel(z, O.precond_apply(V, F, b)) <= (TOL32 if prec == 0 else 1e-9)
+
+
+def test_precond_step_matches_exact_saddle_solution(lib):
+    import torch
+    V, F = workload("icosphere_l3")
+    A0, V0 = O.total_area(V, F), O.total_volume(V, F)
+    tau = 0.5
+    ref = O.precond_step(V, F, A0, V0, fixed_tau=tau)
+    with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as m:
+        c = lib.tp_constraints(flags=lib.TP_CONSTRAINT_AREA | lib.TP_CONSTRAINT_VOLUME, A0=A0, V0=V0)
+        p = lib.params(precision=1, krylov_tol=1e-11, cg_tol=1e-12, fixed_tau=1, tau0=tau)
+        rep = lib.precond_step(m, c, p)
+        f_new = m.get_positions()
+    assert rep["status"] == 0
+    assert rel(f_new - V, ref["f_new"] - V) < 1e-7
+    assert rel(rep["E_before"], ref["E0"]) < 1e-10
+    assert rel(rep["E_after"], ref["E1"]) < 1e-8
+    # one Newton correction with the Jacobian of f: linear reduction of |Phi|
+    assert max(abs(x) for x in rep["phi_after"]) < 0.1 * max(abs(x) for x in rep["phi_before"])
+
+
+def test_precond_step_repeated_projection_matches_oracle(lib):
+    import torch
+    V, F = small_mesh("ico2", seed=8)
+    A0, V0 = O.total_area(V, F), O.total_volume(V, F)
+    ref = O.precond_step(V, F, A0, V0, fixed_tau=0.25, proj_iters=4)
+    with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as m:
+        c = lib.tp_constraints(flags=3, A0=A0, V0=V0)
+        p = lib.params(precision=1, krylov_tol=1e-11, cg_tol=1e-12, fixed_tau=1, tau0=0.25, proj_iters=4)
+        rep = lib.precond_step(m, c, p)
+        f_new = m.get_positions()
+    assert rel(f_new - V, ref["f_new"] - V) < 1e-7
+    assert abs(O.total_area(f_new, F) - A0) < 1e-9 * A0
+    assert abs(O.total_volume(f_new, F) - V0) < 1e-9 * abs(V0)
+
+
+def test_precond_step_armijo_descends(lib):
+    import torch
+    V, F = small_mesh("ico3", seed=5)
+    A0, V0 = O.total_area(V, F), O.total_volume(V, F)
+    with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as m:
+        c = lib.tp_constraints(flags=3, A0=A0, V0=V0)
+        p = lib.params(cg_tol=1e-8, proj_iters=3)
+        E = []
+        for _ in range(3):
+            rep = lib.precond_step(m, c, p)
+            assert rep["status"] == 0 and rep["slope"] < 0
+            E.append((rep["E_before"], rep["E_after"]))
+        f = m.get_positions()
+    assert all(b < a for a, b in E)
+    assert abs(O.total_area(f, F) - A0) < 1e-6 * A0
+    assert abs(O.total_volume(f, F) - V0) < 1e-6 * abs(V0)
+
+
+# ---------------------------------------------------------------------------
+# full size: the 20,000-face torus in the benchmark's launch configuration
+# ---------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def torus(lib):
+    import torch
+    V, F = workload("torus_20k")
+    m = lib.Mesh(dev(V, torch.float64), dev(F, torch.int32))
+    yield V, F, m
+    m.close()
+
+
+def _golden(name):
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "full_size.json")
+    return json.load(open(path))[name]
+
+
+def test_torus20k_energy_full(lib, torus):
+    # stored oracle value (tests/golden/make_golden.py) and sampled rows
+    V, F, m = torus
+    E32 = lib.tp_energy(m, lib.params())
+    assert rel(E32, _golden("torus_20k")["energy"]) <= TOL32
+    tg = np.random.default_rng(7).choice(len(F), 256, replace=False).astype(np.int32)
+    assert rel(lib.tp_energy_rows(m, tg, lib.params()), O.energy_rows(V, F, 6.0, tg)) <= TOL32
+
+
+def test_torus20k_differential_sampled(lib, torus):
+    V, F, m = torus
+    g, _ = lib.tp_differential(m, lib.params())
+    idx = np.random.default_rng(202).choice(len(V), 64, replace=False)
+    ref = O.differential_at_vertices(V, F, idx)
+    assert rel(g[idx], ref) <= TOL32
+
+
+@pytest.mark.parametrize("op", ["A", "L"])
+def test_torus20k_apply_sampled(lib, torus, op):
+    V, F, m = torus
+    u = vertex_vectors(len(V), 3, 202)
+    y = lib.fractional_apply(m, op, u, lib.params())
+    idx = np.random.default_rng(203).choice(len(V), 48, replace=False)
+    ref = O.apply_operator_at_vertices(V, F, u, op, idx)
+    assert rel(y[idx], ref) <= TOL32
+
+
+def test_autograd_energy_backward_is_differential(lib, meshes):
+    import torch
+    V, F, m = meshes["ico2"]
+    f = dev(V, torch.float64).requires_grad_(True)
+    E = lib.TangentPointEnergy.apply(f, m, lib.params())
+    E.backward()
+    assert rel(f.grad.cpu().numpy(), O.differential(V, F)) <= TOL32
+    assert rel(E.item(), O.energy(V, F)) <= TOL32
+
+
+def test_invalid_inputs_are_rejected(lib):
+    import torch
+    V, F = small_mesh("octa")
+    bad = F.copy()
+    bad[0, 0] = 99
+    with pytest.raises(lib.TpError) as e:
+        lib.Mesh(V, bad)
+    assert e.value.code == lib.TP_ERR_INVALID_ARG
+    degenerate = V.copy()
+    degenerate[F[0, 1]] = degenerate[F[0, 0]]
+    with pytest.raises(lib.TpError) as e:
+        lib.Mesh(degenerate, F)
+    assert e.value.code == lib.TP_ERR_DEGENERATE
+    with lib.Mesh(V, F) as m:
+        with pytest.raises(lib.TpError):
+            lib.fractional_apply(m, "A", np.zeros((len(V), 10)), lib.params())
+        with pytest.raises(lib.TpError):
+            lib.tp_energy(m, lib.params(p=1.0))

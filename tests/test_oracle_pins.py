@@ -270,6 +270,18 @@ def test_step_decreases_energy_and_projects():
     assert after < 0.2 * before
 
 
+def test_repeated_projection_converges_linearly():
+    # §3.3.2: the correction may be repeated; with the Jacobian of f each
+    # repeat shrinks the violation by a constant factor
+    V, F = small_mesh("ico2", seed=8)
+    A0, V0 = O.total_area(V, F), O.total_volume(V, F)
+    viol = []
+    for k in range(4):
+        r = O.precond_step(V, F, A0, V0, fixed_tau=0.25, proj_iters=k)
+        viol.append(np.abs(O.constraint_values(r["f_new"], F, A0, V0) / [A0, V0]).max())
+    assert all(viol[i + 1] < 0.1 * viol[i] for i in range(3)), viol
+
+
 def test_linked_tori_generator_gap():
     # the two tubes (r = 0.25) have centre lines at distance >= 1, so no
     # vertex of one torus comes closer than ~0.5 to the other's vertices
@@ -326,3 +338,13 @@ def test_pin_catches_transposed_low_order_kernel(monkeypatch):
     monkeypatch.setattr(O, "_kernel_rows", broken)
     M = O.operator_matrix(V, F, "B0")
     assert np.abs(M - M.T).max() > 1e-6 * np.abs(M).max()
+
+
+@pytest.mark.parametrize("op", ["A", "B", "B0", "L"])
+def test_sampled_operator_rows_match_full(op):
+    V, F = small_mesh("torus10x5", seed=4)
+    u = np.random.default_rng(3).standard_normal((len(V), 3))
+    y = O.apply_operator(V, F, u, op)
+    idx = [0, 11, 27, len(V) - 1]
+    assert np.allclose(O.apply_operator_at_vertices(V, F, u, op, idx), y[idx], rtol=1e-12,
+                       atol=1e-12 * np.abs(y).max())
