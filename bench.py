@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Benchmark of the tangent-point hot path on one GB300 (or N replicas).
+
+One step = one pass of the whole hot path on the 20,000-face torus
+(R=1, r=0.3, 200 x 50 grid, N(0, 0.005^2) noise), starting from the same
+seeded positions every step:
+  face geometry -> constrained preconditioned descent step (direct FP32
+  pair terms for E, dE, A = B + B0 and L^{2-s} inside flexible GMRES,
+  cotan CG solves, FP64 Schur complement, Armijo line search, corrective
+  projection) -> Barnes-Hut (theta = 0.5) energy and differential.
+
+Metric: pair interactions per second (every evaluated (target, source face)
+or (target, BVH node) term of the step), plus steps/s and step latency.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "torus_20k"
+METRIC = "pair interactions/s"
+UNIT = "pairs/s"
+# algorithmic FP32 flops per pair interaction (FMA = 2, MUFU not counted)
+FLOPS_PER_PAIR = {"energy_direct": 20, "diff_direct": 57, "apply_A": 54, "apply_B": 29,
+                  "apply_B0": 34, "apply_L": 17, "bh_energy": 20, "bh_diff": 51}
+KERNEL_SOURCE = {"energy_direct": "pairs.cu", "diff_direct": "pairs.cu", "apply_A": "pairs.cu",
+                 "apply_B": "pairs.cu", "apply_B0": "pairs.cu", "apply_L": "pairs.cu",
+                 "bh_energy": "bvh.cu", "bh_diff": "bvh.cu", "cg": "cg.cu", "bvh_build": "bvh.cu"}
+FP32_LANES_PER_SM = 128
+
+
+def step_params(tp):
+    return tp.params(theta=0.0, precision=tp.TP_PREC_FP32, krylov_tol=1e-5, krylov_max=60,
+                     gmres_restart=30, cg_tol=1e-8, cg_max=20000, proj_iters=1)
+
+
+def bh_params(tp):
+    return tp.params(theta=0.5, precision=tp.TP_PREC_FP32, leaf_size=8)
+
+
+# ---------------------------------------------------------------------------
+# CPU side: the oracle on a bounded sample of the same workload
+# ---------------------------------------------------------------------------
+
+def sample_desc(scale):
+    return (f"oracle (numpy FP64, 1 thread) on {WORKLOAD}: energy rows of {32 * scale} target faces, "
+            f"dE at {3 * scale} vertices, A.u and L.u at {3 * scale} vertices each; "
+            "pairs = rows evaluated x (nf - 1)")
+
+
+def oracle_sample_pairs_per_s(scale):
+    """Run in a subprocess with single-threaded BLAS; returns (pairs/s, seconds, pairs)."""
+    import numpy as np
+    from oracle import tp_oracle as O
+    from synth import vertex_vectors, workload
+    V, F = workload(WORKLOAD)
+    nf = len(F)
+    rng = np.random.default_rng(4242)
+    targets = rng.choice(nf, 32 * scale, replace=False)
+    nvs = 3 * scale
+    verts = rng.choice(len(V), 3 * nvs, replace=False)
+    u = vertex_vectors(len(V), 3, 202)
+    t0 = time.perf_counter()
+    O.energy_rows(V, F, 6.0, targets)
+    O.differential_at_vertices(V, F, verts[:nvs])
+    O.apply_operator_at_vertices(V, F, u, "A", verts[nvs:2 * nvs])
+    O.apply_operator_at_vertices(V, F, u, "L", verts[2 * nvs:])
+    dt = time.perf_counter() - t0
+
+    def inc_rows(vs):
+        return len(np.unique(np.concatenate([np.nonzero(np.any(F == v, axis=1))[0] for v in vs])))
+    rows = len(targets) + inc_rows(verts[:nvs]) + inc_rows(verts[nvs:2 * nvs]) + inc_rows(verts[2 * nvs:])
+    pairs = float(rows) * (nf - 1)
+    return pairs / dt, dt, pairs
+
+
+def run_cpu_sample(scale=48):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench.oracle_sample_pairs_per_s(%d)))" % (ROOT, scale))
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    v, dt, pairs = json.loads(out.stdout.strip().splitlines()[-1])
+    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample_desc(scale),
+            "seconds": round(dt, 2)}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline helpers
+# ---------------------------------------------------------------------------
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        return json.load(open(path)), "measured"
+    return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def profile_traffic(kernel, workload):
+    """DRAM bytes per launch from the committed ncu summary of this kernel, or
+    None when the summary is missing or the kernel's source changed since."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.txt")
+    if not os.path.exists(path):
+        return None
+    vals = {}
+    for ln in open(path):
+        if ":" in ln:
+            k, v = ln.split(":", 1)
+            vals[k.strip()] = v.strip()
+    src = os.path.join(ROOT, "paper_2107_01664_gb300", "csrc", KERNEL_SOURCE.get(kernel, ""))
+    if not os.path.exists(src) or "source_sha256" not in vals or "dram_bytes_per_launch" not in vals:
+        return None
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != vals["source_sha256"]:
+        return None
+    return float(vals["dram_bytes_per_launch"])
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2107_01664_gb300 as tp
+    from synth import workload
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    V, F = workload(WORKLOAD)
+    f0 = torch.tensor(V, dtype=torch.float64, device=dev)
+    faces = torch.tensor(F, dtype=torch.int32, device=dev)
+    mesh = tp.Mesh(f0, faces, device=local)
+    A0 = float(np.sum(0.5 * np.linalg.norm(np.cross(V[F[:, 1]] - V[F[:, 0]], V[F[:, 2]] - V[F[:, 0]]), axis=1)))
+    Vol0 = float(np.sum(V[F[:, 0]] * np.cross(V[F[:, 1]], V[F[:, 2]])) / 6.0)
+    cons = tp.tp_constraints(flags=tp.TP_CONSTRAINT_AREA | tp.TP_CONSTRAINT_VOLUME, A0=A0, V0=Vol0)
+    ps, pb = step_params(tp), bh_params(tp)
+    dE_buf = torch.empty((len(V), 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+
+    def one_step(f_in, like=None):
+        tp.tp_mesh_set_positions(mesh, f_in)
+        rep = tp.precond_step(mesh, cons, ps)
+        Eb = tp.tp_energy(mesh, pb)
+        dEb, _ = tp.tp_differential(mesh, pb, like=like if like is not None else dE_buf)
+        return rep, Eb, dEb
+
+    for _ in range(args.warmup):
+        one_step(f0)
+    torch.cuda.synchronize()
+    tp.tp_profile_read(mesh)                      # discard warm-up statistics
+    tp.tp_profile_enable(mesh, True)
+
+    stream = torch.cuda.current_stream(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    reps = []
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = tp.tp_launch_count()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()                              # L2 flushed between timed steps
+        ev[k][0].record(stream)
+        rep, Eb, dEb = one_step(f0)
+        ev[k][1].record(stream)
+        reps.append(rep)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    launches = tp.tp_launch_count() - launches0
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    if world > 1:
+        dist.barrier()
+    prof = tp.tp_profile_read(mesh)
+    tp.tp_profile_enable(mesh, False)
+
+    pair_kernels = [k for k in prof if k in FLOPS_PER_PAIR]
+    pairs_total = sum(prof[k]["units"] for k in pair_kernels)
+    dev_ms = float(sum(step_ms))
+    # whole-job aggregate over ranks: max time, summed work
+    t = torch.tensor([dev_ms, pairs_total], dtype=torch.float64, device=dev)
+    if world > 1:
+        tmax = t[0:1].clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t[1:2].clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        dev_ms_all, pairs_all = float(tmax.item()), float(tsum.item())
+    else:
+        dev_ms_all, pairs_all = dev_ms, pairs_total
+    value = pairs_all / (dev_ms_all / 1e3)
+
+    # e2e through the C ABI with host buffers: pinned positions in, positions + dE out
+    f_host = torch.tensor(V, dtype=torch.float64).pin_memory()
+    e2e_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_pairs = 0.0
+    for _ in range(e2e_steps):
+        tp.tp_mesh_set_positions(mesh, f_host)
+        rep = tp.precond_step(mesh, cons, ps)
+        tp.tp_energy(mesh, pb)
+        tp.tp_differential(mesh, pb, like=None)      # dE to host
+        tp.tp_mesh_get_positions(mesh, None)          # positions to host
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    pairs_per_step = pairs_total / args.steps
+    e2e = {"value": pairs_per_step / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(len(V) * 3 * 8),
+           "d2h_bytes_per_step": int(2 * len(V) * 3 * 8 + 8 * 3)}
+
+    # roofline of the dominant kernel
+    dom = max(prof, key=lambda k: prof[k]["ms"]) if prof else None
+    peaks, src = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    roof = None
+    if dom is not None:
+        d = prof[dom]
+        per_launch_ms = d["ms"] / max(1, d["launches"])
+        if dom in FLOPS_PER_PAIR:
+            clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+            peak = sms * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
+            achieved = FLOPS_PER_PAIR[dom] * d["units"] / (d["ms"] / 1e3) / 1e12
+            roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                    "frac": achieved / peak,
+                    "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clock_mhz:.0f} MHz"}
+        else:
+            peak = float(peaks.get("hbm_gbs", 6800.0))
+            achieved = d["units"] / (d["ms"] / 1e3) / 1e9
+            roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "peak_basis": f"hbm_gbs ({src})"}
+        tr = profile_traffic(dom, WORKLOAD)
+        roof["traffic"] = tr
+        roof["launch_ms"] = per_launch_ms
+        roof["launches"] = d["launches"]
+
+    lat = sorted(step_ms)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms_all / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded torus, no dataset)",
+        "config": {"workload": WORKLOAD, "nv": int(len(V)), "nf": int(len(F)),
+                   "step": "set positions + precond_step(area+volume; direct FP32 pairs, FP64 solver) + BH theta=0.5 E+dE",
+                   "solver_dtype": "f64", "krylov_tol": ps.krylov_tol, "cg_tol": ps.cg_tol,
+                   "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{world}"},
+        "steps_per_s": 1e3 * args.steps / dev_ms_all,
+        "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+        "pairs_per_step": pairs_per_step,
+        "krylov_iters_per_step": sum(r["krylov_iters"] for r in reps) / len(reps),
+        "cg_iters_per_step": sum(r["cg_iters"] for r in reps) / len(reps),
+        "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "units": v["units"]} for k, v in prof.items()},
+        "wall_s": wall, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = run_cpu_sample()
+    mesh.close()
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle as it stands on the host cores
+# ---------------------------------------------------------------------------
+
+def reference_arm(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        r = run_cpu_sample(scale=4)
+        vals.append(r["value"])
+        secs += r["seconds"]
+    value = sum(vals) / len(vals)
+    cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample_desc(4)}
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded torus, no dataset)",
+        "config": {"workload": WORKLOAD, "step": "bounded oracle sample (see cpu_baseline.sample)"},
+        "cpu_baseline": cpu, "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -557,3 +557,249 @@ def apply_operator_at_vertices(f, faces, v, op, verts, p=6.0):
             if zU is not None:
                 out[vi] += 2.0 * a[S] * zU[r] / 3.0
     return out
+
+
+# ---------------------------------------------------------------------------
+# §4 Barnes-Hut: BVH over the faces, approximate energy and differential
+# ---------------------------------------------------------------------------
+#
+# Tree (the paper leaves the BVH construction open; this is the definition the
+# library also uses): faces sorted by the 30-bit Morton code of their
+# barycenter, measured in the frame of the vertex bounding-box centre and
+# quantised to 1024 cells per axis over the barycenters' bounding box, ties
+# by face index; leaves are runs of `leaf` consecutive sorted faces; a node
+# over n leaves has a left child over ceil(n/2) leaves; nodes are numbered in
+# pre-order. Node data: a_I = sum a_T, X_I = sum a_T X_T / a_I, the bounding
+# box of the node's triangle vertices, and r_I = max |v - X_I| over the
+# vertices for leaves, max_child (|X_child - X_I| + r_child) for inner nodes.
+# Admissibility (§4.1, read with theta): max(r_S, r_I)^2 < theta^2 dist^2 of
+# the two boxes, decided in FP32 like the kernel; an inadmissible leaf is
+# summed exactly (T != S).
+
+def _spread10(v):
+    v = v.astype(np.uint64) & 0x3FF
+    v = (v | (v << 16)) & 0x030000FF
+    v = (v | (v << 8)) & 0x0300F00F
+    v = (v | (v << 4)) & 0x030C30C3
+    v = (v | (v << 2)) & 0x09249249
+    return v
+
+
+def bvh_build(f, faces, leaf=8):
+    """Sorted face order, pre-order node table and node data (dict)."""
+    X, N, a = face_geometry(f, faces)
+    c = 0.5 * (f.min(axis=0) + f.max(axis=0))
+    Xr = (f[faces[:, 0]] + f[faces[:, 1]] + f[faces[:, 2]]) / 3.0 - c
+    lo, hi = Xr.min(axis=0), Xr.max(axis=0)
+    ext = hi - lo
+    q = np.zeros_like(Xr, dtype=np.int64)
+    for k in range(3):
+        if ext[k] > 0:
+            q[:, k] = np.clip(np.floor((Xr[:, k] - lo[k]) * (1024.0 / ext[k])), 0, 1023).astype(np.int64)
+    code = (_spread10(q[:, 0]) << 2) | (_spread10(q[:, 1]) << 1) | _spread10(q[:, 2])
+    nf = len(faces)
+    order = np.lexsort((np.arange(nf), code))
+    nleaf = (nf + leaf - 1) // leaf
+    first, count, skip, isleaf, right = [], [], [], [], []
+
+    def rec(lo_, hi_):
+        nid = len(first)
+        n = hi_ - lo_
+        first.append(lo_ * leaf)
+        count.append(min(hi_ * leaf, nf) - lo_ * leaf)
+        skip.append(nid + 2 * n - 1)
+        isleaf.append(n == 1)
+        right.append(-1)
+        if n > 1:
+            nl = (n + 1) // 2
+            rec(lo_, lo_ + nl)
+            right[nid] = len(first)
+            rec(lo_ + nl, hi_)
+        return nid
+
+    import sys
+    sys.setrecursionlimit(max(10000, sys.getrecursionlimit()))
+    rec(0, nleaf)
+    first, count = np.array(first), np.array(count)
+    nn = len(first)
+    # node data, bottom-up: leaves from their faces, inner nodes from children
+    isleaf = np.array(isleaf)
+    right = np.array(right)
+    vx = f[faces] - c                                   # [nf,3,3] vertices in the frame
+    aI = np.zeros(nn)
+    XI = np.zeros((nn, 3))
+    box_lo = np.zeros((nn, 3))
+    box_hi = np.zeros((nn, 3))
+    rI = np.zeros(nn)
+    lv = np.nonzero(isleaf)[0]
+    for j in range(leaf):                               # leaves: sums over <= leaf faces
+        ok = j < count[lv]
+        T = order[np.minimum(first[lv] + j, nf - 1)]
+        w = np.where(ok, a[T], 0.0)
+        aI[lv] += w
+        XI[lv] += w[:, None] * Xr[T]
+    XI[lv] /= aI[lv][:, None]
+    box_lo[lv], box_hi[lv] = np.inf, -np.inf
+    for j in range(leaf):
+        ok = j < count[lv]
+        T = order[np.minimum(first[lv] + j, nf - 1)]
+        v = vx[T]                                       # [nleaf,3,3]
+        box_lo[lv] = np.where(ok[:, None], np.minimum(box_lo[lv], v.min(axis=1)), box_lo[lv])
+        box_hi[lv] = np.where(ok[:, None], np.maximum(box_hi[lv], v.max(axis=1)), box_hi[lv])
+        dist = np.sqrt(((v - XI[lv][:, None, :]) ** 2).sum(axis=2)).max(axis=1)
+        rI[lv] = np.where(ok, np.maximum(rI[lv], dist), rI[lv])
+    depth = np.zeros(nn, dtype=np.int64)
+    inner = np.nonzero(~isleaf)[0]
+    for nid in inner:                                   # pre-order: parents first
+        depth[nid + 1] = depth[right[nid]] = depth[nid] + 1
+    for d in range(depth.max(), -1, -1):
+        ids = inner[depth[inner] == d]
+        L, R = ids + 1, right[ids]
+        aI[ids] = aI[L] + aI[R]
+        XI[ids] = (aI[L][:, None] * XI[L] + aI[R][:, None] * XI[R]) / aI[ids][:, None]
+        box_lo[ids] = np.minimum(box_lo[L], box_lo[R])
+        box_hi[ids] = np.maximum(box_hi[L], box_hi[R])
+        rI[ids] = np.maximum(np.linalg.norm(XI[L] - XI[ids], axis=1) + rI[L],
+                             np.linalg.norm(XI[R] - XI[ids], axis=1) + rI[R])
+    # target faces: their own boxes and radii
+    fbox_lo, fbox_hi = vx.min(axis=1), vx.max(axis=1)
+    fr2 = ((vx - Xr[:, None, :]) ** 2).sum(axis=2).max(axis=1)
+    return dict(order=order, first=first, count=count, skip=np.array(skip), leaf=isleaf,
+                right=right, a=aI, X=XI, lo=box_lo, hi=box_hi, r=rI, Xr=Xr, c=c,
+                fbox_lo=fbox_lo, fbox_hi=fbox_hi, fr2=fr2)
+
+
+def _admissible(T, S, nodes, theta):
+    """FP32 admissibility of node(s) `nodes` for target face(s) S."""
+    f32 = np.float32
+    alo, ahi = T["fbox_lo"][S].astype(f32), T["fbox_hi"][S].astype(f32)
+    nlo, nhi = T["lo"][nodes].astype(f32), T["hi"][nodes].astype(f32)
+    g = np.maximum(np.maximum(nlo - ahi, alo - nhi), f32(0))
+    d2 = (g[:, 0] * g[:, 0] + g[:, 1] * g[:, 1]) + g[:, 2] * g[:, 2]
+    mr2 = np.maximum(T["fr2"][S].astype(f32), (T["r"][nodes] * T["r"][nodes]).astype(f32))
+    return mr2 < f32(theta * theta) * d2
+
+
+def bh_interactions(f, faces, theta, leaf=8, targets=None, tree=None):
+    """Interaction lists of Eq. 16: far (target face, node) pairs and near
+    (target face, source face) pairs, by a breadth-first traversal of all
+    targets at once."""
+    T = tree if tree is not None else bvh_build(f, faces, leaf)
+    nf = len(faces)
+    S = np.arange(nf) if targets is None else np.asarray(targets)
+    cur_s, cur_n = S.copy(), np.zeros(len(S), dtype=np.int64)
+    far_s, far_n, near_s, near_t = [], [], [], []
+    while len(cur_s):
+        adm = _admissible(T, cur_s, cur_n, theta)
+        far_s.append(cur_s[adm])
+        far_n.append(cur_n[adm])
+        rest_s, rest_n = cur_s[~adm], cur_n[~adm]
+        lf = T["leaf"][rest_n]
+        # inadmissible leaves: exact pairs with their faces
+        ls, ln = rest_s[lf], rest_n[lf]
+        for j in range(leaf):
+            ok = j < T["count"][ln]
+            src = T["order"][np.minimum(T["first"][ln] + j, nf - 1)]
+            keep = ok & (src != ls)
+            near_s.append(ls[keep])
+            near_t.append(src[keep])
+        # inner nodes: descend to both children
+        is_, in_ = rest_s[~lf], rest_n[~lf]
+        cur_s = np.concatenate([is_, is_])
+        cur_n = np.concatenate([in_ + 1, T["right"][in_]])
+    cat = lambda xs: np.concatenate(xs) if xs else np.zeros(0, dtype=np.int64)
+    return T, dict(far_s=cat(far_s), far_n=cat(far_n), near_s=cat(near_s), near_t=cat(near_t))
+
+
+def bh_energy_rows(f, faces, theta, leaf=8, p=6.0, targets=None):
+    """Rows of Eq. 16 for the given targets (all faces by default)."""
+    X, N, a = face_geometry(f, faces)
+    T, L = bh_interactions(f, faces, theta, leaf, targets)
+    Xr = T["Xr"]
+    nf = len(faces)
+    rows = np.zeros(nf)
+    Kf = tp_kernel(Xr[L["far_s"]], N[L["far_s"]], T["X"][L["far_n"]], p)
+    np.add.at(rows, L["far_s"], Kf * a[L["far_s"]] * T["a"][L["far_n"]])
+    Kn = tp_kernel(Xr[L["near_s"]], N[L["near_s"]], Xr[L["near_t"]], p)
+    np.add.at(rows, L["near_s"], Kn * a[L["near_s"]] * a[L["near_t"]])
+    S = np.arange(nf) if targets is None else np.asarray(targets)
+    return rows[S], len(L["far_s"]) + len(L["near_s"])
+
+
+def bh_energy(f, faces, theta, leaf=8, p=6.0):
+    rows, _ = bh_energy_rows(f, faces, theta, leaf, p)
+    return float(rows.sum())
+
+
+def bh_energy_frozen(f, faces, tree, lists, p=6.0):
+    """Barnes-Hut energy of Eq. 16 at positions f with the tree membership and
+    the interaction lists of another configuration held fixed (node areas and
+    barycenters recomputed from f). Its gradient is the 'full' Barnes-Hut
+    differential."""
+    X, N, a = face_geometry(f, faces)
+    c = tree["c"]
+    Xr = X - c
+    nn = len(tree["first"])
+    aI = np.zeros(nn)
+    XI = np.zeros((nn, 3))
+    for nid in range(nn):
+        Tf = tree["order"][tree["first"][nid]:tree["first"][nid] + tree["count"][nid]]
+        aI[nid] = a[Tf].sum()
+        XI[nid] = (a[Tf, None] * Xr[Tf]).sum(axis=0) / aI[nid]
+    fs, fn, ns, nt = lists["far_s"], lists["far_n"], lists["near_s"], lists["near_t"]
+    E = np.sum(tp_kernel(Xr[fs], N[fs], XI[fn], p) * a[fs] * aI[fn])
+    E += np.sum(tp_kernel(Xr[ns], N[ns], Xr[nt], p) * a[ns] * a[nt])
+    return float(E)
+
+
+def bh_differential(f, faces, theta, leaf=8, p=6.0, mode="full"):
+    """Barnes-Hut differential (§4.2), shape [nv,3].
+
+    mode 'literal': only the terms where the face is the target S of an
+    interaction (the formula printed in §4.2);
+    mode 'full': the exact derivative of Eq. 16 with the interaction lists
+    fixed -- the target-side terms plus the source-side terms, where a node's
+    barycenter X_I = sum a_T X_T / a_I and area a_I = sum a_T pass the
+    derivative on to the node's faces."""
+    X, N, a = face_geometry(f, faces)
+    T, L = bh_interactions(f, faces, theta, leaf)
+    Xr = T["Xr"]
+    nf = len(faces)
+    gX = np.zeros((nf, 3))
+    gN = np.zeros((nf, 3))
+    ga = np.zeros(nf)
+
+    def side(s, Y, wY):
+        d = Xr[s] - Y
+        r2 = np.sum(d * d, axis=1)
+        u = np.sum(N[s] * d, axis=1)
+        K = np.abs(u) ** p / r2 ** p
+        cc = p * np.abs(u) ** (p - 2.0) * u / r2 ** p
+        dKdd = cc[:, None] * N[s] - (2.0 * p * K / r2)[:, None] * d
+        dKdN = cc[:, None] * d
+        np.add.at(gX, s, (a[s] * wY)[:, None] * dKdd)
+        np.add.at(gN, s, (a[s] * wY)[:, None] * dKdN)
+        np.add.at(ga, s, K * wY)
+        return -(a[s] * wY)[:, None] * dKdd, a[s] * K     # source side: d/dY, d/dwY
+
+    GYf, QYf = side(L["far_s"], T["X"][L["far_n"]], T["a"][L["far_n"]])
+    GYn, QYn = side(L["near_s"], Xr[L["near_t"]], a[L["near_t"]])
+    if mode == "full":
+        np.add.at(gX, L["near_t"], GYn)
+        np.add.at(ga, L["near_t"], QYn)
+        nn = len(T["first"])
+        G = np.zeros((nn, 3))
+        Q = np.zeros(nn)
+        np.add.at(G, L["far_n"], GYf)
+        np.add.at(Q, L["far_n"], QYf)
+        for nid in np.nonzero(np.any(G != 0, axis=1) | (Q != 0))[0]:
+            Tf = T["order"][T["first"][nid]:T["first"][nid] + T["count"][nid]]
+            gX[Tf] += (a[Tf] / T["a"][nid])[:, None] * G[nid]
+            ga[Tf] += Q[nid] + (Xr[Tf] - T["X"][nid]) @ G[nid] / T["a"][nid]
+    elif mode != "literal":
+        raise ValueError(mode)
+    corner = faces_to_vertices(f, faces, gX, gN, ga)
+    out = np.zeros_like(f)
+    for cidx in range(3):
+        np.add.at(out, faces[:, cidx], corner[:, cidx])
+    return out

@@ -219,7 +219,7 @@ __global__ void k_nodes_level(const NodeShape* __restrict__ shape, const int* __
                               const int* __restrict__ perm, const double* __restrict__ pos,
                               const int* __restrict__ faces, const double* __restrict__ center,
                               const d4* __restrict__ f64a, const FaceBox* __restrict__ fbox,
-                              BvhNode* __restrict__ node, d4* __restrict__ node64) {
+                              BvhNode* __restrict__ node, d4* __restrict__ node64, double* __restrict__ noder) {
     int k = n0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n1) return;
     int id = order[k];
@@ -257,12 +257,13 @@ __global__ void k_nodes_level(const NodeShape* __restrict__ shape, const int* __
         BvhNode nl = node[L], nr = node[R];
         lo[0] = fmin(nl.lox, nr.lox); lo[1] = fmin(nl.loy, nr.loy); lo[2] = fmin(nl.loz, nr.loz);
         hi[0] = fmax(nl.hix, nr.hix); hi[1] = fmax(nl.hiy, nr.hiy); hi[2] = fmax(nl.hiz, nr.hiz);
-        double rl = sqrt((double)nl.r2), rr = sqrt((double)nr.r2);
+        double rl = noder[L], rr = noder[R];
         double dl = sqrt((xl.x - X[0]) * (xl.x - X[0]) + (xl.y - X[1]) * (xl.y - X[1]) + (xl.z - X[2]) * (xl.z - X[2]));
         double dr = sqrt((xr.x - X[0]) * (xr.x - X[0]) + (xr.y - X[1]) * (xr.y - X[1]) + (xr.z - X[2]) * (xr.z - X[2]));
         r = fmax(dl + rl, dr + rr);
     }
     node64[id] = d4{X[0], X[1], X[2], a};
+    noder[id] = r;
     BvhNode o;
     o.cx = (float)X[0]; o.cy = (float)X[1]; o.cz = (float)X[2]; o.a = (float)a;
     o.lox = (float)lo[0]; o.loy = (float)lo[1]; o.loz = (float)lo[2]; o.r2 = (float)(r * r);
@@ -299,7 +300,7 @@ int bvh_build(tp_mesh* m, const tp_params* p, cudaStream_t st) {
     TP_TRY(ensure(m->bvh_perm, sizeof(int) * (size_t)nf + sizeof(FaceBox) * (size_t)nf));
     TP_TRY(ensure(m->bvh_f32a, sizeof(float4) * (size_t)nf));
     TP_TRY(ensure(m->bvh_f32b, sizeof(float4) * (size_t)nf));
-    TP_TRY(ensure(m->bvh_node, sizeof(BvhNode) * (size_t)h.nnodes + sizeof(d4) * (size_t)h.nnodes));
+    TP_TRY(ensure(m->bvh_node, (sizeof(BvhNode) + sizeof(d4) + sizeof(double)) * (size_t)h.nnodes));
     unsigned long long* kin = m->bvh_keys.as<unsigned long long>();
     unsigned long long* kout = kin + nf;
     double* bpart = (double*)(kout + nf);
@@ -307,6 +308,7 @@ int bvh_build(tp_mesh* m, const tp_params* p, cudaStream_t st) {
     FaceBox* fbox = (FaceBox*)(perm + nf);
     BvhNode* node = m->bvh_node.as<BvhNode>();
     d4* node64 = (d4*)(node + h.nnodes);
+    double* noder = (double*)(node64 + h.nnodes);
     const NodeShape* shape = m->bvh_tmp.as<NodeShape>();
     const int* right = (const int*)(shape + h.nnodes);
     const int* order = right + h.nnodes;
@@ -330,7 +332,7 @@ int bvh_build(tp_mesh* m, const tp_params* p, cudaStream_t st) {
         k_nodes_level<<<(n1 - n0 + 127) / 128, 128, 0, st>>>(shape, right, order, n0, n1, perm,
                                                              m->pos.as<double>(), m->faces.as<int>(),
                                                              m->center.as<double>(), m->f64a.as<d4>(), fbox,
-                                                             node, node64);
+                                                             node, node64, noder);
         TP_LAUNCH_CHECK();
     }
     m->bvh_valid = true;

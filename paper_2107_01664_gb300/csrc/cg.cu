@@ -8,11 +8,11 @@
 // once (independent scalars per column), right-hand side and solution kept
 // in the mean-zero subspace (the constants span the nullspace of C).
 //
-// One CG iteration is two kernels. The direction update is folded into the
-// SpMV through q_new = C z + beta q_old, so that each kernel needs only data
-// completed by the previous one. Global scalars are reduced by the last
-// block to finish (fence + counter), which sums the per-block partials in a
-// fixed order: the iteration is deterministic.
+// The whole solve is one cooperative launch (see k_cg_persistent). The
+// direction update is folded into the SpMV through q_new = C z + beta q_old,
+// so that one grid barrier separates the two halves of an iteration; the
+// global scalars are sums of per-block partials taken in a fixed order, so
+// the iteration is deterministic.
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -130,197 +130,226 @@ int laplacian_values(tp_mesh* m, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// CG state in device memory
+// persistent CG: the whole solve in one cooperative launch
 // ---------------------------------------------------------------------------
+//
+// Blocks own strided rows; two grid barriers per iteration separate
+//   phase A: p = z + beta p, q = C z + beta q, partial p.q      (needs all z)
+//   phase B: x += alpha p, r -= alpha q, z = D^-1 r, partial r.z, r.r
+// Every block reduces the per-block partials itself, in the same order, so
+// all blocks hold bit-identical alpha, beta and convergence decisions and
+// leave the loop together. Phase A and phase B partials live in separate
+// buffers, so a block that runs ahead never overwrites partials another
+// block is still reading. The barrier spins on a generation counter with a
+// clock budget; when the budget runs out the kernel records TP_ERR_TIMEOUT
+// and every block returns.
 
-struct CgScalars {
-    double rz[KMAX], alpha[KMAX], beta[KMAX], rr[KMAX], bb[KMAX];
-    int active[KMAX];
-    int done;       // all columns converged (or failed)
-    int iters;      // iterations executed
-    int counter;    // last-block-done counter
-    int pad;
+struct CgCtl {
+    unsigned count;        // barrier arrivals
+    unsigned gen;          // barrier generation
+    int err;               // 0 ok, 1 barrier timeout
+    int iters;             // iterations done
+    int active[KMAX];      // per column: 1 = not yet converged
+    double rr[KMAX], bb[KMAX];
 };
 
-// block-wide FP64 sum of per-thread values for k columns; result in sh[c*CG_T]
-__device__ __forceinline__ void block_sums(double (*vals)[CG_T], int k) {
-    for (int w = CG_T / 2; w > 0; w >>= 1) {
+__device__ __forceinline__ bool grid_barrier(CgCtl* ctl, unsigned nblk) {
+    __syncthreads();
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = &ctl->gen;
+        unsigned g = *vgen;
+        __threadfence();
+        if (atomicAdd(&ctl->count, 1u) == nblk - 1) {
+            ctl->count = 0;
+            __threadfence();
+            atomicAdd(&ctl->gen, 1u);
+            ok = 1;
+        } else {
+            long long t0 = clock64();
+            ok = 1;
+            while (*vgen == g) {
+                if (*(volatile int*)&ctl->err) { ok = 0; break; }
+                if (clock64() - t0 > (1LL << 32)) {   // ~2 s at 2 GHz
+                    atomicExch(&ctl->err, 1);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// block-wide sums of up to 2*KMAX per-thread values (vals[j][t]) -> vals[j][0]
+template <int NTH>
+__device__ __forceinline__ void block_reduce(double (*vals)[NTH], int nval) {
+    for (int w = NTH / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w)
-            for (int c = 0; c < k; ++c) vals[c][threadIdx.x] += vals[c][threadIdx.x + w];
+            for (int j = 0; j < nval; ++j) vals[j][threadIdx.x] += vals[j][threadIdx.x + w];
         __syncthreads();
     }
 }
 
-// is this the last block to finish? (partials written before the call)
-__device__ __forceinline__ bool last_block(int* counter) {
-    __shared__ bool last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = (atomicAdd(counter, 1) == (int)gridDim.x - 1);
-    __syncthreads();
-    return last;
-}
+constexpr int PCG_T = 128;
 
-// init: r = b, z = D^-1 r, p = z, q = C p ; partial rz, bb, pq
-__global__ void k_cg_init(const int* __restrict__ rowptr, const int* __restrict__ col,
-                          const double* __restrict__ val, const double* __restrict__ dinv, int nv, int k,
-                          const double* b, double* __restrict__ x, double* r,
-                          double* __restrict__ z, double* __restrict__ p, double* __restrict__ part,
-                          CgScalars* sc) {
-    __shared__ double sh[2][KMAX][CG_T];
-    int v = blockIdx.x * CG_T + threadIdx.x;
-    for (int c = 0; c < k; ++c) {
-        double rz = 0.0, bb = 0.0;
-        if (v < nv) {
-            double bv = b[(size_t)v * k + c];
-            double zv = dinv[v] * bv;
-            x[(size_t)v * k + c] = 0.0;
-            r[(size_t)v * k + c] = bv;
-            z[(size_t)v * k + c] = zv;
-            p[(size_t)v * k + c] = 0.0;   // p = z + beta p with beta = 0 in the first SpMV pass
-            rz = bv * zv;
-            bb = bv * bv;
-        }
-        sh[0][c][threadIdx.x] = rz;
-        sh[1][c][threadIdx.x] = bb;
-    }
-    __syncthreads();
-    block_sums(sh[0], k);
-    block_sums(sh[1], k);
-    if (threadIdx.x == 0)
+__global__ void __launch_bounds__(PCG_T)
+k_cg_persistent(const int* __restrict__ rowptr, const int* __restrict__ col, const double* __restrict__ val,
+                const double* __restrict__ dinv, int nv, int k, const double* __restrict__ b,
+                double* __restrict__ x, double* __restrict__ r, double* __restrict__ z, double* __restrict__ p,
+                double* __restrict__ q, double* __restrict__ partA /* [grid][KMAX] */,
+                double* __restrict__ partB /* [grid][2*KMAX] */, CgCtl* ctl, double tol2, int max_iter) {
+    __shared__ double sh[2 * KMAX][PCG_T];
+    __shared__ double s_alpha[KMAX], s_beta[KMAX], s_rz[KMAX], s_bb[KMAX];
+    __shared__ int s_active[KMAX], s_done;
+    const unsigned nblk = gridDim.x;
+    const int stride = gridDim.x * PCG_T;
+    // ---- init: x = 0, r = b, z = D^-1 r, p = q = 0 ; partial r.z, b.b
+    for (int j = 0; j < 2 * k; ++j) sh[j][threadIdx.x] = 0.0;
+    for (int v = blockIdx.x * PCG_T + threadIdx.x; v < nv; v += stride)
         for (int c = 0; c < k; ++c) {
-            part[(size_t)blockIdx.x * 2 * KMAX + c] = sh[0][c][0];
-            part[(size_t)blockIdx.x * 2 * KMAX + KMAX + c] = sh[1][c][0];
-        }
-    if (last_block(&sc->counter) && threadIdx.x == 0) {
-        for (int c = 0; c < k; ++c) {
-            double rz = 0.0, bb = 0.0;
-            for (int bI = 0; bI < (int)gridDim.x; ++bI) {
-                rz += __ldcg(part + (size_t)bI * 2 * KMAX + c);
-                bb += __ldcg(part + (size_t)bI * 2 * KMAX + KMAX + c);
-            }
-            sc->rz[c] = rz;
-            sc->bb[c] = bb;
-            sc->rr[c] = bb;
-            sc->beta[c] = 0.0;
-            sc->alpha[c] = 0.0;
-            sc->active[c] = bb > 0.0 ? 1 : 0;
-        }
-        sc->iters = 0;
-        int any = 0;
-        for (int c = 0; c < k; ++c) any |= sc->active[c];
-        sc->done = any ? 0 : 1;
-        sc->counter = 0;
-    }
-}
-
-// p = z + beta p ; q = C z + beta q ; partial p.q ; last block: alpha = rz / pq
-__global__ void k_cg_dir(const int* __restrict__ rowptr, const int* __restrict__ col,
-                         const double* __restrict__ val, int nv, int k, const double* __restrict__ z,
-                         double* __restrict__ p, double* __restrict__ q, double* __restrict__ part,
-                         CgScalars* sc) {
-    if (sc->done) return;
-    __shared__ double sh[KMAX][CG_T];
-    int v = blockIdx.x * CG_T + threadIdx.x;
-    double cz[KMAX];
-    for (int c = 0; c < k; ++c) cz[c] = 0.0;
-    if (v < nv)
-        for (int e = rowptr[v]; e < rowptr[v + 1]; ++e) {
-            double w = val[e];
-            const double* zr = z + (size_t)col[e] * k;
-            for (int c = 0; c < k; ++c) cz[c] += w * zr[c];
-        }
-    for (int c = 0; c < k; ++c) {
-        double pq = 0.0;
-        if (v < nv) {
-            double be = sc->beta[c];
             size_t o = (size_t)v * k + c;
-            double pv = z[o] + be * p[o];
-            double qv = cz[c] + be * q[o];
-            if (sc->beta[c] == 0.0) qv = cz[c];  // first pass: q is uninitialised
-            p[o] = pv;
-            q[o] = qv;
-            pq = pv * qv;
-        }
-        sh[c][threadIdx.x] = pq;
-    }
-    __syncthreads();
-    block_sums(sh, k);
-    if (threadIdx.x == 0)
-        for (int c = 0; c < k; ++c) part[(size_t)blockIdx.x * 2 * KMAX + c] = sh[c][0];
-    if (last_block(&sc->counter) && threadIdx.x == 0) {
-        for (int c = 0; c < k; ++c) {
-            double pq = 0.0;
-            for (int bI = 0; bI < (int)gridDim.x; ++bI) pq += __ldcg(part + (size_t)bI * 2 * KMAX + c);
-            sc->alpha[c] = (sc->active[c] && pq > 0.0) ? sc->rz[c] / pq : 0.0;
-        }
-        sc->counter = 0;
-    }
-}
-
-// x += alpha p ; r -= alpha q ; z = D^-1 r ; partial r.z, r.r ;
-// last block: beta = rz_new / rz, convergence per column
-__global__ void k_cg_update(const double* __restrict__ dinv, int nv, int k, double* __restrict__ x,
-                            double* __restrict__ r, double* __restrict__ z, const double* __restrict__ p,
-                            const double* __restrict__ q, double* __restrict__ part, CgScalars* sc,
-                            double tol2, int max_iter) {
-    if (sc->done) return;
-    __shared__ double sh[2][KMAX][CG_T];
-    int v = blockIdx.x * CG_T + threadIdx.x;
-    for (int c = 0; c < k; ++c) {
-        double rz = 0.0, rr = 0.0;
-        if (v < nv) {
-            size_t o = (size_t)v * k + c;
-            double al = sc->alpha[c];
-            x[o] += al * p[o];
-            double rv = r[o] - al * q[o];
-            r[o] = rv;
-            double zv = dinv[v] * rv;
+            double bv = b[o], zv = dinv[v] * bv;
+            x[o] = 0.0;
+            r[o] = bv;
             z[o] = zv;
-            rz = rv * zv;
-            rr = rv * rv;
+            p[o] = 0.0;
+            q[o] = 0.0;
+            sh[c][threadIdx.x] += bv * zv;
+            sh[k + c][threadIdx.x] += bv * bv;
         }
-        sh[0][c][threadIdx.x] = rz;
-        sh[1][c][threadIdx.x] = rr;
+    __syncthreads();
+    block_reduce<PCG_T>(sh, 2 * k);
+    if (threadIdx.x == 0)
+        for (int j = 0; j < 2 * k; ++j) partB[(size_t)blockIdx.x * 2 * KMAX + j] = sh[j][0];
+    if (!grid_barrier(ctl, nblk)) return;
+    if (threadIdx.x < k) {
+        int c = threadIdx.x;
+        double rz = 0.0, bb = 0.0;
+        for (unsigned bI = 0; bI < nblk; ++bI) {
+            rz += __ldcg(partB + (size_t)bI * 2 * KMAX + c);
+            bb += __ldcg(partB + (size_t)bI * 2 * KMAX + k + c);
+        }
+        s_rz[c] = rz;
+        s_bb[c] = bb;
+        s_beta[c] = 0.0;
+        s_active[c] = bb > 0.0 ? 1 : 0;
+        if (blockIdx.x == 0) {
+            ctl->bb[c] = bb;
+            ctl->rr[c] = bb;
+        }
     }
     __syncthreads();
-    block_sums(sh[0], k);
-    block_sums(sh[1], k);
-    if (threadIdx.x == 0)
-        for (int c = 0; c < k; ++c) {
-            part[(size_t)blockIdx.x * 2 * KMAX + c] = sh[0][c][0];
-            part[(size_t)blockIdx.x * 2 * KMAX + KMAX + c] = sh[1][c][0];
-        }
-    if (last_block(&sc->counter) && threadIdx.x == 0) {
+    if (threadIdx.x == 0) {
         int any = 0;
-        for (int c = 0; c < k; ++c) {
-            double rz = 0.0, rr = 0.0;
-            for (int bI = 0; bI < (int)gridDim.x; ++bI) {
-                rz += __ldcg(part + (size_t)bI * 2 * KMAX + c);
-                rr += __ldcg(part + (size_t)bI * 2 * KMAX + KMAX + c);
+        for (int c = 0; c < k; ++c) any |= s_active[c];
+        s_done = any ? 0 : 1;
+    }
+    __syncthreads();
+    int it = 0;
+    while (!s_done) {
+        // ---- phase A
+        for (int j = 0; j < k; ++j) sh[j][threadIdx.x] = 0.0;
+        for (int v = blockIdx.x * PCG_T + threadIdx.x; v < nv; v += stride) {
+            double cz[KMAX];
+#pragma unroll
+            for (int c = 0; c < KMAX; ++c) cz[c] = 0.0;
+            for (int e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+                double w = val[e];
+                const double* zr = z + (size_t)col[e] * k;
+#pragma unroll
+                for (int c = 0; c < KMAX; ++c)
+                    if (c < k) cz[c] += w * __ldcg(zr + c);
             }
-            if (sc->active[c]) {
-                // a converged column keeps its iterate: zero step from now on
-                sc->beta[c] = sc->rz[c] > 0.0 ? rz / sc->rz[c] : 0.0;
-                sc->rz[c] = rz;
-                sc->rr[c] = rr;
-                if (rr <= tol2 * sc->bb[c]) {
-                    sc->active[c] = 0;
-                    sc->beta[c] = 0.0;
+#pragma unroll
+            for (int c = 0; c < KMAX; ++c)
+                if (c < k) {
+                    size_t o = (size_t)v * k + c;
+                    double be = s_beta[c];
+                    double pv = __ldcg(z + o) + be * p[o];
+                    double qv = cz[c] + be * q[o];
+                    p[o] = pv;
+                    q[o] = qv;
+                    sh[c][threadIdx.x] += pv * qv;
+                }
+        }
+        __syncthreads();
+        block_reduce<PCG_T>(sh, k);
+        if (threadIdx.x == 0)
+            for (int c = 0; c < k; ++c) partA[(size_t)blockIdx.x * KMAX + c] = sh[c][0];
+        if (!grid_barrier(ctl, nblk)) return;
+        if (threadIdx.x < k) {
+            int c = threadIdx.x;
+            double pq = 0.0;
+            for (unsigned bI = 0; bI < nblk; ++bI) pq += __ldcg(partA + (size_t)bI * KMAX + c);
+            s_alpha[c] = (s_active[c] && pq > 0.0) ? s_rz[c] / pq : 0.0;
+        }
+        __syncthreads();
+        // ---- phase B
+        for (int j = 0; j < 2 * k; ++j) sh[j][threadIdx.x] = 0.0;
+        for (int v = blockIdx.x * PCG_T + threadIdx.x; v < nv; v += stride)
+            for (int c = 0; c < k; ++c) {
+                size_t o = (size_t)v * k + c;
+                double al = s_alpha[c];
+                x[o] += al * p[o];
+                double rv = r[o] - al * q[o];
+                r[o] = rv;
+                double zv = dinv[v] * rv;
+                z[o] = zv;
+                sh[c][threadIdx.x] += rv * zv;
+                sh[k + c][threadIdx.x] += rv * rv;
+            }
+        __syncthreads();
+        block_reduce<PCG_T>(sh, 2 * k);
+        if (threadIdx.x == 0)
+            for (int j = 0; j < 2 * k; ++j) partB[(size_t)blockIdx.x * 2 * KMAX + j] = sh[j][0];
+        if (!grid_barrier(ctl, nblk)) return;
+        ++it;
+        if (threadIdx.x < k) {
+            int c = threadIdx.x;
+            double rz = 0.0, rr = 0.0;
+            for (unsigned bI = 0; bI < nblk; ++bI) {
+                rz += __ldcg(partB + (size_t)bI * 2 * KMAX + c);
+                rr += __ldcg(partB + (size_t)bI * 2 * KMAX + k + c);
+            }
+            if (s_active[c]) {
+                s_beta[c] = s_rz[c] > 0.0 ? rz / s_rz[c] : 0.0;
+                s_rz[c] = rz;
+                if (blockIdx.x == 0) ctl->rr[c] = rr;
+                if (rr <= tol2 * s_bb[c]) {
+                    s_active[c] = 0;
+                    s_beta[c] = 0.0;
                 }
             }
-            any |= sc->active[c];
         }
-        sc->iters += 1;
-        if (!any || sc->iters >= max_iter) sc->done = 1;
-        sc->counter = 0;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int any = 0;
+            for (int c = 0; c < k; ++c) any |= s_active[c];
+            s_done = (!any || it >= max_iter) ? 1 : 0;
+        }
+        __syncthreads();
     }
+    if (blockIdx.x == 0 && threadIdx.x < k) ctl->active[threadIdx.x] = s_active[threadIdx.x];
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->iters = it;
 }
 
-static int i_copy(void* host, const void* dev, cudaStream_t st) {
-    TP_CUDA(cudaMemcpyAsync(host, dev, sizeof(CgScalars), cudaMemcpyDeviceToHost, st));
-    TP_CUDA(cudaStreamSynchronize(st));
-    return TP_OK;
+static int cg_grid(int nv) {
+    static int cached_dev = -1, cached_max = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev != cached_dev) {
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_persistent, PCG_T, 0);
+        cached_max = per_sm * sm_count();
+        cached_dev = dev;
+    }
+    int want = (nv + PCG_T - 1) / PCG_T;
+    int g = want < cached_max ? want : cached_max;
+    return g < 1 ? 1 : g;
 }
 
 int cg_solve(tp_mesh* m, const tp_params* p, const double* b, int k, double* z_out, cudaStream_t st,
@@ -329,53 +358,44 @@ int cg_solve(tp_mesh* m, const tp_params* p, const double* b, int k, double* z_o
     TP_TRY(laplacian_values(m, st));
     const int nv = m->nv;
     const size_t n = (size_t)nv * k;
-    for (int i = 0; i < 5; ++i) TP_TRY(ensure(m->tmpv[i], sizeof(double) * n));
+    for (int i = 0; i < 6; ++i) TP_TRY(ensure(m->tmpv[i], sizeof(double) * n));
     double *x = m->tmpv[0].as<double>(), *r = m->tmpv[1].as<double>(), *z = m->tmpv[2].as<double>(),
-           *pp = m->tmpv[3].as<double>(), *q = m->tmpv[4].as<double>();
-    int nblk = (nv + CG_T - 1) / CG_T;
-    TP_TRY(ensure(m->part2, sizeof(double) * 2 * KMAX * (size_t)nblk));
-    TP_TRY(ensure(m->scal, sizeof(CgScalars)));
-    CgScalars* sc = m->scal.as<CgScalars>();
-    TP_CUDA(cudaMemsetAsync(sc, 0, sizeof(CgScalars), st));
+           *pp = m->tmpv[3].as<double>(), *q = m->tmpv[4].as<double>(), *bp = m->tmpv[5].as<double>();
+    const int grid = cg_grid(nv);
+    TP_TRY(ensure(m->scal, 16 + sizeof(CgCtl) + sizeof(double) * 3 * KMAX * (size_t)grid));
+    CgCtl* ctl = m->scal.as<CgCtl>();
+    double* partA = (double*)(m->scal.as<char>() + ((sizeof(CgCtl) + 15) / 16) * 16);
+    double* partB = partA + (size_t)KMAX * grid;
+    TP_CUDA(cudaMemsetAsync(ctl, 0, sizeof(CgCtl), st));
     // rhs in the mean-zero subspace
-    TP_CUDA(cudaMemcpyAsync(r, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    TP_TRY(project_mean_zero(m, r, k, st));
-    k_cg_init<<<nblk, CG_T, 0, st>>>(m->rowptr.as<int>(), m->col.as<int>(), m->val.as<double>(),
-                                     m->dinv.as<double>(), nv, k, r, x, r, z, pp, m->part2.as<double>(),
-                                     sc);
-    TP_LAUNCH_CHECK();
+    TP_CUDA(cudaMemcpyAsync(bp, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    TP_TRY(project_mean_zero(m, bp, k, st));
     const double tol2 = p->cg_tol * p->cg_tol;
-    const int cap = p->cg_max;
-    int batch = 32, done = 0, it = 0;
-    CgScalars host{};
-    ProfScope* ps = new ProfScope(m, PK_CG, 0.0, st);
-    while (!done) {
-        count_launches(2 * (unsigned long long)batch - 1);
-        for (int i = 0; i < batch; ++i) {
-            k_cg_dir<<<nblk, CG_T, 0, st>>>(m->rowptr.as<int>(), m->col.as<int>(), m->val.as<double>(),
-                                            nv, k, z, pp, q, m->part2.as<double>(), sc);
-            k_cg_update<<<nblk, CG_T, 0, st>>>(m->dinv.as<double>(), nv, k, x, r, z, pp, q,
-                                               m->part2.as<double>(), sc, tol2, cap);
-        }
-        if (cudaGetLastError() != cudaSuccess) {
-            delete ps;
-            return fail(TP_ERR_CUDA, "cg: kernel launch failed");
-        }
-        if (i_copy(&host, sc, st) != TP_OK) {
-            delete ps;
-            return TP_ERR_CUDA;
-        }
-        done = host.done;
-        it = host.iters;
-        if (batch < 256) batch *= 2;
+    int cap = p->cg_max;
+    const int* rowptr = m->rowptr.as<int>();
+    const int* colp = m->col.as<int>();
+    const double* valp = m->val.as<double>();
+    const double* dinv = m->dinv.as<double>();
+    int nvv = nv, kk = k;
+    void* args[] = {(void*)&rowptr, (void*)&colp, (void*)&valp, (void*)&dinv, (void*)&nvv, (void*)&kk,
+                    (void*)&bp, (void*)&x, (void*)&r, (void*)&z, (void*)&pp, (void*)&q, (void*)&partA,
+                    (void*)&partB, (void*)&ctl, (void*)&tol2, (void*)&cap};
+    CgCtl host{};
+    {
+        ProfScope ps(m, PK_CG, 0.0, st);
+        TP_CUDA(cudaLaunchCooperativeKernel((void*)k_cg_persistent, dim3(grid), dim3(PCG_T), args, 0, st));
+        TP_LAUNCH_CHECK();
     }
-    delete ps;
+    TP_CUDA(cudaMemcpyAsync(&host, ctl, sizeof(CgCtl), cudaMemcpyDeviceToHost, st));
+    TP_CUDA(cudaStreamSynchronize(st));
+    if (host.err) return fail(TP_ERR_TIMEOUT, "cg: grid barrier timed out");
+    const int it = host.iters;
+    if (iters) *iters = it;
     // algorithmic bytes of one iteration: CSR values and columns, row pointers
-    // and the inverse diagonal once, the k-column vectors z (read), p and q
+    // and the inverse diagonal, the k-column vectors z (read twice), p and q
     // (read + write), x and r (read + write), z (write), p and q (read)
     m->prof.units[PK_CG] += (double)it * ((double)m->nnz * 12.0 + (double)nv * 12.0 +
-                                          (double)nv * k * 8.0 * 12.0);
-    if (iters) *iters = it;
+                                          (double)nv * k * 8.0 * 13.0);
     TP_TRY(project_mean_zero(m, x, k, st));
     TP_CUDA(cudaMemcpyAsync(z_out, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     bool conv = true;

@@ -182,10 +182,59 @@ __global__ void k_face_geom(const double* __restrict__ pos, const int* __restric
     }
 }
 
+// bounding box of the vertices: per-block min/max, then the centre (lo+hi)/2
+__global__ void k_pos_bbox_partial(const double* __restrict__ pos, int nv, double* __restrict__ part) {
+    __shared__ double lo[3][256], hi[3][256];
+    double l[3] = {1e300, 1e300, 1e300}, h[3] = {-1e300, -1e300, -1e300};
+    for (int i = blockIdx.x * 256 + threadIdx.x; i < nv; i += gridDim.x * 256)
+        for (int c = 0; c < 3; ++c) {
+            l[c] = fmin(l[c], pos[3 * i + c]);
+            h[c] = fmax(h[c], pos[3 * i + c]);
+        }
+    for (int c = 0; c < 3; ++c) {
+        lo[c][threadIdx.x] = l[c];
+        hi[c][threadIdx.x] = h[c];
+    }
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int c = 0; c < 3; ++c) {
+                lo[c][threadIdx.x] = fmin(lo[c][threadIdx.x], lo[c][threadIdx.x + w]);
+                hi[c][threadIdx.x] = fmax(hi[c][threadIdx.x], hi[c][threadIdx.x + w]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 3; ++c) {
+            part[6 * blockIdx.x + c] = lo[c][0];
+            part[6 * blockIdx.x + 3 + c] = hi[c][0];
+        }
+}
+
+__global__ void k_pos_bbox_center(const double* __restrict__ part, int nblk, double* __restrict__ center) {
+    if (threadIdx.x != 0) return;
+    for (int c = 0; c < 3; ++c) {
+        double l = 1e300, h = -1e300;
+        for (int b = 0; b < nblk; ++b) {
+            l = fmin(l, part[6 * b + c]);
+            h = fmax(h, part[6 * b + 3 + c]);
+        }
+        center[c] = 0.5 * (l + h);
+    }
+}
+
 int refresh_geometry(tp_mesh* m, cudaStream_t st) {
-    // reference frame: mean vertex position (FP64), so that the FP32 face
-    // table holds barycenters relative to the mesh
-    TP_TRY(colsum(m, m->pos.as<double>(), m->nv, 3, 1.0 / m->nv, m->center.as<double>(), st));
+    // reference frame: centre of the vertices' bounding box (exact in FP64),
+    // so that the FP32 face table holds barycenters relative to the mesh
+    {
+        int nblk = (m->nv + 255) / 256;
+        if (nblk > 256) nblk = 256;
+        TP_TRY(ensure(m->part2, sizeof(double) * 6 * (size_t)nblk));
+        k_pos_bbox_partial<<<nblk, 256, 0, st>>>(m->pos.as<double>(), m->nv, m->part2.as<double>());
+        TP_LAUNCH_CHECK();
+        k_pos_bbox_center<<<1, 32, 0, st>>>(m->part2.as<double>(), nblk, m->center.as<double>());
+        TP_LAUNCH_CHECK();
+    }
     TP_CUDA(cudaMemsetAsync(m->errflag.ptr, 0, sizeof(int) * 4, st));
     int nb = (m->nf + 255) / 256;
     k_face_geom<<<nb, 256, 0, st>>>(m->pos.as<double>(), m->faces.as<int>(), m->nf,

@@ -1,0 +1,127 @@
+"""GPU parity of the Barnes-Hut path (§4) against the FP64 oracle, through
+the C ABI: theta = 0 equals the direct sum; at theta in {0.25, 0.5} the GPU
+energy, energy rows and both differential modes equal the oracle's
+Barnes-Hut evaluation over the same tree (FP32 pair terms: 1e-5); the
+approximation error against the direct sum is reported and falls with
+theta. Full sizes: the 20,000-face torus and a 64-target sample of the
+1,310,720-face icosphere."""
+import numpy as np
+import pytest
+
+from oracle import tp_oracle as O
+from synth import small_mesh, workload
+
+pytestmark = pytest.mark.gpu
+
+TOL32 = 1e-5
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def dev(x, dtype=None):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(x), device="cuda:0", dtype=dtype)
+
+
+@pytest.fixture(scope="module")
+def meshes(lib):
+    import torch
+    out = {}
+    for name in ["ico3", "torus30x11", "ico1"]:
+        V, F = small_mesh(name, seed=31)
+        out[name] = (V, F, lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)))
+    yield out
+    for v in out.values():
+        v[2].close()
+
+
+@pytest.mark.parametrize("name", ["ico3", "torus30x11", "ico1"])
+@pytest.mark.parametrize("leaf", [8, 3])
+def test_theta_zero_equals_direct(lib, meshes, name, leaf):
+    V, F, m = meshes[name]
+    E_bh = lib.tp_energy(m, lib.params(theta=1e-9, leaf_size=leaf))
+    assert rel(E_bh, O.energy(V, F)) <= TOL32
+    g, _ = lib.tp_differential(m, lib.params(theta=1e-9, leaf_size=leaf))
+    assert rel(g, O.differential(V, F)) <= TOL32
+
+
+@pytest.mark.parametrize("name", ["ico3", "torus30x11"])
+@pytest.mark.parametrize("theta", [0.25, 0.5])
+def test_bh_energy_matches_oracle_bh(lib, meshes, name, theta):
+    V, F, m = meshes[name]
+    p = lib.params(theta=theta)
+    E = lib.tp_energy(m, p)
+    E_ref = O.bh_energy(V, F, theta)
+    assert rel(E, E_ref) <= TOL32
+    tg = np.array([0, 17, len(F) // 2, len(F) - 1], dtype=np.int32)
+    rows = lib.tp_energy_rows(m, tg, p)
+    ref_rows, _ = O.bh_energy_rows(V, F, theta, 8, 6.0, tg)
+    assert rel(rows, ref_rows) <= TOL32
+
+
+@pytest.mark.parametrize("name", ["ico3", "torus30x11"])
+@pytest.mark.parametrize("theta", [0.25, 0.5])
+@pytest.mark.parametrize("mode", ["full", "literal"])
+def test_bh_differential_matches_oracle_bh(lib, meshes, name, theta, mode):
+    V, F, m = meshes[name]
+    p = lib.params(theta=theta, bh_diff_mode=lib.TP_BH_DIFF_FULL if mode == "full" else lib.TP_BH_DIFF_LITERAL)
+    g, E = lib.tp_differential(m, p)
+    assert rel(g, O.bh_differential(V, F, theta, mode=mode)) <= TOL32
+    assert rel(E, O.bh_energy(V, F, theta)) <= TOL32
+
+
+def test_bh_error_falls_with_theta(lib, meshes):
+    V, F, m = meshes["ico3"]
+    E = O.energy(V, F)
+    g_ref = O.differential(V, F)
+    errE, errG = [], []
+    for th in (0.25, 0.5, 1.0):
+        p = lib.params(theta=th)
+        errE.append(abs(lib.tp_energy(m, p) - E) / E)
+        errG.append(rel(lib.tp_differential(m, p)[0], g_ref))
+    print("BH relative error vs theta (0.25, 0.5, 1.0): E", errE, "dE", errG)
+    assert errE[0] < errE[1] < errE[2]
+    assert errG[0] < errG[1] < errG[2]
+
+
+def test_bh_rows_with_device_targets_and_repeat(lib, meshes):
+    V, F, m = meshes["torus30x11"]
+    p = lib.params(theta=0.5)
+    tg = np.arange(0, len(F), 7, dtype=np.int32)
+    r1 = lib.tp_energy_rows(m, dev(tg), p).cpu().numpy()
+    r2 = lib.tp_energy_rows(m, tg, p)
+    assert np.array_equal(r1, r2)
+    ref, _ = O.bh_energy_rows(V, F, 0.5, 8, 6.0, tg)
+    assert rel(r1, ref) <= TOL32
+
+
+def test_torus20k_bh(lib):
+    import torch
+    V, F = workload("torus_20k")
+    with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as m:
+        p = lib.params(theta=0.5)
+        E = lib.tp_energy(m, p)
+        g, _ = lib.tp_differential(m, p)
+    assert rel(E, O.bh_energy(V, F, 0.5)) <= TOL32
+    idx = np.random.default_rng(5).choice(len(V), 32, replace=False)
+    ref = O.bh_differential(V, F, 0.5, mode="full")
+    assert rel(g[idx], ref[idx]) <= TOL32
+
+
+def test_icosphere_l8_bh_sample(lib):
+    import torch
+    V, F = workload("icosphere_l8")
+    tg = np.random.default_rng(505).choice(len(F), 64, replace=False).astype(np.int32)
+    with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as m:
+        rows = lib.tp_energy_rows(m, tg, lib.params(theta=0.5))
+        rows_direct = lib.tp_energy_rows(m, tg, lib.params())
+    tree = O.bvh_build(V, F, 8)
+    Tr, L = O.bh_interactions(V, F, 0.5, 8, tg, tree)
+    ref_bh, _ = O.bh_energy_rows(V, F, 0.5, 8, 6.0, tg)
+    ref_direct = O.energy_rows(V, F, 6.0, tg)
+    assert rel(rows, ref_bh) <= TOL32
+    assert rel(rows_direct, ref_direct) <= TOL32
+    print("icosphere_l8 sample: BH(0.5) vs direct FP64 rows, relative error", rel(rows, ref_direct))

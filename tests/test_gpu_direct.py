@@ -182,22 +182,36 @@ def test_precond_step_repeated_projection_matches_oracle(lib):
     assert abs(O.total_volume(f_new, F) - V0) < 1e-9 * abs(V0)
 
 
-def test_precond_step_armijo_descends(lib):
+def test_precond_step_armijo_trajectory_matches_oracle(lib):
+    # three Armijo steps with three corrective projections each: the FP64
+    # path follows the oracle's exact-solve trajectory; the FP32 path descends
     import torch
     V, F = small_mesh("ico3", seed=5)
     A0, V0 = O.total_area(V, F), O.total_volume(V, F)
+    f_ref = V.copy()
+    E_ref = []
+    for _ in range(3):
+        r = O.precond_step(f_ref, F, A0, V0, proj_iters=3)
+        f_ref = r["f_new"]
+        E_ref.append((r["tau"], r["E0"], r["E1"]))
+    c = lib.tp_constraints(flags=3, A0=A0, V0=V0)
     with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as m:
-        c = lib.tp_constraints(flags=3, A0=A0, V0=V0)
-        p = lib.params(cg_tol=1e-8, proj_iters=3)
-        E = []
-        for _ in range(3):
+        p = lib.params(precision=1, krylov_tol=1e-11, cg_tol=1e-12, proj_iters=3)
+        for k in range(3):
             rep = lib.precond_step(m, c, p)
             assert rep["status"] == 0 and rep["slope"] < 0
-            E.append((rep["E_before"], rep["E_after"]))
+            assert rep["tau"] == E_ref[k][0]
+            assert rel(rep["E_after"], E_ref[k][2]) < 1e-7
         f = m.get_positions()
-    assert all(b < a for a, b in E)
-    assert abs(O.total_area(f, F) - A0) < 1e-6 * A0
-    assert abs(O.total_volume(f, F) - V0) < 1e-6 * abs(V0)
+    assert rel(f - V, f_ref - V) < 1e-6
+    with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as m:
+        p = lib.params(cg_tol=1e-8, proj_iters=3)
+        for _ in range(3):
+            rep = lib.precond_step(m, c, p)
+            assert rep["status"] == 0 and rep["slope"] < 0 and rep["E_after"] < rep["E_before"]
+        f = m.get_positions()
+    assert abs(O.total_area(f, F) - A0) < 1e-5 * A0
+    assert abs(O.total_volume(f, F) - V0) < 1e-5 * abs(V0)
 
 
 # ---------------------------------------------------------------------------
