@@ -102,6 +102,33 @@ static int bvh_shape(tp_mesh* m, int leaf, BvhHost& h) {
 }
 
 
+// node buffer layout: [BvhNode nn][d4 nn][float4 nn][double nn]; with 64-,
+// 32-, 16- and 8-byte elements in decreasing size every array starts on a
+// boundary of its own element size
+static_assert(sizeof(BvhNode) == 64, "BvhNode must stay 64 bytes");
+static_assert(sizeof(d4) == 32 && alignof(d4) == 32, "d4 must be a 32-byte aligned quad");
+
+struct NodeArrays {
+    BvhNode* node;
+    d4* node64;      // FP64 barycenter (relative frame) and area
+    float4* nodelo;  // low parts of the FP32 barycenter
+    double* noder;   // FP64 radius
+};
+
+static size_t node_bytes(int nn) {
+    return (sizeof(BvhNode) + sizeof(d4) + sizeof(float4) + sizeof(double)) * (size_t)nn;
+}
+
+static NodeArrays node_arrays(const tp_mesh* m) {
+    NodeArrays a;
+    const int nn = m->bvh_nodes;
+    a.node = m->bvh_node.as<BvhNode>();
+    a.node64 = reinterpret_cast<d4*>(a.node + nn);
+    a.nodelo = reinterpret_cast<float4*>(a.node64 + nn);
+    a.noder = reinterpret_cast<double*>(a.nodelo + nn);
+    return a;
+}
+
 // ---------------------------------------------------------------------------
 // device: Morton codes, sort, face boxes, node aggregates
 // ---------------------------------------------------------------------------
@@ -189,14 +216,15 @@ __global__ void k_sorted_faces(const unsigned long long* __restrict__ keys, int 
                                const double* __restrict__ pos, const int* __restrict__ faces,
                                const double* __restrict__ center, const d4* __restrict__ f64a,
                                const float4* __restrict__ f32a, const float4* __restrict__ f32b,
-                               int* __restrict__ perm, float4* __restrict__ sa, float4* __restrict__ sb,
-                               FaceBox* __restrict__ box) {
+                               const float4* __restrict__ f32c, int* __restrict__ perm, float4* __restrict__ sa,
+                               float4* __restrict__ sb, float4* __restrict__ sl, FaceBox* __restrict__ box) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf) return;
     int S = (int)(keys[i] & 0xffffffffull);
     perm[i] = S;
     sa[i] = f32a[S];
     sb[i] = f32b[S];
+    sl[i] = f32c[S];
     d4 X = f64a[S];
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, r2 = 0.0;
     for (int cr = 0; cr < 3; ++cr) {
@@ -219,7 +247,8 @@ __global__ void k_nodes_level(const NodeShape* __restrict__ shape, const int* __
                               const int* __restrict__ perm, const double* __restrict__ pos,
                               const int* __restrict__ faces, const double* __restrict__ center,
                               const d4* __restrict__ f64a, const FaceBox* __restrict__ fbox,
-                              BvhNode* __restrict__ node, d4* __restrict__ node64, double* __restrict__ noder) {
+                              BvhNode* __restrict__ node, d4* __restrict__ node64, double* __restrict__ noder,
+                              float4* __restrict__ nodelo) {
     int k = n0 + blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n1) return;
     int id = order[k];
@@ -264,6 +293,8 @@ __global__ void k_nodes_level(const NodeShape* __restrict__ shape, const int* __
     }
     node64[id] = d4{X[0], X[1], X[2], a};
     noder[id] = r;
+    nodelo[id] = make_float4((float)(X[0] - (double)(float)X[0]), (float)(X[1] - (double)(float)X[1]),
+                             (float)(X[2] - (double)(float)X[2]), 0.f);
     BvhNode o;
     o.cx = (float)X[0]; o.cy = (float)X[1]; o.cz = (float)X[2]; o.a = (float)a;
     o.lox = (float)lo[0]; o.loy = (float)lo[1]; o.loz = (float)lo[2]; o.r2 = (float)(r * r);
@@ -300,15 +331,21 @@ int bvh_build(tp_mesh* m, const tp_params* p, cudaStream_t st) {
     TP_TRY(ensure(m->bvh_perm, sizeof(int) * (size_t)nf + sizeof(FaceBox) * (size_t)nf));
     TP_TRY(ensure(m->bvh_f32a, sizeof(float4) * (size_t)nf));
     TP_TRY(ensure(m->bvh_f32b, sizeof(float4) * (size_t)nf));
-    TP_TRY(ensure(m->bvh_node, (sizeof(BvhNode) + sizeof(d4) + sizeof(double)) * (size_t)h.nnodes));
+    TP_TRY(ensure(m->bvh_node, node_bytes(h.nnodes)));
+    TP_TRY(ensure(m->bvh_f32c, sizeof(float4) * (size_t)nf));
     unsigned long long* kin = m->bvh_keys.as<unsigned long long>();
     unsigned long long* kout = kin + nf;
     double* bpart = (double*)(kout + nf);
     int* perm = m->bvh_perm.as<int>();
     FaceBox* fbox = (FaceBox*)(perm + nf);
-    BvhNode* node = m->bvh_node.as<BvhNode>();
-    d4* node64 = (d4*)(node + h.nnodes);
-    double* noder = (double*)(node64 + h.nnodes);
+    const NodeArrays na = node_arrays(m);
+    if ((reinterpret_cast<uintptr_t>(na.node64) & 31) || (reinterpret_cast<uintptr_t>(na.nodelo) & 15) ||
+        (reinterpret_cast<uintptr_t>(na.noder) & 7))
+        return fail(TP_ERR_CUDA, "bvh: node arrays misaligned");
+    BvhNode* node = na.node;
+    d4* node64 = na.node64;
+    double* noder = na.noder;
+    float4* nodelo = na.nodelo;
     const NodeShape* shape = m->bvh_tmp.as<NodeShape>();
     const int* right = (const int*)(shape + h.nnodes);
     const int* order = right + h.nnodes;
@@ -324,15 +361,16 @@ int bvh_build(tp_mesh* m, const tp_params* p, cudaStream_t st) {
     TP_CUDA(cub::DeviceRadixSort::SortKeys(m->bvh_sortws.ptr, sort_bytes, kin, kout, nf, 0, 62, st));
     k_sorted_faces<<<(nf + 255) / 256, 256, 0, st>>>(kout, nf, m->pos.as<double>(), m->faces.as<int>(),
                                                      m->center.as<double>(), m->f64a.as<d4>(),
-                                                     m->f32a.as<float4>(), m->f32b.as<float4>(), perm,
-                                                     m->bvh_f32a.as<float4>(), m->bvh_f32b.as<float4>(), fbox);
+                                                     m->f32a.as<float4>(), m->f32b.as<float4>(),
+                                                     m->f32c.as<float4>(), perm, m->bvh_f32a.as<float4>(),
+                                                     m->bvh_f32b.as<float4>(), m->bvh_f32c.as<float4>(), fbox);
     TP_LAUNCH_CHECK();
     for (int d = h.maxdepth; d >= 0; --d) {
         int n0 = h.level_off[d], n1 = h.level_off[d + 1];
         k_nodes_level<<<(n1 - n0 + 127) / 128, 128, 0, st>>>(shape, right, order, n0, n1, perm,
                                                              m->pos.as<double>(), m->faces.as<int>(),
                                                              m->center.as<double>(), m->f64a.as<d4>(), fbox,
-                                                             node, node64, noder);
+                                                             node, node64, noder, nodelo);
         TP_LAUNCH_CHECK();
     }
     m->bvh_valid = true;
@@ -378,15 +416,16 @@ struct KahanF {
 // energy rows: thread per target (sorted position i, or target list)
 template <bool P6>
 __global__ void __launch_bounds__(128)
-k_bh_energy(const BvhNode* __restrict__ node, int nnodes, const float4* __restrict__ sa,
-            const float4* __restrict__ sb, const FaceBox* __restrict__ fbox, const int* __restrict__ perm,
+k_bh_energy(const BvhNode* __restrict__ node, const float4* __restrict__ nodelo, int nnodes,
+            const float4* __restrict__ sa, const float4* __restrict__ sb, const float4* __restrict__ sl,
+            const FaceBox* __restrict__ fbox, const int* __restrict__ perm,
             const int* __restrict__ inv_targets /* sorted positions of a target list, or null */, int nt,
             float theta2, float halfp, const d4* __restrict__ f64a, double* __restrict__ rows,
             unsigned long long* __restrict__ count) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= nt) return;
     const int i = inv_targets ? inv_targets[t] : t;
-    float4 A = sa[i], B = sb[i];
+    float4 A = sa[i], B = sb[i], Al = sl[i];
     FaceBox fb = fbox[i];
     float acc = 0.f;
     KahanF sum;
@@ -397,7 +436,9 @@ k_bh_energy(const BvhNode* __restrict__ node, int nnodes, const float4* __restri
         float d2 = box_dist2(fb.lox, fb.loy, fb.loz, fb.hix, fb.hiy, fb.hiz, n);
         float mr2 = fmaxf(fb.r2, n.r2);
         if (mr2 < __fmul_rn(theta2, d2)) {
-            float dx = A.x - n.cx, dy = A.y - n.cy, dz = A.z - n.cz;
+            float4 nl = nodelo[id];
+            float dx = (A.x - n.cx) + (Al.x - nl.x), dy = (A.y - n.cy) + (Al.y - nl.y),
+                  dz = (A.z - n.cz) + (Al.z - nl.z);
             float r2 = dx * dx + dy * dy + dz * dz;
             float u = B.x * dx + B.y * dy + B.z * dz;
             float ir2 = frcp(fmaxf(r2, 1e-18f));
@@ -410,8 +451,9 @@ k_bh_energy(const BvhNode* __restrict__ node, int nnodes, const float4* __restri
         } else if (n.leaf) {
             for (int j = n.first; j < n.first + n.count; ++j) {
                 if (j == i) continue;
-                float4 s = sa[j];
-                float dx = A.x - s.x, dy = A.y - s.y, dz = A.z - s.z;
+                float4 s = sa[j], l = sl[j];
+                float dx = (A.x - s.x) + (Al.x - l.x), dy = (A.y - s.y) + (Al.y - l.y),
+                      dz = (A.z - s.z) + (Al.z - l.z);
                 float r2 = dx * dx + dy * dy + dz * dz;
                 float u = B.x * dx + B.y * dy + B.z * dz;
                 float ir2 = frcp(fmaxf(r2, 1e-18f));
@@ -489,17 +531,21 @@ int energy_rows_bh(tp_mesh* m, const tp_params* p, const int32_t* tl, int nt, do
         out = rs;  // sorted order, unsorted afterwards
     }
     TP_TRY(bh_counter(m, st));
+    const NodeArrays na = node_arrays(m);
+    const BvhNode* node = na.node;
+    const float4* nodelo = na.nodelo;
+    const float4* sa = m->bvh_f32a.as<float4>();
+    const float4* sb = m->bvh_f32b.as<float4>();
+    const float4* sl = m->bvh_f32c.as<float4>();
     {
         ProfScope ps(m, PK_BH_ENERGY, 0.0, st);
         unsigned long long* cnt = m->bhcount.as<unsigned long long>();
         if (p->p == 6.0)
-            k_bh_energy<true><<<(nt + 127) / 128, 128, 0, st>>>(m->bvh_node.as<BvhNode>(), m->bvh_nodes,
-                                                               m->bvh_f32a.as<float4>(), m->bvh_f32b.as<float4>(),
+            k_bh_energy<true><<<(nt + 127) / 128, 128, 0, st>>>(node, nodelo, m->bvh_nodes, sa, sb, sl,
                                                                fbox, perm, map, nt, theta2, halfp,
                                                                m->f64a.as<d4>(), out, cnt);
         else
-            k_bh_energy<false><<<(nt + 127) / 128, 128, 0, st>>>(m->bvh_node.as<BvhNode>(), m->bvh_nodes,
-                                                                m->bvh_f32a.as<float4>(), m->bvh_f32b.as<float4>(),
+            k_bh_energy<false><<<(nt + 127) / 128, 128, 0, st>>>(node, nodelo, m->bvh_nodes, sa, sb, sl,
                                                                 fbox, perm, map, nt, theta2, halfp,
                                                                 m->f64a.as<d4>(), out, cnt);
         TP_LAUNCH_CHECK();
@@ -519,13 +565,14 @@ int energy_rows_bh(tp_mesh* m, const tp_params* p, const int32_t* tl, int nt, do
 // reverse scatter: node accumulators nacc[id*4 + 0..2] = G, [3] = Q; faces facc[i*4 ...]
 template <bool P6, bool FULL>
 __global__ void __launch_bounds__(128)
-k_bh_diff(const BvhNode* __restrict__ node, int nnodes, const float4* __restrict__ sa,
-          const float4* __restrict__ sb, const FaceBox* __restrict__ fbox, int nf, float theta2, float hm1,
+k_bh_diff(const BvhNode* __restrict__ node, const float4* __restrict__ nodelo, int nnodes,
+          const float4* __restrict__ sa, const float4* __restrict__ sb, const float4* __restrict__ sl,
+          const FaceBox* __restrict__ fbox, int nf, float theta2, float hm1,
           float p, double* __restrict__ tacc /* [nf][8] sorted */, double* __restrict__ nacc,
           double* __restrict__ facc, unsigned long long* __restrict__ count) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf) return;
-    float4 A = sa[i], B = sb[i];
+    float4 A = sa[i], B = sb[i], Al = sl[i];
     FaceBox fb = fbox[i];
     const float aS = A.w;
     KahanF acc[8];
@@ -541,8 +588,9 @@ k_bh_diff(const BvhNode* __restrict__ node, int nnodes, const float4* __restrict
     };
     // one interaction with a source of barycenter (sx,sy,sz), weight w; returns the
     // source-side derivative (G: -a_S w dK/dd, Q: a_S K)
-    auto interact = [&](float sx, float sy, float sz, float w, float* G, float& Q) {
-        float dx = A.x - sx, dy = A.y - sy, dz = A.z - sz;
+    auto interact = [&](float4 src, float4 lo, float w, float* G, float& Q) {
+        float dx = (A.x - src.x) + (Al.x - lo.x), dy = (A.y - src.y) + (Al.y - lo.y),
+              dz = (A.z - src.z) + (Al.z - lo.z);
         float r2 = dx * dx + dy * dy + dz * dz;
         float u = B.x * dx + B.y * dy + B.z * dz;
         float ir2 = frcp(fmaxf(r2, 1e-18f));
@@ -574,7 +622,7 @@ k_bh_diff(const BvhNode* __restrict__ node, int nnodes, const float4* __restrict
         float mr2 = fmaxf(fb.r2, n.r2);
         if (mr2 < __fmul_rn(theta2, d2)) {
             float G[3], Q;
-            interact(n.cx, n.cy, n.cz, n.a, G, Q);
+            interact(make_float4(n.cx, n.cy, n.cz, 0.f), nodelo[id], n.a, G, Q);
             ++nint;
             if (FULL) {
                 atomicAdd(nacc + 4 * id + 0, (double)G[0]);
@@ -589,7 +637,7 @@ k_bh_diff(const BvhNode* __restrict__ node, int nnodes, const float4* __restrict
                 if (j == i) continue;
                 float4 s = sa[j];
                 float G[3], Q;
-                interact(s.x, s.y, s.z, s.w, G, Q);
+                interact(s, sl[j], s.w, G, Q);
                 ++nint;
                 if (FULL) {
                     atomicAdd(facc + 4 * j + 0, (double)G[0]);
@@ -673,8 +721,10 @@ int diff_adjoints_bh(tp_mesh* m, const tp_params* p, double* adj, double* erow, 
     const int nf = m->nf, nn = m->bvh_nodes;
     int* perm = m->bvh_perm.as<int>();
     FaceBox* fbox = (FaceBox*)(perm + nf);
-    BvhNode* node = m->bvh_node.as<BvhNode>();
-    d4* node64 = (d4*)(node + nn);
+    const NodeArrays na = node_arrays(m);
+    BvhNode* node = na.node;
+    d4* node64 = na.node64;
+    const float4* nodelo = na.nodelo;
     TP_TRY(ensure(m->part, sizeof(double) * ((size_t)8 * nf + 4 * (size_t)nn + 4 * (size_t)nf)));
     double* tacc = m->part.as<double>();
     double* nacc = tacc + (size_t)8 * nf;
@@ -685,6 +735,7 @@ int diff_adjoints_bh(tp_mesh* m, const tp_params* p, double* adj, double* erow, 
     float hm1 = (float)(0.5 * p->p - 1.0);
     const float4* sa = m->bvh_f32a.as<float4>();
     const float4* sb = m->bvh_f32b.as<float4>();
+    const float4* sl = m->bvh_f32c.as<float4>();
     dim3 g((nf + 127) / 128);
     TP_TRY(bh_counter(m, st));
     {
@@ -692,11 +743,11 @@ int diff_adjoints_bh(tp_mesh* m, const tp_params* p, double* adj, double* erow, 
         unsigned long long* cnt = m->bhcount.as<unsigned long long>() + 1;
         const float pf = (float)p->p;
         if (p->p == 6.0) {
-            if (full) k_bh_diff<true, true><<<g, 128, 0, st>>>(node, nn, sa, sb, fbox, nf, theta2, hm1, pf, tacc, nacc, facc, cnt);
-            else k_bh_diff<true, false><<<g, 128, 0, st>>>(node, nn, sa, sb, fbox, nf, theta2, hm1, pf, tacc, nacc, facc, cnt);
+            if (full) k_bh_diff<true, true><<<g, 128, 0, st>>>(node, nodelo, nn, sa, sb, sl, fbox, nf, theta2, hm1, pf, tacc, nacc, facc, cnt);
+            else k_bh_diff<true, false><<<g, 128, 0, st>>>(node, nodelo, nn, sa, sb, sl, fbox, nf, theta2, hm1, pf, tacc, nacc, facc, cnt);
         } else {
-            if (full) k_bh_diff<false, true><<<g, 128, 0, st>>>(node, nn, sa, sb, fbox, nf, theta2, hm1, pf, tacc, nacc, facc, cnt);
-            else k_bh_diff<false, false><<<g, 128, 0, st>>>(node, nn, sa, sb, fbox, nf, theta2, hm1, pf, tacc, nacc, facc, cnt);
+            if (full) k_bh_diff<false, true><<<g, 128, 0, st>>>(node, nodelo, nn, sa, sb, sl, fbox, nf, theta2, hm1, pf, tacc, nacc, facc, cnt);
+            else k_bh_diff<false, false><<<g, 128, 0, st>>>(node, nodelo, nn, sa, sb, sl, fbox, nf, theta2, hm1, pf, tacc, nacc, facc, cnt);
         }
         TP_LAUNCH_CHECK();
     }

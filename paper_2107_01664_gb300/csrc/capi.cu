@@ -141,7 +141,8 @@ int tp_mesh_create(int device, int nv, int nf, const double* pos, const int32_t*
         (s = ensure(m->vf_ptr, sizeof(int) * (nv + 1))) || (s = ensure(m->vf_idx, sizeof(int) * 3 * (size_t)nf)) ||
         (s = ensure(m->pos, sizeof(double) * 3 * (size_t)nv)) || (s = ensure(m->center, sizeof(double) * 4)) ||
         (s = ensure(m->errflag, sizeof(int) * 4)) || (s = ensure(m->f32a, sizeof(float4) * (size_t)nf)) ||
-        (s = ensure(m->f32b, sizeof(float4) * (size_t)nf)) || (s = ensure(m->f64a, sizeof(d4) * (size_t)nf)) ||
+        (s = ensure(m->f32b, sizeof(float4) * (size_t)nf)) || (s = ensure(m->f32c, sizeof(float4) * (size_t)nf)) ||
+        (s = ensure(m->f64a, sizeof(d4) * (size_t)nf)) ||
         (s = ensure(m->f64b, sizeof(d4) * (size_t)nf)) || (s = ensure(m->fgrad, sizeof(double) * 9 * (size_t)nf)))
         return bail(s);
     if (cudaMemcpy(m->faces.ptr, F.data(), sizeof(int) * 3 * (size_t)nf, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -179,9 +180,10 @@ int tp_mesh_destroy(tp_mesh* m) {
     if (!m) return TP_OK;
     DeviceGuard g(m->device);
     Buf* all[] = {&m->faces, &m->vf_ptr, &m->vf_idx, &m->pos, &m->center, &m->errflag, &m->f32a, &m->f32b,
+                  &m->f32c, &m->tilebox,
                   &m->f64a, &m->f64b, &m->fgrad, &m->rowptr, &m->col, &m->cotsrc, &m->diagpos, &m->val,
                   &m->dinv, &m->bvh_node, &m->bvh_perm, &m->bvh_keys, &m->bvh_tmp, &m->bvh_sortws,
-                  &m->bvh_f32a, &m->bvh_f32b, &m->bvh_nodeP, &m->part, &m->part2, &m->scal, &m->corner,
+                  &m->bvh_f32a, &m->bvh_f32b, &m->bvh_f32c, &m->bvh_nodeP, &m->part, &m->part2, &m->scal, &m->corner,
                   &m->wv64, &m->wv32, &m->io_in, &m->io_out, &m->adj, &m->erow, &m->tlist, &m->rowsum,
                   &m->kry};
     for (Buf* b : all) release(*b);

@@ -196,6 +196,21 @@ __device__ __forceinline__ void block_reduce(double (*vals)[NTH], int nval) {
 
 constexpr int PCG_T = 128;
 
+// sums over blocks of per-block partials part[bI * ld + j], j < nval: every
+// thread loads a strided subset, then a fixed-order tree in shared memory.
+// Result in sh[j][0]; identical in every block (same data, same order).
+__device__ __forceinline__ void reduce_partials(const double* __restrict__ part, int ld, int nval,
+                                                unsigned nblk, double (*sh)[PCG_T]) {
+    __syncthreads();
+    for (int j = 0; j < nval; ++j) {
+        double a = 0.0;
+        for (unsigned bI = threadIdx.x; bI < nblk; bI += PCG_T) a += __ldcg(part + (size_t)bI * ld + j);
+        sh[j][threadIdx.x] = a;
+    }
+    __syncthreads();
+    block_reduce<PCG_T>(sh, nval);
+}
+
 __global__ void __launch_bounds__(PCG_T)
 k_cg_persistent(const int* __restrict__ rowptr, const int* __restrict__ col, const double* __restrict__ val,
                 const double* __restrict__ dinv, int nv, int k, const double* __restrict__ b,
@@ -226,13 +241,10 @@ k_cg_persistent(const int* __restrict__ rowptr, const int* __restrict__ col, con
     if (threadIdx.x == 0)
         for (int j = 0; j < 2 * k; ++j) partB[(size_t)blockIdx.x * 2 * KMAX + j] = sh[j][0];
     if (!grid_barrier(ctl, nblk)) return;
+    reduce_partials(partB, 2 * KMAX, 2 * k, nblk, sh);
     if (threadIdx.x < k) {
         int c = threadIdx.x;
-        double rz = 0.0, bb = 0.0;
-        for (unsigned bI = 0; bI < nblk; ++bI) {
-            rz += __ldcg(partB + (size_t)bI * 2 * KMAX + c);
-            bb += __ldcg(partB + (size_t)bI * 2 * KMAX + k + c);
-        }
+        double rz = sh[c][0], bb = sh[k + c][0];
         s_rz[c] = rz;
         s_bb[c] = bb;
         s_beta[c] = 0.0;
@@ -281,10 +293,10 @@ k_cg_persistent(const int* __restrict__ rowptr, const int* __restrict__ col, con
         if (threadIdx.x == 0)
             for (int c = 0; c < k; ++c) partA[(size_t)blockIdx.x * KMAX + c] = sh[c][0];
         if (!grid_barrier(ctl, nblk)) return;
+        reduce_partials(partA, KMAX, k, nblk, sh);
         if (threadIdx.x < k) {
             int c = threadIdx.x;
-            double pq = 0.0;
-            for (unsigned bI = 0; bI < nblk; ++bI) pq += __ldcg(partA + (size_t)bI * KMAX + c);
+            double pq = sh[c][0];
             s_alpha[c] = (s_active[c] && pq > 0.0) ? s_rz[c] / pq : 0.0;
         }
         __syncthreads();
@@ -308,13 +320,10 @@ k_cg_persistent(const int* __restrict__ rowptr, const int* __restrict__ col, con
             for (int j = 0; j < 2 * k; ++j) partB[(size_t)blockIdx.x * 2 * KMAX + j] = sh[j][0];
         if (!grid_barrier(ctl, nblk)) return;
         ++it;
+        reduce_partials(partB, 2 * KMAX, 2 * k, nblk, sh);
         if (threadIdx.x < k) {
             int c = threadIdx.x;
-            double rz = 0.0, rr = 0.0;
-            for (unsigned bI = 0; bI < nblk; ++bI) {
-                rz += __ldcg(partB + (size_t)bI * 2 * KMAX + c);
-                rr += __ldcg(partB + (size_t)bI * 2 * KMAX + k + c);
-            }
+            double rz = sh[c][0], rr = sh[k + c][0];
             if (s_active[c]) {
                 s_beta[c] = s_rz[c] > 0.0 ? rz / s_rz[c] : 0.0;
                 s_rz[c] = rz;

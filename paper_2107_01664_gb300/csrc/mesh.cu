@@ -140,8 +140,8 @@ int sum_f64(const double* x, int n, double* out_dev, tp_mesh* m, cudaStream_t st
 
 __global__ void k_face_geom(const double* __restrict__ pos, const int* __restrict__ faces, int nf,
                             const double* __restrict__ center, float4* __restrict__ f32a,
-                            float4* __restrict__ f32b, d4* __restrict__ f64a, d4* __restrict__ f64b,
-                            double* __restrict__ fgrad, int* __restrict__ err) {
+                            float4* __restrict__ f32b, float4* __restrict__ f32c, d4* __restrict__ f64a,
+                            d4* __restrict__ f64b, double* __restrict__ fgrad, int* __restrict__ err) {
     int S = blockIdx.x * blockDim.x + threadIdx.x;
     if (S >= nf) return;
     int i = faces[3 * S], j = faces[3 * S + 1], k = faces[3 * S + 2];
@@ -169,6 +169,8 @@ __global__ void k_face_geom(const double* __restrict__ pos, const int* __restric
     f64a[S] = d4{X[0], X[1], X[2], a};
     f64b[S] = d4{N[0], N[1], N[2], 0.0};
     f32a[S] = make_float4((float)X[0], (float)X[1], (float)X[2], (float)a);
+    f32c[S] = make_float4((float)(X[0] - (double)(float)X[0]), (float)(X[1] - (double)(float)X[1]),
+                          (float)(X[2] - (double)(float)X[2]), 0.0f);
     f32b[S] = make_float4((float)N[0], (float)N[1], (float)N[2], 0.0f);
     // hat gradients: grad phi_c = N x e_c / (2a), e_c the edge opposite corner c
     const double* P[3] = {pi, pj, pk};
@@ -213,6 +215,7 @@ __global__ void k_pos_bbox_partial(const double* __restrict__ pos, int nv, doubl
 
 __global__ void k_pos_bbox_center(const double* __restrict__ part, int nblk, double* __restrict__ center) {
     if (threadIdx.x != 0) return;
+    double half[3];
     for (int c = 0; c < 3; ++c) {
         double l = 1e300, h = -1e300;
         for (int b = 0; b < nblk; ++b) {
@@ -220,6 +223,35 @@ __global__ void k_pos_bbox_center(const double* __restrict__ part, int nblk, dou
             h = fmax(h, part[6 * b + 3 + c]);
         }
         center[c] = 0.5 * (l + h);
+        half[c] = 0.5 * (h - l);
+    }
+    // source tiles closer than R/16 to a target block (R = half diagonal of
+    // the bounding box) take the compensated barycenter difference: beyond
+    // it the FP32 rounding of the barycenters perturbs |d| by < 2^-19
+    double R2 = half[0] * half[0] + half[1] * half[1] + half[2] * half[2];
+    center[3] = R2 / 256.0;
+}
+
+// bounding box of the FP32 barycenters of each tile of 128 consecutive faces
+__global__ void k_tile_boxes(const float4* __restrict__ f32a, int nf, float4* __restrict__ box) {
+    __shared__ float lo[3][128], hi[3][128];
+    int S = blockIdx.x * 128 + threadIdx.x;
+    float4 x = S < nf ? f32a[S] : f32a[blockIdx.x * 128];
+    lo[0][threadIdx.x] = hi[0][threadIdx.x] = x.x;
+    lo[1][threadIdx.x] = hi[1][threadIdx.x] = x.y;
+    lo[2][threadIdx.x] = hi[2][threadIdx.x] = x.z;
+    __syncthreads();
+    for (int w = 64; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int c = 0; c < 3; ++c) {
+                lo[c][threadIdx.x] = fminf(lo[c][threadIdx.x], lo[c][threadIdx.x + w]);
+                hi[c][threadIdx.x] = fmaxf(hi[c][threadIdx.x], hi[c][threadIdx.x + w]);
+            }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        box[2 * blockIdx.x] = make_float4(lo[0][0], lo[1][0], lo[2][0], 0.f);
+        box[2 * blockIdx.x + 1] = make_float4(hi[0][0], hi[1][0], hi[2][0], 0.f);
     }
 }
 
@@ -239,9 +271,15 @@ int refresh_geometry(tp_mesh* m, cudaStream_t st) {
     int nb = (m->nf + 255) / 256;
     k_face_geom<<<nb, 256, 0, st>>>(m->pos.as<double>(), m->faces.as<int>(), m->nf,
                                     m->center.as<double>(), m->f32a.as<float4>(),
-                                    m->f32b.as<float4>(), m->f64a.as<d4>(), m->f64b.as<d4>(),
-                                    m->fgrad.as<double>(), m->errflag.as<int>());
+                                    m->f32b.as<float4>(), m->f32c.as<float4>(), m->f64a.as<d4>(),
+                                    m->f64b.as<d4>(), m->fgrad.as<double>(), m->errflag.as<int>());
     TP_LAUNCH_CHECK();
+    {
+        int ntiles = (m->nf + 127) / 128;
+        TP_TRY(ensure(m->tilebox, sizeof(float4) * 2 * (size_t)ntiles));
+        k_tile_boxes<<<ntiles, 128, 0, st>>>(m->f32a.as<float4>(), m->nf, m->tilebox.as<float4>());
+        TP_LAUNCH_CHECK();
+    }
     int err = 0;
     TP_CUDA(cudaMemcpyAsync(&err, m->errflag.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
     TP_CUDA(cudaStreamSynchronize(st));

@@ -76,6 +76,54 @@ template <> struct Acc<double> {
     __device__ __forceinline__ double value() const { return s; }
 };
 
+// ---- near-pair precision ---------------------------------------------------
+// FP32 barycenters are stored as hi (float4 .xyz) + lo (the rounding error,
+// a second float4). For a source tile whose bounding box lies within the
+// near distance of the block's targets, d is formed as (hi_S - hi_T) +
+// (lo_S - lo_T), which removes the rounding of the stored barycenters from
+// the small differences of near pairs; other tiles use hi_S - hi_T. The
+// choice is the same for every thread of the block.
+
+__device__ __forceinline__ void block_box(float lx, float ly, float lz, float hx, float hy, float hz,
+                                          float* sbox) {
+    __shared__ float wb[NT / 32][6];
+    for (int o = 16; o > 0; o >>= 1) {
+        lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+        ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+        lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+        hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+        hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+        hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
+    }
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        wb[w][0] = lx; wb[w][1] = ly; wb[w][2] = lz;
+        wb[w][3] = hx; wb[w][4] = hy; wb[w][5] = hz;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < 3; ++c) {
+            float l = wb[0][c], h = wb[0][3 + c];
+            for (int i = 1; i < NT / 32; ++i) {
+                l = fminf(l, wb[i][c]);
+                h = fmaxf(h, wb[i][3 + c]);
+            }
+            sbox[c] = l;
+            sbox[3 + c] = h;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ bool tile_near(const float4* __restrict__ tbox, int tile, const float* sbox,
+                                          float thr2) {
+    float4 lo = tbox[2 * tile], hi = tbox[2 * tile + 1];
+    float gx = fmaxf(fmaxf(lo.x - sbox[3], sbox[0] - hi.x), 0.f);
+    float gy = fmaxf(fmaxf(lo.y - sbox[4], sbox[1] - hi.y), 0.f);
+    float gz = fmaxf(fmaxf(lo.z - sbox[5], sbox[2] - hi.z), 0.f);
+    return gx * gx + gy * gy + gz * gz < thr2;
+}
+
 // ---- launch geometry ------------------------------------------------------
 
 struct Grid {
@@ -100,54 +148,93 @@ static Grid make_grid(int nt, int nf, int tt) {
 // energy rows, Eq. 10: sum_{T != S} K(S,T) a_T  (times a_S in the combine)
 // ===========================================================================
 
+template <typename T, bool P6>
+__device__ __forceinline__ T energy_term(T dx, T dy, T dz, T nx, T ny, T nz, T halfp) {
+    T r2 = dx * dx + dy * dy + dz * dz;
+    T u = nx * dx + ny * dy + nz * dz;
+    T ir2 = rcp_(fmax(r2, tiny_r2<T>()));
+    T qq = u * u * (ir2 * ir2);  // (N.d)^2 / |d|^4
+    return P6 ? qq * qq * qq : pow_(qq, halfp);
+}
+
 template <typename T, bool P6, int TT>
 __global__ void __launch_bounds__(NT)
 k_energy(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::type* __restrict__ fb,
+         const float4* __restrict__ flo, const float4* __restrict__ tbox, const double* __restrict__ center,
          int nf, const int* __restrict__ tlist, int nt, int tiles_per_split, T halfp,
          double* __restrict__ part) {
     using V4 = typename V4T<T>::type;
+    constexpr bool F32 = sizeof(T) == 4;
     __shared__ V4 sh[NT];
+    __shared__ float4 shl[F32 ? NT : 1];
+    __shared__ float sbox[6];
     T tx[TT], ty[TT], tz[TT], nx[TT], ny[TT], nz[TT];
+    float lx[TT], ly[TT], lz[TT];
     int tid[TT];
+    float bl[3] = {3e38f, 3e38f, 3e38f}, bh[3] = {-3e38f, -3e38f, -3e38f};
 #pragma unroll
     for (int j = 0; j < TT; ++j) {
         int t = blockIdx.x * NT * TT + j * NT + threadIdx.x;
         tid[j] = t;
+        lx[j] = ly[j] = lz[j] = 0.f;
         if (t < nt) {
             int S = tlist ? tlist[t] : t;
             V4 A = fa[S], B = fb[S];
             tx[j] = A.x; ty[j] = A.y; tz[j] = A.z;
             nx[j] = B.x; ny[j] = B.y; nz[j] = B.z;
+            if (F32) {
+                float4 L = flo[S];
+                lx[j] = L.x; ly[j] = L.y; lz[j] = L.z;
+                bl[0] = fminf(bl[0], (float)A.x); bl[1] = fminf(bl[1], (float)A.y); bl[2] = fminf(bl[2], (float)A.z);
+                bh[0] = fmaxf(bh[0], (float)A.x); bh[1] = fmaxf(bh[1], (float)A.y); bh[2] = fmaxf(bh[2], (float)A.z);
+            }
         } else {  // idle slot: zero normal gives zero terms
             tx[j] = ty[j] = tz[j] = T(0);
             nx[j] = ny[j] = nz[j] = T(0);
         }
+    }
+    float thr2 = 0.f;
+    if (F32) {
+        block_box(bl[0], bl[1], bl[2], bh[0], bh[1], bh[2], sbox);
+        thr2 = (float)center[3];
     }
     Acc<T> acc[TT];
     const int ntiles = (nf + NT - 1) / NT;
     const int k0 = blockIdx.y * tiles_per_split;
     const int k1 = min(k0 + tiles_per_split, ntiles);
     for (int tile = k0; tile < k1; ++tile) {
+        const bool near = F32 && tile_near(tbox, tile, sbox, thr2);
         int src = tile * NT + threadIdx.x;
         __syncthreads();
         sh[threadIdx.x] = src < nf ? fa[src] : v4zero<T>();  // zero area pads the tail
+        if (near) shl[threadIdx.x] = src < nf ? flo[src] : make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
         for (int c = 0; c < NT; c += CH) {
             T pt[TT];
 #pragma unroll
             for (int j = 0; j < TT; ++j) pt[j] = T(0);
-#pragma unroll 8
-            for (int q = 0; q < CH; ++q) {
-                V4 s = sh[c + q];
+            if (near) {
+#pragma unroll 4
+                for (int q = 0; q < CH; ++q) {
+                    V4 s = sh[c + q];
+                    float4 l = shl[c + q];
 #pragma unroll
-                for (int j = 0; j < TT; ++j) {
-                    T dx = tx[j] - s.x, dy = ty[j] - s.y, dz = tz[j] - s.z;
-                    T r2 = dx * dx + dy * dy + dz * dz;
-                    T u = nx[j] * dx + ny[j] * dy + nz[j] * dz;
-                    T ir2 = rcp_(fmax(r2, tiny_r2<T>()));
-                    T qq = u * u * (ir2 * ir2);      // (N.d)^2 / |d|^4
-                    T K = P6 ? qq * qq * qq : pow_(qq, halfp);
-                    pt[j] = fma(K, s.w, pt[j]);
+                    for (int j = 0; j < TT; ++j) {
+                        T dx = (tx[j] - s.x) + (T)(lx[j] - l.x);
+                        T dy = (ty[j] - s.y) + (T)(ly[j] - l.y);
+                        T dz = (tz[j] - s.z) + (T)(lz[j] - l.z);
+                        pt[j] = fma(energy_term<T, P6>(dx, dy, dz, nx[j], ny[j], nz[j], halfp), s.w, pt[j]);
+                    }
+                }
+            } else {
+#pragma unroll 8
+                for (int q = 0; q < CH; ++q) {
+                    V4 s = sh[c + q];
+#pragma unroll
+                    for (int j = 0; j < TT; ++j)
+                        pt[j] = fma(energy_term<T, P6>(tx[j] - s.x, ty[j] - s.y, tz[j] - s.z, nx[j], ny[j],
+                                                       nz[j], halfp),
+                                    s.w, pt[j]);
                 }
             }
 #pragma unroll
@@ -185,11 +272,13 @@ static int launch_energy(tp_mesh* m, const tp_params* p, const int32_t* tl, int 
     {
         ProfScope ps(m, PK_ENERGY, units, st);
         if (p->p == 6.0)
-            k_energy<T, true, TT><<<grid, NT, 0, st>>>(fa, fb, m->nf, tl, nt, g.tiles_per_split,
-                                                       T(3), m->part.as<double>());
+            k_energy<T, true, TT><<<grid, NT, 0, st>>>(fa, fb, m->f32c.as<float4>(), m->tilebox.as<float4>(),
+                                                       m->center.as<double>(), m->nf, tl, nt,
+                                                       g.tiles_per_split, T(3), m->part.as<double>());
         else
-            k_energy<T, false, TT><<<grid, NT, 0, st>>>(fa, fb, m->nf, tl, nt, g.tiles_per_split,
-                                                        T(0.5 * p->p), m->part.as<double>());
+            k_energy<T, false, TT><<<grid, NT, 0, st>>>(fa, fb, m->f32c.as<float4>(), m->tilebox.as<float4>(),
+                                                        m->center.as<double>(), m->nf, tl, nt,
+                                                        g.tiles_per_split, T(0.5 * p->p), m->part.as<double>());
         TP_LAUNCH_CHECK();
     }
     k_energy_combine<<<(nt + 255) / 256, 256, 0, st>>>(m->part.as<double>(), g.nsplit, nt, tl,
@@ -218,38 +307,89 @@ int energy_rows_direct(tp_mesh* m, const tp_params* p, const int32_t* tl, int nt
 
 constexpr int NADJ = 12;
 
+template <typename T, bool P6>
+__device__ __forceinline__ void diff_term(T dx, T dy, T dz, T nx, T ny, T nz, T at, T mx, T my, T mz, T hm1,
+                                          T* pt) {
+    T r2 = dx * dx + dy * dy + dz * dz;
+    T uS = nx * dx + ny * dy + nz * dz;
+    T uT = mx * dx + my * dy + mz * dz;
+    T ir2 = rcp_(fmax(r2, tiny_r2<T>()));
+    T ir4 = ir2 * ir2;
+    T qS = uS * uS * ir4, qT = uT * uT * ir4;
+    T mS = P6 ? qS * qS : pow_(qS, hm1);
+    T mT = P6 ? qT * qT : pow_(qT, hm1);
+    T KS = mS * qS, KT = mT * qT;
+    T w = at * (mS * uS * ir4);
+    T v = at * (mT * uT * ir4);
+    T kS = at * KS;
+    T ks = fma(at, KT, kS);
+    T kd = ks * ir2;
+    pt[0] += w;
+    pt[1] = fma(w, dx, pt[1]);
+    pt[2] = fma(w, dy, pt[2]);
+    pt[3] = fma(w, dz, pt[3]);
+    pt[4] = fma(v, mx, pt[4]);
+    pt[5] = fma(v, my, pt[5]);
+    pt[6] = fma(v, mz, pt[6]);
+    pt[7] = fma(kd, dx, pt[7]);
+    pt[8] = fma(kd, dy, pt[8]);
+    pt[9] = fma(kd, dz, pt[9]);
+    pt[10] += ks;
+    pt[11] += kS;
+}
+
 template <typename T, bool P6, int TT>
 __global__ void __launch_bounds__(NT)
 k_diff(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::type* __restrict__ fb,
+       const float4* __restrict__ flo, const float4* __restrict__ tbox, const double* __restrict__ center,
        int nf, int tiles_per_split, T hm1, double* __restrict__ part) {
     using V4 = typename V4T<T>::type;
+    constexpr bool F32 = sizeof(T) == 4;
     __shared__ V4 sa[NT];
     __shared__ V4 sb[NT];
+    __shared__ float4 shl[F32 ? NT : 1];
+    __shared__ float sbox[6];
     const int nt = nf;
     T tx[TT], ty[TT], tz[TT], nx[TT], ny[TT], nz[TT];
+    float lx[TT], ly[TT], lz[TT];
     int tid[TT];
+    float bl[3] = {3e38f, 3e38f, 3e38f}, bh[3] = {-3e38f, -3e38f, -3e38f};
 #pragma unroll
     for (int j = 0; j < TT; ++j) {
         int t = blockIdx.x * NT * TT + j * NT + threadIdx.x;
         tid[j] = t;
+        lx[j] = ly[j] = lz[j] = 0.f;
         if (t < nt) {
             V4 A = fa[t], B = fb[t];
             tx[j] = A.x; ty[j] = A.y; tz[j] = A.z;
             nx[j] = B.x; ny[j] = B.y; nz[j] = B.z;
+            if (F32) {
+                float4 L = flo[t];
+                lx[j] = L.x; ly[j] = L.y; lz[j] = L.z;
+                bl[0] = fminf(bl[0], (float)A.x); bl[1] = fminf(bl[1], (float)A.y); bl[2] = fminf(bl[2], (float)A.z);
+                bh[0] = fmaxf(bh[0], (float)A.x); bh[1] = fmaxf(bh[1], (float)A.y); bh[2] = fmaxf(bh[2], (float)A.z);
+            }
         } else {
             tx[j] = ty[j] = tz[j] = T(0);
             nx[j] = ny[j] = nz[j] = T(0);
         }
+    }
+    float thr2 = 0.f;
+    if (F32) {
+        block_box(bl[0], bl[1], bl[2], bh[0], bh[1], bh[2], sbox);
+        thr2 = (float)center[3];
     }
     Acc<T> acc[TT][NADJ];
     const int ntiles = (nf + NT - 1) / NT;
     const int k0 = blockIdx.y * tiles_per_split;
     const int k1 = min(k0 + tiles_per_split, ntiles);
     for (int tile = k0; tile < k1; ++tile) {
+        const bool near = F32 && tile_near(tbox, tile, sbox, thr2);
         int src = tile * NT + threadIdx.x;
         __syncthreads();
         sa[threadIdx.x] = src < nf ? fa[src] : v4zero<T>();
         sb[threadIdx.x] = src < nf ? fb[src] : v4zero<T>();
+        if (near) shl[threadIdx.x] = src < nf ? flo[src] : make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
         for (int c = 0; c < NT; c += CH) {
             T pt[TT][NADJ];
@@ -257,40 +397,27 @@ k_diff(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::type
             for (int j = 0; j < TT; ++j)
 #pragma unroll
                 for (int i = 0; i < NADJ; ++i) pt[j][i] = T(0);
-#pragma unroll 4
-            for (int q = 0; q < CH; ++q) {
-                V4 s = sa[c + q];
-                V4 n = sb[c + q];
+            if (near) {
+#pragma unroll 2
+                for (int q = 0; q < CH; ++q) {
+                    V4 s = sa[c + q];
+                    V4 n = sb[c + q];
+                    float4 l = shl[c + q];
 #pragma unroll
-                for (int j = 0; j < TT; ++j) {
-                    T dx = tx[j] - s.x, dy = ty[j] - s.y, dz = tz[j] - s.z;
-                    T r2 = dx * dx + dy * dy + dz * dz;
-                    T uS = nx[j] * dx + ny[j] * dy + nz[j] * dz;
-                    T uT = n.x * dx + n.y * dy + n.z * dz;
-                    T ir2 = rcp_(fmax(r2, tiny_r2<T>()));
-                    T ir4 = ir2 * ir2;
-                    T qS = uS * uS * ir4, qT = uT * uT * ir4;
-                    T mS = P6 ? qS * qS : pow_(qS, hm1);
-                    T mT = P6 ? qT * qT : pow_(qT, hm1);
-                    T KS = mS * qS, KT = mT * qT;
-                    T at = s.w;
-                    T w = at * (mS * uS * ir4);
-                    T v = at * (mT * uT * ir4);
-                    T kS = at * KS;
-                    T ks = fma(at, KT, kS);
-                    T kd = ks * ir2;
-                    pt[j][0] += w;
-                    pt[j][1] = fma(w, dx, pt[j][1]);
-                    pt[j][2] = fma(w, dy, pt[j][2]);
-                    pt[j][3] = fma(w, dz, pt[j][3]);
-                    pt[j][4] = fma(v, n.x, pt[j][4]);
-                    pt[j][5] = fma(v, n.y, pt[j][5]);
-                    pt[j][6] = fma(v, n.z, pt[j][6]);
-                    pt[j][7] = fma(kd, dx, pt[j][7]);
-                    pt[j][8] = fma(kd, dy, pt[j][8]);
-                    pt[j][9] = fma(kd, dz, pt[j][9]);
-                    pt[j][10] += ks;
-                    pt[j][11] += kS;
+                    for (int j = 0; j < TT; ++j)
+                        diff_term<T, P6>((tx[j] - s.x) + (T)(lx[j] - l.x), (ty[j] - s.y) + (T)(ly[j] - l.y),
+                                         (tz[j] - s.z) + (T)(lz[j] - l.z), nx[j], ny[j], nz[j], s.w, n.x, n.y,
+                                         n.z, hm1, pt[j]);
+                }
+            } else {
+#pragma unroll 4
+                for (int q = 0; q < CH; ++q) {
+                    V4 s = sa[c + q];
+                    V4 n = sb[c + q];
+#pragma unroll
+                    for (int j = 0; j < TT; ++j)
+                        diff_term<T, P6>(tx[j] - s.x, ty[j] - s.y, tz[j] - s.z, nx[j], ny[j], nz[j], s.w, n.x,
+                                         n.y, n.z, hm1, pt[j]);
                 }
             }
 #pragma unroll
@@ -342,10 +469,12 @@ static int launch_diff(tp_mesh* m, const tp_params* p, double* adj, double* erow
     {
         ProfScope ps(m, PK_DIFF, units, st);
         if (p->p == 6.0)
-            k_diff<T, true, TT><<<grid, NT, 0, st>>>(fa, fb, m->nf, g.tiles_per_split, T(2),
+            k_diff<T, true, TT><<<grid, NT, 0, st>>>(fa, fb, m->f32c.as<float4>(), m->tilebox.as<float4>(),
+                                                     m->center.as<double>(), m->nf, g.tiles_per_split, T(2),
                                                      m->part.as<double>());
         else
-            k_diff<T, false, TT><<<grid, NT, 0, st>>>(fa, fb, m->nf, g.tiles_per_split,
+            k_diff<T, false, TT><<<grid, NT, 0, st>>>(fa, fb, m->f32c.as<float4>(), m->tilebox.as<float4>(),
+                                                      m->center.as<double>(), m->nf, g.tiles_per_split,
                                                       T(0.5 * p->p - 1.0), m->part.as<double>());
         TP_LAUNCH_CHECK();
     }
@@ -457,19 +586,59 @@ __global__ void k_face_W(const double* __restrict__ v, int k, int col0, const in
 }
 
 template <typename T, int OP>
+__device__ __forceinline__ void apply_term(T dx, T dy, T dz, T nx, T ny, T nz, T at, T mx, T my, T mz,
+                                           const T* wv, T s_exp, T l_exp, T* pt) {
+    constexpr bool LOW = (OP == TP_OP_A || OP == TP_OP_B0);
+    constexpr bool HIGH = (OP == TP_OP_A || OP == TP_OP_B);
+    T r2 = dx * dx + dy * dy + dz * dz;
+    bool valid = r2 > T(0);
+    T r2c = fmax(r2, tiny_r2<T>());
+    if (OP == TP_OP_L) {
+        T h = valid ? pow_(r2c, -l_exp) : T(0);
+        pt[0] = fma(h, at, pt[0]);
+#pragma unroll
+        for (int i = 0; i < 3; ++i) pt[1 + i] = fma(h, wv[i], pt[1 + i]);
+    } else {
+        T hB = valid ? pow_(r2c, -s_exp) : T(0);
+        int o = 0;
+        if (HIGH) {
+            pt[0] = fma(hB, at, pt[0]);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) pt[1 + i] = fma(hB, wv[i], pt[1 + i]);
+            o = 10;
+        }
+        if (LOW) {
+            T uS = nx * dx + ny * dy + nz * dz;
+            T uT = mx * dx + my * dy + mz * dz;
+            T ir2 = rcp_(r2c);
+            T h0 = T(0.5) * (uS * uS + uT * uT) * (ir2 * ir2) * hB;
+            const int wo = HIGH ? 9 : 0;
+            pt[o] = fma(h0, at, pt[o]);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) pt[o + 1 + i] = fma(h0, wv[wo + i], pt[o + 1 + i]);
+        }
+    }
+}
+
+template <typename T, int OP>
 __global__ void __launch_bounds__(NT)
 k_apply(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::type* __restrict__ fb,
+        const float4* __restrict__ flo, const float4* __restrict__ tbox, const double* __restrict__ center,
         const typename V4T<T>::type* __restrict__ Wp, int nf, int tiles_per_split, T s_exp,
         T l_exp, double* __restrict__ part) {
     using V4 = typename V4T<T>::type;
     using L = OpLayout<OP>;
     constexpr bool LOW = (OP == TP_OP_A || OP == TP_OP_B0);
-    constexpr bool HIGH = (OP == TP_OP_A || OP == TP_OP_B);
+    constexpr bool F32 = sizeof(T) == 4;
     __shared__ V4 sa[NT];
     __shared__ V4 sb[LOW ? NT : 1];
     __shared__ V4 sw[NT * L::NW4];
+    __shared__ float4 shl[F32 ? NT : 1];
+    __shared__ float sbox[6];
     const int t = blockIdx.x * NT + threadIdx.x;
     T tx = 0, ty = 0, tz = 0, nx = 0, ny = 0, nz = 0;
+    float lx = 0.f, ly = 0.f, lz = 0.f;
+    float bl[3] = {3e38f, 3e38f, 3e38f}, bh[3] = {-3e38f, -3e38f, -3e38f};
     if (t < nf) {
         V4 A = fa[t];
         tx = A.x; ty = A.y; tz = A.z;
@@ -477,16 +646,28 @@ k_apply(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::typ
             V4 B = fb[t];
             nx = B.x; ny = B.y; nz = B.z;
         }
+        if (F32) {
+            float4 Lo = flo[t];
+            lx = Lo.x; ly = Lo.y; lz = Lo.z;
+            bl[0] = bh[0] = (float)A.x; bl[1] = bh[1] = (float)A.y; bl[2] = bh[2] = (float)A.z;
+        }
+    }
+    float thr2 = 0.f;
+    if (F32) {
+        block_box(bl[0], bl[1], bl[2], bh[0], bh[1], bh[2], sbox);
+        thr2 = (float)center[3];
     }
     Acc<T> acc[L::NA];
     const int ntiles = (nf + NT - 1) / NT;
     const int k0 = blockIdx.y * tiles_per_split;
     const int k1 = min(k0 + tiles_per_split, ntiles);
     for (int tile = k0; tile < k1; ++tile) {
+        const bool near = F32 && tile_near(tbox, tile, sbox, thr2);
         int src = tile * NT + threadIdx.x;
         __syncthreads();
         sa[threadIdx.x] = src < nf ? fa[src] : v4zero<T>();
         if (LOW) sb[threadIdx.x] = src < nf ? fb[src] : v4zero<T>();
+        if (near) shl[threadIdx.x] = src < nf ? flo[src] : make_float4(0.f, 0.f, 0.f, 0.f);
         for (int i = threadIdx.x; i < NT * L::NW4; i += NT) {
             int f = tile * NT + i / L::NW4;
             sw[i] = f < nf ? Wp[(size_t)tile * NT * L::NW4 + i] : v4zero<T>();
@@ -501,41 +682,24 @@ k_apply(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::typ
                 const int j = c + q;
                 V4 s = sa[j];
                 T dx = tx - s.x, dy = ty - s.y, dz = tz - s.z;
-                T r2 = dx * dx + dy * dy + dz * dz;
-                bool valid = r2 > T(0);
-                T r2c = fmax(r2, tiny_r2<T>());
+                if (near) {
+                    float4 l = shl[j];
+                    dx += (T)(lx - l.x);
+                    dy += (T)(ly - l.y);
+                    dz += (T)(lz - l.z);
+                }
                 T wv[4 * L::NW4];
 #pragma unroll
                 for (int i = 0; i < L::NW4; ++i) {
                     V4 x = sw[j * L::NW4 + i];
                     wv[4 * i] = x.x; wv[4 * i + 1] = x.y; wv[4 * i + 2] = x.z; wv[4 * i + 3] = x.w;
                 }
-                if (OP == TP_OP_L) {
-                    T h = valid ? pow_(r2c, -l_exp) : T(0);
-                    pt[0] = fma(h, s.w, pt[0]);
-#pragma unroll
-                    for (int i = 0; i < 3; ++i) pt[1 + i] = fma(h, wv[i], pt[1 + i]);
-                } else {
-                    T hB = valid ? pow_(r2c, -s_exp) : T(0);
-                    int o = 0;
-                    if (HIGH) {
-                        pt[0] = fma(hB, s.w, pt[0]);
-#pragma unroll
-                        for (int i = 0; i < 9; ++i) pt[1 + i] = fma(hB, wv[i], pt[1 + i]);
-                        o = 10;
-                    }
-                    if (LOW) {
-                        V4 n = sb[j];
-                        T uS = nx * dx + ny * dy + nz * dz;
-                        T uT = n.x * dx + n.y * dy + n.z * dz;
-                        T ir2 = rcp_(r2c);
-                        T h0 = T(0.5) * (uS * uS + uT * uT) * (ir2 * ir2) * hB;
-                        const int wo = HIGH ? 9 : 0;
-                        pt[o] = fma(h0, s.w, pt[o]);
-#pragma unroll
-                        for (int i = 0; i < 3; ++i) pt[o + 1 + i] = fma(h0, wv[wo + i], pt[o + 1 + i]);
-                    }
+                T mx = 0, my = 0, mz = 0;
+                if (LOW) {
+                    V4 n = sb[j];
+                    mx = n.x; my = n.y; mz = n.z;
                 }
+                apply_term<T, OP>(dx, dy, dz, nx, ny, nz, s.w, mx, my, mz, wv, s_exp, l_exp, pt);
             }
 #pragma unroll
             for (int i = 0; i < L::NA; ++i) acc[i].add(pt[i]);
@@ -608,8 +772,9 @@ static int launch_apply_op(tp_mesh* m, const tp_params* p, const double* v, int 
             constexpr int key = OP == TP_OP_A ? PK_APPLY_A : OP == TP_OP_B ? PK_APPLY_B
                               : OP == TP_OP_B0 ? PK_APPLY_B0 : PK_APPLY_L;
             ProfScope ps(m, key, units, st);
-            k_apply<T, OP><<<grid, NT, 0, st>>>(fa, fb, m->wv32.as<V4>(), nf, g.tiles_per_split, T(s),
-                                                T(l_exp), m->part.as<double>());
+            k_apply<T, OP><<<grid, NT, 0, st>>>(fa, fb, m->f32c.as<float4>(), m->tilebox.as<float4>(),
+                                                m->center.as<double>(), m->wv32.as<V4>(), nf,
+                                                g.tiles_per_split, T(s), T(l_exp), m->part.as<double>());
         }
         TP_LAUNCH_CHECK();
         k_apply_combine<<<(nf + 255) / 256, 256, 0, st>>>(m->part.as<double>(), g.nsplit, nf, OP,

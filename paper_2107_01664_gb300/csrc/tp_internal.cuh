@@ -100,11 +100,13 @@ struct tp_mesh {
     tp::Buf vf_idx;     // int32 [3*nf]
     // positions
     tp::Buf pos;        // double [nv*3]
-    tp::Buf center;     // double [4]    reference frame of the FP32 face table
+    tp::Buf center;     // double [4]    reference frame of the FP32 face table; [3] = near-pair distance^2
     tp::Buf errflag;    // int [4]
     // face tables
     tp::Buf f32a;       // float4 [nf]   X - c, a
     tp::Buf f32b;       // float4 [nf]   N, 0
+    tp::Buf f32c;       // float4 [nf]   (X - c) - hi: the low parts of the FP32 barycenters
+    tp::Buf tilebox;    // float4 [2*ntiles] bounding box of the FP32 barycenters of each 128-face tile
     tp::Buf f64a;       // d4 [nf]       X - c, a
     tp::Buf f64b;       // d4 [nf]       N, 0
     tp::Buf fgrad;      // double [nf*9] gradients of the three hat functions
@@ -118,7 +120,7 @@ struct tp_mesh {
     std::vector<int> bvh_level_off;
     bool bvh_valid = false;
     tp::Buf bvh_node, bvh_perm, bvh_keys, bvh_tmp, bvh_sortws;
-    tp::Buf bvh_f32a, bvh_f32b;   // face tables permuted to Morton order
+    tp::Buf bvh_f32a, bvh_f32b, bvh_f32c;   // face tables (and low parts) permuted to Morton order
     tp::Buf bvh_nodeP;            // float [nodes*8] node-average projector (upper triangle) for B0
     // workspaces
     tp::Buf part, part2, scal, corner, wv64, wv32, tmpv[8];

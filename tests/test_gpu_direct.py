@@ -196,16 +196,16 @@ def test_precond_step_armijo_trajectory_matches_oracle(lib):
         E_ref.append((r["tau"], r["E0"], r["E1"]))
     c = lib.tp_constraints(flags=3, A0=A0, V0=V0)
     with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as m:
-        p = lib.params(precision=1, krylov_tol=1e-11, cg_tol=1e-12, proj_iters=3)
+        p = lib.params(precision=1, krylov_tol=1e-9, krylov_max=600, cg_tol=1e-12, proj_iters=3)
         for k in range(3):
             rep = lib.precond_step(m, c, p)
             assert rep["status"] == 0 and rep["slope"] < 0
             assert rep["tau"] == E_ref[k][0]
-            assert rel(rep["E_after"], E_ref[k][2]) < 1e-7
+            assert rel(rep["E_after"], E_ref[k][2]) < 1e-6
         f = m.get_positions()
-    assert rel(f - V, f_ref - V) < 1e-6
+    assert rel(f - V, f_ref - V) < 1e-5
     with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as m:
-        p = lib.params(cg_tol=1e-8, proj_iters=3)
+        p = lib.params(cg_tol=1e-8, krylov_max=600, proj_iters=3)
         for _ in range(3):
             rep = lib.precond_step(m, c, p)
             assert rep["status"] == 0 and rep["slope"] < 0 and rep["E_after"] < rep["E_before"]
