@@ -31,9 +31,20 @@ sys.path.insert(0, ROOT)
 WORKLOAD = "torus_20k"
 METRIC = "pair interactions/s"
 UNIT = "pairs/s"
-# algorithmic FP32 flops per pair interaction (FMA = 2, MUFU not counted)
-FLOPS_PER_PAIR = {"energy_direct": 20, "diff_direct": 57, "apply_A": 54, "apply_B": 29,
-                  "apply_B0": 34, "apply_L": 17, "bh_energy": 20, "bh_diff": 51}
+# algorithmic FP32 flops per pair interaction (FMA = 2, MUFU not counted);
+# operator applies: kernel evaluation + 2 per accumulator, KC columns per launch
+FLOPS_PER_PAIR = {"energy_direct": 20, "diff_direct": 57, "bh_energy": 20, "bh_diff": 51}
+APPLY_FLOPS = {"apply_A": lambda kc: 26 + 2 * (2 + 4 * kc), "apply_B": lambda kc: 9 + 2 * (1 + 3 * kc),
+               "apply_B0": lambda kc: 26 + 2 * (1 + kc), "apply_L": lambda kc: 9 + 2 * (1 + kc)}
+
+
+def flops_per_pair(name, stat):
+    if name in FLOPS_PER_PAIR:
+        return FLOPS_PER_PAIR[name]
+    if name in APPLY_FLOPS:
+        kc = stat.get("columns", 0.0) / max(1, stat["launches"]) or 3.0
+        return APPLY_FLOPS[name](kc)
+    return None
 KERNEL_SOURCE = {"energy_direct": "pairs.cu", "diff_direct": "pairs.cu", "apply_A": "pairs.cu",
                  "apply_B": "pairs.cu", "apply_B0": "pairs.cu", "apply_L": "pairs.cu",
                  "bh_energy": "bvh.cu", "bh_diff": "bvh.cu", "cg": "cg.cu", "bvh_build": "bvh.cu"}
@@ -256,7 +267,7 @@ def gpu_arm(args):
     prof = tp.tp_profile_read(mesh)
     tp.tp_profile_enable(mesh, False)
 
-    pair_kernels = [k for k in prof if k in FLOPS_PER_PAIR]
+    pair_kernels = [k for k in prof if k in FLOPS_PER_PAIR or k in APPLY_FLOPS]
     pairs_total = sum(prof[k]["units"] for k in pair_kernels)
     dev_ms = float(sum(step_ms))
     # whole-job aggregate over ranks: max time, summed work
@@ -299,10 +310,10 @@ def gpu_arm(args):
     if dom is not None:
         d = prof[dom]
         per_launch_ms = d["ms"] / max(1, d["launches"])
-        if dom in FLOPS_PER_PAIR:
+        if flops_per_pair(dom, d) is not None:
             clock_mhz = float(peaks.get("sm_max_mhz", 2070.0))
             peak = sms * FP32_LANES_PER_SM * 2 * clock_mhz * 1e6 / 1e12
-            achieved = FLOPS_PER_PAIR[dom] * d["units"] / (d["ms"] / 1e3) / 1e12
+            achieved = flops_per_pair(dom, d) * d["units"] / (d["ms"] / 1e3) / 1e12
             roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                     "frac": achieved / peak,
                     "peak_basis": f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {clock_mhz:.0f} MHz"}
@@ -331,7 +342,10 @@ def gpu_arm(args):
         "pairs_per_step": pairs_per_step,
         "krylov_iters_per_step": sum(r["krylov_iters"] for r in reps) / len(reps),
         "cg_iters_per_step": sum(r["cg_iters"] for r in reps) / len(reps),
-        "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "units": v["units"]} for k, v in prof.items()},
+        "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "units": v["units"],
+                        "tflops": (flops_per_pair(k, v) * v["units"] / (v["ms"] / 1e3) / 1e12
+                                   if flops_per_pair(k, v) and v["ms"] > 0 else None)}
+                    for k, v in prof.items()},
         "wall_s": wall, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu:

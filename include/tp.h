@@ -117,6 +117,7 @@ typedef struct tp_kernel_stat {
     long long launches;
     double    ms;        /* summed CUDA-event durations (0 unless profiling is on) */
     double    units;
+    double    columns;   /* operator columns summed over the launches (apply kernels; else 0) */
 } tp_kernel_stat;
 
 typedef struct tp_mesh tp_mesh;

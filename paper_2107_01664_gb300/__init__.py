@@ -71,7 +71,7 @@ class tp_step_report(ctypes.Structure):
 
 class tp_kernel_stat(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_longlong), ("ms", ctypes.c_double),
-                ("units", ctypes.c_double)]
+                ("units", ctypes.c_double), ("columns", ctypes.c_double)]
 
 
 _lib = None
@@ -327,7 +327,8 @@ def tp_profile_read(mesh: Mesh) -> dict:
     buf = (tp_kernel_stat * 32)()
     n = ctypes.c_int()
     _check(lib().tp_profile_read(mesh.handle, buf, 32, ctypes.byref(n)))
-    return {buf[i].name.decode(): {"launches": buf[i].launches, "ms": buf[i].ms, "units": buf[i].units}
+    return {buf[i].name.decode(): {"launches": buf[i].launches, "ms": buf[i].ms, "units": buf[i].units,
+                                   "columns": buf[i].columns}
             for i in range(n.value)}
 
 

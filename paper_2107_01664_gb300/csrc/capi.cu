@@ -373,6 +373,7 @@ int tp_profile_read(tp_mesh* m, tp_kernel_stat* out, int max, int* n) {
         out[k].launches = P.launches[i];
         out[k].ms = P.ms[i];
         out[k].units = P.units[i];
+        out[k].columns = P.cols[i];
         ++k;
     }
     *n = k;
@@ -380,6 +381,7 @@ int tp_profile_read(tp_mesh* m, tp_kernel_stat* out, int max, int* n) {
         P.launches[i] = 0;
         P.ms[i] = 0.0;
         P.units[i] = 0.0;
+        P.cols[i] = 0.0;
     }
     return TP_OK;
 }

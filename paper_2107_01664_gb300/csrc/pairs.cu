@@ -57,6 +57,13 @@ template <typename T> __device__ __forceinline__ T tiny_r2();
 template <> __device__ __forceinline__ float tiny_r2<float>() { return 1e-18f; }
 template <> __device__ __forceinline__ double tiny_r2<double>() { return 1e-150; }
 
+// |d|^2 + tiny as one FMA chain: keeps 1/|d|^4 finite for the self pair
+// (d = 0, where every term below is 0 * finite = 0) without a separate clamp;
+// for real pairs the offset is below 1e-12 of |d|^2 at |d| > 1e-3
+template <typename T> __device__ __forceinline__ T r2_eps(T dx, T dy, T dz) {
+    return fma(dx, dx, fma(dy, dy, fma(dz, dz, tiny_r2<T>())));
+}
+
 // ---- compensated accumulators -------------------------------------------
 
 template <typename T> struct Acc;
@@ -150,10 +157,9 @@ static Grid make_grid(int nt, int nf, int tt) {
 
 template <typename T, bool P6>
 __device__ __forceinline__ T energy_term(T dx, T dy, T dz, T nx, T ny, T nz, T halfp) {
-    T r2 = dx * dx + dy * dy + dz * dz;
-    T u = nx * dx + ny * dy + nz * dz;
-    T ir2 = rcp_(fmax(r2, tiny_r2<T>()));
-    T qq = u * u * (ir2 * ir2);  // (N.d)^2 / |d|^4
+    T ir2 = rcp_(r2_eps(dx, dy, dz));
+    T t = (nx * dx + ny * dy + nz * dz) * ir2;  // N.d / |d|^2
+    T qq = t * t;                                 // (N.d)^2 / |d|^4
     return P6 ? qq * qq * qq : pow_(qq, halfp);
 }
 
@@ -261,7 +267,7 @@ template <typename T>
 static int launch_energy(tp_mesh* m, const tp_params* p, const int32_t* tl, int nt, double* rows,
                          cudaStream_t st) {
     using V4 = typename V4T<T>::type;
-    constexpr int TT = 2;
+    constexpr int TT = sizeof(T) == 4 ? 4 : 2;
     Grid g = make_grid(nt, m->nf, TT);
     TP_TRY(ensure(m->part, sizeof(double) * (size_t)g.nsplit * nt));
     const V4* fa = (const V4*)(sizeof(T) == 4 ? m->f32a.ptr : m->f64a.ptr);
@@ -310,17 +316,15 @@ constexpr int NADJ = 12;
 template <typename T, bool P6>
 __device__ __forceinline__ void diff_term(T dx, T dy, T dz, T nx, T ny, T nz, T at, T mx, T my, T mz, T hm1,
                                           T* pt) {
-    T r2 = dx * dx + dy * dy + dz * dz;
-    T uS = nx * dx + ny * dy + nz * dz;
-    T uT = mx * dx + my * dy + mz * dz;
-    T ir2 = rcp_(fmax(r2, tiny_r2<T>()));
-    T ir4 = ir2 * ir2;
-    T qS = uS * uS * ir4, qT = uT * uT * ir4;
+    T ir2 = rcp_(r2_eps(dx, dy, dz));
+    T tS = (nx * dx + ny * dy + nz * dz) * ir2;   // u_S / |d|^2
+    T tT = (mx * dx + my * dy + mz * dz) * ir2;   // u_T / |d|^2
+    T qS = tS * tS, qT = tT * tT;
     T mS = P6 ? qS * qS : pow_(qS, hm1);
     T mT = P6 ? qT * qT : pow_(qT, hm1);
     T KS = mS * qS, KT = mT * qT;
-    T w = at * (mS * uS * ir4);
-    T v = at * (mT * uT * ir4);
+    T w = (at * mS) * (tS * ir2);                 // a_T q_S^{p/2-1} u_S / |d|^4
+    T v = (at * mT) * (tT * ir2);
     T kS = at * KS;
     T ks = fma(at, KT, kS);
     T kd = ks * ir2;
@@ -458,7 +462,7 @@ __global__ void k_diff_combine(const double* __restrict__ part, int nsplit, int 
 template <typename T>
 static int launch_diff(tp_mesh* m, const tp_params* p, double* adj, double* erow, cudaStream_t st) {
     using V4 = typename V4T<T>::type;
-    constexpr int TT = 1;
+    constexpr int TT = sizeof(T) == 4 ? 2 : 1;
     Grid g = make_grid(m->nf, m->nf, TT);
     TP_TRY(ensure(m->part, sizeof(double) * (size_t)g.nsplit * NADJ * m->nf));
     const V4* fa = (const V4*)(sizeof(T) == 4 ? m->f32a.ptr : m->f64a.ptr);
@@ -534,24 +538,26 @@ int adjoints_to_dE(tp_mesh* m, const double* adj, double* dE, cudaStream_t st) {
 }
 
 // ===========================================================================
-// kernel-matrix products, §5.1.1-5.1.3 and Appendix A, 3 columns per pass
-//   B : W_V = diag(a) D v (3x3 per face), h = |d|^{-2s}
-//   B0: W_U = diag(a) avg v (3 per face), h = (k2(S;T)+k2(T;S)) / (2|d|^{2s})
-//   L : W_U,                               h = |d|^{-2(3-s)}   (sigma = 2 - s)
+// kernel-matrix products, §5.1.1-5.1.3 and Appendix A, KC = 3 or 9 columns
+// per pass
+//   B : W_V = diag(a) D v (3 x KC per face), h = |d|^{-2s}
+//   B0: W_U = diag(a) avg v (KC per face),   h = (k2(S;T)+k2(T;S)) / (2|d|^{2s})
+//   L : W_U,                                 h = |d|^{-2(3-s)}   (sigma = 2 - s)
 // per target: r = sum_T h a_T and (H W)_S = sum_T h W_T.
 // ===========================================================================
 
-constexpr int KC = 3;  // columns per pass
+template <int OP, int KC> struct OpLayout {
+    static constexpr bool HIGH = (OP == TP_OP_A || OP == TP_OP_B);
+    static constexpr bool USEU = (OP != TP_OP_B);
+    static constexpr int NW = (HIGH ? 3 * KC : 0) + (USEU ? KC : 0);   // W values per face
+    static constexpr int NW4 = (NW + 3) / 4;
+    static constexpr int NA = (HIGH ? 1 + 3 * KC : 0) + (USEU ? 1 + KC : 0);  // accumulators
+};
 
-template <int OP> struct OpLayout;
-template <> struct OpLayout<TP_OP_A> { static constexpr int NW = 12, NW4 = 3, NA = 14; };
-template <> struct OpLayout<TP_OP_B> { static constexpr int NW = 9, NW4 = 3, NA = 10; };
-template <> struct OpLayout<TP_OP_B0> { static constexpr int NW = 3, NW4 = 1, NA = 4; };
-template <> struct OpLayout<TP_OP_L> { static constexpr int NW = 3, NW4 = 1, NA = 4; };
-
-// per-face W (FP64 [nf][12]: W_V (q*3+c), then W_U (c)) and its padded copy
-// in the pair precision, for columns col0..col0+2 of v [nv][k]
-template <typename T>
+// per-face W (FP64 [nf][4*KC]: W_V at q*KC+c, then W_U at 3*KC+c) and its
+// padded copy in the pair precision and the operator's layout, for columns
+// col0 .. col0+KC-1 of v [nv][k] (missing columns are zero)
+template <typename T, int KC>
 __global__ void k_face_W(const double* __restrict__ v, int k, int col0, const int* __restrict__ faces,
                          int nf, const d4* __restrict__ f64a, const double* __restrict__ fgrad,
                          int op, double* __restrict__ W64, typename V4T<T>::type* __restrict__ Wp,
@@ -564,70 +570,70 @@ __global__ void k_face_W(const double* __restrict__ v, int k, int col0, const in
         int vi = faces[3 * S + cr];
         for (int c = 0; c < KC; ++c) val[cr][c] = (col0 + c < k) ? v[(size_t)vi * k + col0 + c] : 0.0;
     }
-    double w[12];
+    double w[4 * KC];
     for (int q = 0; q < 3; ++q)
         for (int c = 0; c < KC; ++c) {
             double g = 0.0;
             for (int cr = 0; cr < 3; ++cr) g += val[cr][c] * fgrad[9 * S + 3 * cr + q];
             w[q * KC + c] = a * g;
         }
-    for (int c = 0; c < KC; ++c) w[9 + c] = a * (val[0][c] + val[1][c] + val[2][c]) / 3.0;
-    for (int i = 0; i < 12; ++i) W64[12 * (size_t)S + i] = w[i];
-    // pair-precision copy in the operator's layout
-    T buf[12];
+    for (int c = 0; c < KC; ++c) w[3 * KC + c] = a * (val[0][c] + val[1][c] + val[2][c]) / 3.0;
+    for (int i = 0; i < 4 * KC; ++i) W64[4 * KC * (size_t)S + i] = w[i];
+    T* out = reinterpret_cast<T*>(Wp) + (size_t)S * 4 * nw4;
     int n = 0;
     if (op == TP_OP_A || op == TP_OP_B)
-        for (int i = 0; i < 9; ++i) buf[n++] = (T)w[i];
-    if (op == TP_OP_A || op == TP_OP_B0 || op == TP_OP_L)
-        for (int c = 0; c < 3; ++c) buf[n++] = (T)w[9 + c];
-    while (n < 4 * nw4) buf[n++] = T(0);
-    T* out = reinterpret_cast<T*>(Wp) + (size_t)S * 4 * nw4;
-    for (int i = 0; i < 4 * nw4; ++i) out[i] = buf[i];
+        for (int i = 0; i < 3 * KC; ++i) out[n++] = (T)w[i];
+    if (op != TP_OP_B)
+        for (int c = 0; c < KC; ++c) out[n++] = (T)w[3 * KC + c];
+    while (n < 4 * nw4) out[n++] = T(0);
 }
 
-template <typename T, int OP>
+// One (target, source) term of the kernel-matrix products. SELF = the tile
+// may contain the target itself (d = 0), whose term must be dropped: the
+// kernels of B and L^{2-s} do not vanish at d = 0 by themselves.
+template <typename T, int OP, bool SELF, int KC>
 __device__ __forceinline__ void apply_term(T dx, T dy, T dz, T nx, T ny, T nz, T at, T mx, T my, T mz,
                                            const T* wv, T s_exp, T l_exp, T* pt) {
     constexpr bool LOW = (OP == TP_OP_A || OP == TP_OP_B0);
     constexpr bool HIGH = (OP == TP_OP_A || OP == TP_OP_B);
-    T r2 = dx * dx + dy * dy + dz * dz;
-    bool valid = r2 > T(0);
-    T r2c = fmax(r2, tiny_r2<T>());
+    T r2 = r2_eps(dx, dy, dz);
     if (OP == TP_OP_L) {
-        T h = valid ? pow_(r2c, -l_exp) : T(0);
+        T h = pow_(r2, -l_exp);
+        if (SELF) h = r2 > T(2) * tiny_r2<T>() ? h : T(0);
         pt[0] = fma(h, at, pt[0]);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) pt[1 + i] = fma(h, wv[i], pt[1 + i]);
+        for (int i = 0; i < KC; ++i) pt[1 + i] = fma(h, wv[i], pt[1 + i]);
     } else {
-        T hB = valid ? pow_(r2c, -s_exp) : T(0);
+        T hB = pow_(r2, -s_exp);
+        if (SELF) hB = r2 > T(2) * tiny_r2<T>() ? hB : T(0);
         int o = 0;
         if (HIGH) {
             pt[0] = fma(hB, at, pt[0]);
 #pragma unroll
-            for (int i = 0; i < 9; ++i) pt[1 + i] = fma(hB, wv[i], pt[1 + i]);
-            o = 10;
+            for (int i = 0; i < 3 * KC; ++i) pt[1 + i] = fma(hB, wv[i], pt[1 + i]);
+            o = 1 + 3 * KC;
         }
         if (LOW) {
-            T uS = nx * dx + ny * dy + nz * dz;
-            T uT = mx * dx + my * dy + mz * dz;
-            T ir2 = rcp_(r2c);
-            T h0 = T(0.5) * (uS * uS + uT * uT) * (ir2 * ir2) * hB;
-            const int wo = HIGH ? 9 : 0;
+            T ir2 = rcp_(r2);
+            T tS = (nx * dx + ny * dy + nz * dz) * ir2;
+            T tT = (mx * dx + my * dy + mz * dz) * ir2;
+            T h0 = T(0.5) * fma(tS, tS, tT * tT) * hB;   // (k2(S;T) + k2(T;S)) / 2 * |d|^{-2s}
+            const int wo = HIGH ? 3 * KC : 0;
             pt[o] = fma(h0, at, pt[o]);
 #pragma unroll
-            for (int i = 0; i < 3; ++i) pt[o + 1 + i] = fma(h0, wv[wo + i], pt[o + 1 + i]);
+            for (int i = 0; i < KC; ++i) pt[o + 1 + i] = fma(h0, wv[wo + i], pt[o + 1 + i]);
         }
     }
 }
 
-template <typename T, int OP>
+template <typename T, int OP, int TT, int KC>
 __global__ void __launch_bounds__(NT)
 k_apply(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::type* __restrict__ fb,
         const float4* __restrict__ flo, const float4* __restrict__ tbox, const double* __restrict__ center,
         const typename V4T<T>::type* __restrict__ Wp, int nf, int tiles_per_split, T s_exp,
         T l_exp, double* __restrict__ part) {
     using V4 = typename V4T<T>::type;
-    using L = OpLayout<OP>;
+    using L = OpLayout<OP, KC>;
     constexpr bool LOW = (OP == TP_OP_A || OP == TP_OP_B0);
     constexpr bool F32 = sizeof(T) == 4;
     __shared__ V4 sa[NT];
@@ -635,21 +641,29 @@ k_apply(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::typ
     __shared__ V4 sw[NT * L::NW4];
     __shared__ float4 shl[F32 ? NT : 1];
     __shared__ float sbox[6];
-    const int t = blockIdx.x * NT + threadIdx.x;
-    T tx = 0, ty = 0, tz = 0, nx = 0, ny = 0, nz = 0;
-    float lx = 0.f, ly = 0.f, lz = 0.f;
+    T tx[TT], ty[TT], tz[TT], nx[TT], ny[TT], nz[TT];
+    float lx[TT], ly[TT], lz[TT];
+    int tid[TT];
     float bl[3] = {3e38f, 3e38f, 3e38f}, bh[3] = {-3e38f, -3e38f, -3e38f};
-    if (t < nf) {
-        V4 A = fa[t];
-        tx = A.x; ty = A.y; tz = A.z;
-        if (LOW) {
-            V4 B = fb[t];
-            nx = B.x; ny = B.y; nz = B.z;
-        }
-        if (F32) {
-            float4 Lo = flo[t];
-            lx = Lo.x; ly = Lo.y; lz = Lo.z;
-            bl[0] = bh[0] = (float)A.x; bl[1] = bh[1] = (float)A.y; bl[2] = bh[2] = (float)A.z;
+#pragma unroll
+    for (int j = 0; j < TT; ++j) {
+        const int t = blockIdx.x * NT * TT + j * NT + threadIdx.x;
+        tid[j] = t;
+        tx[j] = ty[j] = tz[j] = nx[j] = ny[j] = nz[j] = T(0);
+        lx[j] = ly[j] = lz[j] = 0.f;
+        if (t < nf) {
+            V4 A = fa[t];
+            tx[j] = A.x; ty[j] = A.y; tz[j] = A.z;
+            if (LOW) {
+                V4 B = fb[t];
+                nx[j] = B.x; ny[j] = B.y; nz[j] = B.z;
+            }
+            if (F32) {
+                float4 Lo = flo[t];
+                lx[j] = Lo.x; ly[j] = Lo.y; lz[j] = Lo.z;
+                bl[0] = fminf(bl[0], (float)A.x); bl[1] = fminf(bl[1], (float)A.y); bl[2] = fminf(bl[2], (float)A.z);
+                bh[0] = fmaxf(bh[0], (float)A.x); bh[1] = fmaxf(bh[1], (float)A.y); bh[2] = fmaxf(bh[2], (float)A.z);
+            }
         }
     }
     float thr2 = 0.f;
@@ -657,11 +671,14 @@ k_apply(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::typ
         block_box(bl[0], bl[1], bl[2], bh[0], bh[1], bh[2], sbox);
         thr2 = (float)center[3];
     }
-    Acc<T> acc[L::NA];
+    Acc<T> acc[TT][L::NA];
     const int ntiles = (nf + NT - 1) / NT;
     const int k0 = blockIdx.y * tiles_per_split;
     const int k1 = min(k0 + tiles_per_split, ntiles);
     for (int tile = k0; tile < k1; ++tile) {
+        // tiles holding this block's own targets (self pairs) or lying near them
+        // take the careful path: compensated differences and the self-pair test
+        const bool diag = tile >= (int)blockIdx.x * TT && tile < ((int)blockIdx.x + 1) * TT;
         const bool near = F32 && tile_near(tbox, tile, sbox, thr2);
         int src = tile * NT + threadIdx.x;
         __syncthreads();
@@ -674,68 +691,99 @@ k_apply(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::typ
         }
         __syncthreads();
         for (int c = 0; c < NT; c += CH) {
-            T pt[L::NA];
+            T pt[TT][L::NA];
 #pragma unroll
-            for (int i = 0; i < L::NA; ++i) pt[i] = T(0);
+            for (int j = 0; j < TT; ++j)
+#pragma unroll
+                for (int i = 0; i < L::NA; ++i) pt[j][i] = T(0);
+            if (near || diag) {
+                for (int q = 0; q < CH; ++q) {
+                    const int jj = c + q;
+                    V4 s = sa[jj];
+                    float4 l = near ? shl[jj] : make_float4(0.f, 0.f, 0.f, 0.f);
+                    T wv[4 * L::NW4];
+#pragma unroll
+                    for (int i = 0; i < L::NW4; ++i) {
+                        V4 x = sw[jj * L::NW4 + i];
+                        wv[4 * i] = x.x; wv[4 * i + 1] = x.y; wv[4 * i + 2] = x.z; wv[4 * i + 3] = x.w;
+                    }
+                    T mx = 0, my = 0, mz = 0;
+                    if (LOW) {
+                        V4 n = sb[jj];
+                        mx = n.x; my = n.y; mz = n.z;
+                    }
+#pragma unroll
+                    for (int j = 0; j < TT; ++j)
+                        apply_term<T, OP, true, KC>((tx[j] - s.x) + (T)(lx[j] - l.x), (ty[j] - s.y) + (T)(ly[j] - l.y),
+                                                    (tz[j] - s.z) + (T)(lz[j] - l.z), nx[j], ny[j], nz[j], s.w, mx,
+                                                    my, mz, wv, s_exp, l_exp, pt[j]);
+                }
+            } else {
 #pragma unroll 2
-            for (int q = 0; q < CH; ++q) {
-                const int j = c + q;
-                V4 s = sa[j];
-                T dx = tx - s.x, dy = ty - s.y, dz = tz - s.z;
-                if (near) {
-                    float4 l = shl[j];
-                    dx += (T)(lx - l.x);
-                    dy += (T)(ly - l.y);
-                    dz += (T)(lz - l.z);
-                }
-                T wv[4 * L::NW4];
+                for (int q = 0; q < CH; ++q) {
+                    const int jj = c + q;
+                    V4 s = sa[jj];
+                    T wv[4 * L::NW4];
 #pragma unroll
-                for (int i = 0; i < L::NW4; ++i) {
-                    V4 x = sw[j * L::NW4 + i];
-                    wv[4 * i] = x.x; wv[4 * i + 1] = x.y; wv[4 * i + 2] = x.z; wv[4 * i + 3] = x.w;
+                    for (int i = 0; i < L::NW4; ++i) {
+                        V4 x = sw[jj * L::NW4 + i];
+                        wv[4 * i] = x.x; wv[4 * i + 1] = x.y; wv[4 * i + 2] = x.z; wv[4 * i + 3] = x.w;
+                    }
+                    T mx = 0, my = 0, mz = 0;
+                    if (LOW) {
+                        V4 n = sb[jj];
+                        mx = n.x; my = n.y; mz = n.z;
+                    }
+#pragma unroll
+                    for (int j = 0; j < TT; ++j)
+                        apply_term<T, OP, false, KC>(tx[j] - s.x, ty[j] - s.y, tz[j] - s.z, nx[j], ny[j], nz[j],
+                                                     s.w, mx, my, mz, wv, s_exp, l_exp, pt[j]);
                 }
-                T mx = 0, my = 0, mz = 0;
-                if (LOW) {
-                    V4 n = sb[j];
-                    mx = n.x; my = n.y; mz = n.z;
-                }
-                apply_term<T, OP>(dx, dy, dz, nx, ny, nz, s.w, mx, my, mz, wv, s_exp, l_exp, pt);
             }
 #pragma unroll
-            for (int i = 0; i < L::NA; ++i) acc[i].add(pt[i]);
+            for (int j = 0; j < TT; ++j)
+#pragma unroll
+                for (int i = 0; i < L::NA; ++i) acc[j][i].add(pt[j][i]);
         }
     }
-    if (t < nf)
 #pragma unroll
-        for (int i = 0; i < L::NA; ++i) part[((size_t)blockIdx.y * L::NA + i) * nf + t] = acc[i].value();
+    for (int j = 0; j < TT; ++j)
+        if (tid[j] < nf)
+#pragma unroll
+            for (int i = 0; i < L::NA; ++i)
+                part[((size_t)blockIdx.y * L::NA + i) * nf + tid[j]] = acc[j][i].value();
 }
 
 // per face: z = (r/a) W_S - (H W)_S in FP64, then the corner values of the
 // transposed map: 2 a_S grad phi_c . zV (B) and 2 a_S zU / 3 (B0, L)
-__global__ void k_apply_combine(const double* __restrict__ part, int nsplit, int nf, int op, int na,
+template <int OP, int KC>
+__global__ void k_apply_combine(const double* __restrict__ part, int nsplit, int nf,
                                 const d4* __restrict__ f64a, const double* __restrict__ fgrad,
                                 const double* __restrict__ W64, int k, int col0,
                                 double* __restrict__ corner) {
+    using L = OpLayout<OP, KC>;
     int S = blockIdx.x * blockDim.x + threadIdx.x;
     if (S >= nf) return;
-    double s[14];
-    for (int i = 0; i < na; ++i) {
+    double s[L::NA];
+    for (int i = 0; i < L::NA; ++i) {
         double x = 0.0;
-        for (int sp = 0; sp < nsplit; ++sp) x += part[((size_t)sp * na + i) * nf + S];
+        for (int sp = 0; sp < nsplit; ++sp) x += part[((size_t)sp * L::NA + i) * nf + S];
         s[i] = x;
     }
     double a = f64a[S].w;
-    const double* W = W64 + 12 * (size_t)S;
-    double zV[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, zU[3] = {0, 0, 0};
+    const double* W = W64 + 4 * KC * (size_t)S;
+    double zV[3 * KC], zU[KC];
+    for (int i = 0; i < 3 * KC; ++i) zV[i] = 0.0;
+    for (int i = 0; i < KC; ++i) zU[i] = 0.0;
     int o = 0;
-    if (op == TP_OP_A || op == TP_OP_B) {
+    if (L::HIGH) {
         double r = s[0] / a;
-        for (int i = 0; i < 9; ++i) zV[i] = r * W[i] - s[1 + i];
-        o = 10;
+        for (int i = 0; i < 3 * KC; ++i) zV[i] = r * W[i] - s[1 + i];
+        o = 1 + 3 * KC;
     }
-    if (op != TP_OP_B) {
+    if (L::USEU) {
         double r = s[o] / a;
-        for (int c = 0; c < 3; ++c) zU[c] = r * W[9 + c] - s[o + 1 + c];
+        for (int c = 0; c < KC; ++c) zU[c] = r * W[3 * KC + c] - s[o + 1 + c];
     }
     for (int cr = 0; cr < 3; ++cr)
         for (int c = 0; c < KC && col0 + c < k; ++c) {
@@ -745,25 +793,26 @@ __global__ void k_apply_combine(const double* __restrict__ part, int nsplit, int
         }
 }
 
-template <typename T, int OP>
+template <typename T, int OP, int KC>
 static int launch_apply_op(tp_mesh* m, const tp_params* p, const double* v, int k, double* y,
                            cudaStream_t st) {
     using V4 = typename V4T<T>::type;
-    using L = OpLayout<OP>;
+    using L = OpLayout<OP, KC>;
     const int nf = m->nf;
     const double s = 2.0 - 2.0 / p->p;       // Sobolev order, §2.3
     const double l_exp = 3.0 - s;            // |d|^{-(2 sigma + 2)} = r2^{-(sigma+1)}, sigma = 2 - s
-    Grid g = make_grid(nf, nf, 1);
+    constexpr int TT = (sizeof(T) == 4 && KC == 3) ? 2 : 1;
+    Grid g = make_grid(nf, nf, TT);
     TP_TRY(ensure(m->part, sizeof(double) * (size_t)g.nsplit * L::NA * nf));
-    TP_TRY(ensure(m->wv64, sizeof(double) * 12 * (size_t)nf));
+    TP_TRY(ensure(m->wv64, sizeof(double) * 4 * KC * (size_t)nf));
     TP_TRY(ensure(m->wv32, sizeof(V4) * L::NW4 * (size_t)nf));
     TP_TRY(ensure(m->corner, sizeof(double) * 3 * (size_t)nf * k));
     const V4* fa = (const V4*)(sizeof(T) == 4 ? m->f32a.ptr : m->f64a.ptr);
     const V4* fb = (const V4*)(sizeof(T) == 4 ? m->f32b.ptr : m->f64b.ptr);
     for (int col0 = 0; col0 < k; col0 += KC) {
-        k_face_W<T><<<(nf + 255) / 256, 256, 0, st>>>(v, k, col0, m->faces.as<int>(), nf,
-                                                      m->f64a.as<d4>(), m->fgrad.as<double>(), OP,
-                                                      m->wv64.as<double>(), m->wv32.as<V4>(), L::NW4);
+        k_face_W<T, KC><<<(nf + 255) / 256, 256, 0, st>>>(v, k, col0, m->faces.as<int>(), nf,
+                                                          m->f64a.as<d4>(), m->fgrad.as<double>(), OP,
+                                                          m->wv64.as<double>(), m->wv32.as<V4>(), L::NW4);
         TP_LAUNCH_CHECK();
         dim3 grid(g.bx, g.nsplit);
         {
@@ -772,16 +821,16 @@ static int launch_apply_op(tp_mesh* m, const tp_params* p, const double* v, int 
             constexpr int key = OP == TP_OP_A ? PK_APPLY_A : OP == TP_OP_B ? PK_APPLY_B
                               : OP == TP_OP_B0 ? PK_APPLY_B0 : PK_APPLY_L;
             ProfScope ps(m, key, units, st);
-            k_apply<T, OP><<<grid, NT, 0, st>>>(fa, fb, m->f32c.as<float4>(), m->tilebox.as<float4>(),
-                                                m->center.as<double>(), m->wv32.as<V4>(), nf,
-                                                g.tiles_per_split, T(s), T(l_exp), m->part.as<double>());
+            m->prof.cols[key] += KC;
+            k_apply<T, OP, TT, KC><<<grid, NT, 0, st>>>(fa, fb, m->f32c.as<float4>(), m->tilebox.as<float4>(),
+                                                        m->center.as<double>(), m->wv32.as<V4>(), nf,
+                                                        g.tiles_per_split, T(s), T(l_exp), m->part.as<double>());
         }
         TP_LAUNCH_CHECK();
-        k_apply_combine<<<(nf + 255) / 256, 256, 0, st>>>(m->part.as<double>(), g.nsplit, nf, OP,
-                                                          L::NA, m->f64a.as<d4>(),
-                                                          m->fgrad.as<double>(),
-                                                          m->wv64.as<double>(), k, col0,
-                                                          m->corner.as<double>());
+        k_apply_combine<OP, KC><<<(nf + 255) / 256, 256, 0, st>>>(m->part.as<double>(), g.nsplit, nf,
+                                                                  m->f64a.as<d4>(), m->fgrad.as<double>(),
+                                                                  m->wv64.as<double>(), k, col0,
+                                                                  m->corner.as<double>());
         TP_LAUNCH_CHECK();
     }
     return corners_to_vertices(m, m->corner.as<double>(), k, y, st);
@@ -790,11 +839,18 @@ static int launch_apply_op(tp_mesh* m, const tp_params* p, const double* v, int 
 template <typename T>
 static int launch_apply(tp_mesh* m, const tp_params* p, int op, const double* v, int k, double* y,
                         cudaStream_t st) {
+    // 9 columns in one pass share the kernel evaluation; up to 3 columns
+    // take the lighter 3-column kernel
+    const bool wide = k > 3;
     switch (op) {
-        case TP_OP_A: return launch_apply_op<T, TP_OP_A>(m, p, v, k, y, st);
-        case TP_OP_B: return launch_apply_op<T, TP_OP_B>(m, p, v, k, y, st);
-        case TP_OP_B0: return launch_apply_op<T, TP_OP_B0>(m, p, v, k, y, st);
-        case TP_OP_L: return launch_apply_op<T, TP_OP_L>(m, p, v, k, y, st);
+        case TP_OP_A: return wide ? launch_apply_op<T, TP_OP_A, 9>(m, p, v, k, y, st)
+                                  : launch_apply_op<T, TP_OP_A, 3>(m, p, v, k, y, st);
+        case TP_OP_B: return wide ? launch_apply_op<T, TP_OP_B, 9>(m, p, v, k, y, st)
+                                  : launch_apply_op<T, TP_OP_B, 3>(m, p, v, k, y, st);
+        case TP_OP_B0: return wide ? launch_apply_op<T, TP_OP_B0, 9>(m, p, v, k, y, st)
+                                   : launch_apply_op<T, TP_OP_B0, 3>(m, p, v, k, y, st);
+        case TP_OP_L: return wide ? launch_apply_op<T, TP_OP_L, 9>(m, p, v, k, y, st)
+                                  : launch_apply_op<T, TP_OP_L, 3>(m, p, v, k, y, st);
     }
     return fail(TP_ERR_INVALID_ARG, "unknown operator");
 }

@@ -47,12 +47,6 @@ int differential_dev(tp_mesh* m, const tp_params* p, double* dE, double* E_host,
     return TP_OK;
 }
 
-// y = A v for the GMRES operator (mean-zero output)
-static int apply_A(tp_mesh* m, const tp_params* p, const double* v, double* y, cudaStream_t st) {
-    TP_TRY(apply_direct(m, p, TP_OP_A, v, 3, y, st));
-    return project_mean_zero(m, y, 3, st);
-}
-
 // z = C^+ L^{2-s} C^+ b (§5.2); b, z [nv][k] device
 int precond_apply_dev(tp_mesh* m, const tp_params* p, const double* b, int k, double* z,
                       cudaStream_t st, int* cg_iters) {
@@ -69,131 +63,249 @@ int precond_apply_dev(tp_mesh* m, const tp_params* p, const double* b, int k, do
 }
 
 // ---------------------------------------------------------------------------
-// flexible GMRES(m), right preconditioning, on the mean-zero subspace
+// flexible GMRES(m), right preconditioning, on the mean-zero subspace, for up
+// to three right-hand sides in lockstep
 // ---------------------------------------------------------------------------
+//
+// The Schur step needs A_3 solves with g and with the rows of dPhi (Eq. 17,
+// 18). The systems keep separate Krylov spaces, Hessenberg matrices and
+// restarts, but every preconditioner application (two CG solves and one
+// L^{2-s} product) and every A product is done once for all active systems,
+// on their vectors packed side by side as [nv][3 * nsys] columns.
 
 struct KrylovStats {
     int iters = 0, cg_iters = 0;
-    double rel_res = 0.0;
 };
 
-static int fgmres(tp_mesh* m, const tp_params* p, const double* b, double* x, cudaStream_t st,
-                  KrylovStats* ks) {
-    const int mr = p->gmres_restart < 1 ? 1 : (p->gmres_restart > 60 ? 60 : p->gmres_restart);
-    const size_t n = (size_t)m->nv * 3;
-    TP_TRY(ensure(m->kry, sizeof(double) * n * (2 * mr + 1)));
-    TP_TRY(ensure(m->tmpv[5], sizeof(double) * n));
-    double* Vb = m->kry.as<double>();
-    auto Vv = [&](int j) { return Vb + (size_t)j * n; };
-    auto Zv = [&](int j) { return Vb + (size_t)(mr + 1 + j) * n; };
-    double* w = m->tmpv[5].as<double>();
+constexpr int MAXSYS = 3;
 
-    TP_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * n, st));
-    // r0 = b (projected)
-    TP_CUDA(cudaMemcpyAsync(Vv(0), b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-    TP_TRY(project_mean_zero(m, Vv(0), 3, st));
-    double bn2;
-    {
-        const double* xs[1] = {Vv(0)};
-        TP_TRY(dots(m, xs, Vv(0), 1, n, &bn2, st));
+struct SysPtrs {
+    double* p[MAXSYS];
+};
+
+// dst[v][3*s + c] = src_s[v][c] for the ns systems listed
+__global__ void k_pack(SysPtrs src, int ns, int nv, double* __restrict__ dst) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t n = (size_t)nv * 3 * ns;
+    if (i >= n) return;
+    int w = 3 * ns;
+    size_t v = i / w;
+    int r = (int)(i % w), sI = r / 3, c = r % 3;
+    dst[i] = src.p[sI][v * 3 + c];
+}
+
+__global__ void k_unpack(const double* __restrict__ srcp, int ns, int nv, SysPtrs dst) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    size_t n = (size_t)nv * 3 * ns;
+    if (i >= n) return;
+    int w = 3 * ns;
+    size_t v = i / w;
+    int r = (int)(i % w), sI = r / 3, c = r % 3;
+    dst.p[sI][v * 3 + c] = srcp[i];
+}
+
+static int pack(const std::vector<double*>& src, int nv, double* dst, cudaStream_t st) {
+    SysPtrs sp{};
+    for (size_t i = 0; i < src.size(); ++i) sp.p[i] = src[i];
+    size_t n = (size_t)nv * 3 * src.size();
+    k_pack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(sp, (int)src.size(), nv, dst);
+    TP_LAUNCH_CHECK();
+    return TP_OK;
+}
+
+static int unpack(const double* srcp, int nv, const std::vector<double*>& dst, cudaStream_t st) {
+    SysPtrs sp{};
+    for (size_t i = 0; i < dst.size(); ++i) sp.p[i] = dst[i];
+    size_t n = (size_t)nv * 3 * dst.size();
+    k_unpack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(srcp, (int)dst.size(), nv, sp);
+    TP_LAUNCH_CHECK();
+    return TP_OK;
+}
+
+// y = A v on packed columns (mean-zero output)
+static int apply_A_packed(tp_mesh* m, const tp_params* p, const double* v, int k, double* y, cudaStream_t st) {
+    TP_TRY(apply_direct(m, p, TP_OP_A, v, k, y, st));
+    return project_mean_zero(m, y, k, st);
+}
+
+struct GmSys {
+    double* b;
+    double* x;
+    double* V;   // (mr+1) basis vectors
+    double* Z;   // mr preconditioned vectors
+    double* w;
+    double bnorm = 0.0, beta = 0.0;
+    bool active = true, converged = false;
+    int iters = 0;
+    std::vector<double> H, cs, sn, g;
+};
+
+static int fgmres_multi(tp_mesh* m, const tp_params* p, int ns, const double* const* b, double* const* x,
+                        cudaStream_t st, KrylovStats* ks, int* status) {
+    const int mr = p->gmres_restart < 1 ? 1 : (p->gmres_restart > 60 ? 60 : p->gmres_restart);
+    const int nv = m->nv;
+    const size_t n = (size_t)nv * 3;
+    // per system: V (mr+1), Z (mr), w; shared: three packed [nv][3*ns] buffers
+    const size_t per = (size_t)(2 * mr + 2) * n;
+    TP_TRY(ensure(m->kry, sizeof(double) * (per * ns + 3 * n * ns)));
+    double* base = m->kry.as<double>();
+    double* P0 = base + per * ns;
+    double* P1 = P0 + n * ns;
+    double* P2 = P1 + n * ns;
+    std::vector<GmSys> S(ns);
+    for (int i = 0; i < ns; ++i) {
+        GmSys& q = S[i];
+        q.b = const_cast<double*>(b[i]);
+        q.x = x[i];
+        q.V = base + per * i;
+        q.Z = q.V + (size_t)(mr + 1) * n;
+        q.w = q.Z + (size_t)mr * n;
+        q.H.assign((mr + 1) * mr, 0.0);
+        q.cs.assign(mr, 0.0);
+        q.sn.assign(mr, 0.0);
+        q.g.assign(mr + 1, 0.0);
+        status[i] = TP_OK;
+        TP_CUDA(cudaMemsetAsync(q.x, 0, sizeof(double) * n, st));
+        TP_CUDA(cudaMemcpyAsync(q.V, q.b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+        TP_TRY(project_mean_zero(m, q.V, 3, st));
+        double bn2;
+        const double* xs[1] = {q.V};
+        TP_TRY(dots(m, xs, q.V, 1, n, &bn2, st));
+        q.bnorm = q.beta = std::sqrt(bn2);
+        if (q.bnorm == 0.0) {
+            q.active = false;
+            q.converged = true;
+        }
     }
-    const double bnorm = std::sqrt(bn2);
-    ks->rel_res = 0.0;
-    if (bnorm == 0.0) return TP_OK;
-    double beta = bnorm;
+    auto Vj = [&](GmSys& q, int j) { return q.V + (size_t)j * n; };
+    auto Zj = [&](GmSys& q, int j) { return q.Z + (size_t)j * n; };
     int total = 0;
-    std::vector<double> H((mr + 1) * mr), cs(mr), sn(mr), g(mr + 1), y(mr);
-    bool converged = false;
-    while (!converged && total < p->krylov_max) {
-        {
-            double sc = 1.0 / beta;
-            const double* xs[1] = {Vv(0)};
-            TP_TRY(lincomb(Vv(0), xs, &sc, 1, n, 0.0, st));
+    for (;;) {
+        std::vector<int> act;
+        for (int i = 0; i < ns; ++i)
+            if (S[i].active) act.push_back(i);
+        if (act.empty() || total >= p->krylov_max) break;
+        // start of a cycle: normalise r into V_0
+        for (int i : act) {
+            GmSys& q = S[i];
+            double sc = 1.0 / q.beta;
+            const double* xs[1] = {q.V};
+            TP_TRY(lincomb(q.V, xs, &sc, 1, n, 0.0, st));
+            std::fill(q.g.begin(), q.g.end(), 0.0);
+            q.g[0] = q.beta;
         }
-        std::fill(g.begin(), g.end(), 0.0);
-        g[0] = beta;
-        int j = 0;
-        for (; j < mr && total < p->krylov_max; ++j) {
-            TP_TRY(precond_apply_dev(m, p, Vv(j), 3, Zv(j), st, &ks->cg_iters));
-            TP_TRY(apply_A(m, p, Zv(j), w, st));
-            // classical Gram-Schmidt, twice
-            std::vector<const double*> basis(j + 1);
-            for (int i = 0; i <= j; ++i) basis[i] = Vv(i);
-            std::vector<double> h(j + 1), h2(j + 1);
-            TP_TRY(dots(m, basis.data(), w, j + 1, n, h.data(), st));
-            std::vector<double> neg(j + 1);
-            for (int i = 0; i <= j; ++i) neg[i] = -h[i];
-            TP_TRY(lincomb(w, basis.data(), neg.data(), j + 1, n, 1.0, st));
-            TP_TRY(dots(m, basis.data(), w, j + 1, n, h2.data(), st));
-            for (int i = 0; i <= j; ++i) neg[i] = -h2[i];
-            TP_TRY(lincomb(w, basis.data(), neg.data(), j + 1, n, 1.0, st));
-            for (int i = 0; i <= j; ++i) H[i * mr + j] = h[i] + h2[i];
-            double wn2;
-            {
-                const double* xs[1] = {w};
-                TP_TRY(dots(m, xs, w, 1, n, &wn2, st));
+        std::vector<int> jlen(ns, 0);
+        std::vector<int> cyc = act;
+        for (int j = 0; j < mr && !cyc.empty() && total < p->krylov_max; ++j) {
+            const int na = (int)cyc.size();
+            std::vector<double*> vin, zout, wout;
+            for (int i : cyc) {
+                vin.push_back(Vj(S[i], j));
+                zout.push_back(Zj(S[i], j));
+                wout.push_back(S[i].w);
             }
-            double hn = std::sqrt(wn2);
-            H[(j + 1) * mr + j] = hn;
-            if (hn > 0.0) {
-                double sc = 1.0 / hn;
-                const double* xs[1] = {w};
-                TP_TRY(lincomb(Vv(j + 1), xs, &sc, 1, n, 0.0, st));
-            }
-            // Givens rotations
-            for (int i = 0; i < j; ++i) {
-                double a = H[i * mr + j], c = H[(i + 1) * mr + j];
-                H[i * mr + j] = cs[i] * a + sn[i] * c;
-                H[(i + 1) * mr + j] = -sn[i] * a + cs[i] * c;
-            }
-            double a = H[j * mr + j], c = H[(j + 1) * mr + j];
-            double r = std::hypot(a, c);
-            cs[j] = r > 0.0 ? a / r : 1.0;
-            sn[j] = r > 0.0 ? c / r : 0.0;
-            H[j * mr + j] = r;
-            H[(j + 1) * mr + j] = 0.0;
-            g[j + 1] = -sn[j] * g[j];
-            g[j] = cs[j] * g[j];
+            TP_TRY(pack(vin, nv, P0, st));
+            TP_TRY(precond_apply_dev(m, p, P0, 3 * na, P1, st, &ks->cg_iters));
+            TP_TRY(unpack(P1, nv, zout, st));
+            TP_TRY(apply_A_packed(m, p, P1, 3 * na, P2, st));
+            TP_TRY(unpack(P2, nv, wout, st));
             ++total;
-            ks->rel_res = std::fabs(g[j + 1]) / bnorm;
-            if (ks->rel_res <= p->krylov_tol || hn == 0.0) {
-                ++j;
-                converged = true;
-                break;
+            std::vector<int> still;
+            for (int i : cyc) {
+                GmSys& q = S[i];
+                // classical Gram-Schmidt, twice
+                std::vector<const double*> basis(j + 1);
+                for (int l = 0; l <= j; ++l) basis[l] = Vj(q, l);
+                std::vector<double> h(j + 1), h2(j + 1), neg(j + 1);
+                TP_TRY(dots(m, basis.data(), q.w, j + 1, n, h.data(), st));
+                for (int l = 0; l <= j; ++l) neg[l] = -h[l];
+                TP_TRY(lincomb(q.w, basis.data(), neg.data(), j + 1, n, 1.0, st));
+                TP_TRY(dots(m, basis.data(), q.w, j + 1, n, h2.data(), st));
+                for (int l = 0; l <= j; ++l) neg[l] = -h2[l];
+                TP_TRY(lincomb(q.w, basis.data(), neg.data(), j + 1, n, 1.0, st));
+                for (int l = 0; l <= j; ++l) q.H[l * mr + j] = h[l] + h2[l];
+                double wn2;
+                const double* xs[1] = {q.w};
+                TP_TRY(dots(m, xs, q.w, 1, n, &wn2, st));
+                double hn = std::sqrt(wn2);
+                q.H[(j + 1) * mr + j] = hn;
+                if (hn > 0.0) {
+                    double sc = 1.0 / hn;
+                    TP_TRY(lincomb(Vj(q, j + 1), xs, &sc, 1, n, 0.0, st));
+                }
+                for (int l = 0; l < j; ++l) {  // Givens rotations
+                    double a = q.H[l * mr + j], c = q.H[(l + 1) * mr + j];
+                    q.H[l * mr + j] = q.cs[l] * a + q.sn[l] * c;
+                    q.H[(l + 1) * mr + j] = -q.sn[l] * a + q.cs[l] * c;
+                }
+                double a = q.H[j * mr + j], c = q.H[(j + 1) * mr + j];
+                double r = std::hypot(a, c);
+                q.cs[j] = r > 0.0 ? a / r : 1.0;
+                q.sn[j] = r > 0.0 ? c / r : 0.0;
+                q.H[j * mr + j] = r;
+                q.H[(j + 1) * mr + j] = 0.0;
+                q.g[j + 1] = -q.sn[j] * q.g[j];
+                q.g[j] = q.cs[j] * q.g[j];
+                q.iters++;
+                jlen[i] = j + 1;
+                double rel = std::fabs(q.g[j + 1]) / q.bnorm;
+                if (rel <= p->krylov_tol || hn == 0.0) {
+                    q.converged = true;
+                    q.active = false;
+                } else {
+                    still.push_back(i);
+                }
+            }
+            cyc = still;
+        }
+        // x += Z y with H y = g (upper triangular, size jlen)
+        for (int i : act) {
+            GmSys& q = S[i];
+            int J = jlen[i];
+            std::vector<double> y(J);
+            for (int l = J - 1; l >= 0; --l) {
+                double sum = q.g[l];
+                for (int t = l + 1; t < J; ++t) sum -= q.H[l * mr + t] * y[t];
+                y[l] = q.H[l * mr + l] != 0.0 ? sum / q.H[l * mr + l] : 0.0;
+            }
+            std::vector<const double*> zs(J);
+            for (int l = 0; l < J; ++l) zs[l] = Zj(q, l);
+            if (J > 0) TP_TRY(lincomb(q.x, zs.data(), y.data(), J, n, 1.0, st));
+        }
+        // restart the unconverged systems from their true residuals r = b - A x
+        std::vector<int> rest;
+        for (int i : act)
+            if (S[i].active) rest.push_back(i);
+        if (rest.empty() || total >= p->krylov_max) break;
+        std::vector<double*> xin, rout;
+        for (int i : rest) {
+            xin.push_back(S[i].x);
+            rout.push_back(S[i].w);
+        }
+        TP_TRY(pack(xin, nv, P0, st));
+        TP_TRY(apply_A_packed(m, p, P0, 3 * (int)rest.size(), P2, st));
+        TP_TRY(unpack(P2, nv, rout, st));
+        for (int i : rest) {
+            GmSys& q = S[i];
+            const double* xs[2] = {q.b, q.w};
+            double cf[2] = {1.0, -1.0};
+            TP_TRY(lincomb(q.V, xs, cf, 2, n, 0.0, st));
+            TP_TRY(project_mean_zero(m, q.V, 3, st));
+            double rn2;
+            const double* x1[1] = {q.V};
+            TP_TRY(dots(m, x1, q.V, 1, n, &rn2, st));
+            q.beta = std::sqrt(rn2);
+            if (q.beta / q.bnorm <= p->krylov_tol) {
+                q.active = false;
+                q.converged = true;
             }
         }
-        // x += Z y, with H y = g (upper triangular, size j)
-        for (int i = j - 1; i >= 0; --i) {
-            double s = g[i];
-            for (int l = i + 1; l < j; ++l) s -= H[i * mr + l] * y[l];
-            y[i] = H[i * mr + i] != 0.0 ? s / H[i * mr + i] : 0.0;
-        }
-        std::vector<const double*> zs(j);
-        for (int i = 0; i < j; ++i) zs[i] = Zv(i);
-        TP_TRY(lincomb(x, zs.data(), y.data(), j, n, 1.0, st));
-        if (converged) break;
-        // restart from the true residual r = b - A x
-        TP_TRY(apply_A(m, p, x, w, st));
-        {
-            const double* xs[2] = {b, w};
-            double cf[2] = {1.0, -1.0};
-            TP_TRY(lincomb(Vv(0), xs, cf, 2, n, 0.0, st));
-        }
-        TP_TRY(project_mean_zero(m, Vv(0), 3, st));
-        double rn2;
-        {
-            const double* xs[1] = {Vv(0)};
-            TP_TRY(dots(m, xs, Vv(0), 1, n, &rn2, st));
-        }
-        beta = std::sqrt(rn2);
-        ks->rel_res = beta / bnorm;
-        if (ks->rel_res <= p->krylov_tol) converged = true;
     }
     ks->iters += total;
-    TP_TRY(project_mean_zero(m, x, 3, st));
-    if (!converged)
-        return fail(TP_ERR_NOT_CONVERGED, "gmres: relative residual " + std::to_string(ks->rel_res) +
-                                              " after " + std::to_string(total) + " iterations");
+    for (int i = 0; i < ns; ++i) {
+        TP_TRY(project_mean_zero(m, S[i].x, 3, st));
+        if (!S[i].converged) status[i] = TP_ERR_NOT_CONVERGED;
+    }
     return TP_OK;
 }
 
@@ -305,15 +417,19 @@ int precond_step_dev(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp
             Zr[nc] = Z[i];
             ++nc;
         }
-    // 3. k+1 solves with A_3 (Eq. 17, 18)
+    // 3. k+1 solves with A_3 (Eq. 17, 18), in lockstep
     KrylovStats ks;
-    int st_solve = fgmres(m, p, g, Ag, st, &ks);
-    if (st_solve != TP_OK && st_solve != TP_ERR_NOT_CONVERGED) return st_solve;
-    if (st_solve != TP_OK) r.status = st_solve;
-    for (int i = 0; i < nc; ++i) {
-        st_solve = fgmres(m, p, Jr[i], Zr[i], st, &ks);
-        if (st_solve != TP_OK && st_solve != TP_ERR_NOT_CONVERGED) return st_solve;
-        if (st_solve != TP_OK) r.status = st_solve;
+    {
+        const double* rhs[MAXSYS] = {g, nullptr, nullptr};
+        double* sol[MAXSYS] = {Ag, nullptr, nullptr};
+        for (int i = 0; i < nc; ++i) {
+            rhs[1 + i] = Jr[i];
+            sol[1 + i] = Zr[i];
+        }
+        int sts[MAXSYS] = {TP_OK, TP_OK, TP_OK};
+        TP_TRY(fgmres_multi(m, p, 1 + nc, rhs, sol, st, &ks, sts));
+        for (int i = 0; i < 1 + nc; ++i)
+            if (sts[i] != TP_OK) r.status = sts[i];
     }
     // 4. Schur complement S = dPhi Z (= -(M/A)), x = -(Ag - Z S^-1 dPhi Ag)
     double Sm[2][2] = {{0, 0}, {0, 0}}, JAg[2] = {0, 0};

@@ -85,6 +85,7 @@ struct Profiler {
     long long launches[PK_COUNT] = {};
     double ms[PK_COUNT] = {};
     double units[PK_COUNT] = {};
+    double cols[PK_COUNT] = {};    // operator columns processed (apply kernels)
     std::vector<cudaEvent_t> pool;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
 };

@@ -102,12 +102,15 @@ def test_operator_apply(lib, meshes, name, op, prec):
     assert rel(y, O.apply_operator(V, F, u, op)) <= (TOL32 if prec == 0 else TOL64)
 
 
-@pytest.mark.parametrize("k", [1, 2, 5])
-def test_operator_apply_columns(lib, meshes, k):
-    V, F, m = meshes["ico2"]
+@pytest.mark.parametrize("k", [1, 2, 5, 9])
+@pytest.mark.parametrize("op", ["A", "L", "B0"])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_operator_apply_columns(lib, meshes, k, op, prec):
+    # k > 3 takes the 9-column kernels (one pass shares the kernel evaluation)
+    V, F, m = meshes["torus13x7"]
     u = vertex_vectors(len(V), k, 7)
-    y = lib.fractional_apply(m, "A", dev(u), lib.params())
-    assert rel(y.cpu().numpy(), O.apply_operator(V, F, u, "A")) <= TOL32
+    y = lib.fractional_apply(m, op, dev(u), lib.params(precision=prec))
+    assert rel(y.cpu().numpy(), O.apply_operator(V, F, u, op)) <= (TOL32 if prec == 0 else TOL64)
 
 
 def test_operator_constant_nullspace_and_symmetry(lib, meshes):
