@@ -335,7 +335,7 @@ def gpu_arm(args):
         "data": "synthetic (seeded torus, no dataset)",
         "config": {"workload": WORKLOAD, "nv": int(len(V)), "nf": int(len(F)),
                    "step": "set positions + precond_step(area+volume; direct FP32 pairs, FP64 solver) + BH theta=0.5 E+dE",
-                   "solver_dtype": "f64", "krylov_tol": ps.krylov_tol, "cg_tol": ps.cg_tol,
+                   "solver_dtype": "f64 (CG, FGMRES, Schur)", "krylov_tol": ps.krylov_tol, "cg_tol": ps.cg_tol,
                    "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{world}"},
         "steps_per_s": 1e3 * args.steps / dev_ms_all,
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},

@@ -79,7 +79,7 @@ typedef struct tp_params {
     double krylov_tol;    /* relative residual of the outer GMRES solves */
     int    krylov_max;    /* iteration cap of one GMRES solve (all restarts) */
     int    gmres_restart; /* restart length m */
-    double cg_tol;        /* relative residual of the Poisson CG solves */
+    double cg_tol;        /* relative residual of the Poisson CG solves (FP64) */
     int    cg_max;        /* iteration cap of one CG solve */
     double armijo_c;      /* sufficient-decrease constant of the line search */
     double armijo_shrink; /* step shrink factor */
@@ -124,7 +124,7 @@ typedef struct tp_mesh tp_mesh;
 
 /* Fill *p with the defaults: p=6, theta=0, leaf_size=8, FP32 pairs,
  * full BH differential, krylov_tol=1e-6, krylov_max=200, restart 30,
- * cg_tol=1e-10, cg_max=20000, Armijo c=1e-4, shrink 0.5, tau0=1, ls_max=30,
+ * cg_tol=1e-6, cg_max=20000, Armijo c=1e-4, shrink 0.5, tau0=1, ls_max=30,
  * proj_iters=1. */
 void tp_params_default(tp_params* p);
 
@@ -174,8 +174,9 @@ int fractional_apply(tp_mesh* m, const tp_params* p, int op, const double* v,
 
 /* z = C^+ b: Jacobi-preconditioned CG on the cotan stiffness matrix C of
  * the current positions (§5.2), k columns (1 <= k <= 9), right-hand side
- * and solution projected to zero mean. *iters_out (host, may be NULL)
- * receives the iteration count. TP_ERR_NOT_CONVERGED if cg_max is hit. */
+ * and solution projected to zero mean, all in FP64. *iters_out (host, may be NULL) receives the iteration count.
+ * TP_ERR_NOT_CONVERGED if cg_max is hit; TP_ERR_TIMEOUT if a device-side
+ * wait gave up. */
 int cotan_solve(tp_mesh* m, const tp_params* p, const double* b, int k, double* z,
                 int ptr_kind, void* stream, int* iters_out);
 

@@ -570,8 +570,8 @@ def apply_operator_at_vertices(f, faces, v, op, verts, p=6.0):
 # by face index; leaves are runs of `leaf` consecutive sorted faces; a node
 # over n leaves has a left child over ceil(n/2) leaves; nodes are numbered in
 # pre-order. Node data: a_I = sum a_T, X_I = sum a_T X_T / a_I, the bounding
-# box of the node's triangle vertices, and r_I = max |v - X_I| over the
-# vertices for leaves, max_child (|X_child - X_I| + r_child) for inner nodes.
+# box of the node's triangle vertices, and the radius r_I = max |v - X_I|
+# over the vertices of the node's faces (§4.1: radius from the barycenter).
 # Admissibility (§4.1, read with theta): max(r_S, r_I)^2 < theta^2 dist^2 of
 # the two boxes, decided in FP32 like the kernel; an inadmissible leaf is
 # summed exactly (T != S).
@@ -659,8 +659,18 @@ def bvh_build(f, faces, leaf=8):
         XI[ids] = (aI[L][:, None] * XI[L] + aI[R][:, None] * XI[R]) / aI[ids][:, None]
         box_lo[ids] = np.minimum(box_lo[L], box_lo[R])
         box_hi[ids] = np.maximum(box_hi[L], box_hi[R])
-        rI[ids] = np.maximum(np.linalg.norm(XI[L] - XI[ids], axis=1) + rI[L],
-                             np.linalg.norm(XI[R] - XI[ids], axis=1) + rI[R])
+    # exact radii of the inner nodes: max over the vertices of their faces
+    for d in range(depth.max() + 1):
+        ids = inner[depth[inner] == d]
+        if len(ids) == 0:
+            continue
+        cnt = count[ids]
+        starts = np.concatenate([[0], np.cumsum(cnt)[:-1]])       # segment starts
+        seg = np.repeat(np.arange(len(ids)), cnt)                  # node of each entry
+        fidx = np.repeat(first[ids] - starts, cnt) + np.arange(cnt.sum())   # sorted face positions
+        v = vx[order[fidx]]                                        # [m,3,3]
+        dist = np.sqrt(((v - XI[ids][seg][:, None, :]) ** 2).sum(axis=2)).max(axis=1)
+        rI[ids] = np.maximum.reduceat(dist, starts)
     # target faces: their own boxes and radii
     fbox_lo, fbox_hi = vx.min(axis=1), vx.max(axis=1)
     fr2 = ((vx - Xr[:, None, :]) ** 2).sum(axis=2).max(axis=1)

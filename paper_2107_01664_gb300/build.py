@@ -63,7 +63,8 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(s, verbose, extra), SOURCES))
     tmp = LIB + ".tmp"
-    cmd = [nvcc(), "-shared", "-o", tmp, *objs, *ARCH, "-lcudart"]
+    # -z defs: an undefined symbol fails the link instead of the first dlopen
+    cmd = [nvcc(), "-shared", "-o", tmp, *objs, *ARCH, "-lcudart", "-Xlinker", "-z", "-Xlinker", "defs"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

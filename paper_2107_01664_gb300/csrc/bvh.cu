@@ -303,6 +303,52 @@ __global__ void k_nodes_level(const NodeShape* __restrict__ shape, const int* __
     node[id] = o;
 }
 
+// Exact node radii r_I = max |v - X_I| over the vertices of the node's faces.
+// Each sorted face walks its root-to-leaf path and raises the radius of every
+// node on it; non-negative doubles order like their bit patterns, so a 64-bit
+// integer max is exact and independent of the order of the updates.
+__global__ void k_node_radius_exact(const int* __restrict__ perm, int nf, int leaf,
+                                    const NodeShape* __restrict__ shape, const int* __restrict__ right,
+                                    const d4* __restrict__ node64, const double* __restrict__ pos,
+                                    const int* __restrict__ faces, const double* __restrict__ center,
+                                    unsigned long long* __restrict__ rbits) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    int S = perm[i];
+    double v[3][3];
+    for (int cr = 0; cr < 3; ++cr) {
+        int vi = faces[3 * S + cr];
+        for (int c = 0; c < 3; ++c) v[cr][c] = pos[3 * vi + c] - center[c];
+    }
+    const int lf = i / leaf;
+    int id = 0;
+    for (;;) {
+        d4 X = node64[id];
+        double d2 = 0.0;
+        for (int cr = 0; cr < 3; ++cr) {
+            double dx = v[cr][0] - X.x, dy = v[cr][1] - X.y, dz = v[cr][2] - X.z;
+            d2 = fmax(d2, dx * dx + dy * dy + dz * dz);
+        }
+        unsigned long long b = (unsigned long long)__double_as_longlong(sqrt(d2));
+        if (b > rbits[id]) atomicMax(rbits + id, b);
+        NodeShape sh = shape[id];
+        if (sh.leaf) break;
+        const int L = id + 1;
+        NodeShape sl = shape[L];
+        int lfirst = sl.first / leaf, lcount = (sl.skip - L + 1) / 2;
+        id = (lf >= lfirst && lf < lfirst + lcount) ? L : right[id];
+    }
+}
+
+__global__ void k_node_radius_apply(const unsigned long long* __restrict__ rbits, int nn, double* __restrict__ noder,
+                                    BvhNode* __restrict__ node) {
+    int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= nn) return;
+    double r = __longlong_as_double((long long)rbits[id]);
+    noder[id] = r;
+    node[id].r2 = (float)(r * r);
+}
+
 int bvh_build(tp_mesh* m, const tp_params* p, cudaStream_t st) {
     if (m->bvh_shape_leaf != p->leaf_size) {
         BvhHost h;
@@ -373,6 +419,17 @@ int bvh_build(tp_mesh* m, const tp_params* p, cudaStream_t st) {
                                                              node, node64, noder, nodelo);
         TP_LAUNCH_CHECK();
     }
+    // exact radii (the per-level pass above used the child bound for inner nodes)
+    {
+        unsigned long long* rbits = reinterpret_cast<unsigned long long*>(kin);   // keys no longer needed
+        TP_CUDA(cudaMemsetAsync(rbits, 0, sizeof(unsigned long long) * (size_t)h.nnodes, st));
+        k_node_radius_exact<<<(nf + 255) / 256, 256, 0, st>>>(perm, nf, h.leaf, shape, right, node64,
+                                                              m->pos.as<double>(), m->faces.as<int>(),
+                                                              m->center.as<double>(), rbits);
+        TP_LAUNCH_CHECK();
+        k_node_radius_apply<<<(h.nnodes + 255) / 256, 256, 0, st>>>(rbits, h.nnodes, noder, node);
+        TP_LAUNCH_CHECK();
+    }
     m->bvh_valid = true;
     return TP_OK;
 }
@@ -413,7 +470,16 @@ struct KahanF {
     __device__ __forceinline__ double value() const { return (double)s - (double)c; }
 };
 
-// energy rows: thread per target (sorted position i, or target list)
+// Warp-cooperative traversal. Each lane owns one target (sorted position
+// i); the warp walks the pre-order node sequence together, and lane L is
+// active at node id only when id >= skip_L. When a lane finishes a node (an
+// admissible node, or an inadmissible leaf summed exactly) it sets skip_L to
+// the node's escape index; the warp descends (id + 1) if any active lane needs
+// to, else jumps to the escape index. Every jump target lies at or before
+// the escape index of each lane's finished nodes, so each lane sees exactly
+// the nodes of its own stackless traversal: the admissible sets are those of
+// the per-target definition, while node loads and leaf-face loads are the
+// same address across the warp.
 template <bool P6>
 __global__ void __launch_bounds__(128)
 k_bh_energy(const BvhNode* __restrict__ node, const float4* __restrict__ nodelo, int nnodes,
@@ -422,57 +488,62 @@ k_bh_energy(const BvhNode* __restrict__ node, const float4* __restrict__ nodelo,
             const int* __restrict__ inv_targets /* sorted positions of a target list, or null */, int nt,
             float theta2, float halfp, const d4* __restrict__ f64a, double* __restrict__ rows,
             unsigned long long* __restrict__ count) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= nt) return;
-    const int i = inv_targets ? inv_targets[t] : t;
-    float4 A = sa[i], B = sb[i], Al = sl[i];
-    FaceBox fb = fbox[i];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool has = t < nt;
+    const int i = has ? (inv_targets ? inv_targets[t] : t) : 0;
+    const float4 A = sa[i], B = sb[i], Al = sl[i];
+    const FaceBox fb = fbox[i];
+    int skip = has ? 0 : nnodes;
     float acc = 0.f;
     KahanF sum;
     int nint = 0, run = 0;
     int id = 0;
     while (id < nnodes) {
-        BvhNode n = node[id];
-        float d2 = box_dist2(fb.lox, fb.loy, fb.loz, fb.hix, fb.hiy, fb.hiz, n);
-        float mr2 = fmaxf(fb.r2, n.r2);
-        if (mr2 < __fmul_rn(theta2, d2)) {
-            float4 nl = nodelo[id];
-            float dx = (A.x - n.cx) + (Al.x - nl.x), dy = (A.y - n.cy) + (Al.y - nl.y),
-                  dz = (A.z - n.cz) + (Al.z - nl.z);
-            float r2 = dx * dx + dy * dy + dz * dz;
-            float u = B.x * dx + B.y * dy + B.z * dz;
-            float ir2 = frcp(fmaxf(r2, 1e-18f));
-            float q = u * u * (ir2 * ir2);
-            float K = P6 ? q * q * q : fpow(q, halfp);
-            acc = fmaf(K, n.a, acc);
-            ++nint;
-            if (++run == 32) { sum.add(acc); acc = 0.f; run = 0; }
-            id = n.skip;
-        } else if (n.leaf) {
-            for (int j = n.first; j < n.first + n.count; ++j) {
-                if (j == i) continue;
-                float4 s = sa[j], l = sl[j];
-                float dx = (A.x - s.x) + (Al.x - l.x), dy = (A.y - s.y) + (Al.y - l.y),
-                      dz = (A.z - s.z) + (Al.z - l.z);
+        const BvhNode n = node[id];
+        bool desc = false;
+        if (id >= skip) {
+            float d2 = box_dist2(fb.lox, fb.loy, fb.loz, fb.hix, fb.hiy, fb.hiz, n);
+            float mr2 = fmaxf(fb.r2, n.r2);
+            if (mr2 < __fmul_rn(theta2, d2)) {
+                float4 nl = nodelo[id];
+                float dx = (A.x - n.cx) + (Al.x - nl.x), dy = (A.y - n.cy) + (Al.y - nl.y),
+                      dz = (A.z - n.cz) + (Al.z - nl.z);
                 float r2 = dx * dx + dy * dy + dz * dz;
                 float u = B.x * dx + B.y * dy + B.z * dz;
                 float ir2 = frcp(fmaxf(r2, 1e-18f));
                 float q = u * u * (ir2 * ir2);
                 float K = P6 ? q * q * q : fpow(q, halfp);
-                acc = fmaf(K, s.w, acc);
+                acc = fmaf(K, n.a, acc);
                 ++nint;
+                if (++run == 32) { sum.add(acc); acc = 0.f; run = 0; }
+                skip = n.skip;
+            } else if (n.leaf) {
+                for (int j = n.first; j < n.first + n.count; ++j) {
+                    if (j == i) continue;
+                    float4 s = sa[j], l = sl[j];
+                    float dx = (A.x - s.x) + (Al.x - l.x), dy = (A.y - s.y) + (Al.y - l.y),
+                          dz = (A.z - s.z) + (Al.z - l.z);
+                    float r2 = dx * dx + dy * dy + dz * dz;
+                    float u = B.x * dx + B.y * dy + B.z * dz;
+                    float ir2 = frcp(fmaxf(r2, 1e-18f));
+                    float q = u * u * (ir2 * ir2);
+                    float K = P6 ? q * q * q : fpow(q, halfp);
+                    acc = fmaf(K, s.w, acc);
+                    ++nint;
+                }
+                sum.add(acc);
+                acc = 0.f;
+                run = 0;
+                skip = n.skip;
+            } else {
+                desc = true;
             }
-            sum.add(acc);
-            acc = 0.f;
-            run = 0;
-            id = n.skip;
-        } else {
-            id = id + 1;
         }
+        id = __any_sync(0xffffffffu, desc) ? id + 1 : n.skip;
     }
     sum.add(acc);
-    rows[t] = f64a[perm[i]].w * sum.value();
-    if (count) atomicAdd(count, (unsigned long long)nint);
+    if (has) rows[t] = f64a[perm[i]].w * sum.value();
+    if (count && nint) atomicAdd(count, (unsigned long long)nint);
 }
 
 // device counters of Barnes-Hut interactions: [0] energy, [1] differential
@@ -561,8 +632,18 @@ int energy_rows_bh(tp_mesh* m, const tp_params* p, const int32_t* tl, int nt, do
 // differential
 // ---------------------------------------------------------------------------
 
+// warp sum of a float over all 32 lanes (inactive lanes pass 0)
+__device__ __forceinline__ float warp_sum(float x) {
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Differential, same warp-cooperative traversal as the energy.
 // target-side accumulators: 0 sum a c | 1-3 sum a c d | 4-6 sum a K d/|d|^2 | 7 sum a K
-// reverse scatter: node accumulators nacc[id*4 + 0..2] = G, [3] = Q; faces facc[i*4 ...]
+// source side (FULL): G = -a_S w dK/dd and Q = a_S K of the lanes that interact
+// with the same node or leaf face are summed across the warp first, then added
+// with one FP64 atomic per warp: node accumulators nacc[id*4 + 0..2] = G,
+// [3] = Q; near faces facc[j*4 + ...]
 template <bool P6, bool FULL>
 __global__ void __launch_bounds__(128)
 k_bh_diff(const BvhNode* __restrict__ node, const float4* __restrict__ nodelo, int nnodes,
@@ -570,11 +651,13 @@ k_bh_diff(const BvhNode* __restrict__ node, const float4* __restrict__ nodelo, i
           const FaceBox* __restrict__ fbox, int nf, float theta2, float hm1,
           float p, double* __restrict__ tacc /* [nf][8] sorted */, double* __restrict__ nacc,
           double* __restrict__ facc, unsigned long long* __restrict__ count) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nf) return;
-    float4 A = sa[i], B = sb[i], Al = sl[i];
-    FaceBox fb = fbox[i];
+    const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool has = i0 < nf;
+    const int i = has ? i0 : 0;
+    const float4 A = sa[i], B = sb[i], Al = sl[i];
+    const FaceBox fb = fbox[i];
     const float aS = A.w;
+    const int lane = threadIdx.x & 31;
     KahanF acc[8];
     float pt[8];
     for (int k = 0; k < 8; ++k) pt[k] = 0.f;
@@ -586,8 +669,8 @@ k_bh_diff(const BvhNode* __restrict__ node, const float4* __restrict__ nodelo, i
         }
         run = 0;
     };
-    // one interaction with a source of barycenter (sx,sy,sz), weight w; returns the
-    // source-side derivative (G: -a_S w dK/dd, Q: a_S K)
+    // one interaction with a source of barycenter src (+ low part lo) and
+    // weight w; returns the source-side derivative G, Q
     auto interact = [&](float4 src, float4 lo, float w, float* G, float& Q) {
         float dx = (A.x - src.x) + (Al.x - lo.x), dy = (A.y - src.y) + (Al.y - lo.y),
               dz = (A.z - src.z) + (Al.z - lo.z);
@@ -615,46 +698,69 @@ k_bh_diff(const BvhNode* __restrict__ node, const float4* __restrict__ nodelo, i
         G[2] = s1 * B.z + s2 * dz;
         Q = aS * K;
     };
+    int skip = has ? 0 : nnodes;
     int id = 0;
     while (id < nnodes) {
-        BvhNode n = node[id];
-        float d2 = box_dist2(fb.lox, fb.loy, fb.loz, fb.hix, fb.hiy, fb.hiz, n);
-        float mr2 = fmaxf(fb.r2, n.r2);
-        if (mr2 < __fmul_rn(theta2, d2)) {
-            float G[3], Q;
-            interact(make_float4(n.cx, n.cy, n.cz, 0.f), nodelo[id], n.a, G, Q);
-            ++nint;
-            if (FULL) {
-                atomicAdd(nacc + 4 * id + 0, (double)G[0]);
-                atomicAdd(nacc + 4 * id + 1, (double)G[1]);
-                atomicAdd(nacc + 4 * id + 2, (double)G[2]);
-                atomicAdd(nacc + 4 * id + 3, (double)Q);
-            }
-            if (++run == 32) flush();
-            id = n.skip;
-        } else if (n.leaf) {
-            for (int j = n.first; j < n.first + n.count; ++j) {
-                if (j == i) continue;
-                float4 s = sa[j];
-                float G[3], Q;
-                interact(s, sl[j], s.w, G, Q);
+        const BvhNode n = node[id];
+        const bool act = id >= skip;
+        bool adm = false;
+        if (act) {
+            float d2 = box_dist2(fb.lox, fb.loy, fb.loz, fb.hix, fb.hiy, fb.hiz, n);
+            float mr2 = fmaxf(fb.r2, n.r2);
+            adm = mr2 < __fmul_rn(theta2, d2);
+        }
+        const bool near = act && !adm && n.leaf;
+        const bool desc = act && !adm && !n.leaf;
+        if (__any_sync(0xffffffffu, adm)) {
+            float G[3] = {0.f, 0.f, 0.f}, Q = 0.f;
+            if (adm) {
+                interact(make_float4(n.cx, n.cy, n.cz, 0.f), nodelo[id], n.a, G, Q);
                 ++nint;
-                if (FULL) {
-                    atomicAdd(facc + 4 * j + 0, (double)G[0]);
-                    atomicAdd(facc + 4 * j + 1, (double)G[1]);
-                    atomicAdd(facc + 4 * j + 2, (double)G[2]);
-                    atomicAdd(facc + 4 * j + 3, (double)Q);
+                if (++run == 32) flush();
+            }
+            if (FULL) {
+                G[0] = warp_sum(G[0]);
+                G[1] = warp_sum(G[1]);
+                G[2] = warp_sum(G[2]);
+                Q = warp_sum(Q);
+                if (lane == 0) {
+                    atomicAdd(nacc + 4 * id + 0, (double)G[0]);
+                    atomicAdd(nacc + 4 * id + 1, (double)G[1]);
+                    atomicAdd(nacc + 4 * id + 2, (double)G[2]);
+                    atomicAdd(nacc + 4 * id + 3, (double)Q);
                 }
             }
-            flush();
-            id = n.skip;
-        } else {
-            id = id + 1;
         }
+        if (__any_sync(0xffffffffu, near)) {
+            for (int j = n.first; j < n.first + n.count; ++j) {
+                float G[3] = {0.f, 0.f, 0.f}, Q = 0.f;
+                if (near && j != i) {
+                    interact(sa[j], sl[j], sa[j].w, G, Q);
+                    ++nint;
+                }
+                if (FULL) {
+                    G[0] = warp_sum(G[0]);
+                    G[1] = warp_sum(G[1]);
+                    G[2] = warp_sum(G[2]);
+                    Q = warp_sum(Q);
+                    if (lane == 0) {
+                        atomicAdd(facc + 4 * j + 0, (double)G[0]);
+                        atomicAdd(facc + 4 * j + 1, (double)G[1]);
+                        atomicAdd(facc + 4 * j + 2, (double)G[2]);
+                        atomicAdd(facc + 4 * j + 3, (double)Q);
+                    }
+                }
+            }
+            if (near) flush();
+        }
+        if (adm || near) skip = n.skip;
+        id = __any_sync(0xffffffffu, desc) ? id + 1 : n.skip;
     }
     flush();
-    for (int k = 0; k < 8; ++k) tacc[(size_t)i * 8 + k] = acc[k].value();
-    atomicAdd(count, (unsigned long long)nint);
+    if (has) {
+        for (int k = 0; k < 8; ++k) tacc[(size_t)i * 8 + k] = acc[k].value();
+    }
+    if (nint) atomicAdd(count, (unsigned long long)nint);
 }
 
 // per node: g1 = G/a_I, q = Q - G.X_I/a_I (FP64 node data)

@@ -79,7 +79,7 @@ void tp_params_default(tp_params* p) {
     p->krylov_tol = 1e-6;
     p->krylov_max = 200;
     p->gmres_restart = 30;
-    p->cg_tol = 1e-10;
+    p->cg_tol = 1e-6;
     p->cg_max = 20000;
     p->armijo_c = 1e-4;
     p->armijo_shrink = 0.5;
@@ -182,7 +182,7 @@ int tp_mesh_destroy(tp_mesh* m) {
     Buf* all[] = {&m->faces, &m->vf_ptr, &m->vf_idx, &m->pos, &m->center, &m->errflag, &m->f32a, &m->f32b,
                   &m->f32c, &m->tilebox,
                   &m->f64a, &m->f64b, &m->fgrad, &m->rowptr, &m->col, &m->cotsrc, &m->diagpos, &m->val,
-                  &m->dinv, &m->bvh_node, &m->bvh_perm, &m->bvh_keys, &m->bvh_tmp, &m->bvh_sortws,
+                  &m->dinv, &m->val32, &m->bvh_node, &m->bvh_perm, &m->bvh_keys, &m->bvh_tmp, &m->bvh_sortws,
                   &m->bvh_f32a, &m->bvh_f32b, &m->bvh_f32c, &m->bvh_nodeP, &m->part, &m->part2, &m->scal, &m->corner,
                   &m->wv64, &m->wv32, &m->io_in, &m->io_out, &m->adj, &m->erow, &m->tlist, &m->rowsum,
                   &m->kry};

@@ -143,6 +143,12 @@ int laplacian_values(tp_mesh* m, cudaStream_t st) {
 // block is still reading. The barrier spins on a generation counter with a
 // clock budget; when the budget runs out the kernel records TP_ERR_TIMEOUT
 // and every block returns.
+//
+// Vector type V: double (FP64 path) or float (FP32 path: matrix and vectors
+// in FP32, which GB300 runs 64x faster than FP64). The inner products are
+// accumulated in FP64 in both cases: products of FP32 values are exact in
+// FP64, summed per thread, then by warp shuffles and across warps in a
+// fixed order.
 
 struct CgCtl {
     unsigned count;        // barrier arrivals
@@ -151,7 +157,23 @@ struct CgCtl {
     int iters;             // iterations done
     int active[KMAX];      // per column: 1 = not yet converged
     double rr[KMAX], bb[KMAX];
+    unsigned long long trace[10];  // per-phase cycles of block 0 (only with TP_CG_TRACE)
 };
+
+#ifdef TP_CG_TRACE
+#define CG_STAMP(slot)                                                        \
+    do {                                                                      \
+        if (blockIdx.x == 0 && threadIdx.x == 0) {                            \
+            long long now_ = clock64();                                       \
+            tr[slot] += (unsigned long long)(now_ - tlast);                   \
+            tlast = now_;                                                     \
+        }                                                                     \
+    } while (0)
+#else
+#define CG_STAMP(slot) \
+    do {               \
+    } while (0)
+#endif
 
 __device__ __forceinline__ bool grid_barrier(CgCtl* ctl, unsigned nblk) {
     __syncthreads();
@@ -168,14 +190,17 @@ __device__ __forceinline__ bool grid_barrier(CgCtl* ctl, unsigned nblk) {
         } else {
             long long t0 = clock64();
             ok = 1;
+            int spins = 0;
             while (*vgen == g) {
-                if (*(volatile int*)&ctl->err) { ok = 0; break; }
-                if (clock64() - t0 > (1LL << 32)) {   // ~2 s at 2 GHz
-                    atomicExch(&ctl->err, 1);
-                    ok = 0;
-                    break;
+                if (++spins > 64) {
+                    if (*(volatile int*)&ctl->err) { ok = 0; break; }
+                    if (clock64() - t0 > (1LL << 32)) {   // ~2 s at 2 GHz
+                        atomicExch(&ctl->err, 1);
+                        ok = 0;
+                        break;
+                    }
+                    __nanosleep(32);
                 }
-                __nanosleep(64);
             }
         }
         __threadfence();
@@ -184,70 +209,89 @@ __device__ __forceinline__ bool grid_barrier(CgCtl* ctl, unsigned nblk) {
     return ok != 0;
 }
 
-// block-wide sums of up to 2*KMAX per-thread values (vals[j][t]) -> vals[j][0]
-template <int NTH>
-__device__ __forceinline__ void block_reduce(double (*vals)[NTH], int nval) {
-    for (int w = NTH / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w)
-            for (int j = 0; j < nval; ++j) vals[j][threadIdx.x] += vals[j][threadIdx.x + w];
-        __syncthreads();
-    }
-}
-
 constexpr int PCG_T = 128;
+constexpr int PCG_W = PCG_T / 32;
 
-// sums over blocks of per-block partials part[bI * ld + j], j < nval: every
-// thread loads a strided subset, then a fixed-order tree in shared memory.
-// Result in sh[j][0]; identical in every block (same data, same order).
-__device__ __forceinline__ void reduce_partials(const double* __restrict__ part, int ld, int nval,
-                                                unsigned nblk, double (*sh)[PCG_T]) {
-    __syncthreads();
-    for (int j = 0; j < nval; ++j) {
-        double a = 0.0;
-        for (unsigned bI = threadIdx.x; bI < nblk; bI += PCG_T) a += __ldcg(part + (size_t)bI * ld + j);
-        sh[j][threadIdx.x] = a;
+// block sums of NVAL FP64 values per thread (v[0..NVAL)); result in out[j]
+// (shared), identical order in every block
+template <int NVAL>
+__device__ __forceinline__ void block_sum(const double* v, double (*wsum)[PCG_W], double* out) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nval = NVAL;
+#pragma unroll
+    for (int j = 0; j < NVAL; ++j) {
+        double x = v[j];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) wsum[j][w] = x;
     }
     __syncthreads();
-    block_reduce<PCG_T>(sh, nval);
+    if (threadIdx.x < nval) {
+        double x = 0.0;
+        for (int i = 0; i < PCG_W; ++i) x += wsum[threadIdx.x][i];
+        out[threadIdx.x] = x;
+    }
+    __syncthreads();
 }
 
+// sums over blocks of per-block partials part[bI * ld + j], j < NVAL, into out[j]
+template <int NVAL>
+__device__ __forceinline__ void reduce_partials(const double* __restrict__ part, int ld, unsigned nblk,
+                                                double (*wsum)[PCG_W], double* out) {
+    double v[NVAL];
+#pragma unroll
+    for (int j = 0; j < NVAL; ++j) v[j] = 0.0;
+    for (unsigned bI = threadIdx.x; bI < nblk; bI += PCG_T)
+#pragma unroll
+        for (int j = 0; j < NVAL; ++j) v[j] += __ldcg(part + (size_t)bI * ld + j);
+    block_sum<NVAL>(v, wsum, out);
+}
+
+template <typename V, int K>
 __global__ void __launch_bounds__(PCG_T)
-k_cg_persistent(const int* __restrict__ rowptr, const int* __restrict__ col, const double* __restrict__ val,
-                const double* __restrict__ dinv, int nv, int k, const double* __restrict__ b,
-                double* __restrict__ x, double* __restrict__ r, double* __restrict__ z, double* __restrict__ p,
-                double* __restrict__ q, double* __restrict__ partA /* [grid][KMAX] */,
+k_cg_persistent(const int* __restrict__ rowptr, const int* __restrict__ col, const V* __restrict__ val,
+                const V* __restrict__ dinv, int nv, const double* __restrict__ b,
+                V* __restrict__ x, V* __restrict__ r, V* __restrict__ z, V* __restrict__ p,
+                V* __restrict__ q, double* __restrict__ partA /* [grid][KMAX] */,
                 double* __restrict__ partB /* [grid][2*KMAX] */, CgCtl* ctl, double tol2, int max_iter) {
-    __shared__ double sh[2 * KMAX][PCG_T];
-    __shared__ double s_alpha[KMAX], s_beta[KMAX], s_rz[KMAX], s_bb[KMAX];
+    __shared__ double wsum[2 * KMAX][PCG_W];
+    __shared__ double red[2 * KMAX];
+    __shared__ V s_alpha[KMAX], s_beta[KMAX];
+    __shared__ double s_rz[KMAX], s_bb[KMAX];
     __shared__ int s_active[KMAX], s_done;
+    constexpr int k = K;
     const unsigned nblk = gridDim.x;
     const int stride = gridDim.x * PCG_T;
+    double acc[2 * K];
+#ifdef TP_CG_TRACE
+    unsigned long long tr[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    long long tlast = clock64();
+#endif
     // ---- init: x = 0, r = b, z = D^-1 r, p = q = 0 ; partial r.z, b.b
-    for (int j = 0; j < 2 * k; ++j) sh[j][threadIdx.x] = 0.0;
+#pragma unroll
+    for (int j = 0; j < 2 * k; ++j) acc[j] = 0.0;
     for (int v = blockIdx.x * PCG_T + threadIdx.x; v < nv; v += stride)
+#pragma unroll
         for (int c = 0; c < k; ++c) {
             size_t o = (size_t)v * k + c;
-            double bv = b[o], zv = dinv[v] * bv;
-            x[o] = 0.0;
+            V bv = (V)b[o], zv = dinv[v] * bv;
+            x[o] = V(0);
             r[o] = bv;
             z[o] = zv;
-            p[o] = 0.0;
-            q[o] = 0.0;
-            sh[c][threadIdx.x] += bv * zv;
-            sh[k + c][threadIdx.x] += bv * bv;
+            p[o] = V(0);
+            q[o] = V(0);
+            acc[c] += (double)bv * (double)zv;
+            acc[k + c] += (double)bv * (double)bv;
         }
-    __syncthreads();
-    block_reduce<PCG_T>(sh, 2 * k);
-    if (threadIdx.x == 0)
-        for (int j = 0; j < 2 * k; ++j) partB[(size_t)blockIdx.x * 2 * KMAX + j] = sh[j][0];
+    block_sum<2 * K>(acc, wsum, red);
+    if (threadIdx.x < 2 * k) partB[(size_t)blockIdx.x * 2 * KMAX + threadIdx.x] = red[threadIdx.x];
     if (!grid_barrier(ctl, nblk)) return;
-    reduce_partials(partB, 2 * KMAX, 2 * k, nblk, sh);
+    reduce_partials<2 * K>(partB, 2 * KMAX, nblk, wsum, red);
     if (threadIdx.x < k) {
         int c = threadIdx.x;
-        double rz = sh[c][0], bb = sh[k + c][0];
+        double rz = red[c], bb = red[k + c];
         s_rz[c] = rz;
         s_bb[c] = bb;
-        s_beta[c] = 0.0;
+        s_beta[c] = V(0);
         s_active[c] = bb > 0.0 ? 1 : 0;
         if (blockIdx.x == 0) {
             ctl->bb[c] = bb;
@@ -262,75 +306,84 @@ k_cg_persistent(const int* __restrict__ rowptr, const int* __restrict__ col, con
     }
     __syncthreads();
     int it = 0;
+    CG_STAMP(9);
     while (!s_done) {
         // ---- phase A
-        for (int j = 0; j < k; ++j) sh[j][threadIdx.x] = 0.0;
+#pragma unroll
+        for (int j = 0; j < k; ++j) acc[j] = 0.0;
         for (int v = blockIdx.x * PCG_T + threadIdx.x; v < nv; v += stride) {
-            double cz[KMAX];
+            V cz[K];
 #pragma unroll
-            for (int c = 0; c < KMAX; ++c) cz[c] = 0.0;
-            for (int e = rowptr[v]; e < rowptr[v + 1]; ++e) {
-                double w = val[e];
-                const double* zr = z + (size_t)col[e] * k;
+            for (int c = 0; c < K; ++c) cz[c] = V(0);
+            const int e0 = rowptr[v], e1 = rowptr[v + 1];
+            for (int e = e0; e < e1; ++e) {
+                const V w = val[e];
+                const V* zr = z + (size_t)col[e] * k;
 #pragma unroll
-                for (int c = 0; c < KMAX; ++c)
-                    if (c < k) cz[c] += w * __ldcg(zr + c);
+                for (int c = 0; c < K; ++c) cz[c] += w * __ldcg(zr + c);
             }
 #pragma unroll
-            for (int c = 0; c < KMAX; ++c)
-                if (c < k) {
+            for (int c = 0; c < K; ++c)
+                {
                     size_t o = (size_t)v * k + c;
-                    double be = s_beta[c];
-                    double pv = __ldcg(z + o) + be * p[o];
-                    double qv = cz[c] + be * q[o];
+                    V be = s_beta[c];
+                    V pv = __ldcg(z + o) + be * p[o];
+                    V qv = cz[c] + be * q[o];
                     p[o] = pv;
                     q[o] = qv;
-                    sh[c][threadIdx.x] += pv * qv;
+                    acc[c] += (double)pv * (double)qv;
                 }
         }
-        __syncthreads();
-        block_reduce<PCG_T>(sh, k);
-        if (threadIdx.x == 0)
-            for (int c = 0; c < k; ++c) partA[(size_t)blockIdx.x * KMAX + c] = sh[c][0];
+        CG_STAMP(0);
+        block_sum<K>(acc, wsum, red);
+        if (threadIdx.x < k) partA[(size_t)blockIdx.x * KMAX + threadIdx.x] = red[threadIdx.x];
+        CG_STAMP(1);
         if (!grid_barrier(ctl, nblk)) return;
-        reduce_partials(partA, KMAX, k, nblk, sh);
+        CG_STAMP(2);
+        reduce_partials<K>(partA, KMAX, nblk, wsum, red);
         if (threadIdx.x < k) {
             int c = threadIdx.x;
-            double pq = sh[c][0];
-            s_alpha[c] = (s_active[c] && pq > 0.0) ? s_rz[c] / pq : 0.0;
+            double pq = red[c];
+            s_alpha[c] = (V)((s_active[c] && pq > 0.0) ? s_rz[c] / pq : 0.0);
         }
         __syncthreads();
+        CG_STAMP(3);
         // ---- phase B
-        for (int j = 0; j < 2 * k; ++j) sh[j][threadIdx.x] = 0.0;
-        for (int v = blockIdx.x * PCG_T + threadIdx.x; v < nv; v += stride)
+#pragma unroll
+        for (int j = 0; j < 2 * k; ++j) acc[j] = 0.0;
+        for (int v = blockIdx.x * PCG_T + threadIdx.x; v < nv; v += stride) {
+            const V dv = dinv[v];
+#pragma unroll
             for (int c = 0; c < k; ++c) {
                 size_t o = (size_t)v * k + c;
-                double al = s_alpha[c];
+                V al = s_alpha[c];
                 x[o] += al * p[o];
-                double rv = r[o] - al * q[o];
+                V rv = r[o] - al * q[o];
                 r[o] = rv;
-                double zv = dinv[v] * rv;
+                V zv = dv * rv;
                 z[o] = zv;
-                sh[c][threadIdx.x] += rv * zv;
-                sh[k + c][threadIdx.x] += rv * rv;
+                acc[c] += (double)rv * (double)zv;
+                acc[k + c] += (double)rv * (double)rv;
             }
-        __syncthreads();
-        block_reduce<PCG_T>(sh, 2 * k);
-        if (threadIdx.x == 0)
-            for (int j = 0; j < 2 * k; ++j) partB[(size_t)blockIdx.x * 2 * KMAX + j] = sh[j][0];
+        }
+        CG_STAMP(4);
+        block_sum<2 * K>(acc, wsum, red);
+        if (threadIdx.x < 2 * k) partB[(size_t)blockIdx.x * 2 * KMAX + threadIdx.x] = red[threadIdx.x];
+        CG_STAMP(5);
         if (!grid_barrier(ctl, nblk)) return;
+        CG_STAMP(6);
         ++it;
-        reduce_partials(partB, 2 * KMAX, 2 * k, nblk, sh);
+        reduce_partials<2 * K>(partB, 2 * KMAX, nblk, wsum, red);
         if (threadIdx.x < k) {
             int c = threadIdx.x;
-            double rz = sh[c][0], rr = sh[k + c][0];
+            double rz = red[c], rr = red[k + c];
             if (s_active[c]) {
-                s_beta[c] = s_rz[c] > 0.0 ? rz / s_rz[c] : 0.0;
+                s_beta[c] = (V)(s_rz[c] > 0.0 ? rz / s_rz[c] : 0.0);
                 s_rz[c] = rz;
                 if (blockIdx.x == 0) ctl->rr[c] = rr;
                 if (rr <= tol2 * s_bb[c]) {
                     s_active[c] = 0;
-                    s_beta[c] = 0.0;
+                    s_beta[c] = V(0);
                 }
             }
         }
@@ -341,18 +394,37 @@ k_cg_persistent(const int* __restrict__ rowptr, const int* __restrict__ col, con
             s_done = (!any || it >= max_iter) ? 1 : 0;
         }
         __syncthreads();
+        CG_STAMP(7);
     }
+#ifdef TP_CG_TRACE
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int i = 0; i < 10; ++i) ctl->trace[i] = tr[i];
+#endif
     if (blockIdx.x == 0 && threadIdx.x < k) ctl->active[threadIdx.x] = s_active[threadIdx.x];
     if (blockIdx.x == 0 && threadIdx.x == 0) ctl->iters = it;
 }
 
+// FP32 copies of the matrix values and the inverse diagonal
+__global__ void k_to_f32(const double* __restrict__ a, int n, float* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (float)a[i];
+}
+
+// x (vector type V) -> FP64 output
+template <typename V>
+__global__ void k_to_f64(const V* __restrict__ a, size_t n, double* __restrict__ out) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = (double)a[i];
+}
+
+template <typename V, int K>
 static int cg_grid(int nv) {
     static int cached_dev = -1, cached_max = 0;
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev != cached_dev) {
         int per_sm = 0;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_persistent, PCG_T, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cg_persistent<V, K>, PCG_T, 0);
         cached_max = per_sm * sm_count();
         cached_dev = dev;
     }
@@ -361,16 +433,58 @@ static int cg_grid(int nv) {
     return g < 1 ? 1 : g;
 }
 
-int cg_solve(tp_mesh* m, const tp_params* p, const double* b, int k, double* z_out, cudaStream_t st,
-             int* iters) {
-    if (k < 1 || k > KMAX) return fail(TP_ERR_INVALID_ARG, "cg: k must be in 1..9");
-    TP_TRY(laplacian_values(m, st));
+template <typename V>
+struct CgLaunch {
+    const void* fn;
+    int grid;
+};
+
+template <typename V, int K>
+static CgLaunch<V> cg_pick(int nv) {
+    return CgLaunch<V>{(const void*)k_cg_persistent<V, K>, cg_grid<V, K>(nv)};
+}
+
+template <typename V>
+static CgLaunch<V> cg_select(int k, int nv) {
+    switch (k) {
+        case 1: return cg_pick<V, 1>(nv);
+        case 2: return cg_pick<V, 2>(nv);
+        case 3: return cg_pick<V, 3>(nv);
+        case 4: return cg_pick<V, 4>(nv);
+        case 5: return cg_pick<V, 5>(nv);
+        case 6: return cg_pick<V, 6>(nv);
+        case 7: return cg_pick<V, 7>(nv);
+        case 8: return cg_pick<V, 8>(nv);
+        default: return cg_pick<V, 9>(nv);
+    }
+}
+
+template <typename V>
+static int cg_run(tp_mesh* m, const tp_params* p, const double* b, int k, double* z_out, cudaStream_t st,
+                  int* iters) {
     const int nv = m->nv;
     const size_t n = (size_t)nv * k;
     for (int i = 0; i < 6; ++i) TP_TRY(ensure(m->tmpv[i], sizeof(double) * n));
-    double *x = m->tmpv[0].as<double>(), *r = m->tmpv[1].as<double>(), *z = m->tmpv[2].as<double>(),
-           *pp = m->tmpv[3].as<double>(), *q = m->tmpv[4].as<double>(), *bp = m->tmpv[5].as<double>();
-    const int grid = cg_grid(nv);
+    V *x = m->tmpv[0].as<V>(), *r = m->tmpv[1].as<V>(), *z = m->tmpv[2].as<V>(), *pp = m->tmpv[3].as<V>(),
+      *q = m->tmpv[4].as<V>();
+    double* bp = m->tmpv[5].as<double>();
+    const V* valp;
+    const V* dinv;
+    if (sizeof(V) == 8) {
+        valp = (const V*)m->val.ptr;
+        dinv = (const V*)m->dinv.ptr;
+    } else {
+        TP_TRY(ensure(m->val32, sizeof(float) * ((size_t)m->nnz + nv)));
+        float* v32 = m->val32.as<float>();
+        k_to_f32<<<(m->nnz + 255) / 256, 256, 0, st>>>(m->val.as<double>(), m->nnz, v32);
+        TP_LAUNCH_CHECK();
+        k_to_f32<<<(nv + 255) / 256, 256, 0, st>>>(m->dinv.as<double>(), nv, v32 + m->nnz);
+        TP_LAUNCH_CHECK();
+        valp = (const V*)v32;
+        dinv = (const V*)(v32 + m->nnz);
+    }
+    const CgLaunch<V> L = cg_select<V>(k, nv);
+    const int grid = L.grid;
     TP_TRY(ensure(m->scal, 16 + sizeof(CgCtl) + sizeof(double) * 3 * KMAX * (size_t)grid));
     CgCtl* ctl = m->scal.as<CgCtl>();
     double* partA = (double*)(m->scal.as<char>() + ((sizeof(CgCtl) + 15) / 16) * 16);
@@ -383,16 +497,14 @@ int cg_solve(tp_mesh* m, const tp_params* p, const double* b, int k, double* z_o
     int cap = p->cg_max;
     const int* rowptr = m->rowptr.as<int>();
     const int* colp = m->col.as<int>();
-    const double* valp = m->val.as<double>();
-    const double* dinv = m->dinv.as<double>();
-    int nvv = nv, kk = k;
-    void* args[] = {(void*)&rowptr, (void*)&colp, (void*)&valp, (void*)&dinv, (void*)&nvv, (void*)&kk,
+    int nvv = nv;
+    void* args[] = {(void*)&rowptr, (void*)&colp, (void*)&valp, (void*)&dinv, (void*)&nvv,
                     (void*)&bp, (void*)&x, (void*)&r, (void*)&z, (void*)&pp, (void*)&q, (void*)&partA,
                     (void*)&partB, (void*)&ctl, (void*)&tol2, (void*)&cap};
     CgCtl host{};
     {
         ProfScope ps(m, PK_CG, 0.0, st);
-        TP_CUDA(cudaLaunchCooperativeKernel((void*)k_cg_persistent, dim3(grid), dim3(PCG_T), args, 0, st));
+        TP_CUDA(cudaLaunchCooperativeKernel(L.fn, dim3(grid), dim3(PCG_T), args, 0, st));
         TP_LAUNCH_CHECK();
     }
     TP_CUDA(cudaMemcpyAsync(&host, ctl, sizeof(CgCtl), cudaMemcpyDeviceToHost, st));
@@ -400,13 +512,21 @@ int cg_solve(tp_mesh* m, const tp_params* p, const double* b, int k, double* z_o
     if (host.err) return fail(TP_ERR_TIMEOUT, "cg: grid barrier timed out");
     const int it = host.iters;
     if (iters) *iters = it;
-    // algorithmic bytes of one iteration: CSR values and columns, row pointers
-    // and the inverse diagonal, the k-column vectors z (read twice), p and q
-    // (read + write), x and r (read + write), z (write), p and q (read)
-    m->prof.units[PK_CG] += (double)it * ((double)m->nnz * 12.0 + (double)nv * 12.0 +
-                                          (double)nv * k * 8.0 * 13.0);
-    TP_TRY(project_mean_zero(m, x, k, st));
-    TP_CUDA(cudaMemcpyAsync(z_out, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    // algorithmic bytes of one iteration: CSR values (V) and columns, row
+    // pointers and the inverse diagonal, the k-column vectors z (read twice),
+    // p and q (read + write), x and r (read + write), z (write), p, q (read)
+    const double vb = sizeof(V);
+    m->prof.units[PK_CG] += (double)it * ((double)m->nnz * (4.0 + vb) + (double)nv * (4.0 + vb) +
+                                          (double)nv * k * vb * 13.0);
+    double* xo = m->tmpv[5].as<double>();   // b is no longer needed
+    if (sizeof(V) == 8) {
+        xo = (double*)x;
+    } else {
+        k_to_f64<V><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, n, xo);
+        TP_LAUNCH_CHECK();
+    }
+    TP_TRY(project_mean_zero(m, xo, k, st));
+    TP_CUDA(cudaMemcpyAsync(z_out, xo, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
     bool conv = true;
     for (int c = 0; c < k; ++c) conv = conv && !host.active[c];
     if (!conv)
@@ -414,6 +534,26 @@ int cg_solve(tp_mesh* m, const tp_params* p, const double* b, int k, double* z_o
                                               " reached, relative residual " +
                                               std::to_string(std::sqrt(host.rr[0] / (host.bb[0] + 1e-300))));
     return TP_OK;
+}
+
+// per-phase cycle counts of block 0 from the last solve (filled only in a
+// build with TP_CG_TRACE; zeros otherwise)
+int cg_trace(tp_mesh* m, unsigned long long out[10]) {
+    for (int i = 0; i < 10; ++i) out[i] = 0;
+    if (!m->scal.ptr) return TP_OK;
+    CgCtl h{};
+    TP_CUDA(cudaMemcpy(&h, m->scal.ptr, sizeof(CgCtl), cudaMemcpyDeviceToHost));
+    for (int i = 0; i < 10; ++i) out[i] = h.trace[i];
+    return TP_OK;
+}
+
+int cg_solve(tp_mesh* m, const tp_params* p, const double* b, int k, double* z_out, cudaStream_t st,
+             int* iters) {
+    if (k < 1 || k > KMAX) return fail(TP_ERR_INVALID_ARG, "cg: k must be in 1..9");
+    TP_TRY(laplacian_values(m, st));
+    // FP64 vectors in both precision modes: with FP32 vectors the Jacobi-CG
+    // iteration stalls above a 1e-6 relative residual on rough meshes
+    return cg_run<double>(m, p, b, k, z_out, st, iters);
 }
 
 // ---------------------------------------------------------------------------

@@ -48,16 +48,21 @@ int differential_dev(tp_mesh* m, const tp_params* p, double* dE, double* E_host,
 }
 
 // z = C^+ L^{2-s} C^+ b (§5.2); b, z [nv][k] device
+// With strict = false (inside flexible GMRES) an inner CG solve that stops at
+// its iteration cap still returns its iterate: the outer method only needs
+// some fixed-quality approximation of the preconditioner.
 int precond_apply_dev(tp_mesh* m, const tp_params* p, const double* b, int k, double* z,
-                      cudaStream_t st, int* cg_iters) {
+                      cudaStream_t st, int* cg_iters, bool strict) {
     const size_t n = (size_t)m->nv * k;
     TP_TRY(ensure(m->prec[0], sizeof(double) * n));
     TP_TRY(ensure(m->prec[1], sizeof(double) * n));
     int it1 = 0, it2 = 0;
-    TP_TRY(cg_solve(m, p, b, k, m->prec[0].as<double>(), st, &it1));
+    int s1 = cg_solve(m, p, b, k, m->prec[0].as<double>(), st, &it1);
+    if (s1 != TP_OK && (strict || s1 != TP_ERR_NOT_CONVERGED)) return s1;
     TP_TRY(apply_direct(m, p, TP_OP_L, m->prec[0].as<double>(), k, m->prec[1].as<double>(), st));
     TP_TRY(project_mean_zero(m, m->prec[1].as<double>(), k, st));
-    TP_TRY(cg_solve(m, p, m->prec[1].as<double>(), k, z, st, &it2));
+    int s2 = cg_solve(m, p, m->prec[1].as<double>(), k, z, st, &it2);
+    if (s2 != TP_OK && (strict || s2 != TP_ERR_NOT_CONVERGED)) return s2;
     if (cg_iters) *cg_iters += it1 + it2;
     return TP_OK;
 }
@@ -205,7 +210,7 @@ static int fgmres_multi(tp_mesh* m, const tp_params* p, int ns, const double* co
                 wout.push_back(S[i].w);
             }
             TP_TRY(pack(vin, nv, P0, st));
-            TP_TRY(precond_apply_dev(m, p, P0, 3 * na, P1, st, &ks->cg_iters));
+            TP_TRY(precond_apply_dev(m, p, P0, 3 * na, P1, st, &ks->cg_iters, false));
             TP_TRY(unpack(P1, nv, zout, st));
             TP_TRY(apply_A_packed(m, p, P1, 3 * na, P2, st));
             TP_TRY(unpack(P2, nv, wout, st));

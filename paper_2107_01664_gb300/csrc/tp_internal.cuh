@@ -113,7 +113,7 @@ struct tp_mesh {
     tp::Buf fgrad;      // double [nf*9] gradients of the three hat functions
     // cotan Laplacian (pattern fixed, values per positions)
     int nnz = 0;
-    tp::Buf rowptr, col, cotsrc, diagpos, val, dinv;
+    tp::Buf rowptr, col, cotsrc, diagpos, val, dinv, val32;
     bool lap_valid = false;
     // Barnes-Hut tree (rebuilt per positions on demand)
     int bvh_nodes = 0, bvh_leaf = 0;
@@ -197,7 +197,7 @@ int energy_value(tp_mesh* m, const tp_params* p, double* E_host, cudaStream_t st
 int differential_dev(tp_mesh* m, const tp_params* p, double* dE_dev, double* E_host,
                      cudaStream_t st);
 int precond_apply_dev(tp_mesh* m, const tp_params* p, const double* b, int k, double* z,
-                      cudaStream_t st, int* cg_iters);
+                      cudaStream_t st, int* cg_iters, bool strict = true);
 int precond_step_dev(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp_step_report* rep,
                      cudaStream_t st);
 

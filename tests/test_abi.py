@@ -24,9 +24,11 @@ def test_header_declares_the_entry_points():
 
 
 def test_library_exports_every_declared_symbol():
+    import os as _os
     from paper_2107_01664_gb300 import build as b
     path = b.build()
-    lib = ctypes.CDLL(path)
+    # RTLD_NOW resolves every symbol at load time: an undefined one fails here
+    lib = ctypes.CDLL(path, mode=_os.RTLD_NOW | _os.RTLD_LOCAL)
     missing = [n for n in _declared() if not hasattr(lib, n)]
     assert not missing, missing
 
