@@ -205,6 +205,25 @@ int tp_profile_read(tp_mesh* m, tp_kernel_stat* out, int max, int* n);
 /* Number of CUDA kernels this library has launched in this process. */
 unsigned long long tp_launch_count(void);
 
+/* Direct energy E of Eq. 10 (FP32 pair terms, compensated sums, FP64
+ * reduction) for callers that cannot allocate device memory: code inside a
+ * CUDA graph being captured, plug-ins of hosts that own the device
+ * allocator, real-time loops that must not take allocator locks. The paper
+ * has no counterpart of this entry point: it is a deployment convenience.
+ *   pos   device float64 [nv][3], faces device int32 [nf][3] (faces with an
+ *         index outside 0..nv-1 are left out), E device float64 [1] (output),
+ *         all on the calling thread's current CUDA device; p > 2.
+ * Allocates nothing: every intermediate lives in one static device array of
+ * about 5.3 MB that each GPU loading the library holds until the process
+ * exits. At most 32768 faces (larger meshes: TP_ERR_INVALID_ARG, use
+ * tp_mesh_create + tp_energy). The first call on a device looks up that
+ * array's device address; make it before any stream capture. Calls share
+ * the array: calls whose kernels overlap on the GPU (other streams, other
+ * threads) race, so the caller must serialise them. Asynchronous on
+ * `stream`; *E is valid once the stream has passed the call. */
+int tp_energy_noalloc(const double* pos, int nv, const int32_t* faces, int nf,
+                      double p, double* E, void* stream);
+
 /* Thread-local description of the last error of this thread ("" if none). */
 const char* tp_last_error(void);
 

@@ -26,6 +26,7 @@ __all__ = [
     "tp_mesh_footprint_bytes", "tp_energy", "tp_energy_rows", "tp_differential",
     "fractional_apply", "cotan_solve", "precond_apply", "precond_step", "TangentPointEnergy",
     "lib_path", "lib", "tp_kernel_stat", "tp_profile_enable", "tp_profile_read", "tp_launch_count",
+    "tp_energy_noalloc",
 ]
 
 TP_OK, TP_ERR_INVALID_ARG, TP_ERR_DEGENERATE, TP_ERR_OOM = 0, 1, 2, 3
@@ -111,6 +112,7 @@ def lib():
         "tp_profile_enable": (c_int, [vp, c_int]),
         "tp_profile_read": (c_int, [vp, P(tp_kernel_stat), c_int, P(c_int)]),
         "tp_launch_count": (ctypes.c_ulonglong, []),
+        "tp_energy_noalloc": (c_int, [vp, c_int, vp, c_int, c_double, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -334,6 +336,15 @@ def tp_profile_read(mesh: Mesh) -> dict:
 
 def tp_launch_count() -> int:
     return int(lib().tp_launch_count())
+
+
+def tp_energy_noalloc(positions, faces, E_out, p: float = 6.0) -> None:
+    """Direct energy into the CUDA tensor E_out (float64, 1 element) without
+    any device allocation; positions [nv,3] float64 and faces [nf,3] int32
+    must be CUDA tensors on the current device (at most 32768 faces)."""
+    _check(lib().tp_energy_noalloc(ctypes.c_void_p(positions.data_ptr()), int(positions.shape[0]),
+                                   ctypes.c_void_p(faces.data_ptr()), int(faces.shape[0]), float(p),
+                                   ctypes.c_void_p(E_out.data_ptr()), _stream_ptr(positions)))
 
 
 # ---------------------------------------------------------------------------
