@@ -53,7 +53,7 @@ FP32_LANES_PER_SM = 128
 
 def step_params(tp):
     return tp.params(theta=0.0, precision=tp.TP_PREC_FP32, krylov_tol=1e-5, krylov_max=60,
-                     gmres_restart=30, cg_tol=1e-8, cg_max=20000, proj_iters=1)
+                     gmres_restart=30, cg_tol=1e-6, cg_max=20000, proj_iters=1)
 
 
 def bh_params(tp):

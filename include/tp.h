@@ -75,7 +75,6 @@ typedef struct tp_params {
     int    leaf_size;     /* BVH leaf size l, 1..32; paper default 8 (§4.1) */
     int    precision;     /* TP_PREC_FP32 or TP_PREC_FP64 */
     int    bh_diff_mode;  /* TP_BH_DIFF_FULL or TP_BH_DIFF_LITERAL */
-    int    bh_apply;      /* 1 = Barnes-Hut traversal also for fractional_apply when theta > 0 */
     double krylov_tol;    /* relative residual of the outer GMRES solves */
     int    krylov_max;    /* iteration cap of one GMRES solve (all restarts) */
     int    gmres_restart; /* restart length m */
@@ -165,7 +164,8 @@ int tp_differential(tp_mesh* m, const tp_params* p, double* dE, int ptr_kind,
                     double* E_out, void* stream);
 
 /* y = O v for op in TP_OP_* and k columns (1 <= k <= 9), each column
- * separately (the vector operator O_3 of §3.2.1 for k = 3), through the
+ * separately, always by the direct all-pairs sums (theta is not used here;
+ * the vector operator O_3 of §3.2.1 for k = 3), through the
  * kernel-matrix form of §5.1.1-5.1.3 and Appendix A:
  *   O v = 2 W^T [diag(diag(a)^-1 H a) - H] W v,
  * W = diag(a) D (op B) or the area-weighted face average (ops B0, L). */

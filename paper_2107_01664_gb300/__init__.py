@@ -48,7 +48,7 @@ class TpError(RuntimeError):
 class tp_params(ctypes.Structure):
     _fields_ = [
         ("p", ctypes.c_double), ("theta", ctypes.c_double), ("leaf_size", ctypes.c_int),
-        ("precision", ctypes.c_int), ("bh_diff_mode", ctypes.c_int), ("bh_apply", ctypes.c_int),
+        ("precision", ctypes.c_int), ("bh_diff_mode", ctypes.c_int),
         ("krylov_tol", ctypes.c_double), ("krylov_max", ctypes.c_int), ("gmres_restart", ctypes.c_int),
         ("cg_tol", ctypes.c_double), ("cg_max", ctypes.c_int), ("armijo_c", ctypes.c_double),
         ("armijo_shrink", ctypes.c_double), ("tau0", ctypes.c_double), ("ls_max", ctypes.c_int),

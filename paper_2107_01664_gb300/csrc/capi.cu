@@ -75,7 +75,6 @@ void tp_params_default(tp_params* p) {
     p->leaf_size = 8;
     p->precision = TP_PREC_FP32;
     p->bh_diff_mode = TP_BH_DIFF_FULL;
-    p->bh_apply = 0;
     p->krylov_tol = 1e-6;
     p->krylov_max = 200;
     p->gmres_restart = 30;

@@ -156,6 +156,7 @@ struct CgCtl {
     int err;               // 0 ok, 1 barrier timeout
     int iters;             // iterations done
     int active[KMAX];      // per column: 1 = not yet converged
+    int gdone[KMAX];       // per column group: 1 = all its columns converged (or the cap hit)
     double rr[KMAX], bb[KMAX];
     unsigned long long trace[10];  // per-phase cycles of block 0 (only with TP_CG_TRACE)
 };
@@ -175,24 +176,27 @@ struct CgCtl {
     } while (0)
 #endif
 
+// arrive with release semantics, then poll with acquire loads; the last
+// arrival resets the counter and publishes the next generation
 __device__ __forceinline__ bool grid_barrier(CgCtl* ctl, unsigned nblk) {
     __syncthreads();
     __shared__ int ok;
     if (threadIdx.x == 0) {
-        volatile unsigned* vgen = &ctl->gen;
-        unsigned g = *vgen;
-        __threadfence();
-        if (atomicAdd(&ctl->count, 1u) == nblk - 1) {
-            ctl->count = 0;
-            __threadfence();
-            atomicAdd(&ctl->gen, 1u);
-            ok = 1;
+        unsigned g;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(&ctl->gen) : "memory");
+        unsigned prev;
+        asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(prev) : "l"(&ctl->count) : "memory");
+        ok = 1;
+        if (prev == nblk - 1) {
+            asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(&ctl->count) : "memory");
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&ctl->gen) : "memory");
         } else {
             long long t0 = clock64();
-            ok = 1;
-            int spins = 0;
-            while (*vgen == g) {
-                if (++spins > 64) {
+            unsigned cur;
+            for (int spins = 0;; ++spins) {
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&ctl->gen) : "memory");
+                if (cur != g) break;
+                if (spins > 64) {
                     if (*(volatile int*)&ctl->err) { ok = 0; break; }
                     if (clock64() - t0 > (1LL << 32)) {   // ~2 s at 2 GHz
                         atomicExch(&ctl->err, 1);
@@ -203,7 +207,6 @@ __device__ __forceinline__ bool grid_barrier(CgCtl* ctl, unsigned nblk) {
                 }
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return ok != 0;
@@ -211,84 +214,144 @@ __device__ __forceinline__ bool grid_barrier(CgCtl* ctl, unsigned nblk) {
 
 constexpr int PCG_T = 128;
 constexpr int PCG_W = PCG_T / 32;
+constexpr int CGRP = 3;   // columns per block (column group)
 
-// block sums of NVAL FP64 values per thread (v[0..NVAL)); result in out[j]
-// (shared), identical order in every block
-template <int NVAL>
+// Warp-level folding butterfly over NV values held by every lane: at each
+// level a lane keeps half of its values and adds the partner's matching
+// half, so P values (NV padded to a power of two) cost P-1 additions instead
+// of P log2(32). Lane L ends with the sum over the warp of value base(L).
+template <int NV>
+struct Fold {
+    static constexpr int P = NV <= 1 ? 1 : NV <= 2 ? 2 : NV <= 4 ? 4 : NV <= 8 ? 8 : NV <= 16 ? 16 : 32;
+};
+
+template <int NV>
+__device__ __forceinline__ double warp_fold(const double* v, int& base) {
+    constexpr int P = Fold<NV>::P;
+    double x[P];
+#pragma unroll
+    for (int j = 0; j < P; ++j) x[j] = j < NV ? v[j] : 0.0;
+    const int lane = threadIdx.x & 31;
+    base = 0;
+    int c = P;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        if (c > 1) {
+            const int h = c / 2;
+            const bool up = (lane & o) != 0;
+#pragma unroll
+            for (int j = 0; j < P / 2; ++j) {
+                if (j < h) {
+                    // send the half I give away, receive the partner's copy of the half I keep
+                    double give = up ? x[j] : x[j + h];
+                    double got = __shfl_xor_sync(0xffffffffu, give, o);
+                    x[j] = (up ? x[j + h] : x[j]) + got;
+                }
+            }
+            if (up) base += h;
+            c = h;
+        } else {
+            x[0] += __shfl_xor_sync(0xffffffffu, x[0], o);
+        }
+    }
+    return x[0];
+}
+
+// block sums of NV per-thread values, written to out[0..NV) (shared); the
+// same order in every block
+template <int NV>
 __device__ __forceinline__ void block_sum(const double* v, double (*wsum)[PCG_W], double* out) {
+    int base = 0;
+    double x = warp_fold<NV>(v, base);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int nval = NVAL;
-#pragma unroll
-    for (int j = 0; j < NVAL; ++j) {
-        double x = v[j];
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) wsum[j][w] = x;
-    }
+    // lanes holding the same base carry equal sums; the lowest one writes
+    constexpr int P = Fold<NV>::P;
+    const bool writer = (lane & (32 / P - 1)) == 0;
+    if (writer && base < NV) wsum[base][w] = x;
     __syncthreads();
-    if (threadIdx.x < nval) {
-        double x = 0.0;
-        for (int i = 0; i < PCG_W; ++i) x += wsum[threadIdx.x][i];
-        out[threadIdx.x] = x;
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < PCG_W; ++i) s += wsum[threadIdx.x][i];
+        out[threadIdx.x] = s;
     }
     __syncthreads();
 }
 
-// sums over blocks of per-block partials part[bI * ld + j], j < NVAL, into out[j]
-template <int NVAL>
-__device__ __forceinline__ void reduce_partials(const double* __restrict__ part, int ld, unsigned nblk,
+// sums over nbx blocks of partials part[bI * ld + off + j], j < NV
+template <int NV>
+__device__ __forceinline__ void reduce_partials(const double* __restrict__ part, int ld, int off, unsigned nbx,
                                                 double (*wsum)[PCG_W], double* out) {
-    double v[NVAL];
+    double v[NV];
 #pragma unroll
-    for (int j = 0; j < NVAL; ++j) v[j] = 0.0;
-    for (unsigned bI = threadIdx.x; bI < nblk; bI += PCG_T)
+    for (int j = 0; j < NV; ++j) v[j] = 0.0;
+    for (unsigned bI = threadIdx.x; bI < nbx; bI += PCG_T)
 #pragma unroll
-        for (int j = 0; j < NVAL; ++j) v[j] += __ldcg(part + (size_t)bI * ld + j);
-    block_sum<NVAL>(v, wsum, out);
+        for (int j = 0; j < NV; ++j) v[j] += __ldcg(part + (size_t)bI * ld + off + j);
+    block_sum<NV>(v, wsum, out);
 }
 
+// Block (bx, g) owns rows bx*PCG_T + t (strided) and columns 3g .. 3g+2 of
+// the K-column solve. Partials: partA[bx][c] = p.q, partB[bx][c] = r.z,
+// partB[bx][K + c] = r.r. alpha of a block's columns needs only its group's
+// p.q; every block reduces all columns' r.z and r.r, so the convergence of
+// all columns, and with it the exit from the loop, is decided identically
+// everywhere.
 template <typename V, int K>
 __global__ void __launch_bounds__(PCG_T)
 k_cg_persistent(const int* __restrict__ rowptr, const int* __restrict__ col, const V* __restrict__ val,
                 const V* __restrict__ dinv, int nv, const double* __restrict__ b,
                 V* __restrict__ x, V* __restrict__ r, V* __restrict__ z, V* __restrict__ p,
-                V* __restrict__ q, double* __restrict__ partA /* [grid][KMAX] */,
-                double* __restrict__ partB /* [grid][2*KMAX] */, CgCtl* ctl, double tol2, int max_iter) {
+                V* __restrict__ q, double* __restrict__ partA /* [gridDim.x][KMAX] */,
+                double* __restrict__ partB /* [gridDim.x][2*KMAX] */, CgCtl* ctl, double tol2, int max_iter) {
+    constexpr int k = K;
+    constexpr int NG = (K + CGRP - 1) / CGRP;
     __shared__ double wsum[2 * KMAX][PCG_W];
     __shared__ double red[2 * KMAX];
     __shared__ V s_alpha[KMAX], s_beta[KMAX];
     __shared__ double s_rz[KMAX], s_bb[KMAX];
     __shared__ int s_active[KMAX], s_done;
-    constexpr int k = K;
-    const unsigned nblk = gridDim.x;
+    const unsigned nbx = gridDim.x, nblk = gridDim.x * gridDim.y;
+    const int g = blockIdx.y;
+    const int c0 = g * CGRP;
+    const int nc = (c0 + CGRP <= K) ? CGRP : K - c0;   // columns of this block
     const int stride = gridDim.x * PCG_T;
-    double acc[2 * K];
+    const int row0 = blockIdx.x * PCG_T + threadIdx.x;
+    double acc[2 * CGRP];
 #ifdef TP_CG_TRACE
     unsigned long long tr[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     long long tlast = clock64();
 #endif
+    (void)NG;
     // ---- init: x = 0, r = b, z = D^-1 r, p = q = 0 ; partial r.z, b.b
 #pragma unroll
-    for (int j = 0; j < 2 * k; ++j) acc[j] = 0.0;
-    for (int v = blockIdx.x * PCG_T + threadIdx.x; v < nv; v += stride)
+    for (int j = 0; j < 2 * CGRP; ++j) acc[j] = 0.0;
+    for (int v = row0; v < nv; v += stride)
 #pragma unroll
-        for (int c = 0; c < k; ++c) {
-            size_t o = (size_t)v * k + c;
-            V bv = (V)b[o], zv = dinv[v] * bv;
-            x[o] = V(0);
-            r[o] = bv;
-            z[o] = zv;
-            p[o] = V(0);
-            q[o] = V(0);
-            acc[c] += (double)bv * (double)zv;
-            acc[k + c] += (double)bv * (double)bv;
-        }
-    block_sum<2 * K>(acc, wsum, red);
-    if (threadIdx.x < 2 * k) partB[(size_t)blockIdx.x * 2 * KMAX + threadIdx.x] = red[threadIdx.x];
+        for (int cc = 0; cc < CGRP; ++cc)
+            if (cc < nc) {
+                const size_t o = (size_t)v * k + c0 + cc;
+                V bv = (V)b[o], zv = dinv[v] * bv;
+                x[o] = V(0);
+                r[o] = bv;
+                z[o] = zv;
+                p[o] = V(0);
+                q[o] = V(0);
+                acc[cc] += (double)bv * (double)zv;
+                acc[CGRP + cc] += (double)bv * (double)bv;
+            }
+    block_sum<2 * CGRP>(acc, wsum, red);
+    if (threadIdx.x < nc) {
+        partB[(size_t)blockIdx.x * 2 * KMAX + c0 + threadIdx.x] = red[threadIdx.x];
+        partB[(size_t)blockIdx.x * 2 * KMAX + K + c0 + threadIdx.x] = red[CGRP + threadIdx.x];
+    }
     if (!grid_barrier(ctl, nblk)) return;
-    reduce_partials<2 * K>(partB, 2 * KMAX, nblk, wsum, red);
-    if (threadIdx.x < k) {
-        int c = threadIdx.x;
-        double rz = red[c], bb = red[k + c];
+    // own columns: r.z and b.b
+    reduce_partials<CGRP>(partB, 2 * KMAX, c0, nbx, wsum, red);
+    reduce_partials<CGRP>(partB, 2 * KMAX, K + c0, nbx, wsum, red + CGRP);
+    if (threadIdx.x < nc) {
+        const int c = c0 + threadIdx.x;
+        const double rz = red[threadIdx.x], bb = red[CGRP + threadIdx.x];
         s_rz[c] = rz;
         s_bb[c] = bb;
         s_beta[c] = V(0);
@@ -299,84 +362,98 @@ k_cg_persistent(const int* __restrict__ rowptr, const int* __restrict__ col, con
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int any = 0;
-        for (int c = 0; c < k; ++c) any |= s_active[c];
-        s_done = any ? 0 : 1;
-    }
-    __syncthreads();
     int it = 0;
     CG_STAMP(9);
-    while (!s_done) {
-        // ---- phase A
+    // Loop exit: each group publishes gdone[g] after its r.r test (block 0 of
+    // the group writes it); every block reads all groups' flags after the next
+    // barrier, so all blocks leave at the same point. A group that finished
+    // earlier idles with alpha = beta = 0.
+    for (;;) {
+        // ---- phase A: p = z + beta p ; q = C z + beta q (own columns) ; p.q
 #pragma unroll
-        for (int j = 0; j < k; ++j) acc[j] = 0.0;
-        for (int v = blockIdx.x * PCG_T + threadIdx.x; v < nv; v += stride) {
-            V cz[K];
+        for (int j = 0; j < CGRP; ++j) acc[j] = 0.0;
+        for (int v = row0; v < nv; v += stride) {
+            V cz[CGRP];
 #pragma unroll
-            for (int c = 0; c < K; ++c) cz[c] = V(0);
+            for (int cc = 0; cc < CGRP; ++cc) cz[cc] = V(0);
             const int e0 = rowptr[v], e1 = rowptr[v + 1];
             for (int e = e0; e < e1; ++e) {
                 const V w = val[e];
-                const V* zr = z + (size_t)col[e] * k;
+                const V* zr = z + (size_t)col[e] * k + c0;
 #pragma unroll
-                for (int c = 0; c < K; ++c) cz[c] += w * __ldcg(zr + c);
+                for (int cc = 0; cc < CGRP; ++cc)
+                    if (cc < nc) cz[cc] += w * __ldcg(zr + cc);
             }
 #pragma unroll
-            for (int c = 0; c < K; ++c)
-                {
-                    size_t o = (size_t)v * k + c;
-                    V be = s_beta[c];
-                    V pv = __ldcg(z + o) + be * p[o];
-                    V qv = cz[c] + be * q[o];
+            for (int cc = 0; cc < CGRP; ++cc)
+                if (cc < nc) {
+                    const size_t o = (size_t)v * k + c0 + cc;
+                    const V be = s_beta[c0 + cc];
+                    const V pv = __ldcg(z + o) + be * p[o];
+                    const V qv = cz[cc] + be * q[o];
                     p[o] = pv;
                     q[o] = qv;
-                    acc[c] += (double)pv * (double)qv;
+                    acc[cc] += (double)pv * (double)qv;
                 }
         }
         CG_STAMP(0);
-        block_sum<K>(acc, wsum, red);
-        if (threadIdx.x < k) partA[(size_t)blockIdx.x * KMAX + threadIdx.x] = red[threadIdx.x];
+        block_sum<CGRP>(acc, wsum, red);
+        if (threadIdx.x < nc) partA[(size_t)blockIdx.x * KMAX + c0 + threadIdx.x] = red[threadIdx.x];
         CG_STAMP(1);
         if (!grid_barrier(ctl, nblk)) return;
         CG_STAMP(2);
-        reduce_partials<K>(partA, KMAX, nblk, wsum, red);
-        if (threadIdx.x < k) {
-            int c = threadIdx.x;
-            double pq = red[c];
+        if (it > 0) {
+            // flags published before this barrier: identical in every block
+            if (threadIdx.x == 0) {
+                int all = 1;
+                for (int gg = 0; gg < (int)gridDim.y; ++gg) all &= ((volatile int*)ctl->gdone)[gg];
+                s_done = all;
+            }
+            __syncthreads();
+            if (s_done) break;
+        }
+        reduce_partials<CGRP>(partA, KMAX, c0, nbx, wsum, red);   // own group's p.q
+        if (threadIdx.x < nc) {
+            const int c = c0 + threadIdx.x;
+            const double pq = red[threadIdx.x];
             s_alpha[c] = (V)((s_active[c] && pq > 0.0) ? s_rz[c] / pq : 0.0);
         }
         __syncthreads();
         CG_STAMP(3);
-        // ---- phase B
+        // ---- phase B: x += alpha p ; r -= alpha q ; z = D^-1 r ; r.z, r.r
 #pragma unroll
-        for (int j = 0; j < 2 * k; ++j) acc[j] = 0.0;
-        for (int v = blockIdx.x * PCG_T + threadIdx.x; v < nv; v += stride) {
+        for (int j = 0; j < 2 * CGRP; ++j) acc[j] = 0.0;
+        for (int v = row0; v < nv; v += stride) {
             const V dv = dinv[v];
 #pragma unroll
-            for (int c = 0; c < k; ++c) {
-                size_t o = (size_t)v * k + c;
-                V al = s_alpha[c];
-                x[o] += al * p[o];
-                V rv = r[o] - al * q[o];
-                r[o] = rv;
-                V zv = dv * rv;
-                z[o] = zv;
-                acc[c] += (double)rv * (double)zv;
-                acc[k + c] += (double)rv * (double)rv;
-            }
+            for (int cc = 0; cc < CGRP; ++cc)
+                if (cc < nc) {
+                    const size_t o = (size_t)v * k + c0 + cc;
+                    const V al = s_alpha[c0 + cc];
+                    x[o] += al * p[o];
+                    const V rv = r[o] - al * q[o];
+                    r[o] = rv;
+                    const V zv = dv * rv;
+                    z[o] = zv;
+                    acc[cc] += (double)rv * (double)zv;
+                    acc[CGRP + cc] += (double)rv * (double)rv;
+                }
         }
         CG_STAMP(4);
-        block_sum<2 * K>(acc, wsum, red);
-        if (threadIdx.x < 2 * k) partB[(size_t)blockIdx.x * 2 * KMAX + threadIdx.x] = red[threadIdx.x];
+        block_sum<2 * CGRP>(acc, wsum, red);
+        if (threadIdx.x < nc) {
+            partB[(size_t)blockIdx.x * 2 * KMAX + c0 + threadIdx.x] = red[threadIdx.x];
+            partB[(size_t)blockIdx.x * 2 * KMAX + K + c0 + threadIdx.x] = red[CGRP + threadIdx.x];
+        }
         CG_STAMP(5);
         if (!grid_barrier(ctl, nblk)) return;
         CG_STAMP(6);
         ++it;
-        reduce_partials<2 * K>(partB, 2 * KMAX, nblk, wsum, red);
-        if (threadIdx.x < k) {
-            int c = threadIdx.x;
-            double rz = red[c], rr = red[k + c];
+        reduce_partials<CGRP>(partB, 2 * KMAX, c0, nbx, wsum, red);          // own r.z
+        reduce_partials<CGRP>(partB, 2 * KMAX, K + c0, nbx, wsum, red + CGRP);  // own r.r
+        if (threadIdx.x < nc) {
+            const int c = c0 + threadIdx.x;
+            const double rz = red[threadIdx.x], rr = red[CGRP + threadIdx.x];
             if (s_active[c]) {
                 s_beta[c] = (V)(s_rz[c] > 0.0 ? rz / s_rz[c] : 0.0);
                 s_rz[c] = rz;
@@ -388,20 +465,19 @@ k_cg_persistent(const int* __restrict__ rowptr, const int* __restrict__ col, con
             }
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && blockIdx.x == 0) {
             int any = 0;
-            for (int c = 0; c < k; ++c) any |= s_active[c];
-            s_done = (!any || it >= max_iter) ? 1 : 0;
+            for (int cc = 0; cc < nc; ++cc) any |= s_active[c0 + cc];
+            ((volatile int*)ctl->gdone)[g] = (!any || it >= max_iter) ? 1 : 0;
         }
-        __syncthreads();
         CG_STAMP(7);
     }
 #ifdef TP_CG_TRACE
-    if (blockIdx.x == 0 && threadIdx.x == 0)
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
         for (int i = 0; i < 10; ++i) ctl->trace[i] = tr[i];
 #endif
-    if (blockIdx.x == 0 && threadIdx.x < k) ctl->active[threadIdx.x] = s_active[threadIdx.x];
-    if (blockIdx.x == 0 && threadIdx.x == 0) ctl->iters = it;
+    if (blockIdx.x == 0 && threadIdx.x < nc) ctl->active[c0 + threadIdx.x] = s_active[c0 + threadIdx.x];
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) ctl->iters = it;
 }
 
 // FP32 copies of the matrix values and the inverse diagonal
@@ -417,6 +493,8 @@ __global__ void k_to_f64(const V* __restrict__ a, size_t n, double* __restrict__
     if (i < n) out[i] = (double)a[i];
 }
 
+// blocks along the rows for a K-column solve: all rows covered when the
+// co-resident capacity allows, and never more than the device holds at once
 template <typename V, int K>
 static int cg_grid(int nv) {
     static int cached_dev = -1, cached_max = 0;
@@ -428,20 +506,23 @@ static int cg_grid(int nv) {
         cached_max = per_sm * sm_count();
         cached_dev = dev;
     }
+    constexpr int NG = (K + CGRP - 1) / CGRP;
     int want = (nv + PCG_T - 1) / PCG_T;
-    int g = want < cached_max ? want : cached_max;
+    int cap = cached_max / NG;
+    int g = want < cap ? want : cap;
     return g < 1 ? 1 : g;
 }
 
 template <typename V>
 struct CgLaunch {
     const void* fn;
-    int grid;
+    int grid;    // blocks along the rows
+    int groups;  // column groups
 };
 
 template <typename V, int K>
 static CgLaunch<V> cg_pick(int nv) {
-    return CgLaunch<V>{(const void*)k_cg_persistent<V, K>, cg_grid<V, K>(nv)};
+    return CgLaunch<V>{(const void*)k_cg_persistent<V, K>, cg_grid<V, K>(nv), (K + CGRP - 1) / CGRP};
 }
 
 template <typename V>
@@ -504,7 +585,7 @@ static int cg_run(tp_mesh* m, const tp_params* p, const double* b, int k, double
     CgCtl host{};
     {
         ProfScope ps(m, PK_CG, 0.0, st);
-        TP_CUDA(cudaLaunchCooperativeKernel(L.fn, dim3(grid), dim3(PCG_T), args, 0, st));
+        TP_CUDA(cudaLaunchCooperativeKernel(L.fn, dim3(grid, L.groups), dim3(PCG_T), args, 0, st));
         TP_LAUNCH_CHECK();
     }
     TP_CUDA(cudaMemcpyAsync(&host, ctl, sizeof(CgCtl), cudaMemcpyDeviceToHost, st));
