@@ -47,7 +47,8 @@ def flops_per_pair(name, stat):
     return None
 KERNEL_SOURCE = {"energy_direct": "pairs.cu", "diff_direct": "pairs.cu", "apply_A": "pairs.cu",
                  "apply_B": "pairs.cu", "apply_B0": "pairs.cu", "apply_L": "pairs.cu",
-                 "bh_energy": "bvh.cu", "bh_diff": "bvh.cu", "cg": "cg.cu", "bvh_build": "bvh.cu"}
+                 "bh_energy": "bvh.cu", "bh_diff": "bvh.cu", "cg": "cg.cu", "bvh_build": "bvh.cu",
+                 "chol_factor": "chol.cu", "chol_solve": "chol.cu"}
 FP32_LANES_PER_SM = 128
 
 
@@ -198,6 +199,45 @@ def profile_traffic(kernel, workload):
 
 
 # ---------------------------------------------------------------------------
+# large single mesh: Barnes-Hut on the 1,310,720-face icosphere
+# ---------------------------------------------------------------------------
+
+def large_bh(tp, dev, reps=3):
+    """Device time of the Barnes-Hut (theta = 0.5, leaf 8) energy and
+    differential on icosphere level 8 with spherical-harmonic bumps, and of one
+    direct all-pairs energy for comparison (interactions per second)."""
+    import torch
+    from synth import workload
+    V, F = workload("icosphere_l8")
+    mesh = tp.Mesh(torch.tensor(V, dtype=torch.float64, device=dev),
+                   torch.tensor(F, dtype=torch.int32, device=dev), device=dev.index or 0)
+    pb = bh_params(tp)
+    dE = torch.empty((len(V), 3), dtype=torch.float64, device=dev)
+    tp.tp_energy(mesh, pb)
+    tp.tp_differential(mesh, pb, like=dE)
+    torch.cuda.synchronize()
+    tp.tp_profile_read(mesh)
+    tp.tp_profile_enable(mesh, True)
+    for _ in range(reps):
+        tp.tp_mesh_set_positions(mesh, torch.tensor(V, dtype=torch.float64, device=dev))  # rebuilds the BVH
+        tp.tp_energy(mesh, pb)
+        tp.tp_differential(mesh, pb, like=dE)
+    tp.tp_energy(mesh, tp.params())                       # one direct pass
+    torch.cuda.synchronize()
+    prof = tp.tp_profile_read(mesh)
+    tp.tp_profile_enable(mesh, False)
+    mesh.close()
+    out = {"workload": "icosphere_l8", "nf": int(len(F)), "theta": pb.theta, "leaf_size": pb.leaf_size}
+    for k in ("bh_energy", "bh_diff", "bvh_build", "energy_direct"):
+        if k in prof and prof[k]["launches"]:
+            d = prof[k]
+            n = d["launches"]
+            out[k] = {"ms_per_launch": d["ms"] / n, "units_per_launch": d["units"] / n,
+                      "per_s": d["units"] / (d["ms"] / 1e3) if d["ms"] > 0 else None}
+    return out
+
+
+# ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
 
@@ -251,6 +291,7 @@ def gpu_arm(args):
     clocks.start()
     launches0 = tp.tp_launch_count()
     wall0 = time.perf_counter()
+    torch.cuda.nvtx.range_push("timed_steps")     # lets a profiler select the timed launches
     for k in range(args.steps):
         flush.zero_()                              # L2 flushed between timed steps
         ev[k][0].record(stream)
@@ -258,6 +299,7 @@ def gpu_arm(args):
         ev[k][1].record(stream)
         reps.append(rep)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     wall = time.perf_counter() - wall0
     launches = tp.tp_launch_count() - launches0
     clk = clocks.stop()
@@ -348,6 +390,8 @@ def gpu_arm(args):
                     for k, v in prof.items()},
         "wall_s": wall, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "clocks": clk,
     }
+    if not args.no_large:
+        line["large_mesh_bh"] = large_bh(tp, dev)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = run_cpu_sample()
     mesh.close()
@@ -383,6 +427,37 @@ def reference_arm(args):
     }))
 
 
+# ---------------------------------------------------------------------------
+# serving: continuous batching of descent steps (separate report)
+# ---------------------------------------------------------------------------
+
+SERVE_DESC = ("Poisson arrivals of one-step requests on perturbed icospheres and tori (sigma=0.01), "
+              "face counts log-uniform in [f_min, f_max]; slots = concurrent host threads on their own "
+              "CUDA streams; admission by tp_mesh_footprint_bytes against an HBM budget")
+
+
+def serve_arm(args):
+    """Served steps/s and p50/p99 latency of the FP32-pair path and of the
+    plain FP64 direct path on the same request stream (scaled-down stream:
+    the full 512-request, 2k-200k-face stream of the plain FP64 path would
+    take hours; sizes are stated in the output)."""
+    import paper_2107_01664_gb300 as tp
+    from paper_2107_01664_gb300 import serve
+    out = {"metric": "served steps/s", "unit": "steps/s", "mode": "serve", "description": SERVE_DESC}
+    for name, prec, n, fmin, fmax, rate in (("fp32_pairs", tp.TP_PREC_FP32, args.serve_n, 2000, args.serve_fmax, args.serve_rate),
+                                             ("fp64_direct", tp.TP_PREC_FP64, max(4, args.serve_n // 8), 2000, 8000, args.serve_rate / 8)):
+        p = tp.params(precision=prec, krylov_tol=1e-5, krylov_max=30, cg_tol=1e-6)
+        reqs = serve.make_requests(n, fmin, fmax, rate=rate, seed=404)
+        srv = serve.Server(slots=args.serve_slots, step_params=p)
+        res = srv.run(reqs)
+        summ = serve.summarize(res, srv.wall)
+        summ.update({"n_requests": n, "f_range": [fmin, fmax], "rate_per_s": rate, "slots": args.serve_slots,
+                     "max_concurrency": srv.max_concurrency, "peak_admitted_bytes": srv.peak_used,
+                     "budget_bytes": srv.budget, "krylov_max": p.krylov_max})
+        out[name] = summ
+    print(json.dumps(out))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -390,7 +465,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
+    ap.add_argument("--no-large", action="store_true", help="skip the 1.31M-face Barnes-Hut section")
+    ap.add_argument("--serve", action="store_true", help="run the serving benchmark instead")
+    ap.add_argument("--serve-n", type=int, default=64)
+    ap.add_argument("--serve-fmax", type=int, default=50000)
+    ap.add_argument("--serve-rate", type=float, default=8.0)
+    ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()
+    if args.serve:
+        serve_arm(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
     else:

@@ -16,6 +16,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <mutex>
 #include <vector>
 
 #include "tp_internal.cuh"
@@ -584,12 +585,19 @@ static int cg_run(tp_mesh* m, const tp_params* p, const double* b, int k, double
                     (void*)&partB, (void*)&ctl, (void*)&tol2, (void*)&cap};
     CgCtl host{};
     {
-        ProfScope ps(m, PK_CG, 0.0, st);
-        TP_CUDA(cudaLaunchCooperativeKernel(L.fn, dim3(grid, L.groups), dim3(PCG_T), args, 0, st));
-        TP_LAUNCH_CHECK();
+        // One persistent grid at a time per process: two cooperative grids
+        // sized to the whole GPU, launched from two meshes on two streams,
+        // could each hold part of the SMs while waiting for the rest.
+        static std::mutex coop_mutex;
+        std::lock_guard<std::mutex> lock(coop_mutex);
+        {
+            ProfScope ps(m, PK_CG, 0.0, st);
+            TP_CUDA(cudaLaunchCooperativeKernel(L.fn, dim3(grid, L.groups), dim3(PCG_T), args, 0, st));
+            TP_LAUNCH_CHECK();
+        }
+        TP_CUDA(cudaMemcpyAsync(&host, ctl, sizeof(CgCtl), cudaMemcpyDeviceToHost, st));
+        TP_CUDA(cudaStreamSynchronize(st));
     }
-    TP_CUDA(cudaMemcpyAsync(&host, ctl, sizeof(CgCtl), cudaMemcpyDeviceToHost, st));
-    TP_CUDA(cudaStreamSynchronize(st));
     if (host.err) return fail(TP_ERR_TIMEOUT, "cg: grid barrier timed out");
     const int it = host.iters;
     if (iters) *iters = it;
