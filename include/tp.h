@@ -65,6 +65,10 @@ extern "C" {
 #define TP_BH_DIFF_FULL     0  /* forward terms plus node-level reverse terms pushed to faces */
 #define TP_BH_DIFF_LITERAL  1  /* only the terms in which the face is the target S */
 
+/* Poisson solver of the preconditioner (§5.2) */
+#define TP_POISSON_CHOLESKY 0  /* pre-factorised C (sparse Cholesky, FP32 factor, FP64 refinement) */
+#define TP_POISSON_CG       1  /* Jacobi-preconditioned CG, FP64 */
+
 /* constraint flags (the barycenter constraint of §7.1.1 is always on) */
 #define TP_CONSTRAINT_AREA    1  /* total area, §7.1.3 */
 #define TP_CONSTRAINT_VOLUME  2  /* total signed volume, §7.1.4 */
@@ -78,14 +82,15 @@ typedef struct tp_params {
     double krylov_tol;    /* relative residual of the outer GMRES solves */
     int    krylov_max;    /* iteration cap of one GMRES solve (all restarts) */
     int    gmres_restart; /* restart length m */
-    double cg_tol;        /* relative residual of the Poisson CG solves (FP64) */
-    int    cg_max;        /* iteration cap of one CG solve */
+    double cg_tol;        /* relative residual of the Poisson solves (FP64 residual, both solvers) */
+    int    cg_max;        /* iteration cap of one CG solve (refinement sweeps: min(cg_max, 40)) */
     double armijo_c;      /* sufficient-decrease constant of the line search */
     double armijo_shrink; /* step shrink factor */
     double tau0;          /* initial step */
     int    ls_max;        /* maximum line-search trials */
     int    fixed_tau;     /* 1 = take tau0 without line search */
     int    proj_iters;    /* corrective projections per step (§3.3.2: one suffices; repeats allowed) */
+    int    poisson_solver; /* TP_POISSON_CHOLESKY (default) or TP_POISSON_CG */
 } tp_params;
 
 typedef struct tp_constraints {
@@ -102,7 +107,7 @@ typedef struct tp_step_report {
     double phi_before[2];  /* constraint values at f + tau x (area, volume) */
     double phi_after[2];   /* constraint values at f_new */
     int    krylov_iters;   /* total GMRES iterations of the step */
-    int    cg_iters;       /* total CG iterations of the step */
+    int    cg_iters;       /* total Poisson-solver iterations of the step (CG iterations or refinement sweeps) */
     int    ls_trials;      /* energy evaluations of the line search */
     int    status;         /* TP_OK or the first non-fatal solver status */
     double pair_interactions; /* (target, source) terms evaluated during the step */
@@ -124,7 +129,7 @@ typedef struct tp_mesh tp_mesh;
 /* Fill *p with the defaults: p=6, theta=0, leaf_size=8, FP32 pairs,
  * full BH differential, krylov_tol=1e-6, krylov_max=200, restart 30,
  * cg_tol=1e-6, cg_max=20000, Armijo c=1e-4, shrink 0.5, tau0=1, ls_max=30,
- * proj_iters=1. */
+ * proj_iters=1, Cholesky Poisson solver. */
 void tp_params_default(tp_params* p);
 
 /* Create a mesh on CUDA device `device` from nv positions and nf faces.
@@ -172,13 +177,38 @@ int tp_differential(tp_mesh* m, const tp_params* p, double* dE, int ptr_kind,
 int fractional_apply(tp_mesh* m, const tp_params* p, int op, const double* v,
                      int k, double* y, int ptr_kind, void* stream);
 
-/* z = C^+ b: Jacobi-preconditioned CG on the cotan stiffness matrix C of
- * the current positions (§5.2), k columns (1 <= k <= 9), right-hand side
- * and solution projected to zero mean, all in FP64. *iters_out (host, may be NULL) receives the iteration count.
- * TP_ERR_NOT_CONVERGED if cg_max is hit; TP_ERR_TIMEOUT if a device-side
- * wait gave up. */
+/* z = C^+ b for the cotan stiffness matrix C of the current positions
+ * (§5.2), k columns (1 <= k <= 9), b and z FP64 [nv][k].
+ * TP_POISSON_CHOLESKY: the pre-factorisation of §5.2. One vertex per
+ * connected component is pinned, the rest is factored by a supernodal sparse
+ * Cholesky (nested-dissection order, FP32 factor on the device, recomputed
+ * when the positions change); b is projected to zero mean per component and
+ * FP64 iterative refinement runs until every column has
+ * |b - C z| <= cg_tol |b|; z has zero mean per component. A mesh whose
+ * largest supernode panel does not fit in shared memory, or a solve whose
+ * refinement stops converging, is handed to the CG solver.
+ * TP_POISSON_CG: Jacobi-preconditioned CG (FP64) with b and z projected to
+ * zero mean over the whole mesh (connected meshes).
+ * *iters_out (host, may be NULL) receives the CG iterations or refinement
+ * sweeps. TP_ERR_NOT_CONVERGED if cg_max is hit; TP_ERR_TIMEOUT if a
+ * device-side wait gave up. */
 int cotan_solve(tp_mesh* m, const tp_params* p, const double* b, int k, double* z,
                 int ptr_kind, void* stream, int* iters_out);
+
+/* Structure of the sparse Cholesky factor of C (§5.2) of a mesh: computed
+ * on the first call (host analysis of the topology), no device work. */
+typedef struct tp_chol_info {
+    int    available;      /* 1 if the factorised solver serves this mesh */
+    int    components;     /* connected components (one pinned vertex each) */
+    int    unknowns;       /* factored unknowns: nv - components */
+    int    supernodes;     /* supernodes of the elimination tree */
+    int    levels;         /* tree height + 1 (sequential launches per substitution) */
+    int    max_front;      /* largest front (own + structure rows) */
+    double factor_floats;  /* stored factor entries (L11^-1 and L21 blocks) */
+    double update_floats;  /* update-matrix entries */
+} tp_chol_info;
+
+int cotan_factor_info(tp_mesh* m, tp_chol_info* out);
 
 /* z = C^+ L^{2-s} C^+ b, the preconditioner of §5.2, k columns. */
 int precond_apply(tp_mesh* m, const tp_params* p, const double* b, int k,

@@ -26,7 +26,7 @@ __all__ = [
     "tp_mesh_footprint_bytes", "tp_energy", "tp_energy_rows", "tp_differential",
     "fractional_apply", "cotan_solve", "precond_apply", "precond_step", "TangentPointEnergy",
     "lib_path", "lib", "tp_kernel_stat", "tp_profile_enable", "tp_profile_read", "tp_launch_count",
-    "tp_energy_noalloc",
+    "tp_energy_noalloc", "tp_chol_info", "cotan_factor_info", "TP_POISSON_CHOLESKY", "TP_POISSON_CG",
 ]
 
 TP_OK, TP_ERR_INVALID_ARG, TP_ERR_DEGENERATE, TP_ERR_OOM = 0, 1, 2, 3
@@ -36,6 +36,7 @@ TP_PREC_FP32, TP_PREC_FP64 = 0, 1
 TP_OP_A, TP_OP_B, TP_OP_B0, TP_OP_L = 0, 1, 2, 3
 TP_BH_DIFF_FULL, TP_BH_DIFF_LITERAL = 0, 1
 TP_CONSTRAINT_AREA, TP_CONSTRAINT_VOLUME = 1, 2
+TP_POISSON_CHOLESKY, TP_POISSON_CG = 0, 1
 _OPS = {"A": TP_OP_A, "B": TP_OP_B, "B0": TP_OP_B0, "L": TP_OP_L}
 
 
@@ -52,7 +53,7 @@ class tp_params(ctypes.Structure):
         ("krylov_tol", ctypes.c_double), ("krylov_max", ctypes.c_int), ("gmres_restart", ctypes.c_int),
         ("cg_tol", ctypes.c_double), ("cg_max", ctypes.c_int), ("armijo_c", ctypes.c_double),
         ("armijo_shrink", ctypes.c_double), ("tau0", ctypes.c_double), ("ls_max", ctypes.c_int),
-        ("fixed_tau", ctypes.c_int), ("proj_iters", ctypes.c_int),
+        ("fixed_tau", ctypes.c_int), ("proj_iters", ctypes.c_int), ("poisson_solver", ctypes.c_int),
     ]
 
 
@@ -68,6 +69,12 @@ class tp_step_report(ctypes.Structure):
         ("cg_iters", ctypes.c_int), ("ls_trials", ctypes.c_int), ("status", ctypes.c_int),
         ("pair_interactions", ctypes.c_double),
     ]
+
+
+class tp_chol_info(ctypes.Structure):
+    _fields_ = [("available", ctypes.c_int), ("components", ctypes.c_int), ("unknowns", ctypes.c_int),
+                ("supernodes", ctypes.c_int), ("levels", ctypes.c_int), ("max_front", ctypes.c_int),
+                ("factor_floats", ctypes.c_double), ("update_floats", ctypes.c_double)]
 
 
 class tp_kernel_stat(ctypes.Structure):
@@ -106,6 +113,7 @@ def lib():
         "tp_differential": (c_int, [vp, P(tp_params), vp, c_int, P(c_double), vp]),
         "fractional_apply": (c_int, [vp, P(tp_params), c_int, vp, c_int, vp, c_int, vp]),
         "cotan_solve": (c_int, [vp, P(tp_params), vp, c_int, vp, c_int, vp, P(c_int)]),
+        "cotan_factor_info": (c_int, [vp, P(tp_chol_info)]),
         "precond_apply": (c_int, [vp, P(tp_params), vp, c_int, vp, c_int, vp]),
         "precond_step": (c_int, [vp, P(tp_params), P(tp_constraints), P(tp_step_report), vp]),
         "tp_last_error": (ctypes.c_char_p, []),
@@ -296,6 +304,13 @@ def cotan_solve(mesh: Mesh, b, p: tp_params | None = None):
     it = ctypes.c_int()
     _check(lib().cotan_solve(mesh.handle, ctypes.byref(p), bp, k, ptr, bk, _stream_ptr(b), ctypes.byref(it)))
     return out, it.value
+
+
+def cotan_factor_info(mesh: Mesh) -> dict:
+    """Structure of the sparse Cholesky factor of the mesh's cotan Laplacian."""
+    info = tp_chol_info()
+    _check(lib().cotan_factor_info(mesh.handle, ctypes.byref(info)))
+    return {name: getattr(info, name) for name, _ in tp_chol_info._fields_}
 
 
 def precond_apply(mesh: Mesh, b, p: tp_params | None = None):

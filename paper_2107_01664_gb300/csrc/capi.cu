@@ -36,6 +36,8 @@ int check_params(const tp_params* p) {
         return fail(TP_ERR_INVALID_ARG, "unknown precision");
     if (p->theta > 0.0 && p->precision != TP_PREC_FP32)
         return fail(TP_ERR_INVALID_ARG, "Barnes-Hut (theta > 0) runs in TP_PREC_FP32 only");
+    if (p->poisson_solver != TP_POISSON_CHOLESKY && p->poisson_solver != TP_POISSON_CG)
+        return fail(TP_ERR_INVALID_ARG, "unknown Poisson solver");
     return TP_OK;
 }
 
@@ -86,6 +88,7 @@ void tp_params_default(tp_params* p) {
     p->ls_max = 30;
     p->fixed_tau = 0;
     p->proj_iters = 1;
+    p->poisson_solver = TP_POISSON_CHOLESKY;
 }
 
 const char* tp_last_error(void) { return tp::last_error(); }
@@ -186,6 +189,7 @@ int tp_mesh_destroy(tp_mesh* m) {
                   &m->wv64, &m->wv32, &m->io_in, &m->io_out, &m->adj, &m->erow, &m->tlist, &m->rowsum,
                   &m->kry};
     for (Buf* b : all) release(*b);
+    chol_release(m);
     release(m->bhcount);
     prof_release(m);
     for (auto& b : m->tmpv) release(b);
@@ -206,7 +210,13 @@ size_t tp_mesh_footprint_bytes(int nv, int nf, const tp_params* p) {
     size_t pairs = nsplit * F * 14 * 8 + F * (96 + 72 + 72 + 56 + 8);
     size_t krylov = (size_t)(2 * restart + 1) * 3 * V * 8;
     size_t vecs = 24 * 3 * V * 8;
-    return geom + lap + bvh + pairs + krylov + vecs;
+    // sparse Cholesky (nested dissection on a surface: factor and update
+    // matrices grow like V log V; about 190 floats per vertex at 10^4
+    // vertices) plus its FP32 and FP64 solve vectors
+    size_t chol = 0;
+    if (!p || p->poisson_solver == TP_POISSON_CHOLESKY)
+        chol = (size_t)(V * 4.0 * 24.0 * std::log2((double)V + 2.0)) + V * 9 * (4 * 3 + 8 * 3) + V * 64;
+    return geom + lap + bvh + pairs + krylov + vecs + chol;
 }
 
 int tp_energy(tp_mesh* m, const tp_params* p, double* E_out, void* stream) {
@@ -303,6 +313,14 @@ int cotan_solve(tp_mesh* m, const tp_params* p, const double* b, int k, double* 
     return TP_OK;
 }
 
+int cotan_factor_info(tp_mesh* m, tp_chol_info* out) {
+    set_error("");
+    TP_TRY(check_mesh(m));
+    if (!out) return fail(TP_ERR_INVALID_ARG, "out is NULL");
+    DeviceGuard g(m->device);
+    return chol_info(m, out);
+}
+
 int precond_apply(tp_mesh* m, const tp_params* p, const double* b, int k, double* z, int ptr_kind, void* stream) {
     set_error("");
     TP_TRY(check_mesh(m));
@@ -349,7 +367,8 @@ int tp_profile_read(tp_mesh* m, tp_kernel_stat* out, int max, int* n) {
     if (!n || (max > 0 && !out)) return fail(TP_ERR_INVALID_ARG, "NULL output");
     DeviceGuard g(m->device);
     static const char* names[PK_COUNT] = {"energy_direct", "diff_direct", "apply_A", "apply_B", "apply_B0",
-                                          "apply_L", "bh_energy", "bh_diff", "bvh_build", "cg"};
+                                          "apply_L", "bh_energy", "bh_diff", "bvh_build", "cg",
+                                          "chol_factor", "chol_solve"};
     Profiler& P = m->prof;
     for (auto& pe : P.pending) {
         float ms = 0.f;

@@ -640,6 +640,11 @@ int cg_solve(tp_mesh* m, const tp_params* p, const double* b, int k, double* z_o
              int* iters) {
     if (k < 1 || k > KMAX) return fail(TP_ERR_INVALID_ARG, "cg: k must be in 1..9");
     TP_TRY(laplacian_values(m, st));
+    if (p->poisson_solver == TP_POISSON_CHOLESKY) {
+        bool used = false;
+        TP_TRY(chol_solve(m, p, b, k, z_out, st, iters, &used));
+        if (used) return TP_OK;
+    }
     // FP64 vectors in both precision modes: with FP32 vectors the Jacobi-CG
     // iteration stalls above a 1e-6 relative residual on rough meshes
     return cg_run<double>(m, p, b, k, z_out, st, iters);
@@ -665,7 +670,9 @@ int project_mean_zero(tp_mesh* m, double* x, int k, cudaStream_t st) {
 }
 
 constexpr int DOT_T = 256;
-constexpr int DOT_MAXV = 64;
+constexpr int DOT_MAXV = 128;
+constexpr int DOT_CH = 8;   // dot products accumulated per pass over the elements
+constexpr int DOT_PAIRS_MAX = 512;
 
 struct PtrList {
     const double* p[DOT_MAXV];
@@ -674,22 +681,51 @@ struct CoefList {
     double c[DOT_MAXV];
 };
 
-__global__ void k_multidot(PtrList xs, const double* __restrict__ y, int nvec, size_t n,
-                           double* __restrict__ part) {
-    __shared__ double sh[DOT_T];
-    size_t per = (n + gridDim.x - 1) / gridDim.x;
-    size_t i0 = (size_t)blockIdx.x * per, i1 = i0 + per < n ? i0 + per : n;
-    for (int j = 0; j < nvec; ++j) {
-        double s = 0.0;
-        const double* x = xs.p[j];
-        for (size_t i = i0 + threadIdx.x; i < i1; i += DOT_T) s += x[i] * y[i];
-        sh[threadIdx.x] = s;
-        __syncthreads();
-        for (int w = DOT_T / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-            __syncthreads();
+// part[blockIdx.x][j] = sum over this block's elements of xs[j][i] * ys[j][i].
+// Each thread owns one element per grid stride and accumulates DOT_CH
+// products at a time; the block sums fold across the warp (P-1 additions
+// for P values) and then across warps, always in the same order.
+__global__ void __launch_bounds__(DOT_T)
+k_multidot(PtrList xs, PtrList ys, int nvec, size_t n, double* __restrict__ part) {
+    __shared__ double wsum[DOT_CH][DOT_T / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    for (int j0 = 0; j0 < nvec; j0 += DOT_CH) {
+        double acc[DOT_CH];
+#pragma unroll
+        for (int c = 0; c < DOT_CH; ++c) acc[c] = 0.0;
+        for (size_t i = (size_t)blockIdx.x * DOT_T + threadIdx.x; i < n; i += (size_t)gridDim.x * DOT_T) {
+#pragma unroll
+            for (int c = 0; c < DOT_CH; ++c)
+                if (j0 + c < nvec) acc[c] += xs.p[j0 + c][i] * ys.p[j0 + c][i];
         }
-        if (threadIdx.x == 0) part[(size_t)blockIdx.x * nvec + j] = sh[0];
+        // folding butterfly: lane L ends with the warp sum of value (L / 4) % 8
+        int base = 0, cnt = DOT_CH;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            if (cnt > 1) {
+                const int h = cnt / 2;
+                const bool up = (lane & o) != 0;
+#pragma unroll
+                for (int c = 0; c < DOT_CH / 2; ++c)
+                    if (c < h) {
+                        double give = up ? acc[c] : acc[c + h];
+                        double got = __shfl_xor_sync(0xffffffffu, give, o);
+                        acc[c] = (up ? acc[c + h] : acc[c]) + got;
+                    }
+                if (up) base += h;
+                cnt = h;
+            } else {
+                acc[0] += __shfl_xor_sync(0xffffffffu, acc[0], o);
+            }
+        }
+        if ((lane & (32 / DOT_CH - 1)) == 0) wsum[base][w] = acc[0];
+        __syncthreads();
+        if (threadIdx.x < DOT_CH && j0 + threadIdx.x < nvec) {
+            double s = 0.0;
+#pragma unroll
+            for (int q = 0; q < DOT_T / 32; ++q) s += wsum[threadIdx.x][q];
+            part[(size_t)blockIdx.x * nvec + j0 + threadIdx.x] = s;
+        }
         __syncthreads();
     }
 }
@@ -703,23 +739,36 @@ __global__ void k_multidot_final(const double* __restrict__ part, int nblk, int 
     out[j] = s;
 }
 
-int dots(tp_mesh* m, const double* const* xs, const double* y, int nvec, size_t n, double* out_host,
-         cudaStream_t st) {
-    if (nvec < 1 || nvec > DOT_MAXV) return fail(TP_ERR_INVALID_ARG, "dots: too many vectors");
-    PtrList pl;
-    for (int j = 0; j < nvec; ++j) pl.p[j] = xs[j];
-    int nblk = (int)std::min<size_t>((n + 2047) / 2048, (size_t)sm_count() * 2);
+// out_host[j] = xs[j] . ys[j] (FP64, n elements each), one host sync
+int dot_pairs(tp_mesh* m, const double* const* xs, const double* const* ys, int nvec, size_t n, double* out_host,
+              cudaStream_t st) {
+    if (nvec < 1 || nvec > DOT_PAIRS_MAX) return fail(TP_ERR_INVALID_ARG, "dots: too many vectors");
+    int nblk = (int)std::min<size_t>((n + DOT_T - 1) / DOT_T, (size_t)sm_count());
     if (nblk < 1) nblk = 1;
-    TP_TRY(ensure(m->part2, sizeof(double) * (size_t)nblk * nvec + sizeof(double) * DOT_MAXV));
+    TP_TRY(ensure(m->part2, sizeof(double) * ((size_t)nblk * DOT_MAXV + DOT_PAIRS_MAX)));
     double* part = m->part2.as<double>();
-    double* out = part + (size_t)nblk * nvec;
-    k_multidot<<<nblk, DOT_T, 0, st>>>(pl, y, nvec, n, part);
-    TP_LAUNCH_CHECK();
-    k_multidot_final<<<1, DOT_MAXV, 0, st>>>(part, nblk, nvec, out);
-    TP_LAUNCH_CHECK();
+    double* out = part + (size_t)nblk * DOT_MAXV;
+    for (int j0 = 0; j0 < nvec; j0 += DOT_MAXV) {
+        const int nc = std::min(DOT_MAXV, nvec - j0);
+        PtrList px, py;
+        for (int j = 0; j < nc; ++j) {
+            px.p[j] = xs[j0 + j];
+            py.p[j] = ys[j0 + j];
+        }
+        k_multidot<<<nblk, DOT_T, 0, st>>>(px, py, nc, n, part);
+        TP_LAUNCH_CHECK();
+        k_multidot_final<<<1, DOT_MAXV, 0, st>>>(part, nblk, nc, out + j0);
+        TP_LAUNCH_CHECK();
+    }
     TP_CUDA(cudaMemcpyAsync(out_host, out, sizeof(double) * nvec, cudaMemcpyDeviceToHost, st));
     TP_CUDA(cudaStreamSynchronize(st));
     return TP_OK;
+}
+
+int dots(tp_mesh* m, const double* const* xs, const double* y, int nvec, size_t n, double* out_host,
+         cudaStream_t st) {
+    std::vector<const double*> ys(nvec, y);
+    return dot_pairs(m, xs, ys.data(), nvec, n, out_host, st);
 }
 
 __global__ void k_lincomb(double* __restrict__ y, PtrList xs, CoefList cf, int nvec, size_t n,

@@ -216,26 +216,57 @@ static int fgmres_multi(tp_mesh* m, const tp_params* p, int ns, const double* co
             TP_TRY(unpack(P2, nv, wout, st));
             ++total;
             std::vector<int> still;
-            for (int i : cyc) {
-                GmSys& q = S[i];
-                // classical Gram-Schmidt, twice
+            // classical Gram-Schmidt, twice, for all systems of the cycle at
+            // once: pass 1 h = V^T w; pass 2 h2 = V^T w' together with |w'|^2,
+            // so |w''|^2 = |w'|^2 - |h2|^2 (V orthonormal); two host syncs
+            std::vector<const double*> dx, dy;
+            for (int i : cyc)
+                for (int l = 0; l <= j; ++l) {
+                    dx.push_back(Vj(S[i], l));
+                    dy.push_back(S[i].w);
+                }
+            std::vector<double> h1(dx.size()), h2(dx.size() + cyc.size());
+            TP_TRY(dot_pairs(m, dx.data(), dy.data(), (int)dx.size(), n, h1.data(), st));
+            for (size_t ii = 0; ii < cyc.size(); ++ii) {
+                GmSys& q = S[cyc[ii]];
                 std::vector<const double*> basis(j + 1);
-                for (int l = 0; l <= j; ++l) basis[l] = Vj(q, l);
-                std::vector<double> h(j + 1), h2(j + 1), neg(j + 1);
-                TP_TRY(dots(m, basis.data(), q.w, j + 1, n, h.data(), st));
-                for (int l = 0; l <= j; ++l) neg[l] = -h[l];
+                std::vector<double> neg(j + 1);
+                for (int l = 0; l <= j; ++l) {
+                    basis[l] = Vj(q, l);
+                    neg[l] = -h1[ii * (j + 1) + l];
+                }
                 TP_TRY(lincomb(q.w, basis.data(), neg.data(), j + 1, n, 1.0, st));
-                TP_TRY(dots(m, basis.data(), q.w, j + 1, n, h2.data(), st));
-                for (int l = 0; l <= j; ++l) neg[l] = -h2[l];
+            }
+            for (int i : cyc) {
+                dx.push_back(S[i].w);
+                dy.push_back(S[i].w);
+            }
+            TP_TRY(dot_pairs(m, dx.data(), dy.data(), (int)dx.size(), n, h2.data(), st));
+            for (size_t ii = 0; ii < cyc.size(); ++ii) {
+                const int i = cyc[ii];
+                GmSys& q = S[i];
+                const double* hh = h2.data() + ii * (j + 1);
+                std::vector<const double*> basis(j + 1);
+                std::vector<double> neg(j + 1);
+                double hh2 = 0.0;
+                for (int l = 0; l <= j; ++l) {
+                    basis[l] = Vj(q, l);
+                    neg[l] = -hh[l];
+                    hh2 += hh[l] * hh[l];
+                }
                 TP_TRY(lincomb(q.w, basis.data(), neg.data(), j + 1, n, 1.0, st));
-                for (int l = 0; l <= j; ++l) q.H[l * mr + j] = h[l] + h2[l];
-                double wn2;
-                const double* xs[1] = {q.w};
-                TP_TRY(dots(m, xs, q.w, 1, n, &wn2, st));
-                double hn = std::sqrt(wn2);
+                for (int l = 0; l <= j; ++l) q.H[l * mr + j] = h1[ii * (j + 1) + l] + hh[l];
+                const double ww = h2[(size_t)cyc.size() * (j + 1) + ii];
+                double hn2 = ww - hh2;
+                if (!(hn2 > 1e-6 * ww)) {   // near breakdown: measure |w''| directly
+                    const double* xs[1] = {q.w};
+                    TP_TRY(dots(m, xs, q.w, 1, n, &hn2, st));
+                }
+                double hn = std::sqrt(std::max(0.0, hn2));
                 q.H[(j + 1) * mr + j] = hn;
                 if (hn > 0.0) {
                     double sc = 1.0 / hn;
+                    const double* xs[1] = {q.w};
                     TP_TRY(lincomb(Vj(q, j + 1), xs, &sc, 1, n, 0.0, st));
                 }
                 for (int l = 0; l < j; ++l) {  // Givens rotations

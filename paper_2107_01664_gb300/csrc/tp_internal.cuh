@@ -78,7 +78,7 @@ struct BvhNode {          // 64 bytes, FP32 (pair path)
 // ---------------------------------------------------------------------------
 
 enum ProfKey { PK_ENERGY = 0, PK_DIFF, PK_APPLY_A, PK_APPLY_B, PK_APPLY_B0, PK_APPLY_L, PK_BH_ENERGY,
-               PK_BH_DIFF, PK_BVH_BUILD, PK_CG, PK_COUNT };
+               PK_BH_DIFF, PK_BVH_BUILD, PK_CG, PK_CHOL_FACTOR, PK_CHOL_SOLVE, PK_COUNT };
 
 struct Profiler {
     bool on = false;
@@ -91,6 +91,10 @@ struct Profiler {
 };
 
 }  // namespace tp
+
+namespace tp {
+struct CholState;   // sparse Cholesky factor of the cotan Laplacian (chol.cu)
+}
 
 struct tp_mesh {
     int device = 0;
@@ -115,6 +119,7 @@ struct tp_mesh {
     int nnz = 0;
     tp::Buf rowptr, col, cotsrc, diagpos, val, dinv, val32;
     bool lap_valid = false;
+    tp::CholState* chol = nullptr;   // created on the first factorised solve
     // Barnes-Hut tree (rebuilt per positions on demand)
     int bvh_nodes = 0, bvh_leaf = 0;
     int bvh_shape_leaf = 0, bvh_maxdepth = 0;
@@ -184,10 +189,20 @@ int laplacian_setup(tp_mesh* m);                        // CSR pattern (host, on
 int laplacian_values(tp_mesh* m, cudaStream_t st);      // cotan values for current positions
 int cg_solve(tp_mesh* m, const tp_params* p, const double* b_dev, int k, double* z_dev,
              cudaStream_t st, int* iters);
+// -------- chol.cu ----------------------------------------------------------
+// z = C^+ b through the sparse Cholesky factor; *used = false when the
+// factor cannot serve the mesh (panel too large) or refinement stalled
+int chol_solve(tp_mesh* m, const tp_params* p, const double* b_dev, int k, double* z_dev,
+               cudaStream_t st, int* iters, bool* used);
+int chol_info(tp_mesh* m, tp_chol_info* out);
+void chol_invalidate(tp_mesh* m);   // positions changed: refactor before the next solve
+void chol_release(tp_mesh* m);
 // vector helpers (device, FP64, deterministic)
 int project_mean_zero(tp_mesh* m, double* x_dev, int k, cudaStream_t st);
 int dots(tp_mesh* m, const double* const* xs, const double* y, int nvec, size_t n,
          double* out_host, cudaStream_t st);
+int dot_pairs(tp_mesh* m, const double* const* xs, const double* const* ys, int nvec, size_t n,
+              double* out_host, cudaStream_t st);   // out_host[j] = xs[j] . ys[j], nvec <= 512
 int axpy(double* y, const double* x, double a, size_t n, cudaStream_t st);
 int lincomb(double* y, const double* const* xs, const double* coef_host, int nvec, size_t n,
             double beta, cudaStream_t st);

@@ -125,24 +125,81 @@ def test_operator_constant_nullspace_and_symmetry(lib, meshes):
                float(b[:, 0] @ lib.fractional_apply(m, "A", a, p)[:, 0])) < 1e-10
 
 
-@pytest.mark.parametrize("name", ["torus13x7", "ico3"])
+@pytest.mark.parametrize("name", ["tetra", "octa", "torus13x7", "ico3"])
 @pytest.mark.parametrize("k", [1, 3, 9])
-def test_cotan_solve(lib, meshes, name, k):
+@pytest.mark.parametrize("solver", [0, 1])
+def test_cotan_solve(lib, meshes, name, k, solver):
     V, F, m = meshes[name]
     b = O.project_mean_zero(vertex_vectors(len(V), k, 9))
     ref = O.poisson_solve(O.cotan_laplacian(V, F), b)
-    z, it = lib.cotan_solve(m, b, lib.params(precision=1, cg_tol=1e-12))     # FP64 CG
+    z, it = lib.cotan_solve(m, b, lib.params(precision=1, cg_tol=1e-12, poisson_solver=solver))
     assert rel(z, ref) <= 1e-9
     assert it > 0
-    z32, it32 = lib.cotan_solve(m, b, lib.params(cg_tol=1e-12))              # FP32 pair path: same CG
+    # the pair precision does not touch the Poisson solve
+    z32, it32 = lib.cotan_solve(m, b, lib.params(cg_tol=1e-12, poisson_solver=solver))
     assert rel(z32, ref) <= 1e-9
 
 
-def test_cotan_solve_not_converged_is_reported(lib, meshes):
+def test_cholesky_refinement_sweeps(lib, meshes):
+    # FP32 factor + FP64 refinement: a few sweeps reach 1e-6, more reach 1e-12
+    V, F, m = meshes["ico3"]
+    b = O.project_mean_zero(vertex_vectors(len(V), 3, 2))
+    ref = O.poisson_solve(O.cotan_laplacian(V, F), b)
+    z, it = lib.cotan_solve(m, b, lib.params(cg_tol=1e-6))
+    assert 1 <= it <= 4
+    C = O.cotan_laplacian(V, F)
+    assert np.linalg.norm(C @ z - b, axis=0).max() <= 1e-6 * np.linalg.norm(b, axis=0).max()
+    z2, it2 = lib.cotan_solve(m, b, lib.params(cg_tol=1e-12))
+    assert it2 > it and rel(z2, ref) <= 1e-9
+
+
+def test_cotan_factor_info(lib, meshes):
+    V, F, m = meshes["ico3"]
+    info = lib.cotan_factor_info(m)
+    assert info["available"] == 1 and info["components"] == 1 and info["unknowns"] == len(V) - 1
+    assert info["supernodes"] >= 1 and info["levels"] >= 1 and info["max_front"] >= 1
+    assert info["factor_floats"] > 0
+
+
+def test_cholesky_two_components(lib):
+    # two disjoint meshes: one pinned vertex per component, C^+ b per component
+    import torch
+    A = small_mesh("ico2", seed=3)
+    B = small_mesh("torus13x7", seed=4)
+    V = np.concatenate([A[0], B[0] + np.array([5.0, 0.0, 0.0])])
+    F = np.concatenate([A[1], B[1] + len(A[0])]).astype(np.int32)
+    na = len(A[0])
+    b = vertex_vectors(len(V), 3, 12)
+    with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as m:
+        info = lib.cotan_factor_info(m)
+        assert info["components"] == 2 and info["unknowns"] == len(V) - 2
+        z, it = lib.cotan_solve(m, b, lib.params(cg_tol=1e-12))
+    for (Vc, Fc), sl in ((A, slice(0, na)), (B, slice(na, len(V)))):
+        ref = O.poisson_solve(O.cotan_laplacian(Vc, Fc), O.project_mean_zero(b[sl]))
+        assert rel(z[sl], ref) <= 1e-9
+
+
+def test_cholesky_refactors_after_moving(lib):
+    import torch
+    V, F = small_mesh("torus13x7", seed=2)
+    b = O.project_mean_zero(vertex_vectors(len(V), 2, 3))
+    W = V + 0.05 * vertex_vectors(len(V), 3, 4)
+    with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as m:
+        z0, _ = lib.cotan_solve(m, b, lib.params(cg_tol=1e-12))
+        m.set_positions(dev(W, torch.float64))
+        z1, _ = lib.cotan_solve(m, b, lib.params(cg_tol=1e-12))
+    assert rel(z0, O.poisson_solve(O.cotan_laplacian(V, F), b)) <= 1e-9
+    assert rel(z1, O.poisson_solve(O.cotan_laplacian(W, F), b)) <= 1e-9
+
+
+@pytest.mark.parametrize("solver", [0, 1])
+def test_cotan_solve_not_converged_is_reported(lib, meshes, solver):
+    # an unreachable tolerance with a cap of 3: the factorised solve hands
+    # over to CG, which reports the cap
     V, F, m = meshes["ico3"]
     b = O.project_mean_zero(vertex_vectors(len(V), 1, 9))
     with pytest.raises(lib.TpError) as e:
-        lib.cotan_solve(m, b, lib.params(cg_tol=1e-14, cg_max=3))
+        lib.cotan_solve(m, b, lib.params(cg_tol=1e-30, cg_max=3, poisson_solver=solver))
     assert e.value.code == lib.TP_ERR_NOT_CONVERGED
 
 
