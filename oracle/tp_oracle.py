@@ -762,6 +762,84 @@ def bh_energy_frozen(f, faces, tree, lists, p=6.0):
     return float(E)
 
 
+def bvh_node_sums(tree, vals):
+    """Sums of per-face rows `vals` [nf, m] over each node's faces."""
+    first, count = tree["first"], tree["count"]
+    sv = np.asarray(vals)[tree["order"]]
+    out = np.zeros((len(first),) + sv.shape[1:])
+    for nid in range(len(first)):
+        out[nid] = sv[first[nid]:first[nid] + count[nid]].sum(axis=0)
+    return out
+
+
+def bvh_average_projectors(f, faces, tree):
+    """Node-average projectors P_I = a_I^-1 sum_{S in I} a_S N_S N_S^T (§5.1.4)."""
+    X, N, a = face_geometry(f, faces)
+    aP = a[:, None, None] * N[:, :, None] * N[:, None, :]
+    return bvh_node_sums(tree, aP) / tree["a"][:, None, None]
+
+
+def bh_kernel_apply(tree, lists, Xr, N, a, W, kind, expo, Pbar):
+    """z = [diag(diag(a)^-1 H~ a) - H~] W, H~ the Barnes-Hut version of the
+    kernel matrix of the operator applies (§5.1.1-5.1.3 with the per-target
+    admissible sets of §4.1): a far pair (S, node I) contributes
+    h(X_S, P_S; X_I, P_I) times the node sums of a and W, with the
+    node-average projector P_I in the source-side k_2 (§5.1.4); a near pair
+    (S, T) in an inadmissible leaf contributes the exact h(X_S, P_S; X_T, P_T)."""
+    nf = len(Xr)
+    aW = np.concatenate([a[:, None], W], axis=1)
+    nodeS = bvh_node_sums(tree, aW)
+    H = np.zeros_like(aW)
+
+    def add(s, Y, Q, src):
+        d = Xr[s] - Y
+        r2 = np.sum(d * d, axis=1)
+        h = r2 ** (-0.5 * expo)
+        if kind == "low":
+            uS = np.sum(N[s] * d, axis=1)
+            Qd = np.einsum("nij,nj->ni", Q, d)
+            h = h * (uS * uS + np.sum(Qd * Qd, axis=1)) / (2.0 * r2 * r2)
+        np.add.at(H, s, h[:, None] * src)
+
+    fs, fn, ns, nt = lists["far_s"], lists["far_n"], lists["near_s"], lists["near_t"]
+    if len(fs):
+        add(fs, tree["X"][fn], Pbar[fn], nodeS[fn])
+    if len(ns):
+        PT = N[nt][:, :, None] * N[nt][:, None, :]
+        add(ns, Xr[nt], PT, aW[nt])
+    return (H[:, 0] / a)[:, None] * W - H[:, 1:]
+
+
+def bh_apply_operator(f, faces, v, op, theta, leaf=8, p=6.0):
+    """Barnes-Hut version of apply_operator: the same assembly (Appendix A
+    form) with every kernel-matrix product taken over the Barnes-Hut
+    interaction lists of the energy (§4.1). theta = 0 gives apply_operator."""
+    nv = len(f)
+    nf = len(faces)
+    X, N, a = face_geometry(f, faces)
+    s = sobolev_s(p)
+    T, L = bh_interactions(f, faces, theta, leaf)
+    Xr = T["Xr"]
+    Pbar = bvh_average_projectors(f, faces, T)
+    Ubar = hat_average_matrix(faces, nv)
+    y = np.zeros_like(v)
+    if op in ("B", "A"):
+        W = a[:, None, None] * D_apply(f, faces, v)
+        nk = v.shape[1]
+        z = bh_kernel_apply(T, L, Xr, N, a, W.reshape(nf, 3 * nk), "plain", 2.0 * s, Pbar)
+        y += 2.0 * D_transpose(f, faces, a[:, None, None] * z.reshape(-1, 3, nk), nv)
+    if op in ("B0", "A"):
+        W = a[:, None] * (Ubar @ v)
+        z = bh_kernel_apply(T, L, Xr, N, a, W, "low", 2.0 * s, Pbar)
+        y += 2.0 * (Ubar.T @ (a[:, None] * z))
+    if op == "L":
+        sigma = 2.0 - s
+        W = a[:, None] * (Ubar @ v)
+        z = bh_kernel_apply(T, L, Xr, N, a, W, "plain", 2.0 * sigma + 2.0, Pbar)
+        y += 2.0 * (Ubar.T @ (a[:, None] * z))
+    return y
+
+
 def bh_differential(f, faces, theta, leaf=8, p=6.0, mode="full"):
     """Barnes-Hut differential (§4.2), shape [nv,3].
 
