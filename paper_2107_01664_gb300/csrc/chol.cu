@@ -716,23 +716,50 @@ __global__ void k_chol_check(const double* __restrict__ part, int nblk, int k, d
     }
 }
 
-// per-component means of the k columns, in a fixed order (one block per component)
-__global__ void k_comp_mean(const int* __restrict__ comp_ptr, const int* __restrict__ comp_verts,
-                            const double* __restrict__ x, int k, double* __restrict__ mean) {
-    __shared__ double sh[256];
-    const int c = blockIdx.x, v0 = comp_ptr[c], v1 = comp_ptr[c + 1];
-    for (int j = 0; j < k; ++j) {
-        double s = 0.0;
-        for (int i = v0 + threadIdx.x; i < v1; i += 256) s += x[(size_t)comp_verts[i] * k + j];
-        sh[threadIdx.x] = s;
-        __syncthreads();
-        for (int w = 128; w > 0; w >>= 1) {
-            if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) mean[(size_t)c * k + j] = sh[0] / (double)(v1 - v0);
-        __syncthreads();
+// per-component means of the k columns in a fixed order: block (c, s)
+// sums slice s of component c's vertex list (CH_MSPLIT slices), then one
+// block per component adds the slices in order
+constexpr int CH_MSPLIT = 16;
+
+__global__ void __launch_bounds__(256)
+k_comp_partial(const int* __restrict__ comp_ptr, const int* __restrict__ comp_verts, const double* __restrict__ x,
+               int k, double* __restrict__ part) {
+    __shared__ double sh[256 / 32][CH_KMAX];
+    const int c = blockIdx.x, s = blockIdx.y;
+    const int v0 = comp_ptr[c], v1 = comp_ptr[c + 1];
+    const int len = (v1 - v0 + CH_MSPLIT - 1) / CH_MSPLIT;
+    const int a0 = v0 + s * len, a1 = min(v1, a0 + len);
+    double acc[CH_KMAX];
+#pragma unroll
+    for (int j = 0; j < CH_KMAX; ++j) acc[j] = 0.0;
+    for (int i = a0 + threadIdx.x; i < a1; i += 256) {
+        const double* xv = x + (size_t)comp_verts[i] * k;
+#pragma unroll
+        for (int j = 0; j < CH_KMAX; ++j)
+            if (j < k) acc[j] += xv[j];
     }
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < CH_KMAX; ++j) {
+        double v = acc[j];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[w][j] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < k) {
+        double t = 0.0;
+        for (int q = 0; q < 256 / 32; ++q) t += sh[q][threadIdx.x];
+        part[((size_t)c * CH_MSPLIT + s) * k + threadIdx.x] = t;
+    }
+}
+
+__global__ void k_comp_final(const int* __restrict__ comp_ptr, const double* __restrict__ part, int k,
+                             double* __restrict__ mean) {
+    const int c = blockIdx.x, j = threadIdx.x;
+    if (j >= k) return;
+    double t = 0.0;
+    for (int s = 0; s < CH_MSPLIT; ++s) t += part[((size_t)c * CH_MSPLIT + s) * k + j];
+    mean[(size_t)c * k + j] = t / (double)(comp_ptr[c + 1] - comp_ptr[c]);
 }
 
 __global__ void k_comp_sub(const int* __restrict__ comp_of, const double* __restrict__ mean, int nv, int k,
@@ -917,8 +944,12 @@ static int chol_factor(tp_mesh* m, cudaStream_t st) {
 // dst = src minus its per-component mean (k columns)
 static int comp_project(tp_mesh* m, const double* src, double* dst, int k, cudaStream_t st) {
     CholState* c = m->chol;
-    double* mean = c->part.as<double>();   // the first ncomp * 9 doubles of the partial-sum buffer
-    k_comp_mean<<<c->ncomp, 256, 0, st>>>(c->comp_ptr.as<int>(), c->comp_verts.as<int>(), src, k, mean);
+    double* mean = c->part.as<double>();                        // ncomp * 9 doubles
+    double* slices = mean + (size_t)c->ncomp * CH_KMAX;          // ncomp * CH_MSPLIT * 9 doubles
+    k_comp_partial<<<dim3(c->ncomp, CH_MSPLIT), 256, 0, st>>>(c->comp_ptr.as<int>(), c->comp_verts.as<int>(), src,
+                                                              k, slices);
+    TP_LAUNCH_CHECK();
+    k_comp_final<<<c->ncomp, 32, 0, st>>>(c->comp_ptr.as<int>(), slices, k, mean);
     TP_LAUNCH_CHECK();
     const size_t n = (size_t)m->nv * k;
     k_comp_sub<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c->comp_of.as<int>(), mean, m->nv, k, src, dst);
@@ -1029,8 +1060,9 @@ static int chol_run(tp_mesh* m, const tp_params* p, const double* b, double* z_o
     // per-block partials of the initial residual (rgrid blocks) and of the
     // sweep kernel (up to 2 blocks per SM)
     const size_t nparts = (size_t)std::max(rgrid, 2 * sm_count());
-    TP_TRY(ensure(c->part, sizeof(double) * ((size_t)c->ncomp * CH_KMAX + nparts * CH_KMAX) + 64));
-    double* partr = c->part.as<double>() + (size_t)c->ncomp * CH_KMAX;
+    const size_t head = (size_t)c->ncomp * CH_KMAX * (1 + CH_MSPLIT);   // means and their slices
+    TP_TRY(ensure(c->part, sizeof(double) * (head + nparts * CH_KMAX) + 64));
+    double* partr = c->part.as<double>() + head;
     TP_TRY(comp_project(m, b, c->bp.as<double>(), K, st));
     TP_CUDA(cudaMemsetAsync(c->x.ptr, 0, sizeof(double) * n, st));
     // clear done .. arrive; bad_pivot (from the factorisation) and the epoch stay

@@ -546,12 +546,19 @@ int adjoints_to_dE(tp_mesh* m, const double* adj, double* dE, cudaStream_t st) {
 // per target: r = sum_T h a_T and (H W)_S = sum_T h W_T.
 // ===========================================================================
 
+// Per source face the pair kernels read one vector X of NA values: [a, W_V]
+// (the operators with the high-order part) then [a, W_U] (those with a
+// low-order part); accumulator i gains h X[i], with h the high-order kernel
+// on the first NH entries and the low-order one on the rest. NH and NA are
+// even, so the pairs of packed FP32 arithmetic never straddle the parts.
 template <int OP, int KC> struct OpLayout {
     static constexpr bool HIGH = (OP == TP_OP_A || OP == TP_OP_B);
     static constexpr bool USEU = (OP != TP_OP_B);
-    static constexpr int NW = (HIGH ? 3 * KC : 0) + (USEU ? KC : 0);   // W values per face
-    static constexpr int NW4 = (NW + 3) / 4;
-    static constexpr int NA = (HIGH ? 1 + 3 * KC : 0) + (USEU ? 1 + KC : 0);  // accumulators
+    static constexpr int NH = HIGH ? 1 + 3 * KC : 0;          // high-order entries [a, W_V]
+    static constexpr int NL = USEU ? 1 + KC : 0;              // low-order entries [a, W_U]
+    static constexpr int NA = NH + NL;                        // accumulators = X entries
+    static constexpr int NW4 = (NA + 3) / 4;                  // X in 4-vectors
+    static_assert(NH % 2 == 0 && NA % 2 == 0, "pairs of accumulators stay within a part");
 };
 
 // per-face W (FP64 [nf][4*KC]: W_V at q*KC+c, then W_U at 3*KC+c) and its
@@ -581,47 +588,113 @@ __global__ void k_face_W(const double* __restrict__ v, int k, int col0, const in
     for (int i = 0; i < 4 * KC; ++i) W64[4 * KC * (size_t)S + i] = w[i];
     T* out = reinterpret_cast<T*>(Wp) + (size_t)S * 4 * nw4;
     int n = 0;
-    if (op == TP_OP_A || op == TP_OP_B)
+    if (op == TP_OP_A || op == TP_OP_B) {
+        out[n++] = (T)a;
         for (int i = 0; i < 3 * KC; ++i) out[n++] = (T)w[i];
-    if (op != TP_OP_B)
+    }
+    if (op != TP_OP_B) {
+        out[n++] = (T)a;
         for (int c = 0; c < KC; ++c) out[n++] = (T)w[3 * KC + c];
+    }
     while (n < 4 * nw4) out[n++] = T(0);
 }
 
-// One (target, source) term of the kernel-matrix products. SELF = the tile
-// may contain the target itself (d = 0), whose term must be dropped: the
-// kernels of B and L^{2-s} do not vanish at d = 0 by themselves.
+// ---- pairs of accumulators ------------------------------------------------
+// FP32: packed f32x2 arithmetic (one instruction for two IEEE operations,
+// the same results as two scalar ones); FP64: two scalar operations.
+template <typename T> struct P2T;
+template <> struct P2T<float> { using type = float2; };
+template <> struct P2T<double> { using type = double2; };
+
+__device__ __forceinline__ float2 pfma(float a, float2 b, float2 c) {   // a * b + c, a in both lanes
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %2};\n\tmov.b64 rb, {%3, %4};\n\tmov.b64 rc, {%5, %6};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ double2 pfma(double a, double2 b, double2 c) {
+    return make_double2(fma(a, b.x, c.x), fma(a, b.y, c.y));
+}
+__device__ __forceinline__ float2 padd(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+
+template <typename T> struct Acc2;
+template <> struct Acc2<float> {   // two Kahan accumulators
+    float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+    __device__ __forceinline__ void add(float2 x) {
+        const float2 y = psub(x, c);
+        const float2 t = padd(s, y);
+        c = psub(psub(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double value(int lane) const {
+        return lane ? (double)s.y - (double)c.y : (double)s.x - (double)c.x;
+    }
+};
+template <> struct Acc2<double> {
+    double2 s = make_double2(0.0, 0.0);
+    __device__ __forceinline__ void add(double2 x) {
+        s.x += x.x;
+        s.y += x.y;
+    }
+    __device__ __forceinline__ double value(int lane) const { return lane ? s.y : s.x; }
+};
+
+template <typename T>
+__device__ __forceinline__ typename P2T<T>::type p2zero() {
+    typename P2T<T>::type z;
+    z.x = T(0);
+    z.y = T(0);
+    return z;
+}
+
+// One (target, source) term of the kernel-matrix products on the source's
+// vector X (pairs x2[i] = X[2i], X[2i+1]). SELF = the tile may contain the
+// target itself (d = 0), whose term must be dropped: the kernels of B and
+// L^{2-s} do not vanish at d = 0 by themselves.
 template <typename T, int OP, bool SELF, int KC>
-__device__ __forceinline__ void apply_term(T dx, T dy, T dz, T nx, T ny, T nz, T at, T mx, T my, T mz,
-                                           const T* wv, T s_exp, T l_exp, T* pt) {
+__device__ __forceinline__ void apply_term(T dx, T dy, T dz, T nx, T ny, T nz, T mx, T my, T mz,
+                                           const typename P2T<T>::type* x2, T s_exp, T l_exp,
+                                           typename P2T<T>::type* pt) {
+    using L = OpLayout<OP, KC>;
     constexpr bool LOW = (OP == TP_OP_A || OP == TP_OP_B0);
-    constexpr bool HIGH = (OP == TP_OP_A || OP == TP_OP_B);
     T r2 = r2_eps(dx, dy, dz);
     if (OP == TP_OP_L) {
         T h = pow_(r2, -l_exp);
         if (SELF) h = r2 > T(2) * tiny_r2<T>() ? h : T(0);
-        pt[0] = fma(h, at, pt[0]);
 #pragma unroll
-        for (int i = 0; i < KC; ++i) pt[1 + i] = fma(h, wv[i], pt[1 + i]);
+        for (int i = 0; i < L::NA / 2; ++i) pt[i] = pfma(h, x2[i], pt[i]);
     } else {
         T hB = pow_(r2, -s_exp);
         if (SELF) hB = r2 > T(2) * tiny_r2<T>() ? hB : T(0);
-        int o = 0;
-        if (HIGH) {
-            pt[0] = fma(hB, at, pt[0]);
 #pragma unroll
-            for (int i = 0; i < 3 * KC; ++i) pt[1 + i] = fma(hB, wv[i], pt[1 + i]);
-            o = 1 + 3 * KC;
-        }
+        for (int i = 0; i < L::NH / 2; ++i) pt[i] = pfma(hB, x2[i], pt[i]);
         if (LOW) {
             T ir2 = rcp_(r2);
             T tS = (nx * dx + ny * dy + nz * dz) * ir2;
             T tT = (mx * dx + my * dy + mz * dz) * ir2;
             T h0 = T(0.5) * fma(tS, tS, tT * tT) * hB;   // (k2(S;T) + k2(T;S)) / 2 * |d|^{-2s}
-            const int wo = HIGH ? 3 * KC : 0;
-            pt[o] = fma(h0, at, pt[o]);
 #pragma unroll
-            for (int i = 0; i < KC; ++i) pt[o + 1 + i] = fma(h0, wv[wo + i], pt[o + 1 + i]);
+            for (int i = L::NH / 2; i < L::NA / 2; ++i) pt[i] = pfma(h0, x2[i], pt[i]);
         }
     }
 }
@@ -671,7 +744,9 @@ k_apply(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::typ
         block_box(bl[0], bl[1], bl[2], bh[0], bh[1], bh[2], sbox);
         thr2 = (float)center[3];
     }
-    Acc<T> acc[TT][L::NA];
+    using P2 = typename P2T<T>::type;
+    constexpr int NP = L::NA / 2;   // accumulator pairs
+    Acc2<T> acc[TT][NP];
     const int ntiles = (nf + NT - 1) / NT;
     const int k0 = blockIdx.y * tiles_per_split;
     const int k1 = min(k0 + tiles_per_split, ntiles);
@@ -691,21 +766,21 @@ k_apply(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::typ
         }
         __syncthreads();
         for (int c = 0; c < NT; c += CH) {
-            T pt[TT][L::NA];
+            P2 pt[TT][NP];
 #pragma unroll
             for (int j = 0; j < TT; ++j)
 #pragma unroll
-                for (int i = 0; i < L::NA; ++i) pt[j][i] = T(0);
+                for (int i = 0; i < NP; ++i) pt[j][i] = p2zero<T>();
             if (near || diag) {
                 for (int q = 0; q < CH; ++q) {
                     const int jj = c + q;
                     V4 s = sa[jj];
                     float4 l = near ? shl[jj] : make_float4(0.f, 0.f, 0.f, 0.f);
-                    T wv[4 * L::NW4];
+                    P2 wv[2 * L::NW4];
 #pragma unroll
                     for (int i = 0; i < L::NW4; ++i) {
                         V4 x = sw[jj * L::NW4 + i];
-                        wv[4 * i] = x.x; wv[4 * i + 1] = x.y; wv[4 * i + 2] = x.z; wv[4 * i + 3] = x.w;
+                        wv[2 * i].x = x.x; wv[2 * i].y = x.y; wv[2 * i + 1].x = x.z; wv[2 * i + 1].y = x.w;
                     }
                     T mx = 0, my = 0, mz = 0;
                     if (LOW) {
@@ -715,7 +790,7 @@ k_apply(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::typ
 #pragma unroll
                     for (int j = 0; j < TT; ++j)
                         apply_term<T, OP, true, KC>((tx[j] - s.x) + (T)(lx[j] - l.x), (ty[j] - s.y) + (T)(ly[j] - l.y),
-                                                    (tz[j] - s.z) + (T)(lz[j] - l.z), nx[j], ny[j], nz[j], s.w, mx,
+                                                    (tz[j] - s.z) + (T)(lz[j] - l.z), nx[j], ny[j], nz[j], mx,
                                                     my, mz, wv, s_exp, l_exp, pt[j]);
                 }
             } else {
@@ -723,11 +798,11 @@ k_apply(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::typ
                 for (int q = 0; q < CH; ++q) {
                     const int jj = c + q;
                     V4 s = sa[jj];
-                    T wv[4 * L::NW4];
+                    P2 wv[2 * L::NW4];
 #pragma unroll
                     for (int i = 0; i < L::NW4; ++i) {
                         V4 x = sw[jj * L::NW4 + i];
-                        wv[4 * i] = x.x; wv[4 * i + 1] = x.y; wv[4 * i + 2] = x.z; wv[4 * i + 3] = x.w;
+                        wv[2 * i].x = x.x; wv[2 * i].y = x.y; wv[2 * i + 1].x = x.z; wv[2 * i + 1].y = x.w;
                     }
                     T mx = 0, my = 0, mz = 0;
                     if (LOW) {
@@ -737,13 +812,13 @@ k_apply(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::typ
 #pragma unroll
                     for (int j = 0; j < TT; ++j)
                         apply_term<T, OP, false, KC>(tx[j] - s.x, ty[j] - s.y, tz[j] - s.z, nx[j], ny[j], nz[j],
-                                                     s.w, mx, my, mz, wv, s_exp, l_exp, pt[j]);
+                                                     mx, my, mz, wv, s_exp, l_exp, pt[j]);
                 }
             }
 #pragma unroll
             for (int j = 0; j < TT; ++j)
 #pragma unroll
-                for (int i = 0; i < L::NA; ++i) acc[j][i].add(pt[j][i]);
+                for (int i = 0; i < NP; ++i) acc[j][i].add(pt[j][i]);
         }
     }
 #pragma unroll
@@ -751,7 +826,7 @@ k_apply(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::typ
         if (tid[j] < nf)
 #pragma unroll
             for (int i = 0; i < L::NA; ++i)
-                part[((size_t)blockIdx.y * L::NA + i) * nf + tid[j]] = acc[j][i].value();
+                part[((size_t)blockIdx.y * L::NA + i) * nf + tid[j]] = acc[j][i / 2].value(i & 1);
 }
 
 // per face: z = (r/a) W_S - (H W)_S in FP64, then the corner values of the
