@@ -169,11 +169,17 @@ int tp_differential(tp_mesh* m, const tp_params* p, double* dE, int ptr_kind,
                     double* E_out, void* stream);
 
 /* y = O v for op in TP_OP_* and k columns (1 <= k <= 9), each column
- * separately, always by the direct all-pairs sums (theta is not used here;
- * the vector operator O_3 of §3.2.1 for k = 3), through the
+ * separately (the vector operator O_3 of §3.2.1 for k = 3), through the
  * kernel-matrix form of §5.1.1-5.1.3 and Appendix A:
  *   O v = 2 W^T [diag(diag(a)^-1 H a) - H] W v,
- * W = diag(a) D (op B) or the area-weighted face average (ops B0, L). */
+ * W = diag(a) D (op B) or the area-weighted face average (ops B0, L).
+ * theta = 0: H by the direct all-pairs sums. theta > 0 (FP32 only): H by
+ * Barnes-Hut over the tree and admissibility test of the energy (§4.1):
+ * an admissible node I contributes h(X_S, P_S; X_I, P_I) times the node
+ * sums of a and W, P_I the node-average projector of §5.1.4 (in the
+ * low-order kernel); inadmissible leaves are summed exactly. The row sums
+ * H a use the same approximation, so constants stay in the nullspace.
+ * precond_apply and precond_step use the same choice for their applies. */
 int fractional_apply(tp_mesh* m, const tp_params* p, int op, const double* v,
                      int k, double* y, int ptr_kind, void* stream);
 

@@ -207,11 +207,6 @@ __global__ void k_morton(const d4* __restrict__ X, int nf, const double* __restr
 }
 
 // sorted face tables, face boxes and radii
-struct FaceBox {
-    float lox, loy, loz, r2;
-    float hix, hiy, hiz, a;
-};
-
 __global__ void k_sorted_faces(const unsigned long long* __restrict__ keys, int nf,
                                const double* __restrict__ pos, const int* __restrict__ faces,
                                const double* __restrict__ center, const d4* __restrict__ f64a,
@@ -434,18 +429,29 @@ int bvh_build(tp_mesh* m, const tp_params* p, cudaStream_t st) {
     return TP_OK;
 }
 
+int bvh_view(tp_mesh* m, const tp_params* p, cudaStream_t st, BvhView* v) {
+    TP_TRY(bvh_build(m, p, st));
+    const NodeArrays na = node_arrays(m);
+    const NodeShape* shape = m->bvh_tmp.as<NodeShape>();
+    const int* right = (const int*)(shape + m->bvh_nodes);
+    v->nnodes = m->bvh_nodes;
+    v->maxdepth = m->bvh_maxdepth;
+    v->node = na.node;
+    v->nodelo = na.nodelo;
+    v->sa = m->bvh_f32a.as<float4>();
+    v->sb = m->bvh_f32b.as<float4>();
+    v->sl = m->bvh_f32c.as<float4>();
+    v->perm = m->bvh_perm.as<int>();
+    v->fbox = (const FaceBox*)(v->perm + m->nf);
+    v->right = right;
+    v->level_order = right + m->bvh_nodes;
+    v->level_off = m->bvh_level_off.data();
+    return TP_OK;
+}
+
 // ---------------------------------------------------------------------------
 // traversal
 // ---------------------------------------------------------------------------
-
-// squared distance between two boxes; max(0, ...) per axis, fixed op order
-__device__ __forceinline__ float box_dist2(float alx, float aly, float alz, float ahx, float ahy, float ahz,
-                                           const BvhNode& n) {
-    float gx = fmaxf(fmaxf(__fsub_rn(n.lox, ahx), __fsub_rn(alx, n.hix)), 0.f);
-    float gy = fmaxf(fmaxf(__fsub_rn(n.loy, ahy), __fsub_rn(aly, n.hiy)), 0.f);
-    float gz = fmaxf(fmaxf(__fsub_rn(n.loz, ahz), __fsub_rn(alz, n.hiz)), 0.f);
-    return __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
-}
 
 __device__ __forceinline__ float frcp(float x) {
     float r;
@@ -549,17 +555,17 @@ k_bh_energy(const BvhNode* __restrict__ node, const float4* __restrict__ nodelo,
 // device counters of Barnes-Hut interactions: [0] energy, [1] differential
 int bh_counter(tp_mesh* m, cudaStream_t st) {
     if (m->bhcount.ptr) return TP_OK;
-    TP_TRY(ensure(m->bhcount, 2 * sizeof(unsigned long long)));
-    TP_CUDA(cudaMemsetAsync(m->bhcount.ptr, 0, 2 * sizeof(unsigned long long), st));
+    TP_TRY(ensure(m->bhcount, BH_NCOUNT * sizeof(unsigned long long)));
+    TP_CUDA(cudaMemsetAsync(m->bhcount.ptr, 0, BH_NCOUNT * sizeof(unsigned long long), st));
     return TP_OK;
 }
 
-int bh_counts_read(tp_mesh* m, unsigned long long out[2], bool reset, cudaStream_t st) {
-    out[0] = out[1] = 0;
+int bh_counts_read(tp_mesh* m, unsigned long long out[BH_NCOUNT], bool reset, cudaStream_t st) {
+    for (int i = 0; i < BH_NCOUNT; ++i) out[i] = 0;
     if (!m->bhcount.ptr) return TP_OK;
-    TP_CUDA(cudaMemcpyAsync(out, m->bhcount.ptr, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+    TP_CUDA(cudaMemcpyAsync(out, m->bhcount.ptr, BH_NCOUNT * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     TP_CUDA(cudaStreamSynchronize(st));
-    if (reset) TP_CUDA(cudaMemsetAsync(m->bhcount.ptr, 0, 2 * sizeof(unsigned long long), st));
+    if (reset) TP_CUDA(cudaMemsetAsync(m->bhcount.ptr, 0, BH_NCOUNT * sizeof(unsigned long long), st));
     return TP_OK;
 }
 

@@ -185,7 +185,7 @@ int tp_mesh_destroy(tp_mesh* m) {
                   &m->f32c, &m->tilebox,
                   &m->f64a, &m->f64b, &m->fgrad, &m->rowptr, &m->col, &m->cotsrc, &m->diagpos, &m->val,
                   &m->dinv, &m->val32, &m->bvh_node, &m->bvh_perm, &m->bvh_keys, &m->bvh_tmp, &m->bvh_sortws,
-                  &m->bvh_f32a, &m->bvh_f32b, &m->bvh_f32c, &m->bvh_nodeP, &m->part, &m->part2, &m->scal, &m->corner,
+                  &m->bvh_f32a, &m->bvh_f32b, &m->bvh_f32c, &m->bh_apply_ws, &m->part, &m->part2, &m->scal, &m->corner,
                   &m->wv64, &m->wv32, &m->io_in, &m->io_out, &m->adj, &m->erow, &m->tlist, &m->rowsum,
                   &m->kry};
     for (Buf* b : all) release(*b);
@@ -285,7 +285,7 @@ int fractional_apply(tp_mesh* m, const tp_params* p, int op, const double* v, in
     TP_TRY(stage_in(m->io_in, v, bytes, ptr_kind, st, &vin));
     TP_TRY(ensure(m->io_out, bytes));
     double* out = ptr_kind == TP_PTR_DEVICE ? y : m->io_out.as<double>();
-    TP_TRY(apply_direct(m, p, op, (const double*)vin, k, out, st));
+    TP_TRY(apply_op(m, p, op, (const double*)vin, k, out, st));
     if (ptr_kind == TP_PTR_HOST) TP_TRY(copy_out(y, out, bytes, TP_PTR_HOST, st));
     return TP_OK;
 }
@@ -368,7 +368,7 @@ int tp_profile_read(tp_mesh* m, tp_kernel_stat* out, int max, int* n) {
     DeviceGuard g(m->device);
     static const char* names[PK_COUNT] = {"energy_direct", "diff_direct", "apply_A", "apply_B", "apply_B0",
                                           "apply_L", "bh_energy", "bh_diff", "bvh_build", "cg",
-                                          "chol_factor", "chol_solve"};
+                                          "chol_factor", "chol_solve", "bh_apply"};
     Profiler& P = m->prof;
     for (auto& pe : P.pending) {
         float ms = 0.f;
@@ -379,10 +379,11 @@ int tp_profile_read(tp_mesh* m, tp_kernel_stat* out, int max, int* n) {
         P.pool.push_back(pe.second.second);
     }
     P.pending.clear();
-    unsigned long long bh[2];
+    unsigned long long bh[BH_NCOUNT];
     TP_TRY(bh_counts_read(m, bh, true, nullptr));
     P.units[PK_BH_ENERGY] += (double)bh[0];
     P.units[PK_BH_DIFF] += (double)bh[1];
+    P.units[PK_BH_APPLY] += (double)bh[2];
     int k = 0;
     for (int i = 0; i < PK_COUNT && k < max; ++i) {
         if (P.launches[i] == 0) continue;

@@ -930,6 +930,273 @@ static int launch_apply(tp_mesh* m, const tp_params* p, int op, const double* v,
     return fail(TP_ERR_INVALID_ARG, "unknown operator");
 }
 
+// ===========================================================================
+// Barnes-Hut operator applies: the kernel-matrix products of §5.1.1-5.1.3
+// taken over the admissible sets of §4.1 (the same tree and test as the
+// Barnes-Hut energy). An admissible node I contributes h(X_S, P_S; X_I, P_I)
+// times the node sums of the source vectors X = [a, W_V, a, W_U]; the
+// source-side k_2 of the low-order kernel uses the node-average projector
+// P_I = a_I^-1 sum a_T N_T N_T^T (§5.1.4). An inadmissible leaf is summed
+// exactly, face by face. The diagonal of [diag(H a / a) - H] uses the same
+// approximate row sums, so constants stay in the nullspace.
+// ===========================================================================
+
+// sorted copies of the per-face vectors X
+template <int NW4>
+__global__ void k_sort_X(const float4* __restrict__ Wp, const int* __restrict__ perm, int nf,
+                         float4* __restrict__ Ws) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    const float4* src = Wp + (size_t)perm[i] * NW4;
+    float4* dst = Ws + (size_t)i * NW4;
+#pragma unroll
+    for (int q = 0; q < NW4; ++q) dst[q] = src[q];
+}
+
+__device__ __forceinline__ float4 f4add(float4 a, float4 b) {
+    return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+
+// node sums of X and (PROJ) node-average projectors (upper triangle xx, xy,
+// xz, yy, yz, zz in two float4), one depth level per launch, deepest first
+template <int NW4, bool PROJ>
+__global__ void k_node_X(const BvhNode* __restrict__ node, const int* __restrict__ right,
+                         const int* __restrict__ order, int n0, int n1, const float4* __restrict__ Ws,
+                         const float4* __restrict__ sa, const float4* __restrict__ sb,
+                         float4* __restrict__ nodeX, float4* __restrict__ nodeP) {
+    const int k = n0 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n1) return;
+    const int id = order[k];
+    const BvhNode n = node[id];
+    float4 acc[NW4];
+#pragma unroll
+    for (int q = 0; q < NW4; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    float P[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (n.leaf) {
+        float asum = 0.f;
+        for (int i = n.first; i < n.first + n.count; ++i) {
+#pragma unroll
+            for (int q = 0; q < NW4; ++q) acc[q] = f4add(acc[q], Ws[(size_t)i * NW4 + q]);
+            if (PROJ) {
+                const float a = sa[i].w;
+                const float4 N = sb[i];
+                P[0] += a * N.x * N.x; P[1] += a * N.x * N.y; P[2] += a * N.x * N.z;
+                P[3] += a * N.y * N.y; P[4] += a * N.y * N.z; P[5] += a * N.z * N.z;
+                asum += a;
+            }
+        }
+        if (PROJ)
+            for (int c = 0; c < 6; ++c) P[c] /= asum;
+    } else {
+        const int L = id + 1, R = right[id];
+#pragma unroll
+        for (int q = 0; q < NW4; ++q) acc[q] = f4add(nodeX[(size_t)L * NW4 + q], nodeX[(size_t)R * NW4 + q]);
+        if (PROJ) {
+            const float aL = node[L].a, aR = node[R].a, ia = 1.f / (aL + aR);
+            const float4 l0 = nodeP[2 * L], l1 = nodeP[2 * L + 1], r0 = nodeP[2 * R], r1 = nodeP[2 * R + 1];
+            P[0] = (aL * l0.x + aR * r0.x) * ia; P[1] = (aL * l0.y + aR * r0.y) * ia;
+            P[2] = (aL * l0.z + aR * r0.z) * ia; P[3] = (aL * l0.w + aR * r0.w) * ia;
+            P[4] = (aL * l1.x + aR * r1.x) * ia; P[5] = (aL * l1.y + aR * r1.y) * ia;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < NW4; ++q) nodeX[(size_t)id * NW4 + q] = acc[q];
+    if (PROJ) {
+        nodeP[2 * id] = make_float4(P[0], P[1], P[2], P[3]);
+        nodeP[2 * id + 1] = make_float4(P[4], P[5], 0.f, 0.f);
+    }
+}
+
+// Warp-cooperative traversal (as in the Barnes-Hut energy): each lane owns
+// one sorted target; the warp walks the pre-order node sequence together and
+// a lane is active at node id only when id >= its escape marker. Near pairs
+// use the compensated (hi + lo) barycenter differences. The sums per target
+// run in FP32 chunks of 32 terms folded into Kahan accumulators, written in
+// face order for the FP64 combine.
+template <int OP, int KC>
+__global__ void __launch_bounds__(128)
+k_bh_apply(const BvhNode* __restrict__ node, const float4* __restrict__ nodelo, int nnodes,
+           const float4* __restrict__ sa, const float4* __restrict__ sb, const float4* __restrict__ sl,
+           const FaceBox* __restrict__ fbox, const int* __restrict__ perm, int nf,
+           const float4* __restrict__ Ws, const float4* __restrict__ nodeX, const float4* __restrict__ nodeP,
+           float theta2, float s_exp, float l_exp, double* __restrict__ part,
+           unsigned long long* __restrict__ count) {
+    using L = OpLayout<OP, KC>;
+    constexpr bool LOW = (OP == TP_OP_A || OP == TP_OP_B0);
+    constexpr int NP = L::NA / 2;
+    constexpr int NW4 = L::NW4;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool has = i < nf;
+    const int ii = has ? i : 0;
+    const float4 A = sa[ii], B = sb[ii], Al = sl[ii];
+    const FaceBox fb = fbox[ii];
+    int skip = has ? 0 : nnodes;
+    float2 pt[NP];
+    Acc2<float> acc[NP];
+#pragma unroll
+    for (int c = 0; c < NP; ++c) pt[c] = make_float2(0.f, 0.f);
+    int run = 0;
+    unsigned nint = 0;
+    int id = 0;
+    while (id < nnodes) {
+        const BvhNode n = node[id];
+        bool desc = false;
+        if (id >= skip) {
+            const float d2 = box_dist2(fb.lox, fb.loy, fb.loz, fb.hix, fb.hiy, fb.hiz, n);
+            const float mr2 = fmaxf(fb.r2, n.r2);
+            if (mr2 < __fmul_rn(theta2, d2)) {
+                const float4 nl = nodelo[id];
+                const float dx = (A.x - n.cx) + (Al.x - nl.x), dy = (A.y - n.cy) + (Al.y - nl.y),
+                            dz = (A.z - n.cz) + (Al.z - nl.z);
+                float2 x2[2 * NW4];
+#pragma unroll
+                for (int q = 0; q < NW4; ++q) {
+                    const float4 x = nodeX[(size_t)id * NW4 + q];
+                    x2[2 * q] = make_float2(x.x, x.y);
+                    x2[2 * q + 1] = make_float2(x.z, x.w);
+                }
+                const float r2 = r2_eps(dx, dy, dz);
+                if (OP == TP_OP_L) {
+                    const float h = pow_(r2, -l_exp);
+#pragma unroll
+                    for (int c = 0; c < NP; ++c) pt[c] = pfma(h, x2[c], pt[c]);
+                } else {
+                    const float hB = pow_(r2, -s_exp);
+#pragma unroll
+                    for (int c = 0; c < L::NH / 2; ++c) pt[c] = pfma(hB, x2[c], pt[c]);
+                    if (LOW) {
+                        const float4 p0 = nodeP[2 * id], p1 = nodeP[2 * id + 1];
+                        const float ir2 = rcp_(r2);
+                        const float tS = (B.x * dx + B.y * dy + B.z * dz) * ir2;
+                        const float qx = p0.x * dx + p0.y * dy + p0.z * dz;
+                        const float qy = p0.y * dx + p0.w * dy + p1.x * dz;
+                        const float qz = p0.z * dx + p1.x * dy + p1.y * dz;
+                        const float tT2 = (qx * qx + qy * qy + qz * qz) * (ir2 * ir2);   // |P_I d|^2 / |d|^4
+                        const float h0 = 0.5f * fmaf(tS, tS, tT2) * hB;
+#pragma unroll
+                        for (int c = L::NH / 2; c < NP; ++c) pt[c] = pfma(h0, x2[c], pt[c]);
+                    }
+                }
+                ++nint;
+                if (++run == 32) {
+#pragma unroll
+                    for (int c = 0; c < NP; ++c) {
+                        acc[c].add(pt[c]);
+                        pt[c] = make_float2(0.f, 0.f);
+                    }
+                    run = 0;
+                }
+                skip = n.skip;
+            } else if (n.leaf) {
+                for (int j = n.first; j < n.first + n.count; ++j) {
+                    if (j == i) continue;
+                    const float4 s = sa[j], l = sl[j], m = sb[j];
+                    float2 x2[2 * NW4];
+#pragma unroll
+                    for (int q = 0; q < NW4; ++q) {
+                        const float4 x = Ws[(size_t)j * NW4 + q];
+                        x2[2 * q] = make_float2(x.x, x.y);
+                        x2[2 * q + 1] = make_float2(x.z, x.w);
+                    }
+                    apply_term<float, OP, false, KC>((A.x - s.x) + (Al.x - l.x), (A.y - s.y) + (Al.y - l.y),
+                                                     (A.z - s.z) + (Al.z - l.z), B.x, B.y, B.z, m.x, m.y, m.z,
+                                                     x2, s_exp, l_exp, pt);
+                    ++nint;
+                }
+#pragma unroll
+                for (int c = 0; c < NP; ++c) {
+                    acc[c].add(pt[c]);
+                    pt[c] = make_float2(0.f, 0.f);
+                }
+                run = 0;
+                skip = n.skip;
+            } else {
+                desc = true;
+            }
+        }
+        id = __any_sync(0xffffffffu, desc) ? id + 1 : n.skip;
+    }
+#pragma unroll
+    for (int c = 0; c < NP; ++c) acc[c].add(pt[c]);
+    if (has) {
+        const int S = perm[i];
+#pragma unroll
+        for (int c = 0; c < L::NA; ++c) part[(size_t)c * nf + S] = acc[c / 2].value(c & 1);
+    }
+    if (count && nint) atomicAdd(count, (unsigned long long)nint);
+}
+
+template <int OP, int KC>
+static int launch_bh_apply_op(tp_mesh* m, const tp_params* p, const double* v, int k, double* y,
+                              cudaStream_t st) {
+    using L = OpLayout<OP, KC>;
+    constexpr bool LOW = (OP == TP_OP_A || OP == TP_OP_B0);
+    constexpr int NW4 = L::NW4;
+    BvhView bv;
+    TP_TRY(bvh_view(m, p, st, &bv));
+    const int nf = m->nf, nn = bv.nnodes;
+    const double s = 2.0 - 2.0 / p->p;
+    const double l_exp = 3.0 - s;
+    TP_TRY(ensure(m->part, sizeof(double) * (size_t)L::NA * nf));
+    TP_TRY(ensure(m->wv64, sizeof(double) * 4 * KC * (size_t)nf));
+    TP_TRY(ensure(m->wv32, sizeof(float4) * NW4 * (size_t)nf));
+    TP_TRY(ensure(m->corner, sizeof(double) * 3 * (size_t)nf * k));
+    TP_TRY(ensure(m->bh_apply_ws, sizeof(float4) * ((size_t)NW4 * nf + (size_t)NW4 * nn + 2 * (size_t)nn)));
+    float4* Ws = m->bh_apply_ws.as<float4>();
+    float4* nodeX = Ws + (size_t)NW4 * nf;
+    float4* nodeP = nodeX + (size_t)NW4 * nn;
+    TP_TRY(bh_counter(m, st));
+    unsigned long long* cnt = m->bhcount.as<unsigned long long>() + 2;
+    for (int col0 = 0; col0 < k; col0 += KC) {
+        k_face_W<float, KC><<<(nf + 255) / 256, 256, 0, st>>>(v, k, col0, m->faces.as<int>(), nf,
+                                                              m->f64a.as<d4>(), m->fgrad.as<double>(), OP,
+                                                              m->wv64.as<double>(), m->wv32.as<float4>(), NW4);
+        TP_LAUNCH_CHECK();
+        k_sort_X<NW4><<<(nf + 255) / 256, 256, 0, st>>>(m->wv32.as<float4>(), bv.perm, nf, Ws);
+        TP_LAUNCH_CHECK();
+        for (int d = bv.maxdepth; d >= 0; --d) {
+            const int n0 = bv.level_off[d], n1 = bv.level_off[d + 1];
+            k_node_X<NW4, LOW><<<(n1 - n0 + 127) / 128, 128, 0, st>>>(bv.node, bv.right, bv.level_order, n0, n1,
+                                                                     Ws, bv.sa, bv.sb, nodeX, nodeP);
+            TP_LAUNCH_CHECK();
+        }
+        {
+            ProfScope ps(m, PK_BH_APPLY, 0.0, st);
+            m->prof.cols[PK_BH_APPLY] += KC;
+            k_bh_apply<OP, KC><<<(nf + 127) / 128, 128, 0, st>>>(
+                bv.node, bv.nodelo, nn, bv.sa, bv.sb, bv.sl, bv.fbox, bv.perm, nf, Ws, nodeX, nodeP,
+                (float)(p->theta * p->theta), (float)s, (float)l_exp, m->part.as<double>(), cnt);
+        }
+        TP_LAUNCH_CHECK();
+        k_apply_combine<OP, KC><<<(nf + 255) / 256, 256, 0, st>>>(m->part.as<double>(), 1, nf,
+                                                                  m->f64a.as<d4>(), m->fgrad.as<double>(),
+                                                                  m->wv64.as<double>(), k, col0,
+                                                                  m->corner.as<double>());
+        TP_LAUNCH_CHECK();
+    }
+    return corners_to_vertices(m, m->corner.as<double>(), k, y, st);
+}
+
+int apply_bh(tp_mesh* m, const tp_params* p, int op, const double* v, int k, double* y, cudaStream_t st) {
+    if (p->precision != TP_PREC_FP32) return fail(TP_ERR_INVALID_ARG, "Barnes-Hut applies run in FP32 only");
+    const bool wide = k > 3;
+    switch (op) {
+        case TP_OP_A: return wide ? launch_bh_apply_op<TP_OP_A, 9>(m, p, v, k, y, st)
+                                  : launch_bh_apply_op<TP_OP_A, 3>(m, p, v, k, y, st);
+        case TP_OP_B: return wide ? launch_bh_apply_op<TP_OP_B, 9>(m, p, v, k, y, st)
+                                  : launch_bh_apply_op<TP_OP_B, 3>(m, p, v, k, y, st);
+        case TP_OP_B0: return wide ? launch_bh_apply_op<TP_OP_B0, 9>(m, p, v, k, y, st)
+                                   : launch_bh_apply_op<TP_OP_B0, 3>(m, p, v, k, y, st);
+        case TP_OP_L: return wide ? launch_bh_apply_op<TP_OP_L, 9>(m, p, v, k, y, st)
+                                  : launch_bh_apply_op<TP_OP_L, 3>(m, p, v, k, y, st);
+    }
+    return fail(TP_ERR_INVALID_ARG, "unknown operator");
+}
+
+int apply_op(tp_mesh* m, const tp_params* p, int op, const double* v, int k, double* y, cudaStream_t st) {
+    return p->theta > 0.0 ? apply_bh(m, p, op, v, k, y, st) : apply_direct(m, p, op, v, k, y, st);
+}
+
 int apply_direct(tp_mesh* m, const tp_params* p, int op, const double* v, int k, double* y,
                  cudaStream_t st) {
     return p->precision == TP_PREC_FP64 ? launch_apply<double>(m, p, op, v, k, y, st)

@@ -59,7 +59,7 @@ int precond_apply_dev(tp_mesh* m, const tp_params* p, const double* b, int k, do
     int it1 = 0, it2 = 0;
     int s1 = cg_solve(m, p, b, k, m->prec[0].as<double>(), st, &it1);
     if (s1 != TP_OK && (strict || s1 != TP_ERR_NOT_CONVERGED)) return s1;
-    TP_TRY(apply_direct(m, p, TP_OP_L, m->prec[0].as<double>(), k, m->prec[1].as<double>(), st));
+    TP_TRY(apply_op(m, p, TP_OP_L, m->prec[0].as<double>(), k, m->prec[1].as<double>(), st));
     TP_TRY(project_mean_zero(m, m->prec[1].as<double>(), k, st));
     int s2 = cg_solve(m, p, m->prec[1].as<double>(), k, z, st, &it2);
     if (s2 != TP_OK && (strict || s2 != TP_ERR_NOT_CONVERGED)) return s2;
@@ -129,7 +129,7 @@ static int unpack(const double* srcp, int nv, const std::vector<double*>& dst, c
 
 // y = A v on packed columns (mean-zero output)
 static int apply_A_packed(tp_mesh* m, const tp_params* p, const double* v, int k, double* y, cudaStream_t st) {
-    TP_TRY(apply_direct(m, p, TP_OP_A, v, k, y, st));
+    TP_TRY(apply_op(m, p, TP_OP_A, v, k, y, st));
     return project_mean_zero(m, y, k, st);
 }
 
@@ -432,7 +432,7 @@ int precond_step_dev(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp
     tp_step_report r{};
     r.status = TP_OK;
     const double pairs0 = m->pairs;
-    unsigned long long bh0[2];
+    unsigned long long bh0[BH_NCOUNT];
     TP_TRY(bh_counts_read(m, bh0, false, st));
     TP_CUDA(cudaMemcpyAsync(f0, m->pos.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
 
@@ -554,9 +554,10 @@ int precond_step_dev(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp
     TP_TRY(energy_value(m, p, &r.E_after, st));
     r.krylov_iters = ks.iters;
     r.cg_iters = ks.cg_iters;
-    unsigned long long bh1[2];
+    unsigned long long bh1[BH_NCOUNT];
     TP_TRY(bh_counts_read(m, bh1, false, st));
-    r.pair_interactions = (m->pairs - pairs0) + (double)(bh1[0] - bh0[0]) + (double)(bh1[1] - bh0[1]);
+    r.pair_interactions = (m->pairs - pairs0) + (double)(bh1[0] - bh0[0]) + (double)(bh1[1] - bh0[1]) +
+                          (double)(bh1[2] - bh0[2]);
     if (rep) *rep = r;
     return TP_OK;
 }

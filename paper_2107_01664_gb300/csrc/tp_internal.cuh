@@ -73,12 +73,45 @@ struct BvhNode {          // 64 bytes, FP32 (pair path)
     int first, count, skip, leaf;  // face range in Morton order, escape index, leaf flag
 };
 
+// sorted (Morton order) target face: bounding box of its vertices, squared
+// radius from its barycenter, area
+struct FaceBox {
+    float lox, loy, loz, r2;
+    float hix, hiy, hiz, a;
+};
+
+// squared distance between a face box and a node box; max(0, ...) per axis,
+// fixed operation order (the admissibility test of §4.1 is decided in FP32
+// identically by every kernel)
+__device__ __forceinline__ float box_dist2(float alx, float aly, float alz, float ahx, float ahy, float ahz,
+                                           const BvhNode& n) {
+    float gx = fmaxf(fmaxf(__fsub_rn(n.lox, ahx), __fsub_rn(alx, n.hix)), 0.f);
+    float gy = fmaxf(fmaxf(__fsub_rn(n.loy, ahy), __fsub_rn(aly, n.hiy)), 0.f);
+    float gz = fmaxf(fmaxf(__fsub_rn(n.loz, ahz), __fsub_rn(alz, n.hiz)), 0.f);
+    return __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
+}
+
+// read-only view of a built tree for kernels outside bvh.cu
+struct BvhView {
+    int nnodes = 0, maxdepth = 0;
+    const BvhNode* node = nullptr;
+    const float4* nodelo = nullptr;      // low parts of the node barycenters
+    const float4* sa = nullptr;          // sorted faces: X - c, a
+    const float4* sb = nullptr;          // sorted faces: N
+    const float4* sl = nullptr;          // sorted faces: low parts of X - c
+    const FaceBox* fbox = nullptr;
+    const int* perm = nullptr;           // sorted position -> face
+    const int* right = nullptr;          // right child of an inner node
+    const int* level_order = nullptr;    // nodes grouped by depth
+    const int* level_off = nullptr;      // host: offsets of the depths in level_order
+};
+
 // ---------------------------------------------------------------------------
 // per-mesh kernel statistics (CUDA events on the launching stream)
 // ---------------------------------------------------------------------------
 
 enum ProfKey { PK_ENERGY = 0, PK_DIFF, PK_APPLY_A, PK_APPLY_B, PK_APPLY_B0, PK_APPLY_L, PK_BH_ENERGY,
-               PK_BH_DIFF, PK_BVH_BUILD, PK_CG, PK_CHOL_FACTOR, PK_CHOL_SOLVE, PK_COUNT };
+               PK_BH_DIFF, PK_BVH_BUILD, PK_CG, PK_CHOL_FACTOR, PK_CHOL_SOLVE, PK_BH_APPLY, PK_COUNT };
 
 struct Profiler {
     bool on = false;
@@ -127,7 +160,7 @@ struct tp_mesh {
     bool bvh_valid = false;
     tp::Buf bvh_node, bvh_perm, bvh_keys, bvh_tmp, bvh_sortws;
     tp::Buf bvh_f32a, bvh_f32b, bvh_f32c;   // face tables (and low parts) permuted to Morton order
-    tp::Buf bvh_nodeP;            // float [nodes*8] node-average projector (upper triangle) for B0
+    tp::Buf bh_apply_ws;          // Barnes-Hut applies: sorted X vectors, node sums, node projectors
     // workspaces
     tp::Buf part, part2, scal, corner, wv64, wv32, tmpv[8];
     tp::Buf io_in, io_out, adj, erow, tlist, rowsum;
@@ -174,6 +207,12 @@ int adjoints_to_dE(tp_mesh* m, const double* adj_dev, double* dE_dev, cudaStream
 // y = O v (device, [nv*k]); direct all pairs
 int apply_direct(tp_mesh* m, const tp_params* p, int op, const double* v_dev, int k,
                  double* y_dev, cudaStream_t st);
+// y = O v over the Barnes-Hut interaction lists (theta > 0, FP32)
+int apply_bh(tp_mesh* m, const tp_params* p, int op, const double* v_dev, int k, double* y_dev,
+             cudaStream_t st);
+// direct for theta = 0, Barnes-Hut otherwise
+int apply_op(tp_mesh* m, const tp_params* p, int op, const double* v_dev, int k, double* y_dev,
+             cudaStream_t st);
 
 // -------- bvh.cu -----------------------------------------------------------
 int bvh_build(tp_mesh* m, const tp_params* p, cudaStream_t st);
@@ -182,7 +221,10 @@ int energy_rows_bh(tp_mesh* m, const tp_params* p, const int32_t* targets_dev, i
 int diff_adjoints_bh(tp_mesh* m, const tp_params* p, double* adj_dev, double* erow_dev,
                      cudaStream_t st);
 int bh_counter(tp_mesh* m, cudaStream_t st);
-int bh_counts_read(tp_mesh* m, unsigned long long out[2], bool reset, cudaStream_t st);
+// device counters of Barnes-Hut interactions: [0] energy, [1] differential, [2] operator applies
+constexpr int BH_NCOUNT = 3;
+int bh_counts_read(tp_mesh* m, unsigned long long out[BH_NCOUNT], bool reset, cudaStream_t st);
+int bvh_view(tp_mesh* m, const tp_params* p, cudaStream_t st, BvhView* out);   // builds the tree if needed
 
 // -------- cg.cu ------------------------------------------------------------
 int laplacian_setup(tp_mesh* m);                        // CSR pattern (host, once)

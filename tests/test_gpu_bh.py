@@ -3,8 +3,10 @@ the C ABI: theta = 0 equals the direct sum; at theta in {0.25, 0.5} the GPU
 energy, energy rows and both differential modes equal the oracle's
 Barnes-Hut evaluation over the same tree (FP32 pair terms: 1e-5); the
 approximation error against the direct sum is reported and falls with
-theta. Full sizes: the 20,000-face torus and a 64-target sample of the
-1,310,720-face icosphere."""
+theta. The Barnes-Hut operator applies (A, B, B0, L^{2-s}, 3 and 9
+columns) equal the oracle's over the same tree to 1e-5 and keep constants
+in the nullspace; a constrained step runs on them. Full sizes: the
+20,000-face torus and a 64-target sample of the 1,310,720-face icosphere."""
 import numpy as np
 import pytest
 
@@ -96,6 +98,75 @@ def test_bh_rows_with_device_targets_and_repeat(lib, meshes):
     assert np.array_equal(r1, r2)
     ref, _ = O.bh_energy_rows(V, F, 0.5, 8, 6.0, tg)
     assert rel(r1, ref) <= TOL32
+
+
+@pytest.mark.parametrize("op", ["A", "B", "B0", "L"])
+@pytest.mark.parametrize("name", ["ico3", "torus30x11"])
+@pytest.mark.parametrize("k", [3, 9])
+def test_bh_apply_matches_oracle_bh(lib, meshes, op, name, k):
+    from synth import vertex_vectors
+    V, F, m = meshes[name]
+    v = vertex_vectors(len(V), k, 13)
+    ref = O.bh_apply_operator(V, F, v, op, 0.5)
+    got = lib.fractional_apply(m, op, v, lib.params(theta=0.5))
+    assert rel(got, ref) <= TOL32
+
+
+@pytest.mark.parametrize("op", ["A", "L"])
+def test_bh_apply_tiny_theta_is_direct_and_keeps_constants(lib, meshes, op):
+    from synth import vertex_vectors
+    V, F, m = meshes["ico3"]
+    v = vertex_vectors(len(V), 3, 14)
+    got = lib.fractional_apply(m, op, v, lib.params(theta=1e-9))
+    assert rel(got, O.apply_operator(V, F, v, op)) <= TOL32
+    scale = np.abs(lib.fractional_apply(m, op, v, lib.params(theta=0.7))).max()
+    one = lib.fractional_apply(m, op, np.ones((len(V), 1)), lib.params(theta=0.7))
+    assert np.abs(one).max() <= 1e-5 * scale
+
+
+def test_bh_apply_leaf_size_and_error_trend(lib, meshes):
+    from synth import vertex_vectors
+    V, F, m = meshes["torus30x11"]
+    v = vertex_vectors(len(V), 3, 15)
+    exact = O.apply_operator(V, F, v, "A")
+    errs = []
+    for th in (0.25, 0.5, 1.0):
+        got = lib.fractional_apply(m, "A", v, lib.params(theta=th, leaf_size=4))
+        assert rel(got, O.bh_apply_operator(V, F, v, "A", th, leaf=4)) <= TOL32
+        errs.append(rel(got, exact))
+    assert errs[0] < errs[1] < errs[2]
+
+
+def test_precond_step_on_bh_applies(lib):
+    # theta > 0: energy, differential and every operator apply of the step
+    # use the tree; the step descends and meets the constraints
+    import torch
+    V, F = workload("icosphere_l3")
+    A0, V0 = O.total_area(V, F), O.total_volume(V, F)
+    with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as m:
+        c = lib.tp_constraints(flags=3, A0=A0, V0=V0)
+        rep_bh = lib.precond_step(m, c, lib.params(theta=0.5, krylov_max=300, proj_iters=3))
+        f_bh = m.get_positions()
+    with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as m:
+        rep = lib.precond_step(m, c, lib.params(krylov_max=300, proj_iters=3))
+    assert rep_bh["status"] == 0 and rep_bh["slope"] < 0 and rep_bh["E_after"] < rep_bh["E_before"]
+    assert abs(O.total_area(f_bh, F) - A0) < 1e-7 * A0
+    assert 0 < rep_bh["pair_interactions"] < rep["pair_interactions"]
+
+
+def test_torus20k_bh_apply(lib):
+    # full size: constants in the nullspace, approximation error of the
+    # 9-column A apply against the direct apply at theta = 0.5
+    import torch
+    from synth import vertex_vectors
+    V, F = workload("torus_20k")
+    v = vertex_vectors(len(V), 9, 16)
+    with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as m:
+        d = lib.fractional_apply(m, "A", v, lib.params())
+        b = lib.fractional_apply(m, "A", v, lib.params(theta=0.5))
+        one = lib.fractional_apply(m, "A", np.ones((len(V), 1)), lib.params(theta=0.5))
+    assert rel(b, d) < 2e-3
+    assert np.abs(one).max() <= 1e-5 * np.abs(b).max()
 
 
 def test_torus20k_bh(lib):
