@@ -12,7 +12,10 @@
 // FP32 and the runs are added with Kahan compensation; partials and the
 // final per-face combination are FP64. The FP64 path runs the same kernels
 // with double arithmetic.
+#include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
 
 #include "tp_internal.cuh"
 
@@ -137,17 +140,50 @@ struct Grid {
     int bx, nsplit, tiles_per_split;
 };
 
-static Grid make_grid(int nt, int nf, int tt) {
+// resident blocks per SM of a kernel (cached per kernel and device)
+static int resident_per_sm(const void* fn, int threads) {
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> cache;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(fn, dev);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, 0) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = 1;
+    }
+    cache[key] = n;
+    return n;
+}
+
+// Source splits. Each block of a target row takes tiles_per_split source
+// tiles, and the grid runs in waves of (resident blocks per SM x SMs), so
+// the kernel time goes like waves x tiles_per_split. The split count
+// minimises that, plus a small charge per split for the partial sums the
+// FP64 combine reads (a split's partials cost about a twentieth of a tile).
+static Grid make_grid(int nt, int nf, int tt, int per_sm) {
     Grid g;
     g.bx = (nt + NT * tt - 1) / (NT * tt);
     if (g.bx < 1) g.bx = 1;
-    int ntiles = (nf + NT - 1) / NT;
-    int want = sm_count() * 8;  // blocks in flight for a full GPU
-    int ns = (want + g.bx - 1) / g.bx;
-    if (ns < 1) ns = 1;
-    if (ns > ntiles) ns = ntiles;
-    g.tiles_per_split = (ntiles + ns - 1) / ns;
-    g.nsplit = (ntiles + g.tiles_per_split - 1) / g.tiles_per_split;
+    const int ntiles = (nf + NT - 1) / NT;
+    const long slots = (long)std::max(1, per_sm) * sm_count();
+    double best = 1e300;
+    g.tiles_per_split = ntiles;
+    g.nsplit = 1;
+    for (int ns = 1; ns <= std::min(ntiles, 64); ++ns) {
+        const int tps = (ntiles + ns - 1) / ns;
+        const int nsp = (ntiles + tps - 1) / tps;
+        const long waves = ((long)g.bx * nsp + slots - 1) / slots;
+        const double cost = (double)waves * tps + 0.05 * nsp;
+        if (cost < best - 1e-9) {
+            best = cost;
+            g.tiles_per_split = tps;
+            g.nsplit = nsp;
+        }
+    }
     return g;
 }
 
@@ -268,7 +304,7 @@ static int launch_energy(tp_mesh* m, const tp_params* p, const int32_t* tl, int 
                          cudaStream_t st) {
     using V4 = typename V4T<T>::type;
     constexpr int TT = sizeof(T) == 4 ? 4 : 2;
-    Grid g = make_grid(nt, m->nf, TT);
+    Grid g = make_grid(nt, m->nf, TT, resident_per_sm((const void*)k_energy<T, true, TT>, NT));
     TP_TRY(ensure(m->part, sizeof(double) * (size_t)g.nsplit * nt));
     const V4* fa = (const V4*)(sizeof(T) == 4 ? m->f32a.ptr : m->f64a.ptr);
     const V4* fb = (const V4*)(sizeof(T) == 4 ? m->f32b.ptr : m->f64b.ptr);
@@ -463,7 +499,7 @@ template <typename T>
 static int launch_diff(tp_mesh* m, const tp_params* p, double* adj, double* erow, cudaStream_t st) {
     using V4 = typename V4T<T>::type;
     constexpr int TT = sizeof(T) == 4 ? 2 : 1;
-    Grid g = make_grid(m->nf, m->nf, TT);
+    Grid g = make_grid(m->nf, m->nf, TT, resident_per_sm((const void*)k_diff<T, true, TT>, NT));
     TP_TRY(ensure(m->part, sizeof(double) * (size_t)g.nsplit * NADJ * m->nf));
     const V4* fa = (const V4*)(sizeof(T) == 4 ? m->f32a.ptr : m->f64a.ptr);
     const V4* fb = (const V4*)(sizeof(T) == 4 ? m->f32b.ptr : m->f64b.ptr);
@@ -627,28 +663,17 @@ __device__ __forceinline__ float2 padd(float2 a, float2 b) {
         : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
     return d;
 }
-__device__ __forceinline__ float2 psub(float2 a, float2 b) {
-    float2 d;
-    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
-        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
-        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
-        : "=f"(d.x), "=f"(d.y)
-        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
-}
-
+// Running sums of the chunk sums (32 terms each) over one source split.
+// A split covers at most tiles_per_split x 128 sources and the splits meet
+// in the FP64 combine, so a plain FP32 sum suffices: against the FP64
+// oracle the applies stay near 1e-6 relative, as with a compensated sum,
+// and the compensation terms would cost a register per accumulator (the
+// 9-column A kernel would drop from four resident blocks per SM to three).
 template <typename T> struct Acc2;
-template <> struct Acc2<float> {   // two Kahan accumulators
-    float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
-    __device__ __forceinline__ void add(float2 x) {
-        const float2 y = psub(x, c);
-        const float2 t = padd(s, y);
-        c = psub(psub(t, s), y);
-        s = t;
-    }
-    __device__ __forceinline__ double value(int lane) const {
-        return lane ? (double)s.y - (double)c.y : (double)s.x - (double)c.x;
-    }
+template <> struct Acc2<float> {
+    float2 s = make_float2(0.f, 0.f);
+    __device__ __forceinline__ void add(float2 x) { s = padd(s, x); }
+    __device__ __forceinline__ double value(int lane) const { return lane ? (double)s.y : (double)s.x; }
 };
 template <> struct Acc2<double> {
     double2 s = make_double2(0.0, 0.0);
@@ -831,18 +856,21 @@ k_apply(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::typ
 
 // per face: z = (r/a) W_S - (H W)_S in FP64, then the corner values of the
 // transposed map: 2 a_S grad phi_c . zV (B) and 2 a_S zU / 3 (B0, L)
+// (perm != null: the partials are in sorted order, thread t combines face
+// perm[t] from partial row t)
 template <int OP, int KC>
 __global__ void k_apply_combine(const double* __restrict__ part, int nsplit, int nf,
                                 const d4* __restrict__ f64a, const double* __restrict__ fgrad,
                                 const double* __restrict__ W64, int k, int col0,
-                                double* __restrict__ corner) {
+                                double* __restrict__ corner, const int* __restrict__ perm) {
     using L = OpLayout<OP, KC>;
-    int S = blockIdx.x * blockDim.x + threadIdx.x;
-    if (S >= nf) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nf) return;
+    const int S = perm ? perm[t] : t;
     double s[L::NA];
     for (int i = 0; i < L::NA; ++i) {
         double x = 0.0;
-        for (int sp = 0; sp < nsplit; ++sp) x += part[((size_t)sp * L::NA + i) * nf + S];
+        for (int sp = 0; sp < nsplit; ++sp) x += part[((size_t)sp * L::NA + i) * nf + t];
         s[i] = x;
     }
     double a = f64a[S].w;
@@ -877,7 +905,7 @@ static int launch_apply_op(tp_mesh* m, const tp_params* p, const double* v, int 
     const double s = 2.0 - 2.0 / p->p;       // Sobolev order, §2.3
     const double l_exp = 3.0 - s;            // |d|^{-(2 sigma + 2)} = r2^{-(sigma+1)}, sigma = 2 - s
     constexpr int TT = (sizeof(T) == 4 && KC == 3) ? 2 : 1;
-    Grid g = make_grid(nf, nf, TT);
+    Grid g = make_grid(nf, nf, TT, resident_per_sm((const void*)k_apply<T, OP, TT, KC>, NT));
     TP_TRY(ensure(m->part, sizeof(double) * (size_t)g.nsplit * L::NA * nf));
     TP_TRY(ensure(m->wv64, sizeof(double) * 4 * KC * (size_t)nf));
     TP_TRY(ensure(m->wv32, sizeof(V4) * L::NW4 * (size_t)nf));
@@ -905,7 +933,7 @@ static int launch_apply_op(tp_mesh* m, const tp_params* p, const double* v, int 
         k_apply_combine<OP, KC><<<(nf + 255) / 256, 256, 0, st>>>(m->part.as<double>(), g.nsplit, nf,
                                                                   m->f64a.as<d4>(), m->fgrad.as<double>(),
                                                                   m->wv64.as<double>(), k, col0,
-                                                                  m->corner.as<double>());
+                                                                  m->corner.as<double>(), nullptr);
         TP_LAUNCH_CHECK();
     }
     return corners_to_vertices(m, m->corner.as<double>(), k, y, st);
@@ -1012,7 +1040,7 @@ __global__ void k_node_X(const BvhNode* __restrict__ node, const int* __restrict
 // a lane is active at node id only when id >= its escape marker. Near pairs
 // use the compensated (hi + lo) barycenter differences. The sums per target
 // run in FP32 chunks of 32 terms folded into Kahan accumulators, written in
-// face order for the FP64 combine.
+// sorted order for the FP64 combine.
 template <int OP, int KC>
 __global__ void __launch_bounds__(128)
 k_bh_apply(const BvhNode* __restrict__ node, const float4* __restrict__ nodelo, int nnodes,
@@ -1118,11 +1146,9 @@ k_bh_apply(const BvhNode* __restrict__ node, const float4* __restrict__ nodelo, 
     }
 #pragma unroll
     for (int c = 0; c < NP; ++c) acc[c].add(pt[c]);
-    if (has) {
-        const int S = perm[i];
+    if (has)   // sorted order: consecutive lanes write consecutive words
 #pragma unroll
-        for (int c = 0; c < L::NA; ++c) part[(size_t)c * nf + S] = acc[c / 2].value(c & 1);
-    }
+        for (int c = 0; c < L::NA; ++c) part[(size_t)c * nf + i] = acc[c / 2].value(c & 1);
     if (count && nint) atomicAdd(count, (unsigned long long)nint);
 }
 
@@ -1171,7 +1197,7 @@ static int launch_bh_apply_op(tp_mesh* m, const tp_params* p, const double* v, i
         k_apply_combine<OP, KC><<<(nf + 255) / 256, 256, 0, st>>>(m->part.as<double>(), 1, nf,
                                                                   m->f64a.as<d4>(), m->fgrad.as<double>(),
                                                                   m->wv64.as<double>(), k, col0,
-                                                                  m->corner.as<double>());
+                                                                  m->corner.as<double>(), bv.perm);
         TP_LAUNCH_CHECK();
     }
     return corners_to_vertices(m, m->corner.as<double>(), k, y, st);

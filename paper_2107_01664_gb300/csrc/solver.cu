@@ -59,8 +59,8 @@ int precond_apply_dev(tp_mesh* m, const tp_params* p, const double* b, int k, do
     int it1 = 0, it2 = 0;
     int s1 = cg_solve(m, p, b, k, m->prec[0].as<double>(), st, &it1);
     if (s1 != TP_OK && (strict || s1 != TP_ERR_NOT_CONVERGED)) return s1;
+    // (the second solve projects its right-hand side itself)
     TP_TRY(apply_op(m, p, TP_OP_L, m->prec[0].as<double>(), k, m->prec[1].as<double>(), st));
-    TP_TRY(project_mean_zero(m, m->prec[1].as<double>(), k, st));
     int s2 = cg_solve(m, p, m->prec[1].as<double>(), k, z, st, &it2);
     if (s2 != TP_OK && (strict || s2 != TP_ERR_NOT_CONVERGED)) return s2;
     if (cg_iters) *cg_iters += it1 + it2;
