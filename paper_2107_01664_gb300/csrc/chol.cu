@@ -241,16 +241,32 @@ __device__ __forceinline__ unsigned long long gtimer() {
     } while (0)
 #endif
 
-// forward step of node J, in two halves. fwd_prepare does what does not
-// depend on the children (factor block to shared memory, w = (r_J ; 0));
-// fwd_finish adds the children's update vectors and forms y_J = L11^-1 w_J
-// and u_J = w_S - L21 y_J (one warp per output row, lanes split the inner
-// index).
 constexpr int CH_MAXCH = 16;   // children whose records are prefetched to shared memory
 
 struct ChildRec {
-    int voff, mJ, s0, pad;
+    int voff, mJ, s0, row0;   // row0: first row of this child in the staged update vectors
 };
+
+// store(e, load(e)) for e < count, the block's threads taking entries
+// e = tid, tid + CHS_T, ...: each thread issues B independent loads before
+// its stores, so a gather costs one memory round trip per B entries
+// instead of one per entry
+template <int B, class Load, class Store>
+__device__ __forceinline__ void gather_batched(int count, Load load, Store store) {
+    for (int e0 = threadIdx.x; e0 < count; e0 += CHS_T * B) {
+        float v[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int e = e0 + b * CHS_T;
+            if (e < count) v[b] = load(e);
+        }
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            const int e = e0 + b * CHS_T;
+            if (e < count) store(e, v[b]);
+        }
+    }
+}
 
 // K columns padded to whole float4s in shared memory
 template <int K>
@@ -321,6 +337,7 @@ struct StepSmem {
     float* vec;
     float* scratch;
     double* xo;
+    int* aux;      // forward: the children's target rows, then their update vectors; backward: struct(J)
     __device__ StepSmem(const CholNode& nd, float* smem) {
         constexpr int KP = Kp<K>::P;
         const int n = nd.nJ, m = nd.mJ;
@@ -328,6 +345,7 @@ struct StepSmem {
         vec = smem + 4 * ((n * ldn + n * ldm + 3) >> 2);
         scratch = vec + (m + 2 * n) * KP;
         xo = reinterpret_cast<double*>(scratch + 128 * KP);
+        aux = reinterpret_cast<int*>(xo + n * K);
     }
 };
 
@@ -340,15 +358,28 @@ __device__ __forceinline__ void fwd_prepare(const SweepArgs& A, const CholNode& 
     constexpr int KP = Kp<K>::P;
     const int n = nd.nJ, t = nd.t, tid = threadIdx.x;
     stage_factor(A.L, nd, smem);
-    float* w = StepSmem<K>(nd, smem).vec;   // t x KP
-    for (int idx = tid; idx < t * K; idx += CHS_T) {
-        const int a = idx / K, c = idx - a * K;
-        w[a * KP + c] = a < n ? (float)__ldcg(A.r + (size_t)A.perm[nd.p0 + a] * K + c) : 0.f;
-    }
-    const int nc = min(nd.child1 - nd.child0, CH_MAXCH);
-    if (tid < nc) {
-        const CholNode cn = A.nodes[A.child_idx[nd.child0 + tid]];
-        kids[tid] = ChildRec{cn.voff, cn.mJ, cn.s0, 0};
+    const StepSmem<K> sm(nd, smem);
+    float* w = sm.vec;   // t x KP
+    const int* perm = A.perm + nd.p0;
+    gather_batched<8>(t * K,
+                      [&](int e) { const int a = e / K; return a < n ? (float)__ldcg(A.r + (size_t)perm[a] * K + (e - a * K)) : 0.f; },
+                      [&](int e, float v) { const int a = e / K; w[a * KP + (e - a * K)] = v; });
+    const int nc = nd.child1 - nd.child0;
+    if (nc <= CH_MAXCH) {
+        // the children's records, then their target rows in this front
+        if (tid == 0) {
+            int row0 = 0;
+            for (int ci = 0; ci < nc; ++ci) {
+                const CholNode cn = A.nodes[A.child_idx[nd.child0 + ci]];
+                kids[ci] = ChildRec{cn.voff, cn.mJ, cn.s0, row0};
+                row0 += cn.mJ;
+            }
+        }
+        __syncthreads();
+        for (int ci = 0; ci < nc; ++ci) {
+            const ChildRec cr = kids[ci];
+            for (int x = tid; x < cr.mJ; x += CHS_T) sm.aux[cr.row0 + x] = A.rel[cr.s0 + x];
+        }
     }
 }
 
@@ -362,21 +393,41 @@ __device__ void fwd_finish(const SweepArgs& A, const CholNode& nd, float* smem, 
     float* y = w + t * KP;        // n x KP
     const float* Li = smem;       // n x n, leading dimension ldn
     const float* L21 = smem + n * ldn;   // m x n, leading dimension ldm
-    for (int ci = 0; ci < nd.child1 - nd.child0; ++ci) {
-        ChildRec cr;
-        if (ci < CH_MAXCH) {
-            cr = kids[ci];
-        } else {
-            const CholNode cn = A.nodes[A.child_idx[nd.child0 + ci]];
-            cr = ChildRec{cn.voff, cn.mJ, cn.s0, 0};
-        }
-        const int* rl = A.rel + cr.s0;
-        const float* uc = A.uvec + (size_t)cr.voff * K;
-        for (int idx = tid; idx < cr.mJ * K; idx += CHS_T) {
-            const int x = idx / K, c = idx - x * K;
-            w[rl[x] * KP + c] += __ldcg(uc + idx);
-        }
+    const int nc = nd.child1 - nd.child0;
+    if (nc <= CH_MAXCH) {
+        // every child's update vector in one batched pass, then the
+        // extend-add from shared memory, one child at a time
+        const int rows = nc ? kids[nc - 1].row0 + kids[nc - 1].mJ : 0;
+        const int* krow = sm.aux;
+        float* kval = reinterpret_cast<float*>(sm.aux + rows);
+        gather_batched<8>(rows * K,
+                          [&](int e) {
+                              const int r = e / K;
+                              int ci = 0;
+                              while (ci + 1 < nc && kids[ci + 1].row0 <= r) ++ci;
+                              return __ldcg(A.uvec + ((size_t)kids[ci].voff + (r - kids[ci].row0)) * K + (e - r * K));
+                          },
+                          [&](int e, float v) { kval[e] = v; });
         __syncthreads();
+        for (int ci = 0; ci < nc; ++ci) {
+            const ChildRec cr = kids[ci];
+            for (int idx = tid; idx < cr.mJ * K; idx += CHS_T) {
+                const int x = idx / K, c = idx - x * K;
+                w[krow[cr.row0 + x] * KP + c] += kval[cr.row0 * K + idx];
+            }
+            __syncthreads();
+        }
+    } else {
+        for (int ci = 0; ci < nc; ++ci) {
+            const CholNode cn = A.nodes[A.child_idx[nd.child0 + ci]];
+            const int* rl = A.rel + cn.s0;
+            const float* uc = A.uvec + (size_t)cn.voff * K;
+            for (int idx = tid; idx < cn.mJ * K; idx += CHS_T) {
+                const int x = idx / K, c = idx - x * K;
+                w[rl[x] * KP + c] += __ldcg(uc + idx);
+            }
+            __syncthreads();
+        }
     }
     float* yb = A.ybuf + (size_t)nd.p0 * K;
     rows_matvec<K>(Li, 1, ldn, n, n, 0, w, sm.scratch, [&](int r, const float (&acc)[K]) {
@@ -400,11 +451,12 @@ __device__ void fwd_finish(const SweepArgs& A, const CholNode& nd, float* smem, 
 template <int K>
 __device__ __forceinline__ void bwd_prepare(const SweepArgs& A, const CholNode& nd, float* smem) {
     stage_factor(A.L, nd, smem);
-    double* xo = StepSmem<K>(nd, smem).xo;
+    const StepSmem<K> sm(nd, smem);
     for (int idx = threadIdx.x; idx < nd.nJ * K; idx += CHS_T) {
         const int a = idx / K, c = idx - a * K;
-        xo[idx] = A.x[(size_t)A.perm[nd.p0 + a] * K + c];
+        sm.xo[idx] = A.x[(size_t)A.perm[nd.p0 + a] * K + c];
     }
+    for (int x = threadIdx.x; x < nd.mJ; x += CHS_T) sm.aux[x] = A.struct_pos[nd.s0 + x];
 }
 
 template <int K>
@@ -418,15 +470,24 @@ __device__ void bwd_finish(const SweepArgs& A, const CholNode& nd, float* smem) 
     float* z = yj + n * KP;       // n x KP
     const float* Li = smem;
     const float* L21 = smem + n * ldn;
-    for (int idx = tid; idx < (m + n) * K; idx += CHS_T) {
-        if (idx < m * K) {
-            const int x = idx / K, c = idx - x * K;
-            xs[x * KP + c] = __ldcg(A.xbuf + (size_t)A.struct_pos[nd.s0 + x] * K + c);
-        } else {
-            const int j = idx - m * K, a = j / K, c = j - a * K;
-            yj[a * KP + c] = __ldcg(A.ybuf + (size_t)nd.p0 * K + j);
-        }
-    }
+    const int* spos = sm.aux;   // struct(J), staged before the wait
+    gather_batched<8>((m + n) * K,
+                      [&](int e) {
+                          if (e < m * K) {
+                              const int x = e / K;
+                              return __ldcg(A.xbuf + (size_t)spos[x] * K + (e - x * K));
+                          }
+                          return __ldcg(A.ybuf + (size_t)nd.p0 * K + (e - m * K));
+                      },
+                      [&](int e, float v) {
+                          if (e < m * K) {
+                              const int x = e / K;
+                              xs[x * KP + (e - x * K)] = v;
+                          } else {
+                              const int j = e - m * K, a = j / K;
+                              yj[a * KP + (j - a * K)] = v;
+                          }
+                      });
     __syncthreads();
     rows_matvec<K>(L21, ldm, 1, n, m, 2, xs, sm.scratch, [&](int r, const float (&acc)[K]) {
 #pragma unroll
@@ -840,12 +901,16 @@ static int chol_setup(tp_mesh* m) {
             const size_t sm = sizeof(float) * ((size_t)(S.nJ[J] + S.mJ[J]) * S.nJ[J] + (size_t)S.nJ[J] * S.nJ[J]);
             c->lvl_factor_smem[h] = std::max(c->lvl_factor_smem[h], sm);
             // factor block (rounded to 16 bytes), the vectors (rows of 12
-            // floats for up to 9 columns), the 128-row scratch, then the
-            // node's FP64 solution entries (see StepSmem)
+            // floats for up to 9 columns), the 128-row scratch, the node's
+            // FP64 solution entries, then the staged rows and update vectors
+            // of the children or struct(J) (see StepSmem)
+            size_t csum = 0;   // rows of the children's update vectors
+            for (int ci = S.child_ptr[J]; ci < S.child_ptr[J + 1]; ++ci) csum += S.mJ[S.child_idx[ci]];
             const size_t ss = sizeof(float) * ((((size_t)S.nJ[J] * chol_ld(S.nJ[J]) +
                                                  (size_t)S.nJ[J] * chol_ld(S.mJ[J]) + 3) & ~size_t(3)) +
                                                ((size_t)S.mJ[J] + 2 * S.nJ[J]) * 12 + 128 * 12 +
-                                               2 * (size_t)S.nJ[J] * CH_KMAX);
+                                               2 * (size_t)S.nJ[J] * CH_KMAX +
+                                               std::max(csum * (CH_KMAX + 1), (size_t)S.mJ[J]));
             c->lvl_solve_smem[h] = std::max(c->lvl_solve_smem[h], ss);
             worst = std::max(worst, sm);
             // partial Cholesky, Schur update of struct x struct, triangular inverse
