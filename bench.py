@@ -223,18 +223,55 @@ def large_bh(tp, dev, reps=3):
         tp.tp_energy(mesh, pb)
         tp.tp_differential(mesh, pb, like=dE)
     tp.tp_energy(mesh, tp.params())                       # one direct pass
+    # Barnes-Hut operator applies: A and L^{2-s} on 3 columns
+    v3 = torch.randn((len(V), 3), dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(7))
+    for op in ("A", "L"):
+        tp.fractional_apply(mesh, op, v3, pb)
     torch.cuda.synchronize()
     prof = tp.tp_profile_read(mesh)
     tp.tp_profile_enable(mesh, False)
     mesh.close()
     out = {"workload": "icosphere_l8", "nf": int(len(F)), "theta": pb.theta, "leaf_size": pb.leaf_size}
-    for k in ("bh_energy", "bh_diff", "bvh_build", "energy_direct"):
+    for k in ("bh_energy", "bh_diff", "bh_apply", "bvh_build", "energy_direct"):
         if k in prof and prof[k]["launches"]:
             d = prof[k]
             n = d["launches"]
             out[k] = {"ms_per_launch": d["ms"] / n, "units_per_launch": d["units"] / n,
                       "per_s": d["units"] / (d["ms"] / 1e3) if d["ms"] > 0 else None}
+    out["bh_step_linked_tori"] = bh_step(tp, dev)
     return out
+
+
+def bh_step(tp, dev, steps=2):
+    """Constrained steps with every pair sum on the tree (theta = 0.5: energy,
+    differential, and the A and L^{2-s} applies of the Krylov loop) on the
+    two linked 25,000-face tori; device time per step."""
+    import numpy as np
+    import torch
+    from synth import workload
+    V, F = workload("linked_tori_50k")
+    A0 = float(np.sum(0.5 * np.linalg.norm(np.cross(V[F[:, 1]] - V[F[:, 0]], V[F[:, 2]] - V[F[:, 0]]), axis=1)))
+    Vol0 = float(np.sum(V[F[:, 0]] * np.cross(V[F[:, 1]], V[F[:, 2]])) / 6.0)
+    cons = tp.tp_constraints(flags=tp.TP_CONSTRAINT_AREA | tp.TP_CONSTRAINT_VOLUME, A0=A0, V0=Vol0)
+    p = tp.params(theta=0.5, krylov_tol=1e-5, krylov_max=60, cg_tol=1e-6)
+    f0 = torch.tensor(V, dtype=torch.float64, device=dev)
+    mesh = tp.Mesh(f0, torch.tensor(F, dtype=torch.int32, device=dev), device=dev.index or 0)
+    tp.precond_step(mesh, cons, p)                        # warm-up (tree, factor, graphs)
+    tp.tp_mesh_set_positions(mesh, f0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = []
+    e0.record()
+    for _ in range(steps):
+        reps.append(tp.precond_step(mesh, cons, p))
+    e1.record()
+    torch.cuda.synchronize()
+    mesh.close()
+    ms = e0.elapsed_time(e1) / steps
+    return {"workload": "linked_tori_50k", "nf": int(len(F)), "theta": 0.5, "ms_per_step": ms,
+            "interactions_per_step": sum(r["pair_interactions"] for r in reps) / steps,
+            "krylov_iters_per_step": sum(r["krylov_iters"] for r in reps) / steps,
+            "E": [r["E_after"] for r in reps], "status": [r["status"] for r in reps]}
 
 
 # ---------------------------------------------------------------------------
@@ -383,6 +420,9 @@ def gpu_arm(args):
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "pairs_per_step": pairs_per_step,
         "krylov_iters_per_step": sum(r["krylov_iters"] for r in reps) / len(reps),
+        # steps whose FGMRES met krylov_tol within krylov_max (status 0); status 4 = the
+        # fixed iteration budget ran out first (the step is still taken)
+        "krylov_converged_steps": sum(1 for r in reps if r["status"] == 0),
         "cg_iters_per_step": sum(r["cg_iters"] for r in reps) / len(reps),
         "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3), "units": v["units"],
                         "tflops": (flops_per_pair(k, v) * v["units"] / (v["ms"] / 1e3) / 1e12

@@ -654,6 +654,15 @@ __device__ __forceinline__ float2 pfma(float a, float2 b, float2 c) {   // a * b
 __device__ __forceinline__ double2 pfma(double a, double2 b, double2 c) {
     return make_double2(fma(a, b.x, c.x), fma(a, b.y, c.y));
 }
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
 __device__ __forceinline__ float2 padd(float2 a, float2 b) {
     float2 d;
     asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
@@ -663,17 +672,21 @@ __device__ __forceinline__ float2 padd(float2 a, float2 b) {
         : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
     return d;
 }
-// Running sums of the chunk sums (32 terms each) over one source split.
-// A split covers at most tiles_per_split x 128 sources and the splits meet
-// in the FP64 combine, so a plain FP32 sum suffices: against the FP64
-// oracle the applies stay near 1e-6 relative, as with a compensated sum,
-// and the compensation terms would cost a register per accumulator (the
-// 9-column A kernel would drop from four resident blocks per SM to three).
+// Per-block compensated sums: the chunk sums (32 terms each) of a source
+// split are added into Kahan pairs (packed: two accumulators per
+// instruction); the splits meet in the FP64 combine.
 template <typename T> struct Acc2;
 template <> struct Acc2<float> {
-    float2 s = make_float2(0.f, 0.f);
-    __device__ __forceinline__ void add(float2 x) { s = padd(s, x); }
-    __device__ __forceinline__ double value(int lane) const { return lane ? (double)s.y : (double)s.x; }
+    float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+    __device__ __forceinline__ void add(float2 x) {
+        const float2 y = psub(x, c);
+        const float2 t = padd(s, y);
+        c = psub(psub(t, s), y);
+        s = t;
+    }
+    __device__ __forceinline__ double value(int lane) const {
+        return lane ? (double)s.y - (double)c.y : (double)s.x - (double)c.x;
+    }
 };
 template <> struct Acc2<double> {
     double2 s = make_double2(0.0, 0.0);
