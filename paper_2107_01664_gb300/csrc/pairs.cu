@@ -67,6 +67,94 @@ template <typename T> __device__ __forceinline__ T r2_eps(T dx, T dy, T dz) {
     return fma(dx, dx, fma(dy, dy, fma(dz, dz, tiny_r2<T>())));
 }
 
+// ---- packed FP32 arithmetic on float pairs (one f32x2 instruction, IEEE per lane)
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 f2b(float a) { return make_float2(a, a); }
+
+// two floats as one packed pair register (lane 0 = a)
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 upk2(unsigned long long r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+
+// Energy term (p = 6) for two targets against one source, all on packed
+// pair registers: p + ((N.d)^2 / |d|^4)^3 a per lane, d = X_target - X_s,
+// |d|^2 with the tiny offset in the FMA chain (as r2_eps). t* / n* hold the
+// two targets' barycenters and normals, s* the source broadcast to both
+// lanes, eps the offset in both lanes.
+__device__ __forceinline__ unsigned long long energy2_p6(unsigned long long tx, unsigned long long ty,
+                                                         unsigned long long tz, unsigned long long nx,
+                                                         unsigned long long ny, unsigned long long nz,
+                                                         unsigned long long sx, unsigned long long sy,
+                                                         unsigned long long sz, unsigned long long sa,
+                                                         unsigned long long eps, unsigned long long p) {
+    unsigned long long out;
+    asm("{\n\t.reg .b64 dx, dy, dz, r2, ir2, t, q, q3;\n\t.reg .f32 lo, hi;\n\t"
+        "sub.rn.f32x2 dx, %1, %7;\n\t"
+        "sub.rn.f32x2 dy, %2, %8;\n\t"
+        "sub.rn.f32x2 dz, %3, %9;\n\t"
+        "fma.rn.f32x2 r2, dz, dz, %11;\n\t"
+        "fma.rn.f32x2 r2, dy, dy, r2;\n\t"
+        "fma.rn.f32x2 r2, dx, dx, r2;\n\t"
+        "mov.b64 {lo, hi}, r2;\n\t"
+        "rcp.approx.ftz.f32 lo, lo;\n\t"
+        "rcp.approx.ftz.f32 hi, hi;\n\t"
+        "mov.b64 ir2, {lo, hi};\n\t"
+        "mul.rn.f32x2 t, %6, dz;\n\t"
+        "fma.rn.f32x2 t, %5, dy, t;\n\t"
+        "fma.rn.f32x2 t, %4, dx, t;\n\t"
+        "mul.rn.f32x2 t, t, ir2;\n\t"
+        "mul.rn.f32x2 q, t, t;\n\t"
+        "mul.rn.f32x2 q3, q, q;\n\t"
+        "mul.rn.f32x2 q3, q3, q;\n\t"
+        "fma.rn.f32x2 %0, q3, %10, %12;\n\t}"
+        : "=l"(out)
+        : "l"(tx), "l"(ty), "l"(tz), "l"(nx), "l"(ny), "l"(nz), "l"(sx), "l"(sy), "l"(sz), "l"(sa), "l"(eps),
+          "l"(p));
+    return out;
+}
+
 // ---- compensated accumulators -------------------------------------------
 
 template <typename T> struct Acc;
@@ -207,8 +295,11 @@ k_energy(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::ty
          double* __restrict__ part) {
     using V4 = typename V4T<T>::type;
     constexpr bool F32 = sizeof(T) == 4;
+    // packed path (FP32, p = 6): sources also staged broadcast to pairs
+    constexpr bool PACK = F32 && P6 && TT % 2 == 0;
     __shared__ V4 sh[NT];
     __shared__ float4 shl[F32 ? NT : 1];
+    __shared__ ulonglong2 shp[PACK ? 2 * NT : 1];
     __shared__ float sbox[6];
     T tx[TT], ty[TT], tz[TT], nx[TT], ny[TT], nz[TT];
     float lx[TT], ly[TT], lz[TT];
@@ -241,6 +332,21 @@ k_energy(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::ty
         thr2 = (float)center[3];
     }
     Acc<T> acc[TT];
+    unsigned long long TX[PACK ? TT / 2 : 1], TY[PACK ? TT / 2 : 1], TZ[PACK ? TT / 2 : 1];
+    unsigned long long NX[PACK ? TT / 2 : 1], NY[PACK ? TT / 2 : 1], NZ[PACK ? TT / 2 : 1];
+    unsigned long long EPS = 0ull;
+    if constexpr (PACK) {
+#pragma unroll
+        for (int jj = 0; jj < TT / 2; ++jj) {
+            TX[jj] = pk2((float)tx[2 * jj], (float)tx[2 * jj + 1]);
+            TY[jj] = pk2((float)ty[2 * jj], (float)ty[2 * jj + 1]);
+            TZ[jj] = pk2((float)tz[2 * jj], (float)tz[2 * jj + 1]);
+            NX[jj] = pk2((float)nx[2 * jj], (float)nx[2 * jj + 1]);
+            NY[jj] = pk2((float)ny[2 * jj], (float)ny[2 * jj + 1]);
+            NZ[jj] = pk2((float)nz[2 * jj], (float)nz[2 * jj + 1]);
+        }
+        EPS = pk2(1e-18f, 1e-18f);
+    }
     const int ntiles = (nf + NT - 1) / NT;
     const int k0 = blockIdx.y * tiles_per_split;
     const int k1 = min(k0 + tiles_per_split, ntiles);
@@ -248,7 +354,12 @@ k_energy(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::ty
         const bool near = F32 && tile_near(tbox, tile, sbox, thr2);
         int src = tile * NT + threadIdx.x;
         __syncthreads();
-        sh[threadIdx.x] = src < nf ? fa[src] : v4zero<T>();  // zero area pads the tail
+        const V4 sv = src < nf ? fa[src] : v4zero<T>();   // zero area pads the tail
+        sh[threadIdx.x] = sv;
+        if constexpr (PACK) {
+            shp[2 * threadIdx.x] = make_ulonglong2(pk2((float)sv.x, (float)sv.x), pk2((float)sv.y, (float)sv.y));
+            shp[2 * threadIdx.x + 1] = make_ulonglong2(pk2((float)sv.z, (float)sv.z), pk2((float)sv.w, (float)sv.w));
+        }
         if (near) shl[threadIdx.x] = src < nf ? flo[src] : make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
         for (int c = 0; c < NT; c += CH) {
@@ -267,6 +378,25 @@ k_energy(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::ty
                         T dz = (tz[j] - s.z) + (T)(lz[j] - l.z);
                         pt[j] = fma(energy_term<T, P6>(dx, dy, dz, nx[j], ny[j], nz[j], halfp), s.w, pt[j]);
                     }
+                }
+            } else if constexpr (PACK) {
+                // two targets per packed instruction
+                unsigned long long P[TT / 2];
+#pragma unroll
+                for (int jj = 0; jj < TT / 2; ++jj) P[jj] = 0ull;
+#pragma unroll 8
+                for (int q = 0; q < CH; ++q) {
+                    const ulonglong2 u0 = shp[2 * (c + q)], u1 = shp[2 * (c + q) + 1];
+#pragma unroll
+                    for (int jj = 0; jj < TT / 2; ++jj)
+                        P[jj] = energy2_p6(TX[jj], TY[jj], TZ[jj], NX[jj], NY[jj], NZ[jj], u0.x, u0.y, u1.x, u1.y,
+                                           EPS, P[jj]);
+                }
+#pragma unroll
+                for (int jj = 0; jj < TT / 2; ++jj) {
+                    const float2 v = upk2(P[jj]);
+                    pt[2 * jj] = v.x;
+                    pt[2 * jj + 1] = v.y;
                 }
             } else {
 #pragma unroll 8
@@ -378,6 +508,36 @@ __device__ __forceinline__ void diff_term(T dx, T dy, T dz, T nx, T ny, T nz, T 
     pt[11] += kS;
 }
 
+// diff_term (p = 6) for two targets (lanes) against one source, packed;
+// pt[i] holds accumulator i of both targets
+__device__ __forceinline__ void diff_pair_p6(float2 dx, float2 dy, float2 dz, float2 nx, float2 ny, float2 nz, float at,
+                                             float mx, float my, float mz, float2* pt) {
+    const float2 r2 = f2fma(dx, dx, f2fma(dy, dy, f2fma(dz, dz, f2b(tiny_r2<float>()))));
+    const float2 ir2 = make_float2(rcp_(r2.x), rcp_(r2.y));
+    const float2 tS = f2mul(f2fma(nx, dx, f2fma(ny, dy, f2mul(nz, dz))), ir2);
+    const float2 tT = f2mul(f2fma(f2b(mx), dx, f2fma(f2b(my), dy, f2mul(f2b(mz), dz))), ir2);
+    const float2 qS = f2mul(tS, tS), qT = f2mul(tT, tT);
+    const float2 mS = f2mul(qS, qS), mT = f2mul(qT, qT);
+    const float2 A = f2b(at);
+    const float2 w = f2mul(f2mul(A, mS), f2mul(tS, ir2));
+    const float2 v = f2mul(f2mul(A, mT), f2mul(tT, ir2));
+    const float2 kS = f2mul(A, f2mul(mS, qS));
+    const float2 ks = f2fma(A, f2mul(mT, qT), kS);
+    const float2 kd = f2mul(ks, ir2);
+    pt[0] = f2add(pt[0], w);
+    pt[1] = f2fma(w, dx, pt[1]);
+    pt[2] = f2fma(w, dy, pt[2]);
+    pt[3] = f2fma(w, dz, pt[3]);
+    pt[4] = f2fma(v, f2b(mx), pt[4]);
+    pt[5] = f2fma(v, f2b(my), pt[5]);
+    pt[6] = f2fma(v, f2b(mz), pt[6]);
+    pt[7] = f2fma(kd, dx, pt[7]);
+    pt[8] = f2fma(kd, dy, pt[8]);
+    pt[9] = f2fma(kd, dz, pt[9]);
+    pt[10] = f2add(pt[10], ks);
+    pt[11] = f2add(pt[11], kS);
+}
+
 template <typename T, bool P6, int TT>
 __global__ void __launch_bounds__(NT)
 k_diff(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::type* __restrict__ fb,
@@ -448,6 +608,27 @@ k_diff(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::type
                         diff_term<T, P6>((tx[j] - s.x) + (T)(lx[j] - l.x), (ty[j] - s.y) + (T)(ly[j] - l.y),
                                          (tz[j] - s.z) + (T)(lz[j] - l.z), nx[j], ny[j], nz[j], s.w, n.x, n.y,
                                          n.z, hm1, pt[j]);
+                }
+            } else if constexpr (F32 && P6 && TT == 2) {
+                // both targets per packed instruction
+                float2 p2[NADJ];
+#pragma unroll
+                for (int i = 0; i < NADJ; ++i) p2[i] = make_float2(0.f, 0.f);
+                const float2 TXp = make_float2((float)tx[0], (float)tx[1]), TYp = make_float2((float)ty[0], (float)ty[1]),
+                             TZp = make_float2((float)tz[0], (float)tz[1]);
+                const float2 NXp = make_float2((float)nx[0], (float)nx[1]), NYp = make_float2((float)ny[0], (float)ny[1]),
+                             NZp = make_float2((float)nz[0], (float)nz[1]);
+#pragma unroll 4
+                for (int q = 0; q < CH; ++q) {
+                    const float4 s = reinterpret_cast<const float4&>(sa[c + q]);
+                    const float4 n = reinterpret_cast<const float4&>(sb[c + q]);
+                    diff_pair_p6(f2sub(TXp, f2b(s.x)), f2sub(TYp, f2b(s.y)), f2sub(TZp, f2b(s.z)), NXp, NYp, NZp, s.w,
+                                 n.x, n.y, n.z, p2);
+                }
+#pragma unroll
+                for (int i = 0; i < NADJ; ++i) {
+                    pt[0][i] = p2[i].x;
+                    pt[1][i] = p2[i].y;
                 }
             } else {
 #pragma unroll 4
