@@ -352,3 +352,35 @@ def test_invalid_inputs_are_rejected(lib):
             lib.fractional_apply(m, "A", np.zeros((len(V), 10)), lib.params())
         with pytest.raises(lib.TpError):
             lib.tp_energy(m, lib.params(p=1.0))
+
+
+def test_torus20k_cotan_solve_full(lib, torus):
+    # full size, the benchmark's launch configuration (9 columns, cg_tol
+    # 1e-6): the factorised solve against the oracle's exact sparse solve
+    V, F, m = torus
+    b = O.project_mean_zero(vertex_vectors(len(V), 9, 204))
+    z, it = lib.cotan_solve(m, b, lib.params(cg_tol=1e-6))
+    C = O.cotan_laplacian(V, F)
+    ref = O.poisson_solve(C, b)
+    assert it <= 4
+    assert np.linalg.norm(C @ z - b) <= 1e-6 * np.linalg.norm(b)
+    assert rel(z, ref) <= 1e-3   # residual 1e-6 times at most the condition of C
+    z2, _ = lib.cotan_solve(m, b, lib.params(cg_tol=1e-10))
+    assert rel(z2, ref) <= 1e-8
+
+
+def test_linked_tori_factor_two_components(lib):
+    import torch
+    V, F = workload("linked_tori_50k")
+    with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as m:
+        info = lib.cotan_factor_info(m)
+        assert info["available"] == 1 and info["components"] == 2 and info["unknowns"] == len(V) - 2
+        b = vertex_vectors(len(V), 3, 205)
+        z, _ = lib.cotan_solve(m, b, lib.params(cg_tol=1e-10))
+    C = O.cotan_laplacian(V, F)
+    nv1 = len(V) // 2
+    for sl in (slice(0, nv1), slice(nv1, len(V))):
+        bs = b[sl] - b[sl].mean(axis=0)
+        zs = z[sl]
+        assert abs(zs.mean()) <= 1e-10 * np.abs(zs).max()
+        assert np.linalg.norm(C[sl, sl] @ zs - bs) <= 1e-8 * np.linalg.norm(bs)
