@@ -274,6 +274,64 @@ def bh_step(tp, dev, steps=2):
             "E": [r["E_after"] for r in reps], "status": [r["status"] for r in reps]}
 
 
+def long_run(args):
+    """Long Barnes-Hut run on the two linked 25,000-face tori: args.long_run
+    constrained steps (area + volume) with every pair sum on the tree
+    (theta = 0.5); the tree is refit each step and rebuilt every 20 steps.
+    Reports the energy trace, device time per step, the tree's share and the
+    plateau: the first step after which no 10-step window lowers the energy
+    by 0.1% or more."""
+    import numpy as np
+    import torch
+    import paper_2107_01664_gb300 as tp
+    from synth import workload
+    dev = torch.device("cuda", 0)
+    V, F = workload("linked_tori_50k")
+    A0 = float(np.sum(0.5 * np.linalg.norm(np.cross(V[F[:, 1]] - V[F[:, 0]], V[F[:, 2]] - V[F[:, 0]]), axis=1)))
+    Vol0 = float(np.sum(V[F[:, 0]] * np.cross(V[F[:, 1]], V[F[:, 2]])) / 6.0)
+    cons = tp.tp_constraints(flags=tp.TP_CONSTRAINT_AREA | tp.TP_CONSTRAINT_VOLUME, A0=A0, V0=Vol0)
+    mesh = tp.Mesh(torch.tensor(V, dtype=torch.float64, device=dev),
+                   torch.tensor(F, dtype=torch.int32, device=dev), device=0)
+    base = dict(theta=0.5, krylov_tol=1e-5, krylov_max=60, cg_tol=1e-6)
+    E_exact0 = tp.tp_energy(mesh, tp.params())
+    tp.tp_profile_read(mesh)
+    tp.tp_profile_enable(mesh, True)
+    E, ms, status = [], [], []
+    wall0 = time.perf_counter()
+    for k in range(args.long_run):
+        p = tp.params(bvh_refit=0 if k % 20 == 0 else 1, **base)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        rep = tp.precond_step(mesh, cons, p)
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+        E.append(rep["E_after"])
+        status.append(rep["status"])
+    wall = time.perf_counter() - wall0
+    # plateau: the first step after which no 10-step window lowers E by 0.1%
+    drops = [k for k in range(10, len(E)) if (E[k - 10] - E[k]) >= 1e-3 * abs(E[k])]
+    plateau = (drops[-1] + 1) if drops else 0
+    if plateau >= len(E):
+        plateau = None
+    prof = tp.tp_profile_read(mesh)
+    tp.tp_profile_enable(mesh, False)
+    E_exact = tp.tp_energy(mesh, tp.params())
+    f = tp.tp_mesh_get_positions(mesh)
+    mesh.close()
+    A1 = float(np.sum(0.5 * np.linalg.norm(np.cross(f[F[:, 1]] - f[F[:, 0]], f[F[:, 2]] - f[F[:, 0]]), axis=1)))
+    total_ms = sum(ms)
+    out = {"mode": "long_run", "workload": "linked_tori_50k", "steps": args.long_run, "theta": 0.5,
+           "tree": "refit each step, rebuilt every 20", "ms_per_step_mean": total_ms / len(ms),
+           "device_s_total": total_ms / 1e3, "wall_s": wall,
+           "plateau_step": plateau, "time_to_plateau_s": (sum(ms[:plateau + 1]) / 1e3) if plateau is not None else None,
+           "E_exact_start": E_exact0, "E_exact_end": E_exact, "E_bh_trace_every_10": E[::10],
+           "area_rel_drift_end": abs(A1 - A0) / A0, "krylov_converged_steps": sum(1 for s_ in status if s_ == 0),
+           "bvh_build_share": (prof["bvh_build"]["ms"] / total_ms) if "bvh_build" in prof else None,
+           "kernel_ms": {k: round(v["ms"], 1) for k, v in prof.items()}}
+    print(json.dumps(out))
+
+
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
@@ -557,12 +615,16 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
     ap.add_argument("--no-large", action="store_true", help="skip the 1.31M-face Barnes-Hut section")
     ap.add_argument("--serve", action="store_true", help="run the serving benchmark instead")
+    ap.add_argument("--long-run", type=int, default=0, help="run N Barnes-Hut steps on the linked tori instead")
     ap.add_argument("--serve-n", type=int, default=64)
     ap.add_argument("--serve-fmax", type=int, default=50000)
     ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()
     if args.serve:
         serve_arm(args)
+        return
+    if args.long_run:
+        long_run(args)
         return
     if args.impl == "reference":
         reference_arm(args)

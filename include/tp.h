@@ -91,6 +91,8 @@ typedef struct tp_params {
     int    fixed_tau;     /* 1 = take tau0 without line search */
     int    proj_iters;    /* corrective projections per step (§3.3.2: one suffices; repeats allowed) */
     int    poisson_solver; /* TP_POISSON_CHOLESKY (default) or TP_POISSON_CG */
+    int    bvh_refit;     /* 1 = after the positions change, keep the tree's face order and
+                             recompute only the node data (refit); 0 = rebuild (new Morton order) */
 } tp_params;
 
 typedef struct tp_constraints {

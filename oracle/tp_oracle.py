@@ -585,8 +585,10 @@ def _spread10(v):
     return v
 
 
-def bvh_build(f, faces, leaf=8):
-    """Sorted face order, pre-order node table and node data (dict)."""
+def bvh_build(f, faces, leaf=8, order=None):
+    """Sorted face order, pre-order node table and node data (dict). With
+    `order` given, that face order is kept and only the node data come from
+    f (a refit of a tree built on other positions)."""
     X, N, a = face_geometry(f, faces)
     c = 0.5 * (f.min(axis=0) + f.max(axis=0))
     Xr = (f[faces[:, 0]] + f[faces[:, 1]] + f[faces[:, 2]]) / 3.0 - c
@@ -598,7 +600,10 @@ def bvh_build(f, faces, leaf=8):
             q[:, k] = np.clip(np.floor((Xr[:, k] - lo[k]) * (1024.0 / ext[k])), 0, 1023).astype(np.int64)
     code = (_spread10(q[:, 0]) << 2) | (_spread10(q[:, 1]) << 1) | _spread10(q[:, 2])
     nf = len(faces)
-    order = np.lexsort((np.arange(nf), code))
+    if order is None:
+        order = np.lexsort((np.arange(nf), code))
+    else:
+        order = np.asarray(order)
     nleaf = (nf + leaf - 1) // leaf
     first, count, skip, isleaf, right = [], [], [], [], []
 
@@ -721,10 +726,12 @@ def bh_interactions(f, faces, theta, leaf=8, targets=None, tree=None):
     return T, dict(far_s=cat(far_s), far_n=cat(far_n), near_s=cat(near_s), near_t=cat(near_t))
 
 
-def bh_energy_rows(f, faces, theta, leaf=8, p=6.0, targets=None):
-    """Rows of Eq. 16 for the given targets (all faces by default)."""
+def bh_energy_rows(f, faces, theta, leaf=8, p=6.0, targets=None, order=None):
+    """Rows of Eq. 16 for the given targets (all faces by default); `order`:
+    the face order of a refit tree (see bvh_build)."""
     X, N, a = face_geometry(f, faces)
-    T, L = bh_interactions(f, faces, theta, leaf, targets)
+    tree = bvh_build(f, faces, leaf, order) if order is not None else None
+    T, L = bh_interactions(f, faces, theta, leaf, targets, tree)
     Xr = T["Xr"]
     nf = len(faces)
     rows = np.zeros(nf)
@@ -736,8 +743,8 @@ def bh_energy_rows(f, faces, theta, leaf=8, p=6.0, targets=None):
     return rows[S], len(L["far_s"]) + len(L["near_s"])
 
 
-def bh_energy(f, faces, theta, leaf=8, p=6.0):
-    rows, _ = bh_energy_rows(f, faces, theta, leaf, p)
+def bh_energy(f, faces, theta, leaf=8, p=6.0, order=None):
+    rows, _ = bh_energy_rows(f, faces, theta, leaf, p, order=order)
     return float(rows.sum())
 
 

@@ -10,7 +10,10 @@
 // traversal needs no stack. The shape depends only on (nf, leaf_size) and
 // is built once per mesh; the Morton order and the node data (area a_I,
 // area-weighted barycenter X_I, bounding box of the faces' vertices, radius
-// r_I from X_I) are rebuilt bottom-up whenever the positions change.
+// r_I from X_I) are rebuilt bottom-up whenever the positions change. With
+// bvh_refit the face order of the last build is kept and only the node data
+// are recomputed: any face order gives a valid tree (the admissibility test
+// uses the actual boxes and radii), only its quality drifts.
 //
 // Admissibility of node I for target face S (read with the separation
 // parameter theta, which the printed inequality omits):
@@ -207,6 +210,12 @@ __global__ void k_morton(const d4* __restrict__ X, int nf, const double* __restr
 }
 
 // sorted face tables, face boxes and radii
+// sort keys that reproduce a given face order (refit): the low 32 bits carry the face
+__global__ void k_keys_from_perm(const int* __restrict__ perm, int nf, unsigned long long* __restrict__ keys) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nf) keys[i] = (unsigned long long)(unsigned)perm[i];
+}
+
 __global__ void k_sorted_faces(const unsigned long long* __restrict__ keys, int nf,
                                const double* __restrict__ pos, const int* __restrict__ faces,
                                const double* __restrict__ center, const d4* __restrict__ f64a,
@@ -353,6 +362,7 @@ int bvh_build(tp_mesh* m, const tp_params* p, cudaStream_t st) {
         m->bvh_nodes = h.nnodes;
         m->bvh_level_off = h.level_off;
         m->bvh_valid = false;
+        m->bvh_ordered = false;
     }
     if (m->bvh_valid) return TP_OK;
     BvhHost h;
@@ -392,14 +402,20 @@ int bvh_build(tp_mesh* m, const tp_params* p, cudaStream_t st) {
     const int* order = right + h.nnodes;
 
     ProfScope ps(m, PK_BVH_BUILD, (double)nf, st);
-    int nblk = std::min(1024, (nf + 255) / 256);
-    k_bbox_partial<<<nblk, 256, 0, st>>>(m->f64a.as<d4>(), nf, bpart);
-    TP_LAUNCH_CHECK();
-    k_bbox_final<<<1, 32, 0, st>>>(bpart, nblk);
-    TP_LAUNCH_CHECK();
-    k_morton<<<(nf + 255) / 256, 256, 0, st>>>(m->f64a.as<d4>(), nf, bpart + 6 * 1024, kin);
-    TP_LAUNCH_CHECK();
-    TP_CUDA(cub::DeviceRadixSort::SortKeys(m->bvh_sortws.ptr, sort_bytes, kin, kout, nf, 0, 62, st));
+    if (p->bvh_refit && m->bvh_ordered) {
+        // refit: the face order of the last build, node data from the new positions
+        k_keys_from_perm<<<(nf + 255) / 256, 256, 0, st>>>(perm, nf, kout);
+        TP_LAUNCH_CHECK();
+    } else {
+        int nblk = std::min(1024, (nf + 255) / 256);
+        k_bbox_partial<<<nblk, 256, 0, st>>>(m->f64a.as<d4>(), nf, bpart);
+        TP_LAUNCH_CHECK();
+        k_bbox_final<<<1, 32, 0, st>>>(bpart, nblk);
+        TP_LAUNCH_CHECK();
+        k_morton<<<(nf + 255) / 256, 256, 0, st>>>(m->f64a.as<d4>(), nf, bpart + 6 * 1024, kin);
+        TP_LAUNCH_CHECK();
+        TP_CUDA(cub::DeviceRadixSort::SortKeys(m->bvh_sortws.ptr, sort_bytes, kin, kout, nf, 0, 62, st));
+    }
     k_sorted_faces<<<(nf + 255) / 256, 256, 0, st>>>(kout, nf, m->pos.as<double>(), m->faces.as<int>(),
                                                      m->center.as<double>(), m->f64a.as<d4>(),
                                                      m->f32a.as<float4>(), m->f32b.as<float4>(),
@@ -426,6 +442,7 @@ int bvh_build(tp_mesh* m, const tp_params* p, cudaStream_t st) {
         TP_LAUNCH_CHECK();
     }
     m->bvh_valid = true;
+    m->bvh_ordered = true;
     return TP_OK;
 }
 

@@ -38,6 +38,7 @@ int check_params(const tp_params* p) {
         return fail(TP_ERR_INVALID_ARG, "Barnes-Hut (theta > 0) runs in TP_PREC_FP32 only");
     if (p->poisson_solver != TP_POISSON_CHOLESKY && p->poisson_solver != TP_POISSON_CG)
         return fail(TP_ERR_INVALID_ARG, "unknown Poisson solver");
+    if (p->bvh_refit != 0 && p->bvh_refit != 1) return fail(TP_ERR_INVALID_ARG, "bvh_refit must be 0 or 1");
     return TP_OK;
 }
 
@@ -89,6 +90,7 @@ void tp_params_default(tp_params* p) {
     p->fixed_tau = 0;
     p->proj_iters = 1;
     p->poisson_solver = TP_POISSON_CHOLESKY;
+    p->bvh_refit = 0;
 }
 
 const char* tp_last_error(void) { return tp::last_error(); }

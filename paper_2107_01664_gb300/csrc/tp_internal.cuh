@@ -158,6 +158,7 @@ struct tp_mesh {
     int bvh_shape_leaf = 0, bvh_maxdepth = 0;
     std::vector<int> bvh_level_off;
     bool bvh_valid = false;
+    bool bvh_ordered = false;     // perm holds a face order for the current leaf size (refit keeps it)
     tp::Buf bvh_node, bvh_perm, bvh_keys, bvh_tmp, bvh_sortws;
     tp::Buf bvh_f32a, bvh_f32b, bvh_f32c;   // face tables (and low parts) permuted to Morton order
     tp::Buf bh_apply_ws;          // Barnes-Hut applies: sorted X vectors, node sums, node projectors

@@ -196,3 +196,25 @@ def test_icosphere_l8_bh_sample(lib):
     assert rel(rows, ref_bh) <= TOL32
     assert rel(rows_direct, ref_direct) <= TOL32
     print("icosphere_l8 sample: BH(0.5) vs direct FP64 rows, relative error", rel(rows, ref_direct))
+
+
+def test_bvh_refit_matches_oracle_refit(lib):
+    # build on V, move to W: with bvh_refit the tree keeps V's face order
+    # (oracle: bh_energy over that order at W); without, it is rebuilt
+    import torch
+    from synth import vertex_vectors
+    V, F = small_mesh("torus30x11", seed=41)
+    W = V + 0.004 * vertex_vectors(len(V), 3, 42)
+    order_V = O.bvh_build(V, F, 8)["order"]
+    with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as m:
+        p_refit = lib.params(theta=0.5, bvh_refit=1)
+        E_V = lib.tp_energy(m, p_refit)                 # first build (Morton order of V)
+        assert rel(E_V, O.bh_energy(V, F, 0.5)) <= TOL32
+        m.set_positions(dev(W, torch.float64))
+        E_refit = lib.tp_energy(m, p_refit)
+        assert rel(E_refit, O.bh_energy(W, F, 0.5, order=order_V)) <= TOL32
+        g, _ = lib.tp_differential(m, p_refit)
+        m.set_positions(dev(W, torch.float64))
+        E_build = lib.tp_energy(m, lib.params(theta=0.5))
+        assert rel(E_build, O.bh_energy(W, F, 0.5)) <= TOL32
+    assert np.all(np.isfinite(g))

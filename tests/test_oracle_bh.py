@@ -224,3 +224,38 @@ def test_bh_far_field_pin_catches_a_plain_centroid():
         z_ex = O.kernel_apply(T["Xr"], N, a, W, "plain", 10.0 / 3.0)[:8, 0]
         errs.append(np.abs(z_bh - z_ex).max() / np.abs(z_ex).max())
     assert not (3.0 < errs[0] / errs[1] < 5.5 and 3.0 < errs[1] / errs[2] < 5.5)
+
+
+# ---------------------------------------------------------------------------
+# refit: a tree keeps the face order of other positions (only node data move)
+# ---------------------------------------------------------------------------
+
+def test_refit_tree_is_valid_for_any_order():
+    # any face order gives a partition: theta = 0 stays exact, node data are
+    # those of the new positions, radii bound the vertices
+    V, F = small_mesh("torus20x9", seed=11)
+    order = np.random.default_rng(3).permutation(len(F))
+    T = O.bvh_build(V, F, 8, order=order)
+    assert list(T["order"]) == list(order)
+    assert O.bh_energy(V, F, 0.0, 8, order=order) == pytest.approx(O.energy(V, F), rel=1e-13)
+    a = O.face_geometry(V, F)[2]
+    assert T["a"][0] == pytest.approx(a.sum(), rel=1e-13)
+    vx = V[F] - T["c"]
+    for nid in range(len(T["first"])):
+        Tf = T["order"][T["first"][nid]:T["first"][nid] + T["count"][nid]]
+        assert np.linalg.norm(vx[Tf].reshape(-1, 3) - T["X"][nid], axis=1).max() <= T["r"][nid] * (1 + 1e-12)
+
+
+def test_refit_with_the_own_order_is_the_build_and_drifts_gently():
+    V, F = small_mesh("ico3", seed=12)
+    own = O.bvh_build(V, F, 8)["order"]
+    assert O.bh_energy(V, F, 0.5, order=own) == pytest.approx(O.bh_energy(V, F, 0.5), rel=1e-14)
+    # a small motion: the refit (old order) approximates the new energy as
+    # well as a rebuild does (the tree quality drifts only with large motion)
+    from synth import vertex_vectors
+    for eps in (0.001, 0.01):
+        W = V + eps * vertex_vectors(len(V), 3, 13)
+        ex = O.energy(W, F)
+        e_refit = abs(O.bh_energy(W, F, 0.5, order=own) - ex) / ex
+        e_build = abs(O.bh_energy(W, F, 0.5) - ex) / ex
+        assert e_refit <= 1.2 * e_build + 1e-3
