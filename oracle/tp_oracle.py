@@ -448,11 +448,29 @@ def saddle_matrix(f, faces, use_area=True, use_volume=True, p=6.0):
     return M, J
 
 
-def descent_direction(f, faces, use_area=True, use_volume=True, p=6.0):
-    """x of Eq. 14: [A_3 dPhi^T; dPhi 0][x; lambda] = [-dE; 0], solved
-    densely. Returns (x [nv,3], g = dE [nv,3])."""
-    nv = len(f)
+def _total_energy(f, faces, p, obstacle):
+    """E of Eq. 10 plus, when `obstacle` = (f_O, faces_O, weight) is given,
+    the static-obstacle term of §7.3.2 (obstacle_energy)."""
+    E = energy(f, faces, p)
+    if obstacle is not None:
+        E += obstacle_energy(f, faces, obstacle[0], obstacle[1], p, obstacle[2])
+    return E
+
+
+def _total_differential(f, faces, p, obstacle):
     g = differential(f, faces, p)
+    if obstacle is not None:
+        g = g + obstacle_differential(f, faces, obstacle[0], obstacle[1], p, obstacle[2])
+    return g
+
+
+def descent_direction(f, faces, use_area=True, use_volume=True, p=6.0, obstacle=None):
+    """x of Eq. 14: [A_3 dPhi^T; dPhi 0][x; lambda] = [-dE; 0], solved
+    densely. Returns (x [nv,3], g = dE [nv,3]). With an obstacle (see
+    _total_energy) dE is the differential of the sum: the obstacle term is
+    one more energy in the flow, the metric A is unchanged."""
+    nv = len(f)
+    g = _total_differential(f, faces, p, obstacle)
     M, J = saddle_matrix(f, faces, use_area, use_volume, p)
     rhs = np.zeros(M.shape[0])
     rhs[:3 * nv] = -g.reshape(-1)
@@ -489,23 +507,26 @@ def constraint_values(f, faces, A0, V0, use_area=True, use_volume=True):
 
 
 def precond_step(f, faces, A0, V0, use_area=True, use_volume=True, p=6.0,
-                 tau0=1.0, armijo_c=1e-4, shrink=0.5, ls_max=30, fixed_tau=None, proj_iters=1):
+                 tau0=1.0, armijo_c=1e-4, shrink=0.5, ls_max=30, fixed_tau=None, proj_iters=1,
+                 obstacle=None):
     """One constrained descent step (§3, steps 1-5; §5.4 with exact solves):
     direction by Eq. 14, Armijo backtracking from tau0 (E(f + tau x) <=
     E(f) + c tau dE.x), then corrective projections by Eq. 15 with the
     left-hand side of Eq. 14 (Jacobian at f) and Phi at the current point;
-    §3.3.2 says one suffices and allows repeats (proj_iters).
+    §3.3.2 says one suffices and allows repeats (proj_iters). With
+    `obstacle` = (f_O, faces_O, weight) the energy is E of Eq. 10 plus the
+    static-obstacle term of §7.3.2.
     Returns dict(f_new, x, tau, E0, E1, h)."""
     nv = len(f)
-    x, g = descent_direction(f, faces, use_area, use_volume, p)
-    E0 = energy(f, faces, p)
+    x, g = descent_direction(f, faces, use_area, use_volume, p, obstacle)
+    E0 = _total_energy(f, faces, p, obstacle)
     slope = float(np.sum(g * x))
     if fixed_tau is not None:
         tau = fixed_tau
     else:
         tau = tau0
         for _ in range(ls_max):
-            if energy(f + tau * x, faces, p) <= E0 + armijo_c * tau * slope:
+            if _total_energy(f + tau * x, faces, p, obstacle) <= E0 + armijo_c * tau * slope:
                 break
             tau *= shrink
     f1 = f + tau * x
@@ -518,7 +539,8 @@ def precond_step(f, faces, A0, V0, use_area=True, use_volume=True, p=6.0,
         dh = np.linalg.solve(M, rhs)[:3 * nv].reshape(nv, 3)
         f2 = f2 + dh
         h = h + dh
-    return dict(f_new=f2, x=x, tau=tau, E0=E0, E1=energy(f2, faces, p), h=h, slope=slope)
+    return dict(f_new=f2, x=x, tau=tau, E0=E0, E1=_total_energy(f2, faces, p, obstacle), h=h,
+                slope=slope)
 
 
 def apply_operator_at_vertices(f, faces, v, op, verts, p=6.0):
@@ -898,3 +920,126 @@ def bh_differential(f, faces, theta, leaf=8, p=6.0, mode="full"):
     for cidx in range(3):
         np.add.at(out, faces[:, cidx], corner[:, cidx])
     return out
+
+
+# ---------------------------------------------------------------------------
+# §7.3.2 static obstacles
+# ---------------------------------------------------------------------------
+
+def obstacle_potential(x, fO, facesO, p=6.0, grad=False):
+    """Potential of a static obstacle mesh at points x [m,3] (§7.3.2):
+        E_obs(x) = sum_{S in F_O} |f_O(S) - x|^{-p} a_O(S),
+    f_O(S) the barycenter and a_O(S) the area of obstacle face S (the face
+    data of §3.1), p the tangent-point exponent. With grad=True also returns
+        dE_obs/dx = p sum_S a_O(S) |f_O(S) - x|^{-p-2} (f_O(S) - x)   [m,3]."""
+    Y, _, aO = face_geometry(fO, facesO)
+    x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+    phi = np.zeros(len(x))
+    g = np.zeros((len(x), 3))
+    step = max(1, 2 ** 22 // max(1, len(Y)))
+    for i0 in range(0, len(x), step):
+        d = Y[None, :, :] - x[i0:i0 + step, None, :]
+        r2 = np.sum(d * d, axis=2)
+        w = aO[None, :] * r2 ** (-0.5 * p)
+        phi[i0:i0 + step] = w.sum(axis=1)
+        if grad:
+            g[i0:i0 + step] = p * np.einsum("ij,ijk->ik", w / r2, d)
+    return (phi, g) if grad else phi
+
+
+def obstacle_energy_rows(f, faces, fO, facesO, p=6.0, weight=1.0):
+    """Per-face obstacle terms weight * a_T * E_obs(X_T). Reading: the
+    potential E_obs of §7.3.2 is a density over the surface, integrated with
+    the same one-point (barycenter) rule per face as Eq. 10, and scaled by
+    a user weight."""
+    X, _, a = face_geometry(f, faces)
+    return weight * a * obstacle_potential(X, fO, facesO, p)
+
+
+def obstacle_energy(f, faces, fO, facesO, p=6.0, weight=1.0):
+    return float(obstacle_energy_rows(f, faces, fO, facesO, p, weight).sum())
+
+
+def obstacle_differential(f, faces, fO, facesO, p=6.0, weight=1.0):
+    """d/df of obstacle_energy, shape [nv,3]: face adjoints
+    gX_T = weight a_T dE_obs/dx(X_T), ga_T = weight E_obs(X_T), gN_T = 0,
+    through the chain rule of §3.1 (faces_to_vertices)."""
+    X, _, a = face_geometry(f, faces)
+    phi, g = obstacle_potential(X, fO, facesO, p, grad=True)
+    gX = weight * a[:, None] * g
+    ga = weight * phi
+    corner = faces_to_vertices(f, faces, gX, np.zeros_like(gX), ga)
+    out = np.zeros_like(f)
+    for c in range(3):
+        np.add.at(out, faces[:, c], corner[:, c])
+    return out
+
+
+def _admissible_point(T, xr, nodes, theta):
+    """FP32 admissibility of node(s) for point target(s) xr (tree frame): the
+    test of §4.1 with a point in place of the target face (radius 0, box the
+    point itself)."""
+    f32 = np.float32
+    x = xr.astype(f32)
+    nlo, nhi = T["lo"][nodes].astype(f32), T["hi"][nodes].astype(f32)
+    g = np.maximum(np.maximum(nlo - x, x - nhi), f32(0))
+    d2 = (g[:, 0] * g[:, 0] + g[:, 1] * g[:, 1]) + g[:, 2] * g[:, 2]
+    r2 = (T["r"][nodes] * T["r"][nodes]).astype(f32)
+    return r2 < f32(theta * theta) * d2
+
+
+def bh_obstacle_potential(x, fO, facesO, theta, leaf=8, p=6.0, grad=False):
+    """Barnes-Hut approximation of obstacle_potential (§7.3.2 with §4.1): a
+    BVH over the obstacle's faces; a node I admissible for x contributes
+    a_I |X_I - x|^{-p} (X_I its area-weighted barycenter, a_I its area),
+    inadmissible leaves are summed face by face. Returns (phi, g, count) with
+    count the interactions evaluated."""
+    T = bvh_build(fO, facesO, leaf)
+    YO, _, aO = face_geometry(fO, facesO)
+    Yr = T["Xr"]
+    xr = np.atleast_2d(np.asarray(x, dtype=np.float64)) - T["c"]
+    m = len(xr)
+    nfo = len(facesO)
+    phi = np.zeros(m)
+    g = np.zeros((m, 3))
+    count = 0
+
+    def add(s, Y, w):
+        d = Y - xr[s]
+        r2 = np.sum(d * d, axis=1)
+        t = w * r2 ** (-0.5 * p)
+        np.add.at(phi, s, t)
+        if grad:
+            np.add.at(g, s, (p * t / r2)[:, None] * d)
+
+    cur_s, cur_n = np.arange(m), np.zeros(m, dtype=np.int64)
+    while len(cur_s):
+        adm = _admissible_point(T, xr[cur_s], cur_n, theta)
+        add(cur_s[adm], T["X"][cur_n[adm]], T["a"][cur_n[adm]])
+        count += int(adm.sum())
+        rest_s, rest_n = cur_s[~adm], cur_n[~adm]
+        lf = T["leaf"][rest_n]
+        ls, ln = rest_s[lf], rest_n[lf]
+        for j in range(leaf):
+            ok = j < T["count"][ln]
+            src = T["order"][np.minimum(T["first"][ln] + j, nfo - 1)]
+            add(ls[ok], Yr[src[ok]], aO[src[ok]])
+            count += int(ok.sum())
+        is_, in_ = rest_s[~lf], rest_n[~lf]
+        cur_s = np.concatenate([is_, is_])
+        cur_n = np.concatenate([in_ + 1, T["right"][in_]])
+    return phi, g, count
+
+
+def bh_obstacle_energy(f, faces, fO, facesO, theta, leaf=8, p=6.0, weight=1.0):
+    """obstacle_energy with the Barnes-Hut potential; also returns dE/df
+    (exact derivative of the approximation with the interaction lists fixed:
+    the obstacle is static, so only the surface side moves) and the count."""
+    X, _, a = face_geometry(f, faces)
+    phi, g, count = bh_obstacle_potential(X, fO, facesO, theta, leaf, p, grad=True)
+    gX = weight * a[:, None] * g
+    corner = faces_to_vertices(f, faces, gX, np.zeros_like(gX), weight * phi)
+    dE = np.zeros_like(f)
+    for c in range(3):
+        np.add.at(dE, faces[:, c], corner[:, c])
+    return float(np.sum(weight * a * phi)), dE, count

@@ -18,6 +18,13 @@ hot path):
 * ``icosphere_l8``   -- icosphere level 8 (655,362 vertices, 1,310,720
   triangles) with a radial bump 0.05 g / max|g|, g a random combination of
   real spherical harmonics of degree 1..8.
+
+Static-obstacle scene:
+
+* ``ball_in_torus_hole`` -- a sphere of radius 0.5 (icosphere level 5,
+  10,242 vertices, 20,480 triangles, no noise) centred at the origin, i.e.
+  in the hole of ``torus_20k`` (hole radius 0.7): the obstacle mesh of the
+  obstacle benchmark, with ``torus_20k`` as the moving surface.
 """
 from __future__ import annotations
 
@@ -25,7 +32,7 @@ import numpy as np
 
 __all__ = [
     "icosphere", "torus", "linked_tori", "gaussian_noise", "sh_bumps",
-    "vertex_vectors", "workload", "WORKLOADS", "small_mesh",
+    "vertex_vectors", "workload", "WORKLOADS", "small_mesh", "obstacle", "OBSTACLES",
 ]
 
 
@@ -221,6 +228,20 @@ WORKLOADS = {
 def workload(name: str):
     """(V float64 [nv,3], F int32 [nf,3]) of a named workload."""
     return WORKLOADS[name]()
+
+
+def _ball_in_torus_hole():
+    return icosphere(5, 0.5)
+
+
+OBSTACLES = {
+    "ball_in_torus_hole": _ball_in_torus_hole,
+}
+
+
+def obstacle(name: str):
+    """(V float64 [nv,3], F int32 [nf,3]) of a named static obstacle mesh."""
+    return OBSTACLES[name]()
 
 
 def small_mesh(kind: str, seed: int = 7):
