@@ -34,6 +34,9 @@ UNIT = "pairs/s"
 # algorithmic FP32 flops per pair interaction (FMA = 2, MUFU not counted);
 # operator applies: kernel evaluation + 2 per accumulator, KC columns per launch
 FLOPS_PER_PAIR = {"energy_direct": 20, "diff_direct": 57, "bh_energy": 20, "bh_diff": 51}
+# static-obstacle pair (surface face, obstacle face) with its gradient: d (3), |d|^2 (5),
+# |d|^-6 (2), times a (1), sum (1), |d|^-8 a (1), 3 gradient FMAs (6)
+OBSTACLE_FLOPS_PER_PAIR = 19
 APPLY_FLOPS = {"apply_A": lambda kc: 26 + 2 * (2 + 4 * kc), "apply_B": lambda kc: 9 + 2 * (1 + 3 * kc),
                "apply_B0": lambda kc: 26 + 2 * (1 + kc), "apply_L": lambda kc: 9 + 2 * (1 + kc)}
 
@@ -48,7 +51,8 @@ def flops_per_pair(name, stat):
 KERNEL_SOURCE = {"energy_direct": "pairs.cu", "diff_direct": "pairs.cu", "apply_A": "pairs.cu",
                  "apply_B": "pairs.cu", "apply_B0": "pairs.cu", "apply_L": "pairs.cu",
                  "bh_energy": "bvh.cu", "bh_diff": "bvh.cu", "cg": "cg.cu", "bvh_build": "bvh.cu",
-                 "chol_factor": "chol.cu", "chol_solve": "chol.cu"}
+                 "chol_factor": "chol.cu", "chol_solve": "chol.cu", "obstacle_direct": "obstacle.cu",
+                 "bh_obstacle": "obstacle.cu"}
 FP32_LANES_PER_SM = 128
 
 
@@ -239,6 +243,73 @@ def large_bh(tp, dev, reps=3):
             out[k] = {"ms_per_launch": d["ms"] / n, "units_per_launch": d["units"] / n,
                       "per_s": d["units"] / (d["ms"] / 1e3) if d["ms"] > 0 else None}
     out["bh_step_linked_tori"] = bh_step(tp, dev)
+    return out
+
+
+def obstacle_scene(tp, dev, reps=5, steps=2):
+    """Static-obstacle term (§7.3.2) on torus_20k around the 20,480-face ball
+    in its hole: device time of the direct FP32 energy + differential (all
+    20,000 x 20,480 pairs), of the Barnes-Hut one (theta = 0.5, leaf 8), and
+    of constrained steps whose energy includes the obstacle term."""
+    import numpy as np
+    import torch
+    from synth import obstacle, workload
+    V, F = workload(WORKLOAD)
+    VO, FO = obstacle("ball_in_torus_hole")
+    f0 = torch.tensor(V, dtype=torch.float64, device=dev)
+    mesh = tp.Mesh(f0, torch.tensor(F, dtype=torch.int32, device=dev), device=dev.index or 0)
+    tp.tp_obstacle_set(mesh, torch.tensor(VO, dtype=torch.float64, device=dev),
+                       torch.tensor(FO, dtype=torch.int32, device=dev), 1.0)
+    dE = torch.empty((len(V), 3), dtype=torch.float64, device=dev)
+    pd, pb = tp.params(), bh_params(tp)
+    tp.tp_obstacle_energy(mesh, pd, like=dE)
+    tp.tp_obstacle_energy(mesh, pb, like=dE)
+    torch.cuda.synchronize()
+    tp.tp_profile_read(mesh)
+    tp.tp_profile_enable(mesh, True)
+    E = Eb = None
+    for _ in range(reps):
+        E, _ = tp.tp_obstacle_energy(mesh, pd, like=dE)
+        Eb, _ = tp.tp_obstacle_energy(mesh, pb, like=dE)
+    torch.cuda.synchronize()
+    prof = tp.tp_profile_read(mesh)
+    tp.tp_profile_enable(mesh, False)
+    out = {"workload": "torus_20k+ball_in_torus_hole", "nf": int(len(F)), "nf_obstacle": int(len(FO)),
+           "E_direct": E, "E_bh": Eb}
+    for k in ("obstacle_direct", "bh_obstacle"):
+        if k in prof and prof[k]["launches"]:
+            d = prof[k]
+            n = d["launches"]
+            out[k] = {"ms_per_launch": d["ms"] / n, "units_per_launch": d["units"] / n,
+                      "per_s": d["units"] / (d["ms"] / 1e3) if d["ms"] > 0 else None}
+    if "obstacle_direct" in out and prof["obstacle_direct"]["ms"] > 0:
+        d = prof["obstacle_direct"]
+        peaks, _ = measured_peaks()
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak = sms * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        tfl = OBSTACLE_FLOPS_PER_PAIR * d["units"] / (d["ms"] / 1e3) / 1e12
+        out["obstacle_direct"]["tflops"] = tfl
+        out["obstacle_direct"]["frac_of_fp32_peak"] = tfl / peak
+    # constrained steps on E + E_O (direct pairs, the benchmark's step settings)
+    A0 = float(np.sum(0.5 * np.linalg.norm(np.cross(V[F[:, 1]] - V[F[:, 0]], V[F[:, 2]] - V[F[:, 0]]), axis=1)))
+    Vol0 = float(np.sum(V[F[:, 0]] * np.cross(V[F[:, 1]], V[F[:, 2]])) / 6.0)
+    cons = tp.tp_constraints(flags=tp.TP_CONSTRAINT_AREA | tp.TP_CONSTRAINT_VOLUME, A0=A0, V0=Vol0)
+    ps = step_params(tp)
+    tp.precond_step(mesh, cons, ps)
+    tp.tp_mesh_set_positions(mesh, f0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps_ = []
+    e0.record()
+    for _ in range(steps):
+        tp.tp_mesh_set_positions(mesh, f0)
+        reps_.append(tp.precond_step(mesh, cons, ps))
+    e1.record()
+    torch.cuda.synchronize()
+    mesh.close()
+    out["step"] = {"ms_per_step": e0.elapsed_time(e1) / steps,
+                   "E_before": reps_[0]["E_before"], "E_after": reps_[0]["E_after"],
+                   "tau": reps_[0]["tau"], "status": [r["status"] for r in reps_]}
     return out
 
 
@@ -490,6 +561,7 @@ def gpu_arm(args):
     }
     if not args.no_large:
         line["large_mesh_bh"] = large_bh(tp, dev)
+        line["obstacle"] = obstacle_scene(tp, dev)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = run_cpu_sample()
     mesh.close()
@@ -616,6 +688,8 @@ def main():
     ap.add_argument("--no-large", action="store_true", help="skip the 1.31M-face Barnes-Hut section")
     ap.add_argument("--serve", action="store_true", help="run the serving benchmark instead")
     ap.add_argument("--long-run", type=int, default=0, help="run N Barnes-Hut steps on the linked tori instead")
+    ap.add_argument("--obstacle", action="store_true",
+                    help="run only the static-obstacle scene (torus_20k around a ball) instead")
     ap.add_argument("--serve-n", type=int, default=64)
     ap.add_argument("--serve-fmax", type=int, default=50000)
     ap.add_argument("--serve-slots", type=int, default=4)
@@ -625,6 +699,12 @@ def main():
         return
     if args.long_run:
         long_run(args)
+        return
+    if args.obstacle:
+        import torch
+        import paper_2107_01664_gb300 as tp
+        torch.cuda.set_device(0)
+        print(json.dumps({"obstacle": obstacle_scene(tp, torch.device("cuda", 0))}))
         return
     if args.impl == "reference":
         reference_arm(args)

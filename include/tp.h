@@ -230,6 +230,32 @@ int precond_apply(tp_mesh* m, const tp_params* p, const double* b, int k,
 int precond_step(tp_mesh* m, const tp_params* p, const tp_constraints* c,
                  tp_step_report* rep, void* stream);
 
+/* Static mesh obstacle of a mesh (§7.3.2). The obstacle is a fixed triangle
+ * mesh O (nv positions float64 [nv][3], nf faces int32 [nf][3], validated
+ * like tp_mesh_create); every point x of the surface feels the potential
+ *   E_obs(x) = sum_{S in F_O} |f_O(S) - x|^{-p} a_O(S)
+ * (f_O(S), a_O(S): barycenter and area of obstacle face S; p of tp_params).
+ * Reading of the paper: the potential is a density over the surface,
+ * integrated with the one-point rule of Eq. 10 and scaled by `weight`:
+ *   E_O = weight * sum_T a_T E_obs(X_T).
+ * Once set, precond_step minimises E + E_O (its report's energies are the
+ * sum); tp_energy and tp_differential stay Eq. 10 / Eq. 16 alone.
+ * The library copies the obstacle (the caller keeps its arrays) and keeps
+ * it until it is replaced, removed (nf = 0; pos and faces may then be
+ * NULL) or the mesh is destroyed. weight >= 0. Synchronises `stream`. */
+int tp_obstacle_set(tp_mesh* m, int nv, int nf, const double* pos, const int32_t* faces,
+                    double weight, int ptr_kind, void* stream);
+
+/* E_O (host, may be NULL) and dE_O/df (float64 [nv][3], may be NULL) of
+ * the obstacle set on the mesh: theta = 0 by direct sums over all
+ * (surface face, obstacle face) pairs in the precision of tp_params;
+ * theta > 0 (FP32) by Barnes-Hut over a BVH of the obstacle (leaf_size),
+ * an admissible node I adding a_I |X_I - x|^{-p}, X_I its area-weighted
+ * barycenter. The differential goes through the face barycenters and
+ * areas (§3.1 chain rule). TP_ERR_INVALID_ARG if no obstacle is set. */
+int tp_obstacle_energy(tp_mesh* m, const tp_params* p, double* E_out, double* dE, int ptr_kind,
+                       void* stream);
+
 /* Turn per-launch CUDA-event timing of the pair, Barnes-Hut and CG kernels
  * of this mesh on (1) or off (0). Events are recorded on the launching
  * stream; launches and units are counted whether or not timing is on. */

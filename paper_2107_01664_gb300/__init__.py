@@ -27,6 +27,7 @@ __all__ = [
     "fractional_apply", "cotan_solve", "precond_apply", "precond_step", "TangentPointEnergy",
     "lib_path", "lib", "tp_kernel_stat", "tp_profile_enable", "tp_profile_read", "tp_launch_count",
     "tp_energy_noalloc", "tp_chol_info", "cotan_factor_info", "TP_POISSON_CHOLESKY", "TP_POISSON_CG",
+    "tp_obstacle_set", "tp_obstacle_energy",
 ]
 
 TP_OK, TP_ERR_INVALID_ARG, TP_ERR_DEGENERATE, TP_ERR_OOM = 0, 1, 2, 3
@@ -122,6 +123,8 @@ def lib():
         "tp_profile_read": (c_int, [vp, P(tp_kernel_stat), c_int, P(c_int)]),
         "tp_launch_count": (ctypes.c_ulonglong, []),
         "tp_energy_noalloc": (c_int, [vp, c_int, vp, c_int, c_double, vp, vp]),
+        "tp_obstacle_set": (c_int, [vp, c_int, c_int, vp, vp, c_double, c_int, vp]),
+        "tp_obstacle_energy": (c_int, [vp, P(tp_params), P(c_double), vp, c_int, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -334,6 +337,33 @@ def precond_step(mesh: Mesh, constraints: tp_constraints, p: tp_params | None = 
         "krylov_iters": rep.krylov_iters, "cg_iters": rep.cg_iters, "ls_trials": rep.ls_trials,
         "status": rep.status, "pair_interactions": rep.pair_interactions,
     }
+
+
+def tp_obstacle_set(mesh: Mesh, positions=None, faces=None, weight: float = 1.0):
+    """Attach a static obstacle mesh (§7.3.2) to `mesh`; positions=None removes it."""
+    if positions is None:
+        _check(lib().tp_obstacle_set(mesh.handle, 0, 0, None, None, 0.0, TP_PTR_HOST, _stream_ptr()))
+        return
+    pp, pk, keep_p = _as_buffer(positions, np.float64)
+    fp, fk, keep_f = _as_buffer(faces, np.int32)
+    if pk != fk:
+        raise ValueError("positions and faces must both be host or both be device arrays")
+    nv, nf = int(np.shape(positions)[0]), int(np.shape(faces)[0])
+    _check(lib().tp_obstacle_set(mesh.handle, nv, nf, pp, fp, float(weight), pk, _stream_ptr(positions)))
+
+
+def tp_obstacle_energy(mesh: Mesh, p: tp_params | None = None, like=None, grad: bool = True):
+    """(E_O, dE_O [nv,3] or None) of the obstacle set on `mesh`; dE_O in the
+    memory kind of `like` (host by default)."""
+    p = p or params()
+    E = ctypes.c_double()
+    if not grad:
+        _check(lib().tp_obstacle_energy(mesh.handle, ctypes.byref(p), ctypes.byref(E), None, TP_PTR_HOST,
+                                        _stream_ptr(like)))
+        return E.value, None
+    out, ptr, kind = _empty_like_kind(like, (mesh.nv, 3))
+    _check(lib().tp_obstacle_energy(mesh.handle, ctypes.byref(p), ctypes.byref(E), ptr, kind, _stream_ptr(like)))
+    return E.value, out
 
 
 def tp_profile_enable(mesh: Mesh, on: bool = True):

@@ -191,6 +191,7 @@ int tp_mesh_destroy(tp_mesh* m) {
                   &m->wv64, &m->wv32, &m->io_in, &m->io_out, &m->adj, &m->erow, &m->tlist, &m->rowsum,
                   &m->kry};
     for (Buf* b : all) release(*b);
+    obstacle_release(m);
     chol_release(m);
     release(m->bhcount);
     prof_release(m);
@@ -356,6 +357,64 @@ int precond_step(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp_ste
     return precond_step_dev(m, p, c, rep, (cudaStream_t)stream);
 }
 
+int tp_obstacle_set(tp_mesh* m, int nv, int nf, const double* pos, const int32_t* faces, double weight,
+                    int ptr_kind, void* stream) {
+    set_error("");
+    TP_TRY(check_mesh(m));
+    TP_TRY(check_kind(ptr_kind));
+    if (nf < 0 || nv < 0) return fail(TP_ERR_INVALID_ARG, "negative obstacle size");
+    if (!std::isfinite(weight) || weight < 0.0) return fail(TP_ERR_INVALID_ARG, "weight must be finite and >= 0");
+    DeviceGuard g(m->device);
+    if (!g.ok) return fail(TP_ERR_CUDA, "cudaSetDevice failed");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (nf == 0) {
+        TP_CUDA(cudaStreamSynchronize(st));
+        obstacle_release(m);
+        return TP_OK;
+    }
+    tp_mesh* o = nullptr;
+    TP_TRY(tp_mesh_create(m->device, nv, nf, pos, faces, ptr_kind, stream, &o));
+    TP_CUDA(cudaStreamSynchronize(st));
+    obstacle_release(m);
+    m->obs = o;
+    m->obs_weight = weight;
+    const int s = obstacle_frame(m, st);
+    if (s != TP_OK) {
+        obstacle_release(m);
+        return s;
+    }
+    return TP_OK;
+}
+
+int tp_obstacle_energy(tp_mesh* m, const tp_params* p, double* E_out, double* dE, int ptr_kind, void* stream) {
+    set_error("");
+    TP_TRY(check_mesh(m));
+    TP_TRY(check_params(p));
+    TP_TRY(check_kind(ptr_kind));
+    if (!m->obs) return fail(TP_ERR_INVALID_ARG, "no obstacle is set on this mesh");
+    DeviceGuard g(m->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    TP_TRY(ensure(m->erow, sizeof(double) * m->nf));
+    TP_TRY(ensure(m->rowsum, sizeof(double) * 8));
+    if (dE) {
+        TP_TRY(ensure(m->adj, sizeof(double) * 7 * (size_t)m->nf));
+        TP_TRY(obstacle_terms(m, p, true, false, m->erow.as<double>(), m->adj.as<double>(), st));
+        const size_t bytes = sizeof(double) * 3 * (size_t)m->nv;
+        TP_TRY(ensure(m->io_out, bytes));
+        double* out = ptr_kind == TP_PTR_DEVICE ? dE : m->io_out.as<double>();
+        TP_TRY(adjoints_to_dE(m, m->adj.as<double>(), out, st));
+        if (ptr_kind == TP_PTR_HOST) TP_TRY(copy_out(dE, out, bytes, TP_PTR_HOST, st));
+    } else {
+        TP_TRY(obstacle_terms(m, p, false, false, m->erow.as<double>(), nullptr, st));
+    }
+    if (E_out) {
+        TP_TRY(sum_f64(m->erow.as<double>(), m->nf, m->rowsum.as<double>(), m, st));
+        TP_CUDA(cudaMemcpyAsync(E_out, m->rowsum.ptr, sizeof(double), cudaMemcpyDeviceToHost, st));
+        TP_CUDA(cudaStreamSynchronize(st));
+    }
+    return TP_OK;
+}
+
 int tp_profile_enable(tp_mesh* m, int on) {
     set_error("");
     TP_TRY(check_mesh(m));
@@ -370,7 +429,8 @@ int tp_profile_read(tp_mesh* m, tp_kernel_stat* out, int max, int* n) {
     DeviceGuard g(m->device);
     static const char* names[PK_COUNT] = {"energy_direct", "diff_direct", "apply_A", "apply_B", "apply_B0",
                                           "apply_L", "bh_energy", "bh_diff", "bvh_build", "cg",
-                                          "chol_factor", "chol_solve", "bh_apply"};
+                                          "chol_factor", "chol_solve", "bh_apply", "obstacle_direct",
+                                          "bh_obstacle"};
     Profiler& P = m->prof;
     for (auto& pe : P.pending) {
         float ms = 0.f;
@@ -386,6 +446,7 @@ int tp_profile_read(tp_mesh* m, tp_kernel_stat* out, int max, int* n) {
     P.units[PK_BH_ENERGY] += (double)bh[0];
     P.units[PK_BH_DIFF] += (double)bh[1];
     P.units[PK_BH_APPLY] += (double)bh[2];
+    P.units[PK_BH_OBSTACLE] += (double)bh[3];
     int k = 0;
     for (int i = 0; i < PK_COUNT && k < max; ++i) {
         if (P.launches[i] == 0) continue;

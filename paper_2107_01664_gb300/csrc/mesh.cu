@@ -280,6 +280,7 @@ int refresh_geometry(tp_mesh* m, cudaStream_t st) {
         k_tile_boxes<<<ntiles, 128, 0, st>>>(m->f32a.as<float4>(), m->nf, m->tilebox.as<float4>());
         TP_LAUNCH_CHECK();
     }
+    TP_TRY(obstacle_frame(m, st));   // the frame moved with the positions
     int err = 0;
     TP_CUDA(cudaMemcpyAsync(&err, m->errflag.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
     TP_CUDA(cudaStreamSynchronize(st));

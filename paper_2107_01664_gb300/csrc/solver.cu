@@ -17,26 +17,30 @@ namespace tp {
 // energy / differential dispatch
 // ---------------------------------------------------------------------------
 
-int energy_value(tp_mesh* m, const tp_params* p, double* E_host, cudaStream_t st) {
+int energy_value(tp_mesh* m, const tp_params* p, double* E_host, cudaStream_t st, bool obstacle) {
     TP_TRY(ensure(m->erow, sizeof(double) * m->nf));
     TP_TRY(ensure(m->rowsum, sizeof(double) * 8));
     if (p->theta > 0.0)
         TP_TRY(energy_rows_bh(m, p, nullptr, m->nf, m->erow.as<double>(), st));
     else
         TP_TRY(energy_rows_direct(m, p, nullptr, m->nf, m->erow.as<double>(), st));
+    if (obstacle) TP_TRY(obstacle_terms(m, p, false, true, m->erow.as<double>(), nullptr, st));
     TP_TRY(sum_f64(m->erow.as<double>(), m->nf, m->rowsum.as<double>(), m, st));
     TP_CUDA(cudaMemcpyAsync(E_host, m->rowsum.ptr, sizeof(double), cudaMemcpyDeviceToHost, st));
     TP_CUDA(cudaStreamSynchronize(st));
     return TP_OK;
 }
 
-int differential_dev(tp_mesh* m, const tp_params* p, double* dE, double* E_host, cudaStream_t st) {
+int differential_dev(tp_mesh* m, const tp_params* p, double* dE, double* E_host, cudaStream_t st,
+                     bool obstacle) {
     TP_TRY(ensure(m->adj, sizeof(double) * 7 * (size_t)m->nf));
     TP_TRY(ensure(m->erow, sizeof(double) * m->nf));
     if (p->theta > 0.0)
         TP_TRY(diff_adjoints_bh(m, p, m->adj.as<double>(), m->erow.as<double>(), st));
     else
         TP_TRY(diff_adjoints_direct(m, p, m->adj.as<double>(), m->erow.as<double>(), st));
+    if (obstacle)
+        TP_TRY(obstacle_terms(m, p, true, true, m->erow.as<double>(), m->adj.as<double>(), st));
     TP_TRY(adjoints_to_dE(m, m->adj.as<double>(), dE, st));
     if (E_host) {
         TP_TRY(ensure(m->rowsum, sizeof(double) * 8));
@@ -438,7 +442,7 @@ int precond_step_dev(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp
 
     // 1. differential
     double E0 = 0.0;
-    TP_TRY(differential_dev(m, p, g, &E0, st));
+    TP_TRY(differential_dev(m, p, g, &E0, st, true));
     r.E_before = E0;
     // 2. constraint Jacobian rows at f
     int use[2] = {(c->flags & TP_CONSTRAINT_AREA) ? 1 : 0, (c->flags & TP_CONSTRAINT_VOLUME) ? 1 : 0};
@@ -515,7 +519,7 @@ int precond_step_dev(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp
         int gs = refresh_geometry(m, st);
         ++trials;
         if (gs == TP_OK) {
-            TP_TRY(energy_value(m, p, &E1, st));
+            TP_TRY(energy_value(m, p, &E1, st, true));
             if (p->fixed_tau || E1 <= E0 + p->armijo_c * tau * r.slope) break;
         } else if (gs != TP_ERR_DEGENERATE) {
             return gs;
@@ -551,13 +555,13 @@ int precond_step_dev(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp
     TP_TRY(constraints_eval(m, m->pos.as<double>(), phi2, nullptr, nullptr, st));
     r.phi_after[0] = use[0] ? phi2[0] - c->A0 : 0.0;
     r.phi_after[1] = use[1] ? phi2[1] - c->V0 : 0.0;
-    TP_TRY(energy_value(m, p, &r.E_after, st));
+    TP_TRY(energy_value(m, p, &r.E_after, st, true));
     r.krylov_iters = ks.iters;
     r.cg_iters = ks.cg_iters;
     unsigned long long bh1[BH_NCOUNT];
     TP_TRY(bh_counts_read(m, bh1, false, st));
-    r.pair_interactions = (m->pairs - pairs0) + (double)(bh1[0] - bh0[0]) + (double)(bh1[1] - bh0[1]) +
-                          (double)(bh1[2] - bh0[2]);
+    r.pair_interactions = m->pairs - pairs0;
+    for (int i = 0; i < BH_NCOUNT; ++i) r.pair_interactions += (double)(bh1[i] - bh0[i]);
     if (rep) *rep = r;
     return TP_OK;
 }

@@ -111,7 +111,8 @@ struct BvhView {
 // ---------------------------------------------------------------------------
 
 enum ProfKey { PK_ENERGY = 0, PK_DIFF, PK_APPLY_A, PK_APPLY_B, PK_APPLY_B0, PK_APPLY_L, PK_BH_ENERGY,
-               PK_BH_DIFF, PK_BVH_BUILD, PK_CG, PK_CHOL_FACTOR, PK_CHOL_SOLVE, PK_BH_APPLY, PK_COUNT };
+               PK_BH_DIFF, PK_BVH_BUILD, PK_CG, PK_CHOL_FACTOR, PK_CHOL_SOLVE, PK_BH_APPLY,
+               PK_OBSTACLE, PK_BH_OBSTACLE, PK_COUNT };
 
 struct Profiler {
     bool on = false;
@@ -169,6 +170,11 @@ struct tp_mesh {
     tp::Buf stepv[8];   // vectors of the constrained step
     tp::Buf prec[3];    // preconditioner temporaries
     tp::Buf bhcount;    // device counter of Barnes-Hut interactions
+    // static obstacle (§7.3.2): a mesh of its own (positions, face tables,
+    // BVH), and its faces re-expressed in this mesh's frame for the direct sums
+    tp_mesh* obs = nullptr;
+    double obs_weight = 0.0;
+    tp::Buf obs_f64a, obs_f32a, obs_f32c, obs_tilebox, obs_thr, obs_part;
     tp::Profiler prof;
     double pairs = 0.0; // pair interactions evaluated (host-known part)
 };
@@ -222,8 +228,9 @@ int energy_rows_bh(tp_mesh* m, const tp_params* p, const int32_t* targets_dev, i
 int diff_adjoints_bh(tp_mesh* m, const tp_params* p, double* adj_dev, double* erow_dev,
                      cudaStream_t st);
 int bh_counter(tp_mesh* m, cudaStream_t st);
-// device counters of Barnes-Hut interactions: [0] energy, [1] differential, [2] operator applies
-constexpr int BH_NCOUNT = 3;
+// device counters of Barnes-Hut interactions: [0] energy, [1] differential, [2] operator applies,
+// [3] obstacle potential
+constexpr int BH_NCOUNT = 4;
 int bh_counts_read(tp_mesh* m, unsigned long long out[BH_NCOUNT], bool reset, cudaStream_t st);
 int bvh_view(tp_mesh* m, const tp_params* p, cudaStream_t st, BvhView* out);   // builds the tree if needed
 
@@ -250,10 +257,19 @@ int axpy(double* y, const double* x, double a, size_t n, cudaStream_t st);
 int lincomb(double* y, const double* const* xs, const double* coef_host, int nvec, size_t n,
             double beta, cudaStream_t st);
 
+// -------- obstacle.cu ------------------------------------------------------
+int obstacle_frame(tp_mesh* m, cudaStream_t st);   // obstacle faces in m's current frame
+// obstacle rows w a_T E_obs(X_T) into erow_dev (and with diff its face
+// adjoints into adj_dev [nf*7]); accumulate: add to what is there
+int obstacle_terms(tp_mesh* m, const tp_params* p, bool diff, bool accumulate, double* erow_dev,
+                   double* adj_dev, cudaStream_t st);
+void obstacle_release(tp_mesh* m);
+
 // -------- solver.cu --------------------------------------------------------
-int energy_value(tp_mesh* m, const tp_params* p, double* E_host, cudaStream_t st);
+// E (host) of Eq. 10 or 16; with obstacle = true plus the static-obstacle term
+int energy_value(tp_mesh* m, const tp_params* p, double* E_host, cudaStream_t st, bool obstacle = false);
 int differential_dev(tp_mesh* m, const tp_params* p, double* dE_dev, double* E_host,
-                     cudaStream_t st);
+                     cudaStream_t st, bool obstacle = false);
 int precond_apply_dev(tp_mesh* m, const tp_params* p, const double* b, int k, double* z,
                       cudaStream_t st, int* cg_iters, bool strict = true);
 int precond_step_dev(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp_step_report* rep,
