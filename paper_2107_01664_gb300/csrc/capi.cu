@@ -375,14 +375,8 @@ int tp_obstacle_set(tp_mesh* m, int nv, int nf, const double* pos, const int32_t
     tp_mesh* o = nullptr;
     TP_TRY(tp_mesh_create(m->device, nv, nf, pos, faces, ptr_kind, stream, &o));
     TP_CUDA(cudaStreamSynchronize(st));
-    obstacle_release(m);
-    m->obs = o;
-    m->obs_weight = weight;
-    const int s = obstacle_frame(m, st);
-    if (s != TP_OK) {
-        obstacle_release(m);
-        return s;
-    }
+    TP_TRY(obstacle_attach(m, o, weight, st));
+    TP_CUDA(cudaStreamSynchronize(st));
     return TP_OK;
 }
 

@@ -82,26 +82,93 @@ __device__ __forceinline__ T obs_term(T r2, T halfp, T& ir2) {
     return P6 ? ir2 * ir2 * ir2 : opow(ir2, halfp);
 }
 
+// two floats as one packed pair register (lane 0 = a), and back
+__device__ __forceinline__ unsigned long long opk2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 oupk2(unsigned long long r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+
+// p = 6 terms of two targets (one per lane of the packed pair registers)
+// against one source broadcast to both lanes, in packed FP32 (f32x2, IEEE
+// per lane): d = X_target - f_O(S), k = a_S |d|^-6,
+//   e += k;  with the gradient also g += k |d|^-2 d.
+__device__ __forceinline__ void obs2_p6(unsigned long long tx, unsigned long long ty, unsigned long long tz,
+                                        unsigned long long sx, unsigned long long sy, unsigned long long sz,
+                                        unsigned long long sa, unsigned long long& e) {
+    asm("{\n\t.reg .b64 dx, dy, dz, r2, ir2, k;\n\t.reg .f32 lo, hi;\n\t"
+        "sub.rn.f32x2 dx, %1, %4;\n\t"
+        "sub.rn.f32x2 dy, %2, %5;\n\t"
+        "sub.rn.f32x2 dz, %3, %6;\n\t"
+        "mul.rn.f32x2 r2, dz, dz;\n\t"
+        "fma.rn.f32x2 r2, dy, dy, r2;\n\t"
+        "fma.rn.f32x2 r2, dx, dx, r2;\n\t"
+        "mov.b64 {lo, hi}, r2;\n\t"
+        "rcp.approx.ftz.f32 lo, lo;\n\t"
+        "rcp.approx.ftz.f32 hi, hi;\n\t"
+        "mov.b64 ir2, {lo, hi};\n\t"
+        "mul.rn.f32x2 k, ir2, ir2;\n\t"
+        "mul.rn.f32x2 k, k, ir2;\n\t"
+        "fma.rn.f32x2 %0, k, %7, %0;\n\t}"
+        : "+l"(e)
+        : "l"(tx), "l"(ty), "l"(tz), "l"(sx), "l"(sy), "l"(sz), "l"(sa));
+}
+__device__ __forceinline__ void obs2_p6_grad(unsigned long long tx, unsigned long long ty, unsigned long long tz,
+                                             unsigned long long sx, unsigned long long sy, unsigned long long sz,
+                                             unsigned long long sa, unsigned long long& e, unsigned long long& gx,
+                                             unsigned long long& gy, unsigned long long& gz) {
+    asm("{\n\t.reg .b64 dx, dy, dz, r2, ir2, k;\n\t.reg .f32 lo, hi;\n\t"
+        "sub.rn.f32x2 dx, %4, %7;\n\t"
+        "sub.rn.f32x2 dy, %5, %8;\n\t"
+        "sub.rn.f32x2 dz, %6, %9;\n\t"
+        "mul.rn.f32x2 r2, dz, dz;\n\t"
+        "fma.rn.f32x2 r2, dy, dy, r2;\n\t"
+        "fma.rn.f32x2 r2, dx, dx, r2;\n\t"
+        "mov.b64 {lo, hi}, r2;\n\t"
+        "rcp.approx.ftz.f32 lo, lo;\n\t"
+        "rcp.approx.ftz.f32 hi, hi;\n\t"
+        "mov.b64 ir2, {lo, hi};\n\t"
+        "mul.rn.f32x2 k, ir2, ir2;\n\t"
+        "mul.rn.f32x2 k, k, ir2;\n\t"
+        "mul.rn.f32x2 k, k, %10;\n\t"
+        "add.rn.f32x2 %0, %0, k;\n\t"
+        "mul.rn.f32x2 k, k, ir2;\n\t"
+        "fma.rn.f32x2 %1, k, dx, %1;\n\t"
+        "fma.rn.f32x2 %2, k, dy, %2;\n\t"
+        "fma.rn.f32x2 %3, k, dz, %3;\n\t}"
+        : "+l"(e), "+l"(gx), "+l"(gy), "+l"(gz)
+        : "l"(tx), "l"(ty), "l"(tz), "l"(sx), "l"(sy), "l"(sz), "l"(sa));
+}
+
 // ---------------------------------------------------------------------------
 // obstacle faces in the surface's frame
 // ---------------------------------------------------------------------------
 
 // f_O(S) - c (c: the surface's reference frame) from the obstacle's
-// positions, in FP64 and as FP32 hi + lo, with the obstacle face areas
+// positions, in FP64 and as FP32 hi + lo, with the obstacle face areas;
+// entry i holds face S = perm[i] (the obstacle's Morton order, so that a
+// tile of consecutive entries is a compact patch of the obstacle)
 __global__ void k_obs_frame(const double* __restrict__ pos, const int* __restrict__ faces, int nf,
-                            const d4* __restrict__ of64a, const double* __restrict__ center,
-                            d4* __restrict__ f64a, float4* __restrict__ f32a, float4* __restrict__ f32c) {
-    int S = blockIdx.x * blockDim.x + threadIdx.x;
-    if (S >= nf) return;
+                            const int* __restrict__ perm, const d4* __restrict__ of64a,
+                            const double* __restrict__ center, d4* __restrict__ f64a, float4* __restrict__ f32a,
+                            float4* __restrict__ f32c) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    const int S = perm[i];
     const double* pi = pos + 3 * faces[3 * S];
     const double* pj = pos + 3 * faces[3 * S + 1];
     const double* pk = pos + 3 * faces[3 * S + 2];
     double X[3];
     for (int c = 0; c < 3; ++c) X[c] = (pi[c] + pj[c] + pk[c]) / 3.0 - center[c];
     const double a = of64a[S].w;
-    f64a[S] = d4{X[0], X[1], X[2], a};
-    f32a[S] = make_float4((float)X[0], (float)X[1], (float)X[2], (float)a);
-    f32c[S] = make_float4((float)(X[0] - (double)(float)X[0]), (float)(X[1] - (double)(float)X[1]),
+    f64a[i] = d4{X[0], X[1], X[2], a};
+    f32a[i] = make_float4((float)X[0], (float)X[1], (float)X[2], (float)a);
+    f32c[i] = make_float4((float)(X[0] - (double)(float)X[0]), (float)(X[1] - (double)(float)X[1]),
                           (float)(X[2] - (double)(float)X[2]), 0.f);
 }
 
@@ -166,7 +233,9 @@ __device__ __forceinline__ void obs_block_box(float lx, float ly, float lz, floa
 
 // Per target face T (surface order) and source split: accumulator 0 gets
 // sum_S a_S |d|^{-p}, accumulators 1..3 (DIFF) sum_S a_S |d|^{-p-2} d with
-// d = X_T - f_O(S) (target minus source).
+// d = X_T - f_O(S) (target minus source). FP32 with p = 6 on far tiles:
+// two targets per packed f32x2 instruction, the sources staged in shared
+// memory already broadcast to both lanes.
 template <typename T, bool P6, bool DIFF, int TT>
 __global__ void __launch_bounds__(NT)
 k_obstacle(const typename V4O<T>::type* __restrict__ ta, const float4* __restrict__ tlo, int nt,
@@ -175,9 +244,12 @@ k_obstacle(const typename V4O<T>::type* __restrict__ ta, const float4* __restric
            T halfp, double* __restrict__ part) {
     using V4 = typename V4O<T>::type;
     constexpr bool F32 = sizeof(T) == 4;
+    constexpr bool PACK = F32 && P6 && TT % 2 == 0;
     constexpr int NACC = DIFF ? 4 : 1;
+    constexpr int TP = PACK ? TT / 2 : 1;
     __shared__ V4 sh[NT];
     __shared__ float4 shl[F32 ? NT : 1];
+    __shared__ ulonglong2 shp[PACK ? 2 * NT : 1];
     __shared__ float sbox[6];
     T tx[TT], ty[TT], tz[TT];
     float lx[TT], ly[TT], lz[TT];
@@ -205,6 +277,15 @@ k_obstacle(const typename V4O<T>::type* __restrict__ ta, const float4* __restric
         obs_block_box(bl[0], bl[1], bl[2], bh[0], bh[1], bh[2], sbox);
         thr2 = (float)thr[0];
     }
+    unsigned long long TX[TP], TY[TP], TZ[TP];
+    if constexpr (PACK) {
+#pragma unroll
+        for (int jj = 0; jj < TP; ++jj) {
+            TX[jj] = opk2((float)tx[2 * jj], (float)tx[2 * jj + 1]);
+            TY[jj] = opk2((float)ty[2 * jj], (float)ty[2 * jj + 1]);
+            TZ[jj] = opk2((float)tz[2 * jj], (float)tz[2 * jj + 1]);
+        }
+    }
     OAcc<T> acc[TT][NACC];
     const int ntiles = (no + NT - 1) / NT;
     const int k0 = blockIdx.y * tiles_per_split;
@@ -220,12 +301,16 @@ k_obstacle(const typename V4O<T>::type* __restrict__ ta, const float4* __restric
         }
         const int src = tile * NT + threadIdx.x;
         __syncthreads();
+        V4 sv;
         if (src < no) {
-            sh[threadIdx.x] = oa[src];
+            sv = oa[src];
         } else {
-            V4 pad;
-            pad.x = T(PAD_X); pad.y = T(0); pad.z = T(0); pad.w = T(0);
-            sh[threadIdx.x] = pad;
+            sv.x = T(PAD_X); sv.y = T(0); sv.z = T(0); sv.w = T(0);
+        }
+        sh[threadIdx.x] = sv;
+        if constexpr (PACK) {
+            shp[2 * threadIdx.x] = make_ulonglong2(opk2((float)sv.x, (float)sv.x), opk2((float)sv.y, (float)sv.y));
+            shp[2 * threadIdx.x + 1] = make_ulonglong2(opk2((float)sv.z, (float)sv.z), opk2((float)sv.w, (float)sv.w));
         }
         if (near) shl[threadIdx.x] = src < no ? olo[src] : make_float4(0.f, 0.f, 0.f, 0.f);
         __syncthreads();
@@ -256,6 +341,32 @@ k_obstacle(const typename V4O<T>::type* __restrict__ ta, const float4* __restric
                         }
                     }
                 }
+            } else if constexpr (PACK) {
+                unsigned long long P[TP][NACC];
+#pragma unroll
+                for (int jj = 0; jj < TP; ++jj)
+#pragma unroll
+                    for (int i = 0; i < NACC; ++i) P[jj][i] = 0ull;
+#pragma unroll 8
+                for (int q = 0; q < CH; ++q) {
+                    const ulonglong2 u0 = shp[2 * (c + q)], u1 = shp[2 * (c + q) + 1];
+#pragma unroll
+                    for (int jj = 0; jj < TP; ++jj) {
+                        if constexpr (DIFF)
+                            obs2_p6_grad(TX[jj], TY[jj], TZ[jj], u0.x, u0.y, u1.x, u1.y, P[jj][0], P[jj][1],
+                                         P[jj][2], P[jj][3]);
+                        else
+                            obs2_p6(TX[jj], TY[jj], TZ[jj], u0.x, u0.y, u1.x, u1.y, P[jj][0]);
+                    }
+                }
+#pragma unroll
+                for (int jj = 0; jj < TP; ++jj)
+#pragma unroll
+                    for (int i = 0; i < NACC; ++i) {
+                        const float2 v = oupk2(P[jj][i]);
+                        pt[2 * jj][i] = v.x;
+                        pt[2 * jj + 1][i] = v.y;
+                    }
             } else {
 #pragma unroll 8
                 for (int q = 0; q < CH; ++q) {
@@ -544,7 +655,7 @@ int obstacle_frame(tp_mesh* m, cudaStream_t st) {
     TP_TRY(ensure(m->obs_tilebox, sizeof(float4) * 2 * (size_t)ntiles));
     TP_TRY(ensure(m->obs_thr, sizeof(double)));
     k_obs_frame<<<(no + 255) / 256, 256, 0, st>>>(m->obs->pos.as<double>(), m->obs->faces.as<int>(), no,
-                                                  m->obs->f64a.as<d4>(), m->center.as<double>(),
+                                                  m->obs_perm.as<int>(), m->obs->f64a.as<d4>(), m->center.as<double>(),
                                                   m->obs_f64a.as<d4>(), m->obs_f32a.as<float4>(),
                                                   m->obs_f32c.as<float4>());
     TP_LAUNCH_CHECK();
@@ -554,6 +665,25 @@ int obstacle_frame(tp_mesh* m, cudaStream_t st) {
                                  m->obs_thr.as<double>());
     TP_LAUNCH_CHECK();
     return TP_OK;
+}
+
+// Attach obstacle mesh o (owned by m from here on): its Morton order (from
+// its BVH) fixes the order of the obstacle's faces in the direct sums.
+int obstacle_attach(tp_mesh* m, tp_mesh* o, double weight, cudaStream_t st) {
+    obstacle_release(m);
+    m->obs = o;
+    m->obs_weight = weight;
+    tp_params dp;
+    tp_params_default(&dp);
+    BvhView v;
+    int s = bvh_view(o, &dp, st, &v);
+    if (s == TP_OK) s = ensure(m->obs_perm, sizeof(int) * (size_t)o->nf);
+    if (s == TP_OK && cudaMemcpyAsync(m->obs_perm.ptr, v.perm, sizeof(int) * (size_t)o->nf,
+                                      cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        s = fail(TP_ERR_CUDA, "copying the obstacle's face order failed");
+    if (s == TP_OK) s = obstacle_frame(m, st);
+    if (s != TP_OK) obstacle_release(m);
+    return s;
 }
 
 int obstacle_terms(tp_mesh* m, const tp_params* p, bool diff, bool accumulate, double* erow, double* adj,
@@ -570,7 +700,8 @@ int obstacle_terms(tp_mesh* m, const tp_params* p, bool diff, bool accumulate, d
 }
 
 void obstacle_release(tp_mesh* m) {
-    Buf* all[] = {&m->obs_f64a, &m->obs_f32a, &m->obs_f32c, &m->obs_tilebox, &m->obs_thr, &m->obs_part};
+    Buf* all[] = {&m->obs_f64a, &m->obs_f32a, &m->obs_f32c, &m->obs_tilebox, &m->obs_thr, &m->obs_part,
+                  &m->obs_perm};
     for (Buf* b : all) release(*b);
     if (m->obs) {
         tp_mesh_destroy(m->obs);

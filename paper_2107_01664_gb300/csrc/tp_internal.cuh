@@ -174,7 +174,7 @@ struct tp_mesh {
     // BVH), and its faces re-expressed in this mesh's frame for the direct sums
     tp_mesh* obs = nullptr;
     double obs_weight = 0.0;
-    tp::Buf obs_f64a, obs_f32a, obs_f32c, obs_tilebox, obs_thr, obs_part;
+    tp::Buf obs_perm, obs_f64a, obs_f32a, obs_f32c, obs_tilebox, obs_thr, obs_part;
     tp::Profiler prof;
     double pairs = 0.0; // pair interactions evaluated (host-known part)
 };
@@ -258,6 +258,7 @@ int lincomb(double* y, const double* const* xs, const double* coef_host, int nve
             double beta, cudaStream_t st);
 
 // -------- obstacle.cu ------------------------------------------------------
+int obstacle_attach(tp_mesh* m, tp_mesh* obstacle, double weight, cudaStream_t st);  // m owns it
 int obstacle_frame(tp_mesh* m, cudaStream_t st);   // obstacle faces in m's current frame
 // obstacle rows w a_T E_obs(X_T) into erow_dev (and with diff its face
 // adjoints into adj_dev [nf*7]); accumulate: add to what is there
