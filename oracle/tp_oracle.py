@@ -367,10 +367,34 @@ def poisson_solve(C, b):
     return project_mean_zero(z)
 
 
-def precond_apply(f, faces, b, p=6.0):
+def pinned_poisson_solve(C, b, pins):
+    """Poisson solve with vertex pins appended to the Laplacian (§7.2: the
+    pin rows and columns added to the integer Laplacian): the first block of
+    the solution of [C S^T; S 0][z; mu] = [b; 0], S the rows of the identity
+    at the pinned vertices (one pin fixes all three coordinates, and the
+    three coordinates are independent columns of b). b [nv,k]."""
+    nv = C.shape[0]
+    pins = np.asarray(pins)
+    S = sp.csr_matrix((np.ones(len(pins)), (np.arange(len(pins)), pins)), shape=(len(pins), nv))
+    K = sp.bmat([[C, S.T], [S, None]]).tocsc()
+    lu = spla.splu(K)
+    z = np.zeros_like(b)
+    for c in range(b.shape[1]):
+        rhs = np.concatenate([b[:, c], np.zeros(len(pins))])
+        z[:, c] = lu.solve(rhs)[:nv]
+    return z
+
+
+def precond_apply(f, faces, b, p=6.0, pins=None):
     """Preconditioner of §5.2: C^+ L^{2-s} C^+ b (the two integer Laplacians
-    are the cotan stiffness matrix; all vectors kept mean-zero)."""
+    are the cotan stiffness matrix; all vectors kept mean-zero). With vertex
+    pins (§7.2) the pin rows are appended to both Laplacian solves
+    (pinned_poisson_solve) and nothing is projected: the pins remove the
+    nullspace."""
     C = cotan_laplacian(f, faces)
+    if pins is not None and len(pins):
+        z = pinned_poisson_solve(C, b, pins)
+        return pinned_poisson_solve(C, apply_operator(f, faces, z, "L", p), pins)
     z = poisson_solve(C, b)
     z = project_mean_zero(apply_operator(f, faces, z, "L", p))
     return poisson_solve(C, z)
@@ -420,7 +444,9 @@ def _constraint_rows(f, faces, use_area, use_volume):
         rows.append(area_gradient(f, faces).reshape(-1))
     if use_volume:
         rows.append(volume_gradient(f, faces).reshape(-1))
-    return np.array(rows).reshape(len(rows), -1)
+    if not rows:
+        return np.zeros((0, 3 * len(f)))
+    return np.array(rows)
 
 
 def _barycenter_rows(nv):
@@ -432,13 +458,33 @@ def _barycenter_rows(nv):
     return J
 
 
-def saddle_matrix(f, faces, use_area=True, use_volume=True, p=6.0):
-    """[A_3 dPhi^T; dPhi 0] of Eq. 14 with the barycenter rows (§7.1.1) plus
+def _pin_rows(nv, pins):
+    """Jacobian of the vertex pins Phi_P(f) = f(i) - f_0(i) (§7.1.2): per
+    pinned vertex, a copy of I_3 in the block of that vertex."""
+    J = np.zeros((3 * len(pins), 3 * nv))
+    for k, i in enumerate(pins):
+        for c in range(3):
+            J[3 * k + c, 3 * i + c] = 1.0
+    return J
+
+
+def _positional_rows(nv, pins):
+    """The linear positional rows of the step: the barycenter rows, or the
+    pin rows when pins are given (a pin removes the nullspace, so the
+    barycenter constraint is then not needed, §7.1.2)."""
+    if pins is not None and len(pins):
+        return _pin_rows(nv, pins)
+    return _barycenter_rows(nv)
+
+
+def saddle_matrix(f, faces, use_area=True, use_volume=True, p=6.0, pins=None):
+    """[A_3 dPhi^T; dPhi 0] of Eq. 14 with the barycenter rows (§7.1.1), or
+    the vertex pin rows (§7.1.2, included in the matrix as in §7.2), plus
     area and volume rows; A_3 = A (x) I_3 on the [nv,3] ordering."""
     nv = len(f)
     A = operator_matrix(f, faces, "A", p)
     A3 = np.kron(A, np.eye(3))
-    J = np.concatenate([_barycenter_rows(nv),
+    J = np.concatenate([_positional_rows(nv, pins),
                         _constraint_rows(f, faces, use_area, use_volume)], axis=0)
     m = J.shape[0]
     M = np.zeros((3 * nv + m, 3 * nv + m))
@@ -464,31 +510,44 @@ def _total_differential(f, faces, p, obstacle):
     return g
 
 
-def descent_direction(f, faces, use_area=True, use_volume=True, p=6.0, obstacle=None):
+def descent_direction(f, faces, use_area=True, use_volume=True, p=6.0, obstacle=None, pins=None):
     """x of Eq. 14: [A_3 dPhi^T; dPhi 0][x; lambda] = [-dE; 0], solved
     densely. Returns (x [nv,3], g = dE [nv,3]). With an obstacle (see
     _total_energy) dE is the differential of the sum: the obstacle term is
     one more energy in the flow, the metric A is unchanged."""
     nv = len(f)
     g = _total_differential(f, faces, p, obstacle)
-    M, J = saddle_matrix(f, faces, use_area, use_volume, p)
+    M, J = saddle_matrix(f, faces, use_area, use_volume, p, pins)
     rhs = np.zeros(M.shape[0])
     rhs[:3 * nv] = -g.reshape(-1)
     sol = np.linalg.solve(M, rhs)
     return sol[:3 * nv].reshape(nv, 3), g
 
 
-def schur_direction(f, faces, use_area=True, use_volume=True, p=6.0):
+def schur_direction(f, faces, use_area=True, use_volume=True, p=6.0, pins=None):
     """The same direction via the Schur complement of §5.3 (Eq. 17, Eq. 18)
     with A_3^{-1} applied in the mean-zero subspace (where the barycenter
     rows are satisfied), g = dE, Z = A_3^{-1} dPhi^T:
-        x = -(A^{-1} g - Z (dPhi Z)^{-1} dPhi A^{-1} g)."""
+        x = -(A^{-1} g - Z (dPhi Z)^{-1} dPhi A^{-1} g).
+    With pins, the pin rows stay in the matrix (§7.2): A_3^{-1} is the solve
+    of the pinned saddle system, i.e. A restricted to the free vertices with
+    zero pinned rows, and only area and volume go through the Schur
+    complement."""
     nv = len(f)
     g = differential(f, faces, p)
     A = operator_matrix(f, faces, "A", p)
-    P = np.eye(nv) - np.full((nv, nv), 1.0 / nv)
-    Ainv = np.linalg.pinv(P @ A @ P)
-    Ainv3 = lambda w: (Ainv @ project_mean_zero(w.reshape(nv, 3))).reshape(-1)
+    if pins is not None and len(pins):
+        free = np.setdiff1d(np.arange(nv), np.asarray(pins))
+        AFFi = np.linalg.inv(A[np.ix_(free, free)])
+
+        def Ainv3(w):
+            out = np.zeros((nv, 3))
+            out[free] = AFFi @ w.reshape(nv, 3)[free]
+            return out.reshape(-1)
+    else:
+        P = np.eye(nv) - np.full((nv, nv), 1.0 / nv)
+        Ainv = np.linalg.pinv(P @ A @ P)
+        Ainv3 = lambda w: (Ainv @ project_mean_zero(w.reshape(nv, 3))).reshape(-1)
     J = _constraint_rows(f, faces, use_area, use_volume)
     Ag = Ainv3(g.reshape(-1))
     Z = np.stack([Ainv3(row) for row in J], axis=1)
@@ -508,17 +567,20 @@ def constraint_values(f, faces, A0, V0, use_area=True, use_volume=True):
 
 def precond_step(f, faces, A0, V0, use_area=True, use_volume=True, p=6.0,
                  tau0=1.0, armijo_c=1e-4, shrink=0.5, ls_max=30, fixed_tau=None, proj_iters=1,
-                 obstacle=None):
+                 obstacle=None, pins=None):
     """One constrained descent step (§3, steps 1-5; §5.4 with exact solves):
     direction by Eq. 14, Armijo backtracking from tau0 (E(f + tau x) <=
     E(f) + c tau dE.x), then corrective projections by Eq. 15 with the
     left-hand side of Eq. 14 (Jacobian at f) and Phi at the current point;
     §3.3.2 says one suffices and allows repeats (proj_iters). With
     `obstacle` = (f_O, faces_O, weight) the energy is E of Eq. 10 plus the
-    static-obstacle term of §7.3.2.
+    static-obstacle term of §7.3.2. With `pins` (vertex indices) the pin rows
+    replace the barycenter rows; the pinned positions f_0 are those of f, so
+    Phi_P = 0 at the start and every row of the projection's right-hand side
+    for a pin is 0.
     Returns dict(f_new, x, tau, E0, E1, h)."""
     nv = len(f)
-    x, g = descent_direction(f, faces, use_area, use_volume, p, obstacle)
+    x, g = descent_direction(f, faces, use_area, use_volume, p, obstacle, pins)
     E0 = _total_energy(f, faces, p, obstacle)
     slope = float(np.sum(g * x))
     if fixed_tau is not None:
@@ -530,12 +592,15 @@ def precond_step(f, faces, A0, V0, use_area=True, use_volume=True, p=6.0,
                 break
             tau *= shrink
     f1 = f + tau * x
-    M, J = saddle_matrix(f, faces, use_area, use_volume, p)
+    M, J = saddle_matrix(f, faces, use_area, use_volume, p, pins)
+    npos = _positional_rows(nv, pins).shape[0]
     f2 = f1
     h = np.zeros_like(f)
     for _ in range(proj_iters):
         rhs = np.zeros(M.shape[0])
-        rhs[3 * nv + 3:] = -constraint_values(f2, faces, A0, V0, use_area, use_volume)
+        if pins is not None and len(pins):
+            rhs[3 * nv:3 * nv + npos] = -(f2[pins] - f[pins]).reshape(-1)
+        rhs[3 * nv + npos:] = -constraint_values(f2, faces, A0, V0, use_area, use_volume)
         dh = np.linalg.solve(M, rhs)[:3 * nv].reshape(nv, 3)
         f2 = f2 + dh
         h = h + dh
