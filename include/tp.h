@@ -69,7 +69,10 @@ extern "C" {
 #define TP_POISSON_CHOLESKY 0  /* pre-factorised C (sparse Cholesky, FP32 factor, FP64 refinement) */
 #define TP_POISSON_CG       1  /* Jacobi-preconditioned CG, FP64 */
 
-/* constraint flags (the barycenter constraint of §7.1.1 is always on) */
+/* largest number of vertex pins of a mesh (tp_pins_set) */
+#define TP_MAX_PINS 64
+
+/* constraint flags (the barycenter constraint of §7.1.1 is on unless pins are set) */
 #define TP_CONSTRAINT_AREA    1  /* total area, §7.1.3 */
 #define TP_CONSTRAINT_VOLUME  2  /* total signed volume, §7.1.4 */
 
@@ -197,6 +200,10 @@ int fractional_apply(tp_mesh* m, const tp_params* p, int op, const double* v,
  * refinement stops converging, is handed to the CG solver.
  * TP_POISSON_CG: Jacobi-preconditioned CG (FP64) with b and z projected to
  * zero mean over the whole mesh (connected meshes).
+ * With vertex pins set (tp_pins_set) the pin rows are appended to C (§7.2):
+ * z solves [C S^T; S 0] [z; mu] = [b; 0] (z = 0 at the pins, C z = b on the
+ * free vertices, b's pinned rows ignored), computed from the unpinned solver
+ * above by a correction with one solve per pin (once per positions).
  * *iters_out (host, may be NULL) receives the CG iterations or refinement
  * sweeps. TP_ERR_NOT_CONVERGED if cg_max is hit; TP_ERR_TIMEOUT if a
  * device-side wait gave up. */
@@ -221,6 +228,18 @@ int cotan_factor_info(tp_mesh* m, tp_chol_info* out);
 /* z = C^+ L^{2-s} C^+ b, the preconditioner of §5.2, k columns. */
 int precond_apply(tp_mesh* m, const tp_params* p, const double* b, int k,
                   double* z, int ptr_kind, void* stream);
+
+/* Vertex pins (§7.1.2) of a mesh, handled as fast positional constraints
+ * (§7.2): n vertex indices (int32, 0 <= n <= TP_MAX_PINS; n = 0 removes the
+ * pins and `vertices` may be NULL). A pin keeps its vertex where it is:
+ * precond_step solves the saddle system with the pin rows inside A (the
+ * Krylov vectors are zero at the pins) and appends them to the Laplacians
+ * of the preconditioner (cotan_solve and precond_apply then solve the pinned
+ * systems), so the step and its projection leave pinned vertices in place.
+ * Pins replace the barycenter constraint of §7.1.1 (they remove the
+ * nullspace). TP_ERR_INVALID_ARG for an index out of range, a repeated
+ * vertex, or a connected component without a pin. Synchronises `stream`. */
+int tp_pins_set(tp_mesh* m, int n, const int32_t* vertices, int ptr_kind, void* stream);
 
 /* One constrained descent step (§5.4): dE, the Schur-complement solution
  * of the saddle problem (Eq. 14, 17, 18) with GMRES on A_3 preconditioned

@@ -27,7 +27,7 @@ __all__ = [
     "fractional_apply", "cotan_solve", "precond_apply", "precond_step", "TangentPointEnergy",
     "lib_path", "lib", "tp_kernel_stat", "tp_profile_enable", "tp_profile_read", "tp_launch_count",
     "tp_energy_noalloc", "tp_chol_info", "cotan_factor_info", "TP_POISSON_CHOLESKY", "TP_POISSON_CG",
-    "tp_obstacle_set", "tp_obstacle_energy",
+    "tp_obstacle_set", "tp_obstacle_energy", "tp_pins_set", "TP_MAX_PINS",
 ]
 
 TP_OK, TP_ERR_INVALID_ARG, TP_ERR_DEGENERATE, TP_ERR_OOM = 0, 1, 2, 3
@@ -38,6 +38,7 @@ TP_OP_A, TP_OP_B, TP_OP_B0, TP_OP_L = 0, 1, 2, 3
 TP_BH_DIFF_FULL, TP_BH_DIFF_LITERAL = 0, 1
 TP_CONSTRAINT_AREA, TP_CONSTRAINT_VOLUME = 1, 2
 TP_POISSON_CHOLESKY, TP_POISSON_CG = 0, 1
+TP_MAX_PINS = 64
 _OPS = {"A": TP_OP_A, "B": TP_OP_B, "B0": TP_OP_B0, "L": TP_OP_L}
 
 
@@ -124,6 +125,7 @@ def lib():
         "tp_launch_count": (ctypes.c_ulonglong, []),
         "tp_energy_noalloc": (c_int, [vp, c_int, vp, c_int, c_double, vp, vp]),
         "tp_obstacle_set": (c_int, [vp, c_int, c_int, vp, vp, c_double, c_int, vp]),
+        "tp_pins_set": (c_int, [vp, c_int, vp, c_int, vp]),
         "tp_obstacle_energy": (c_int, [vp, P(tp_params), P(c_double), vp, c_int, vp]),
     }
     for name, (res, args) in sig.items():
@@ -337,6 +339,15 @@ def precond_step(mesh: Mesh, constraints: tp_constraints, p: tp_params | None = 
         "krylov_iters": rep.krylov_iters, "cg_iters": rep.cg_iters, "ls_trials": rep.ls_trials,
         "status": rep.status, "pair_interactions": rep.pair_interactions,
     }
+
+
+def tp_pins_set(mesh: Mesh, vertices=None):
+    """Pin the given vertices (§7.1.2, §7.2); None or an empty list removes the pins."""
+    if vertices is None or len(vertices) == 0:
+        _check(lib().tp_pins_set(mesh.handle, 0, None, TP_PTR_HOST, _stream_ptr()))
+        return
+    vp, vk, keep = _as_buffer(vertices, np.int32)
+    _check(lib().tp_pins_set(mesh.handle, int(np.shape(vertices)[0]), vp, vk, _stream_ptr(vertices)))
 
 
 def tp_obstacle_set(mesh: Mesh, positions=None, faces=None, weight: float = 1.0):

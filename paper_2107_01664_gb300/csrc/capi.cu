@@ -192,6 +192,7 @@ int tp_mesh_destroy(tp_mesh* m) {
                   &m->kry};
     for (Buf* b : all) release(*b);
     obstacle_release(m);
+    pins_release(m);
     chol_release(m);
     release(m->bhcount);
     prof_release(m);
@@ -309,7 +310,8 @@ int cotan_solve(tp_mesh* m, const tp_params* p, const double* b, int k, double* 
     TP_TRY(ensure(m->io_out, bytes));
     double* out = ptr_kind == TP_PTR_DEVICE ? z : m->io_out.as<double>();
     int it = 0;
-    int s = cg_solve(m, p, (const double*)bin, k, out, st, &it);
+    int s = m->npins ? pinned_solve(m, p, (const double*)bin, k, out, st, &it)
+                     : cg_solve(m, p, (const double*)bin, k, out, st, &it);
     if (iters_out) *iters_out = it;
     if (s != TP_OK) return s;
     if (ptr_kind == TP_PTR_HOST) TP_TRY(copy_out(z, out, bytes, TP_PTR_HOST, st));
@@ -378,6 +380,26 @@ int tp_obstacle_set(tp_mesh* m, int nv, int nf, const double* pos, const int32_t
     TP_TRY(obstacle_attach(m, o, weight, st));
     TP_CUDA(cudaStreamSynchronize(st));
     return TP_OK;
+}
+
+int tp_pins_set(tp_mesh* m, int n, const int32_t* vertices, int ptr_kind, void* stream) {
+    set_error("");
+    TP_TRY(check_mesh(m));
+    TP_TRY(check_kind(ptr_kind));
+    if (n < 0 || n > TP_MAX_PINS) return fail(TP_ERR_INVALID_ARG, "n must be in 0..TP_MAX_PINS");
+    if (n > 0 && !vertices) return fail(TP_ERR_INVALID_ARG, "vertices is NULL");
+    DeviceGuard g(m->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int> idx(n);
+    if (n > 0) {
+        if (ptr_kind == TP_PTR_HOST) {
+            std::memcpy(idx.data(), vertices, sizeof(int) * (size_t)n);
+        } else {
+            TP_CUDA(cudaMemcpyAsync(idx.data(), vertices, sizeof(int) * (size_t)n, cudaMemcpyDeviceToHost, st));
+            TP_CUDA(cudaStreamSynchronize(st));
+        }
+    }
+    return pins_set(m, n, idx.data(), st);
 }
 
 int tp_obstacle_energy(tp_mesh* m, const tp_params* p, double* E_out, double* dE, int ptr_kind, void* stream) {

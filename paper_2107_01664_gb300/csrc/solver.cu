@@ -61,11 +61,15 @@ int precond_apply_dev(tp_mesh* m, const tp_params* p, const double* b, int k, do
     TP_TRY(ensure(m->prec[0], sizeof(double) * n));
     TP_TRY(ensure(m->prec[1], sizeof(double) * n));
     int it1 = 0, it2 = 0;
-    int s1 = cg_solve(m, p, b, k, m->prec[0].as<double>(), st, &it1);
+    // with pins the pin rows are appended to both Laplacians (§7.2)
+    auto solve = [&](const double* rhs, double* out, int* it) {
+        return m->npins ? pinned_solve(m, p, rhs, k, out, st, it) : cg_solve(m, p, rhs, k, out, st, it);
+    };
+    int s1 = solve(b, m->prec[0].as<double>(), &it1);
     if (s1 != TP_OK && (strict || s1 != TP_ERR_NOT_CONVERGED)) return s1;
-    // (the second solve projects its right-hand side itself)
+    // (the second solve projects its right-hand side itself, or ignores its pinned rows)
     TP_TRY(apply_op(m, p, TP_OP_L, m->prec[0].as<double>(), k, m->prec[1].as<double>(), st));
-    int s2 = cg_solve(m, p, m->prec[1].as<double>(), k, z, st, &it2);
+    int s2 = solve(m->prec[1].as<double>(), z, &it2);
     if (s2 != TP_OK && (strict || s2 != TP_ERR_NOT_CONVERGED)) return s2;
     if (cg_iters) *cg_iters += it1 + it2;
     return TP_OK;
@@ -134,7 +138,7 @@ static int unpack(const double* srcp, int nv, const std::vector<double*>& dst, c
 // y = A v on packed columns (mean-zero output)
 static int apply_A_packed(tp_mesh* m, const tp_params* p, const double* v, int k, double* y, cudaStream_t st) {
     TP_TRY(apply_op(m, p, TP_OP_A, v, k, y, st));
-    return project_mean_zero(m, y, k, st);
+    return project_space(m, y, k, st);
 }
 
 struct GmSys {
@@ -176,7 +180,7 @@ static int fgmres_multi(tp_mesh* m, const tp_params* p, int ns, const double* co
         status[i] = TP_OK;
         TP_CUDA(cudaMemsetAsync(q.x, 0, sizeof(double) * n, st));
         TP_CUDA(cudaMemcpyAsync(q.V, q.b, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
-        TP_TRY(project_mean_zero(m, q.V, 3, st));
+        TP_TRY(project_space(m, q.V, 3, st));
         double bn2;
         const double* xs[1] = {q.V};
         TP_TRY(dots(m, xs, q.V, 1, n, &bn2, st));
@@ -330,7 +334,7 @@ static int fgmres_multi(tp_mesh* m, const tp_params* p, int ns, const double* co
             const double* xs[2] = {q.b, q.w};
             double cf[2] = {1.0, -1.0};
             TP_TRY(lincomb(q.V, xs, cf, 2, n, 0.0, st));
-            TP_TRY(project_mean_zero(m, q.V, 3, st));
+            TP_TRY(project_space(m, q.V, 3, st));
             double rn2;
             const double* x1[1] = {q.V};
             TP_TRY(dots(m, x1, q.V, 1, n, &rn2, st));
@@ -343,7 +347,7 @@ static int fgmres_multi(tp_mesh* m, const tp_params* p, int ns, const double* co
     }
     ks->iters += total;
     for (int i = 0; i < ns; ++i) {
-        TP_TRY(project_mean_zero(m, S[i].x, 3, st));
+        TP_TRY(project_space(m, S[i].x, 3, st));
         if (!S[i].converged) status[i] = TP_ERR_NOT_CONVERGED;
     }
     return TP_OK;

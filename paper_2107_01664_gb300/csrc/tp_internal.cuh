@@ -175,6 +175,12 @@ struct tp_mesh {
     tp_mesh* obs = nullptr;
     double obs_weight = 0.0;
     tp::Buf obs_perm, obs_f64a, obs_f32a, obs_f32c, obs_tilebox, obs_thr, obs_part;
+    // vertex pins (§7.1.2, §7.2): indices, component of each vertex and
+    // pinned flags, W = C^+ S^T and the inverse of the pins' small system
+    int npins = 0, pin_ncomp = 0;
+    bool pin_valid = false;          // W and the small system match the positions
+    std::vector<int> pin_host, pin_comp_host;
+    tp::Buf pin_idx, pin_vcomp, pin_W, pin_Minv, pin_tmp;
     tp::Profiler prof;
     double pairs = 0.0; // pair interactions evaluated (host-known part)
 };
@@ -265,6 +271,16 @@ int obstacle_frame(tp_mesh* m, cudaStream_t st);   // obstacle faces in m's curr
 int obstacle_terms(tp_mesh* m, const tp_params* p, bool diff, bool accumulate, double* erow_dev,
                    double* adj_dev, cudaStream_t st);
 void obstacle_release(tp_mesh* m);
+
+// -------- pins.cu ----------------------------------------------------------
+int pins_set(tp_mesh* m, int n, const int* idx_host, cudaStream_t st);   // n = 0 removes the pins
+void pins_release(tp_mesh* m);
+// z = first block of [C S^T; S 0]^{-1} [b; 0] (k <= 9 columns); TP_ERR_NOT_CONVERGED
+// from the inner solve is passed on with z filled
+int pinned_solve(tp_mesh* m, const tp_params* p, const double* b_dev, int k, double* z_dev,
+                 cudaStream_t st, int* iters);
+// zero the pinned rows (pins set) or remove the mean (no pins)
+int project_space(tp_mesh* m, double* x_dev, int k, cudaStream_t st);
 
 // -------- solver.cu --------------------------------------------------------
 // E (host) of Eq. 10 or 16; with obstacle = true plus the static-obstacle term
