@@ -385,18 +385,53 @@ def pinned_poisson_solve(C, b, pins):
     return z
 
 
-def precond_apply(f, faces, b, p=6.0, pins=None):
+PREC_SELF_WEIGHT = 8.0
+
+
+def self_term_stiffness(f, faces, sigma, kappa):
+    """Within-face term of the L^sigma double integral that the pairwise
+    discretization of §5.1.1 (ordered pairs S != T, face averages) leaves
+    out. For a piecewise-linear u the pairs (x, y) inside one face S give
+    int_{SxS} (grad u . (x - y))^2 / |x - y|^{2 sigma + 2}, which is
+    |grad u_S|^2 times a constant times a_S^{2 - sigma}; summed over the faces
+    this is the P1 stiffness matrix with face weights w_S = kappa a_S^{1-sigma}:
+        G_ij = sum_S w_S a_S grad phi_i . grad phi_j
+    (the cotan matrix of the face-weighted cotangents). kappa is a design
+    constant of the preconditioner."""
+    nv = len(f)
+    X, N, a = face_geometry(f, faces)
+    G = hat_gradients(f, faces)
+    w = kappa * a ** (1.0 - sigma)
+    I, J, Wv = [], [], []
+    for i in range(3):
+        for j in range(3):
+            I.append(faces[:, i])
+            J.append(faces[:, j])
+            Wv.append(w * a * np.sum(G[:, i] * G[:, j], axis=1))
+    return sp.csr_matrix((np.concatenate(Wv), (np.concatenate(I), np.concatenate(J))), shape=(nv, nv))
+
+
+def precond_apply(f, faces, b, p=6.0, pins=None, self_weight=PREC_SELF_WEIGHT):
     """Preconditioner of §5.2: C^+ L^{2-s} C^+ b (the two integer Laplacians
-    are the cotan stiffness matrix; all vectors kept mean-zero). With vertex
-    pins (§7.2) the pin rows are appended to both Laplacian solves
-    (pinned_poisson_solve) and nothing is projected: the pins remove the
-    nullspace."""
+    are the cotan stiffness matrix; all vectors kept mean-zero). The forward
+    fractional operator is L^{2-s} plus its within-face term
+    (self_term_stiffness, weight self_weight; 0 gives L^{2-s} of §5.1.1
+    alone). With vertex pins (§7.2) the pin rows are appended to both
+    Laplacian solves (pinned_poisson_solve) and nothing is projected: the
+    pins remove the nullspace."""
     C = cotan_laplacian(f, faces)
+    sigma = 2.0 - sobolev_s(p)
+    G = self_term_stiffness(f, faces, sigma, self_weight) if self_weight else None
+
+    def middle(z):
+        y = apply_operator(f, faces, z, "L", p)
+        return y + G @ z if G is not None else y
+
     if pins is not None and len(pins):
         z = pinned_poisson_solve(C, b, pins)
-        return pinned_poisson_solve(C, apply_operator(f, faces, z, "L", p), pins)
+        return pinned_poisson_solve(C, middle(z), pins)
     z = poisson_solve(C, b)
-    z = project_mean_zero(apply_operator(f, faces, z, "L", p))
+    z = project_mean_zero(middle(z))
     return poisson_solve(C, z)
 
 
