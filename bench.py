@@ -313,6 +313,59 @@ def obstacle_scene(tp, dev, reps=5, steps=2):
     return out
 
 
+def pinned_steps(tp, dev, steps=2):
+    """Vertex pins as fast positional constraints (§7.1.2, §7.2): constrained
+    steps on torus_20k with 8 pinned vertices (the benchmark's step settings),
+    and the Krylov iterations to krylov_tol on the smooth torus (no noise)
+    with the barycenter constraint and with the pins."""
+    import numpy as np
+    import torch
+    from synth import torus, workload
+    pins = np.arange(0, 10000, 1250, dtype=np.int32)
+
+    def cons_of(V, F):
+        A0 = float(np.sum(0.5 * np.linalg.norm(np.cross(V[F[:, 1]] - V[F[:, 0]], V[F[:, 2]] - V[F[:, 0]]), axis=1)))
+        Vol0 = float(np.sum(V[F[:, 0]] * np.cross(V[F[:, 1]], V[F[:, 2]])) / 6.0)
+        return tp.tp_constraints(flags=tp.TP_CONSTRAINT_AREA | tp.TP_CONSTRAINT_VOLUME, A0=A0, V0=Vol0)
+
+    V, F = workload(WORKLOAD)
+    cons = cons_of(V, F)
+    ps = step_params(tp)
+    f0 = torch.tensor(V, dtype=torch.float64, device=dev)
+    mesh = tp.Mesh(f0, torch.tensor(F, dtype=torch.int32, device=dev), device=dev.index or 0)
+    tp.tp_pins_set(mesh, pins)
+    tp.precond_step(mesh, cons, ps)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = []
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        tp.tp_mesh_set_positions(mesh, f0)
+        reps.append(tp.precond_step(mesh, cons, ps))
+    e1.record()
+    torch.cuda.synchronize()
+    f = tp.tp_mesh_get_positions(mesh)
+    mesh.close()
+    out = {"workload": "torus_20k", "pins": int(len(pins)), "ms_per_step": e0.elapsed_time(e1) / steps,
+           "krylov_iters_per_step": sum(r["krylov_iters"] for r in reps) / steps,
+           "pins_moved": bool(np.any(f[pins] != V[pins])), "status": [r["status"] for r in reps]}
+    # Krylov iterations to tolerance on the smooth torus
+    Vs, Fs = torus(200, 50, 1.0, 0.3)
+    cs = cons_of(Vs, Fs)
+    pt = tp.params(krylov_tol=1e-5, krylov_max=400, cg_tol=1e-6)
+    its = {}
+    for name, pv in (("barycenter", None), ("pins", pins)):
+        m2 = tp.Mesh(torch.tensor(Vs, dtype=torch.float64, device=dev),
+                     torch.tensor(Fs, dtype=torch.int32, device=dev), device=dev.index or 0)
+        if pv is not None:
+            tp.tp_pins_set(m2, pv)
+        r = tp.precond_step(m2, cs, pt)
+        its[name] = {"krylov_iters": r["krylov_iters"], "status": r["status"]}
+        m2.close()
+    out["smooth_torus_krylov"] = its
+    return out
+
+
 def bh_step(tp, dev, steps=2):
     """Constrained steps with every pair sum on the tree (theta = 0.5: energy,
     differential, and the A and L^{2-s} applies of the Krylov loop) on the
@@ -562,6 +615,7 @@ def gpu_arm(args):
     if not args.no_large:
         line["large_mesh_bh"] = large_bh(tp, dev)
         line["obstacle"] = obstacle_scene(tp, dev)
+        line["pins"] = pinned_steps(tp, dev)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = run_cpu_sample()
     mesh.close()
@@ -690,6 +744,8 @@ def main():
     ap.add_argument("--long-run", type=int, default=0, help="run N Barnes-Hut steps on the linked tori instead")
     ap.add_argument("--obstacle", action="store_true",
                     help="run only the static-obstacle scene (torus_20k around a ball) instead")
+    ap.add_argument("--pins", action="store_true",
+                    help="run only the vertex-pin steps (torus_20k with 8 pins) instead")
     ap.add_argument("--serve-n", type=int, default=64)
     ap.add_argument("--serve-fmax", type=int, default=50000)
     ap.add_argument("--serve-slots", type=int, default=4)
@@ -705,6 +761,12 @@ def main():
         import paper_2107_01664_gb300 as tp
         torch.cuda.set_device(0)
         print(json.dumps({"obstacle": obstacle_scene(tp, torch.device("cuda", 0))}))
+        return
+    if args.pins:
+        import torch
+        import paper_2107_01664_gb300 as tp
+        torch.cuda.set_device(0)
+        print(json.dumps({"pins": pinned_steps(tp, torch.device("cuda", 0))}))
         return
     if args.impl == "reference":
         reference_arm(args)

@@ -96,6 +96,8 @@ typedef struct tp_params {
     int    poisson_solver; /* TP_POISSON_CHOLESKY (default) or TP_POISSON_CG */
     int    bvh_refit;     /* 1 = after the positions change, keep the tree's face order and
                              recompute only the node data (refit); 0 = rebuild (new Morton order) */
+    double prec_self_weight; /* kappa >= 0 of the within-face term added to L^{2-s} in the
+                                preconditioner (see precond_apply); 0 = L^{2-s} of §5.1.1 alone */
 } tp_params;
 
 typedef struct tp_constraints {
@@ -134,7 +136,7 @@ typedef struct tp_mesh tp_mesh;
 /* Fill *p with the defaults: p=6, theta=0, leaf_size=8, FP32 pairs,
  * full BH differential, krylov_tol=1e-6, krylov_max=200, restart 30,
  * cg_tol=1e-6, cg_max=20000, Armijo c=1e-4, shrink 0.5, tau0=1, ls_max=30,
- * proj_iters=1, Cholesky Poisson solver. */
+ * proj_iters=1, Cholesky Poisson solver, prec_self_weight=8. */
 void tp_params_default(tp_params* p);
 
 /* Create a mesh on CUDA device `device` from nv positions and nf faces.
@@ -225,7 +227,14 @@ typedef struct tp_chol_info {
 
 int cotan_factor_info(tp_mesh* m, tp_chol_info* out);
 
-/* z = C^+ L^{2-s} C^+ b, the preconditioner of §5.2, k columns. */
+/* z = C^+ (L^{2-s} + G) C^+ b, the preconditioner of §5.2, k columns.
+ * G is the within-face part of the L^{2-s} double integral that the pair
+ * sums of §5.1.1 leave out (pairs of points inside one face): for
+ * piecewise-linear functions it is the P1 stiffness matrix with face
+ * weights kappa a_S^{1-(2-s)}, kappa = prec_self_weight (default 8; 0 gives
+ * the paper's C^+ L^{2-s} C^+). It makes the preconditioned operator's
+ * spectrum mesh-independent and narrow; it does not change the solutions
+ * of the Krylov solves. With pins set, both Laplacian solves are pinned. */
 int precond_apply(tp_mesh* m, const tp_params* p, const double* b, int k,
                   double* z, int ptr_kind, void* stream);
 

@@ -56,7 +56,7 @@ class tp_params(ctypes.Structure):
         ("cg_tol", ctypes.c_double), ("cg_max", ctypes.c_int), ("armijo_c", ctypes.c_double),
         ("armijo_shrink", ctypes.c_double), ("tau0", ctypes.c_double), ("ls_max", ctypes.c_int),
         ("fixed_tau", ctypes.c_int), ("proj_iters", ctypes.c_int), ("poisson_solver", ctypes.c_int),
-        ("bvh_refit", ctypes.c_int),
+        ("bvh_refit", ctypes.c_int), ("prec_self_weight", ctypes.c_double),
     ]
 
 

@@ -39,6 +39,8 @@ int check_params(const tp_params* p) {
     if (p->poisson_solver != TP_POISSON_CHOLESKY && p->poisson_solver != TP_POISSON_CG)
         return fail(TP_ERR_INVALID_ARG, "unknown Poisson solver");
     if (p->bvh_refit != 0 && p->bvh_refit != 1) return fail(TP_ERR_INVALID_ARG, "bvh_refit must be 0 or 1");
+    if (!(p->prec_self_weight >= 0.0) || !std::isfinite(p->prec_self_weight))
+        return fail(TP_ERR_INVALID_ARG, "prec_self_weight must be finite and >= 0");
     return TP_OK;
 }
 
@@ -91,6 +93,7 @@ void tp_params_default(tp_params* p) {
     p->proj_iters = 1;
     p->poisson_solver = TP_POISSON_CHOLESKY;
     p->bvh_refit = 0;
+    p->prec_self_weight = 8.0;
 }
 
 const char* tp_last_error(void) { return tp::last_error(); }
@@ -186,7 +189,7 @@ int tp_mesh_destroy(tp_mesh* m) {
     Buf* all[] = {&m->faces, &m->vf_ptr, &m->vf_idx, &m->pos, &m->center, &m->errflag, &m->f32a, &m->f32b,
                   &m->f32c, &m->tilebox,
                   &m->f64a, &m->f64b, &m->fgrad, &m->rowptr, &m->col, &m->cotsrc, &m->diagpos, &m->val,
-                  &m->dinv, &m->val32, &m->bvh_node, &m->bvh_perm, &m->bvh_keys, &m->bvh_tmp, &m->bvh_sortws,
+                  &m->dinv, &m->val32, &m->gval, &m->bvh_node, &m->bvh_perm, &m->bvh_keys, &m->bvh_tmp, &m->bvh_sortws,
                   &m->bvh_f32a, &m->bvh_f32b, &m->bvh_f32c, &m->bh_apply_ws, &m->part, &m->part2, &m->scal, &m->corner,
                   &m->wv64, &m->wv32, &m->io_in, &m->io_out, &m->adj, &m->erow, &m->tlist, &m->rowsum,
                   &m->kry};

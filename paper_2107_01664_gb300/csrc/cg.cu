@@ -131,6 +131,61 @@ int laplacian_values(tp_mesh* m, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
+// within-face term of the preconditioner's L^{2-s}: the P1 stiffness with
+// face weights w_S = kappa a_S^{1-sigma}, i.e. the cotan matrix of the
+// cotangents scaled by the weight of their face (same CSR pattern as C)
+// ---------------------------------------------------------------------------
+
+__global__ void k_corner_cot_weighted(const double* __restrict__ cot, const d4* __restrict__ f64a, int nf,
+                                      double kappa, double expo, double* __restrict__ wcot) {
+    const int S = blockIdx.x * blockDim.x + threadIdx.x;
+    if (S >= nf) return;
+    const double w = kappa * pow(f64a[S].w, expo);
+    for (int c = 0; c < 3; ++c) wcot[3 * S + c] = w * cot[3 * S + c];
+}
+
+// y[v][j] += sum_e val[e] x[col[e]][j], k columns
+__global__ void k_csr_add(const int* __restrict__ rowptr, const int* __restrict__ col,
+                          const double* __restrict__ val, int nv, int k, const double* __restrict__ x,
+                          double* __restrict__ y) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)nv * k) return;
+    const int v = (int)(i / k), j = (int)(i % k);
+    double s = 0.0;
+    for (int e = rowptr[v]; e < rowptr[v + 1]; ++e) s += val[e] * x[(size_t)col[e] * k + j];
+    y[i] += s;
+}
+
+int self_term_add(tp_mesh* m, const tp_params* p, const double* x, int k, double* y, cudaStream_t st) {
+    const double kappa = p->prec_self_weight;
+    if (!(kappa > 0.0)) return TP_OK;
+    const double sigma = 2.0 - (2.0 - 2.0 / p->p);   // 2 - s, s = 2 - 2/p
+    if (!m->gself_valid || m->gself_kappa != kappa || m->gself_sigma != sigma) {
+        TP_TRY(ensure(m->tmpv[7], sizeof(double) * 6 * (size_t)m->nf));
+        TP_TRY(ensure(m->gval, sizeof(double) * (size_t)m->nnz + sizeof(double) * m->nv));
+        double* cot = m->tmpv[7].as<double>();
+        double* wcot = cot + 3 * (size_t)m->nf;
+        k_corner_cot<<<(m->nf + 255) / 256, 256, 0, st>>>(m->pos.as<double>(), m->faces.as<int>(), m->nf, cot);
+        TP_LAUNCH_CHECK();
+        k_corner_cot_weighted<<<(m->nf + 255) / 256, 256, 0, st>>>(cot, m->f64a.as<d4>(), m->nf, kappa,
+                                                                   1.0 - sigma, wcot);
+        TP_LAUNCH_CHECK();
+        k_lap_values<<<(m->nv + 255) / 256, 256, 0, st>>>(m->rowptr.as<int>(), m->col.as<int>(),
+                                                          m->cotsrc.as<int>(), wcot, m->nv, m->gval.as<double>(),
+                                                          m->gval.as<double>() + m->nnz);
+        TP_LAUNCH_CHECK();
+        m->gself_valid = true;
+        m->gself_kappa = kappa;
+        m->gself_sigma = sigma;
+    }
+    const size_t n = (size_t)m->nv * k;
+    k_csr_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m->rowptr.as<int>(), m->col.as<int>(),
+                                                           m->gval.as<double>(), m->nv, k, x, y);
+    TP_LAUNCH_CHECK();
+    return TP_OK;
+}
+
+// ---------------------------------------------------------------------------
 // persistent CG: the whole solve in one cooperative launch
 // ---------------------------------------------------------------------------
 //

@@ -69,6 +69,7 @@ int precond_apply_dev(tp_mesh* m, const tp_params* p, const double* b, int k, do
     if (s1 != TP_OK && (strict || s1 != TP_ERR_NOT_CONVERGED)) return s1;
     // (the second solve projects its right-hand side itself, or ignores its pinned rows)
     TP_TRY(apply_op(m, p, TP_OP_L, m->prec[0].as<double>(), k, m->prec[1].as<double>(), st));
+    TP_TRY(self_term_add(m, p, m->prec[0].as<double>(), k, m->prec[1].as<double>(), st));
     int s2 = solve(m->prec[1].as<double>(), z, &it2);
     if (s2 != TP_OK && (strict || s2 != TP_ERR_NOT_CONVERGED)) return s2;
     if (cg_iters) *cg_iters += it1 + it2;

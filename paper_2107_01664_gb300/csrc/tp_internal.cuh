@@ -153,6 +153,11 @@ struct tp_mesh {
     int nnz = 0;
     tp::Buf rowptr, col, cotsrc, diagpos, val, dinv, val32;
     bool lap_valid = false;
+    // within-face term of the preconditioner's L^{2-s} (values on the CSR
+    // pattern of C, for the weight and order it was built with)
+    tp::Buf gval;
+    bool gself_valid = false;
+    double gself_kappa = 0.0, gself_sigma = 0.0;
     tp::CholState* chol = nullptr;   // created on the first factorised solve
     // Barnes-Hut tree (rebuilt per positions on demand)
     int bvh_nodes = 0, bvh_leaf = 0;
@@ -245,6 +250,10 @@ int laplacian_setup(tp_mesh* m);                        // CSR pattern (host, on
 int laplacian_values(tp_mesh* m, cudaStream_t st);      // cotan values for current positions
 int cg_solve(tp_mesh* m, const tp_params* p, const double* b_dev, int k, double* z_dev,
              cudaStream_t st, int* iters);
+// y += G x (k columns), G the within-face term of the preconditioner's
+// L^{2-s} with weight p->prec_self_weight (nothing when the weight is 0)
+int self_term_add(tp_mesh* m, const tp_params* p, const double* x_dev, int k, double* y_dev,
+                  cudaStream_t st);
 // -------- chol.cu ----------------------------------------------------------
 // z = C^+ b through the sparse Cholesky factor; *used = false when the
 // factor cannot serve the mesh (panel too large) or refinement stalled

@@ -204,11 +204,14 @@ def test_cotan_solve_not_converged_is_reported(lib, meshes, solver):
 
 
 @pytest.mark.parametrize("prec", [0, 1])
-def test_precond_apply(lib, meshes, prec):
-    V, F, m = meshes["ico3"]
+@pytest.mark.parametrize("kappa", [8.0, 0.0, 3.0])
+@pytest.mark.parametrize("name", ["ico3", "torus13x7"])
+def test_precond_apply(lib, meshes, prec, kappa, name):
+    # default within-face weight, the paper's L^{2-s} alone (0), another weight
+    V, F, m = meshes[name]
     b = O.project_mean_zero(vertex_vectors(len(V), 3, 11))
-    z = lib.precond_apply(m, b, lib.params(precision=prec, cg_tol=1e-12))
-    assert rel(z, O.precond_apply(V, F, b)) <= (TOL32 if prec == 0 else 1e-9)
+    z = lib.precond_apply(m, b, lib.params(precision=prec, cg_tol=1e-12, prec_self_weight=kappa))
+    assert rel(z, O.precond_apply(V, F, b, self_weight=kappa)) <= (TOL32 if prec == 0 else 1e-9)
 
 
 def test_precond_step_matches_exact_saddle_solution(lib):
@@ -322,6 +325,23 @@ def test_torus20k_apply_sampled(lib, torus, op):
     idx = np.random.default_rng(203).choice(len(V), 48, replace=False)
     ref = O.apply_operator_at_vertices(V, F, u, op, idx)
     assert rel(y[idx], ref) <= TOL32
+
+
+def test_torus20k_step_krylov_converges(lib, torus):
+    # the benchmark's step: with the within-face term in the preconditioner,
+    # FGMRES meets krylov_tol = 1e-5 well inside its 60-iteration budget on
+    # the rough torus (without it the budget runs out)
+    import torch
+    V, F, m = torus
+    A0, V0 = O.total_area(V, F), O.total_volume(V, F)
+    c = lib.tp_constraints(flags=3, A0=A0, V0=V0)
+    with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as mm:
+        rep = lib.precond_step(mm, c, lib.params(krylov_tol=1e-5, krylov_max=60, cg_tol=1e-6))
+        rep0 = lib.precond_step(mm, c, lib.params(krylov_tol=1e-5, krylov_max=60, cg_tol=1e-6,
+                                                  prec_self_weight=0.0))
+    assert rep["status"] == 0 and rep["krylov_iters"] < 60
+    assert rep["slope"] < 0 and rep["E_after"] < rep["E_before"]
+    assert rep0["status"] == lib.TP_ERR_NOT_CONVERGED
 
 
 def test_autograd_energy_backward_is_differential(lib, meshes):
