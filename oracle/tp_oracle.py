@@ -348,23 +348,45 @@ def cotan_laplacian(f, faces):
     return (off + sp.diags(diag)).tocsr()
 
 
-def project_mean_zero(b):
+def mesh_components(nv, faces):
+    """Connected component of every vertex (through the face edges)."""
+    from scipy.sparse.csgraph import connected_components
+    I = np.concatenate([faces[:, 0], faces[:, 1], faces[:, 2]])
+    J = np.concatenate([faces[:, 1], faces[:, 2], faces[:, 0]])
+    adj = sp.csr_matrix((np.ones(len(I)), (I, J)), shape=(nv, nv))
+    return connected_components(adj, directed=False)[1]
+
+
+def project_mean_zero(b, comp=None):
     """Remove the constant component of each column (the nullspace of C and
-    of the fractional operators)."""
-    return b - b.mean(axis=0, keepdims=True)
+    of the fractional operators); with `comp` (component labels) the mean
+    of each connected component separately (the nullspace of C)."""
+    if comp is None:
+        return b - b.mean(axis=0, keepdims=True)
+    out = b.copy()
+    for c in np.unique(comp):
+        sel = comp == c
+        out[sel] -= out[sel].mean(axis=0, keepdims=True)
+    return out
 
 
-def poisson_solve(C, b):
+def poisson_solve(C, b, comp=None):
     """Solve C z = b in the mean-zero subspace (exact sparse direct solve:
     the system with the first vertex's row and column removed, then the
-    mean removed). b [nv,k]."""
-    b = project_mean_zero(b)
-    Cr = C[1:, 1:].tocsc()
+    mean removed); with `comp`, per connected component (one vertex of each
+    component removed, means per component). b [nv,k]."""
+    nv = C.shape[0]
+    if comp is None:
+        comp = np.zeros(nv, dtype=np.int64)
+    b = project_mean_zero(b, comp)
+    drop = np.array([np.nonzero(comp == c)[0][0] for c in np.unique(comp)])
+    keep = np.setdiff1d(np.arange(nv), drop)
+    Cr = C[keep][:, keep].tocsc()
     z = np.zeros_like(b)
     lu = spla.splu(Cr)
     for c in range(b.shape[1]):
-        z[1:, c] = lu.solve(b[1:, c])
-    return project_mean_zero(z)
+        z[keep, c] = lu.solve(b[keep, c])
+    return project_mean_zero(z, comp)
 
 
 def pinned_poisson_solve(C, b, pins):
@@ -420,6 +442,7 @@ def precond_apply(f, faces, b, p=6.0, pins=None, self_weight=PREC_SELF_WEIGHT):
     Laplacian solves (pinned_poisson_solve) and nothing is projected: the
     pins remove the nullspace."""
     C = cotan_laplacian(f, faces)
+    comp = mesh_components(len(f), faces)
     sigma = 2.0 - sobolev_s(p)
     G = self_term_stiffness(f, faces, sigma, self_weight) if self_weight else None
 
@@ -430,9 +453,9 @@ def precond_apply(f, faces, b, p=6.0, pins=None, self_weight=PREC_SELF_WEIGHT):
     if pins is not None and len(pins):
         z = pinned_poisson_solve(C, b, pins)
         return pinned_poisson_solve(C, middle(z), pins)
-    z = poisson_solve(C, b)
-    z = project_mean_zero(middle(z))
-    return poisson_solve(C, z)
+    z = poisson_solve(C, b, comp)
+    z = project_mean_zero(middle(z), comp)
+    return poisson_solve(C, z, comp)
 
 
 # ---------------------------------------------------------------------------
@@ -484,12 +507,19 @@ def _constraint_rows(f, faces, use_area, use_volume):
     return np.array(rows)
 
 
-def _barycenter_rows(nv):
+def _barycenter_rows(nv, comp=None):
     """Jacobian of the fixed-barycenter constraint read as |V| copies of I_3
-    (§7.1.1), one row per coordinate, in the [nv,3] row-major ordering."""
-    J = np.zeros((3, 3 * nv))
-    for c in range(3):
-        J[c, c::3] = 1.0
+    (§7.1.1), one row per coordinate, in the [nv,3] row-major ordering; with
+    several components, one barycenter per component (3 rows each, copies of
+    I_3 over that component's vertices)."""
+    if comp is None:
+        comp = np.zeros(nv, dtype=np.int64)
+    labels = np.unique(comp)
+    J = np.zeros((3 * len(labels), 3 * nv))
+    for k, lab in enumerate(labels):
+        vs = np.nonzero(comp == lab)[0]
+        for c in range(3):
+            J[3 * k + c, 3 * vs + c] = 1.0
     return J
 
 
@@ -503,13 +533,13 @@ def _pin_rows(nv, pins):
     return J
 
 
-def _positional_rows(nv, pins):
-    """The linear positional rows of the step: the barycenter rows, or the
-    pin rows when pins are given (a pin removes the nullspace, so the
-    barycenter constraint is then not needed, §7.1.2)."""
+def _positional_rows(nv, pins, comp=None):
+    """The linear positional rows of the step: the barycenter rows (per
+    component), or the pin rows when pins are given (a pin removes the
+    nullspace, so the barycenter constraint is then not needed, §7.1.2)."""
     if pins is not None and len(pins):
         return _pin_rows(nv, pins)
-    return _barycenter_rows(nv)
+    return _barycenter_rows(nv, comp)
 
 
 def saddle_matrix(f, faces, use_area=True, use_volume=True, p=6.0, pins=None):
@@ -519,7 +549,7 @@ def saddle_matrix(f, faces, use_area=True, use_volume=True, p=6.0, pins=None):
     nv = len(f)
     A = operator_matrix(f, faces, "A", p)
     A3 = np.kron(A, np.eye(3))
-    J = np.concatenate([_positional_rows(nv, pins),
+    J = np.concatenate([_positional_rows(nv, pins, mesh_components(nv, faces)),
                         _constraint_rows(f, faces, use_area, use_volume)], axis=0)
     m = J.shape[0]
     M = np.zeros((3 * nv + m, 3 * nv + m))
@@ -561,8 +591,8 @@ def descent_direction(f, faces, use_area=True, use_volume=True, p=6.0, obstacle=
 
 def schur_direction(f, faces, use_area=True, use_volume=True, p=6.0, pins=None):
     """The same direction via the Schur complement of §5.3 (Eq. 17, Eq. 18)
-    with A_3^{-1} applied in the mean-zero subspace (where the barycenter
-    rows are satisfied), g = dE, Z = A_3^{-1} dPhi^T:
+    with A_3^{-1} applied in the subspace of zero mean per component (where
+    the barycenter rows are satisfied), g = dE, Z = A_3^{-1} dPhi^T:
         x = -(A^{-1} g - Z (dPhi Z)^{-1} dPhi A^{-1} g).
     With pins, the pin rows stay in the matrix (§7.2): A_3^{-1} is the solve
     of the pinned saddle system, i.e. A restricted to the free vertices with
@@ -580,9 +610,13 @@ def schur_direction(f, faces, use_area=True, use_volume=True, p=6.0, pins=None):
             out[free] = AFFi @ w.reshape(nv, 3)[free]
             return out.reshape(-1)
     else:
-        P = np.eye(nv) - np.full((nv, nv), 1.0 / nv)
-        Ainv = np.linalg.pinv(P @ A @ P)
-        Ainv3 = lambda w: (Ainv @ project_mean_zero(w.reshape(nv, 3))).reshape(-1)
+        # inverse on the subspace of zero mean per component: P A P plus the
+        # projector onto the constants is invertible and maps that subspace
+        # to itself
+        comp = mesh_components(nv, faces)
+        P = project_mean_zero(np.eye(nv), comp)
+        Ainv = np.linalg.inv(P @ A @ P + (np.eye(nv) - P))
+        Ainv3 = lambda w: project_mean_zero(Ainv @ project_mean_zero(w.reshape(nv, 3), comp), comp).reshape(-1)
     J = _constraint_rows(f, faces, use_area, use_volume)
     Ag = Ainv3(g.reshape(-1))
     Z = np.stack([Ainv3(row) for row in J], axis=1)
@@ -628,7 +662,7 @@ def precond_step(f, faces, A0, V0, use_area=True, use_volume=True, p=6.0,
             tau *= shrink
     f1 = f + tau * x
     M, J = saddle_matrix(f, faces, use_area, use_volume, p, pins)
-    npos = _positional_rows(nv, pins).shape[0]
+    npos = _positional_rows(nv, pins, mesh_components(nv, faces)).shape[0]
     f2 = f1
     h = np.zeros_like(f)
     for _ in range(proj_iters):
