@@ -136,7 +136,7 @@ typedef struct tp_mesh tp_mesh;
 /* Fill *p with the defaults: p=6, theta=0, leaf_size=8, FP32 pairs,
  * full BH differential, krylov_tol=1e-6, krylov_max=200, restart 30,
  * cg_tol=1e-6, cg_max=20000, Armijo c=1e-4, shrink 0.5, tau0=1, ls_max=30,
- * proj_iters=1, Cholesky Poisson solver, prec_self_weight=8. */
+ * proj_iters=1, Cholesky Poisson solver, prec_self_weight=24. *
 void tp_params_default(tp_params* p);
 
 /* Create a mesh on CUDA device `device` from nv positions and nf faces.
@@ -231,7 +231,7 @@ int cotan_factor_info(tp_mesh* m, tp_chol_info* out);
  * G is the within-face part of the L^{2-s} double integral that the pair
  * sums of §5.1.1 leave out (pairs of points inside one face): for
  * piecewise-linear functions it is the P1 stiffness matrix with face
- * weights kappa a_S^{1-(2-s)}, kappa = prec_self_weight (default 8; 0 gives
+ * weights kappa a_S^{1-(2-s)}, kappa = prec_self_weight (default 24; 0 gives
  * the paper's C^+ L^{2-s} C^+). It makes the preconditioned operator's
  * spectrum mesh-independent and narrow; it does not change the solutions
  * of the Krylov solves. With pins set, both Laplacian solves are pinned. */

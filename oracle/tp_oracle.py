@@ -407,7 +407,7 @@ def pinned_poisson_solve(C, b, pins):
     return z
 
 
-PREC_SELF_WEIGHT = 8.0
+PREC_SELF_WEIGHT = 24.0
 
 
 def self_term_stiffness(f, faces, sigma, kappa):

@@ -93,7 +93,7 @@ void tp_params_default(tp_params* p) {
     p->proj_iters = 1;
     p->poisson_solver = TP_POISSON_CHOLESKY;
     p->bvh_refit = 0;
-    p->prec_self_weight = 8.0;
+    p->prec_self_weight = 24.0;
 }
 
 const char* tp_last_error(void) { return tp::last_error(); }
@@ -156,6 +156,7 @@ int tp_mesh_create(int device, int nv, int nf, const double* pos, const int32_t*
         cudaMemcpy(m->vf_ptr.ptr, vptr.data(), sizeof(int) * (nv + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(m->vf_idx.ptr, vidx.data(), sizeof(int) * 3 * (size_t)nf, cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(fail(TP_ERR_CUDA, "copying the topology failed"));
+    if ((s = components_setup(m, F))) return bail(s);
     if ((s = laplacian_setup(m))) return bail(s);
     if ((s = copy_in(m->pos.ptr, pos, sizeof(double) * 3 * (size_t)nv, ptr_kind, st))) return bail(s);
     if ((s = refresh_geometry(m, st))) return bail(s);
@@ -186,7 +187,7 @@ int tp_mesh_get_positions(tp_mesh* m, double* pos, int ptr_kind, void* stream) {
 int tp_mesh_destroy(tp_mesh* m) {
     if (!m) return TP_OK;
     DeviceGuard g(m->device);
-    Buf* all[] = {&m->faces, &m->vf_ptr, &m->vf_idx, &m->pos, &m->center, &m->errflag, &m->f32a, &m->f32b,
+    Buf* all[] = {&m->faces, &m->vf_ptr, &m->vf_idx, &m->vcomp, &m->comp_ptr, &m->comp_verts, &m->pos, &m->center, &m->errflag, &m->f32a, &m->f32b,
                   &m->f32c, &m->tilebox,
                   &m->f64a, &m->f64b, &m->fgrad, &m->rowptr, &m->col, &m->cotsrc, &m->diagpos, &m->val,
                   &m->dinv, &m->val32, &m->gval, &m->bvh_node, &m->bvh_perm, &m->bvh_keys, &m->bvh_tmp, &m->bvh_sortws,

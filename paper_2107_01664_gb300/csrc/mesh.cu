@@ -255,6 +255,83 @@ __global__ void k_tile_boxes(const float4* __restrict__ f32a, int nf, float4* __
     }
 }
 
+// connected components by union-find over the face edges, labelled in
+// order of their smallest vertex
+int components_setup(tp_mesh* m, const std::vector<int>& F) {
+    const int nv = m->nv;
+    std::vector<int> parent(nv);
+    for (int v = 0; v < nv; ++v) parent[v] = v;
+    auto find = [&](int x) {
+        while (parent[x] != x) {
+            parent[x] = parent[parent[x]];
+            x = parent[x];
+        }
+        return x;
+    };
+    for (size_t e = 0; e + 2 < F.size(); e += 3)
+        for (int c = 0; c < 3; ++c) {
+            const int a = find(F[e + c]), b = find(F[e + (c + 1) % 3]);
+            if (a != b) parent[a > b ? a : b] = a < b ? a : b;
+        }
+    std::vector<int> label(nv, -1);
+    m->comp_host.assign(nv, 0);
+    int nc = 0;
+    for (int v = 0; v < nv; ++v) {
+        const int r = find(v);
+        if (label[r] < 0) label[r] = nc++;
+        m->comp_host[v] = label[r];
+    }
+    m->ncomp = nc;
+    std::vector<int> ptr(nc + 1, 0), verts(nv);
+    for (int v = 0; v < nv; ++v) ptr[m->comp_host[v] + 1]++;
+    for (int c = 0; c < nc; ++c) ptr[c + 1] += ptr[c];
+    {
+        std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+        for (int v = 0; v < nv; ++v) verts[fill[m->comp_host[v]]++] = v;
+    }
+    TP_TRY(ensure(m->vcomp, sizeof(int) * (size_t)nv));
+    TP_TRY(ensure(m->comp_ptr, sizeof(int) * (size_t)(nc + 1)));
+    TP_TRY(ensure(m->comp_verts, sizeof(int) * (size_t)nv));
+    TP_CUDA(cudaMemcpy(m->vcomp.ptr, m->comp_host.data(), sizeof(int) * (size_t)nv, cudaMemcpyHostToDevice));
+    TP_CUDA(cudaMemcpy(m->comp_ptr.ptr, ptr.data(), sizeof(int) * (size_t)(nc + 1), cudaMemcpyHostToDevice));
+    TP_CUDA(cudaMemcpy(m->comp_verts.ptr, verts.data(), sizeof(int) * (size_t)nv, cudaMemcpyHostToDevice));
+    return TP_OK;
+}
+
+// mean[c][j] of column j over component c (one block per (c, j), fixed order)
+__global__ void k_comp_mean(const int* __restrict__ ptr, const int* __restrict__ verts, const double* __restrict__ x,
+                            int k, double* __restrict__ mean) {
+    const int c = blockIdx.x, j = blockIdx.y;
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int e = ptr[c] + threadIdx.x; e < ptr[c + 1]; e += blockDim.x) s += x[(size_t)verts[e] * k + j];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) mean[(size_t)c * k + j] = red[0] / (double)(ptr[c + 1] - ptr[c]);
+}
+
+__global__ void k_comp_remove(const int* __restrict__ vcomp, int nv, int k, const double* __restrict__ mean,
+                              double* __restrict__ x) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)nv * k) return;
+    x[i] -= mean[(size_t)vcomp[i / k] * k + (i % k)];
+}
+
+int project_components(tp_mesh* m, double* x, int k, cudaStream_t st) {
+    TP_TRY(ensure(m->part2, sizeof(double) * (size_t)m->ncomp * k));
+    double* mean = m->part2.as<double>();
+    k_comp_mean<<<dim3(m->ncomp, k), 256, 0, st>>>(m->comp_ptr.as<int>(), m->comp_verts.as<int>(), x, k, mean);
+    TP_LAUNCH_CHECK();
+    const size_t n = (size_t)m->nv * k;
+    k_comp_remove<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m->vcomp.as<int>(), m->nv, k, mean, x);
+    TP_LAUNCH_CHECK();
+    return TP_OK;
+}
+
 int refresh_geometry(tp_mesh* m, cudaStream_t st) {
     // reference frame: centre of the vertices' bounding box (exact in FP64),
     // so that the FP32 face table holds barycenters relative to the mesh

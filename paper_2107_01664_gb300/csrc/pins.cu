@@ -200,31 +200,9 @@ int pins_set(tp_mesh* m, int n, const int* idx_host, cudaStream_t st) {
         if (sorted[i] < 0 || sorted[i] >= m->nv) return fail(TP_ERR_INVALID_ARG, "pins: vertex index out of range");
         if (i > 0 && sorted[i] == sorted[i - 1]) return fail(TP_ERR_INVALID_ARG, "pins: repeated vertex");
     }
-    // connected components of the mesh (union-find over the face edges)
-    std::vector<int> F(3 * (size_t)m->nf);
-    TP_CUDA(cudaMemcpyAsync(F.data(), m->faces.ptr, sizeof(int) * F.size(), cudaMemcpyDeviceToHost, st));
-    TP_CUDA(cudaStreamSynchronize(st));
-    std::vector<int> parent(m->nv);
-    std::iota(parent.begin(), parent.end(), 0);
-    auto find = [&](int x) {
-        while (parent[x] != x) {
-            parent[x] = parent[parent[x]];
-            x = parent[x];
-        }
-        return x;
-    };
-    for (size_t e = 0; e < F.size(); e += 3)
-        for (int c = 0; c < 3; ++c) {
-            const int a = find(F[e + c]), b = find(F[e + (c + 1) % 3]);
-            if (a != b) parent[std::max(a, b)] = std::min(a, b);
-        }
-    std::vector<int> label(m->nv, -1), comp(m->nv);
-    int nc = 0;
-    for (int v = 0; v < m->nv; ++v) {
-        const int r = find(v);
-        if (label[r] < 0) label[r] = nc++;
-        comp[v] = label[r];
-    }
+    // connected components of the mesh (computed at creation)
+    const std::vector<int>& comp = m->comp_host;
+    const int nc = m->ncomp;
     std::vector<int> has(nc, 0), pin_comp(n);
     for (int i = 0; i < n; ++i) {
         pin_comp[i] = comp[pins[i]];
@@ -287,10 +265,11 @@ int pinned_solve(tp_mesh* m, const tp_params* p, const double* b, int k, double*
     return s;
 }
 
-// zero the pinned rows (pins) or remove the mean (no pins): the subspace the
-// step's vectors live in
+// zero the pinned rows (pins) or remove the mean of each connected component
+// (no pins: one barycenter per component, §7.1.1): the subspace the step's
+// vectors live in
 int project_space(tp_mesh* m, double* x, int k, cudaStream_t st) {
-    if (m->npins == 0) return project_mean_zero(m, x, k, st);
+    if (m->npins == 0) return m->ncomp == 1 ? project_mean_zero(m, x, k, st) : project_components(m, x, k, st);
     const int cnt = m->npins * k;
     k_zero_rows<<<(cnt + 255) / 256, 256, 0, st>>>(m->pin_idx.as<int>(), m->npins, k, x);
     TP_LAUNCH_CHECK();

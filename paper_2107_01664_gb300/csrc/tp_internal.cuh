@@ -137,6 +137,12 @@ struct tp_mesh {
     tp::Buf faces;      // int32 [nf*3]
     tp::Buf vf_ptr;     // int32 [nv+1]  vertex -> incident (face*3+corner)
     tp::Buf vf_idx;     // int32 [3*nf]
+    // connected components (through the face edges): one barycenter each (§7.1.1)
+    int ncomp = 1;
+    std::vector<int> comp_host;   // component of each vertex
+    tp::Buf vcomp;      // int32 [nv]        component of each vertex
+    tp::Buf comp_ptr;   // int32 [ncomp+1]   vertices of component c: comp_verts[comp_ptr[c] .. comp_ptr[c+1])
+    tp::Buf comp_verts; // int32 [nv]
     // positions
     tp::Buf pos;        // double [nv*3]
     tp::Buf center;     // double [4]    reference frame of the FP32 face table; [3] = near-pair distance^2
@@ -194,6 +200,9 @@ namespace tp {
 
 // -------- mesh.cu ----------------------------------------------------------
 int refresh_geometry(tp_mesh* m, cudaStream_t st);   // face tables from m->pos
+int components_setup(tp_mesh* m, const std::vector<int>& faces_host);   // at creation
+// remove the mean of each connected component from each column of x [nv][k]
+int project_components(tp_mesh* m, double* x_dev, int k, cudaStream_t st);
 int corners_to_vertices(tp_mesh* m, const double* corner, int k, double* y, cudaStream_t st);
 int copy_in(void* dst, const void* src, size_t bytes, int ptr_kind, cudaStream_t st);
 int copy_out(void* dst, const void* src, size_t bytes, int ptr_kind, cudaStream_t st);
@@ -288,7 +297,7 @@ void pins_release(tp_mesh* m);
 // from the inner solve is passed on with z filled
 int pinned_solve(tp_mesh* m, const tp_params* p, const double* b_dev, int k, double* z_dev,
                  cudaStream_t st, int* iters);
-// zero the pinned rows (pins set) or remove the mean (no pins)
+// zero the pinned rows (pins set) or remove the mean of each component (no pins)
 int project_space(tp_mesh* m, double* x_dev, int k, cudaStream_t st);
 
 // -------- solver.cu --------------------------------------------------------

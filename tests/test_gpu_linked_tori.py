@@ -70,3 +70,22 @@ def test_gradient_matches_oracle_at_sampled_vertices(lib, tori):
     g, _ = lib.tp_differential(m, lib.params())
     idx = np.random.default_rng(3).choice(len(V), 24, replace=False)
     assert rel(g[idx], O.differential_at_vertices(V, F, idx)) <= 1e-5
+
+
+def test_constrained_step_converges_with_one_barycenter_per_torus(lib):
+    # one barycenter per component: the Krylov space (per-component mean-zero
+    # preconditioner outputs) contains the solution, so FGMRES converges on
+    # the two tori; each torus keeps its barycenter
+    import torch
+    V, F = workload("linked_tori_50k")
+    A0, V0 = O.total_area(V, F), O.total_volume(V, F)
+    comp = O.mesh_components(len(V), F)
+    with lib.Mesh(torch.tensor(V, dtype=torch.float64, device="cuda"),
+                  torch.tensor(F, dtype=torch.int32, device="cuda")) as m:
+        c = lib.tp_constraints(flags=3, A0=A0, V0=V0)
+        rep = lib.precond_step(m, c, lib.params(theta=0.5, krylov_tol=1e-5, krylov_max=60, cg_tol=1e-6))
+        f = m.get_positions()
+    assert rep["status"] == 0 and rep["slope"] < 0 and rep["E_after"] < rep["E_before"]
+    for lab in np.unique(comp):
+        sel = comp == lab
+        assert np.abs(f[sel].mean(axis=0) - V[sel].mean(axis=0)).max() < 1e-6
