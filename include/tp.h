@@ -136,7 +136,7 @@ typedef struct tp_mesh tp_mesh;
 /* Fill *p with the defaults: p=6, theta=0, leaf_size=8, FP32 pairs,
  * full BH differential, krylov_tol=1e-6, krylov_max=200, restart 30,
  * cg_tol=1e-6, cg_max=20000, Armijo c=1e-4, shrink 0.5, tau0=1, ls_max=30,
- * proj_iters=1, Cholesky Poisson solver, prec_self_weight=24. *
+ * proj_iters=1, Cholesky Poisson solver, prec_self_weight=24. */
 void tp_params_default(tp_params* p);
 
 /* Create a mesh on CUDA device `device` from nv positions and nf faces.
