@@ -542,12 +542,15 @@ def _positional_rows(nv, pins, comp=None):
     return _barycenter_rows(nv, comp)
 
 
-def saddle_matrix(f, faces, use_area=True, use_volume=True, p=6.0, pins=None):
+def saddle_matrix(f, faces, use_area=True, use_volume=True, p=6.0, pins=None, willmore=0.0):
     """[A_3 dPhi^T; dPhi 0] of Eq. 14 with the barycenter rows (§7.1.1), or
     the vertex pin rows (§7.1.2, included in the matrix as in §7.2), plus
-    area and volume rows; A_3 = A (x) I_3 on the [nv,3] ordering."""
+    area and volume rows; A_3 = A (x) I_3 on the [nv,3] ordering. With a
+    Willmore weight w, w C M^{-1} C is added to A (the H^2 term of §7.3.5)."""
     nv = len(f)
     A = operator_matrix(f, faces, "A", p)
+    if willmore:
+        A = A + willmore * willmore_metric(f, faces)
     A3 = np.kron(A, np.eye(3))
     J = np.concatenate([_positional_rows(nv, pins, mesh_components(nv, faces)),
                         _constraint_rows(f, faces, use_area, use_volume)], axis=0)
@@ -559,30 +562,36 @@ def saddle_matrix(f, faces, use_area=True, use_volume=True, p=6.0, pins=None):
     return M, J
 
 
-def _total_energy(f, faces, p, obstacle):
+def _total_energy(f, faces, p, obstacle, willmore=0.0):
     """E of Eq. 10 plus, when `obstacle` = (f_O, faces_O, weight) is given,
-    the static-obstacle term of §7.3.2 (obstacle_energy)."""
+    the static-obstacle term of §7.3.2 (obstacle_energy), plus willmore
+    times the Willmore energy of §7.3.5."""
     E = energy(f, faces, p)
     if obstacle is not None:
         E += obstacle_energy(f, faces, obstacle[0], obstacle[1], p, obstacle[2])
+    if willmore:
+        E += willmore * willmore_energy(f, faces)
     return E
 
 
-def _total_differential(f, faces, p, obstacle):
+def _total_differential(f, faces, p, obstacle, willmore=0.0):
     g = differential(f, faces, p)
     if obstacle is not None:
         g = g + obstacle_differential(f, faces, obstacle[0], obstacle[1], p, obstacle[2])
+    if willmore:
+        g = g + willmore * willmore_differential(f, faces)
     return g
 
 
-def descent_direction(f, faces, use_area=True, use_volume=True, p=6.0, obstacle=None, pins=None):
+def descent_direction(f, faces, use_area=True, use_volume=True, p=6.0, obstacle=None, pins=None,
+                      willmore=0.0):
     """x of Eq. 14: [A_3 dPhi^T; dPhi 0][x; lambda] = [-dE; 0], solved
     densely. Returns (x [nv,3], g = dE [nv,3]). With an obstacle (see
     _total_energy) dE is the differential of the sum: the obstacle term is
     one more energy in the flow, the metric A is unchanged."""
     nv = len(f)
-    g = _total_differential(f, faces, p, obstacle)
-    M, J = saddle_matrix(f, faces, use_area, use_volume, p, pins)
+    g = _total_differential(f, faces, p, obstacle, willmore)
+    M, J = saddle_matrix(f, faces, use_area, use_volume, p, pins, willmore)
     rhs = np.zeros(M.shape[0])
     rhs[:3 * nv] = -g.reshape(-1)
     sol = np.linalg.solve(M, rhs)
@@ -636,7 +645,7 @@ def constraint_values(f, faces, A0, V0, use_area=True, use_volume=True):
 
 def precond_step(f, faces, A0, V0, use_area=True, use_volume=True, p=6.0,
                  tau0=1.0, armijo_c=1e-4, shrink=0.5, ls_max=30, fixed_tau=None, proj_iters=1,
-                 obstacle=None, pins=None):
+                 obstacle=None, pins=None, willmore=0.0):
     """One constrained descent step (§3, steps 1-5; §5.4 with exact solves):
     direction by Eq. 14, Armijo backtracking from tau0 (E(f + tau x) <=
     E(f) + c tau dE.x), then corrective projections by Eq. 15 with the
@@ -646,22 +655,23 @@ def precond_step(f, faces, A0, V0, use_area=True, use_volume=True, p=6.0,
     static-obstacle term of §7.3.2. With `pins` (vertex indices) the pin rows
     replace the barycenter rows; the pinned positions f_0 are those of f, so
     Phi_P = 0 at the start and every row of the projection's right-hand side
-    for a pin is 0.
+    for a pin is 0. With a Willmore weight w the energy gains w E_W and the
+    matrix w C M^{-1} C (§7.3.5).
     Returns dict(f_new, x, tau, E0, E1, h)."""
     nv = len(f)
-    x, g = descent_direction(f, faces, use_area, use_volume, p, obstacle, pins)
-    E0 = _total_energy(f, faces, p, obstacle)
+    x, g = descent_direction(f, faces, use_area, use_volume, p, obstacle, pins, willmore)
+    E0 = _total_energy(f, faces, p, obstacle, willmore)
     slope = float(np.sum(g * x))
     if fixed_tau is not None:
         tau = fixed_tau
     else:
         tau = tau0
         for _ in range(ls_max):
-            if _total_energy(f + tau * x, faces, p, obstacle) <= E0 + armijo_c * tau * slope:
+            if _total_energy(f + tau * x, faces, p, obstacle, willmore) <= E0 + armijo_c * tau * slope:
                 break
             tau *= shrink
     f1 = f + tau * x
-    M, J = saddle_matrix(f, faces, use_area, use_volume, p, pins)
+    M, J = saddle_matrix(f, faces, use_area, use_volume, p, pins, willmore)
     npos = _positional_rows(nv, pins, mesh_components(nv, faces)).shape[0]
     f2 = f1
     h = np.zeros_like(f)
@@ -673,7 +683,7 @@ def precond_step(f, faces, A0, V0, use_area=True, use_volume=True, p=6.0,
         dh = np.linalg.solve(M, rhs)[:3 * nv].reshape(nv, 3)
         f2 = f2 + dh
         h = h + dh
-    return dict(f_new=f2, x=x, tau=tau, E0=E0, E1=_total_energy(f2, faces, p, obstacle), h=h,
+    return dict(f_new=f2, x=x, tau=tau, E0=E0, E1=_total_energy(f2, faces, p, obstacle, willmore), h=h,
                 slope=slope)
 
 
@@ -1177,3 +1187,69 @@ def bh_obstacle_energy(f, faces, fO, facesO, theta, leaf=8, p=6.0, weight=1.0):
     for c in range(3):
         np.add.at(dE, faces[:, c], corner[:, c])
     return float(np.sum(weight * a * phi)), dE, count
+
+
+# ---------------------------------------------------------------------------
+# §7.3.5 Willmore energy and its H^2 inner product term
+# ---------------------------------------------------------------------------
+
+def lumped_mass(f, faces):
+    """Lumped mass of every vertex: a third of the area of each face around
+    it (the diagonal mass matrix M of §7.3.5)."""
+    a = face_geometry(f, faces)[2]
+    m = np.zeros(len(f))
+    for c in range(3):
+        np.add.at(m, faces[:, c], a / 3.0)
+    return m
+
+
+def willmore_energy(f, faces):
+    """E_W = f^T C M^{-1} C f (§7.3.5, summed over the three coordinate
+    columns of f), C the cotan stiffness matrix, M the lumped mass."""
+    C = cotan_laplacian(f, faces)
+    h = C @ f
+    return float(np.sum(h * h / lumped_mass(f, faces)[:, None]))
+
+
+def willmore_differential(f, faces):
+    """dE_W/df, shape [nv,3]. With h = C f, m the lumped mass, g = 2 h / m:
+        dE_W = g . (C df) + g . (dC f) - sum_i |h_i|^2 / m_i^2 dm_i,
+    the first term is C g (C symmetric); in the second, corner k of face S
+    opposite the edge (i, j) adds cot(theta_k)/2 (f_i - f_j) to h_i (and the
+    opposite to h_j), so it contributes (g_i - g_j).(f_i - f_j)/2 times
+    d cot(theta_k); in the third, m_i gains a_S/3 from each face S around i,
+    and da_S is the area gradient of §7.1.3."""
+    nv = len(f)
+    C = cotan_laplacian(f, faces)
+    m = lumped_mass(f, faces)
+    h = C @ f
+    g = 2.0 * h / m[:, None]
+    out = C @ g
+    q = np.sum(h * h, axis=1) / (m * m)
+    X, N, a = face_geometry(f, faces)
+    for c in range(3):
+        k, i, j = faces[:, c], faces[:, (c + 1) % 3], faces[:, (c + 2) % 3]
+        u, v = f[i] - f[k], f[j] - f[k]
+        w = np.cross(u, v)
+        s = np.linalg.norm(w, axis=1)
+        nhat = w / s[:, None]
+        cot = np.sum(u * v, axis=1) / s
+        # d cot / du, d cot / dv (u, v the edges from corner k)
+        dcu = v / s[:, None] - (cot / s)[:, None] * np.cross(v, nhat)
+        dcv = u / s[:, None] - (cot / s)[:, None] * np.cross(nhat, u)
+        coef = 0.5 * np.sum((g[i] - g[j]) * (f[i] - f[j]), axis=1)
+        np.add.at(out, i, coef[:, None] * dcu)
+        np.add.at(out, j, coef[:, None] * dcv)
+        np.add.at(out, k, -coef[:, None] * (dcu + dcv))
+    # mass term: dm_i = sum_S da_S / 3
+    fi, fj, fk = f[faces[:, 0]], f[faces[:, 1]], f[faces[:, 2]]
+    qS = (q[faces[:, 0]] + q[faces[:, 1]] + q[faces[:, 2]]) / 3.0
+    for c, e in enumerate((fk - fj, fi - fk, fj - fi)):
+        np.add.at(out, faces[:, c], -qS[:, None] * 0.5 * np.cross(N, e))
+    return out
+
+
+def willmore_metric(f, faces):
+    """The H^2 inner product term C M^{-1} C of §7.3.5 (dense, per coordinate)."""
+    C = cotan_laplacian(f, faces).toarray()
+    return C @ (C / lumped_mass(f, faces)[:, None])
