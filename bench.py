@@ -366,6 +366,47 @@ def pinned_steps(tp, dev, steps=2):
     return out
 
 
+def willmore_steps(tp, dev, steps=2, weight=100.0):
+    """Willmore term (§7.3.5) on torus_20k: device time of E_W + dE_W, and
+    constrained steps minimising E + w E_W with the H^2 term in the operator
+    (w = 100 makes w E_W about a sixth of E on this mesh)."""
+    import numpy as np
+    import torch
+    from synth import workload
+    V, F = workload(WORKLOAD)
+    A0 = float(np.sum(0.5 * np.linalg.norm(np.cross(V[F[:, 1]] - V[F[:, 0]], V[F[:, 2]] - V[F[:, 0]]), axis=1)))
+    Vol0 = float(np.sum(V[F[:, 0]] * np.cross(V[F[:, 1]], V[F[:, 2]])) / 6.0)
+    cons = tp.tp_constraints(flags=tp.TP_CONSTRAINT_AREA | tp.TP_CONSTRAINT_VOLUME, A0=A0, V0=Vol0)
+    f0 = torch.tensor(V, dtype=torch.float64, device=dev)
+    mesh = tp.Mesh(f0, torch.tensor(F, dtype=torch.int32, device=dev), device=dev.index or 0)
+    dE = torch.empty((len(V), 3), dtype=torch.float64, device=dev)
+    EW, _ = tp.tp_willmore_energy(mesh, like=dE)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(10):
+        tp.tp_willmore_energy(mesh, like=dE)
+    e1.record()
+    torch.cuda.synchronize()
+    ew_ms = e0.elapsed_time(e1) / 10
+    tp.tp_willmore_set(mesh, weight)
+    ps = step_params(tp)
+    tp.precond_step(mesh, cons, ps)
+    reps = []
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(steps):
+        tp.tp_mesh_set_positions(mesh, f0)
+        reps.append(tp.precond_step(mesh, cons, ps))
+    e1.record()
+    torch.cuda.synchronize()
+    mesh.close()
+    return {"workload": "torus_20k", "weight": weight, "E_W": EW, "E_W_and_dE_W_ms": ew_ms,
+            "ms_per_step": e0.elapsed_time(e1) / steps,
+            "krylov_iters_per_step": sum(r["krylov_iters"] for r in reps) / steps,
+            "E_before": reps[0]["E_before"], "E_after": reps[0]["E_after"], "status": [r["status"] for r in reps]}
+
+
 def bh_step(tp, dev, steps=2):
     """Constrained steps with every pair sum on the tree (theta = 0.5: energy,
     differential, and the A and L^{2-s} applies of the Krylov loop) on the
@@ -616,6 +657,7 @@ def gpu_arm(args):
         line["large_mesh_bh"] = large_bh(tp, dev)
         line["obstacle"] = obstacle_scene(tp, dev)
         line["pins"] = pinned_steps(tp, dev)
+        line["willmore"] = willmore_steps(tp, dev)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = run_cpu_sample()
     mesh.close()
@@ -746,6 +788,8 @@ def main():
                     help="run only the static-obstacle scene (torus_20k around a ball) instead")
     ap.add_argument("--pins", action="store_true",
                     help="run only the vertex-pin steps (torus_20k with 8 pins) instead")
+    ap.add_argument("--willmore", action="store_true",
+                    help="run only the Willmore steps (torus_20k, weight 100) instead")
     ap.add_argument("--serve-n", type=int, default=64)
     ap.add_argument("--serve-fmax", type=int, default=50000)
     ap.add_argument("--serve-slots", type=int, default=4)
@@ -767,6 +811,12 @@ def main():
         import paper_2107_01664_gb300 as tp
         torch.cuda.set_device(0)
         print(json.dumps({"pins": pinned_steps(tp, torch.device("cuda", 0))}))
+        return
+    if args.willmore:
+        import torch
+        import paper_2107_01664_gb300 as tp
+        torch.cuda.set_device(0)
+        print(json.dumps({"willmore": willmore_steps(tp, torch.device("cuda", 0))}))
         return
     if args.impl == "reference":
         reference_arm(args)

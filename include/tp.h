@@ -250,6 +250,21 @@ int precond_apply(tp_mesh* m, const tp_params* p, const double* b, int k,
  * vertex, or a connected component without a pin. Synchronises `stream`. */
 int tp_pins_set(tp_mesh* m, int n, const int32_t* vertices, int ptr_kind, void* stream);
 
+/* Willmore term of a mesh (§7.3.5): with weight w > 0, precond_step
+ * minimises E + w E_W, E_W = f^T C M^{-1} C f (C the cotan stiffness
+ * matrix, M the lumped mass: a third of the area of each face around a
+ * vertex, summed over the three coordinate columns of f), and adds the H^2
+ * term w C M^{-1} C to the operator it inverts (its report's energies are
+ * E + w E_W). w = 0 (the default) removes the term. TP_ERR_INVALID_ARG for a
+ * negative or non-finite weight. */
+int tp_willmore_set(tp_mesh* m, double weight);
+
+/* E_W (host, may be NULL) and dE_W/df (float64 [nv][3], may be NULL; not
+ * both NULL) of the current positions, whatever weight is set: FP64 sparse
+ * products on the pattern of C and per-face corner terms (derivatives of
+ * the cotangents and of the lumped mass). */
+int tp_willmore_energy(tp_mesh* m, double* E_out, double* dE, int ptr_kind, void* stream);
+
 /* One constrained descent step (§5.4): dE, the Schur-complement solution
  * of the saddle problem (Eq. 14, 17, 18) with GMRES on A_3 preconditioned
  * by precond_apply, Armijo line search, and proj_iters corrective

@@ -27,7 +27,8 @@ __all__ = [
     "fractional_apply", "cotan_solve", "precond_apply", "precond_step", "TangentPointEnergy",
     "lib_path", "lib", "tp_kernel_stat", "tp_profile_enable", "tp_profile_read", "tp_launch_count",
     "tp_energy_noalloc", "tp_chol_info", "cotan_factor_info", "TP_POISSON_CHOLESKY", "TP_POISSON_CG",
-    "tp_obstacle_set", "tp_obstacle_energy", "tp_pins_set", "TP_MAX_PINS",
+    "tp_obstacle_set", "tp_obstacle_energy", "tp_pins_set", "TP_MAX_PINS", "tp_willmore_set",
+    "tp_willmore_energy",
 ]
 
 TP_OK, TP_ERR_INVALID_ARG, TP_ERR_DEGENERATE, TP_ERR_OOM = 0, 1, 2, 3
@@ -126,6 +127,8 @@ def lib():
         "tp_energy_noalloc": (c_int, [vp, c_int, vp, c_int, c_double, vp, vp]),
         "tp_obstacle_set": (c_int, [vp, c_int, c_int, vp, vp, c_double, c_int, vp]),
         "tp_pins_set": (c_int, [vp, c_int, vp, c_int, vp]),
+        "tp_willmore_set": (c_int, [vp, c_double]),
+        "tp_willmore_energy": (c_int, [vp, P(c_double), vp, c_int, vp]),
         "tp_obstacle_energy": (c_int, [vp, P(tp_params), P(c_double), vp, c_int, vp]),
     }
     for name, (res, args) in sig.items():
@@ -339,6 +342,19 @@ def precond_step(mesh: Mesh, constraints: tp_constraints, p: tp_params | None = 
         "krylov_iters": rep.krylov_iters, "cg_iters": rep.cg_iters, "ls_trials": rep.ls_trials,
         "status": rep.status, "pair_interactions": rep.pair_interactions,
     }
+
+
+def tp_willmore_set(mesh: Mesh, weight: float):
+    """Weight of the Willmore term and its H^2 metric term in precond_step (§7.3.5)."""
+    _check(lib().tp_willmore_set(mesh.handle, float(weight)))
+
+
+def tp_willmore_energy(mesh: Mesh, like=None):
+    """(E_W, dE_W [nv,3]) of the current positions; dE_W in the memory kind of `like`."""
+    out, ptr, kind = _empty_like_kind(like, (mesh.nv, 3))
+    E = ctypes.c_double()
+    _check(lib().tp_willmore_energy(mesh.handle, ctypes.byref(E), ptr, kind, _stream_ptr(like)))
+    return E.value, out
 
 
 def tp_pins_set(mesh: Mesh, vertices=None):

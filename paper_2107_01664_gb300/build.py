@@ -17,7 +17,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtpsurf.so")
-SOURCES = ["mesh.cu", "pairs.cu", "bvh.cu", "cg.cu", "chol.cu", "solver.cu", "capi.cu", "noalloc.cu", "obstacle.cu", "pins.cu"]
+SOURCES = ["mesh.cu", "pairs.cu", "bvh.cu", "cg.cu", "chol.cu", "solver.cu", "capi.cu", "noalloc.cu", "obstacle.cu", "pins.cu", "willmore.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

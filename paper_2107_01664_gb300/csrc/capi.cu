@@ -190,7 +190,7 @@ int tp_mesh_destroy(tp_mesh* m) {
     Buf* all[] = {&m->faces, &m->vf_ptr, &m->vf_idx, &m->vcomp, &m->comp_ptr, &m->comp_verts, &m->pos, &m->center, &m->errflag, &m->f32a, &m->f32b,
                   &m->f32c, &m->tilebox,
                   &m->f64a, &m->f64b, &m->fgrad, &m->rowptr, &m->col, &m->cotsrc, &m->diagpos, &m->val,
-                  &m->dinv, &m->val32, &m->gval, &m->bvh_node, &m->bvh_perm, &m->bvh_keys, &m->bvh_tmp, &m->bvh_sortws,
+                  &m->dinv, &m->val32, &m->gval, &m->wm, &m->bvh_node, &m->bvh_perm, &m->bvh_keys, &m->bvh_tmp, &m->bvh_sortws,
                   &m->bvh_f32a, &m->bvh_f32b, &m->bvh_f32c, &m->bh_apply_ws, &m->part, &m->part2, &m->scal, &m->corner,
                   &m->wv64, &m->wv32, &m->io_in, &m->io_out, &m->adj, &m->erow, &m->tlist, &m->rowsum,
                   &m->kry};
@@ -383,6 +383,38 @@ int tp_obstacle_set(tp_mesh* m, int nv, int nf, const double* pos, const int32_t
     TP_CUDA(cudaStreamSynchronize(st));
     TP_TRY(obstacle_attach(m, o, weight, st));
     TP_CUDA(cudaStreamSynchronize(st));
+    return TP_OK;
+}
+
+int tp_willmore_set(tp_mesh* m, double weight) {
+    set_error("");
+    TP_TRY(check_mesh(m));
+    if (!std::isfinite(weight) || weight < 0.0) return fail(TP_ERR_INVALID_ARG, "weight must be finite and >= 0");
+    m->willmore_w = weight;
+    return TP_OK;
+}
+
+int tp_willmore_energy(tp_mesh* m, double* E_out, double* dE, int ptr_kind, void* stream) {
+    set_error("");
+    TP_TRY(check_mesh(m));
+    TP_TRY(check_kind(ptr_kind));
+    if (!E_out && !dE) return fail(TP_ERR_INVALID_ARG, "E_out and dE are both NULL");
+    DeviceGuard g(m->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    TP_TRY(ensure(m->rowsum, sizeof(double) * 8));
+    const size_t bytes = sizeof(double) * 3 * (size_t)m->nv;
+    double* out = nullptr;
+    if (dE) {
+        TP_TRY(ensure(m->io_out, bytes));
+        out = ptr_kind == TP_PTR_DEVICE ? dE : m->io_out.as<double>();
+        TP_CUDA(cudaMemsetAsync(out, 0, bytes, st));
+    }
+    TP_TRY(willmore_eval(m, E_out ? m->rowsum.as<double>() + 1 : nullptr, out, 1.0, st));
+    if (dE && ptr_kind == TP_PTR_HOST) TP_TRY(copy_out(dE, out, bytes, TP_PTR_HOST, st));
+    if (E_out) {
+        TP_CUDA(cudaMemcpyAsync(E_out, m->rowsum.as<double>() + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+        TP_CUDA(cudaStreamSynchronize(st));
+    }
     return TP_OK;
 }
 

@@ -363,6 +363,7 @@ int refresh_geometry(tp_mesh* m, cudaStream_t st) {
     TP_CUDA(cudaStreamSynchronize(st));
     m->lap_valid = false;
     m->gself_valid = false;
+    m->wm_valid = false;
     m->pin_valid = false;
     chol_invalidate(m);
     m->bvh_valid = false;

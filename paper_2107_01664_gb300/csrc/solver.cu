@@ -17,36 +17,44 @@ namespace tp {
 // energy / differential dispatch
 // ---------------------------------------------------------------------------
 
-int energy_value(tp_mesh* m, const tp_params* p, double* E_host, cudaStream_t st, bool obstacle) {
+int energy_value(tp_mesh* m, const tp_params* p, double* E_host, cudaStream_t st, bool aux) {
     TP_TRY(ensure(m->erow, sizeof(double) * m->nf));
     TP_TRY(ensure(m->rowsum, sizeof(double) * 8));
     if (p->theta > 0.0)
         TP_TRY(energy_rows_bh(m, p, nullptr, m->nf, m->erow.as<double>(), st));
     else
         TP_TRY(energy_rows_direct(m, p, nullptr, m->nf, m->erow.as<double>(), st));
-    if (obstacle) TP_TRY(obstacle_terms(m, p, false, true, m->erow.as<double>(), nullptr, st));
+    if (aux) TP_TRY(obstacle_terms(m, p, false, true, m->erow.as<double>(), nullptr, st));
     TP_TRY(sum_f64(m->erow.as<double>(), m->nf, m->rowsum.as<double>(), m, st));
-    TP_CUDA(cudaMemcpyAsync(E_host, m->rowsum.ptr, sizeof(double), cudaMemcpyDeviceToHost, st));
+    const bool wm = aux && m->willmore_w > 0.0;
+    if (wm) TP_TRY(willmore_eval(m, m->rowsum.as<double>() + 1, nullptr, 0.0, st));
+    double r[2] = {0.0, 0.0};
+    TP_CUDA(cudaMemcpyAsync(r, m->rowsum.ptr, sizeof(double) * (wm ? 2 : 1), cudaMemcpyDeviceToHost, st));
     TP_CUDA(cudaStreamSynchronize(st));
+    *E_host = r[0] + (wm ? m->willmore_w * r[1] : 0.0);
     return TP_OK;
 }
 
 int differential_dev(tp_mesh* m, const tp_params* p, double* dE, double* E_host, cudaStream_t st,
-                     bool obstacle) {
+                     bool aux) {
     TP_TRY(ensure(m->adj, sizeof(double) * 7 * (size_t)m->nf));
     TP_TRY(ensure(m->erow, sizeof(double) * m->nf));
     if (p->theta > 0.0)
         TP_TRY(diff_adjoints_bh(m, p, m->adj.as<double>(), m->erow.as<double>(), st));
     else
         TP_TRY(diff_adjoints_direct(m, p, m->adj.as<double>(), m->erow.as<double>(), st));
-    if (obstacle)
+    if (aux)
         TP_TRY(obstacle_terms(m, p, true, true, m->erow.as<double>(), m->adj.as<double>(), st));
     TP_TRY(adjoints_to_dE(m, m->adj.as<double>(), dE, st));
+    TP_TRY(ensure(m->rowsum, sizeof(double) * 8));
+    const bool wm = aux && m->willmore_w > 0.0;
+    if (wm) TP_TRY(willmore_eval(m, m->rowsum.as<double>() + 1, dE, m->willmore_w, st));
     if (E_host) {
-        TP_TRY(ensure(m->rowsum, sizeof(double) * 8));
         TP_TRY(sum_f64(m->erow.as<double>(), m->nf, m->rowsum.as<double>(), m, st));
-        TP_CUDA(cudaMemcpyAsync(E_host, m->rowsum.ptr, sizeof(double), cudaMemcpyDeviceToHost, st));
+        double r[2] = {0.0, 0.0};
+        TP_CUDA(cudaMemcpyAsync(r, m->rowsum.ptr, sizeof(double) * (wm ? 2 : 1), cudaMemcpyDeviceToHost, st));
         TP_CUDA(cudaStreamSynchronize(st));
+        *E_host = r[0] + (wm ? m->willmore_w * r[1] : 0.0);
     }
     return TP_OK;
 }
@@ -136,9 +144,11 @@ static int unpack(const double* srcp, int nv, const std::vector<double*>& dst, c
     return TP_OK;
 }
 
-// y = A v on packed columns (mean-zero output)
+// y = A v on packed columns (plus w C M^-1 C v with a Willmore weight w, the
+// H^2 term of §7.3.5), projected to the step's subspace
 static int apply_A_packed(tp_mesh* m, const tp_params* p, const double* v, int k, double* y, cudaStream_t st) {
     TP_TRY(apply_op(m, p, TP_OP_A, v, k, y, st));
+    if (m->willmore_w > 0.0) TP_TRY(willmore_operator_add(m, v, k, y, m->willmore_w, st));
     return project_space(m, y, k, st);
 }
 

@@ -163,6 +163,10 @@ struct tp_mesh {
     // pattern of C, for the weight and order it was built with)
     tp::Buf gval;
     bool gself_valid = false;
+    // Willmore term (§7.3.5): weight in the step, workspace, lumped mass valid for the positions
+    double willmore_w = 0.0;
+    tp::Buf wm;
+    bool wm_valid = false;
     double gself_kappa = 0.0, gself_sigma = 0.0;
     tp::CholState* chol = nullptr;   // created on the first factorised solve
     // Barnes-Hut tree (rebuilt per positions on demand)
@@ -300,11 +304,18 @@ int pinned_solve(tp_mesh* m, const tp_params* p, const double* b_dev, int k, dou
 // zero the pinned rows (pins set) or remove the mean of each component (no pins)
 int project_space(tp_mesh* m, double* x_dev, int k, cudaStream_t st);
 
+// -------- willmore.cu -------------------------------------------------------
+// E_W = f^T C M^-1 C f into E_dev (device scalar, may be null); with dE_dev, dE += w dE_W
+int willmore_eval(tp_mesh* m, double* E_dev, double* dE_dev, double w, cudaStream_t st);
+// y += w C M^-1 C v (k <= 9 columns)
+int willmore_operator_add(tp_mesh* m, const double* v_dev, int k, double* y_dev, double w, cudaStream_t st);
+
 // -------- solver.cu --------------------------------------------------------
-// E (host) of Eq. 10 or 16; with obstacle = true plus the static-obstacle term
-int energy_value(tp_mesh* m, const tp_params* p, double* E_host, cudaStream_t st, bool obstacle = false);
+// E (host) of Eq. 10 or 16; with aux = true plus the terms the step adds (static
+// obstacle, weighted Willmore energy), as is the differential
+int energy_value(tp_mesh* m, const tp_params* p, double* E_host, cudaStream_t st, bool aux = false);
 int differential_dev(tp_mesh* m, const tp_params* p, double* dE_dev, double* E_host,
-                     cudaStream_t st, bool obstacle = false);
+                     cudaStream_t st, bool aux = false);
 int precond_apply_dev(tp_mesh* m, const tp_params* p, const double* b, int k, double* z,
                       cudaStream_t st, int* cg_iters, bool strict = true);
 int precond_step_dev(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp_step_report* rep,
