@@ -24,7 +24,6 @@
 namespace tp {
 
 constexpr int KMAX = 9;
-constexpr int CG_T = 256;
 
 // ---------------------------------------------------------------------------
 // pattern (host, once per mesh)

@@ -24,7 +24,6 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <numeric>
 #include <vector>
 
 #include "tp_internal.cuh"
