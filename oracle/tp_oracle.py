@@ -634,6 +634,20 @@ def schur_direction(f, faces, use_area=True, use_volume=True, p=6.0, pins=None):
     return x.reshape(nv, 3), Z, S
 
 
+def barycenter_motion(f, faces, g):
+    """The translation added to the descent direction when the barycenter may
+    float (the barycenter-motion option of §7.1.1): minus the average of the
+    L^2 gradient g over the vertices, weighted by the vertex areas (the lumped
+    mass), per connected component. Returns [nv,3]."""
+    comp = mesh_components(len(f), faces)
+    m = lumped_mass(f, faces)
+    out = np.zeros_like(f)
+    for c in np.unique(comp):
+        sel = comp == c
+        out[sel] = -(m[sel, None] * g[sel]).sum(axis=0) / m[sel].sum()
+    return out
+
+
 def constraint_values(f, faces, A0, V0, use_area=True, use_volume=True):
     vals = []
     if use_area:
@@ -645,7 +659,7 @@ def constraint_values(f, faces, A0, V0, use_area=True, use_volume=True):
 
 def precond_step(f, faces, A0, V0, use_area=True, use_volume=True, p=6.0,
                  tau0=1.0, armijo_c=1e-4, shrink=0.5, ls_max=30, fixed_tau=None, proj_iters=1,
-                 obstacle=None, pins=None, willmore=0.0):
+                 obstacle=None, pins=None, willmore=0.0, free_barycenter=False):
     """One constrained descent step (§3, steps 1-5; §5.4 with exact solves):
     direction by Eq. 14, Armijo backtracking from tau0 (E(f + tau x) <=
     E(f) + c tau dE.x), then corrective projections by Eq. 15 with the
@@ -656,10 +670,13 @@ def precond_step(f, faces, A0, V0, use_area=True, use_volume=True, p=6.0,
     replace the barycenter rows; the pinned positions f_0 are those of f, so
     Phi_P = 0 at the start and every row of the projection's right-hand side
     for a pin is 0. With a Willmore weight w the energy gains w E_W and the
-    matrix w C M^{-1} C (§7.3.5).
+    matrix w C M^{-1} C (§7.3.5). With free_barycenter the direction gains
+    barycenter_motion (§7.1.1).
     Returns dict(f_new, x, tau, E0, E1, h)."""
     nv = len(f)
     x, g = descent_direction(f, faces, use_area, use_volume, p, obstacle, pins, willmore)
+    if free_barycenter:
+        x = x + barycenter_motion(f, faces, g)
     E0 = _total_energy(f, faces, p, obstacle, willmore)
     slope = float(np.sum(g * x))
     if fixed_tau is not None:

@@ -157,3 +157,23 @@ def test_step_with_obstacle_descends_and_zero_weight_is_plain_step():
     assert np.allclose(r0["f_new"], rp["f_new"], rtol=0, atol=1e-14)
     # the obstacle term changes the direction
     assert np.abs(r["x"] - rp["x"]).max() > 1e-6
+
+
+def test_free_barycenter_moves_the_surface_away_from_the_obstacle():
+    # with the barycenter free (§7.1.1), a small sphere off-centre in a
+    # spherical obstacle is translated towards the centre; the area and
+    # volume still hold, and without the option the barycenter stays
+    V, F = icosphere(2, 0.2)
+    V = V + np.array([0.4, 0.0, 0.0])
+    VO, FO = icosphere(3, 1.0)
+    A0, V0 = O.total_area(V, F), O.total_volume(V, F)
+    ob = (VO, FO, 1e-3)
+    r = O.precond_step(V, F, A0, V0, proj_iters=2, obstacle=ob, free_barycenter=True)
+    r0 = O.precond_step(V, F, A0, V0, proj_iters=2, obstacle=ob)
+    assert r["f_new"].mean(axis=0)[0] < V.mean(axis=0)[0] - 1e-6
+    assert abs(r0["f_new"].mean(axis=0)[0] - V.mean(axis=0)[0]) < 1e-12
+    assert abs(O.total_area(r["f_new"], F) - A0) < 1e-6 * A0
+    assert r["E1"] < r["E0"]
+    # the translation is the area-weighted mean of -dE, the same for all vertices
+    t = O.barycenter_motion(V, F, np.ones_like(V))
+    assert np.allclose(t, -1.0)
