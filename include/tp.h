@@ -75,6 +75,9 @@ extern "C" {
 /* constraint flags (the barycenter constraint of §7.1.1 is on unless pins are set) */
 #define TP_CONSTRAINT_AREA    1  /* total area, §7.1.3 */
 #define TP_CONSTRAINT_VOLUME  2  /* total signed volume, §7.1.4 */
+#define TP_CONSTRAINT_FREE_BARYCENTER 4  /* let each component's barycenter float (§7.1.1, barycenter
+                                            motions): the direction gains minus the area-weighted mean of
+                                            dE per component; not with pins */
 
 typedef struct tp_params {
     double p;             /* tangent-point exponent p (numerator |P d|^p, denominator |d|^{2p}); paper default 6 (§2.1) */

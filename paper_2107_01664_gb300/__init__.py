@@ -20,7 +20,7 @@ from . import build as _build
 
 __all__ = [
     "TP_OK", "TP_OP_A", "TP_OP_B", "TP_OP_B0", "TP_OP_L", "TP_PREC_FP32", "TP_PREC_FP64",
-    "TP_CONSTRAINT_AREA", "TP_CONSTRAINT_VOLUME", "TP_BH_DIFF_FULL", "TP_BH_DIFF_LITERAL",
+    "TP_CONSTRAINT_AREA", "TP_CONSTRAINT_VOLUME", "TP_CONSTRAINT_FREE_BARYCENTER", "TP_BH_DIFF_FULL", "TP_BH_DIFF_LITERAL",
     "TpError", "tp_params", "tp_constraints", "tp_step_report", "params", "Mesh",
     "tp_mesh_create", "tp_mesh_set_positions", "tp_mesh_get_positions", "tp_mesh_destroy",
     "tp_mesh_footprint_bytes", "tp_energy", "tp_energy_rows", "tp_differential",
@@ -37,7 +37,7 @@ TP_PTR_HOST, TP_PTR_DEVICE = 0, 1
 TP_PREC_FP32, TP_PREC_FP64 = 0, 1
 TP_OP_A, TP_OP_B, TP_OP_B0, TP_OP_L = 0, 1, 2, 3
 TP_BH_DIFF_FULL, TP_BH_DIFF_LITERAL = 0, 1
-TP_CONSTRAINT_AREA, TP_CONSTRAINT_VOLUME = 1, 2
+TP_CONSTRAINT_AREA, TP_CONSTRAINT_VOLUME, TP_CONSTRAINT_FREE_BARYCENTER = 1, 2, 4
 TP_POISSON_CHOLESKY, TP_POISSON_CG = 0, 1
 TP_MAX_PINS = 64
 _OPS = {"A": TP_OP_A, "B": TP_OP_B, "B0": TP_OP_B0, "L": TP_OP_L}

@@ -354,8 +354,10 @@ int precond_step(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp_ste
     TP_TRY(check_mesh(m));
     TP_TRY(check_params(p));
     if (!c) return fail(TP_ERR_INVALID_ARG, "constraints is NULL");
-    if (c->flags & ~(TP_CONSTRAINT_AREA | TP_CONSTRAINT_VOLUME))
+    if (c->flags & ~(TP_CONSTRAINT_AREA | TP_CONSTRAINT_VOLUME | TP_CONSTRAINT_FREE_BARYCENTER))
         return fail(TP_ERR_INVALID_ARG, "unknown constraint flag");
+    if ((c->flags & TP_CONSTRAINT_FREE_BARYCENTER) && m->npins)
+        return fail(TP_ERR_INVALID_ARG, "a free barycenter cannot be combined with pins");
     if (p->krylov_max < 1 || p->cg_max < 1 || p->ls_max < 1 || p->proj_iters < 0 || p->proj_iters > 100 ||
         !(p->armijo_shrink > 0.0 && p->armijo_shrink < 1.0))
         return fail(TP_ERR_INVALID_ARG, "bad solver parameters");

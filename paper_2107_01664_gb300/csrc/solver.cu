@@ -438,6 +438,56 @@ static int set_positions_dev(tp_mesh* m, const double* src, cudaStream_t st) {
     return refresh_geometry(m, st);
 }
 
+// Barycenter motion (§7.1.1): per connected component, t_c = -(sum m_i g_i) /
+// (sum m_i) with m_i the lumped mass (a third of the area of each face around
+// vertex i); one block per (component, coordinate), fixed summation order
+__global__ void k_bary_motion(const int* __restrict__ comp_ptr, const int* __restrict__ comp_verts,
+                              const int* __restrict__ vf_ptr, const int* __restrict__ vf_idx,
+                              const d4* __restrict__ f64a, const double* __restrict__ g, double* __restrict__ t) {
+    const int c = blockIdx.x, j = blockIdx.y;
+    __shared__ double rs[256], rw[256];
+    double s = 0.0, w = 0.0;
+    for (int e = comp_ptr[c] + threadIdx.x; e < comp_ptr[c + 1]; e += blockDim.x) {
+        const int v = comp_verts[e];
+        double mv = 0.0;
+        for (int q = vf_ptr[v]; q < vf_ptr[v + 1]; ++q) mv += f64a[vf_idx[q] / 3].w;
+        mv /= 3.0;
+        s += mv * g[3 * (size_t)v + j];
+        w += mv;
+    }
+    rs[threadIdx.x] = s;
+    rw[threadIdx.x] = w;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) {
+            rs[threadIdx.x] += rs[threadIdx.x + k];
+            rw[threadIdx.x] += rw[threadIdx.x + k];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) t[3 * c + j] = -rs[0] / rw[0];
+}
+
+__global__ void k_bary_add(const int* __restrict__ vcomp, int nv, const double* __restrict__ t,
+                           double* __restrict__ x) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)nv * 3) return;
+    x[i] += t[3 * (size_t)vcomp[i / 3] + (i % 3)];
+}
+
+// x += the translation of each component by minus the area-weighted mean of g
+static int barycenter_motion(tp_mesh* m, const double* g, double* x, cudaStream_t st) {
+    TP_TRY(ensure(m->part2, sizeof(double) * 3 * (size_t)m->ncomp));
+    double* t = m->part2.as<double>();
+    k_bary_motion<<<dim3(m->ncomp, 3), 256, 0, st>>>(m->comp_ptr.as<int>(), m->comp_verts.as<int>(),
+                                                    m->vf_ptr.as<int>(), m->vf_idx.as<int>(), m->f64a.as<d4>(), g, t);
+    TP_LAUNCH_CHECK();
+    const size_t n = (size_t)m->nv * 3;
+    k_bary_add<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(m->vcomp.as<int>(), m->nv, t, x);
+    TP_LAUNCH_CHECK();
+    return TP_OK;
+}
+
 int precond_step_dev(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp_step_report* rep,
                      cudaStream_t st) {
     const size_t n = (size_t)m->nv * 3;
@@ -518,6 +568,7 @@ int precond_step_dev(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp
         }
         TP_TRY(lincomb(x, xs.data(), cf.data(), (int)xs.size(), n, 0.0, st));
     }
+    if (c->flags & TP_CONSTRAINT_FREE_BARYCENTER) TP_TRY(barycenter_motion(m, g, x, st));
     {
         const double* a1[1] = {g};
         TP_TRY(dots(m, a1, x, 1, n, &r.slope, st));

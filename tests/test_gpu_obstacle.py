@@ -227,3 +227,34 @@ def test_torus20k_ball_obstacle_full(lib):
     Eb_ref, gb_ref, _ = O.bh_obstacle_energy(V, F, VO, FO, 0.5, 8)
     assert rel(Eb, Eb_ref) <= TOL32
     assert rel(gb, gb_ref) <= TOL32
+
+
+def test_free_barycenter_step_matches_oracle(lib):
+    # barycenter motion (§7.1.1) with an obstacle: the FP64 step equals the
+    # oracle's; the surface is translated away from the nearer wall; pins
+    # and a free barycenter are rejected together
+    import torch
+    V, F = icosphere(2, 0.2)
+    V = V + np.array([0.4, 0.0, 0.0])
+    VO, FO = icosphere(3, 1.0)
+    A0, V0 = O.total_area(V, F), O.total_volume(V, F)
+    ref = O.precond_step(V, F, A0, V0, fixed_tau=0.02, obstacle=(VO, FO, 1e-3), free_barycenter=True)
+    flags = lib.TP_CONSTRAINT_AREA | lib.TP_CONSTRAINT_VOLUME | lib.TP_CONSTRAINT_FREE_BARYCENTER
+    with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as m:
+        lib.tp_obstacle_set(m, VO, FO, 1e-3)
+        c = lib.tp_constraints(flags=flags, A0=A0, V0=V0)
+        p = lib.params(precision=1, krylov_tol=1e-11, cg_tol=1e-12, fixed_tau=1, tau0=0.02, krylov_max=400)
+        rep = lib.precond_step(m, c, p)
+        f_new = m.get_positions()
+        assert rep["status"] == 0 and rep["slope"] < 0
+        # FP32 Armijo steps keep moving the sphere towards the centre
+        for _ in range(2):
+            rep = lib.precond_step(m, c, lib.params(krylov_max=300, proj_iters=2))
+            assert rep["E_after"] < rep["E_before"]
+        f2 = m.get_positions()
+        lib.tp_pins_set(m, np.array([0], dtype=np.int32))
+        with pytest.raises(lib.TpError):
+            lib.precond_step(m, c, lib.params())
+    assert rel(f_new - V, ref["f_new"] - V) < 1e-7
+    assert f_new.mean(axis=0)[0] < V.mean(axis=0)[0]
+    assert f2.mean(axis=0)[0] < f_new.mean(axis=0)[0]
