@@ -501,6 +501,20 @@ def long_run(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def aggregate_ranks(dev_ms, units, device, world):
+    """Whole-job aggregate over the ranks of the process group: the maximum
+    device time and the summed work (replicas: no data-path collective)."""
+    if world <= 1:
+        return dev_ms, units
+    import torch
+    import torch.distributed as dist
+    tmax = torch.tensor([dev_ms], dtype=torch.float64, device=device)
+    tsum = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax.item()), float(tsum.item())
+
+
 def gpu_arm(args):
     import numpy as np
     import torch
@@ -572,16 +586,7 @@ def gpu_arm(args):
     pair_kernels = [k for k in prof if k in FLOPS_PER_PAIR or k in APPLY_FLOPS]
     pairs_total = sum(prof[k]["units"] for k in pair_kernels)
     dev_ms = float(sum(step_ms))
-    # whole-job aggregate over ranks: max time, summed work
-    t = torch.tensor([dev_ms, pairs_total], dtype=torch.float64, device=dev)
-    if world > 1:
-        tmax = t[0:1].clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t[1:2].clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        dev_ms_all, pairs_all = float(tmax.item()), float(tsum.item())
-    else:
-        dev_ms_all, pairs_all = dev_ms, pairs_total
+    dev_ms_all, pairs_all = aggregate_ranks(dev_ms, pairs_total, dev, world)
     value = pairs_all / (dev_ms_all / 1e3)
 
     # e2e through the C ABI with host buffers: pinned positions in, positions + dE out
