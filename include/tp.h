@@ -158,7 +158,10 @@ int tp_mesh_get_positions(tp_mesh* m, double* pos, int ptr_kind, void* stream);
 /* Free every device resource of the mesh. Accepts NULL. */
 int tp_mesh_destroy(tp_mesh* m);
 
-/* Device bytes a mesh of this size holds, for admission control. */
+/* Device bytes a mesh of this size holds, for admission control. Not
+ * included: a static obstacle (a mesh of its own), vertex pins (8 nv bytes
+ * per pin) and the Willmore workspace (192 nv bytes), which exist only once
+ * set. */
 size_t tp_mesh_footprint_bytes(int nv, int nf, const tp_params* p);
 
 /* Discrete tangent-point energy E (§3.1, Eq. 10; ordered pairs S != T),

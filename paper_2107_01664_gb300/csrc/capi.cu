@@ -212,7 +212,9 @@ size_t tp_mesh_footprint_bytes(int nv, int nf, const tp_params* p) {
     const int restart = p ? std::max(1, std::min(60, p->gmres_restart)) : 30;
     size_t F = (size_t)nf, V = (size_t)nv;
     size_t geom = F * (12 + 4 + 16 + 16 + 32 + 32 + 72) + V * (24 + 4);
-    size_t lap = (7 * V + F) * (4 + 8 + 8) + V * 16;
+    // cotan CSR (pattern, values, FP32 copy), the preconditioner's within-face
+    // term on the same pattern, and the connected-component tables
+    size_t lap = (7 * V + F) * (4 + 8 + 8) + V * 16 + (7 * V) * 8 + V * 12;
     size_t bvh = F * (4 + 8 + 16 + 16 + 16) + F * 64;
     size_t nsplit = 16;
     size_t pairs = nsplit * F * 14 * 8 + F * (96 + 72 + 72 + 56 + 8);
