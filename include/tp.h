@@ -337,6 +337,15 @@ unsigned long long tp_launch_count(void);
 int tp_energy_noalloc(const double* pos, int nv, const int32_t* faces, int nf,
                       double p, double* E, void* stream);
 
+/* Self-test of failure detection (the paper has no counterpart): one
+ * kernel on `device` waits for a device word that nothing sets, with the
+ * bounded wait that the sparse Cholesky sweep uses for its cross-block
+ * signals. The wait gives up after about one second, records the timeout
+ * and returns, so the context stays usable. Returns TP_ERR_TIMEOUT with
+ * *timed_out = 1 when that happened as designed (TP_OK with *timed_out = 0
+ * would mean the wait saw a value it should not have). Synchronous. */
+int tp_selftest_wait(int device, int* timed_out);
+
 /* Thread-local description of the last error of this thread ("" if none). */
 const char* tp_last_error(void);
 

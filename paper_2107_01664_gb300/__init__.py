@@ -28,7 +28,7 @@ __all__ = [
     "lib_path", "lib", "tp_kernel_stat", "tp_profile_enable", "tp_profile_read", "tp_launch_count",
     "tp_energy_noalloc", "tp_chol_info", "cotan_factor_info", "TP_POISSON_CHOLESKY", "TP_POISSON_CG",
     "tp_obstacle_set", "tp_obstacle_energy", "tp_pins_set", "TP_MAX_PINS", "tp_willmore_set",
-    "tp_willmore_energy",
+    "tp_willmore_energy", "tp_selftest_wait",
 ]
 
 TP_OK, TP_ERR_INVALID_ARG, TP_ERR_DEGENERATE, TP_ERR_OOM = 0, 1, 2, 3
@@ -128,6 +128,7 @@ def lib():
         "tp_obstacle_set": (c_int, [vp, c_int, c_int, vp, vp, c_double, c_int, vp]),
         "tp_pins_set": (c_int, [vp, c_int, vp, c_int, vp]),
         "tp_willmore_set": (c_int, [vp, c_double]),
+        "tp_selftest_wait": (c_int, [c_int, P(c_int)]),
         "tp_willmore_energy": (c_int, [vp, P(c_double), vp, c_int, vp]),
         "tp_obstacle_energy": (c_int, [vp, P(tp_params), P(c_double), vp, c_int, vp]),
     }
@@ -342,6 +343,14 @@ def precond_step(mesh: Mesh, constraints: tp_constraints, p: tp_params | None = 
         "krylov_iters": rep.krylov_iters, "cg_iters": rep.cg_iters, "ls_trials": rep.ls_trials,
         "status": rep.status, "pair_interactions": rep.pair_interactions,
     }
+
+
+def tp_selftest_wait(device: int = 0):
+    """(status, timed_out) of the bounded-wait self-test (no exception: a
+    TP_ERR_TIMEOUT status is the expected outcome)."""
+    t = ctypes.c_int()
+    code = lib().tp_selftest_wait(int(device), ctypes.byref(t))
+    return code, t.value
 
 
 def tp_willmore_set(mesh: Mesh, weight: float):

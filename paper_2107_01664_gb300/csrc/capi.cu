@@ -526,4 +526,16 @@ int tp_profile_read(tp_mesh* m, tp_kernel_stat* out, int max, int* n) {
 
 unsigned long long tp_launch_count(void) { return tp::launch_count(); }
 
+int tp_selftest_wait(int device, int* timed_out) {
+    set_error("");
+    if (!timed_out) return fail(TP_ERR_INVALID_ARG, "timed_out is NULL");
+    *timed_out = 0;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(TP_ERR_INVALID_ARG, "no such CUDA device");
+    DeviceGuard g(device);
+    if (!g.ok) return fail(TP_ERR_CUDA, "cudaSetDevice failed");
+    return wait_selftest(timed_out);
+}
+
 }  // extern "C"

@@ -1207,6 +1207,34 @@ int chol_trace(tp_mesh* m, unsigned long long* out, int max_rows, int* nn, int* 
 #endif
 
 // host-side description of the factor (for tests and reports)
+// Self-test of the bounded cross-block wait: one thread waits for a word
+// that nothing sets; the wait gives up after its clock budget (~1 s),
+// records the timeout in the control block and returns.
+__global__ void k_wait_selftest(const unsigned* word, CholCtl* ctl, int* result) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *result = wait_until(word, 1u, true, ctl) ? 0 : 1;
+}
+
+int wait_selftest(int* timed_out) {
+    void* mem = nullptr;
+    const size_t bytes = 256 + sizeof(CholCtl);
+    TP_CUDA(cudaMalloc(&mem, bytes));
+    unsigned* word = (unsigned*)mem;
+    int* result = (int*)((char*)mem + 64);
+    CholCtl* ctl = (CholCtl*)((char*)mem + 256);
+    int h[2] = {0, 0};
+    cudaError_t e = cudaMemset(mem, 0, bytes);
+    if (e == cudaSuccess) {
+        k_wait_selftest<<<1, 32>>>(word, ctl, result);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&h[0], result, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&h[1], &ctl->err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(mem);
+    if (e != cudaSuccess) return fail(TP_ERR_CUDA, cudaGetErrorString(e));
+    *timed_out = (h[0] == 1 && h[1] != 0) ? 1 : 0;
+    return *timed_out ? fail(TP_ERR_TIMEOUT, "self-test: the bounded wait gave up as designed") : TP_OK;
+}
+
 int chol_info(tp_mesh* m, tp_chol_info* out) {
     *out = tp_chol_info{};
     TP_TRY(chol_setup(m));

@@ -273,6 +273,9 @@ int self_term_add(tp_mesh* m, const tp_params* p, const double* x_dev, int k, do
 int chol_solve(tp_mesh* m, const tp_params* p, const double* b_dev, int k, double* z_dev,
                cudaStream_t st, int* iters, bool* used);
 int chol_info(tp_mesh* m, tp_chol_info* out);
+// waits in one kernel on a word nothing sets: TP_ERR_TIMEOUT and *timed_out = 1
+// once the bounded wait gives up (current device)
+int wait_selftest(int* timed_out);
 void chol_invalidate(tp_mesh* m);   // positions changed: refactor before the next solve
 void chol_release(tp_mesh* m);
 // vector helpers (device, FP64, deterministic)
