@@ -407,6 +407,35 @@ def willmore_steps(tp, dev, steps=2, weight=100.0):
             "E_before": reps[0]["E_before"], "E_after": reps[0]["E_after"], "status": [r["status"] for r in reps]}
 
 
+def accuracy(tp, dev):
+    """Errors on torus_20k against the FP64 oracle, from stored oracle values
+    (tests/golden: the energy, and dE and A u (u = 3 seeded N(0,1) columns)
+    at 64 sampled vertices): the FP32 direct path and Barnes-Hut at
+    theta = 0.25 and 0.5 (relative 2-norm errors over the sampled rows)."""
+    import numpy as np
+    import torch
+    from synth import vertex_vectors, workload
+    gold = json.load(open(os.path.join(ROOT, "tests", "golden", "full_size.json")))[WORKLOAD]
+    smp = json.load(open(os.path.join(ROOT, "tests", "golden", "torus20k_samples.json")))
+    V, F = workload(WORKLOAD)
+    idx = np.array(smp["vertices"])
+    dE_ref, Au_ref = np.array(smp["dE"]), np.array(smp["Au"])
+    u = torch.tensor(vertex_vectors(len(V), 3, 202), dtype=torch.float64, device=dev)
+    mesh = tp.Mesh(torch.tensor(V, dtype=torch.float64, device=dev), torch.tensor(F, dtype=torch.int32, device=dev),
+                   device=dev.index or 0)
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    out = {"workload": WORKLOAD, "reference": "FP64 oracle (stored: energy, dE and A u at 64 vertices)"}
+    for name, p in (("fp32_direct", tp.params()), ("bh_theta_0.25", tp.params(theta=0.25)),
+                    ("bh_theta_0.5", tp.params(theta=0.5))):
+        E = tp.tp_energy(mesh, p)
+        dE, _ = tp.tp_differential(mesh, p)
+        Au = tp.fractional_apply(mesh, "A", u, p).cpu().numpy()
+        out[name] = {"E": abs(E - gold["energy"]) / abs(gold["energy"]), "dE": rel(dE[idx], dE_ref),
+                     "Au": rel(Au[idx], Au_ref)}
+    mesh.close()
+    return out
+
+
 def bh_step(tp, dev, steps=2):
     """Constrained steps with every pair sum on the tree (theta = 0.5: energy,
     differential, and the A and L^{2-s} applies of the Krylov loop) on the
@@ -663,6 +692,7 @@ def gpu_arm(args):
         line["obstacle"] = obstacle_scene(tp, dev)
         line["pins"] = pinned_steps(tp, dev)
         line["willmore"] = willmore_steps(tp, dev)
+        line["accuracy"] = accuracy(tp, dev)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = run_cpu_sample()
     mesh.close()
@@ -793,6 +823,8 @@ def main():
                     help="run only the static-obstacle scene (torus_20k around a ball) instead")
     ap.add_argument("--pins", action="store_true",
                     help="run only the vertex-pin steps (torus_20k with 8 pins) instead")
+    ap.add_argument("--accuracy", action="store_true",
+                    help="report only the errors on torus_20k against stored oracle values instead")
     ap.add_argument("--willmore", action="store_true",
                     help="run only the Willmore steps (torus_20k, weight 100) instead")
     ap.add_argument("--serve-n", type=int, default=64)
@@ -816,6 +848,12 @@ def main():
         import paper_2107_01664_gb300 as tp
         torch.cuda.set_device(0)
         print(json.dumps({"pins": pinned_steps(tp, torch.device("cuda", 0))}))
+        return
+    if args.accuracy:
+        import torch
+        import paper_2107_01664_gb300 as tp
+        torch.cuda.set_device(0)
+        print(json.dumps({"accuracy": accuracy(tp, torch.device("cuda", 0))}))
         return
     if args.willmore:
         import torch
