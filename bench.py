@@ -711,6 +711,8 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    for _ in range(args.warmup):       # untimed
+        run_cpu_sample(scale=4)
     vals, secs = [], 0.0
     for _ in range(args.steps):
         r = run_cpu_sample(scale=4)
