@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "host_util.h"
 #include "tp_internal.cuh"
 
 namespace tp {
@@ -255,32 +256,10 @@ __global__ void k_tile_boxes(const float4* __restrict__ f32a, int nf, float4* __
     }
 }
 
-// connected components by union-find over the face edges, labelled in
-// order of their smallest vertex
+// connected components through the face edges (host_util.h)
 int components_setup(tp_mesh* m, const std::vector<int>& F) {
     const int nv = m->nv;
-    std::vector<int> parent(nv);
-    for (int v = 0; v < nv; ++v) parent[v] = v;
-    auto find = [&](int x) {
-        while (parent[x] != x) {
-            parent[x] = parent[parent[x]];
-            x = parent[x];
-        }
-        return x;
-    };
-    for (size_t e = 0; e + 2 < F.size(); e += 3)
-        for (int c = 0; c < 3; ++c) {
-            const int a = find(F[e + c]), b = find(F[e + (c + 1) % 3]);
-            if (a != b) parent[a > b ? a : b] = a < b ? a : b;
-        }
-    std::vector<int> label(nv, -1);
-    m->comp_host.assign(nv, 0);
-    int nc = 0;
-    for (int v = 0; v < nv; ++v) {
-        const int r = find(v);
-        if (label[r] < 0) label[r] = nc++;
-        m->comp_host[v] = label[r];
-    }
+    const int nc = label_components(nv, F, m->comp_host);
     m->ncomp = nc;
     std::vector<int> ptr(nc + 1, 0), verts(nv);
     for (int v = 0; v < nv; ++v) ptr[m->comp_host[v] + 1]++;

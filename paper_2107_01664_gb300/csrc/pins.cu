@@ -26,6 +26,7 @@
 #include <cstring>
 #include <vector>
 
+#include "host_util.h"
 #include "tp_internal.cuh"
 
 namespace tp {
@@ -106,38 +107,6 @@ __global__ void k_zero_rows(const int* __restrict__ idx, int np, int k, double* 
     x[(size_t)idx[i / k] * k + (i % k)] = 0.0;
 }
 
-// inverse of a small dense matrix (Gauss-Jordan, partial pivoting); false if singular
-bool invert(std::vector<double> a, int n, std::vector<double>& inv) {
-    inv.assign((size_t)n * n, 0.0);
-    for (int i = 0; i < n; ++i) inv[(size_t)i * n + i] = 1.0;
-    for (int c = 0; c < n; ++c) {
-        int piv = c;
-        for (int r = c + 1; r < n; ++r)
-            if (std::fabs(a[(size_t)r * n + c]) > std::fabs(a[(size_t)piv * n + c])) piv = r;
-        if (!(std::fabs(a[(size_t)piv * n + c]) > 0.0)) return false;
-        if (piv != c)
-            for (int q = 0; q < n; ++q) {
-                std::swap(a[(size_t)c * n + q], a[(size_t)piv * n + q]);
-                std::swap(inv[(size_t)c * n + q], inv[(size_t)piv * n + q]);
-            }
-        const double d = 1.0 / a[(size_t)c * n + c];
-        for (int q = 0; q < n; ++q) {
-            a[(size_t)c * n + q] *= d;
-            inv[(size_t)c * n + q] *= d;
-        }
-        for (int r = 0; r < n; ++r) {
-            if (r == c) continue;
-            const double f = a[(size_t)r * n + c];
-            if (f == 0.0) continue;
-            for (int q = 0; q < n; ++q) {
-                a[(size_t)r * n + q] -= f * a[(size_t)c * n + q];
-                inv[(size_t)r * n + q] -= f * inv[(size_t)c * n + q];
-            }
-        }
-    }
-    return true;
-}
-
 // W = C^+ S^T for the current positions, and the inverse of the small system
 int pins_prepare(tp_mesh* m, const tp_params* p, cudaStream_t st, int* iters) {
     if (m->pin_valid) return TP_OK;
@@ -175,7 +144,7 @@ int pins_prepare(tp_mesh* m, const tp_params* p, cudaStream_t st, int* iters) {
         M[(size_t)r * n + np + c] = 1.0;
         M[(size_t)(np + c) * n + r] = 1.0;
     }
-    if (!invert(M, n, Minv)) return fail(TP_ERR_DEGENERATE, "pins: singular pin system (repeated pins?)");
+    if (!invert_dense(M, n, Minv)) return fail(TP_ERR_DEGENERATE, "pins: singular pin system (repeated pins?)");
     TP_TRY(ensure(m->pin_Minv, sizeof(double) * (size_t)n * n + sizeof(double) * (size_t)n * PIN_K * 2));
     TP_CUDA(cudaMemcpyAsync(m->pin_Minv.ptr, Minv.data(), sizeof(double) * (size_t)n * n, cudaMemcpyHostToDevice,
                             st));
