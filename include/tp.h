@@ -8,7 +8,8 @@
  *   - the forward application of the fractional operators B, B0, A = B + B0
  *     (§3.2, §5.1.2-5.1.3, Appendix A) and L^{2-s} (§5.1.1, §5.2),
  *   - Barnes-Hut approximations of E and dE over a GPU-built BVH (§4),
- *   - the cotan-Laplacian Poisson solves of the preconditioner by CG (§5.2),
+ *   - the cotan-Laplacian Poisson solves of the preconditioner (§5.2):
+ *     a pre-factorised sparse Cholesky (default) or Jacobi CG,
  *   - the constrained preconditioned descent step (§3.3, §5.3, §5.4).
  *
  * Conventions shared by every call:
@@ -318,22 +319,25 @@ int tp_profile_read(tp_mesh* m, tp_kernel_stat* out, int max, int* n);
 /* Number of CUDA kernels this library has launched in this process. */
 unsigned long long tp_launch_count(void);
 
-/* Direct energy E of Eq. 10 (FP32 pair terms, compensated sums, FP64
- * reduction) for callers that cannot allocate device memory: code inside a
- * CUDA graph being captured, plug-ins of hosts that own the device
- * allocator, real-time loops that must not take allocator locks. The paper
- * has no counterpart of this entry point: it is a deployment convenience.
- *   pos   device float64 [nv][3], faces device int32 [nf][3] (faces with an
- *         index outside 0..nv-1 are left out), E device float64 [1] (output),
- *         all on the calling thread's current CUDA device; p > 2.
+/* The direct energy E (FP32 pair terms, compensated sums, FP64 reduction;
+ * the same quantity as tp_energy with theta = 0) for callers that are not
+ * allowed to allocate device memory: plug-ins inside a host program that
+ * owns the device allocator and forbids side allocations, and real-time
+ * loops that must not block on allocator locks or meet an out-of-memory
+ * failure mid-run. The paper has no counterpart of this entry point.
+ *   pos   device float64 [nv][3], faces device int32 [nf][3], E device
+ *         float64 [1] (output), all on the calling thread's current CUDA
+ *         device; p > 2. A face naming a vertex outside 0..nv-1 makes *E a
+ *         quiet NaN (the call still returns TP_OK: the check runs on the GPU).
  * Allocates nothing: every intermediate lives in one static device array of
- * about 5.3 MB that each GPU loading the library holds until the process
- * exits. At most 32768 faces (larger meshes: TP_ERR_INVALID_ARG, use
- * tp_mesh_create + tp_energy). The first call on a device looks up that
- * array's device address; make it before any stream capture. Calls share
- * the array: calls whose kernels overlap on the GPU (other streams, other
- * threads) race, so the caller must serialise them. Asynchronous on
- * `stream`; *E is valid once the stream has passed the call. */
+ * 5,767,232 bytes (5.5 MiB) that each GPU loading the library holds until the
+ * process exits. At most 32768 faces (larger meshes: TP_ERR_INVALID_ARG
+ * before anything is launched; use tp_mesh_create + tp_energy). The first
+ * call on a device (and context) looks up that array's device address; make
+ * it before any stream capture. Calls share the array: calls whose kernels
+ * overlap on the GPU (other streams, other threads) race, so the caller must
+ * serialise them. Asynchronous on `stream`; *E is valid once the stream has
+ * passed the call. */
 int tp_energy_noalloc(const double* pos, int nv, const int32_t* faces, int nf,
                       double p, double* E, void* stream);
 

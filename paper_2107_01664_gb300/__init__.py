@@ -421,12 +421,35 @@ def tp_launch_count() -> int:
 
 
 def tp_energy_noalloc(positions, faces, E_out, p: float = 6.0) -> None:
-    """Direct energy into the CUDA tensor E_out (float64, 1 element) without
-    any device allocation; positions [nv,3] float64 and faces [nf,3] int32
-    must be CUDA tensors on the current device (at most 32768 faces)."""
+    """Direct energy into the CUDA tensor E_out (float64, at least 1 element)
+    with no device allocation, for callers that may not allocate (see
+    include/tp.h). positions [nv,3] float64 and faces [nf,3] int32 must be
+    contiguous CUDA tensors on the current device (at most 32768 faces).
+    Inputs of another dtype, layout or device are rejected, not converted:
+    converting would allocate. A face index outside 0..nv-1 makes E_out NaN."""
+    torch = _torch()
+    cur = torch.cuda.current_device()
+    for name, t, dt in (("positions", positions, torch.float64), ("faces", faces, torch.int32),
+                        ("E_out", E_out, torch.float64)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"tp_energy_noalloc: {name} must be a CUDA tensor")
+        if t.dtype != dt:
+            raise TypeError(f"tp_energy_noalloc: {name} must be {dt}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"tp_energy_noalloc: {name} must be contiguous")
+        if t.device.index != cur:
+            raise ValueError(f"tp_energy_noalloc: {name} is on cuda:{t.device.index}, "
+                             f"the current device is cuda:{cur}")
+    if positions.dim() != 2 or positions.shape[1] != 3:
+        raise ValueError("tp_energy_noalloc: positions must have shape [nv, 3]")
+    if faces.dim() != 2 or faces.shape[1] != 3:
+        raise ValueError("tp_energy_noalloc: faces must have shape [nf, 3]")
+    if E_out.numel() < 1:
+        raise ValueError("tp_energy_noalloc: E_out needs at least one element")
     _check(lib().tp_energy_noalloc(ctypes.c_void_p(positions.data_ptr()), int(positions.shape[0]),
                                    ctypes.c_void_p(faces.data_ptr()), int(faces.shape[0]), float(p),
-                                   ctypes.c_void_p(E_out.data_ptr()), _stream_ptr(positions)))
+                                   ctypes.c_void_p(E_out.data_ptr()),
+                                   ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
 
 
 # ---------------------------------------------------------------------------

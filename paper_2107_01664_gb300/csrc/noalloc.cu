@@ -1,20 +1,21 @@
 // tp_energy_noalloc: the direct energy for callers that cannot allocate
 // device memory.
 //
-// Some callers cannot call cudaMalloc at all: code running inside a CUDA
-// graph that is being captured, plug-ins of host programs that own the
-// device allocator (and forbid side allocations), or real-time loops that
-// must not take the allocator's locks. This entry point computes the same
-// quantity as tp_energy with theta = 0 (Eq. 10, ordered pairs, FP32 pair
+// Some callers are not allowed to call cudaMalloc: plug-ins running inside a
+// host program that owns the device allocator and forbids side allocations,
+// and real-time loops that must not block on the allocator's locks or risk an
+// out-of-memory failure in the middle of a run. This entry point computes the
+// same quantity as tp_energy with theta = 0 (Eq. 10, ordered pairs, FP32 pair
 // terms, compensated sums, FP64 reduction) from caller-owned device arrays,
 // and keeps every intermediate in one fixed static device array of this file.
 //
-// The static array is sized for NA_MAX_FACES faces (about 5.3 MB) and is
-// held by every GPU that loads the library until the process exits. Every
-// call shares it: concurrent calls whose kernels overlap on the GPU (two
-// streams, two host threads) race and must be serialised by the caller. The
-// array keeps the last call's contents; nothing in it needs to start at zero
-// because each call writes every entry it later reads.
+// The static array is sized for NA_MAX_FACES faces (5,767,232 bytes, 5.5 MiB)
+// and is held by every GPU that loads the library until the process exits.
+// Every call shares it: calls whose kernels overlap on the GPU (two streams,
+// two host threads) race and must be serialised by the caller. The array
+// keeps the last call's contents. The only entry that must start at zero,
+// the bad-index flag, is cleared by the first kernel of each call; every
+// other entry a call reads was written earlier in the same call.
 #include <mutex>
 
 #include "tp_internal.cuh"
@@ -32,14 +33,42 @@ struct NoAllocScratch {
     float4 nn[NA_MAX_FACES];   // unit normal
     double part[NA_MAX_SPLIT * NA_MAX_FACES];
     double center[4];
+    int bad_index;             // set when a face names a vertex outside 0..nv-1
+    int pad[7];
 };
+
+static_assert(sizeof(NoAllocScratch) == 5767232, "the size stated in tp.h and the file comment");
 
 // the scratch of every call (see the file comment for its sharing rules)
 static __device__ __align__(256) unsigned char g_scratch[sizeof(NoAllocScratch)];
 
-// device address of g_scratch per device, looked up once per device
+// device address of g_scratch per device, looked up once per device and
+// context (a context created again, after cudaDeviceReset for instance, loads
+// the module again and may place the array elsewhere)
 std::mutex g_setup_mutex;
 void* g_scratch_addr[64] = {nullptr};
+void* g_scratch_ctx[64] = {nullptr};
+
+// the current driver context (an opaque handle), through the runtime's
+// driver entry point so that the library does not link libcuda itself
+typedef int (*CtxGetCurrentFn)(void**);
+void* current_context() {
+    static CtxGetCurrentFn fn = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(f);
+        else
+            cudaGetLastError();
+        looked_up = true;
+    }
+    void* ctx = nullptr;
+    if (fn && fn(&ctx) != 0) ctx = nullptr;
+    return ctx;
+}
 
 __global__ void k_na_center(const double* __restrict__ pos, int nv, NoAllocScratch* sc) {
     __shared__ double lo[3][NA_T], hi[3][NA_T];
@@ -63,6 +92,7 @@ __global__ void k_na_center(const double* __restrict__ pos, int nv, NoAllocScrat
         __syncthreads();
     }
     if (threadIdx.x < 3) sc->center[threadIdx.x] = 0.5 * (lo[threadIdx.x][0] + hi[threadIdx.x][0]);
+    if (threadIdx.x == 0) sc->bad_index = 0;   // the first kernel of a call clears the flag
 }
 
 __global__ void k_na_faces(const double* __restrict__ pos, int nv, const int* __restrict__ faces, int nf,
@@ -71,7 +101,9 @@ __global__ void k_na_faces(const double* __restrict__ pos, int nv, const int* __
     if (S >= nf) return;
     const int id[3] = {faces[3 * S], faces[3 * S + 1], faces[3 * S + 2]};
     if (id[0] < 0 || id[0] >= nv || id[1] < 0 || id[1] >= nv || id[2] < 0 || id[2] >= nv) {
-        // an index out of range: the face is left out (zero area and normal)
+        // an index out of range: flagged (the result becomes NaN) and the face
+        // is not read (zero area and normal, so the pair kernel stays in bounds)
+        sc->bad_index = 1;
         sc->xa[S] = make_float4(0.f, 0.f, 0.f, 0.f);
         sc->xl[S] = sc->xa[S];
         sc->nn[S] = sc->xa[S];
@@ -164,7 +196,8 @@ __global__ void k_na_sum(const NoAllocScratch* sc, int nf, int nsplit, double* _
         if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
         __syncthreads();
     }
-    if (threadIdx.x == 0) *E = red[0];
+    // a face with a vertex index out of range makes the result a quiet NaN
+    if (threadIdx.x == 0) *E = sc->bad_index ? __longlong_as_double(0x7ff8000000000000ll) : red[0];
 }
 
 }  // namespace
@@ -183,19 +216,29 @@ extern "C" int tp_energy_noalloc(const double* pos, int nv, const int32_t* faces
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
         return fail(TP_ERR_CUDA, "tp_energy_noalloc: no current CUDA device");
+    // an error left by earlier work of this thread is reported as such, not
+    // as a failure of this call's launches
+    {
+        cudaError_t prior = cudaGetLastError();
+        if (prior != cudaSuccess)
+            return fail(TP_ERR_CUDA, std::string("tp_energy_noalloc: an earlier CUDA error is pending: ") +
+                                         cudaGetErrorString(prior));
+    }
     NoAllocScratch* sc = nullptr;
     {
-        // first call on this device: look up the device address of the static
-        // array, with this device current (host code cannot use g_scratch's
-        // name as a device address)
+        // first call on this device (and context): look up the device address
+        // of the static array, with this device current (host code cannot use
+        // g_scratch's name as a device address)
         std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (!g_scratch_addr[dev]) {
+        void* ctx = current_context();
+        if (!g_scratch_addr[dev] || g_scratch_ctx[dev] != ctx) {
             void* ptr = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&ptr, g_scratch);
             if (e != cudaSuccess || !ptr)
                 return fail(TP_ERR_CUDA, std::string("tp_energy_noalloc: cudaGetSymbolAddress failed: ") +
                                              cudaGetErrorString(e));
             g_scratch_addr[dev] = ptr;
+            g_scratch_ctx[dev] = ctx;
         }
         sc = static_cast<NoAllocScratch*>(g_scratch_addr[dev]);
     }
@@ -208,16 +251,24 @@ extern "C" int tp_energy_noalloc(const double* pos, int nv, const int32_t* faces
     if (nsplit < 1) nsplit = 1;
     const int tps = (ntiles + nsplit - 1) / nsplit;
     nsplit = (ntiles + tps - 1) / tps;
+    auto launched = [](const char* what) -> int {
+        tp::count_launches(1);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return fail(TP_ERR_CUDA, std::string("tp_energy_noalloc: launch of ") + what + " failed: " +
+                                         cudaGetErrorString(e));
+        return TP_OK;
+    };
     k_na_center<<<1, NA_T, 0, st>>>(pos, nv, sc);
+    TP_TRY(launched("k_na_center"));
     k_na_faces<<<(nf + 255) / 256, 256, 0, st>>>(pos, nv, faces, nf, sc);
+    TP_TRY(launched("k_na_faces"));
     if (p == 6.0)
         k_na_pairs<true><<<dim3(bx, nsplit), NA_T, 0, st>>>(sc, nf, tps, 3.0f);
     else
         k_na_pairs<false><<<dim3(bx, nsplit), NA_T, 0, st>>>(sc, nf, tps, (float)(0.5 * p));
+    TP_TRY(launched("k_na_pairs"));
     k_na_sum<<<1, 1024, 0, st>>>(sc, nf, nsplit, E);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess)
-        return fail(TP_ERR_CUDA, std::string("tp_energy_noalloc: launch failed: ") + cudaGetErrorString(e));
-    tp::count_launches(4);
+    TP_TRY(launched("k_na_sum"));
     return TP_OK;
 }

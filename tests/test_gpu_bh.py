@@ -23,6 +23,12 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def maxrel(a, b):
+    """max |a - b| over max |b|: a few wrong entries that a 2-norm hides show here"""
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
 def dev(x, dtype=None):
     import torch
     return torch.as_tensor(np.ascontiguousarray(x), device="cuda:0", dtype=dtype)
@@ -179,7 +185,7 @@ def test_torus20k_bh(lib):
     assert rel(E, O.bh_energy(V, F, 0.5)) <= TOL32
     idx = np.random.default_rng(5).choice(len(V), 32, replace=False)
     ref = O.bh_differential(V, F, 0.5, mode="full")
-    assert rel(g[idx], ref[idx]) <= TOL32
+    assert rel(g[idx], ref[idx]) <= TOL32 and maxrel(g[idx], ref[idx]) <= 4 * TOL32
 
 
 def test_icosphere_l8_bh_sample(lib):
@@ -193,8 +199,8 @@ def test_icosphere_l8_bh_sample(lib):
     Tr, L = O.bh_interactions(V, F, 0.5, 8, tg, tree)
     ref_bh, _ = O.bh_energy_rows(V, F, 0.5, 8, 6.0, tg)
     ref_direct = O.energy_rows(V, F, 6.0, tg)
-    assert rel(rows, ref_bh) <= TOL32
-    assert rel(rows_direct, ref_direct) <= TOL32
+    assert rel(rows, ref_bh) <= TOL32 and maxrel(rows, ref_bh) <= 4 * TOL32
+    assert rel(rows_direct, ref_direct) <= TOL32 and maxrel(rows_direct, ref_direct) <= 4 * TOL32
     print("icosphere_l8 sample: BH(0.5) vs direct FP64 rows, relative error", rel(rows, ref_direct))
 
 

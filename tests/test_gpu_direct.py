@@ -24,6 +24,12 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def maxrel(a, b):
+    """max |a - b| over max |b|: a few wrong entries that a 2-norm hides show here"""
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
 def dev(x, dtype=None):
     import torch
     return torch.as_tensor(np.ascontiguousarray(x), device="cuda:0", dtype=dtype)
@@ -285,14 +291,16 @@ def test_precond_step_armijo_trajectory_matches_oracle(lib):
         E_ref.append((r["tau"], r["E0"], r["E1"]))
     c = lib.tp_constraints(flags=3, A0=A0, V0=V0)
     with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as m:
-        p = lib.params(precision=1, krylov_tol=1e-9, krylov_max=600, cg_tol=1e-12, proj_iters=3)
+        # the Krylov solves converged to 1e-11, as in the single-step test
+        # above, so the trajectory carries the same 1e-7 / 1e-6 bounds
+        p = lib.params(precision=1, krylov_tol=1e-11, krylov_max=600, cg_tol=1e-12, proj_iters=3)
         for k in range(3):
             rep = lib.precond_step(m, c, p)
             assert rep["status"] == 0 and rep["slope"] < 0
             assert rep["tau"] == E_ref[k][0]
-            assert rel(rep["E_after"], E_ref[k][2]) < 1e-6
+            assert rel(rep["E_after"], E_ref[k][2]) < 1e-7
         f = m.get_positions()
-    assert rel(f - V, f_ref - V) < 1e-5
+    assert rel(f - V, f_ref - V) < 1e-6
     with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as m:
         p = lib.params(cg_tol=1e-6, krylov_max=600, proj_iters=3)
         for _ in range(3):
@@ -329,7 +337,8 @@ def test_torus20k_energy_full(lib, torus):
     E32 = lib.tp_energy(m, lib.params())
     assert rel(E32, _golden("torus_20k")["energy"]) <= TOL32
     tg = np.random.default_rng(7).choice(len(F), 256, replace=False).astype(np.int32)
-    assert rel(lib.tp_energy_rows(m, tg, lib.params()), O.energy_rows(V, F, 6.0, tg)) <= TOL32
+    rows, ref = lib.tp_energy_rows(m, tg, lib.params()), O.energy_rows(V, F, 6.0, tg)
+    assert rel(rows, ref) <= TOL32 and maxrel(rows, ref) <= 4 * TOL32
 
 
 def test_torus20k_differential_sampled(lib, torus):
@@ -337,7 +346,7 @@ def test_torus20k_differential_sampled(lib, torus):
     g, _ = lib.tp_differential(m, lib.params())
     idx = np.random.default_rng(202).choice(len(V), 64, replace=False)
     ref = O.differential_at_vertices(V, F, idx)
-    assert rel(g[idx], ref) <= TOL32
+    assert rel(g[idx], ref) <= TOL32 and maxrel(g[idx], ref) <= 4 * TOL32
 
 
 @pytest.mark.parametrize("op", ["A", "L"])
@@ -347,7 +356,7 @@ def test_torus20k_apply_sampled(lib, torus, op):
     y = lib.fractional_apply(m, op, u, lib.params())
     idx = np.random.default_rng(203).choice(len(V), 48, replace=False)
     ref = O.apply_operator_at_vertices(V, F, u, op, idx)
-    assert rel(y[idx], ref) <= TOL32
+    assert rel(y[idx], ref) <= TOL32 and maxrel(y[idx], ref) <= 4 * TOL32
 
 
 def test_torus20k_step_krylov_converges(lib, torus):
@@ -409,7 +418,7 @@ def test_torus20k_cotan_solve_full(lib, torus):
     assert np.linalg.norm(C @ z - b) <= 1e-6 * np.linalg.norm(b)
     assert rel(z, ref) <= 1e-3   # residual 1e-6 times at most the condition of C
     z2, _ = lib.cotan_solve(m, b, lib.params(cg_tol=1e-10))
-    assert rel(z2, ref) <= 1e-8
+    assert rel(z2, ref) <= 1e-8 and maxrel(z2, ref) <= 4e-8
 
 
 def test_linked_tori_factor_two_components(lib):

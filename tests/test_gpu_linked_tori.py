@@ -21,6 +21,12 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def maxrel(a, b):
+    """max |a - b| over max |b|: a few wrong entries that a 2-norm hides show here"""
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
 @pytest.fixture(scope="module")
 def tori(lib):
     import torch
@@ -69,7 +75,8 @@ def test_gradient_matches_oracle_at_sampled_vertices(lib, tori):
     V, F, f, m = tori
     g, _ = lib.tp_differential(m, lib.params())
     idx = np.random.default_rng(3).choice(len(V), 24, replace=False)
-    assert rel(g[idx], O.differential_at_vertices(V, F, idx)) <= 1e-5
+    ref = O.differential_at_vertices(V, F, idx)
+    assert rel(g[idx], ref) <= 1e-5 and maxrel(g[idx], ref) <= 4e-5
 
 
 def test_constrained_step_converges_with_one_barycenter_per_torus(lib):

@@ -21,6 +21,12 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+def maxrel(a, b):
+    """max |a - b| over max |b|: a few wrong entries that a 2-norm hides show here"""
+    a, b = np.asarray(a), np.asarray(b)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
 def dev(x, dtype=None):
     import torch
     return torch.as_tensor(np.ascontiguousarray(x), device="cuda:0", dtype=dtype)
@@ -221,12 +227,12 @@ def test_torus20k_ball_obstacle_full(lib):
     idx = np.random.default_rng(31).choice(len(V), 64, replace=False)
     inc = np.nonzero(np.isin(F, idx).any(axis=1))[0]
     ref = O.obstacle_differential(V, F[inc], VO, FO)[idx]
-    assert rel(g[idx], ref) <= TOL32
+    assert rel(g[idx], ref) <= TOL32 and maxrel(g[idx], ref) <= 4 * TOL32
     # Barnes-Hut at the benchmark's theta: the oracle's Barnes-Hut over the
     # same tree (its error against the direct sum is about 4% here)
     Eb_ref, gb_ref, _ = O.bh_obstacle_energy(V, F, VO, FO, 0.5, 8)
     assert rel(Eb, Eb_ref) <= TOL32
-    assert rel(gb, gb_ref) <= TOL32
+    assert rel(gb, gb_ref) <= TOL32 and maxrel(gb, gb_ref) <= 4 * TOL32
 
 
 def test_free_barycenter_step_matches_oracle(lib):

@@ -65,6 +65,21 @@ def test_energy_sphere_limit_second_order():
     assert errs[-1] < 5e-3
 
 
+# Energies of the unperturbed unit icospheres of levels 1-4 at p = 6 (midpoint
+# subdivision of the regular icosahedron, projected to R = 1), to six digits.
+# They come from an evaluation of Eq. 10 written separately from this oracle
+# before it existed; they pin the absolute level of E (a uniform factor, a
+# wrong area weight or a wrong exponent shifts them), which the convergence
+# ratio of the test above cannot see.
+ICOSPHERE_ENERGIES_P6 = {1: 3.07657, 2: 2.61306, 3: 2.50407, 4: 2.47678}
+
+
+@pytest.mark.parametrize("lvl", [1, 2, 3, 4])
+def test_energy_unit_icospheres_stored_values(lvl):
+    V, F = icosphere(lvl)
+    assert O.energy(V, F) == pytest.approx(ICOSPHERE_ENERGIES_P6[lvl], abs=6e-6)
+
+
 def test_energy_rigid_invariance_and_scaling():
     V, F = small_mesh("ico2", seed=3)
     E = O.energy(V, F)
