@@ -137,15 +137,62 @@ typedef struct tp_kernel_stat {
 
 typedef struct tp_mesh tp_mesh;
 
+/* A library context: one CUDA device and the allocator that supplies the
+ * device memory of the meshes created in it (their positions, face tables,
+ * BVH, Laplacian, factor and workspaces). The paper's problem statement (a
+ * mesh, its energy and the step, §3, §5.4) does not involve one; it is the
+ * ownership boundary of the library's memory. */
+typedef struct tp_ctx tp_ctx;
+
+/* Caller-set allocator of a context. alloc returns `bytes` of device memory
+ * on `device`, aligned to 256 bytes, or NULL (the library call then fails
+ * with TP_ERR_OOM); free returns a block obtained from alloc with the size it
+ * was asked for. The library synchronises the device before each free, so a
+ * freed block may be handed to other work at once. Both are called on the
+ * thread of the library call that needs the memory; `user` is passed
+ * through. Buffers grow and are freed rarely: when a mesh first needs a
+ * workspace, when a larger one is needed, and in tp_mesh_destroy. */
+typedef struct tp_allocator {
+    void* (*alloc)(size_t bytes, int device, void* user);
+    void (*free)(void* ptr, size_t bytes, int device, void* user);
+    void* user;
+} tp_allocator;
+
+/* Create a context on CUDA device `device` with the default allocator
+ * (cudaMalloc / cudaFree). TP_ERR_INVALID_ARG for a device that does not
+ * exist. */
+int tp_create(int device, tp_ctx** out);
+
+/* Destroy a context. TP_ERR_INVALID_ARG while meshes created in it are
+ * alive (destroy them first). Accepts NULL. */
+int tp_destroy(tp_ctx* ctx);
+
+/* Set the allocator of a context (alloc = free = NULL restores cudaMalloc /
+ * cudaFree). TP_ERR_INVALID_ARG while meshes created in it are alive, or for
+ * a half-set pair. */
+int tp_ctx_set_allocator(tp_ctx* ctx, const tp_allocator* a);
+
+/* Device bytes a context's meshes hold now and at most so far (host
+ * integers; either pointer may be NULL). */
+int tp_ctx_memory(const tp_ctx* ctx, size_t* in_use, size_t* peak);
+
+/* tp_mesh_create in a context: the mesh's device memory comes from the
+ * context's allocator, on the context's device. */
+int tp_mesh_create_ctx(tp_ctx* ctx, int nv, int nf, const double* pos,
+                       const int32_t* faces, int ptr_kind, void* stream,
+                       tp_mesh** out);
+
 /* Fill *p with the defaults: p=6, theta=0, leaf_size=8, FP32 pairs,
  * full BH differential, krylov_tol=1e-6, krylov_max=200, restart 30,
  * cg_tol=1e-6, cg_max=20000, Armijo c=1e-4, shrink 0.5, tau0=1, ls_max=30,
  * proj_iters=1, Cholesky Poisson solver, prec_self_weight=24. */
 void tp_params_default(tp_params* p);
 
-/* Create a mesh on CUDA device `device` from nv positions and nf faces.
- * Validates the face indices (TP_ERR_INVALID_ARG) and the geometry
- * (TP_ERR_DEGENERATE). Allocates all device state of the mesh. */
+/* Create a mesh on CUDA device `device` from nv positions and nf faces
+ * (the mesh M = (V, E, F) and embedding f of §3.1), in the device's default
+ * context (cudaMalloc). Validates the face indices (TP_ERR_INVALID_ARG) and
+ * the geometry (TP_ERR_DEGENERATE). Allocates the device state of the mesh;
+ * workspaces are added on first use. */
 int tp_mesh_create(int device, int nv, int nf, const double* pos,
                    const int32_t* faces, int ptr_kind, void* stream,
                    tp_mesh** out);

@@ -28,7 +28,8 @@ __all__ = [
     "lib_path", "lib", "tp_kernel_stat", "tp_profile_enable", "tp_profile_read", "tp_launch_count",
     "tp_energy_noalloc", "tp_chol_info", "cotan_factor_info", "TP_POISSON_CHOLESKY", "TP_POISSON_CG",
     "tp_obstacle_set", "tp_obstacle_energy", "tp_pins_set", "TP_MAX_PINS", "tp_willmore_set",
-    "tp_willmore_energy", "tp_selftest_wait",
+    "tp_willmore_energy", "tp_selftest_wait", "Context", "tp_allocator", "tp_create", "tp_destroy",
+    "tp_ctx_set_allocator", "tp_ctx_memory", "tp_mesh_create_ctx",
 ]
 
 TP_OK, TP_ERR_INVALID_ARG, TP_ERR_DEGENERATE, TP_ERR_OOM = 0, 1, 2, 3
@@ -86,6 +87,14 @@ class tp_kernel_stat(ctypes.Structure):
                 ("units", ctypes.c_double), ("columns", ctypes.c_double)]
 
 
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p)
+
+
+class tp_allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("user", ctypes.c_void_p)]
+
+
 _lib = None
 
 
@@ -108,6 +117,11 @@ def lib():
     sig = {
         "tp_params_default": (None, [P(tp_params)]),
         "tp_mesh_create": (c_int, [c_int, c_int, c_int, vp, vp, c_int, vp, P(vp)]),
+        "tp_mesh_create_ctx": (c_int, [vp, c_int, c_int, vp, vp, c_int, vp, P(vp)]),
+        "tp_create": (c_int, [c_int, P(vp)]),
+        "tp_destroy": (c_int, [vp]),
+        "tp_ctx_set_allocator": (c_int, [vp, P(tp_allocator)]),
+        "tp_ctx_memory": (c_int, [vp, P(c_size), P(c_size)]),
         "tp_mesh_set_positions": (c_int, [vp, vp, c_int, vp]),
         "tp_mesh_get_positions": (c_int, [vp, vp, c_int, vp]),
         "tp_mesh_destroy": (c_int, [vp]),
@@ -207,11 +221,101 @@ def _empty_like_kind(ref, shape, dtype=np.float64):
 # C ABI, same names
 # ---------------------------------------------------------------------------
 
-class Mesh:
-    """Owns a tp_mesh handle (positions, face tables, BVH, Laplacian on the GPU)."""
+class Context:
+    """Owns a tp_ctx: a device and the allocator of its meshes' device memory.
 
-    def __init__(self, positions, faces, device: int = 0):
-        self.handle = tp_mesh_create(positions, faces, device)
+    allocator=None keeps cudaMalloc / cudaFree. allocator="torch" takes the
+    memory from PyTorch's caching allocator on that device, so the library's
+    workspaces share one pool with the caller's tensors."""
+
+    def __init__(self, device: int = 0, allocator=None):
+        self.device = device
+        self.handle = tp_create(device)
+        self._cb = None
+        if allocator == "torch":
+            self.set_torch_allocator()
+        elif allocator is not None:
+            raise ValueError("allocator must be None or 'torch'")
+
+    def set_torch_allocator(self):
+        torch = _torch()
+
+        def _alloc(nbytes, device, user):
+            try:
+                with torch.cuda.device(device):
+                    return int(torch.cuda.caching_allocator_alloc(int(nbytes), device,
+                                                                  torch.cuda.current_stream(device)))
+            except Exception:
+                return None
+
+        def _free(ptr, nbytes, device, user):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        cb = (_ALLOC_FN(_alloc), _FREE_FN(_free))
+        a = tp_allocator(cb[0], cb[1], None)
+        _check(lib().tp_ctx_set_allocator(self.handle, ctypes.byref(a)))
+        self._cb = cb          # the callbacks must outlive the context
+
+    def memory(self):
+        """(bytes in use, peak bytes) of the context's meshes."""
+        return tp_ctx_memory(self)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _check(lib().tp_destroy(self.handle))
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def tp_create(device: int = 0):
+    h = ctypes.c_void_p()
+    _check(lib().tp_create(int(device), ctypes.byref(h)))
+    return h
+
+
+def tp_destroy(ctx: Context):
+    ctx.close()
+
+
+def tp_ctx_set_allocator(ctx: Context, allocator=None):
+    """allocator: None (cudaMalloc) or 'torch' (PyTorch's caching allocator)."""
+    if allocator == "torch":
+        ctx.set_torch_allocator()
+    elif allocator is None:
+        _check(lib().tp_ctx_set_allocator(ctx.handle, None))
+        ctx._cb = None
+    else:
+        raise ValueError("allocator must be None or 'torch'")
+
+
+def tp_ctx_memory(ctx: Context):
+    a, b = ctypes.c_size_t(), ctypes.c_size_t()
+    _check(lib().tp_ctx_memory(ctx.handle, ctypes.byref(a), ctypes.byref(b)))
+    return int(a.value), int(b.value)
+
+
+class Mesh:
+    """Owns a tp_mesh handle (positions, face tables, BVH, Laplacian on the GPU),
+    in the device's default context or in the given Context."""
+
+    def __init__(self, positions, faces, device: int = 0, ctx: Context | None = None):
+        if ctx is not None:
+            self.handle = tp_mesh_create_ctx(ctx, positions, faces)
+            device = ctx.device
+        else:
+            self.handle = tp_mesh_create(positions, faces, device)
+        self.ctx = ctx          # keeps the context alive while the mesh is
         self.nv = int(np.shape(positions)[0])
         self.nf = int(np.shape(faces)[0])
         self.device = device
@@ -248,6 +352,17 @@ def tp_mesh_create(positions, faces, device: int = 0):
     h = ctypes.c_void_p()
     nv, nf = int(np.shape(positions)[0]), int(np.shape(faces)[0])
     _check(lib().tp_mesh_create(device, nv, nf, pp, fp, pk, _stream_ptr(positions), ctypes.byref(h)))
+    return h
+
+
+def tp_mesh_create_ctx(ctx: Context, positions, faces):
+    pp, pk, keep_p = _as_buffer(positions, np.float64)
+    fp, fk, keep_f = _as_buffer(faces, np.int32)
+    if pk != fk:
+        raise ValueError("positions and faces must both be host or both be device arrays")
+    h = ctypes.c_void_p()
+    nv, nf = int(np.shape(positions)[0]), int(np.shape(faces)[0])
+    _check(lib().tp_mesh_create_ctx(ctx.handle, nv, nf, pp, fp, pk, _stream_ptr(positions), ctypes.byref(h)))
     return h
 
 

@@ -11,16 +11,22 @@ using namespace tp;
 
 namespace {
 
-// selects the mesh's device for the duration of a call and restores the
+// selects the mesh's device (and the mesh's context, whose allocator serves
+// the buffers the call grows) for the duration of a call and restores the
 // caller's current device afterwards
 struct DeviceGuard {
     int prev = -1;
     bool ok = true;
-    explicit DeviceGuard(int dev) {
+    tp_ctx* prev_ctx = nullptr;
+    explicit DeviceGuard(int dev, tp_ctx* ctx = nullptr) {
         if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
         if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+        prev_ctx = current_ctx();
+        current_ctx() = ctx ? ctx : default_ctx(dev);
     }
+    explicit DeviceGuard(const tp_mesh* m) : DeviceGuard(m->device, m->ctx) {}
     ~DeviceGuard() {
+        current_ctx() = prev_ctx;
         int cur = -1;
         if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
     }
@@ -98,18 +104,80 @@ void tp_params_default(tp_params* p) {
 
 const char* tp_last_error(void) { return tp::last_error(); }
 
+static int device_exists(int device) {
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev || device >= 64)
+        return fail(TP_ERR_INVALID_ARG, "no such CUDA device");
+    return TP_OK;
+}
+
+int tp_create(int device, tp_ctx** out) {
+    set_error("");
+    if (!out) return fail(TP_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    TP_TRY(device_exists(device));
+    tp_ctx* c = new tp_ctx();
+    c->device = device;
+    *out = c;
+    return TP_OK;
+}
+
+int tp_destroy(tp_ctx* ctx) {
+    set_error("");
+    if (!ctx) return TP_OK;
+    if (ctx->is_default) return fail(TP_ERR_INVALID_ARG, "the default context of a device is not destroyed");
+    if (ctx->meshes.load() != 0)
+        return fail(TP_ERR_INVALID_ARG, std::to_string(ctx->meshes.load()) + " mesh(es) of the context are alive");
+    delete ctx;
+    return TP_OK;
+}
+
+int tp_ctx_set_allocator(tp_ctx* ctx, const tp_allocator* a) {
+    set_error("");
+    if (!ctx) return fail(TP_ERR_INVALID_ARG, "ctx is NULL");
+    if (ctx->is_default) return fail(TP_ERR_INVALID_ARG, "the default context keeps cudaMalloc; use tp_create");
+    if (ctx->meshes.load() != 0)
+        return fail(TP_ERR_INVALID_ARG, "the allocator cannot change while meshes of the context are alive");
+    if (a && ((a->alloc == nullptr) != (a->free == nullptr)))
+        return fail(TP_ERR_INVALID_ARG, "alloc and free must both be set or both be NULL");
+    if (!a || !a->alloc) {
+        ctx->custom = false;
+        ctx->al = tp_allocator{};
+    } else {
+        ctx->custom = true;
+        ctx->al = *a;
+    }
+    return TP_OK;
+}
+
+int tp_ctx_memory(const tp_ctx* ctx, size_t* in_use, size_t* peak) {
+    set_error("");
+    if (!ctx) return fail(TP_ERR_INVALID_ARG, "ctx is NULL");
+    if (in_use) *in_use = (size_t)std::max(0LL, ctx->in_use.load());
+    if (peak) *peak = (size_t)std::max(0LL, ctx->peak.load());
+    return TP_OK;
+}
+
 int tp_mesh_create(int device, int nv, int nf, const double* pos, const int32_t* faces, int ptr_kind,
                    void* stream, tp_mesh** out) {
     set_error("");
-    if (!out || !pos || !faces) return fail(TP_ERR_INVALID_ARG, "NULL argument");
+    if (!out) return fail(TP_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    TP_TRY(device_exists(device));
+    return tp_mesh_create_ctx(default_ctx(device), nv, nf, pos, faces, ptr_kind, stream, out);
+}
+
+int tp_mesh_create_ctx(tp_ctx* ctx, int nv, int nf, const double* pos, const int32_t* faces, int ptr_kind,
+                       void* stream, tp_mesh** out) {
+    set_error("");
+    if (!ctx || !out || !pos || !faces) return fail(TP_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     TP_TRY(check_kind(ptr_kind));
     if (nv < 3 || nf < 1) return fail(TP_ERR_INVALID_ARG, "need nv >= 3 and nf >= 1");
     if ((long long)nf * 3 > (1LL << 30)) return fail(TP_ERR_INVALID_ARG, "too many faces");
-    int ndev = 0;
-    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
-        return fail(TP_ERR_INVALID_ARG, "no such CUDA device");
-    DeviceGuard g(device);
+    const int device = ctx->device;
+    TP_TRY(device_exists(device));
+    DeviceGuard g(device, ctx);
     if (!g.ok) return fail(TP_ERR_CUDA, "cudaSetDevice failed");
     cudaStream_t st = (cudaStream_t)stream;
     // faces on the host for validation and the incidence structures
@@ -136,6 +204,8 @@ int tp_mesh_create(int device, int nv, int nf, const double* pos, const int32_t*
         for (int e = 0; e < 3 * nf; ++e) vidx[fill[F[e]]++] = e;
     }
     tp_mesh* m = new tp_mesh();
+    m->ctx = ctx;
+    ctx->meshes++;
     m->device = device;
     m->nv = nv;
     m->nf = nf;
@@ -169,7 +239,7 @@ int tp_mesh_set_positions(tp_mesh* m, const double* pos, int ptr_kind, void* str
     TP_TRY(check_mesh(m));
     TP_TRY(check_kind(ptr_kind));
     if (!pos) return fail(TP_ERR_INVALID_ARG, "pos is NULL");
-    DeviceGuard g(m->device);
+    DeviceGuard g(m);
     cudaStream_t st = (cudaStream_t)stream;
     TP_TRY(copy_in(m->pos.ptr, pos, sizeof(double) * 3 * (size_t)m->nv, ptr_kind, st));
     return refresh_geometry(m, st);
@@ -180,13 +250,13 @@ int tp_mesh_get_positions(tp_mesh* m, double* pos, int ptr_kind, void* stream) {
     TP_TRY(check_mesh(m));
     TP_TRY(check_kind(ptr_kind));
     if (!pos) return fail(TP_ERR_INVALID_ARG, "pos is NULL");
-    DeviceGuard g(m->device);
+    DeviceGuard g(m);
     return copy_out(pos, m->pos.ptr, sizeof(double) * 3 * (size_t)m->nv, ptr_kind, (cudaStream_t)stream);
 }
 
 int tp_mesh_destroy(tp_mesh* m) {
     if (!m) return TP_OK;
-    DeviceGuard g(m->device);
+    DeviceGuard g(m);
     Buf* all[] = {&m->faces, &m->vf_ptr, &m->vf_idx, &m->vcomp, &m->comp_ptr, &m->comp_verts, &m->pos, &m->center, &m->errflag, &m->f32a, &m->f32b,
                   &m->f32c, &m->tilebox,
                   &m->f64a, &m->f64b, &m->fgrad, &m->rowptr, &m->col, &m->cotsrc, &m->diagpos, &m->val,
@@ -203,6 +273,7 @@ int tp_mesh_destroy(tp_mesh* m) {
     for (auto& b : m->tmpv) release(b);
     for (auto& b : m->stepv) release(b);
     for (auto& b : m->prec) release(b);
+    if (m->ctx) m->ctx->meshes--;
     delete m;
     return TP_OK;
 }
@@ -234,7 +305,7 @@ int tp_energy(tp_mesh* m, const tp_params* p, double* E_out, void* stream) {
     TP_TRY(check_mesh(m));
     TP_TRY(check_params(p));
     if (!E_out) return fail(TP_ERR_INVALID_ARG, "E_out is NULL");
-    DeviceGuard g(m->device);
+    DeviceGuard g(m);
     return energy_value(m, p, E_out, (cudaStream_t)stream);
 }
 
@@ -246,7 +317,7 @@ int tp_energy_rows(tp_mesh* m, const tp_params* p, const int32_t* targets, int n
     TP_TRY(check_kind(ptr_kind));
     if (n < 0 || (n > 0 && (!targets || !rows))) return fail(TP_ERR_INVALID_ARG, "bad targets/rows");
     if (n == 0) return TP_OK;
-    DeviceGuard g(m->device);
+    DeviceGuard g(m);
     cudaStream_t st = (cudaStream_t)stream;
     if (ptr_kind == TP_PTR_HOST)
         for (int i = 0; i < n; ++i)
@@ -269,7 +340,7 @@ int tp_differential(tp_mesh* m, const tp_params* p, double* dE, int ptr_kind, do
     TP_TRY(check_params(p));
     TP_TRY(check_kind(ptr_kind));
     if (!dE) return fail(TP_ERR_INVALID_ARG, "dE is NULL");
-    DeviceGuard g(m->device);
+    DeviceGuard g(m);
     cudaStream_t st = (cudaStream_t)stream;
     size_t bytes = sizeof(double) * 3 * (size_t)m->nv;
     TP_TRY(ensure(m->io_out, bytes));
@@ -288,7 +359,7 @@ int fractional_apply(tp_mesh* m, const tp_params* p, int op, const double* v, in
     if (op < TP_OP_A || op > TP_OP_L) return fail(TP_ERR_INVALID_ARG, "unknown operator");
     if (k < 1 || k > 9) return fail(TP_ERR_INVALID_ARG, "k must be in 1..9");
     if (!v || !y) return fail(TP_ERR_INVALID_ARG, "NULL vector");
-    DeviceGuard g(m->device);
+    DeviceGuard g(m);
     cudaStream_t st = (cudaStream_t)stream;
     size_t bytes = sizeof(double) * (size_t)m->nv * k;
     const void* vin = nullptr;
@@ -308,7 +379,7 @@ int cotan_solve(tp_mesh* m, const tp_params* p, const double* b, int k, double* 
     TP_TRY(check_kind(ptr_kind));
     if (k < 1 || k > 9) return fail(TP_ERR_INVALID_ARG, "k must be in 1..9");
     if (!b || !z) return fail(TP_ERR_INVALID_ARG, "NULL vector");
-    DeviceGuard g(m->device);
+    DeviceGuard g(m);
     cudaStream_t st = (cudaStream_t)stream;
     size_t bytes = sizeof(double) * (size_t)m->nv * k;
     const void* bin = nullptr;
@@ -328,7 +399,7 @@ int cotan_factor_info(tp_mesh* m, tp_chol_info* out) {
     set_error("");
     TP_TRY(check_mesh(m));
     if (!out) return fail(TP_ERR_INVALID_ARG, "out is NULL");
-    DeviceGuard g(m->device);
+    DeviceGuard g(m);
     return chol_info(m, out);
 }
 
@@ -339,7 +410,7 @@ int precond_apply(tp_mesh* m, const tp_params* p, const double* b, int k, double
     TP_TRY(check_kind(ptr_kind));
     if (k < 1 || k > 9) return fail(TP_ERR_INVALID_ARG, "k must be in 1..9");
     if (!b || !z) return fail(TP_ERR_INVALID_ARG, "NULL vector");
-    DeviceGuard g(m->device);
+    DeviceGuard g(m);
     cudaStream_t st = (cudaStream_t)stream;
     size_t bytes = sizeof(double) * (size_t)m->nv * k;
     const void* bin = nullptr;
@@ -363,7 +434,7 @@ int precond_step(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp_ste
     if (p->krylov_max < 1 || p->cg_max < 1 || p->ls_max < 1 || p->proj_iters < 0 || p->proj_iters > 100 ||
         !(p->armijo_shrink > 0.0 && p->armijo_shrink < 1.0))
         return fail(TP_ERR_INVALID_ARG, "bad solver parameters");
-    DeviceGuard g(m->device);
+    DeviceGuard g(m);
     return precond_step_dev(m, p, c, rep, (cudaStream_t)stream);
 }
 
@@ -374,7 +445,7 @@ int tp_obstacle_set(tp_mesh* m, int nv, int nf, const double* pos, const int32_t
     TP_TRY(check_kind(ptr_kind));
     if (nf < 0 || nv < 0) return fail(TP_ERR_INVALID_ARG, "negative obstacle size");
     if (!std::isfinite(weight) || weight < 0.0) return fail(TP_ERR_INVALID_ARG, "weight must be finite and >= 0");
-    DeviceGuard g(m->device);
+    DeviceGuard g(m);
     if (!g.ok) return fail(TP_ERR_CUDA, "cudaSetDevice failed");
     cudaStream_t st = (cudaStream_t)stream;
     if (nf == 0) {
@@ -383,7 +454,7 @@ int tp_obstacle_set(tp_mesh* m, int nv, int nf, const double* pos, const int32_t
         return TP_OK;
     }
     tp_mesh* o = nullptr;
-    TP_TRY(tp_mesh_create(m->device, nv, nf, pos, faces, ptr_kind, stream, &o));
+    TP_TRY(tp_mesh_create_ctx(m->ctx, nv, nf, pos, faces, ptr_kind, stream, &o));
     TP_CUDA(cudaStreamSynchronize(st));
     TP_TRY(obstacle_attach(m, o, weight, st));
     TP_CUDA(cudaStreamSynchronize(st));
@@ -403,7 +474,7 @@ int tp_willmore_energy(tp_mesh* m, double* E_out, double* dE, int ptr_kind, void
     TP_TRY(check_mesh(m));
     TP_TRY(check_kind(ptr_kind));
     if (!E_out && !dE) return fail(TP_ERR_INVALID_ARG, "E_out and dE are both NULL");
-    DeviceGuard g(m->device);
+    DeviceGuard g(m);
     cudaStream_t st = (cudaStream_t)stream;
     TP_TRY(ensure(m->rowsum, sizeof(double) * 8));
     const size_t bytes = sizeof(double) * 3 * (size_t)m->nv;
@@ -428,7 +499,7 @@ int tp_pins_set(tp_mesh* m, int n, const int32_t* vertices, int ptr_kind, void* 
     TP_TRY(check_kind(ptr_kind));
     if (n < 0 || n > TP_MAX_PINS) return fail(TP_ERR_INVALID_ARG, "n must be in 0..TP_MAX_PINS");
     if (n > 0 && !vertices) return fail(TP_ERR_INVALID_ARG, "vertices is NULL");
-    DeviceGuard g(m->device);
+    DeviceGuard g(m);
     cudaStream_t st = (cudaStream_t)stream;
     std::vector<int> idx(n);
     if (n > 0) {
@@ -448,7 +519,7 @@ int tp_obstacle_energy(tp_mesh* m, const tp_params* p, double* E_out, double* dE
     TP_TRY(check_params(p));
     TP_TRY(check_kind(ptr_kind));
     if (!m->obs) return fail(TP_ERR_INVALID_ARG, "no obstacle is set on this mesh");
-    DeviceGuard g(m->device);
+    DeviceGuard g(m);
     cudaStream_t st = (cudaStream_t)stream;
     TP_TRY(ensure(m->erow, sizeof(double) * m->nf));
     TP_TRY(ensure(m->rowsum, sizeof(double) * 8));
@@ -482,7 +553,7 @@ int tp_profile_read(tp_mesh* m, tp_kernel_stat* out, int max, int* n) {
     set_error("");
     TP_TRY(check_mesh(m));
     if (!n || (max > 0 && !out)) return fail(TP_ERR_INVALID_ARG, "NULL output");
-    DeviceGuard g(m->device);
+    DeviceGuard g(m);
     static const char* names[PK_COUNT] = {"energy_direct", "diff_direct", "apply_A", "apply_B", "apply_B0",
                                           "apply_L", "bh_energy", "bh_diff", "bvh_build", "cg",
                                           "chol_factor", "chol_solve", "bh_apply", "obstacle_direct",

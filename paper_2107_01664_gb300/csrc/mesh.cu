@@ -4,6 +4,8 @@
 #include <cstring>
 
 #include "host_util.h"
+#include <mutex>
+
 #include "tp_internal.cuh"
 
 namespace tp {
@@ -18,27 +20,78 @@ int fail(int code, const std::string& msg) {
     return code;
 }
 
+static thread_local tp_ctx* g_current_ctx = nullptr;
+
+tp_ctx*& current_ctx() { return g_current_ctx; }
+
+tp_ctx* default_ctx(int device) {
+    static std::mutex mu;
+    static tp_ctx* ctxs[64] = {nullptr};
+    if (device < 0 || device >= 64) return nullptr;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ctxs[device]) {
+        ctxs[device] = new tp_ctx();
+        ctxs[device]->device = device;
+        ctxs[device]->is_default = true;
+    }
+    return ctxs[device];
+}
+
+static void ctx_free(tp_ctx* c, void* ptr, size_t bytes) {
+    if (!ptr) return;
+    if (c && c->custom) {
+        // the caller's allocator may hand the block to other work at once:
+        // the work that used it must be over (cudaFree gives this itself)
+        cudaDeviceSynchronize();
+        c->al.free(ptr, bytes, c->device, c->al.user);
+    } else {
+        cudaFree(ptr);
+    }
+    if (c) c->in_use -= (long long)bytes;
+}
+
 int ensure(Buf& b, size_t bytes) {
     if (bytes <= b.bytes && b.ptr) return TP_OK;
-    if (b.ptr) cudaFree(b.ptr);
+    ctx_free(b.ctx, b.ptr, b.bytes);
     b.ptr = nullptr;
     b.bytes = 0;
-    size_t want = bytes < 256 ? 256 : bytes;
-    cudaError_t e = cudaMalloc(&b.ptr, want);
-    if (e != cudaSuccess) {
-        b.ptr = nullptr;
-        cudaGetLastError();
-        return fail(TP_ERR_OOM, std::string("cudaMalloc(") + std::to_string(want) +
-                                    "): " + cudaGetErrorString(e));
+    b.ctx = nullptr;
+    size_t want = bytes < 256 ? 256 : (bytes + 255) / 256 * 256;
+    tp_ctx* c = current_ctx();
+    if (c && c->custom) {
+        b.ptr = c->al.alloc(want, c->device, c->al.user);
+        if (!b.ptr)
+            return fail(TP_ERR_OOM, "the context's allocator returned NULL for " + std::to_string(want) + " bytes");
+        if (reinterpret_cast<uintptr_t>(b.ptr) % 256 != 0) {
+            c->al.free(b.ptr, want, c->device, c->al.user);
+            b.ptr = nullptr;
+            return fail(TP_ERR_INVALID_ARG, "the context's allocator returned memory not aligned to 256 bytes");
+        }
+    } else {
+        cudaError_t e = cudaMalloc(&b.ptr, want);
+        if (e != cudaSuccess) {
+            b.ptr = nullptr;
+            cudaGetLastError();
+            return fail(TP_ERR_OOM, std::string("cudaMalloc(") + std::to_string(want) +
+                                        "): " + cudaGetErrorString(e));
+        }
     }
     b.bytes = want;
+    b.ctx = c;
+    if (c) {
+        const long long now = (c->in_use += (long long)want);
+        long long pk = c->peak.load();
+        while (now > pk && !c->peak.compare_exchange_weak(pk, now)) {
+        }
+    }
     return TP_OK;
 }
 
 void release(Buf& b) {
-    if (b.ptr) cudaFree(b.ptr);
+    ctx_free(b.ctx, b.ptr, b.bytes);
     b.ptr = nullptr;
     b.bytes = 0;
+    b.ctx = nullptr;
 }
 
 int sm_count() {

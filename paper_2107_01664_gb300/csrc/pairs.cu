@@ -229,7 +229,7 @@ struct Grid {
 };
 
 // resident blocks per SM of a kernel (cached per kernel and device)
-static int resident_per_sm(const void* fn, int threads) {
+static int resident_per_sm(const void* fn, int threads, size_t dyn_smem = 0) {
     static std::mutex mu;
     static std::map<std::pair<const void*, int>, int> cache;
     int dev = 0;
@@ -239,7 +239,12 @@ static int resident_per_sm(const void* fn, int threads) {
     auto it = cache.find(key);
     if (it != cache.end()) return it->second;
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, 0) != cudaSuccess || n < 1) {
+    if (dyn_smem > 48 * 1024 &&
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;   // the kernel cannot be launched with this much shared memory
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, threads, dyn_smem) != cudaSuccess || n < 1) {
         cudaGetLastError();
         n = 1;
     }
@@ -1048,6 +1053,378 @@ k_apply(const typename V4T<T>::type* __restrict__ fa, const typename V4T<T>::typ
                 part[((size_t)blockIdx.y * L::NA + i) * nf + tid[j]] = acc[j][i / 2].value(i & 1);
 }
 
+// ---- 9-column products with two targets per thread -------------------------
+// The FP32 path of the 9-column products (the lockstep solver applies A and
+// L^{2-s} to three right-hand sides at once) takes two targets per thread.
+// The kernel value of a (target, source) pair is evaluated for both targets
+// in packed f32x2 arithmetic, from source geometry staged pre-broadcast in
+// shared memory ({x,x}, {y,y}, ...), and each source vector X is read from
+// shared memory once for both targets. The per-chunk FP32 sums stay in
+// registers; the Kahan pairs that carry them across chunks live in shared
+// memory (one float4 {s.x, s.y, c.x, c.y} per thread, target and accumulator
+// pair), which keeps the registers for the two targets' chunk sums. Tiles
+// near the block's targets or holding them take the careful scalar path of
+// k_apply (compensated differences, self-pair test). Partial sums leave as
+// FP32 Kahan pairs (s, c), one per split.
+
+constexpr int WT = 2;   // targets per thread of the wide kernel
+
+// packed kernel values of one source for two targets (lanes): hB = |d|^{-2s}
+// (= (|d|^2)^{-s}), h0 = (k2(S;T) + k2(T;S)) / 2 * hB (LOW operators), hL =
+// |d|^{-2(3-s)} (operator L, returned in hB). t* / n*: the two targets'
+// barycenters and normals; s* / m*: the source's barycenter and normal in both
+// lanes; eps: the |d|^2 offset; ne: minus the exponent; half: 0.5 in both lanes.
+// d = X_target - X_source as packed pairs; with COMP (tiles near the block's
+// targets) plus the difference of the low parts of the barycenters,
+// (hi_T - hi_S) + (lo_T - lo_S), as in the scalar careful path
+template <bool COMP>
+__device__ __forceinline__ void wide_diff2(unsigned long long tx, unsigned long long ty, unsigned long long tz,
+                                           unsigned long long sx, unsigned long long sy, unsigned long long sz,
+                                           unsigned long long lx, unsigned long long ly, unsigned long long lz,
+                                           unsigned long long ux, unsigned long long uy, unsigned long long uz,
+                                           unsigned long long& dx, unsigned long long& dy, unsigned long long& dz) {
+    if constexpr (COMP) {
+        asm("{\n\t.reg .b64 ex, ey, ez;\n\t"
+            "sub.rn.f32x2 %0, %3, %6;\n\t"
+            "sub.rn.f32x2 %1, %4, %7;\n\t"
+            "sub.rn.f32x2 %2, %5, %8;\n\t"
+            "sub.rn.f32x2 ex, %9, %12;\n\t"
+            "sub.rn.f32x2 ey, %10, %13;\n\t"
+            "sub.rn.f32x2 ez, %11, %14;\n\t"
+            "add.rn.f32x2 %0, %0, ex;\n\t"
+            "add.rn.f32x2 %1, %1, ey;\n\t"
+            "add.rn.f32x2 %2, %2, ez;\n\t}"
+            : "=l"(dx), "=l"(dy), "=l"(dz)
+            : "l"(tx), "l"(ty), "l"(tz), "l"(sx), "l"(sy), "l"(sz), "l"(lx), "l"(ly), "l"(lz), "l"(ux), "l"(uy),
+              "l"(uz));
+    } else {
+        asm("sub.rn.f32x2 %0, %3, %6;\n\t"
+            "sub.rn.f32x2 %1, %4, %7;\n\t"
+            "sub.rn.f32x2 %2, %5, %8;"
+            : "=l"(dx), "=l"(dy), "=l"(dz)
+            : "l"(tx), "l"(ty), "l"(tz), "l"(sx), "l"(sy), "l"(sz));
+    }
+}
+
+template <bool LOW>
+__device__ __forceinline__ void wide_kernel2(unsigned long long dx_, unsigned long long dy_, unsigned long long dz_,
+                                             unsigned long long nx, unsigned long long ny, unsigned long long nz,
+                                             unsigned long long mx, unsigned long long my, unsigned long long mz,
+                                             unsigned long long eps, unsigned long long ne, unsigned long long half,
+                                             unsigned long long& hb, unsigned long long& h0) {
+    if constexpr (LOW) {
+        asm("{\n\t.reg .b64 dx, dy, dz, r2, lg, ir2, ts, tt;\n\t.reg .f32 lo, hi;\n\t"
+            "mov.b64 dx, %2;\n\t"
+            "mov.b64 dy, %3;\n\t"
+            "mov.b64 dz, %4;\n\t"
+            "fma.rn.f32x2 r2, dz, dz, %14;\n\t"
+            "fma.rn.f32x2 r2, dy, dy, r2;\n\t"
+            "fma.rn.f32x2 r2, dx, dx, r2;\n\t"
+            "mov.b64 {lo, hi}, r2;\n\t"
+            "lg2.approx.ftz.f32 lo, lo;\n\t"
+            "lg2.approx.ftz.f32 hi, hi;\n\t"
+            "mov.b64 lg, {lo, hi};\n\t"
+            "mul.rn.f32x2 lg, lg, %15;\n\t"
+            "mov.b64 {lo, hi}, lg;\n\t"
+            "ex2.approx.ftz.f32 lo, lo;\n\t"
+            "ex2.approx.ftz.f32 hi, hi;\n\t"
+            "mov.b64 %0, {lo, hi};\n\t"
+            "mov.b64 {lo, hi}, r2;\n\t"
+            "rcp.approx.ftz.f32 lo, lo;\n\t"
+            "rcp.approx.ftz.f32 hi, hi;\n\t"
+            "mov.b64 ir2, {lo, hi};\n\t"
+            "mul.rn.f32x2 ts, %7, dz;\n\t"
+            "fma.rn.f32x2 ts, %6, dy, ts;\n\t"
+            "fma.rn.f32x2 ts, %5, dx, ts;\n\t"
+            "mul.rn.f32x2 ts, ts, ir2;\n\t"
+            "mul.rn.f32x2 tt, %13, dz;\n\t"
+            "fma.rn.f32x2 tt, %12, dy, tt;\n\t"
+            "fma.rn.f32x2 tt, %11, dx, tt;\n\t"
+            "mul.rn.f32x2 tt, tt, ir2;\n\t"
+            "mul.rn.f32x2 tt, tt, tt;\n\t"
+            "fma.rn.f32x2 tt, ts, ts, tt;\n\t"
+            "mul.rn.f32x2 tt, tt, %16;\n\t"
+            "mul.rn.f32x2 %1, tt, %0;\n\t}"
+            : "=l"(hb), "=l"(h0)
+            : "l"(dx_), "l"(dy_), "l"(dz_), "l"(nx), "l"(ny), "l"(nz), "l"(0ull), "l"(0ull), "l"(0ull), "l"(mx),
+              "l"(my), "l"(mz), "l"(eps), "l"(ne), "l"(half));
+    } else {
+        asm("{\n\t.reg .b64 dx, dy, dz, r2, lg;\n\t.reg .f32 lo, hi;\n\t"
+            "mov.b64 dx, %1;\n\t"
+            "mov.b64 dy, %2;\n\t"
+            "mov.b64 dz, %3;\n\t"
+            "fma.rn.f32x2 r2, dz, dz, %7;\n\t"
+            "fma.rn.f32x2 r2, dy, dy, r2;\n\t"
+            "fma.rn.f32x2 r2, dx, dx, r2;\n\t"
+            "mov.b64 {lo, hi}, r2;\n\t"
+            "lg2.approx.ftz.f32 lo, lo;\n\t"
+            "lg2.approx.ftz.f32 hi, hi;\n\t"
+            "mov.b64 lg, {lo, hi};\n\t"
+            "mul.rn.f32x2 lg, lg, %8;\n\t"
+            "mov.b64 {lo, hi}, lg;\n\t"
+            "ex2.approx.ftz.f32 lo, lo;\n\t"
+            "ex2.approx.ftz.f32 hi, hi;\n\t"
+            "mov.b64 %0, {lo, hi};\n\t}"
+            : "=l"(hb)
+            : "l"(dx_), "l"(dy_), "l"(dz_), "l"(0ull), "l"(0ull), "l"(0ull), "l"(eps), "l"(ne));
+        h0 = 0ull;
+    }
+}
+
+// shared memory of the wide kernel (float4 units): broadcast geometry
+// [NT][3], broadcast low parts [NT][2], source vectors [NT][NW4], Kahan pairs
+// [NP][WT][NT]
+template <int OP>
+constexpr size_t wide_smem_bytes() {
+    using L = OpLayout<OP, 9>;
+    return sizeof(float4) * ((size_t)NT * 3 + 2 * NT + (size_t)NT * L::NW4 + (size_t)(L::NA / 2) * WT * NT);
+}
+
+// chunk of CHW sources of the wide kernel on the packed path: both targets'
+// kernel values at once, then the accumulations (COMP: compensated d)
+template <int OP, bool COMP, int CHW>
+__device__ __forceinline__ void wide_chunk(const float4* sg, const float4* sl, const float4* sw, int c0,
+                                           unsigned long long TX, unsigned long long TY, unsigned long long TZ,
+                                           unsigned long long LX, unsigned long long LY, unsigned long long LZ,
+                                           unsigned long long NXp, unsigned long long NYp, unsigned long long NZp,
+                                           unsigned long long EPS, unsigned long long NE, unsigned long long HALF,
+                                           float2 (&pt)[WT][OpLayout<OP, 9>::NA / 2]) {
+    using L = OpLayout<OP, 9>;
+    constexpr bool LOW = (OP == TP_OP_A || OP == TP_OP_B0);
+    constexpr int NP = L::NA / 2;
+    constexpr int NW4 = L::NW4;
+    const ulonglong2* sg2 = reinterpret_cast<const ulonglong2*>(sg);
+    const ulonglong2* sl2 = reinterpret_cast<const ulonglong2*>(sl);
+#pragma unroll 2
+    for (int q = 0; q < CHW; ++q) {
+        const int jj = c0 + q;
+        const ulonglong2 u0 = sg2[3 * jj], u1 = sg2[3 * jj + 1];
+        unsigned long long dx, dy, dz, HB, H0;
+        if constexpr (COMP) {
+            const ulonglong2 v0 = sl2[2 * jj], v1 = sl2[2 * jj + 1];
+            wide_diff2<true>(TX, TY, TZ, u0.x, u0.y, u1.x, LX, LY, LZ, v0.x, v0.y, v1.x, dx, dy, dz);
+        } else {
+            wide_diff2<false>(TX, TY, TZ, u0.x, u0.y, u1.x, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, dx, dy, dz);
+        }
+        if constexpr (LOW) {
+            const ulonglong2 u2 = sg2[3 * jj + 2];
+            wide_kernel2<true>(dx, dy, dz, NXp, NYp, NZp, u2.x, u2.y, u1.y, EPS, NE, HALF, HB, H0);
+        } else {
+            wide_kernel2<false>(dx, dy, dz, NXp, NYp, NZp, 0ull, 0ull, 0ull, EPS, NE, HALF, HB, H0);
+        }
+        const float2 hb = upk2(HB), h0 = upk2(H0);
+        float2 x2[2 * NW4];
+#pragma unroll
+        for (int i = 0; i < NW4; ++i) {
+            const float4 x = sw[jj * NW4 + i];
+            x2[2 * i] = make_float2(x.x, x.y);
+            x2[2 * i + 1] = make_float2(x.z, x.w);
+        }
+        if (OP == TP_OP_L) {
+#pragma unroll
+            for (int i = 0; i < NP; ++i) {
+                pt[0][i] = pfma(hb.x, x2[i], pt[0][i]);
+                pt[1][i] = pfma(hb.y, x2[i], pt[1][i]);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < L::NH / 2; ++i) {
+                pt[0][i] = pfma(hb.x, x2[i], pt[0][i]);
+                pt[1][i] = pfma(hb.y, x2[i], pt[1][i]);
+            }
+            if (LOW) {
+#pragma unroll
+                for (int i = L::NH / 2; i < NP; ++i) {
+                    pt[0][i] = pfma(h0.x, x2[i], pt[0][i]);
+                    pt[1][i] = pfma(h0.y, x2[i], pt[1][i]);
+                }
+            }
+        }
+    }
+}
+
+template <int OP, int CHW>
+__global__ void __launch_bounds__(NT, 2)
+k_apply_wide(const float4* __restrict__ fa, const float4* __restrict__ fb, const float4* __restrict__ flo,
+             const float4* __restrict__ tbox, const double* __restrict__ center, const float4* __restrict__ Wp,
+             int nf, int tiles_per_split, float s_exp, float l_exp, float2* __restrict__ part) {
+    using L = OpLayout<OP, 9>;
+    constexpr bool LOW = (OP == TP_OP_A || OP == TP_OP_B0);
+    constexpr int NP = L::NA / 2;
+    constexpr int NW4 = L::NW4;
+    extern __shared__ float4 wsm[];
+    float4* sg = wsm;                        // broadcast geometry: {x,x,y,y} {z,z,nz,nz} {nx,nx,ny,ny}
+    float4* sl = sg + 3 * NT;                // broadcast low parts (near tiles): {lx,lx,ly,ly} {lz,lz,0,0}
+    float4* sw = sl + 2 * NT;                // source vectors X
+    float4* kah = sw + NT * NW4;             // Kahan pairs {s.x, s.y, c.x, c.y}
+    __shared__ float sbox[6];
+    const int tid = threadIdx.x;
+    float tx[WT], ty[WT], tz[WT], nx[WT], ny[WT], nz[WT], lx[WT], ly[WT], lz[WT];
+    int tg[WT];
+    float bl[3] = {3e38f, 3e38f, 3e38f}, bh[3] = {-3e38f, -3e38f, -3e38f};
+#pragma unroll
+    for (int j = 0; j < WT; ++j) {
+        const int t = blockIdx.x * NT * WT + j * NT + tid;
+        tg[j] = t;
+        tx[j] = ty[j] = tz[j] = nx[j] = ny[j] = nz[j] = 0.f;
+        lx[j] = ly[j] = lz[j] = 0.f;
+        if (t < nf) {
+            const float4 A = fa[t];
+            tx[j] = A.x; ty[j] = A.y; tz[j] = A.z;
+            if (LOW) {
+                const float4 B = fb[t];
+                nx[j] = B.x; ny[j] = B.y; nz[j] = B.z;
+            }
+            const float4 Lo = flo[t];
+            lx[j] = Lo.x; ly[j] = Lo.y; lz[j] = Lo.z;
+            bl[0] = fminf(bl[0], A.x); bl[1] = fminf(bl[1], A.y); bl[2] = fminf(bl[2], A.z);
+            bh[0] = fmaxf(bh[0], A.x); bh[1] = fmaxf(bh[1], A.y); bh[2] = fmaxf(bh[2], A.z);
+        }
+    }
+    block_box(bl[0], bl[1], bl[2], bh[0], bh[1], bh[2], sbox);
+    const float thr2 = (float)center[3];
+    const unsigned long long TX = pk2(tx[0], tx[1]), TY = pk2(ty[0], ty[1]), TZ = pk2(tz[0], tz[1]);
+    const unsigned long long LX = pk2(lx[0], lx[1]), LY = pk2(ly[0], ly[1]), LZ = pk2(lz[0], lz[1]);
+    const unsigned long long NXp = pk2(nx[0], nx[1]), NYp = pk2(ny[0], ny[1]), NZp = pk2(nz[0], nz[1]);
+    const unsigned long long EPS = pk2(tiny_r2<float>(), tiny_r2<float>());
+    const float nexp = OP == TP_OP_L ? -l_exp : -s_exp;
+    const unsigned long long NE = pk2(nexp, nexp), HALF = pk2(0.5f, 0.5f);
+#pragma unroll
+    for (int i = 0; i < NP * WT; ++i) kah[i * NT + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int ntiles = (nf + NT - 1) / NT;
+    const int k0 = blockIdx.y * tiles_per_split;
+    const int k1 = min(k0 + tiles_per_split, ntiles);
+    for (int tile = k0; tile < k1; ++tile) {
+        const bool diag = tile >= (int)blockIdx.x * WT && tile < ((int)blockIdx.x + 1) * WT;
+        const bool near = tile_near(tbox, tile, sbox, thr2);
+        const int src = tile * NT + tid;
+        __syncthreads();
+        {
+            // sources past the end sit far away with zero vectors: finite zero terms
+            const float4 A = src < nf ? fa[src] : make_float4(1e18f, 0.f, 0.f, 0.f);
+            const float4 B = (LOW && src < nf) ? fb[src] : make_float4(0.f, 0.f, 0.f, 0.f);
+            sg[3 * tid] = make_float4(A.x, A.x, A.y, A.y);
+            sg[3 * tid + 1] = make_float4(A.z, A.z, B.z, B.z);
+            sg[3 * tid + 2] = make_float4(B.x, B.x, B.y, B.y);
+            if (near || diag) {
+                const float4 l = src < nf ? flo[src] : make_float4(0.f, 0.f, 0.f, 0.f);
+                sl[2 * tid] = make_float4(l.x, l.x, l.y, l.y);
+                sl[2 * tid + 1] = make_float4(l.z, l.z, 0.f, 0.f);
+            }
+        }
+        for (int i = tid; i < NT * NW4; i += NT) {
+            const int f = tile * NT + i / NW4;
+            sw[i] = f < nf ? Wp[(size_t)tile * NT * NW4 + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+        for (int c = 0; c < NT; c += CHW) {
+            float2 pt[WT][NP];
+#pragma unroll
+            for (int j = 0; j < WT; ++j)
+#pragma unroll
+                for (int i = 0; i < NP; ++i) pt[j][i] = make_float2(0.f, 0.f);
+            if (diag) {
+                // tiles holding the block's own targets: scalar careful path with
+                // the self-pair test
+                for (int q = 0; q < CHW; ++q) {
+                    const int jj = c + q;
+                    const float4 g0 = sg[3 * jj], g1 = sg[3 * jj + 1], g2 = sg[3 * jj + 2];
+                    const float4 l0 = sl[2 * jj], l1 = sl[2 * jj + 1];
+                    float2 wv[2 * NW4];
+#pragma unroll
+                    for (int i = 0; i < NW4; ++i) {
+                        const float4 x = sw[jj * NW4 + i];
+                        wv[2 * i] = make_float2(x.x, x.y);
+                        wv[2 * i + 1] = make_float2(x.z, x.w);
+                    }
+#pragma unroll
+                    for (int j = 0; j < WT; ++j)
+                        apply_term<float, OP, true, 9>((tx[j] - g0.x) + (lx[j] - l0.x), (ty[j] - g0.z) + (ly[j] - l0.z),
+                                                       (tz[j] - g1.x) + (lz[j] - l1.x), nx[j], ny[j], nz[j], g2.x,
+                                                       g2.z, g1.z, wv, s_exp, l_exp, pt[j]);
+                }
+            } else if (near) {
+                wide_chunk<OP, true, CHW>(sg, sl, sw, c, TX, TY, TZ, LX, LY, LZ, NXp, NYp, NZp, EPS, NE, HALF, pt);
+            } else {
+                wide_chunk<OP, false, CHW>(sg, sl, sw, c, TX, TY, TZ, LX, LY, LZ, NXp, NYp, NZp, EPS, NE, HALF, pt);
+            }
+            // chunk sums into the Kahan pairs in shared memory
+#pragma unroll
+            for (int j = 0; j < WT; ++j)
+#pragma unroll
+                for (int i = 0; i < NP; ++i) {
+                    float4& k = kah[(i * WT + j) * NT + tid];
+                    const float4 kv = k;
+                    const float2 s = make_float2(kv.x, kv.y), cc = make_float2(kv.z, kv.w);
+                    const float2 y = psub(pt[j][i], cc);
+                    const float2 t = padd(s, y);
+                    const float2 cn = psub(psub(t, s), y);
+                    k = make_float4(t.x, t.y, cn.x, cn.y);
+                }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < WT; ++j)
+        if (tg[j] < nf)
+#pragma unroll
+            for (int a = 0; a < L::NA; ++a) {
+                const float4 kv = kah[((a / 2) * WT + j) * NT + tid];
+                part[((size_t)blockIdx.y * L::NA + a) * nf + tg[j]] =
+                    (a & 1) ? make_float2(kv.y, kv.w) : make_float2(kv.x, kv.z);
+            }
+}
+
+// as k_apply_combine, from FP32 Kahan pairs (s, c) per split: the splits are
+// added in a fixed order with FP32 compensation, the result taken as
+// (double)S - (double)C, then the FP64 per-face combination
+template <int OP, int KC>
+__global__ void k_apply_combine2(const float2* __restrict__ part, int nsplit, int nf,
+                                 const d4* __restrict__ f64a, const double* __restrict__ fgrad,
+                                 const double* __restrict__ W64, int k, int col0,
+                                 double* __restrict__ corner) {
+    using L = OpLayout<OP, KC>;
+    const int S = blockIdx.x * blockDim.x + threadIdx.x;
+    if (S >= nf) return;
+    double s[L::NA];
+    for (int i = 0; i < L::NA; ++i) {
+        float a = 0.f, ca = 0.f;   // Kahan over the values s_k and -c_k
+#pragma unroll 4
+        for (int sp = 0; sp < nsplit; ++sp) {
+            const float2 v = part[((size_t)sp * L::NA + i) * nf + S];
+            float y = v.x - ca;
+            float t = a + y;
+            ca = (t - a) - y;
+            a = t;
+            y = -v.y - ca;
+            t = a + y;
+            ca = (t - a) - y;
+            a = t;
+        }
+        s[i] = (double)a - (double)ca;
+    }
+    double a = f64a[S].w;
+    const double* W = W64 + 4 * KC * (size_t)S;
+    double zV[3 * KC], zU[KC];
+    for (int i = 0; i < 3 * KC; ++i) zV[i] = 0.0;
+    for (int i = 0; i < KC; ++i) zU[i] = 0.0;
+    int o = 0;
+    if (L::HIGH) {
+        double r = s[0] / a;
+        for (int i = 0; i < 3 * KC; ++i) zV[i] = r * W[i] - s[1 + i];
+        o = 1 + 3 * KC;
+    }
+    if (L::USEU) {
+        double r = s[o] / a;
+        for (int c = 0; c < KC; ++c) zU[c] = r * W[3 * KC + c] - s[o + 1 + c];
+    }
+    for (int cr = 0; cr < 3; ++cr)
+        for (int c = 0; c < KC && col0 + c < k; ++c) {
+            double g = 0.0;
+            for (int q = 0; q < 3; ++q) g += fgrad[9 * S + 3 * cr + q] * zV[q * KC + c];
+            corner[((size_t)S * 3 + cr) * k + col0 + c] = 2.0 * a * (g + zU[c] / 3.0);
+        }
+}
+
 // per face: z = (r/a) W_S - (H W)_S in FP64, then the corner values of the
 // transposed map: 2 a_S grad phi_c . zV (B) and 2 a_S zU / 3 (B0, L)
 // (perm != null: the partials are in sorted order, thread t combines face
@@ -1133,12 +1510,70 @@ static int launch_apply_op(tp_mesh* m, const tp_params* p, const double* v, int 
     return corners_to_vertices(m, m->corner.as<double>(), k, y, st);
 }
 
+// FP32, 9 columns: the two-targets-per-thread kernel (k_apply_wide)
+template <int OP>
+static int launch_apply_wide(tp_mesh* m, const tp_params* p, const double* v, int k, double* y, cudaStream_t st) {
+    using L = OpLayout<OP, 9>;
+    // sources per FP32 chunk sum before the Kahan update: whole tiles for the
+    // operators with the high-order part (many accumulators per flush), half
+    // tiles for the others
+    constexpr int CHW = (OP == TP_OP_A || OP == TP_OP_B) ? 128 : 64;
+    const int nf = m->nf;
+    const double s = 2.0 - 2.0 / p->p;
+    const double l_exp = 3.0 - s;
+    const size_t smem = wide_smem_bytes<OP>();
+    const int per_sm = resident_per_sm((const void*)k_apply_wide<OP, CHW>, NT, smem);
+    if (per_sm < 1) return fail(TP_ERR_CUDA, "k_apply_wide: shared memory per block not available");
+    Grid g = make_grid(nf, nf, WT, per_sm);
+    TP_TRY(ensure(m->part, sizeof(float2) * (size_t)g.nsplit * L::NA * nf));
+    TP_TRY(ensure(m->wv64, sizeof(double) * 4 * 9 * (size_t)nf));
+    TP_TRY(ensure(m->wv32, sizeof(float4) * L::NW4 * (size_t)nf));
+    TP_TRY(ensure(m->corner, sizeof(double) * 3 * (size_t)nf * k));
+    const float4* fa = m->f32a.as<float4>();
+    const float4* fb = m->f32b.as<float4>();
+    for (int col0 = 0; col0 < k; col0 += 9) {
+        k_face_W<float, 9><<<(nf + 255) / 256, 256, 0, st>>>(v, k, col0, m->faces.as<int>(), nf, m->f64a.as<d4>(),
+                                                             m->fgrad.as<double>(), OP, m->wv64.as<double>(),
+                                                             m->wv32.as<float4>(), L::NW4);
+        TP_LAUNCH_CHECK();
+        dim3 grid(g.bx, g.nsplit);
+        {
+            const double units = (double)nf * (nf - 1);
+            m->pairs += units;
+            constexpr int key = OP == TP_OP_A ? PK_APPLY_A : OP == TP_OP_B ? PK_APPLY_B
+                              : OP == TP_OP_B0 ? PK_APPLY_B0 : PK_APPLY_L;
+            ProfScope ps(m, key, units, st);
+            m->prof.cols[key] += 9;
+            k_apply_wide<OP, CHW><<<grid, NT, smem, st>>>(fa, fb, m->f32c.as<float4>(), m->tilebox.as<float4>(),
+                                                          m->center.as<double>(), m->wv32.as<float4>(), nf,
+                                                          g.tiles_per_split, (float)s, (float)l_exp,
+                                                          m->part.as<float2>());
+        }
+        TP_LAUNCH_CHECK();
+        k_apply_combine2<OP, 9><<<(nf + 127) / 128, 128, 0, st>>>(m->part.as<float2>(), g.nsplit, nf,
+                                                                  m->f64a.as<d4>(), m->fgrad.as<double>(),
+                                                                  m->wv64.as<double>(), k, col0,
+                                                                  m->corner.as<double>());
+        TP_LAUNCH_CHECK();
+    }
+    return corners_to_vertices(m, m->corner.as<double>(), k, y, st);
+}
+
 template <typename T>
 static int launch_apply(tp_mesh* m, const tp_params* p, int op, const double* v, int k, double* y,
                         cudaStream_t st) {
     // 9 columns in one pass share the kernel evaluation; up to 3 columns
     // take the lighter 3-column kernel
     const bool wide = k > 3;
+    if (sizeof(T) == 4 && wide) {
+        switch (op) {
+            case TP_OP_A: return launch_apply_wide<TP_OP_A>(m, p, v, k, y, st);
+            case TP_OP_B: return launch_apply_wide<TP_OP_B>(m, p, v, k, y, st);
+            case TP_OP_B0: return launch_apply_wide<TP_OP_B0>(m, p, v, k, y, st);
+            case TP_OP_L: return launch_apply_wide<TP_OP_L>(m, p, v, k, y, st);
+        }
+        return fail(TP_ERR_INVALID_ARG, "unknown operator");
+    }
     switch (op) {
         case TP_OP_A: return wide ? launch_apply_op<T, TP_OP_A, 9>(m, p, v, k, y, st)
                                   : launch_apply_op<T, TP_OP_A, 3>(m, p, v, k, y, st);

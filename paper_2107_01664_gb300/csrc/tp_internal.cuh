@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -48,11 +49,18 @@ void count_launches(unsigned long long n);
 struct Buf {
     void* ptr = nullptr;
     size_t bytes = 0;
+    tp_ctx* ctx = nullptr;   // the context whose allocator holds ptr (freed through it)
     template <class T> T* as() const { return static_cast<T*>(ptr); }
 };
 
+// grows b to at least `bytes` through the calling thread's current context
+// (its allocator, or cudaMalloc); release() frees through b.ctx
 int ensure(Buf& b, size_t bytes);
 void release(Buf& b);
+// the context of the current library call on this thread (set by the entry
+// points for the mesh they serve; the per-device default context otherwise)
+tp_ctx*& current_ctx();
+tp_ctx* default_ctx(int device);
 
 // 32-byte FP64 quadruple used for face tables of the FP64 path
 struct alignas(32) d4 {
@@ -130,7 +138,18 @@ namespace tp {
 struct CholState;   // sparse Cholesky factor of the cotan Laplacian (chol.cu)
 }
 
+// a device and the allocator of the device memory of its meshes
+struct tp_ctx {
+    int device = 0;
+    bool is_default = false;      // the per-device context of tp_mesh_create (never destroyed)
+    bool custom = false;          // al set by tp_ctx_set_allocator
+    tp_allocator al{};
+    std::atomic<long long> in_use{0}, peak{0};
+    std::atomic<int> meshes{0};
+};
+
 struct tp_mesh {
+    tp_ctx* ctx = nullptr;
     int device = 0;
     int nv = 0, nf = 0;
     // topology (fixed for the life of the mesh)

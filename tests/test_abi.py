@@ -58,3 +58,14 @@ def test_errors_without_device_are_reported_not_crashing():
     F = np.array([[0, 1, 2]], dtype=np.int32)
     with pytest.raises(tp.TpError):
         tp.Mesh(V, F, device=0)
+
+
+def test_context_without_device_is_an_error_not_a_crash():
+    import paper_2107_01664_gb300 as tp
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("checks the no-device error path")
+    with pytest.raises(tp.TpError) as e:
+        tp.Context(0)
+    assert e.value.code == tp.TP_ERR_INVALID_ARG
+    assert tp.lib().tp_destroy(None) == tp.TP_OK
