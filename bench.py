@@ -50,7 +50,8 @@ def flops_per_pair(name, stat):
     return None
 KERNEL_SOURCE = {"energy_direct": "pairs.cu", "diff_direct": "pairs.cu", "apply_A": "pairs.cu",
                  "apply_B": "pairs.cu", "apply_B0": "pairs.cu", "apply_L": "pairs.cu",
-                 "bh_energy": "bvh.cu", "bh_diff": "bvh.cu", "cg": "cg.cu", "bvh_build": "bvh.cu",
+                 "bh_energy": "bvh.cu", "bh_diff": "bvh.cu", "bh_apply": "pairs.cu", "cg": "cg.cu",
+                 "bvh_build": "bvh.cu",
                  "chol_factor": "chol.cu", "chol_solve": "chol.cu", "obstacle_direct": "obstacle.cu",
                  "bh_obstacle": "obstacle.cu"}
 FP32_LANES_PER_SM = 128
@@ -69,49 +70,107 @@ def bh_params(tp):
 # CPU side: the oracle on a bounded sample of the same workload
 # ---------------------------------------------------------------------------
 
-def sample_desc(scale):
-    return (f"oracle (numpy FP64, 1 thread) on {WORKLOAD}: energy rows of {32 * scale} target faces, "
-            f"dE at {3 * scale} vertices, A.u and L.u at {3 * scale} vertices each; "
+def sample_desc(scale, procs=1):
+    per = "per process, " if procs > 1 else ""
+    return (f"oracle (numpy FP64) on {WORKLOAD}, {procs} process(es) with 1 thread each; {per}energy rows of "
+            f"{32 * scale} target faces, dE at {3 * scale} vertices, A.u and L.u at {3 * scale} vertices each; "
             "pairs = rows evaluated x (nf - 1)")
 
 
-def oracle_sample_pairs_per_s(scale):
-    """Run in a subprocess with single-threaded BLAS; returns (pairs/s, seconds, pairs)."""
+def oracle_timed_loop(scale, seed, warm, reps, start_at):
+    """Reference arm, one process: `warm` untimed samples, then from the
+    wall-clock time start_at `reps` timed ones; returns (pairs, start, end)."""
+    for _ in range(warm):
+        oracle_sample_pairs_per_s(scale, seed)
+    time.sleep(max(0.0, start_at - time.time()))
+    pairs, w0, w1 = 0.0, None, None
+    for k in range(reps):
+        r = oracle_sample_pairs_per_s(scale, seed + 1000 * (k + 1))
+        pairs += r[2]
+        w0 = r[3] if w0 is None else w0
+        w1 = r[4]
+    return pairs, w0, w1
+
+
+def oracle_sample_pairs_per_s(scale, seed=4242, start_at=None):
+    """Run in a subprocess with single-threaded BLAS; returns (pairs/s,
+    seconds, pairs, start, end) with start/end on the wall clock (time.time);
+    with start_at the work waits until that wall-clock time, so that
+    concurrent processes compute over the same window."""
     import numpy as np
     from oracle import tp_oracle as O
     from synth import vertex_vectors, workload
     V, F = workload(WORKLOAD)
     nf = len(F)
-    rng = np.random.default_rng(4242)
+    rng = np.random.default_rng(seed)
     targets = rng.choice(nf, 32 * scale, replace=False)
     nvs = 3 * scale
     verts = rng.choice(len(V), 3 * nvs, replace=False)
     u = vertex_vectors(len(V), 3, 202)
+    if start_at is not None:
+        time.sleep(max(0.0, start_at - time.time()))
+    w0 = time.time()
     t0 = time.perf_counter()
     O.energy_rows(V, F, 6.0, targets)
     O.differential_at_vertices(V, F, verts[:nvs])
     O.apply_operator_at_vertices(V, F, u, "A", verts[nvs:2 * nvs])
     O.apply_operator_at_vertices(V, F, u, "L", verts[2 * nvs:])
     dt = time.perf_counter() - t0
+    w1 = time.time()
 
     def inc_rows(vs):
         return len(np.unique(np.concatenate([np.nonzero(np.any(F == v, axis=1))[0] for v in vs])))
     rows = len(targets) + inc_rows(verts[:nvs]) + inc_rows(verts[nvs:2 * nvs]) + inc_rows(verts[2 * nvs:])
     pairs = float(rows) * (nf - 1)
-    return pairs / dt, dt, pairs
+    return pairs / dt, dt, pairs, w0, w1
 
 
-def run_cpu_sample(scale=48):
+def _oracle_procs(scale, procs):
+    """procs concurrent single-threaded oracle processes (different seeded
+    samples of the same workload); returns (summed pairs / wall seconds,
+    wall seconds)."""
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
-    code = ("import json,sys; sys.path.insert(0, %r); import bench; "
-            "print(json.dumps(bench.oracle_sample_pairs_per_s(%d)))" % (ROOT, scale))
-    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=900)
-    if out.returncode != 0:
-        raise RuntimeError(out.stderr[-2000:])
-    v, dt, pairs = json.loads(out.stdout.strip().splitlines()[-1])
-    return {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample_desc(scale),
-            "seconds": round(dt, 2)}
+    # every process loads its inputs first and starts computing at the same
+    # wall-clock time; the window is from that time to the last process's end
+    start_at = time.time() + 4.0 + 0.25 * procs
+    cmds = []
+    for i in range(procs):
+        code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+                "print(json.dumps(bench.oracle_sample_pairs_per_s(%d, %d, %r)))"
+                % (ROOT, scale, 4242 + i, start_at if procs > 1 else None))
+        cmds.append([sys.executable, "-c", code])
+    ps = [subprocess.Popen(c, env=env, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True) for c in cmds]
+    pairs, w0, w1 = 0.0, [], []
+    for pr in ps:
+        out, err = pr.communicate(timeout=900)
+        if pr.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        r = json.loads(out.strip().splitlines()[-1])
+        pairs += r[2]
+        w0.append(r[3])
+        w1.append(r[4])
+    wall = max(w1) - min(w0)
+    return pairs / wall, wall
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def run_cpu_sample(scale=48, all_scale=6):
+    """The oracle on the host cores: one single-threaded process, and one
+    single-threaded process per core at once (the all-cores figure is the
+    reported value)."""
+    v1, dt1 = _oracle_procs(scale, 1)
+    n = host_cores()
+    vn, dtn = _oracle_procs(all_scale, n)
+    return {"value": vn, "unit": UNIT, "cores": n, "kind": "oracle", "sample": sample_desc(all_scale, n),
+            "seconds": round(dtn, 2),
+            "single_thread": {"value": v1, "cores": 1, "sample": sample_desc(scale), "seconds": round(dt1, 2)}}
 
 
 # ---------------------------------------------------------------------------
@@ -206,43 +265,138 @@ def profile_traffic(kernel, workload):
 # large single mesh: Barnes-Hut on the 1,310,720-face icosphere
 # ---------------------------------------------------------------------------
 
-def large_bh(tp, dev, reps=3):
-    """Device time of the Barnes-Hut (theta = 0.5, leaf 8) energy and
-    differential on icosphere level 8 with spherical-harmonic bumps, and of one
-    direct all-pairs energy for comparison (interactions per second)."""
+def fp32_peak_tflops(dev):
     import torch
-    from synth import workload
+    peaks, _ = measured_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    return sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, f"{sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {mhz:.0f} MHz"
+
+
+def kernel_roofline(name, stat, flops_per_unit, workload, dev, bytes_per_unit=None):
+    """Roofline of one kernel class from its profile statistics: FP32
+    TFLOP/s against the FP32 peak (ALU-bound pair kernels) or GB/s against
+    the measured HBM copy bandwidth (bytes_per_unit given); DRAM bytes per
+    launch from the committed ncu summary of this kernel and workload."""
+    n = max(1, stat["launches"])
+    ms = stat["ms"] / n
+    units = stat["units"] / n
+    peaks, src = measured_peaks()
+    tr = profile_traffic(name, workload)
+    out = {"ms_per_launch": ms, "units_per_launch": units, "per_s": units / (ms / 1e3) if ms > 0 else None,
+           "launches": stat["launches"], "traffic": tr}
+    if ms <= 0:
+        return out
+    if bytes_per_unit is None:
+        peak, basis = fp32_peak_tflops(dev)
+        ach = flops_per_unit * units / (ms / 1e3) / 1e12
+        out.update({"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                    "peak_basis": basis})
+    else:
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        ach = bytes_per_unit * units / (ms / 1e3) / 1e9
+        out.update({"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                    "peak_basis": f"hbm_gbs ({src})"})
+    if tr is not None:
+        out["dram_gbs"] = tr / (ms / 1e3) / 1e9
+    return out
+
+
+def large_mesh(tp, dev, reps=3):
+    """The 1,310,720-face icosphere with spherical-harmonic bumps: Barnes-Hut
+    (theta = 0.5, leaf 8) E, dE and A v (3 columns) in FP32 with their
+    rooflines; their errors against stored FP64 direct sums of the oracle
+    (energy rows at 20,000 seeded target faces, dE and A u at 64 seeded
+    vertices; tests/golden/make_l8_samples.py); the FP32 direct rows of the
+    same 20,000 targets; the Poisson solve of the preconditioner (9 columns,
+    cg_tol 1e-6) with its HBM throughput; one direct all-pairs energy."""
+    import numpy as np
+    import torch
+    from synth import vertex_vectors, workload
+    t_start = time.perf_counter()
     V, F = workload("icosphere_l8")
+    smp = json.load(open(os.path.join(ROOT, "tests", "golden", "icosphere_l8_samples.json")))
     mesh = tp.Mesh(torch.tensor(V, dtype=torch.float64, device=dev),
                    torch.tensor(F, dtype=torch.int32, device=dev), device=dev.index or 0)
     pb = bh_params(tp)
     dE = torch.empty((len(V), 3), dtype=torch.float64, device=dev)
+    v3 = torch.tensor(vertex_vectors(len(V), 3, 507), dtype=torch.float64, device=dev)
     tp.tp_energy(mesh, pb)
     tp.tp_differential(mesh, pb, like=dE)
+    tp.fractional_apply(mesh, "A", v3, pb)
     torch.cuda.synchronize()
     tp.tp_profile_read(mesh)
     tp.tp_profile_enable(mesh, True)
     for _ in range(reps):
         tp.tp_mesh_set_positions(mesh, torch.tensor(V, dtype=torch.float64, device=dev))  # rebuilds the BVH
-        tp.tp_energy(mesh, pb)
-        tp.tp_differential(mesh, pb, like=dE)
-    tp.tp_energy(mesh, tp.params())                       # one direct pass
-    # Barnes-Hut operator applies: A and L^{2-s} on 3 columns
-    v3 = torch.randn((len(V), 3), dtype=torch.float64, device=dev, generator=torch.Generator(dev).manual_seed(7))
-    for op in ("A", "L"):
-        tp.fractional_apply(mesh, op, v3, pb)
+        E_bh = tp.tp_energy(mesh, pb)
+        g_bh, _ = tp.tp_differential(mesh, pb, like=dE)
+        Au_bh = tp.fractional_apply(mesh, "A", v3, pb)
     torch.cuda.synchronize()
     prof = tp.tp_profile_read(mesh)
+    out = {"workload": "icosphere_l8", "nf": int(len(F)), "nv": int(len(V)), "theta": pb.theta,
+           "leaf_size": pb.leaf_size, "dtype": "f32"}
+    for k, fl in (("bh_energy", FLOPS_PER_PAIR["bh_energy"]), ("bh_diff", FLOPS_PER_PAIR["bh_diff"]),
+                  ("bh_apply", APPLY_FLOPS["apply_A"](3)), ("bvh_build", None)):
+        if k in prof and prof[k]["launches"]:
+            out[k] = kernel_roofline(k, prof[k], fl or 0.0, "icosphere_l8", dev) if fl else \
+                {"ms_per_launch": prof[k]["ms"] / prof[k]["launches"]}
+    bh_ms = sum(prof[k]["ms"] / prof[k]["launches"] for k in ("bh_energy", "bh_diff", "bh_apply") if k in prof)
+    bh_units = sum(prof[k]["units"] / prof[k]["launches"] for k in ("bh_energy", "bh_diff", "bh_apply") if k in prof)
+    out["bh_E_dE_Av"] = {"ms": bh_ms, "interactions": bh_units,
+                         "interactions_per_s": bh_units / (bh_ms / 1e3) if bh_ms > 0 else None}
+    # accuracy against the stored FP64 direct sums
+    rel = lambda a, b: float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(b))
+    mx = lambda a, b: float(np.abs(np.asarray(a) - np.asarray(b)).max() / np.abs(np.asarray(b)).max())
+    tg = torch.tensor(np.array(smp["targets"], dtype=np.int32), device=dev)
+    rows_ref = np.array(smp["rows"])
+    rows_bh = tp.tp_energy_rows(mesh, tg, pb).cpu().numpy()
+    tp.tp_profile_read(mesh)
+    rows_d = tp.tp_energy_rows(mesh, tg, tp.params()).cpu().numpy()
+    pd = tp.tp_profile_read(mesh)
+    vi = np.array(smp["vertices"])
+    g_h = g_bh.cpu().numpy()[vi]
+    a_h = Au_bh.cpu().numpy()[vi]
+    out["accuracy_vs_fp64_direct"] = {
+        "reference": "oracle FP64 direct sums (stored): energy rows at 20,000 targets, dE and A u at 64 vertices",
+        "bh_theta_0.5": {"rows": rel(rows_bh, rows_ref), "rows_max": mx(rows_bh, rows_ref),
+                         "dE": rel(g_h, smp["dE"]), "Au": rel(a_h, smp["Au"])},
+        "fp32_direct": {"rows": rel(rows_d, rows_ref), "rows_max": mx(rows_d, rows_ref)},
+        "E_bh": E_bh}
+    if "energy_direct" in pd and pd["energy_direct"]["launches"]:
+        out["direct_rows_20k"] = kernel_roofline("energy_direct", pd["energy_direct"],
+                                                 FLOPS_PER_PAIR["energy_direct"], "icosphere_l8", dev)
+    # Poisson solve of the preconditioner on 655,362 vertices
+    info = tp.cotan_factor_info(mesh)
+    b = torch.tensor(vertex_vectors(len(V), 9, 508), dtype=torch.float64, device=dev)
+    tp.cotan_solve(mesh, b, tp.params(cg_tol=1e-6))
+    torch.cuda.synchronize()
+    tp.tp_profile_read(mesh)
+    z, iters = tp.cotan_solve(mesh, b, tp.params(cg_tol=1e-6))
+    torch.cuda.synchronize()
+    pp = tp.tp_profile_read(mesh)
+    key = "chol_solve" if ("chol_solve" in pp and pp["chol_solve"]["launches"]) else "cg"
+    poisson = {"solver": "sparse Cholesky + FP64 refinement" if key == "chol_solve" else "Jacobi CG (FP64)",
+               "factor_available": bool(info["available"]), "columns": 9, "cg_tol": 1e-6, "iterations": iters}
+    if key in pp and pp[key]["ms"] > 0:
+        d = pp[key]
+        poisson.update({"ms": d["ms"], "bytes": d["units"],
+                        "achieved_gbs": d["units"] / (d["ms"] / 1e3) / 1e9,
+                        "hbm_peak_gbs": float(measured_peaks()[0].get("hbm_gbs", 6800.0))})
+        poisson["frac"] = poisson["achieved_gbs"] / poisson["hbm_peak_gbs"]
+    out["poisson_solve"] = poisson
+    # one direct all-pairs energy (FP32)
+    tp.tp_profile_read(mesh)
+    tp.tp_energy(mesh, tp.params())
+    torch.cuda.synchronize()
+    pe = tp.tp_profile_read(mesh)
+    if "energy_direct" in pe:
+        out["energy_direct_all_pairs"] = kernel_roofline("energy_direct", pe["energy_direct"],
+                                                         FLOPS_PER_PAIR["energy_direct"], "icosphere_l8", dev)
     tp.tp_profile_enable(mesh, False)
     mesh.close()
-    out = {"workload": "icosphere_l8", "nf": int(len(F)), "theta": pb.theta, "leaf_size": pb.leaf_size}
-    for k in ("bh_energy", "bh_diff", "bh_apply", "bvh_build", "energy_direct"):
-        if k in prof and prof[k]["launches"]:
-            d = prof[k]
-            n = d["launches"]
-            out[k] = {"ms_per_launch": d["ms"] / n, "units_per_launch": d["units"] / n,
-                      "per_s": d["units"] / (d["ms"] / 1e3) if d["ms"] > 0 else None}
     out["bh_step_linked_tori"] = bh_step(tp, dev)
+    out["section_s"] = round(time.perf_counter() - t_start, 1)
     return out
 
 
@@ -617,6 +771,11 @@ def gpu_arm(args):
     dev_ms = float(sum(step_ms))
     dev_ms_all, pairs_all = aggregate_ranks(dev_ms, pairs_total, dev, world)
     value = pairs_all / (dev_ms_all / 1e3)
+    # the energies of rejected Armijo trials are pair work too; the figure
+    # without them counts only the accepted trial of each step
+    nf = len(F)
+    rejected = sum(max(0, r["ls_trials"] - 1) for r in reps) * float(nf) * (nf - 1)
+    pairs_acc_all = aggregate_ranks(dev_ms, pairs_total - rejected, dev, world)[1]
 
     # e2e through the C ABI with host buffers: pinned positions in, positions + dE out
     f_host = torch.tensor(V, dtype=torch.float64).pin_memory()
@@ -676,6 +835,9 @@ def gpu_arm(args):
         "steps_per_s": 1e3 * args.steps / dev_ms_all,
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "pairs_per_step": pairs_per_step,
+        "value_without_rejected_trials": pairs_acc_all / (dev_ms_all / 1e3),
+        "rejected_trial_pairs_per_step": rejected / args.steps,
+        "ls_trials_per_step": sum(r["ls_trials"] for r in reps) / len(reps),
         "krylov_iters_per_step": sum(r["krylov_iters"] for r in reps) / len(reps),
         # steps whose FGMRES met krylov_tol within krylov_max (status 0); status 4 = the
         # fixed iteration budget ran out first (the step is still taken)
@@ -688,11 +850,12 @@ def gpu_arm(args):
         "wall_s": wall, "e2e": e2e, "gpu_launches": int(launches), "roofline": roof, "clocks": clk,
     }
     if not args.no_large:
-        line["large_mesh_bh"] = large_bh(tp, dev)
+        line["large_mesh"] = large_mesh(tp, dev)
+        line["accuracy"] = accuracy(tp, dev)
+        line["serving"] = serving(tp, dev, n=args.serve_n, slots=args.serve_slots)
         line["obstacle"] = obstacle_scene(tp, dev)
         line["pins"] = pinned_steps(tp, dev)
         line["willmore"] = willmore_steps(tp, dev)
-        line["accuracy"] = accuracy(tp, dev)
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = run_cpu_sample()
     mesh.close()
@@ -711,15 +874,32 @@ def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    for _ in range(args.warmup):       # untimed
-        run_cpu_sample(scale=4)
-    vals, secs = [], 0.0
-    for _ in range(args.steps):
-        r = run_cpu_sample(scale=4)
-        vals.append(r["value"])
-        secs += r["seconds"]
-    value = sum(vals) / len(vals)
-    cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample_desc(4)}
+    # one single-threaded oracle process per host core: W untimed samples
+    # each, then K timed samples each from a common start time
+    n = host_cores()
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    start_at = time.time() + 6.0 + 0.6 * args.warmup
+    ps = []
+    for i in range(n):
+        code = ("import json,sys; sys.path.insert(0, %r); import bench; "
+                "print(json.dumps(bench.oracle_timed_loop(1, %d, %d, %d, %r)))"
+                % (ROOT, 4242 + i, args.warmup, args.steps, start_at))
+        ps.append(subprocess.Popen([sys.executable, "-c", code], env=env, stdout=subprocess.PIPE,
+                                   stderr=subprocess.PIPE, text=True))
+    pairs, w0, w1 = 0.0, [], []
+    for pr in ps:
+        out, err = pr.communicate(timeout=1800)
+        if pr.returncode != 0:
+            raise RuntimeError(err[-2000:])
+        r = json.loads(out.strip().splitlines()[-1])
+        pairs += r[0]
+        w0.append(r[1])
+        w1.append(r[2])
+    secs = max(w1) - min(w0)
+    value = pairs / secs
+    cpu = {"value": value, "unit": UNIT, "cores": n, "kind": "oracle",
+           "sample": sample_desc(1, n) + f"; {args.steps} timed samples per process"}
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
@@ -731,84 +911,103 @@ def reference_arm(args):
 
 
 # ---------------------------------------------------------------------------
-# serving: continuous batching of descent steps (separate report)
+# serving: continuous batching of descent steps
 # ---------------------------------------------------------------------------
 
-SERVE_DESC = ("Poisson arrivals of one-step requests on perturbed icospheres and tori (sigma=0.01), "
-              "face counts log-uniform in [f_min, f_max]; slots = concurrent host threads on their own "
-              "CUDA streams; admission by tp_mesh_footprint_bytes against an HBM budget")
-
-
 def serve_arm(args):
-    """Serving (continuous batching of one-step requests).
-
-    1. fp32_pairs: the FP32-pair / FP64-solve path on a stream of
-       args.serve_n meshes of 2k-serve_fmax faces. A closed-loop run (all
-       requests present at t = 0) measures the capacity; the reported run
-       replays the stream with Poisson arrivals at 0.8x that capacity.
-    2. same_stream: a smaller stream (2k-8k faces) served once on the FP32
-       path and once on the plain FP64 direct path, same arrivals, same
-       meshes; steps/s, p50/p99 latency of both and the largest relative
-       difference between the two paths' new positions (per request:
-       |f32 - f64| / |f64 - f_start|). The full FP64 stream of 2k-200k
-       faces would take hours (FP64 pair terms run at 1/64 of FP32)."""
-    import numpy as np
+    """Serving alone (the same section the default run reports)."""
+    import torch
     import paper_2107_01664_gb300 as tp
-    from paper_2107_01664_gb300 import serve
-    out = {"metric": "served steps/s", "unit": "steps/s", "mode": "serve", "description": SERVE_DESC}
+    torch.cuda.set_device(0)
+    print(json.dumps({"serving": serving(tp, torch.device("cuda", 0), n=args.serve_n, f_max=args.serve_fmax,
+                                         slots=args.serve_slots)}))
 
-    def run(reqs, prec, rate):
-        p = tp.params(precision=prec, krylov_tol=1e-5, krylov_max=30, cg_tol=1e-6)
-        stream = [serve.Request(arrival=(0.0 if rate is None else r.arrival), rid=r.rid, V=r.V, F=r.F, A0=r.A0,
-                                V0=r.V0) for r in reqs]
-        srv = serve.Server(slots=args.serve_slots, step_params=p)
-        res = srv.run(stream)
+
+SERVE_BH_ABOVE = 30000
+
+
+def serving(tp, dev, n=512, f_min=2000, f_max=200000, slots=4, fp64_n=16, fp64_fmax=8000, pilot=64):
+    """Serving as the benchmark's fourth configuration: n one-step requests
+    (perturbed icospheres and tori, sigma = 0.01, faces log-uniform in
+    [f_min, f_max], seed 404) arriving as a Poisson process at 0.7x the
+    capacity measured closed-loop on `pilot` requests spread evenly over the
+    stream (every n/pilot-th request, so the size mix is the stream's); FP32 pair
+    terms with FP64 solves, Barnes-Hut (theta = 0.5) above SERVE_BH_ABOVE
+    faces, admission by HBM footprint, smallest-first within a 1 s fairness
+    window. The plain FP64 direct path serves a seeded sub-stream (the first
+    fp64_n requests of the stream with at most fp64_fmax faces) with the same
+    arrivals as the FP32 path; the full stream in FP64 would take hours (FP64
+    pair terms run at 1/64 of the FP32 rate). The line search of a served step
+    starts where no vertex moves by more than a quarter of a face size
+    (tau0_disp = 0.25)."""
+    import numpy as np
+    from paper_2107_01664_gb300 import serve
+    t_start = time.perf_counter()
+    p32 = tp.params(precision=tp.TP_PREC_FP32, krylov_tol=1e-5, krylov_max=30, cg_tol=1e-6, tau0_disp=0.25)
+    p64 = tp.params(precision=tp.TP_PREC_FP64, krylov_tol=1e-5, krylov_max=30, cg_tol=1e-6, tau0_disp=0.25)
+    reqs = serve.make_requests(n, f_min, f_max, rate=1.0, seed=404)
+
+    def at_rate(rs, rate, seed):
+        rng = np.random.default_rng(seed)
+        t = np.cumsum(rng.exponential(1.0 / rate, len(rs)))
+        return [serve.Request(arrival=float(t[i]), rid=r.rid, V=r.V, F=r.F) for i, r in enumerate(rs)]
+
+    def run(rs, p, bh_above):
+        srv = serve.Server(slots=slots, step_params=p, bh_above=bh_above, keep_positions=True)
+        res = srv.run(rs)
         summ = serve.summarize(res, srv.wall)
-        summ.update({"n_requests": len(reqs), "rate_per_s": rate, "slots": args.serve_slots,
-                     "max_concurrency": srv.max_concurrency, "peak_admitted_bytes": srv.peak_used,
-                     "budget_bytes": srv.budget, "krylov_max": p.krylov_max})
+        summ.update({"max_concurrency": srv.max_concurrency, "peak_admitted_bytes": srv.peak_used,
+                     "budget_bytes": srv.budget})
         return summ, res
 
-    def at_rate(reqs, rate, seed):
-        rng = np.random.default_rng(seed)
-        t = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
-        return [serve.Request(arrival=float(t[i]), rid=r.rid, V=r.V, F=r.F, A0=r.A0, V0=r.V0)
-                for i, r in enumerate(reqs)]
-
-    reqs = serve.make_requests(args.serve_n, 2000, args.serve_fmax, rate=1.0, seed=404)
-    cap, _ = run(reqs, tp.TP_PREC_FP32, None)
-    rate = 0.8 * cap["steps_per_s"]
-    summ, _ = run(at_rate(reqs, rate, 405), tp.TP_PREC_FP32, rate)
-    summ.update({"f_range": [2000, args.serve_fmax], "closed_loop_capacity_steps_per_s": cap["steps_per_s"]})
-    out["fp32_pairs"] = summ
-
-    small = serve.make_requests(max(4, args.serve_n // 4), 2000, 8000, rate=1.0, seed=406)
-    cap64, _ = run(small, tp.TP_PREC_FP64, None)
-    rate_s = 0.8 * cap64["steps_per_s"]
-    stream = at_rate(small, rate_s, 407)
-    s32, r32 = run(stream, tp.TP_PREC_FP32, rate_s)
-    s64, r64 = run(stream, tp.TP_PREC_FP64, rate_s)
-    # accuracy of the FP32 path against the FP64 one, per request: E at the
-    # start of the step (the quantity the 1e-5 tolerance is stated for), the
-    # Armijo step length, and the step itself where both took the same step
-    # length (a different tau is a discrete line-search decision, not an
-    # arithmetic error)
-    dE0, same_tau, dstep = [], 0, []
-    for a, b, q in zip(r32, r64, small):
+    stride = max(1, n // pilot)
+    closed = [serve.Request(arrival=0.0, rid=r.rid, V=r.V, F=r.F) for r in reqs[::stride][:pilot]]
+    cap, _ = run(closed, p32, SERVE_BH_ABOVE)
+    rate = 0.7 * cap["steps_per_s"]
+    main_stream = at_rate(reqs, rate, 405)
+    summ, res = run(main_stream, p32, SERVE_BH_ABOVE)
+    nfs = np.array([len(r.F) for r in reqs])
+    lat = {r.rid: r.latency for r in res if r.status == "ok"}
+    svc = {r.rid: r.end - r.start for r in res if r.status == "ok"}
+    classes = {}
+    for name, lo, hi in (("2k-8k", 0, 8000), ("8k-30k", 8000, 30000), ("30k-200k", 30000, 10 ** 9)):
+        ids = [i for i in range(len(reqs)) if lo < nfs[i] <= hi and i in lat]
+        if ids:
+            ls = np.array([lat[i] for i in ids]) * 1e3
+            sv = np.array([svc[i] for i in ids]) * 1e3
+            classes[name] = {"requests": len(ids), "p50_ms": float(np.percentile(ls, 50)),
+                             "p99_ms": float(np.percentile(ls, 99)),
+                             "service_p50_ms": float(np.percentile(sv, 50))}
+    out = {"metric": "served steps/s", "requests": n, "faces": [f_min, f_max], "slots": slots,
+           "bh_above_faces": SERVE_BH_ABOVE, "pilot_closed_loop_steps_per_s": cap["steps_per_s"],
+           "arrival_rate_per_s": rate, "fp32_pairs": summ, "latency_by_size": classes,
+           "krylov_converged": int(sum(1 for r in res if r.status == "ok" and r.report.get("status") == 0))}
+    # the FP64 direct path on the seeded sub-stream
+    sub = [r for r in main_stream if len(r.F) <= fp64_fmax][:fp64_n]
+    t0 = sub[0].arrival if sub else 0.0
+    sub = [serve.Request(arrival=r.arrival - t0, rid=r.rid, V=r.V, F=r.F) for r in sub]
+    s32, r32 = run(sub, p32, None)
+    s64, r64 = run(sub, p64, None)
+    # per request: E at the start of the step (the quantity the 1e-5 FP32
+    # tolerance is stated for), the step length, and the step per unit
+    # length (f_new - f) / tau of both paths
+    dE0, dtau, dstep = [], [], []
+    byid = {r.rid: r for r in sub}
+    for a, b in zip(r32, r64):
         if a.status != "ok" or b.status != "ok":
             continue
+        f0 = byid[a.rid].V
         dE0.append(abs(a.report["E_before"] - b.report["E_before"]) / abs(b.report["E_before"]))
-        if a.report["tau"] == b.report["tau"]:
-            same_tau += 1
-            dstep.append(float(np.linalg.norm(a.positions - b.positions) /
-                               max(np.linalg.norm(b.positions - q.V), 1e-300)))
-    out["same_stream"] = {"f_range": [2000, 8000], "rate_per_s": rate_s,
-                          "fp64_closed_loop_capacity_steps_per_s": cap64["steps_per_s"],
-                          "fp32_pairs": s32, "fp64_direct": s64,
-                          "max_rel_E_difference_fp32_vs_fp64": max(dE0) if dE0 else None,
-                          "requests_with_same_tau": same_tau,
-                          "max_rel_step_difference_same_tau": max(dstep) if dstep else None}
-    print(json.dumps(out))
+        dtau.append(abs(a.report["tau"] - b.report["tau"]) / b.report["tau"])
+        xa, xb = (a.positions - f0) / a.report["tau"], (b.positions - f0) / b.report["tau"]
+        dstep.append(float(np.linalg.norm(xa - xb) / max(np.linalg.norm(xb), 1e-300)))
+    out["fp64_comparison"] = {"sub_stream": f"first {len(sub)} requests with at most {fp64_fmax} faces, same arrivals",
+                              "fp32_pairs": s32, "fp64_direct": s64,
+                              "max_rel_E_difference": max(dE0) if dE0 else None,
+                              "max_rel_tau_difference": max(dtau) if dtau else None,
+                              "max_rel_step_per_tau_difference": max(dstep) if dstep else None}
+    out["section_s"] = round(time.perf_counter() - t_start, 1)
+    return out
 
 
 def main():
@@ -818,7 +1017,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU baseline leg")
-    ap.add_argument("--no-large", action="store_true", help="skip the 1.31M-face Barnes-Hut section")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the extra sections (1.31M-face mesh, serving, obstacle, pins, Willmore, accuracy)")
+    ap.add_argument("--large", action="store_true", help="run only the 1.31M-face section instead")
     ap.add_argument("--serve", action="store_true", help="run the serving benchmark instead")
     ap.add_argument("--long-run", type=int, default=0, help="run N Barnes-Hut steps on the linked tori instead")
     ap.add_argument("--obstacle", action="store_true",
@@ -829,8 +1030,8 @@ def main():
                     help="report only the errors on torus_20k against stored oracle values instead")
     ap.add_argument("--willmore", action="store_true",
                     help="run only the Willmore steps (torus_20k, weight 100) instead")
-    ap.add_argument("--serve-n", type=int, default=64)
-    ap.add_argument("--serve-fmax", type=int, default=50000)
+    ap.add_argument("--serve-n", type=int, default=512)
+    ap.add_argument("--serve-fmax", type=int, default=200000)
     ap.add_argument("--serve-slots", type=int, default=4)
     args = ap.parse_args()
     if args.serve:
@@ -850,6 +1051,12 @@ def main():
         import paper_2107_01664_gb300 as tp
         torch.cuda.set_device(0)
         print(json.dumps({"pins": pinned_steps(tp, torch.device("cuda", 0))}))
+        return
+    if args.large:
+        import torch
+        import paper_2107_01664_gb300 as tp
+        torch.cuda.set_device(0)
+        print(json.dumps({"large_mesh": large_mesh(tp, torch.device("cuda", 0))}))
         return
     if args.accuracy:
         import torch

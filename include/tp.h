@@ -102,6 +102,9 @@ typedef struct tp_params {
                              recompute only the node data (refit); 0 = rebuild (new Morton order) */
     double prec_self_weight; /* kappa >= 0 of the within-face term added to L^{2-s} in the
                                 preconditioner (see precond_apply); 0 = L^{2-s} of §5.1.1 alone */
+    double tau0_disp;     /* > 0: the line search starts from min(tau0, tau0_disp h / max_v |x_v|),
+                             h = sqrt(total area / nf), so that the first trial moves no vertex by
+                             more than tau0_disp face sizes; 0 (default) = start from tau0 */
 } tp_params;
 
 typedef struct tp_constraints {
@@ -185,7 +188,7 @@ int tp_mesh_create_ctx(tp_ctx* ctx, int nv, int nf, const double* pos,
 /* Fill *p with the defaults: p=6, theta=0, leaf_size=8, FP32 pairs,
  * full BH differential, krylov_tol=1e-6, krylov_max=200, restart 30,
  * cg_tol=1e-6, cg_max=20000, Armijo c=1e-4, shrink 0.5, tau0=1, ls_max=30,
- * proj_iters=1, Cholesky Poisson solver, prec_self_weight=24. */
+ * proj_iters=1, Cholesky Poisson solver, prec_self_weight=24, tau0_disp=0. */
 void tp_params_default(tp_params* p);
 
 /* Create a mesh on CUDA device `device` from nv positions and nf faces
@@ -202,6 +205,12 @@ int tp_mesh_set_positions(tp_mesh* m, const double* pos, int ptr_kind, void* str
 
 /* Copy the current positions (float64 [nv][3]) out. */
 int tp_mesh_get_positions(tp_mesh* m, double* pos, int ptr_kind, void* stream);
+
+/* Total area sum_T a_T (§7.1.3) and enclosed signed volume
+ * (1/6) sum_{ijk} f_i . (f_j x f_k) (§7.1.4) of the current positions: the
+ * quantities the constraints A0 and V0 of precond_step refer to. Either
+ * output (host doubles) may be NULL, not both. Synchronises `stream`. */
+int tp_mesh_area_volume(tp_mesh* m, double* area, double* volume, void* stream);
 
 /* Free every device resource of the mesh. Accepts NULL. */
 int tp_mesh_destroy(tp_mesh* m);

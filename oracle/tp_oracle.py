@@ -659,7 +659,7 @@ def constraint_values(f, faces, A0, V0, use_area=True, use_volume=True):
 
 def precond_step(f, faces, A0, V0, use_area=True, use_volume=True, p=6.0,
                  tau0=1.0, armijo_c=1e-4, shrink=0.5, ls_max=30, fixed_tau=None, proj_iters=1,
-                 obstacle=None, pins=None, willmore=0.0, free_barycenter=False):
+                 obstacle=None, pins=None, willmore=0.0, free_barycenter=False, tau0_disp=0.0):
     """One constrained descent step (§3, steps 1-5; §5.4 with exact solves):
     direction by Eq. 14, Armijo backtracking from tau0 (E(f + tau x) <=
     E(f) + c tau dE.x), then corrective projections by Eq. 15 with the
@@ -671,7 +671,10 @@ def precond_step(f, faces, A0, V0, use_area=True, use_volume=True, p=6.0,
     Phi_P = 0 at the start and every row of the projection's right-hand side
     for a pin is 0. With a Willmore weight w the energy gains w E_W and the
     matrix w C M^{-1} C (§7.3.5). With free_barycenter the direction gains
-    barycenter_motion (§7.1.1).
+    barycenter_motion (§7.1.1). With tau0_disp > 0 the line search starts
+    from min(tau0, tau0_disp h / max_v |x_v|), h = sqrt(total area / #faces)
+    (a first trial that moves no vertex by more than tau0_disp face sizes; the
+    paper leaves the initial step open).
     Returns dict(f_new, x, tau, E0, E1, h)."""
     nv = len(f)
     x, g = descent_direction(f, faces, use_area, use_volume, p, obstacle, pins, willmore)
@@ -683,6 +686,11 @@ def precond_step(f, faces, A0, V0, use_area=True, use_volume=True, p=6.0,
         tau = fixed_tau
     else:
         tau = tau0
+        if tau0_disp > 0.0:
+            h = np.sqrt(total_area(f, faces) / len(faces))
+            xmax = float(np.sqrt(np.max(np.sum(x * x, axis=1))))
+            if xmax > 0.0:
+                tau = min(tau, tau0_disp * h / xmax)
         for _ in range(ls_max):
             if _total_energy(f + tau * x, faces, p, obstacle, willmore) <= E0 + armijo_c * tau * slope:
                 break

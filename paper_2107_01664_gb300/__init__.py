@@ -29,7 +29,7 @@ __all__ = [
     "tp_energy_noalloc", "tp_chol_info", "cotan_factor_info", "TP_POISSON_CHOLESKY", "TP_POISSON_CG",
     "tp_obstacle_set", "tp_obstacle_energy", "tp_pins_set", "TP_MAX_PINS", "tp_willmore_set",
     "tp_willmore_energy", "tp_selftest_wait", "Context", "tp_allocator", "tp_create", "tp_destroy",
-    "tp_ctx_set_allocator", "tp_ctx_memory", "tp_mesh_create_ctx",
+    "tp_ctx_set_allocator", "tp_ctx_memory", "tp_mesh_create_ctx", "tp_mesh_area_volume",
 ]
 
 TP_OK, TP_ERR_INVALID_ARG, TP_ERR_DEGENERATE, TP_ERR_OOM = 0, 1, 2, 3
@@ -58,7 +58,7 @@ class tp_params(ctypes.Structure):
         ("cg_tol", ctypes.c_double), ("cg_max", ctypes.c_int), ("armijo_c", ctypes.c_double),
         ("armijo_shrink", ctypes.c_double), ("tau0", ctypes.c_double), ("ls_max", ctypes.c_int),
         ("fixed_tau", ctypes.c_int), ("proj_iters", ctypes.c_int), ("poisson_solver", ctypes.c_int),
-        ("bvh_refit", ctypes.c_int), ("prec_self_weight", ctypes.c_double),
+        ("bvh_refit", ctypes.c_int), ("prec_self_weight", ctypes.c_double), ("tau0_disp", ctypes.c_double),
     ]
 
 
@@ -125,6 +125,7 @@ def lib():
         "tp_mesh_set_positions": (c_int, [vp, vp, c_int, vp]),
         "tp_mesh_get_positions": (c_int, [vp, vp, c_int, vp]),
         "tp_mesh_destroy": (c_int, [vp]),
+        "tp_mesh_area_volume": (c_int, [vp, P(c_double), P(c_double), vp]),
         "tp_mesh_footprint_bytes": (c_size, [c_int, c_int, P(tp_params)]),
         "tp_energy": (c_int, [vp, P(tp_params), P(c_double), vp]),
         "tp_energy_rows": (c_int, [vp, P(tp_params), vp, c_int, vp, c_int, vp]),
@@ -375,6 +376,13 @@ def tp_mesh_get_positions(mesh: Mesh, like=None):
     out, ptr, kind = _empty_like_kind(like, (mesh.nv, 3))
     _check(lib().tp_mesh_get_positions(mesh.handle, ptr, kind, _stream_ptr(like)))
     return out
+
+
+def tp_mesh_area_volume(mesh: Mesh):
+    """(total area, enclosed signed volume) of the mesh's current positions (§7.1.3, §7.1.4)."""
+    A, V = ctypes.c_double(), ctypes.c_double()
+    _check(lib().tp_mesh_area_volume(mesh.handle, ctypes.byref(A), ctypes.byref(V), _stream_ptr()))
+    return A.value, V.value
 
 
 def tp_mesh_destroy(mesh: Mesh):

@@ -32,6 +32,7 @@
 // X_I = sum a_T X_T / a_I and a_I = sum a_T. "Literal" mode keeps only the
 // target-side terms, the formula printed in §4.2.
 #include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
 
 #include <algorithm>
 #include <cmath>
@@ -443,6 +444,7 @@ int bvh_build(tp_mesh* m, const tp_params* p, cudaStream_t st) {
     }
     m->bvh_valid = true;
     m->bvh_ordered = true;
+    m->bvh_version++;
     return TP_OK;
 }
 
@@ -569,6 +571,243 @@ k_bh_energy(const BvhNode* __restrict__ node, const float4* __restrict__ nodelo,
     if (count && nint) atomicAdd(count, (unsigned long long)nint);
 }
 
+// ---------------------------------------------------------------------------
+// interaction lists
+// ---------------------------------------------------------------------------
+//
+// The per-target admissible sets of §4.1 are kept exactly, but found for a
+// whole group of 32 consecutive sorted targets (one warp) at a time. Every
+// candidate node is first tested against the group: against the bounding box
+// of the group's target boxes with the largest target radius (if admissible
+// there, it is admissible for every target: the box gap only shrinks and the
+// radius only grows) and against the farthest-gap box with the smallest
+// radius (if inadmissible there, it is inadmissible for every target). The
+// FP32 operations are monotone, so both implications hold for the FP32
+// decisions too. Only the nodes that are neither get the exact per-target
+// test of the walk kernels, lane by lane. A candidate carries the mask of the
+// group's targets for which none of its ancestors was admissible; the 32
+// lanes test 32 candidates at once, from a stack in shared memory. The output
+// per group: far entries (node, mask) and near entries (inadmissible leaf,
+// mask). The lists depend only on the tree and theta: they are built once per
+// tree and serve the energy, the differential and every operator apply of
+// the tree, whose evaluation kernels then stream the lists without a walk.
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+__device__ __forceinline__ float wmin(float x) {
+    for (int o = 16; o > 0; o >>= 1) x = fminf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+__device__ __forceinline__ float wmax(float x) {
+    for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+    return x;
+}
+
+// WRITE = false: counts per group; WRITE = true: the entries at the offsets
+template <bool WRITE>
+__global__ void __launch_bounds__(128)
+k_bh_list(const BvhNode* __restrict__ node, const int* __restrict__ right, const FaceBox* __restrict__ fbox,
+          int nf, float theta2, int cap, long long* __restrict__ cnt, const long long* __restrict__ far_off,
+          const long long* __restrict__ near_off, int2* __restrict__ far_out, int2* __restrict__ near_out,
+          int* __restrict__ err) {
+    extern __shared__ int2 lstack[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int ngroups = (nf + BHL_GROUP - 1) / BHL_GROUP;
+    const int g = blockIdx.x * (blockDim.x >> 5) + w;
+    if (g >= ngroups) return;                       // the whole warp
+    int2* stk = lstack + (size_t)w * cap;
+    const int i = g * BHL_GROUP + lane;
+    const bool has = i < nf;
+    const FaceBox fb = fbox[has ? i : 0];
+    const float glx = wmin(has ? fb.lox : 3e38f), gly = wmin(has ? fb.loy : 3e38f), glz = wmin(has ? fb.loz : 3e38f);
+    const float ghx = wmax(has ? fb.hix : -3e38f), ghy = wmax(has ? fb.hiy : -3e38f), ghz = wmax(has ? fb.hiz : -3e38f);
+    const float gr2max = wmax(has ? fb.r2 : 0.f), gr2min = wmin(has ? fb.r2 : 3e38f);
+    const unsigned full = __ballot_sync(0xffffffffu, has);
+    const unsigned lt = lanemask_lt();
+    int sp = 1;
+    if (lane == 0) stk[0] = make_int2(0, (int)full);
+    __syncwarp();
+    long long nfar = 0, nnear = 0;
+    const long long fo = WRITE ? far_off[g] : 0, no = WRITE ? near_off[g] : 0;
+    // writes stay inside the group's range whatever happens (the second pass
+    // must reproduce the first pass's counts; a mismatch is reported)
+    const long long flim = WRITE ? far_off[g + 1] : 0, nlim = WRITE ? near_off[g + 1] : 0;
+    bool over = false;
+    while (sp > 0 && !over) {
+        const int n = min(32, sp);
+        const bool act = lane < n;
+        int2 e = make_int2(0, 0);
+        if (act) e = stk[sp - n + lane];
+        __syncwarp();
+        sp -= n;
+        bool cadm = false, cnot = false, leaf = false;
+        BvhNode nd;
+        if (act) {
+            nd = node[e.x];
+            leaf = nd.leaf != 0;
+            const float d2lo = box_dist2(glx, gly, glz, ghx, ghy, ghz, nd);
+            cadm = fmaxf(gr2max, nd.r2) < __fmul_rn(theta2, d2lo);
+            const float ux = fmaxf(fmaxf(__fsub_rn(nd.lox, glx), __fsub_rn(ghx, nd.hix)), 0.f);
+            const float uy = fmaxf(fmaxf(__fsub_rn(nd.loy, gly), __fsub_rn(ghy, nd.hiy)), 0.f);
+            const float uz = fmaxf(fmaxf(__fsub_rn(nd.loz, glz), __fsub_rn(ghz, nd.hiz)), 0.f);
+            const float d2hi = __fadd_rn(__fadd_rn(__fmul_rn(ux, ux), __fmul_rn(uy, uy)), __fmul_rn(uz, uz));
+            cnot = !cadm && !(fmaxf(gr2min, nd.r2) < __fmul_rn(theta2, d2hi));
+        }
+        // certain for the whole group
+        const unsigned bf = __ballot_sync(0xffffffffu, cadm);
+        if (WRITE && cadm && fo + nfar + __popc(bf & lt) < flim) far_out[fo + nfar + __popc(bf & lt)] = e;
+        nfar += __popc(bf);
+        const unsigned bn = __ballot_sync(0xffffffffu, cnot && leaf);
+        if (WRITE && cnot && leaf && no + nnear + __popc(bn & lt) < nlim) near_out[no + nnear + __popc(bn & lt)] = e;
+        nnear += __popc(bn);
+        const unsigned bd = __ballot_sync(0xffffffffu, cnot && !leaf);
+        if (sp + 2 * __popc(bd) > cap) {
+            over = true;
+        } else {
+            if (cnot && !leaf) {
+                const int at = sp + 2 * __popc(bd & lt);
+                stk[at] = make_int2(right[e.x], e.y);
+                stk[at + 1] = make_int2(e.x + 1, e.y);
+            }
+            sp += 2 * __popc(bd);
+        }
+        // the rest: the exact per-target test, one candidate at a time
+        unsigned bi = __ballot_sync(0xffffffffu, act && !cadm && !cnot);
+        while (bi && !over) {
+            const int src = __ffs(bi) - 1;
+            bi &= bi - 1;
+            const int nid = __shfl_sync(0xffffffffu, e.x, src);
+            const unsigned msk = (unsigned)__shfl_sync(0xffffffffu, e.y, src);
+            const BvhNode n2 = node[nid];
+            bool adm = false;
+            if ((msk >> lane) & 1u) {
+                const float d2 = box_dist2(fb.lox, fb.loy, fb.loz, fb.hix, fb.hiy, fb.hiz, n2);
+                adm = fmaxf(fb.r2, n2.r2) < __fmul_rn(theta2, d2);
+            }
+            const unsigned am = __ballot_sync(0xffffffffu, adm) & msk;
+            const unsigned rest = msk & ~am;
+            if (am) {
+                if (WRITE && lane == 0 && fo + nfar < flim) far_out[fo + nfar] = make_int2(nid, (int)am);
+                ++nfar;
+            }
+            if (rest) {
+                if (n2.leaf) {
+                    if (WRITE && lane == 0 && no + nnear < nlim) near_out[no + nnear] = make_int2(nid, (int)rest);
+                    ++nnear;
+                } else if (sp + 2 > cap) {
+                    over = true;
+                } else {
+                    if (lane == 0) {
+                        stk[sp] = make_int2(right[nid], (int)rest);
+                        stk[sp + 1] = make_int2(nid + 1, (int)rest);
+                    }
+                    sp += 2;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    if (lane == 0) {
+        if (over) atomicExch(err, 1);
+        if (!WRITE) {
+            cnt[g] = nfar;
+            cnt[ngroups + 1 + g] = nnear;
+        } else if (nfar != flim - fo || nnear != nlim - no) {
+            atomicExch(err, 2);   // the two passes must agree
+        }
+    }
+}
+
+int bh_lists(tp_mesh* m, const tp_params* p, cudaStream_t st, BhLists* out, bool* ok) {
+    *ok = false;
+    TP_TRY(bvh_build(m, p, st));
+    const int nf = m->nf, nn = m->bvh_nodes;
+    const int ngroups = (nf + BHL_GROUP - 1) / BHL_GROUP;
+    auto fill = [&]() {
+        const long long* off = m->bhl_cnt.as<long long>();
+        out->ngroups = ngroups;
+        out->far_off = off;
+        out->near_off = off + ngroups + 1;
+        out->far = m->bhl_far.as<int2>();
+        out->near = m->bhl_near.as<int2>();
+    };
+    if (m->bhl_version == m->bvh_version && m->bhl_theta == p->theta) {
+        if (m->bhl_failed) return TP_OK;
+        fill();
+        *ok = true;
+        return TP_OK;
+    }
+    m->bhl_version = m->bvh_version;
+    m->bhl_theta = p->theta;
+    m->bhl_failed = true;
+    const NodeArrays na = node_arrays(m);
+    const NodeShape* shape = m->bvh_tmp.as<NodeShape>();
+    const int* right = (const int*)(shape + nn);
+    const FaceBox* fbox = (const FaceBox*)(m->bvh_perm.as<int>() + nf);
+    const int cap = 64 * (m->bvh_maxdepth + 2);
+    const int warps = 4;
+    const size_t smem = sizeof(int2) * (size_t)cap * warps;
+    if (smem > 200 * 1024) return TP_OK;            // too deep a tree for the stack: walks serve
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (smem > 48 * 1024 && dev >= 0 && dev < 64 && !attr_set[dev]) {
+        TP_CUDA(cudaFuncSetAttribute(k_bh_list<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        TP_CUDA(cudaFuncSetAttribute(k_bh_list<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr_set[dev] = true;
+    }
+    size_t scan_bytes = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, scan_bytes, (long long*)nullptr, (long long*)nullptr, ngroups + 1);
+    // offsets [2 (ngroups + 1)], counts [2 (ngroups + 1)], error word, scan workspace
+    const size_t head = 4 * ((size_t)ngroups + 1) + 8;
+    TP_TRY(ensure(m->bhl_cnt, sizeof(long long) * head + scan_bytes + 256));
+    long long* off = m->bhl_cnt.as<long long>();
+    long long* counts = off + 2 * (ngroups + 1);
+    int* err = reinterpret_cast<int*>(counts + 2 * (ngroups + 1));
+    void* scan_ws = reinterpret_cast<char*>(m->bhl_cnt.ptr) + sizeof(long long) * head;
+    TP_CUDA(cudaMemsetAsync(off, 0, sizeof(long long) * head, st));
+    const float theta2 = (float)(p->theta * p->theta);
+    const int blocks = (ngroups + warps - 1) / warps;
+    k_bh_list<false><<<blocks, 32 * warps, smem, st>>>(na.node, right, fbox, nf, theta2, cap, counts, nullptr,
+                                                       nullptr, nullptr, nullptr, err);
+    TP_LAUNCH_CHECK();
+    // counts -> exclusive offsets (the extra last entry becomes the total)
+    TP_CUDA(cub::DeviceScan::ExclusiveSum(scan_ws, scan_bytes, counts, off, ngroups + 1, st));
+    TP_CUDA(cub::DeviceScan::ExclusiveSum(scan_ws, scan_bytes, counts + ngroups + 1, off + ngroups + 1, ngroups + 1,
+                                          st));
+    long long tot[2] = {0, 0};
+    int e1 = 0;
+    TP_CUDA(cudaMemcpyAsync(&tot[0], off + ngroups, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    TP_CUDA(cudaMemcpyAsync(&tot[1], off + 2 * ngroups + 1, sizeof(long long), cudaMemcpyDeviceToHost, st));
+    TP_CUDA(cudaMemcpyAsync(&e1, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TP_CUDA(cudaStreamSynchronize(st));
+    if (e1 != 0) return TP_OK;                       // a stack overflowed: the walks serve this tree
+    // entries are addressed with int offsets inside the kernels' loops
+    if (tot[0] >= (1LL << 31) || tot[1] >= (1LL << 31)) return TP_OK;
+    if (ensure(m->bhl_far, sizeof(int2) * ((size_t)tot[0] + 1)) != TP_OK ||
+        ensure(m->bhl_near, sizeof(int2) * ((size_t)tot[1] + 1)) != TP_OK) {
+        set_error("");
+        return TP_OK;                                // no room for the lists: the walks serve
+    }
+    k_bh_list<true><<<blocks, 32 * warps, smem, st>>>(na.node, right, fbox, nf, theta2, cap, nullptr, off,
+                                                      off + ngroups + 1, m->bhl_far.as<int2>(),
+                                                      m->bhl_near.as<int2>(), err);
+    TP_LAUNCH_CHECK();
+    TP_CUDA(cudaMemcpyAsync(&e1, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TP_CUDA(cudaStreamSynchronize(st));
+    if (e1 != 0) return TP_OK;
+    m->bhl_nfar = tot[0];
+    m->bhl_nnear = tot[1];
+    m->bhl_failed = false;
+    fill();
+    *ok = true;
+    return TP_OK;
+}
+
 // device counters of Barnes-Hut interactions: [0] energy, [1] differential
 int bh_counter(tp_mesh* m, cudaStream_t st) {
     if (m->bhcount.ptr) return TP_OK;
@@ -602,9 +841,105 @@ __global__ void k_unsort_rows(const double* __restrict__ rs, const int* __restri
     if (i < nf) rows[perm[i]] = rs[i];
 }
 
+// Energy rows from the interaction lists: one warp per group of 32 sorted
+// targets, streaming the group's far entries (node terms) and near entries
+// (exact sums over the leaf's faces, T != S); lanes whose bit is not set in
+// an entry's mask add nothing. FP32 terms in runs of 32 entries, Kahan across
+// runs, FP64 result (sorted order).
+template <bool P6>
+__global__ void __launch_bounds__(128)
+k_bh_energy_list(const float4* __restrict__ node4, const float4* __restrict__ nodelo, const float4* __restrict__ sa,
+                 const float4* __restrict__ sb, const float4* __restrict__ sl, int nf, BhLists L, float halfp,
+                 const d4* __restrict__ f64a, const int* __restrict__ perm, double* __restrict__ rows,
+                 unsigned long long* __restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (g >= L.ngroups) return;
+    const int i = g * BHL_GROUP + lane;
+    const bool has = i < nf;
+    const int ii = has ? i : 0;
+    const float4 A = sa[ii], B = sb[ii], Al = sl[ii];
+    const unsigned me = 1u << lane;
+    KahanF sum;
+    float acc = 0.f;
+    int nint = 0;
+    const int f0 = (int)L.far_off[g], f1 = (int)L.far_off[g + 1];
+    int run = 0;
+#pragma unroll 4
+    for (int e = f0; e < f1; ++e) {
+        const int2 en = L.far[e];
+        const float4 c = node4[4 * en.x];          // barycenter (hi), area
+        const float4 nl = nodelo[en.x];
+        const float dx = (A.x - c.x) + (Al.x - nl.x), dy = (A.y - c.y) + (Al.y - nl.y), dz = (A.z - c.z) + (Al.z - nl.z);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float u = B.x * dx + B.y * dy + B.z * dz;
+        const float ir2 = frcp(fmaxf(r2, 1e-18f));
+        const float q = u * u * (ir2 * ir2);
+        const float K = P6 ? q * q * q : fpow(q, halfp);
+        const bool on = (unsigned)en.y & me;
+        acc = fmaf(on ? K : 0.f, c.w, acc);
+        nint += on;
+        if (++run == 32) {
+            sum.add(acc);
+            acc = 0.f;
+            run = 0;
+        }
+    }
+    sum.add(acc);
+    acc = 0.f;
+    const int n0 = (int)L.near_off[g], n1 = (int)L.near_off[g + 1];
+    for (int e = n0; e < n1; ++e) {
+        const int2 en = L.near[e];
+        const int4 fc = reinterpret_cast<const int4*>(node4)[4 * en.x + 3];   // first, count, skip, leaf
+        const bool on = (unsigned)en.y & me;
+        for (int j = fc.x; j < fc.x + fc.y; ++j) {
+            const float4 s = sa[j], l = sl[j];
+            const float dx = (A.x - s.x) + (Al.x - l.x), dy = (A.y - s.y) + (Al.y - l.y), dz = (A.z - s.z) + (Al.z - l.z);
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            const float u = B.x * dx + B.y * dy + B.z * dz;
+            const float ir2 = frcp(fmaxf(r2, 1e-18f));
+            const float q = u * u * (ir2 * ir2);
+            const float K = P6 ? q * q * q : fpow(q, halfp);
+            const bool t = on && j != i;
+            acc = fmaf(t ? K : 0.f, s.w, acc);
+            nint += t;
+        }
+        sum.add(acc);
+        acc = 0.f;
+    }
+    if (has) rows[perm[i]] = f64a[perm[i]].w * sum.value();
+    if (count && nint) atomicAdd(count, (unsigned long long)nint);
+}
+
 int energy_rows_bh(tp_mesh* m, const tp_params* p, const int32_t* tl, int nt, double* rows, cudaStream_t st) {
     TP_TRY(bvh_build(m, p, st));
     const int nf = m->nf;
+    if (!tl) {
+        // every face a target: the interaction lists of the tree
+        BhLists L;
+        bool ok = false;
+        TP_TRY(bh_lists(m, p, st, &L, &ok));
+        if (ok) {
+            TP_TRY(bh_counter(m, st));
+            const NodeArrays na = node_arrays(m);
+            ProfScope ps(m, PK_BH_ENERGY, 0.0, st);
+            unsigned long long* cnt = m->bhcount.as<unsigned long long>();
+            const float4* n4 = reinterpret_cast<const float4*>(na.node);
+            const int blocks = (L.ngroups + 3) / 4;
+            if (p->p == 6.0)
+                k_bh_energy_list<true><<<blocks, 128, 0, st>>>(n4, na.nodelo, m->bvh_f32a.as<float4>(),
+                                                               m->bvh_f32b.as<float4>(), m->bvh_f32c.as<float4>(), nf,
+                                                               L, 3.f, m->f64a.as<d4>(), m->bvh_perm.as<int>(), rows,
+                                                               cnt);
+            else
+                k_bh_energy_list<false><<<blocks, 128, 0, st>>>(n4, na.nodelo, m->bvh_f32a.as<float4>(),
+                                                                m->bvh_f32b.as<float4>(), m->bvh_f32c.as<float4>(),
+                                                                nf, L, (float)(0.5 * p->p), m->f64a.as<d4>(),
+                                                                m->bvh_perm.as<int>(), rows, cnt);
+            TP_LAUNCH_CHECK();
+            return TP_OK;
+        }
+    }
     int* perm = m->bvh_perm.as<int>();
     FaceBox* fbox = (FaceBox*)(perm + nf);
     float theta2 = (float)(p->theta * p->theta);
@@ -786,6 +1121,136 @@ k_bh_diff(const BvhNode* __restrict__ node, const float4* __restrict__ nodelo, i
     if (nint) atomicAdd(count, (unsigned long long)nint);
 }
 
+// FP32 -> FP64 by rebiasing the exponent with integer operations (exact for
+// normal numbers, zero for FP32 subnormals): a float-to-double conversion
+// instruction runs on the FP64 pipe, which this GPU has little of
+__device__ __forceinline__ double f2d_int(float x) {
+    const unsigned u = __float_as_uint(x);
+    const unsigned e = (u >> 23) & 0xffu;
+    const unsigned long long sgn = (unsigned long long)(u & 0x80000000u) << 32;
+    if (e == 0) return __longlong_as_double((long long)sgn);
+    const unsigned long long de = e == 0xffu ? 0x7ffull : (unsigned long long)(e + (1023 - 127));
+    return __longlong_as_double((long long)(sgn | (de << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+
+// sums of four values over the warp: lanes 0, 8, 16 and 24 end with the sums
+// of v0, v1, v2 and v3 (the lanes of an octet share their value); 6 shuffles
+// instead of 4 x 5
+__device__ __forceinline__ float warp_sum4(float v0, float v1, float v2, float v3) {
+    const int lane = threadIdx.x & 31;
+    const bool b4 = lane & 16, b3 = lane & 8;
+    float k0 = b4 ? v2 : v0, k1 = b4 ? v3 : v1;
+    const float s0 = b4 ? v0 : v2, s1 = b4 ? v1 : v3;
+    k0 += __shfl_xor_sync(0xffffffffu, s0, 16);
+    k1 += __shfl_xor_sync(0xffffffffu, s1, 16);
+    float keep = b3 ? k1 : k0;
+    const float send = b3 ? k0 : k1;
+    keep += __shfl_xor_sync(0xffffffffu, send, 8);
+    keep += __shfl_xor_sync(0xffffffffu, keep, 4);
+    keep += __shfl_xor_sync(0xffffffffu, keep, 2);
+    keep += __shfl_xor_sync(0xffffffffu, keep, 1);
+    return keep;
+}
+
+// Differential from the interaction lists: the target side as in k_bh_diff;
+// the source side (FULL) of an entry is summed over the lanes in its mask and
+// added with one FP64 atomic per entry (node accumulators for far entries,
+// face accumulators for the faces of near leaves).
+template <bool P6, bool FULL>
+__global__ void __launch_bounds__(128)
+k_bh_diff_list(const float4* __restrict__ node4, const float4* __restrict__ nodelo, const float4* __restrict__ sa,
+               const float4* __restrict__ sb, const float4* __restrict__ sl, int nf, BhLists L, float hm1, float p,
+               double* __restrict__ tacc, double* __restrict__ nacc, double* __restrict__ facc,
+               unsigned long long* __restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (g >= L.ngroups) return;
+    const int i0 = g * BHL_GROUP + lane;
+    const bool has = i0 < nf;
+    const int i = has ? i0 : 0;
+    const float4 A = sa[i], B = sb[i], Al = sl[i];
+    const float aS = A.w;
+    const unsigned me = 1u << lane;
+    KahanF acc[8];
+    float pt[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) pt[k] = 0.f;
+    int nint = 0;
+    auto flush = [&]() {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            acc[k].add(pt[k]);
+            pt[k] = 0.f;
+        }
+    };
+    // one interaction (source barycenter src + low part lo, weight w), masked
+    // by on; returns the source-side G, Q of this lane
+    auto interact = [&](float4 src, float4 lo, float w, bool on, float* G, float& Q) {
+        const float dx = (A.x - src.x) + (Al.x - lo.x), dy = (A.y - src.y) + (Al.y - lo.y),
+                    dz = (A.z - src.z) + (Al.z - lo.z);
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float u = B.x * dx + B.y * dy + B.z * dz;
+        const float ir2 = frcp(fmaxf(r2, 1e-18f));
+        const float ir4 = ir2 * ir2;
+        const float q = u * u * ir4;
+        const float mq = P6 ? q * q : fpow(q, hm1);
+        const float K = mq * q;
+        const float c = mq * u * ir4;
+        const float ww = on ? w : 0.f;
+        const float wc = ww * c, wK = ww * K, wKd = wK * ir2;
+        pt[0] += wc;
+        pt[1] = fmaf(wc, dx, pt[1]);
+        pt[2] = fmaf(wc, dy, pt[2]);
+        pt[3] = fmaf(wc, dz, pt[3]);
+        pt[4] = fmaf(wKd, dx, pt[4]);
+        pt[5] = fmaf(wKd, dy, pt[5]);
+        pt[6] = fmaf(wKd, dz, pt[6]);
+        pt[7] += wK;
+        const float s1 = -aS * p * wc, s2 = 2.f * aS * p * wKd;
+        G[0] = s1 * B.x + s2 * dx;
+        G[1] = s1 * B.y + s2 * dy;
+        G[2] = s1 * B.z + s2 * dz;
+        Q = on ? aS * K : 0.f;   // a_S K (the source's area derivative carries no a_T)
+        nint += on;
+    };
+    const int f0 = (int)L.far_off[g], f1 = (int)L.far_off[g + 1];
+    int run = 0;
+    for (int e = f0; e < f1; ++e) {
+        const int2 en = L.far[e];
+        const float4 c = node4[4 * en.x];
+        float G[3], Q;
+        interact(c, nodelo[en.x], c.w, (unsigned)en.y & me, G, Q);
+        if (FULL) {
+            const float r = warp_sum4(G[0], G[1], G[2], Q);
+            if ((lane & 7) == 0) atomicAdd(nacc + 4 * en.x + (lane >> 3), f2d_int(r));
+        }
+        if (++run == 32) {
+            flush();
+            run = 0;
+        }
+    }
+    flush();
+    const int n0 = (int)L.near_off[g], n1 = (int)L.near_off[g + 1];
+    for (int e = n0; e < n1; ++e) {
+        const int2 en = L.near[e];
+        const int4 fc = reinterpret_cast<const int4*>(node4)[4 * en.x + 3];
+        const bool on = (unsigned)en.y & me;
+        for (int j = fc.x; j < fc.x + fc.y; ++j) {
+            const float4 s = sa[j];
+            float G[3], Q;
+            interact(s, sl[j], s.w, on && j != i0, G, Q);
+            if (FULL) {
+                const float r = warp_sum4(G[0], G[1], G[2], Q);
+                if ((lane & 7) == 0) atomicAdd(facc + 4 * j + (lane >> 3), f2d_int(r));
+            }
+        }
+        flush();
+    }
+    if (has)
+        for (int k = 0; k < 8; ++k) tacc[(size_t)i0 * 8 + k] = acc[k].value();
+    if (nint) atomicAdd(count, (unsigned long long)nint);
+}
+
 // per node: g1 = G/a_I, q = Q - G.X_I/a_I (FP64 node data)
 __global__ void k_node_push_terms(double* __restrict__ nacc, const d4* __restrict__ node64, int nnodes) {
     int id = blockIdx.x * blockDim.x + threadIdx.x;
@@ -867,7 +1332,24 @@ int diff_adjoints_bh(tp_mesh* m, const tp_params* p, double* adj, double* erow, 
     const float4* sl = m->bvh_f32c.as<float4>();
     dim3 g((nf + 127) / 128);
     TP_TRY(bh_counter(m, st));
-    {
+    BhLists L;
+    bool lists = false;
+    TP_TRY(bh_lists(m, p, st, &L, &lists));
+    if (lists) {
+        ProfScope ps(m, PK_BH_DIFF, 0.0, st);
+        unsigned long long* cnt = m->bhcount.as<unsigned long long>() + 1;
+        const float pf = (float)p->p;
+        const float4* n4 = reinterpret_cast<const float4*>(node);
+        const int blocks = (L.ngroups + 3) / 4;
+        if (p->p == 6.0) {
+            if (full) k_bh_diff_list<true, true><<<blocks, 128, 0, st>>>(n4, nodelo, sa, sb, sl, nf, L, hm1, pf, tacc, nacc, facc, cnt);
+            else k_bh_diff_list<true, false><<<blocks, 128, 0, st>>>(n4, nodelo, sa, sb, sl, nf, L, hm1, pf, tacc, nacc, facc, cnt);
+        } else {
+            if (full) k_bh_diff_list<false, true><<<blocks, 128, 0, st>>>(n4, nodelo, sa, sb, sl, nf, L, hm1, pf, tacc, nacc, facc, cnt);
+            else k_bh_diff_list<false, false><<<blocks, 128, 0, st>>>(n4, nodelo, sa, sb, sl, nf, L, hm1, pf, tacc, nacc, facc, cnt);
+        }
+        TP_LAUNCH_CHECK();
+    } else {
         ProfScope ps(m, PK_BH_DIFF, 0.0, st);
         unsigned long long* cnt = m->bhcount.as<unsigned long long>() + 1;
         const float pf = (float)p->p;

@@ -47,6 +47,8 @@ int check_params(const tp_params* p) {
     if (p->bvh_refit != 0 && p->bvh_refit != 1) return fail(TP_ERR_INVALID_ARG, "bvh_refit must be 0 or 1");
     if (!(p->prec_self_weight >= 0.0) || !std::isfinite(p->prec_self_weight))
         return fail(TP_ERR_INVALID_ARG, "prec_self_weight must be finite and >= 0");
+    if (!(p->tau0_disp >= 0.0) || !std::isfinite(p->tau0_disp))
+        return fail(TP_ERR_INVALID_ARG, "tau0_disp must be finite and >= 0");
     return TP_OK;
 }
 
@@ -100,6 +102,7 @@ void tp_params_default(tp_params* p) {
     p->poisson_solver = TP_POISSON_CHOLESKY;
     p->bvh_refit = 0;
     p->prec_self_weight = 24.0;
+    p->tau0_disp = 0.0;
 }
 
 const char* tp_last_error(void) { return tp::last_error(); }
@@ -269,6 +272,9 @@ int tp_mesh_destroy(tp_mesh* m) {
     pins_release(m);
     chol_release(m);
     release(m->bhcount);
+    release(m->bhl_cnt);
+    release(m->bhl_far);
+    release(m->bhl_near);
     prof_release(m);
     for (auto& b : m->tmpv) release(b);
     for (auto& b : m->stepv) release(b);
@@ -436,6 +442,18 @@ int precond_step(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp_ste
         return fail(TP_ERR_INVALID_ARG, "bad solver parameters");
     DeviceGuard g(m);
     return precond_step_dev(m, p, c, rep, (cudaStream_t)stream);
+}
+
+int tp_mesh_area_volume(tp_mesh* m, double* area, double* volume, void* stream) {
+    set_error("");
+    TP_TRY(check_mesh(m));
+    if (!area && !volume) return fail(TP_ERR_INVALID_ARG, "area and volume are both NULL");
+    DeviceGuard g(m);
+    double v[2] = {0.0, 0.0};
+    TP_TRY(area_volume(m, v, (cudaStream_t)stream));
+    if (area) *area = v[0];
+    if (volume) *volume = v[1];
+    return TP_OK;
 }
 
 int tp_obstacle_set(tp_mesh* m, int nv, int nf, const double* pos, const int32_t* faces, double weight,

@@ -64,6 +64,14 @@ inline int64_t chol_ld(int64_t r) { return r == 0 ? 0 : (r | 1); }
 
 namespace chol_detail {
 
+// A separator whose front would hold more than SEP_PANEL entries (its
+// vertices times the rows of its front: its own vertices plus the ancestor
+// separator vertices next to the set it cuts, an upper bound of the front)
+// is split into a chain of supernodes of at most SEP_PANEL / rows vertices
+// each (at least SEP_MIN_CHUNK).
+constexpr long long SEP_PANEL = 24576;
+constexpr int SEP_MIN_CHUNK = 8;
+
 struct NestedDissection {
     int nv;
     const int* rowptr;
@@ -72,7 +80,9 @@ struct NestedDissection {
     std::vector<int> mark;    // vertex -> current vertex-set id, -1 once in a separator or pinned
     std::vector<int> seen;    // BFS stamp
     std::vector<int> lev;     // BFS level (valid where seen == stamp)
-    int stamp = 0;
+    std::vector<char> in_sep; // vertex placed in a separator
+    std::vector<int> bstamp;  // stamps of the boundary count
+    int stamp = 0, bst = 0;
     int next_id = 1;
     struct Node {
         std::vector<int> verts;
@@ -194,6 +204,24 @@ struct NestedDissection {
             leaf_node(C, roots);
             return;
         }
+        // rows of the separator's front: its vertices plus the separator
+        // vertices of ancestors next to C (counted before the recursion marks
+        // the separators inside C)
+        ++bst;
+        long long bnd = 0;
+        for (int v : C)
+            for (int e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+                const int u = col[e];
+                if (u != v && in_sep[u] && bstamp[u] != bst) {
+                    bstamp[u] = bst;
+                    ++bnd;
+                }
+            }
+        for (int v : sep) in_sep[v] = 1;
+        const long long rows = (long long)sep.size() + bnd;
+        int chunk = (int)sep.size();
+        if ((long long)sep.size() * rows > SEP_PANEL)
+            chunk = (int)std::max<long long>(SEP_MIN_CHUNK, SEP_PANEL / rows);
         int ia = next_id++, ib = next_id++;
         for (int v : sep) mark[v] = -1;
         for (int v : A) mark[v] = ia;
@@ -201,12 +229,18 @@ struct NestedDissection {
         std::vector<int> kids;
         build(A, ia, kids);
         build(B, ib, kids);
-        Node nd;
         std::sort(sep.begin(), sep.end());
-        nd.verts = sep;
-        nd.kids = kids;
-        nodes.push_back(nd);
-        roots.push_back((int)nodes.size() - 1);
+        // a separator with a wide front becomes a chain of supernodes of at
+        // most `chunk` vertices (same elimination order, same fill): every
+        // panel then stays narrow enough for shared memory
+        for (size_t c0 = 0; c0 < sep.size(); c0 += chunk) {
+            Node nd;
+            nd.verts.assign(sep.begin() + c0, sep.begin() + std::min(sep.size(), c0 + (size_t)chunk));
+            nd.kids = kids;
+            nodes.push_back(nd);
+            kids.assign(1, (int)nodes.size() - 1);
+        }
+        roots.push_back(kids[0]);
     }
 
     void leaf_node(std::vector<int>& C, std::vector<int>& roots) {
@@ -255,6 +289,8 @@ inline bool chol_analyze(int nv, const int* rowptr, const int* col, int leaf, Ch
     nd.mark.assign(nv, 0);
     nd.seen.assign(nv, 0);
     nd.lev.assign(nv, 0);
+    nd.in_sep.assign(nv, 0);
+    nd.bstamp.assign(nv, 0);
     for (int p : S.pinned) nd.mark[p] = -1;
     std::vector<int> all;
     for (int v = 0; v < nv; ++v)

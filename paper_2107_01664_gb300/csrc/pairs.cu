@@ -1781,6 +1781,118 @@ k_bh_apply(const BvhNode* __restrict__ node, const float4* __restrict__ nodelo, 
     if (count && nint) atomicAdd(count, (unsigned long long)nint);
 }
 
+// Barnes-Hut operator products from the interaction lists (one warp per
+// group of 32 sorted targets; lanes outside an entry's mask add nothing)
+template <int OP, int KC>
+__global__ void __launch_bounds__(128)
+k_bh_apply_list(const float4* __restrict__ node4, const float4* __restrict__ nodelo, const float4* __restrict__ sa,
+                const float4* __restrict__ sb, const float4* __restrict__ sl, int nf, BhLists Ls,
+                const float4* __restrict__ Ws, const float4* __restrict__ nodeX, const float4* __restrict__ nodeP,
+                float s_exp, float l_exp, double* __restrict__ part, unsigned long long* __restrict__ count) {
+    using L = OpLayout<OP, KC>;
+    constexpr bool LOW = (OP == TP_OP_A || OP == TP_OP_B0);
+    constexpr int NP = L::NA / 2;
+    constexpr int NW4 = L::NW4;
+    const int lane = threadIdx.x & 31;
+    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (g >= Ls.ngroups) return;
+    const int i = g * BHL_GROUP + lane;
+    const bool has = i < nf;
+    const int ii = has ? i : 0;
+    const float4 A = sa[ii], B = sb[ii], Al = sl[ii];
+    const unsigned me = 1u << lane;
+    float2 pt[NP];
+    Acc2<float> acc[NP];
+#pragma unroll
+    for (int c = 0; c < NP; ++c) pt[c] = make_float2(0.f, 0.f);
+    unsigned nint = 0;
+    const int f0 = (int)Ls.far_off[g], f1 = (int)Ls.far_off[g + 1];
+    int run = 0;
+#pragma unroll 2
+    for (int e = f0; e < f1; ++e) {
+        const int2 en = Ls.far[e];
+        const int id = en.x;
+        const bool on = (unsigned)en.y & me;
+        const float4 c = node4[4 * id];
+        const float4 nl = nodelo[id];
+        const float dx = (A.x - c.x) + (Al.x - nl.x), dy = (A.y - c.y) + (Al.y - nl.y), dz = (A.z - c.z) + (Al.z - nl.z);
+        float2 x2[2 * NW4];
+#pragma unroll
+        for (int q = 0; q < NW4; ++q) {
+            const float4 x = nodeX[(size_t)id * NW4 + q];
+            x2[2 * q] = make_float2(x.x, x.y);
+            x2[2 * q + 1] = make_float2(x.z, x.w);
+        }
+        const float r2 = r2_eps(dx, dy, dz);
+        if (OP == TP_OP_L) {
+            const float h = on ? pow_(r2, -l_exp) : 0.f;
+#pragma unroll
+            for (int k = 0; k < NP; ++k) pt[k] = pfma(h, x2[k], pt[k]);
+        } else {
+            const float hB = on ? pow_(r2, -s_exp) : 0.f;
+#pragma unroll
+            for (int k = 0; k < L::NH / 2; ++k) pt[k] = pfma(hB, x2[k], pt[k]);
+            if (LOW) {
+                const float4 p0 = nodeP[2 * id], p1 = nodeP[2 * id + 1];
+                const float ir2 = rcp_(r2);
+                const float tS = (B.x * dx + B.y * dy + B.z * dz) * ir2;
+                const float qx = p0.x * dx + p0.y * dy + p0.z * dz;
+                const float qy = p0.y * dx + p0.w * dy + p1.x * dz;
+                const float qz = p0.z * dx + p1.x * dy + p1.y * dz;
+                const float tT2 = (qx * qx + qy * qy + qz * qz) * (ir2 * ir2);   // |P_I d|^2 / |d|^4
+                const float h0 = 0.5f * fmaf(tS, tS, tT2) * hB;
+#pragma unroll
+                for (int k = L::NH / 2; k < NP; ++k) pt[k] = pfma(h0, x2[k], pt[k]);
+            }
+        }
+        nint += on;
+        if (++run == 32) {
+#pragma unroll
+            for (int k = 0; k < NP; ++k) {
+                acc[k].add(pt[k]);
+                pt[k] = make_float2(0.f, 0.f);
+            }
+            run = 0;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NP; ++k) {
+        acc[k].add(pt[k]);
+        pt[k] = make_float2(0.f, 0.f);
+    }
+    const int n0 = (int)Ls.near_off[g], n1 = (int)Ls.near_off[g + 1];
+    for (int e = n0; e < n1; ++e) {
+        const int2 en = Ls.near[e];
+        const int4 fc = reinterpret_cast<const int4*>(node4)[4 * en.x + 3];   // first, count, skip, leaf
+        const bool on = (unsigned)en.y & me;
+        for (int j = fc.x; j < fc.x + fc.y; ++j) {
+            const float4 s = sa[j], l = sl[j], mm = sb[j];
+            float2 x2[2 * NW4];
+            const bool t = on && j != i;
+#pragma unroll
+            for (int q = 0; q < NW4; ++q) {
+                const float4 x = t ? Ws[(size_t)j * NW4 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+                x2[2 * q] = make_float2(x.x, x.y);
+                x2[2 * q + 1] = make_float2(x.z, x.w);
+            }
+            // the self pair and masked lanes: zero vectors, and d moved off 0
+            const float dx = t ? (A.x - s.x) + (Al.x - l.x) : 1.f, dy = (A.y - s.y) + (Al.y - l.y),
+                        dz = (A.z - s.z) + (Al.z - l.z);
+            apply_term<float, OP, false, KC>(dx, dy, dz, B.x, B.y, B.z, mm.x, mm.y, mm.z, x2, s_exp, l_exp, pt);
+            nint += t;
+        }
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            acc[k].add(pt[k]);
+            pt[k] = make_float2(0.f, 0.f);
+        }
+    }
+    if (has)   // sorted order: consecutive lanes write consecutive words
+#pragma unroll
+        for (int c = 0; c < L::NA; ++c) part[(size_t)c * nf + i] = acc[c / 2].value(c & 1);
+    if (count && nint) atomicAdd(count, (unsigned long long)nint);
+}
+
 template <int OP, int KC>
 static int launch_bh_apply_op(tp_mesh* m, const tp_params* p, const double* v, int k, double* y,
                               cudaStream_t st) {
@@ -1802,6 +1914,9 @@ static int launch_bh_apply_op(tp_mesh* m, const tp_params* p, const double* v, i
     float4* nodeP = nodeX + (size_t)NW4 * nn;
     TP_TRY(bh_counter(m, st));
     unsigned long long* cnt = m->bhcount.as<unsigned long long>() + 2;
+    BhLists Ls;
+    bool lists = false;
+    TP_TRY(bh_lists(m, p, st, &Ls, &lists));
     for (int col0 = 0; col0 < k; col0 += KC) {
         k_face_W<float, KC><<<(nf + 255) / 256, 256, 0, st>>>(v, k, col0, m->faces.as<int>(), nf,
                                                               m->f64a.as<d4>(), m->fgrad.as<double>(), OP,
@@ -1818,9 +1933,14 @@ static int launch_bh_apply_op(tp_mesh* m, const tp_params* p, const double* v, i
         {
             ProfScope ps(m, PK_BH_APPLY, 0.0, st);
             m->prof.cols[PK_BH_APPLY] += KC;
-            k_bh_apply<OP, KC><<<(nf + 127) / 128, 128, 0, st>>>(
-                bv.node, bv.nodelo, nn, bv.sa, bv.sb, bv.sl, bv.fbox, bv.perm, nf, Ws, nodeX, nodeP,
-                (float)(p->theta * p->theta), (float)s, (float)l_exp, m->part.as<double>(), cnt);
+            if (lists)
+                k_bh_apply_list<OP, KC><<<(Ls.ngroups + 3) / 4, 128, 0, st>>>(
+                    reinterpret_cast<const float4*>(bv.node), bv.nodelo, bv.sa, bv.sb, bv.sl, nf, Ls, Ws, nodeX,
+                    nodeP, (float)s, (float)l_exp, m->part.as<double>(), cnt);
+            else
+                k_bh_apply<OP, KC><<<(nf + 127) / 128, 128, 0, st>>>(
+                    bv.node, bv.nodelo, nn, bv.sa, bv.sb, bv.sl, bv.fbox, bv.perm, nf, Ws, nodeX, nodeP,
+                    (float)(p->theta * p->theta), (float)s, (float)l_exp, m->part.as<double>(), cnt);
         }
         TP_LAUNCH_CHECK();
         k_apply_combine<OP, KC><<<(nf + 255) / 256, 256, 0, st>>>(m->part.as<double>(), 1, nf,

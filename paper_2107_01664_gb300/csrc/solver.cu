@@ -427,6 +427,10 @@ static int constraints_eval(tp_mesh* m, const double* pos, double vals[2], doubl
     return TP_OK;
 }
 
+int area_volume(tp_mesh* m, double out[2], cudaStream_t st) {
+    return constraints_eval(m, m->pos.as<double>(), out, nullptr, nullptr, st);
+}
+
 // ---------------------------------------------------------------------------
 // one constrained descent step
 // ---------------------------------------------------------------------------
@@ -473,6 +477,24 @@ __global__ void k_bary_add(const int* __restrict__ vcomp, int nv, const double* 
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (size_t)nv * 3) return;
     x[i] += t[3 * (size_t)vcomp[i / 3] + (i % 3)];
+}
+
+// max over vertices of |x_v|^2 (one block, fixed order of the final
+// reduction: deterministic)
+__global__ void k_max_norm2(const double* __restrict__ x, int nv, double* __restrict__ out) {
+    __shared__ double red[256];
+    double mx = 0.0;
+    for (int v = threadIdx.x; v < nv; v += blockDim.x) {
+        const double a = x[3 * (size_t)v], b = x[3 * (size_t)v + 1], c = x[3 * (size_t)v + 2];
+        mx = fmax(mx, a * a + b * b + c * c);
+    }
+    red[threadIdx.x] = mx;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + k]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
 }
 
 // x += the translation of each component by minus the area-weighted mean of g
@@ -573,8 +595,19 @@ int precond_step_dev(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp
         const double* a1[1] = {g};
         TP_TRY(dots(m, a1, x, 1, n, &r.slope, st));
     }
-    // 5. Armijo line search on E(f + tau x)
+    // 5. Armijo line search on E(f + tau x); with tau0_disp the first trial
+    //    moves no vertex by more than tau0_disp face sizes
     double tau = p->tau0;
+    if (p->tau0_disp > 0.0) {
+        TP_TRY(ensure(m->rowsum, sizeof(double) * 8));
+        k_max_norm2<<<1, 256, 0, st>>>(x, m->nv, m->rowsum.as<double>() + 4);
+        TP_LAUNCH_CHECK();
+        double mx2 = 0.0;
+        TP_CUDA(cudaMemcpyAsync(&mx2, m->rowsum.as<double>() + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+        TP_CUDA(cudaStreamSynchronize(st));
+        const double h = std::sqrt(std::max(phi0[0], 0.0) / m->nf);
+        if (mx2 > 0.0 && h > 0.0) tau = std::min(tau, p->tau0_disp * h / std::sqrt(mx2));
+    }
     double* ftrial = m->pos.as<double>();
     int trials = 0;
     double E1 = E0;

@@ -99,6 +99,19 @@ __device__ __forceinline__ float box_dist2(float alx, float aly, float alz, floa
     return __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
 }
 
+// Barnes-Hut interaction lists (per group of 32 consecutive sorted targets):
+// far entries (node, mask): node admissible for the targets of the group whose
+// lane bit is set in mask, and none of its ancestors admissible for them;
+// near entries (leaf, mask): an inadmissible leaf of those targets
+constexpr int BHL_GROUP = 32;
+struct BhLists {
+    int ngroups = 0;
+    const long long* far_off = nullptr;    // [ngroups + 1]
+    const long long* near_off = nullptr;   // [ngroups + 1]
+    const int2* far = nullptr;
+    const int2* near = nullptr;
+};
+
 // read-only view of a built tree for kernels outside bvh.cu
 struct BvhView {
     int nnodes = 0, maxdepth = 0;
@@ -197,6 +210,15 @@ struct tp_mesh {
     tp::Buf bvh_node, bvh_perm, bvh_keys, bvh_tmp, bvh_sortws;
     tp::Buf bvh_f32a, bvh_f32b, bvh_f32c;   // face tables (and low parts) permuted to Morton order
     tp::Buf bh_apply_ws;          // Barnes-Hut applies: sorted X vectors, node sums, node projectors
+    // Barnes-Hut interaction lists of the current tree (bhlist.cu): per group
+    // of 32 sorted targets, (node, lane mask) entries of the admissible nodes
+    // and of the inadmissible leaves
+    unsigned long long bvh_version = 0;   // incremented by every tree build or refit
+    unsigned long long bhl_version = 0;   // tree version the lists were built for (0: none)
+    double bhl_theta = -1.0;
+    long long bhl_nfar = 0, bhl_nnear = 0;
+    bool bhl_failed = false;              // the lists could not be built for this tree (walk kernels serve)
+    tp::Buf bhl_cnt, bhl_far, bhl_near;
     // workspaces
     tp::Buf part, part2, scal, corner, wv64, wv32, tmpv[8];
     tp::Buf io_in, io_out, adj, erow, tlist, rowsum;
@@ -276,6 +298,9 @@ int bh_counter(tp_mesh* m, cudaStream_t st);
 constexpr int BH_NCOUNT = 4;
 int bh_counts_read(tp_mesh* m, unsigned long long out[BH_NCOUNT], bool reset, cudaStream_t st);
 int bvh_view(tp_mesh* m, const tp_params* p, cudaStream_t st, BvhView* out);   // builds the tree if needed
+// interaction lists of the tree for p->theta (built on first use per tree and
+// theta); *ok = false when they cannot be built (the walk kernels then serve)
+int bh_lists(tp_mesh* m, const tp_params* p, cudaStream_t st, BhLists* out, bool* ok);
 
 // -------- cg.cu ------------------------------------------------------------
 int laplacian_setup(tp_mesh* m);                        // CSR pattern (host, once)
@@ -342,5 +367,7 @@ int precond_apply_dev(tp_mesh* m, const tp_params* p, const double* b, int k, do
                       cudaStream_t st, int* cg_iters, bool strict = true);
 int precond_step_dev(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp_step_report* rep,
                      cudaStream_t st);
+// total area (§7.1.3) and enclosed signed volume (§7.1.4) of the current positions (host)
+int area_volume(tp_mesh* m, double out[2], cudaStream_t st);
 
 }  // namespace tp

@@ -120,3 +120,18 @@ def test_leaf_of_one_vertex(driver):
     info, z = run(driver, C, b, 1)
     assert info["nnode"] >= 2
     assert np.linalg.norm(C @ z - b) <= 1e-12 * np.linalg.norm(b)
+
+
+def test_long_separators_become_chains(driver):
+    # an icosphere of level 6 (40,962 vertices) has separators whose fronts
+    # are too wide for one panel: they are split into chains of supernodes,
+    # and the factorisation through the chained tree still solves exactly
+    from synth import icosphere
+    V, F = icosphere(6)
+    C = O.cotan_laplacian(V, F)
+    b = O.project_mean_zero(vertex_vectors(len(V), 2, 5))
+    info, z = run(driver, C, b, 64)
+    assert info["n"] == len(V) - 1
+    assert info["levels"] > 12            # the chains deepen the tree
+    ref = O.poisson_solve(C, b)
+    assert np.linalg.norm(O.project_mean_zero(z) - ref) <= 1e-10 * np.linalg.norm(ref)

@@ -262,6 +262,26 @@ def test_precond_step_matches_exact_saddle_solution(lib):
     assert max(abs(x) for x in rep["phi_after"]) < 0.1 * max(abs(x) for x in rep["phi_before"])
 
 
+def test_precond_step_displacement_bounded_first_trial_matches_oracle(lib):
+    # tau0_disp: the line search starts where no vertex moves by more than
+    # 0.25 face sizes; the FP64 path takes the oracle's Armijo step
+    import torch
+    V, F = small_mesh("ico3", seed=9)
+    A0, V0 = O.total_area(V, F), O.total_volume(V, F)
+    ref = O.precond_step(V, F, A0, V0, tau0_disp=0.25)
+    with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as m:
+        c = lib.tp_constraints(flags=3, A0=A0, V0=V0)
+        p = lib.params(precision=1, krylov_tol=1e-11, krylov_max=600, cg_tol=1e-12, tau0_disp=0.25)
+        rep = lib.precond_step(m, c, p)
+        f_new = m.get_positions()
+    assert rep["status"] == 0
+    assert rel(rep["tau"], ref["tau"]) < 1e-9        # the same trial (up to the rounding of max |x|)
+    h = np.sqrt(O.total_area(V, F) / len(F))
+    assert rep["tau"] * np.sqrt((ref["x"] ** 2).sum(axis=1)).max() <= 0.25 * h * (1 + 1e-12)
+    assert rel(f_new - V, ref["f_new"] - V) < 1e-6
+    assert rel(rep["E_after"], ref["E1"]) < 1e-7
+
+
 def test_precond_step_repeated_projection_matches_oracle(lib):
     import torch
     V, F = small_mesh("ico2", seed=8)

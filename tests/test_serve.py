@@ -26,8 +26,21 @@ def test_failing_requests_do_not_stop_the_loop():
     assert srv._used == 0                      # every admission was released
 
 
-def test_admission_respects_the_budget_without_gpu_work():
+def _bare_server(budget, fair_s=None, t0=None):
     srv = serve.Server.__new__(serve.Server)
+    srv.params = None
+    srv.budget = budget
+    srv._used = 0
+    srv.peak_used = 0
+    srv.fair_s = fair_s
+    srv._t0 = t0
+    srv.bh_above = None
+    return srv
+
+
+def test_admission_respects_the_budget_without_gpu_work():
+    # fair_s = None: first come, first served among the requests that fit
+    srv = _bare_server(100)
     srv.params = None
     srv.budget = 100
     srv._used = 0
@@ -47,6 +60,32 @@ def test_admission_respects_the_budget_without_gpu_work():
     assert srv._admit().rid == 3               # larger than the budget: admitted alone
 
 
+def test_admission_smallest_first_within_the_fairness_window():
+    import time
+    # requests that arrived less than fair_s ago go smallest first; one that
+    # waited longer goes before all of them
+    now = time.perf_counter()
+    srv = _bare_server(1000, fair_s=5.0, t0=now - 10.0)      # "now" is 10 s into the run
+    sizes = {0: 300, 1: 100, 2: 200, 3: 50}
+    arrivals = {0: 9.0, 1: 9.5, 2: 2.0, 3: 9.8}                # rid 2 has waited 8 s
+    srv.footprint = lambda r: sizes[r.rid]
+    srv._pending = [serve.Request(arrival=arrivals[i], rid=i, V=np.zeros((3, 3)), F=np.zeros((1, 3)))
+                    for i in range(4)]
+    order = [srv._admit().rid for _ in range(4)]
+    assert order == [2, 3, 1, 0]
+
+
+def test_bh_above_switches_large_meshes_to_barnes_hut():
+    import paper_2107_01664_gb300 as tp
+    srv = _bare_server(1 << 40)
+    srv.params = tp.params()
+    srv.bh_above, srv.bh_theta = 1000, 0.5
+    small = serve.Request(arrival=0.0, rid=0, V=np.zeros((3, 3)), F=np.zeros((800, 3)))
+    large = serve.Request(arrival=0.0, rid=1, V=np.zeros((3, 3)), F=np.zeros((5000, 3)))
+    assert srv.params_for(small).theta == 0.0
+    assert srv.params_for(large).theta == 0.5 and srv.params.theta == 0.0
+
+
 @pytest.mark.gpu
 def test_results_are_the_same_alone_and_in_the_mix(lib):
     import paper_2107_01664_gb300 as tp
@@ -60,7 +99,7 @@ def test_results_are_the_same_alone_and_in_the_mix(lib):
     assert mix.peak_used <= budget
     assert mix.max_concurrency >= 2
     alone = serve.Server(slots=1, hbm_budget=budget, step_params=p)
-    res_alone = alone.run([serve.Request(arrival=0.0, rid=r.rid, V=r.V, F=r.F, A0=r.A0, V0=r.V0) for r in reqs])
+    res_alone = alone.run([serve.Request(arrival=0.0, rid=r.rid, V=r.V, F=r.F) for r in reqs])
     for a, b in zip(res_mix, res_alone):
         d = np.linalg.norm(a.positions - b.positions) / np.linalg.norm(b.positions)
         assert d <= 1e-12, (a.rid, d)
