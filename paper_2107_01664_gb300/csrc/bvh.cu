@@ -911,6 +911,132 @@ k_bh_energy_list(const float4* __restrict__ node4, const float4* __restrict__ no
     if (count && nint) atomicAdd(count, (unsigned long long)nint);
 }
 
+// packed FP32 pair arithmetic (two IEEE lanes per instruction)
+__device__ __forceinline__ unsigned long long bp2(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ float2 bu2(unsigned long long r) {
+    float2 v;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+    return v;
+}
+
+// p = 6 term of one target against two sources (lanes), with compensated
+// differences: K a per lane, d = (t - s) + (tl - sl), K = ((N.d)^2/|d|^4)^3,
+// |d|^2 floored at 1e-18 (the self pair gives 0)
+__device__ __forceinline__ unsigned long long bh_energy2_p6(
+    unsigned long long tx, unsigned long long ty, unsigned long long tz, unsigned long long ux,
+    unsigned long long uy, unsigned long long uz, unsigned long long nx, unsigned long long ny,
+    unsigned long long nz, unsigned long long sx, unsigned long long sy, unsigned long long sz,
+    unsigned long long lx, unsigned long long ly, unsigned long long lz, unsigned long long sa,
+    unsigned long long acc) {
+    unsigned long long out;
+    asm("{\n\t.reg .b64 dx, dy, dz, ex, ey, ez, r2, u, ir2, q;\n\t.reg .f32 lo, hi;\n\t"
+        "sub.rn.f32x2 dx, %1, %10;\n\t"
+        "sub.rn.f32x2 dy, %2, %11;\n\t"
+        "sub.rn.f32x2 dz, %3, %12;\n\t"
+        "sub.rn.f32x2 ex, %4, %13;\n\t"
+        "sub.rn.f32x2 ey, %5, %14;\n\t"
+        "sub.rn.f32x2 ez, %6, %15;\n\t"
+        "add.rn.f32x2 dx, dx, ex;\n\t"
+        "add.rn.f32x2 dy, dy, ey;\n\t"
+        "add.rn.f32x2 dz, dz, ez;\n\t"
+        "mul.rn.f32x2 r2, dx, dx;\n\t"
+        "fma.rn.f32x2 r2, dy, dy, r2;\n\t"
+        "fma.rn.f32x2 r2, dz, dz, r2;\n\t"
+        "mul.rn.f32x2 u, %7, dx;\n\t"
+        "fma.rn.f32x2 u, %8, dy, u;\n\t"
+        "fma.rn.f32x2 u, %9, dz, u;\n\t"
+        "mov.b64 {lo, hi}, r2;\n\t"
+        "max.f32 lo, lo, 0f219392EF;\n\t"
+        "max.f32 hi, hi, 0f219392EF;\n\t"
+        "rcp.approx.ftz.f32 lo, lo;\n\t"
+        "rcp.approx.ftz.f32 hi, hi;\n\t"
+        "mov.b64 ir2, {lo, hi};\n\t"
+        "mul.rn.f32x2 u, u, ir2;\n\t"
+        "mul.rn.f32x2 q, u, u;\n\t"
+        "mul.rn.f32x2 u, q, q;\n\t"
+        "mul.rn.f32x2 q, u, q;\n\t"
+        "fma.rn.f32x2 %0, q, %16, %17;\n\t}"
+        : "=l"(out)
+        : "l"(tx), "l"(ty), "l"(tz), "l"(ux), "l"(uy), "l"(uz), "l"(nx), "l"(ny), "l"(nz), "l"(sx), "l"(sy),
+          "l"(sz), "l"(lx), "l"(ly), "l"(lz), "l"(sa), "l"(acc));
+    return out;
+}
+
+// k_bh_energy_list for p = 6 with two list entries (or two leaf faces) per
+// packed instruction
+__global__ void __launch_bounds__(128)
+k_bh_energy_list2(const float4* __restrict__ node4, const float4* __restrict__ nodelo, const float4* __restrict__ sa,
+                  const float4* __restrict__ sb, const float4* __restrict__ sl, int nf, BhLists L,
+                  const d4* __restrict__ f64a, const int* __restrict__ perm, double* __restrict__ rows,
+                  unsigned long long* __restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (g >= L.ngroups) return;
+    const int i = g * BHL_GROUP + lane;
+    const bool has = i < nf;
+    const int ii = has ? i : 0;
+    const float4 A = sa[ii], B = sb[ii], Al = sl[ii];
+    const unsigned long long TX = bp2(A.x, A.x), TY = bp2(A.y, A.y), TZ = bp2(A.z, A.z);
+    const unsigned long long UX = bp2(Al.x, Al.x), UY = bp2(Al.y, Al.y), UZ = bp2(Al.z, Al.z);
+    const unsigned long long NX = bp2(B.x, B.x), NY = bp2(B.y, B.y), NZ = bp2(B.z, B.z);
+    const unsigned me = 1u << lane;
+    KahanF sum;
+    int nint = 0;
+    const int f0 = (int)L.far_off[g], f1 = (int)L.far_off[g + 1];
+    unsigned long long acc = 0ull;
+    int run = 0;
+#pragma unroll 2
+    for (int e = f0; e < f1; e += 2) {
+        const int2 en0 = L.far[e];
+        const bool two = e + 1 < f1;
+        const int2 en1 = two ? L.far[e + 1] : make_int2(en0.x, 0);
+        const float4 c0 = node4[4 * en0.x], c1 = node4[4 * en1.x];
+        const float4 l0 = nodelo[en0.x], l1 = nodelo[en1.x];
+        const bool on0 = (unsigned)en0.y & me, on1 = (unsigned)en1.y & me;
+        acc = bh_energy2_p6(TX, TY, TZ, UX, UY, UZ, NX, NY, NZ, bp2(c0.x, c1.x), bp2(c0.y, c1.y), bp2(c0.z, c1.z),
+                            bp2(l0.x, l1.x), bp2(l0.y, l1.y), bp2(l0.z, l1.z),
+                            bp2(on0 ? c0.w : 0.f, on1 ? c1.w : 0.f), acc);
+        nint += (int)on0 + (int)on1;
+        if (++run == 16) {
+            const float2 a = bu2(acc);
+            sum.add(a.x + a.y);
+            acc = 0ull;
+            run = 0;
+        }
+    }
+    {
+        const float2 a = bu2(acc);
+        sum.add(a.x + a.y);
+        acc = 0ull;
+    }
+    const int n0 = (int)L.near_off[g], n1 = (int)L.near_off[g + 1];
+    for (int e = n0; e < n1; ++e) {
+        const int2 en = L.near[e];
+        const int4 fc = reinterpret_cast<const int4*>(node4)[4 * en.x + 3];   // first, count, skip, leaf
+        const bool on = (unsigned)en.y & me;
+        const int j1 = fc.x + fc.y;
+        for (int j = fc.x; j < j1; j += 2) {
+            const bool two = j + 1 < j1;
+            const float4 s0 = sa[j], s1 = sa[two ? j + 1 : j];
+            const float4 q0 = sl[j], q1 = sl[two ? j + 1 : j];
+            const bool t0 = on && j != i, t1 = on && two && j + 1 != i;
+            acc = bh_energy2_p6(TX, TY, TZ, UX, UY, UZ, NX, NY, NZ, bp2(s0.x, s1.x), bp2(s0.y, s1.y),
+                                bp2(s0.z, s1.z), bp2(q0.x, q1.x), bp2(q0.y, q1.y), bp2(q0.z, q1.z),
+                                bp2(t0 ? s0.w : 0.f, t1 ? s1.w : 0.f), acc);
+            nint += (int)t0 + (int)t1;
+        }
+        const float2 a = bu2(acc);
+        sum.add(a.x + a.y);
+        acc = 0ull;
+    }
+    if (has) rows[perm[i]] = f64a[perm[i]].w * sum.value();
+    if (count && nint) atomicAdd(count, (unsigned long long)nint);
+}
+
 int energy_rows_bh(tp_mesh* m, const tp_params* p, const int32_t* tl, int nt, double* rows, cudaStream_t st) {
     TP_TRY(bvh_build(m, p, st));
     const int nf = m->nf;
@@ -927,10 +1053,9 @@ int energy_rows_bh(tp_mesh* m, const tp_params* p, const int32_t* tl, int nt, do
             const float4* n4 = reinterpret_cast<const float4*>(na.node);
             const int blocks = (L.ngroups + 3) / 4;
             if (p->p == 6.0)
-                k_bh_energy_list<true><<<blocks, 128, 0, st>>>(n4, na.nodelo, m->bvh_f32a.as<float4>(),
-                                                               m->bvh_f32b.as<float4>(), m->bvh_f32c.as<float4>(), nf,
-                                                               L, 3.f, m->f64a.as<d4>(), m->bvh_perm.as<int>(), rows,
-                                                               cnt);
+                k_bh_energy_list2<<<blocks, 128, 0, st>>>(n4, na.nodelo, m->bvh_f32a.as<float4>(),
+                                                          m->bvh_f32b.as<float4>(), m->bvh_f32c.as<float4>(), nf, L,
+                                                          m->f64a.as<d4>(), m->bvh_perm.as<int>(), rows, cnt);
             else
                 k_bh_energy_list<false><<<blocks, 128, 0, st>>>(n4, na.nodelo, m->bvh_f32a.as<float4>(),
                                                                 m->bvh_f32b.as<float4>(), m->bvh_f32c.as<float4>(),

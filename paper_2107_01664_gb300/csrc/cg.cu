@@ -691,12 +691,12 @@ int cg_trace(tp_mesh* m, unsigned long long out[10]) {
 }
 
 int cg_solve(tp_mesh* m, const tp_params* p, const double* b, int k, double* z_out, cudaStream_t st,
-             int* iters) {
+             int* iters, bool deferred) {
     if (k < 1 || k > KMAX) return fail(TP_ERR_INVALID_ARG, "cg: k must be in 1..9");
     TP_TRY(laplacian_values(m, st));
     if (p->poisson_solver == TP_POISSON_CHOLESKY) {
         bool used = false;
-        TP_TRY(chol_solve(m, p, b, k, z_out, st, iters, &used));
+        TP_TRY(chol_solve(m, p, b, k, z_out, st, iters, &used, deferred));
         if (used) return TP_OK;
     }
     // FP64 vectors in both precision modes: with FP32 vectors the Jacobi-CG
@@ -819,6 +819,30 @@ int dot_pairs(tp_mesh* m, const double* const* xs, const double* const* ys, int 
     return TP_OK;
 }
 
+// as dot_pairs, the results left in device memory out_dev [nvec] (no host
+// synchronisation)
+int dot_pairs_dev(tp_mesh* m, const double* const* xs, const double* const* ys, int nvec, size_t n, double* out_dev,
+                  cudaStream_t st) {
+    if (nvec < 1 || nvec > DOT_PAIRS_MAX) return fail(TP_ERR_INVALID_ARG, "dots: too many vectors");
+    int nblk = (int)std::min<size_t>((n + DOT_T - 1) / DOT_T, (size_t)sm_count());
+    if (nblk < 1) nblk = 1;
+    TP_TRY(ensure(m->part2, sizeof(double) * ((size_t)nblk * DOT_MAXV + DOT_PAIRS_MAX)));
+    double* part = m->part2.as<double>();
+    for (int j0 = 0; j0 < nvec; j0 += DOT_MAXV) {
+        const int nc = std::min(DOT_MAXV, nvec - j0);
+        PtrList px, py;
+        for (int j = 0; j < nc; ++j) {
+            px.p[j] = xs[j0 + j];
+            py.p[j] = ys[j0 + j];
+        }
+        k_multidot<<<nblk, DOT_T, 0, st>>>(px, py, nc, n, part);
+        TP_LAUNCH_CHECK();
+        k_multidot_final<<<1, DOT_MAXV, 0, st>>>(part, nblk, nc, out_dev + j0);
+        TP_LAUNCH_CHECK();
+    }
+    return TP_OK;
+}
+
 int dots(tp_mesh* m, const double* const* xs, const double* y, int nvec, size_t n, double* out_host,
          cudaStream_t st) {
     std::vector<const double*> ys(nvec, y);
@@ -844,6 +868,27 @@ int lincomb(double* y, const double* const* xs, const double* coef, int nvec, si
         cl.c[j] = coef[j];
     }
     k_lincomb<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(y, pl, cl, nvec, n, beta);
+    TP_LAUNCH_CHECK();
+    return TP_OK;
+}
+
+// y = beta y + scale * sum_j coef_dev[j] xs[j], the coefficients read from
+// device memory
+__global__ void k_lincomb_dev(double* __restrict__ y, PtrList xs, const double* __restrict__ coef, double scale,
+                              int nvec, size_t n, double beta) {
+    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = beta == 0.0 ? 0.0 : beta * y[i];
+    for (int j = 0; j < nvec; ++j) s += scale * coef[j] * xs.p[j][i];
+    y[i] = s;
+}
+
+int lincomb_dev(double* y, const double* const* xs, const double* coef_dev, double scale, int nvec, size_t n,
+                double beta, cudaStream_t st) {
+    if (nvec < 0 || nvec > DOT_MAXV) return fail(TP_ERR_INVALID_ARG, "lincomb: too many vectors");
+    PtrList pl;
+    for (int j = 0; j < nvec; ++j) pl.p[j] = xs[j];
+    k_lincomb_dev<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(y, pl, coef_dev, scale, nvec, n, beta);
     TP_LAUNCH_CHECK();
     return TP_OK;
 }

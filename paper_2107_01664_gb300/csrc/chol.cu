@@ -75,6 +75,11 @@ struct CholState {
     int ncomp = 1;
     // refinement sweeps captured as CUDA graphs, one per column count, keyed
     // by the buffers and scalars baked into their launches
+    // deferred solves (inside flexible GMRES): the pivot check of the current
+    // factor is read once, and the sweeps' wait errors and unconverged
+    // columns accumulate in dflags [2] for the caller to read once per step
+    bool pivot_known = false, pivot_ok = false;
+    Buf dflags;
     struct SweepGraph {
         cudaGraphExec_t exec = nullptr;
         const void* key[4] = {};
@@ -841,7 +846,7 @@ void chol_release(tp_mesh* m) {
     Buf* all[] = {&c->nodes, &c->level_nodes, &c->child_idx, &c->rel, &c->struct_pos, &c->asm_dst,
                   &c->asm_src, &c->perm, &c->comp_ptr, &c->comp_verts, &c->comp_of, &c->parent, &c->fdone,
                   &c->bdone, &c->L, &c->U,
-                  &c->uvec, &c->ybuf, &c->xbuf, &c->ctl, &c->part, &c->x, &c->r, &c->bp};
+                  &c->uvec, &c->ybuf, &c->xbuf, &c->ctl, &c->part, &c->x, &c->r, &c->bp, &c->dflags};
     for (Buf* b : all) release(*b);
     for (auto& g : c->graph)
         if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -851,7 +856,34 @@ void chol_release(tp_mesh* m) {
 }
 
 void chol_invalidate(tp_mesh* m) {
-    if (m->chol) m->chol->factored = false;
+    if (m->chol) {
+        m->chol->factored = false;
+        m->chol->pivot_known = false;
+    }
+}
+
+// after the sweeps of a deferred solve: accumulate its wait error and
+// whether it stopped short of the tolerance
+__global__ void k_chol_defer_flags(const CholCtl* __restrict__ ctl, int* __restrict__ flags) {
+    if (threadIdx.x == 0) {
+        if (ctl->err) flags[0] = 1;
+        if (!ctl->done || ctl->stalled) flags[1] = 1;
+    }
+}
+
+int chol_deferred_flags(tp_mesh* m, cudaStream_t st, int* err, int* unconverged, bool reset) {
+    *err = *unconverged = 0;
+    CholState* c = m->chol;
+    if (!c || !c->dflags.ptr) return TP_OK;
+    if (!reset) {
+        int h[2] = {0, 0};
+        TP_CUDA(cudaMemcpyAsync(h, c->dflags.ptr, sizeof(h), cudaMemcpyDeviceToHost, st));
+        TP_CUDA(cudaStreamSynchronize(st));
+        *err = h[0];
+        *unconverged = h[1];
+    }
+    TP_CUDA(cudaMemsetAsync(c->dflags.ptr, 0, 2 * sizeof(int), st));
+    return TP_OK;
 }
 
 template <class T>
@@ -1113,8 +1145,21 @@ static int sweep_graph(tp_mesh* m, int rgrid, double* partr, double tol2, int ca
 
 template <int K>
 static int chol_run(tp_mesh* m, const tp_params* p, const double* b, double* z_out, cudaStream_t st, int* iters,
-                    bool* handed_off) {
+                    bool* handed_off, bool deferred) {
     CholState* c = m->chol;
+    if (deferred && !c->pivot_known) {
+        // the factor's pivot check, once per factorisation
+        int bp = 0;
+        TP_CUDA(cudaMemcpyAsync(&bp, reinterpret_cast<char*>(c->ctl.ptr) + offsetof(CholCtl, bad_pivot), sizeof(int),
+                                cudaMemcpyDeviceToHost, st));
+        TP_CUDA(cudaStreamSynchronize(st));
+        c->pivot_ok = bp == 0;
+        c->pivot_known = true;
+    }
+    if (deferred && !c->pivot_ok) {
+        *handed_off = true;
+        return TP_OK;
+    }
     const int nv = m->nv;
     const size_t n = (size_t)nv * K;
     TP_TRY(ensure(c->x, sizeof(double) * n));
@@ -1142,6 +1187,26 @@ static int chol_run(tp_mesh* m, const tp_params* p, const double* b, double* z_o
     TP_LAUNCH_CHECK();
     CholState::SweepGraph* g = nullptr;
     TP_TRY(sweep_graph<K>(m, rgrid, partr, tol2, cap, &g));
+    if (deferred) {
+        // no host read: the sweeps that cg_tol needs at about three digits
+        // per sweep, then the flags; the caller reads them once per step
+        if (!c->dflags.ptr) {
+            TP_TRY(ensure(c->dflags, 4 * sizeof(int)));
+            TP_CUDA(cudaMemsetAsync(c->dflags.ptr, 0, 4 * sizeof(int), st));   // fresh memory holds garbage
+        }
+        const int sweeps = std::min(cap, std::max(1, (int)std::ceil(-std::log10(std::max(p->cg_tol, 1e-300)) / 3.0)));
+        const int graphs = (sweeps + CH_SWEEPS_PER_GRAPH - 1) / CH_SWEEPS_PER_GRAPH;
+        for (int gi = 0; gi < graphs; ++gi) {
+            ProfScope ps(m, PK_CHOL_SOLVE, c->solve_bytes * CH_SWEEPS_PER_GRAPH, st);
+            TP_CUDA(cudaGraphLaunch(g->exec, st));
+            count_launches(g->kernels);
+        }
+        k_chol_defer_flags<<<1, 32, 0, st>>>(c->ctl.as<CholCtl>(), c->dflags.as<int>());
+        TP_LAUNCH_CHECK();
+        if (iters) *iters = graphs * CH_SWEEPS_PER_GRAPH;
+        TP_TRY(comp_project(m, c->x.as<double>(), z_out, K, st));
+        return TP_OK;
+    }
     CholCtl h{};
     int launched = 0;
     for (;;) {
@@ -1168,7 +1233,7 @@ static int chol_run(tp_mesh* m, const tp_params* p, const double* b, double* z_o
 // z = C^+ b by the factor; *used = false when the factor cannot serve this
 // mesh or this right-hand side (the caller then runs CG)
 int chol_solve(tp_mesh* m, const tp_params* p, const double* b, int k, double* z_out, cudaStream_t st, int* iters,
-               bool* used) {
+               bool* used, bool deferred) {
     *used = false;
     if (k < 1 || k > CH_KMAX) return fail(TP_ERR_INVALID_ARG, "cotan solve: k must be in 1..9");
     TP_TRY(laplacian_values(m, st));
@@ -1178,15 +1243,15 @@ int chol_solve(tp_mesh* m, const tp_params* p, const double* b, int k, double* z
     bool handed = false;
     int it = 0;
     switch (k) {
-        case 1: TP_TRY(chol_run<1>(m, p, b, z_out, st, &it, &handed)); break;
-        case 2: TP_TRY(chol_run<2>(m, p, b, z_out, st, &it, &handed)); break;
-        case 3: TP_TRY(chol_run<3>(m, p, b, z_out, st, &it, &handed)); break;
-        case 4: TP_TRY(chol_run<4>(m, p, b, z_out, st, &it, &handed)); break;
-        case 5: TP_TRY(chol_run<5>(m, p, b, z_out, st, &it, &handed)); break;
-        case 6: TP_TRY(chol_run<6>(m, p, b, z_out, st, &it, &handed)); break;
-        case 7: TP_TRY(chol_run<7>(m, p, b, z_out, st, &it, &handed)); break;
-        case 8: TP_TRY(chol_run<8>(m, p, b, z_out, st, &it, &handed)); break;
-        default: TP_TRY(chol_run<9>(m, p, b, z_out, st, &it, &handed)); break;
+        case 1: TP_TRY(chol_run<1>(m, p, b, z_out, st, &it, &handed, deferred)); break;
+        case 2: TP_TRY(chol_run<2>(m, p, b, z_out, st, &it, &handed, deferred)); break;
+        case 3: TP_TRY(chol_run<3>(m, p, b, z_out, st, &it, &handed, deferred)); break;
+        case 4: TP_TRY(chol_run<4>(m, p, b, z_out, st, &it, &handed, deferred)); break;
+        case 5: TP_TRY(chol_run<5>(m, p, b, z_out, st, &it, &handed, deferred)); break;
+        case 6: TP_TRY(chol_run<6>(m, p, b, z_out, st, &it, &handed, deferred)); break;
+        case 7: TP_TRY(chol_run<7>(m, p, b, z_out, st, &it, &handed, deferred)); break;
+        case 8: TP_TRY(chol_run<8>(m, p, b, z_out, st, &it, &handed, deferred)); break;
+        default: TP_TRY(chol_run<9>(m, p, b, z_out, st, &it, &handed, deferred)); break;
     }
     if (iters) *iters = it;
     *used = !handed;

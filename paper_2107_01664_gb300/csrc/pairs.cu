@@ -1374,34 +1374,40 @@ k_apply_wide(const float4* __restrict__ fa, const float4* __restrict__ fb, const
             }
 }
 
-// as k_apply_combine, from FP32 Kahan pairs (s, c) per split: the splits are
-// added in a fixed order with FP32 compensation, the result taken as
-// (double)S - (double)C, then the FP64 per-face combination
+// sums over the source splits of the wide kernel's partial Kahan pairs, one
+// thread per (accumulator, face): the values s_k and -c_k of the splits in a
+// fixed order with FP32 compensation, the result (double)S - (double)C
+__global__ void k_split_sum2(const float2* __restrict__ part, int nsplit, int na, int nf, double* __restrict__ out) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)na * nf) return;
+    float a = 0.f, ca = 0.f;
+#pragma unroll 4
+    for (int sp = 0; sp < nsplit; ++sp) {
+        const float2 v = part[(size_t)sp * na * nf + idx];
+        float y = v.x - ca;
+        float t = a + y;
+        ca = (t - a) - y;
+        a = t;
+        y = -v.y - ca;
+        t = a + y;
+        ca = (t - a) - y;
+        a = t;
+    }
+    out[idx] = (double)a - (double)ca;
+}
+
+// as k_apply_combine, from the split sums of k_split_sum2 (accumulator a of
+// face S at sums[a * nf + S])
 template <int OP, int KC>
-__global__ void k_apply_combine2(const float2* __restrict__ part, int nsplit, int nf,
-                                 const d4* __restrict__ f64a, const double* __restrict__ fgrad,
-                                 const double* __restrict__ W64, int k, int col0,
+__global__ void k_apply_combine2(const double* __restrict__ sums, int nf, const d4* __restrict__ f64a,
+                                 const double* __restrict__ fgrad, const double* __restrict__ W64, int k, int col0,
                                  double* __restrict__ corner) {
     using L = OpLayout<OP, KC>;
     const int S = blockIdx.x * blockDim.x + threadIdx.x;
     if (S >= nf) return;
     double s[L::NA];
-    for (int i = 0; i < L::NA; ++i) {
-        float a = 0.f, ca = 0.f;   // Kahan over the values s_k and -c_k
-#pragma unroll 4
-        for (int sp = 0; sp < nsplit; ++sp) {
-            const float2 v = part[((size_t)sp * L::NA + i) * nf + S];
-            float y = v.x - ca;
-            float t = a + y;
-            ca = (t - a) - y;
-            a = t;
-            y = -v.y - ca;
-            t = a + y;
-            ca = (t - a) - y;
-            a = t;
-        }
-        s[i] = (double)a - (double)ca;
-    }
+#pragma unroll
+    for (int i = 0; i < L::NA; ++i) s[i] = sums[(size_t)i * nf + S];
     double a = f64a[S].w;
     const double* W = W64 + 4 * KC * (size_t)S;
     double zV[3 * KC], zU[KC];
@@ -1525,7 +1531,7 @@ static int launch_apply_wide(tp_mesh* m, const tp_params* p, const double* v, in
     const int per_sm = resident_per_sm((const void*)k_apply_wide<OP, CHW>, NT, smem);
     if (per_sm < 1) return fail(TP_ERR_CUDA, "k_apply_wide: shared memory per block not available");
     Grid g = make_grid(nf, nf, WT, per_sm);
-    TP_TRY(ensure(m->part, sizeof(float2) * (size_t)g.nsplit * L::NA * nf));
+    TP_TRY(ensure(m->part, sizeof(float2) * (size_t)g.nsplit * L::NA * nf + sizeof(double) * L::NA * (size_t)nf));
     TP_TRY(ensure(m->wv64, sizeof(double) * 4 * 9 * (size_t)nf));
     TP_TRY(ensure(m->wv32, sizeof(float4) * L::NW4 * (size_t)nf));
     TP_TRY(ensure(m->corner, sizeof(double) * 3 * (size_t)nf * k));
@@ -1550,8 +1556,11 @@ static int launch_apply_wide(tp_mesh* m, const tp_params* p, const double* v, in
                                                           m->part.as<float2>());
         }
         TP_LAUNCH_CHECK();
-        k_apply_combine2<OP, 9><<<(nf + 127) / 128, 128, 0, st>>>(m->part.as<float2>(), g.nsplit, nf,
-                                                                  m->f64a.as<d4>(), m->fgrad.as<double>(),
+        double* sums = reinterpret_cast<double*>(m->part.as<float2>() + (size_t)g.nsplit * L::NA * nf);
+        k_split_sum2<<<(unsigned)(((size_t)L::NA * nf + 255) / 256), 256, 0, st>>>(m->part.as<float2>(), g.nsplit,
+                                                                                L::NA, nf, sums);
+        TP_LAUNCH_CHECK();
+        k_apply_combine2<OP, 9><<<(nf + 127) / 128, 128, 0, st>>>(sums, nf, m->f64a.as<d4>(), m->fgrad.as<double>(),
                                                                   m->wv64.as<double>(), k, col0,
                                                                   m->corner.as<double>());
         TP_LAUNCH_CHECK();

@@ -70,8 +70,10 @@ int precond_apply_dev(tp_mesh* m, const tp_params* p, const double* b, int k, do
     TP_TRY(ensure(m->prec[1], sizeof(double) * n));
     int it1 = 0, it2 = 0;
     // with pins the pin rows are appended to both Laplacians (§7.2)
+    // inside flexible GMRES (strict = false) the factorised solves run
+    // deferred: no host read per solve; the step reads their flags once
     auto solve = [&](const double* rhs, double* out, int* it) {
-        return m->npins ? pinned_solve(m, p, rhs, k, out, st, it) : cg_solve(m, p, rhs, k, out, st, it);
+        return m->npins ? pinned_solve(m, p, rhs, k, out, st, it) : cg_solve(m, p, rhs, k, out, st, it, !strict);
     };
     int s1 = solve(b, m->prec[0].as<double>(), &it1);
     if (s1 != TP_OK && (strict || s1 != TP_ERR_NOT_CONVERGED)) return s1;
@@ -245,17 +247,18 @@ static int fgmres_multi(tp_mesh* m, const tp_params* p, int ns, const double* co
                     dy.push_back(S[i].w);
                 }
             std::vector<double> h1(dx.size()), h2(dx.size() + cyc.size());
-            TP_TRY(dot_pairs(m, dx.data(), dy.data(), (int)dx.size(), n, h1.data(), st));
+            // pass 1 stays on the device (coefficients read by the kernel);
+            // its dots reach the host with pass 2's, one synchronisation
+            TP_TRY(ensure(m->gsdev, sizeof(double) * 1024));
+            double* h1dev = m->gsdev.as<double>();
+            TP_TRY(dot_pairs_dev(m, dx.data(), dy.data(), (int)dx.size(), n, h1dev, st));
             for (size_t ii = 0; ii < cyc.size(); ++ii) {
                 GmSys& q = S[cyc[ii]];
                 std::vector<const double*> basis(j + 1);
-                std::vector<double> neg(j + 1);
-                for (int l = 0; l <= j; ++l) {
-                    basis[l] = Vj(q, l);
-                    neg[l] = -h1[ii * (j + 1) + l];
-                }
-                TP_TRY(lincomb(q.w, basis.data(), neg.data(), j + 1, n, 1.0, st));
+                for (int l = 0; l <= j; ++l) basis[l] = Vj(q, l);
+                TP_TRY(lincomb_dev(q.w, basis.data(), h1dev + ii * (j + 1), -1.0, j + 1, n, 1.0, st));
             }
+            TP_CUDA(cudaMemcpyAsync(h1.data(), h1dev, sizeof(double) * h1.size(), cudaMemcpyDeviceToHost, st));
             for (int i : cyc) {
                 dx.push_back(S[i].w);
                 dy.push_back(S[i].w);
@@ -526,6 +529,10 @@ int precond_step_dev(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp
     unsigned long long bh0[BH_NCOUNT];
     TP_TRY(bh_counts_read(m, bh0, false, st));
     TP_CUDA(cudaMemcpyAsync(f0, m->pos.ptr, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+    {
+        int e0 = 0, u0 = 0;
+        TP_TRY(chol_deferred_flags(m, st, &e0, &u0, true));
+    }
 
     // 1. differential
     double E0 = 0.0;
@@ -657,6 +664,14 @@ int precond_step_dev(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp
     TP_TRY(energy_value(m, p, &r.E_after, st, true));
     r.krylov_iters = ks.iters;
     r.cg_iters = ks.cg_iters;
+    {
+        // the deferred Poisson solves of the Krylov loop: a wait that gave up
+        // is an error; solves that stopped short of cg_tol only made the
+        // (flexible) preconditioner less exact
+        int derr = 0, dunc = 0;
+        TP_TRY(chol_deferred_flags(m, st, &derr, &dunc, false));
+        if (derr) return fail(TP_ERR_TIMEOUT, "precond_step: a wait of the factorised sweep gave up");
+    }
     unsigned long long bh1[BH_NCOUNT];
     TP_TRY(bh_counts_read(m, bh1, false, st));
     r.pair_interactions = m->pairs - pairs0;

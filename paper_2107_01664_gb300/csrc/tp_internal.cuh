@@ -223,6 +223,7 @@ struct tp_mesh {
     tp::Buf part, part2, scal, corner, wv64, wv32, tmpv[8];
     tp::Buf io_in, io_out, adj, erow, tlist, rowsum;
     tp::Buf kry;        // FGMRES bases V and Z
+    tp::Buf gsdev;      // FGMRES: first-pass Gram-Schmidt coefficients on the device
     tp::Buf stepv[8];   // vectors of the constrained step
     tp::Buf prec[3];    // preconditioner temporaries
     tp::Buf bhcount;    // device counter of Barnes-Hut interactions
@@ -306,7 +307,7 @@ int bh_lists(tp_mesh* m, const tp_params* p, cudaStream_t st, BhLists* out, bool
 int laplacian_setup(tp_mesh* m);                        // CSR pattern (host, once)
 int laplacian_values(tp_mesh* m, cudaStream_t st);      // cotan values for current positions
 int cg_solve(tp_mesh* m, const tp_params* p, const double* b_dev, int k, double* z_dev,
-             cudaStream_t st, int* iters);
+             cudaStream_t st, int* iters, bool deferred = false);
 // y += G x (k columns), G the within-face term of the preconditioner's
 // L^{2-s} with weight p->prec_self_weight (nothing when the weight is 0)
 int self_term_add(tp_mesh* m, const tp_params* p, const double* x_dev, int k, double* y_dev,
@@ -315,7 +316,11 @@ int self_term_add(tp_mesh* m, const tp_params* p, const double* x_dev, int k, do
 // z = C^+ b through the sparse Cholesky factor; *used = false when the
 // factor cannot serve the mesh (panel too large) or refinement stalled
 int chol_solve(tp_mesh* m, const tp_params* p, const double* b_dev, int k, double* z_dev,
-               cudaStream_t st, int* iters, bool* used);
+               cudaStream_t st, int* iters, bool* used, bool deferred = false);
+// deferred solves (deferred = true: no host read per solve, the sweeps cg_tol
+// needs, flags accumulated on the device): read (unless reset) and clear the
+// accumulated wait error and unconverged-solve flags
+int chol_deferred_flags(tp_mesh* m, cudaStream_t st, int* err, int* unconverged, bool reset);
 int chol_info(tp_mesh* m, tp_chol_info* out);
 // waits in one kernel on a word nothing sets: TP_ERR_TIMEOUT and *timed_out = 1
 // once the bounded wait gives up (current device)
@@ -329,6 +334,12 @@ int dots(tp_mesh* m, const double* const* xs, const double* y, int nvec, size_t 
 int dot_pairs(tp_mesh* m, const double* const* xs, const double* const* ys, int nvec, size_t n,
               double* out_host, cudaStream_t st);   // out_host[j] = xs[j] . ys[j], nvec <= 512
 int axpy(double* y, const double* x, double a, size_t n, cudaStream_t st);
+// device-resident variants (no host synchronisation): dot products into
+// device memory, and a linear combination with coefficients read from it
+int dot_pairs_dev(tp_mesh* m, const double* const* xs, const double* const* ys, int nvec, size_t n,
+                  double* out_dev, cudaStream_t st);
+int lincomb_dev(double* y, const double* const* xs, const double* coef_dev, double scale, int nvec, size_t n,
+                double beta, cudaStream_t st);
 int lincomb(double* y, const double* const* xs, const double* coef_host, int nvec, size_t n,
             double beta, cudaStream_t st);
 
