@@ -613,7 +613,7 @@ __global__ void __launch_bounds__(128)
 k_bh_list(const BvhNode* __restrict__ node, const int* __restrict__ right, const FaceBox* __restrict__ fbox,
           int nf, float theta2, int cap, long long* __restrict__ cnt, const long long* __restrict__ far_off,
           const long long* __restrict__ near_off, int2* __restrict__ far_out, int2* __restrict__ near_out,
-          int* __restrict__ err) {
+          int* __restrict__ err, unsigned long long* __restrict__ inter) {
     extern __shared__ int2 lstack[];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int ngroups = (nf + BHL_GROUP - 1) / BHL_GROUP;
@@ -637,6 +637,15 @@ k_bh_list(const BvhNode* __restrict__ node, const int* __restrict__ right, const
     // must reproduce the first pass's counts; a mismatch is reported)
     const long long flim = WRITE ? far_off[g + 1] : 0, nlim = WRITE ? near_off[g + 1] : 0;
     bool over = false;
+    // interactions the lists give (WRITE pass): popc(mask) per far entry,
+    // and per near leaf popc(mask) x its faces minus the self pairs
+    unsigned long long ninter = 0;
+    const int g0 = g * BHL_GROUP;
+    auto near_terms = [&](const BvhNode& nd, unsigned msk) -> unsigned long long {
+        const int lo = max(nd.first, g0) - g0, hi = min(nd.first + nd.count, g0 + BHL_GROUP) - g0;
+        const unsigned self = hi > lo ? (((hi - lo) >= 32 ? 0xffffffffu : ((1u << (hi - lo)) - 1u)) << lo) : 0u;
+        return (unsigned long long)__popc(msk) * (unsigned)nd.count - (unsigned)__popc(msk & self);
+    };
     while (sp > 0 && !over) {
         const int n = min(32, sp);
         const bool act = lane < n;
@@ -664,6 +673,10 @@ k_bh_list(const BvhNode* __restrict__ node, const int* __restrict__ right, const
         const unsigned bn = __ballot_sync(0xffffffffu, cnot && leaf);
         if (WRITE && cnot && leaf && no + nnear + __popc(bn & lt) < nlim) near_out[no + nnear + __popc(bn & lt)] = e;
         nnear += __popc(bn);
+        if (WRITE) {
+            if (cadm) ninter += (unsigned)__popc((unsigned)e.y);
+            if (cnot && leaf) ninter += near_terms(nd, (unsigned)e.y);
+        }
         const unsigned bd = __ballot_sync(0xffffffffu, cnot && !leaf);
         if (sp + 2 * __popc(bd) > cap) {
             over = true;
@@ -692,11 +705,13 @@ k_bh_list(const BvhNode* __restrict__ node, const int* __restrict__ right, const
             const unsigned rest = msk & ~am;
             if (am) {
                 if (WRITE && lane == 0 && fo + nfar < flim) far_out[fo + nfar] = make_int2(nid, (int)am);
+                if (WRITE && lane == 0) ninter += (unsigned)__popc(am);
                 ++nfar;
             }
             if (rest) {
                 if (n2.leaf) {
                     if (WRITE && lane == 0 && no + nnear < nlim) near_out[no + nnear] = make_int2(nid, (int)rest);
+                    if (WRITE && lane == 0) ninter += near_terms(n2, rest);
                     ++nnear;
                 } else if (sp + 2 > cap) {
                     over = true;
@@ -711,8 +726,12 @@ k_bh_list(const BvhNode* __restrict__ node, const int* __restrict__ right, const
         }
         __syncwarp();
     }
+    if (WRITE) {
+        for (int o = 16; o > 0; o >>= 1) ninter += __shfl_xor_sync(0xffffffffu, ninter, o);
+    }
     if (lane == 0) {
         if (over) atomicExch(err, 1);
+        if (WRITE && ninter) atomicAdd(inter, ninter);
         if (!WRITE) {
             cnt[g] = nfar;
             cnt[ngroups + 1 + g] = nnear;
@@ -734,6 +753,7 @@ int bh_lists(tp_mesh* m, const tp_params* p, cudaStream_t st, BhLists* out, bool
         out->near_off = off + ngroups + 1;
         out->far = m->bhl_far.as<int2>();
         out->near = m->bhl_near.as<int2>();
+        out->interactions = m->bhl_inter;
     };
     if (m->bhl_version == m->bvh_version && m->bhl_theta == p->theta) {
         if (m->bhl_failed) return TP_OK;
@@ -772,8 +792,9 @@ int bh_lists(tp_mesh* m, const tp_params* p, cudaStream_t st, BhLists* out, bool
     TP_CUDA(cudaMemsetAsync(off, 0, sizeof(long long) * head, st));
     const float theta2 = (float)(p->theta * p->theta);
     const int blocks = (ngroups + warps - 1) / warps;
+    unsigned long long* inter = reinterpret_cast<unsigned long long*>(err + 2);
     k_bh_list<false><<<blocks, 32 * warps, smem, st>>>(na.node, right, fbox, nf, theta2, cap, counts, nullptr,
-                                                       nullptr, nullptr, nullptr, err);
+                                                       nullptr, nullptr, nullptr, err, inter);
     TP_LAUNCH_CHECK();
     // counts -> exclusive offsets (the extra last entry becomes the total)
     TP_CUDA(cub::DeviceScan::ExclusiveSum(scan_ws, scan_bytes, counts, off, ngroups + 1, st));
@@ -795,13 +816,16 @@ int bh_lists(tp_mesh* m, const tp_params* p, cudaStream_t st, BhLists* out, bool
     }
     k_bh_list<true><<<blocks, 32 * warps, smem, st>>>(na.node, right, fbox, nf, theta2, cap, nullptr, off,
                                                       off + ngroups + 1, m->bhl_far.as<int2>(),
-                                                      m->bhl_near.as<int2>(), err);
+                                                      m->bhl_near.as<int2>(), err, inter);
     TP_LAUNCH_CHECK();
+    unsigned long long ninter = 0;
     TP_CUDA(cudaMemcpyAsync(&e1, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TP_CUDA(cudaMemcpyAsync(&ninter, inter, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
     TP_CUDA(cudaStreamSynchronize(st));
     if (e1 != 0) return TP_OK;
     m->bhl_nfar = tot[0];
     m->bhl_nnear = tot[1];
+    m->bhl_inter = ninter;
     m->bhl_failed = false;
     fill();
     *ok = true;
@@ -862,7 +886,6 @@ k_bh_energy_list(const float4* __restrict__ node4, const float4* __restrict__ no
     const unsigned me = 1u << lane;
     KahanF sum;
     float acc = 0.f;
-    int nint = 0;
     const int f0 = (int)L.far_off[g], f1 = (int)L.far_off[g + 1];
     int run = 0;
 #pragma unroll 4
@@ -871,14 +894,13 @@ k_bh_energy_list(const float4* __restrict__ node4, const float4* __restrict__ no
         const float4 c = node4[4 * en.x];          // barycenter (hi), area
         const float4 nl = nodelo[en.x];
         const float dx = (A.x - c.x) + (Al.x - nl.x), dy = (A.y - c.y) + (Al.y - nl.y), dz = (A.z - c.z) + (Al.z - nl.z);
-        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, 1e-18f)));
         const float u = B.x * dx + B.y * dy + B.z * dz;
-        const float ir2 = frcp(fmaxf(r2, 1e-18f));
+        const float ir2 = frcp(r2);
         const float q = u * u * (ir2 * ir2);
         const float K = P6 ? q * q * q : fpow(q, halfp);
         const bool on = (unsigned)en.y & me;
         acc = fmaf(on ? K : 0.f, c.w, acc);
-        nint += on;
         if (++run == 32) {
             sum.add(acc);
             acc = 0.f;
@@ -895,20 +917,19 @@ k_bh_energy_list(const float4* __restrict__ node4, const float4* __restrict__ no
         for (int j = fc.x; j < fc.x + fc.y; ++j) {
             const float4 s = sa[j], l = sl[j];
             const float dx = (A.x - s.x) + (Al.x - l.x), dy = (A.y - s.y) + (Al.y - l.y), dz = (A.z - s.z) + (Al.z - l.z);
-            const float r2 = dx * dx + dy * dy + dz * dz;
+            const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, 1e-18f)));
             const float u = B.x * dx + B.y * dy + B.z * dz;
-            const float ir2 = frcp(fmaxf(r2, 1e-18f));
+            const float ir2 = frcp(r2);
             const float q = u * u * (ir2 * ir2);
             const float K = P6 ? q * q * q : fpow(q, halfp);
             const bool t = on && j != i;
             acc = fmaf(t ? K : 0.f, s.w, acc);
-            nint += t;
         }
         sum.add(acc);
         acc = 0.f;
     }
     if (has) rows[perm[i]] = f64a[perm[i]].w * sum.value();
-    if (count && nint) atomicAdd(count, (unsigned long long)nint);
+    if (count && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(count, L.interactions);
 }
 
 // packed FP32 pair arithmetic (two IEEE lanes per instruction)
@@ -925,13 +946,13 @@ __device__ __forceinline__ float2 bu2(unsigned long long r) {
 
 // p = 6 term of one target against two sources (lanes), with compensated
 // differences: K a per lane, d = (t - s) + (tl - sl), K = ((N.d)^2/|d|^4)^3,
-// |d|^2 floored at 1e-18 (the self pair gives 0)
+// |d|^2 + eps in the FMA chain (eps = 1e-18: the self pair gives 0)
 __device__ __forceinline__ unsigned long long bh_energy2_p6(
     unsigned long long tx, unsigned long long ty, unsigned long long tz, unsigned long long ux,
     unsigned long long uy, unsigned long long uz, unsigned long long nx, unsigned long long ny,
     unsigned long long nz, unsigned long long sx, unsigned long long sy, unsigned long long sz,
     unsigned long long lx, unsigned long long ly, unsigned long long lz, unsigned long long sa,
-    unsigned long long acc) {
+    unsigned long long acc, unsigned long long eps) {
     unsigned long long out;
     asm("{\n\t.reg .b64 dx, dy, dz, ex, ey, ez, r2, u, ir2, q;\n\t.reg .f32 lo, hi;\n\t"
         "sub.rn.f32x2 dx, %1, %10;\n\t"
@@ -943,15 +964,13 @@ __device__ __forceinline__ unsigned long long bh_energy2_p6(
         "add.rn.f32x2 dx, dx, ex;\n\t"
         "add.rn.f32x2 dy, dy, ey;\n\t"
         "add.rn.f32x2 dz, dz, ez;\n\t"
-        "mul.rn.f32x2 r2, dx, dx;\n\t"
+        "fma.rn.f32x2 r2, dz, dz, %18;\n\t"
         "fma.rn.f32x2 r2, dy, dy, r2;\n\t"
-        "fma.rn.f32x2 r2, dz, dz, r2;\n\t"
+        "fma.rn.f32x2 r2, dx, dx, r2;\n\t"
         "mul.rn.f32x2 u, %7, dx;\n\t"
         "fma.rn.f32x2 u, %8, dy, u;\n\t"
         "fma.rn.f32x2 u, %9, dz, u;\n\t"
         "mov.b64 {lo, hi}, r2;\n\t"
-        "max.f32 lo, lo, 0f219392EF;\n\t"
-        "max.f32 hi, hi, 0f219392EF;\n\t"
         "rcp.approx.ftz.f32 lo, lo;\n\t"
         "rcp.approx.ftz.f32 hi, hi;\n\t"
         "mov.b64 ir2, {lo, hi};\n\t"
@@ -962,7 +981,7 @@ __device__ __forceinline__ unsigned long long bh_energy2_p6(
         "fma.rn.f32x2 %0, q, %16, %17;\n\t}"
         : "=l"(out)
         : "l"(tx), "l"(ty), "l"(tz), "l"(ux), "l"(uy), "l"(uz), "l"(nx), "l"(ny), "l"(nz), "l"(sx), "l"(sy),
-          "l"(sz), "l"(lx), "l"(ly), "l"(lz), "l"(sa), "l"(acc));
+          "l"(sz), "l"(lx), "l"(ly), "l"(lz), "l"(sa), "l"(acc), "l"(eps));
     return out;
 }
 
@@ -984,8 +1003,8 @@ k_bh_energy_list2(const float4* __restrict__ node4, const float4* __restrict__ n
     const unsigned long long UX = bp2(Al.x, Al.x), UY = bp2(Al.y, Al.y), UZ = bp2(Al.z, Al.z);
     const unsigned long long NX = bp2(B.x, B.x), NY = bp2(B.y, B.y), NZ = bp2(B.z, B.z);
     const unsigned me = 1u << lane;
+    const unsigned long long EPS = bp2(1e-18f, 1e-18f);
     KahanF sum;
-    int nint = 0;
     const int f0 = (int)L.far_off[g], f1 = (int)L.far_off[g + 1];
     unsigned long long acc = 0ull;
     int run = 0;
@@ -999,8 +1018,7 @@ k_bh_energy_list2(const float4* __restrict__ node4, const float4* __restrict__ n
         const bool on0 = (unsigned)en0.y & me, on1 = (unsigned)en1.y & me;
         acc = bh_energy2_p6(TX, TY, TZ, UX, UY, UZ, NX, NY, NZ, bp2(c0.x, c1.x), bp2(c0.y, c1.y), bp2(c0.z, c1.z),
                             bp2(l0.x, l1.x), bp2(l0.y, l1.y), bp2(l0.z, l1.z),
-                            bp2(on0 ? c0.w : 0.f, on1 ? c1.w : 0.f), acc);
-        nint += (int)on0 + (int)on1;
+                            bp2(on0 ? c0.w : 0.f, on1 ? c1.w : 0.f), acc, EPS);
         if (++run == 16) {
             const float2 a = bu2(acc);
             sum.add(a.x + a.y);
@@ -1026,15 +1044,14 @@ k_bh_energy_list2(const float4* __restrict__ node4, const float4* __restrict__ n
             const bool t0 = on && j != i, t1 = on && two && j + 1 != i;
             acc = bh_energy2_p6(TX, TY, TZ, UX, UY, UZ, NX, NY, NZ, bp2(s0.x, s1.x), bp2(s0.y, s1.y),
                                 bp2(s0.z, s1.z), bp2(q0.x, q1.x), bp2(q0.y, q1.y), bp2(q0.z, q1.z),
-                                bp2(t0 ? s0.w : 0.f, t1 ? s1.w : 0.f), acc);
-            nint += (int)t0 + (int)t1;
+                                bp2(t0 ? s0.w : 0.f, t1 ? s1.w : 0.f), acc, EPS);
         }
         const float2 a = bu2(acc);
         sum.add(a.x + a.y);
         acc = 0ull;
     }
     if (has) rows[perm[i]] = f64a[perm[i]].w * sum.value();
-    if (count && nint) atomicAdd(count, (unsigned long long)nint);
+    if (count && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(count, L.interactions);
 }
 
 int energy_rows_bh(tp_mesh* m, const tp_params* p, const int32_t* tl, int nt, double* rows, cudaStream_t st) {
@@ -1300,7 +1317,6 @@ k_bh_diff_list(const float4* __restrict__ node4, const float4* __restrict__ node
     float pt[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) pt[k] = 0.f;
-    int nint = 0;
     auto flush = [&]() {
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
@@ -1313,9 +1329,9 @@ k_bh_diff_list(const float4* __restrict__ node4, const float4* __restrict__ node
     auto interact = [&](float4 src, float4 lo, float w, bool on, float* G, float& Q) {
         const float dx = (A.x - src.x) + (Al.x - lo.x), dy = (A.y - src.y) + (Al.y - lo.y),
                     dz = (A.z - src.z) + (Al.z - lo.z);
-        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, 1e-18f)));
         const float u = B.x * dx + B.y * dy + B.z * dz;
-        const float ir2 = frcp(fmaxf(r2, 1e-18f));
+        const float ir2 = frcp(r2);
         const float ir4 = ir2 * ir2;
         const float q = u * u * ir4;
         const float mq = P6 ? q * q : fpow(q, hm1);
@@ -1336,7 +1352,6 @@ k_bh_diff_list(const float4* __restrict__ node4, const float4* __restrict__ node
         G[1] = s1 * B.y + s2 * dy;
         G[2] = s1 * B.z + s2 * dz;
         Q = on ? aS * K : 0.f;   // a_S K (the source's area derivative carries no a_T)
-        nint += on;
     };
     const int f0 = (int)L.far_off[g], f1 = (int)L.far_off[g + 1];
     int run = 0;
@@ -1373,7 +1388,184 @@ k_bh_diff_list(const float4* __restrict__ node4, const float4* __restrict__ node
     }
     if (has)
         for (int k = 0; k < 8; ++k) tacc[(size_t)i0 * 8 + k] = acc[k].value();
-    if (nint) atomicAdd(count, (unsigned long long)nint);
+    if (count && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(count, L.interactions);
+}
+
+// packed float2 arithmetic (two IEEE lanes per instruction)
+__device__ __forceinline__ float2 q2add(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 q2sub(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 q2mul(float2 a, float2 b) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 q2fma(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 q2(float a) { return make_float2(a, a); }
+
+// sums of eight values over the warp: lane l ends with the sum of value
+// l >> 2 (9 shuffles instead of 8 x 5)
+__device__ __forceinline__ float warp_sum8(const float (&v)[8]) {
+    const int lane = threadIdx.x & 31;
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float k[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float keep = b4 ? v[4 + i] : v[i], send = b4 ? v[i] : v[4 + i];
+        k[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float m[2];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float keep = b3 ? k[2 + i] : k[i], send = b3 ? k[i] : k[2 + i];
+        m[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float r;
+    {
+        const float keep = b2 ? m[1] : m[0], send = b2 ? m[0] : m[1];
+        r = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    r += __shfl_xor_sync(0xffffffffu, r, 2);
+    r += __shfl_xor_sync(0xffffffffu, r, 1);
+    return r;
+}
+
+// k_bh_diff_list for p = 6 with two list entries (or two leaf faces) per
+// packed instruction: the target side as in k_bh_diff_list, the source sides
+// of both entries summed over the warp together (warp_sum8) and added with
+// one FP64 atomic per entry and component
+template <bool FULL>
+__global__ void __launch_bounds__(128)
+k_bh_diff_list2(const float4* __restrict__ node4, const float4* __restrict__ nodelo, const float4* __restrict__ sa,
+                const float4* __restrict__ sb, const float4* __restrict__ sl, int nf, BhLists L, float p,
+                double* __restrict__ tacc, double* __restrict__ nacc, double* __restrict__ facc,
+                unsigned long long* __restrict__ count) {
+    const int lane = threadIdx.x & 31;
+    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (g >= L.ngroups) return;
+    const int i0 = g * BHL_GROUP + lane;
+    const bool has = i0 < nf;
+    const int i = has ? i0 : 0;
+    const float4 A = sa[i], B = sb[i], Al = sl[i];
+    const float aS = A.w;
+    const float2 TX = q2(A.x), TY = q2(A.y), TZ = q2(A.z), UX = q2(Al.x), UY = q2(Al.y), UZ = q2(Al.z);
+    const float2 NX = q2(B.x), NY = q2(B.y), NZ = q2(B.z), EPS2 = q2(1e-18f);
+    const float2 S1 = q2(-aS * p), S2 = q2(2.f * aS * p), AS = q2(aS);
+    const unsigned me = 1u << lane;
+    KahanF acc[8];
+    float2 pt[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) pt[k] = make_float2(0.f, 0.f);
+    auto flush = [&]() {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            acc[k].add(pt[k].x + pt[k].y);
+            pt[k] = make_float2(0.f, 0.f);
+        }
+    };
+    // two interactions (lanes x, y of the float2 arguments): sources at
+    // (SX, SY, SZ) + low parts, weights W (zero where masked), on-flags for Q
+    auto interact2 = [&](float2 SX, float2 SY, float2 SZ, float2 LX, float2 LY, float2 LZ, float2 W, float2 ON,
+                         float (&v)[8]) {
+        const float2 dx = q2add(q2sub(TX, SX), q2sub(UX, LX));
+        const float2 dy = q2add(q2sub(TY, SY), q2sub(UY, LY));
+        const float2 dz = q2add(q2sub(TZ, SZ), q2sub(UZ, LZ));
+        const float2 r2 = q2fma(dx, dx, q2fma(dy, dy, q2fma(dz, dz, EPS2)));
+        const float2 u = q2fma(NX, dx, q2fma(NY, dy, q2mul(NZ, dz)));
+        const float2 ir2 = make_float2(frcp(r2.x), frcp(r2.y));
+        const float2 ir4 = q2mul(ir2, ir2);
+        const float2 q = q2mul(q2mul(u, u), ir4);
+        const float2 mq = q2mul(q, q);
+        const float2 K = q2mul(mq, q);
+        const float2 c = q2mul(q2mul(mq, u), ir4);
+        const float2 wc = q2mul(W, c), wK = q2mul(W, K), wKd = q2mul(wK, ir2);
+        pt[0] = q2add(pt[0], wc);
+        pt[1] = q2fma(wc, dx, pt[1]);
+        pt[2] = q2fma(wc, dy, pt[2]);
+        pt[3] = q2fma(wc, dz, pt[3]);
+        pt[4] = q2fma(wKd, dx, pt[4]);
+        pt[5] = q2fma(wKd, dy, pt[5]);
+        pt[6] = q2fma(wKd, dz, pt[6]);
+        pt[7] = q2add(pt[7], wK);
+        if (FULL) {
+            const float2 s1 = q2mul(S1, wc), s2 = q2mul(S2, wKd);
+            const float2 G0 = q2fma(s2, dx, q2mul(s1, NX)), G1 = q2fma(s2, dy, q2mul(s1, NY)),
+                         G2 = q2fma(s2, dz, q2mul(s1, NZ));
+            const float2 Q = q2mul(q2mul(AS, K), ON);
+            v[0] = G0.x; v[1] = G1.x; v[2] = G2.x; v[3] = Q.x;
+            v[4] = G0.y; v[5] = G1.y; v[6] = G2.y; v[7] = Q.y;
+        }
+    };
+    const int f0 = (int)L.far_off[g], f1 = (int)L.far_off[g + 1];
+    int run = 0;
+    for (int e = f0; e < f1; e += 2) {
+        const int2 en0 = L.far[e];
+        const bool two = e + 1 < f1;
+        const int2 en1 = two ? L.far[e + 1] : make_int2(en0.x, 0);
+        const float4 c0 = node4[4 * en0.x], c1 = node4[4 * en1.x];
+        const float4 l0 = nodelo[en0.x], l1 = nodelo[en1.x];
+        const bool on0 = (unsigned)en0.y & me, on1 = (unsigned)en1.y & me;
+        float v[8];
+        interact2(make_float2(c0.x, c1.x), make_float2(c0.y, c1.y), make_float2(c0.z, c1.z),
+                  make_float2(l0.x, l1.x), make_float2(l0.y, l1.y), make_float2(l0.z, l1.z),
+                  make_float2(on0 ? c0.w : 0.f, on1 ? c1.w : 0.f), make_float2(on0 ? 1.f : 0.f, on1 ? 1.f : 0.f), v);
+        if (FULL) {
+            const float r = warp_sum8(v);
+            const int vi = lane >> 2;             // value: entry vi >> 2, component vi & 3
+            if ((lane & 3) == 0 && (vi < 4 || two))
+                atomicAdd(nacc + 4 * (vi < 4 ? en0.x : en1.x) + (vi & 3), f2d_int(r));
+        }
+        if (++run == 16) {
+            flush();
+            run = 0;
+        }
+    }
+    flush();
+    const int n0 = (int)L.near_off[g], n1 = (int)L.near_off[g + 1];
+    for (int e = n0; e < n1; ++e) {
+        const int2 en = L.near[e];
+        const int4 fc = reinterpret_cast<const int4*>(node4)[4 * en.x + 3];
+        const bool on = (unsigned)en.y & me;
+        const int j1 = fc.x + fc.y;
+        for (int j = fc.x; j < j1; j += 2) {
+            const bool two = j + 1 < j1;
+            const int jb = two ? j + 1 : j;
+            const float4 s0 = sa[j], s1 = sa[jb], q0 = sl[j], q1 = sl[jb];
+            const bool t0 = on && j != i0, t1 = on && two && jb != i0;
+            float v[8];
+            interact2(make_float2(s0.x, s1.x), make_float2(s0.y, s1.y), make_float2(s0.z, s1.z),
+                      make_float2(q0.x, q1.x), make_float2(q0.y, q1.y), make_float2(q0.z, q1.z),
+                      make_float2(t0 ? s0.w : 0.f, t1 ? s1.w : 0.f), make_float2(t0 ? 1.f : 0.f, t1 ? 1.f : 0.f), v);
+            if (FULL) {
+                const float r = warp_sum8(v);
+                const int vi = lane >> 2;
+                if ((lane & 3) == 0 && (vi < 4 || two)) atomicAdd(facc + 4 * (vi < 4 ? j : jb) + (vi & 3), f2d_int(r));
+            }
+        }
+        flush();
+    }
+    if (has)
+        for (int k = 0; k < 8; ++k) tacc[(size_t)i0 * 8 + k] = acc[k].value();
+    if (count && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(count, L.interactions);
 }
 
 // per node: g1 = G/a_I, q = Q - G.X_I/a_I (FP64 node data)
@@ -1467,8 +1659,8 @@ int diff_adjoints_bh(tp_mesh* m, const tp_params* p, double* adj, double* erow, 
         const float4* n4 = reinterpret_cast<const float4*>(node);
         const int blocks = (L.ngroups + 3) / 4;
         if (p->p == 6.0) {
-            if (full) k_bh_diff_list<true, true><<<blocks, 128, 0, st>>>(n4, nodelo, sa, sb, sl, nf, L, hm1, pf, tacc, nacc, facc, cnt);
-            else k_bh_diff_list<true, false><<<blocks, 128, 0, st>>>(n4, nodelo, sa, sb, sl, nf, L, hm1, pf, tacc, nacc, facc, cnt);
+            if (full) k_bh_diff_list2<true><<<blocks, 128, 0, st>>>(n4, nodelo, sa, sb, sl, nf, L, pf, tacc, nacc, facc, cnt);
+            else k_bh_diff_list2<false><<<blocks, 128, 0, st>>>(n4, nodelo, sa, sb, sl, nf, L, pf, tacc, nacc, facc, cnt);
         } else {
             if (full) k_bh_diff_list<false, true><<<blocks, 128, 0, st>>>(n4, nodelo, sa, sb, sl, nf, L, hm1, pf, tacc, nacc, facc, cnt);
             else k_bh_diff_list<false, false><<<blocks, 128, 0, st>>>(n4, nodelo, sa, sb, sl, nf, L, hm1, pf, tacc, nacc, facc, cnt);

@@ -1814,7 +1814,6 @@ k_bh_apply_list(const float4* __restrict__ node4, const float4* __restrict__ nod
     Acc2<float> acc[NP];
 #pragma unroll
     for (int c = 0; c < NP; ++c) pt[c] = make_float2(0.f, 0.f);
-    unsigned nint = 0;
     const int f0 = (int)Ls.far_off[g], f1 = (int)Ls.far_off[g + 1];
     int run = 0;
 #pragma unroll 2
@@ -1854,7 +1853,6 @@ k_bh_apply_list(const float4* __restrict__ node4, const float4* __restrict__ nod
                 for (int k = L::NH / 2; k < NP; ++k) pt[k] = pfma(h0, x2[k], pt[k]);
             }
         }
-        nint += on;
         if (++run == 32) {
 #pragma unroll
             for (int k = 0; k < NP; ++k) {
@@ -1888,7 +1886,6 @@ k_bh_apply_list(const float4* __restrict__ node4, const float4* __restrict__ nod
             const float dx = t ? (A.x - s.x) + (Al.x - l.x) : 1.f, dy = (A.y - s.y) + (Al.y - l.y),
                         dz = (A.z - s.z) + (Al.z - l.z);
             apply_term<float, OP, false, KC>(dx, dy, dz, B.x, B.y, B.z, mm.x, mm.y, mm.z, x2, s_exp, l_exp, pt);
-            nint += t;
         }
 #pragma unroll
         for (int k = 0; k < NP; ++k) {
@@ -1899,7 +1896,7 @@ k_bh_apply_list(const float4* __restrict__ node4, const float4* __restrict__ nod
     if (has)   // sorted order: consecutive lanes write consecutive words
 #pragma unroll
         for (int c = 0; c < L::NA; ++c) part[(size_t)c * nf + i] = acc[c / 2].value(c & 1);
-    if (count && nint) atomicAdd(count, (unsigned long long)nint);
+    if (count && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(count, Ls.interactions);
 }
 
 template <int OP, int KC>

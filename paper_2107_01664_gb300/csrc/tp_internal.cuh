@@ -110,6 +110,7 @@ struct BhLists {
     const long long* near_off = nullptr;   // [ngroups + 1]
     const int2* far = nullptr;
     const int2* near = nullptr;
+    unsigned long long interactions = 0;   // (target, node) plus (target, face) terms of one evaluation
 };
 
 // read-only view of a built tree for kernels outside bvh.cu
@@ -217,6 +218,7 @@ struct tp_mesh {
     unsigned long long bhl_version = 0;   // tree version the lists were built for (0: none)
     double bhl_theta = -1.0;
     long long bhl_nfar = 0, bhl_nnear = 0;
+    unsigned long long bhl_inter = 0;     // interactions of one evaluation over the lists
     bool bhl_failed = false;              // the lists could not be built for this tree (walk kernels serve)
     tp::Buf bhl_cnt, bhl_far, bhl_near;
     // workspaces
