@@ -587,8 +587,9 @@ k_bh_energy(const BvhNode* __restrict__ node, const float4* __restrict__ nodelo,
 // test of the walk kernels, lane by lane. A candidate carries the mask of the
 // group's targets for which none of its ancestors was admissible; the 32
 // lanes test 32 candidates at once, from a stack in shared memory. The output
-// per group: far entries (node, mask) and near entries (inadmissible leaf,
-// mask). The lists depend only on the tree and theta: they are built once per
+// per group: far entries (node, mask) and near entries (first face of an
+// inadmissible leaf, mask; the leaf holds min(leaf size, nf - first) faces).
+// The lists depend only on the tree and theta: they are built once per
 // tree and serve the energy, the differential and every operator apply of
 // the tree, whose evaluation kernels then stream the lists without a walk.
 
@@ -671,7 +672,8 @@ k_bh_list(const BvhNode* __restrict__ node, const int* __restrict__ right, const
         if (WRITE && cadm && fo + nfar + __popc(bf & lt) < flim) far_out[fo + nfar + __popc(bf & lt)] = e;
         nfar += __popc(bf);
         const unsigned bn = __ballot_sync(0xffffffffu, cnot && leaf);
-        if (WRITE && cnot && leaf && no + nnear + __popc(bn & lt) < nlim) near_out[no + nnear + __popc(bn & lt)] = e;
+        if (WRITE && cnot && leaf && no + nnear + __popc(bn & lt) < nlim)
+            near_out[no + nnear + __popc(bn & lt)] = make_int2(nd.first, e.y);
         nnear += __popc(bn);
         if (WRITE) {
             if (cadm) ninter += (unsigned)__popc((unsigned)e.y);
@@ -710,7 +712,7 @@ k_bh_list(const BvhNode* __restrict__ node, const int* __restrict__ right, const
             }
             if (rest) {
                 if (n2.leaf) {
-                    if (WRITE && lane == 0 && no + nnear < nlim) near_out[no + nnear] = make_int2(nid, (int)rest);
+                    if (WRITE && lane == 0 && no + nnear < nlim) near_out[no + nnear] = make_int2(n2.first, (int)rest);
                     if (WRITE && lane == 0) ninter += near_terms(n2, rest);
                     ++nnear;
                 } else if (sp + 2 > cap) {
@@ -754,6 +756,7 @@ int bh_lists(tp_mesh* m, const tp_params* p, cudaStream_t st, BhLists* out, bool
         out->far = m->bhl_far.as<int2>();
         out->near = m->bhl_near.as<int2>();
         out->interactions = m->bhl_inter;
+        out->leaf = m->bvh_shape_leaf;
     };
     if (m->bhl_version == m->bvh_version && m->bhl_theta == p->theta) {
         if (m->bhl_failed) return TP_OK;
@@ -912,7 +915,7 @@ k_bh_energy_list(const float4* __restrict__ node4, const float4* __restrict__ no
     const int n0 = (int)L.near_off[g], n1 = (int)L.near_off[g + 1];
     for (int e = n0; e < n1; ++e) {
         const int2 en = L.near[e];
-        const int4 fc = reinterpret_cast<const int4*>(node4)[4 * en.x + 3];   // first, count, skip, leaf
+        const int2 fc = make_int2(en.x, min(L.leaf, nf - en.x));   // the leaf's first face, count
         const bool on = (unsigned)en.y & me;
         for (int j = fc.x; j < fc.x + fc.y; ++j) {
             const float4 s = sa[j], l = sl[j];
@@ -944,17 +947,117 @@ __device__ __forceinline__ float2 bu2(unsigned long long r) {
     return v;
 }
 
-// p = 6 term of one target against two sources (lanes), with compensated
-// differences: K a per lane, d = (t - s) + (tl - sl), K = ((N.d)^2/|d|^4)^3,
-// |d|^2 + eps in the FMA chain (eps = 1e-18: the self pair gives 0)
+// ---------------------------------------------------------------------------
+// Staged list evaluation (p = 6). A warp streams its group's entries in
+// batches of 32 sources: 32 far entries, or the faces of 32 / leaf near
+// leaves. Lane k loads the record of source k of the NEXT batch while the
+// warp evaluates the current one, so the dependent loads (list entry ->
+// record) of 32 sources are in flight together instead of one entry at a
+// time. A batch sits in shared memory in source pairs, in the order the
+// packed FP32 arithmetic takes them (sources 2q and 2q + 1):
+//     H[2q] = {x0, x1, y0, y1}     H[2q+1] = {z0, z1, a0, a1}
+//     D[2q] = {lx0, lx1, ly0, ly1} D[2q+1] = {lz0, lz1, mask0, mask1}
+// (barycenter hi part and area, low parts, the entry's lane mask). Slots past
+// the end of the list hold a source parked far away with zero area and mask.
+// ---------------------------------------------------------------------------
+
+struct BhSrc {
+    float4 c;        // barycenter (hi), area
+    float4 l;        // low parts of the barycenter
+    unsigned mask;   // lanes of the group that take this source
+    int idx;         // node (far) or face (near)
+};
+
+__device__ __forceinline__ BhSrc bh_parked() {
+    BhSrc s;
+    s.c = make_float4(1e15f, 1e15f, 1e15f, 0.f);
+    s.l = make_float4(0.f, 0.f, 0.f, 0.f);
+    s.mask = 0u;
+    s.idx = -1;
+    return s;
+}
+
+// a group's batch sequence: far batches first, then near batches
+struct BhBatches {
+    int f0, f1, n0, n1;   // entry ranges
+    int nbf, nb;          // far batches, all batches
+    int lb, kl, fi;       // near leaves per batch; this lane's leaf slot and face in it
+    __device__ BhBatches(const BhLists& L, int g, int lane) {
+        f0 = (int)L.far_off[g];
+        f1 = (int)L.far_off[g + 1];
+        n0 = (int)L.near_off[g];
+        n1 = (int)L.near_off[g + 1];
+        lb = 32 / L.leaf;
+        kl = lane / L.leaf;
+        fi = lane - kl * L.leaf;
+        nbf = (f1 - f0 + 31) >> 5;
+        nb = nbf + (n1 - n0 + lb - 1) / lb;
+    }
+    // this lane's list entry in batch b (x < 0: none)
+    __device__ __forceinline__ int2 entry(const BhLists& L, int b, int lane) const {
+        if (b < nbf) {
+            const int e = f0 + 32 * b + lane;
+            return e < f1 ? L.far[e] : make_int2(-1, 0);
+        }
+        const int e = n0 + lb * (b - nbf) + kl;
+        return (kl < lb && e < n1) ? L.near[e] : make_int2(-1, 0);
+    }
+    // sources in batch b (slots 0 .. count - 1 may be taken)
+    __device__ __forceinline__ int count(int b, int leaf) const {
+        if (b < nbf) return min(32, f1 - f0 - 32 * b);
+        return min(lb, n1 - n0 - lb * (b - nbf)) * leaf;
+    }
+};
+
+// the record of this lane's source in batch b: far node (barycenter, area,
+// low part) or near face (the same per face)
+__device__ __forceinline__ BhSrc bh_record(const BhBatches& B, int b, int2 en, int leaf, int nf,
+                                           const float4* __restrict__ node4, const float4* __restrict__ nodelo,
+                                           const float4* __restrict__ sa, const float4* __restrict__ sl) {
+    BhSrc s = bh_parked();
+    if (en.x >= 0) {
+        if (b < B.nbf) {
+            s.c = node4[4 * en.x];
+            s.l = nodelo[en.x];
+            s.mask = (unsigned)en.y;
+            s.idx = en.x;
+        } else if (B.fi < min(leaf, nf - en.x)) {
+            const int j = en.x + B.fi;
+            s.c = sa[j];
+            s.l = sl[j];
+            s.mask = (unsigned)en.y;
+            s.idx = j;
+        }
+    }
+    return s;
+}
+
+// writes the warp's records into the pair layout (two shuffles per value pair)
+__device__ __forceinline__ void bh_stage(float4* H, float4* D, const BhSrc& s, int lane) {
+    const bool odd = lane & 1;
+    const float mk = __uint_as_float(s.mask);
+    const float s0 = odd ? s.c.x : s.c.z, s1 = odd ? s.c.y : s.c.w;
+    const float s2 = odd ? s.l.x : s.l.z, s3 = odd ? s.l.y : mk;
+    const float r0 = __shfl_xor_sync(0xffffffffu, s0, 1), r1 = __shfl_xor_sync(0xffffffffu, s1, 1);
+    const float r2 = __shfl_xor_sync(0xffffffffu, s2, 1), r3 = __shfl_xor_sync(0xffffffffu, s3, 1);
+    H[lane] = odd ? make_float4(r0, s.c.z, r1, s.c.w) : make_float4(s.c.x, r0, s.c.y, r1);
+    D[lane] = odd ? make_float4(r2, s.l.z, r3, mk) : make_float4(s.l.x, r2, s.l.y, r3);
+}
+
+// p = 6 term of one target against a source pair (packed lanes), with
+// compensated differences d = (t - s) + (tl - sl), K = ((N.d)^2/|d|^4)^3 and
+// |d|^2 + eps in the FMA chain (eps = 1e-18: the self pair gives d = 0 and
+// K = 0 exactly). Lanes outside an entry's mask get K = 0 by a bit mask (bit
+// `lane` of the mask moved to the sign and spread), so a large K of a source
+// this lane does not take never reaches the sum. acc += K a.
 __device__ __forceinline__ unsigned long long bh_energy2_p6(
     unsigned long long tx, unsigned long long ty, unsigned long long tz, unsigned long long ux,
     unsigned long long uy, unsigned long long uz, unsigned long long nx, unsigned long long ny,
     unsigned long long nz, unsigned long long sx, unsigned long long sy, unsigned long long sz,
     unsigned long long lx, unsigned long long ly, unsigned long long lz, unsigned long long sa,
-    unsigned long long acc, unsigned long long eps) {
+    unsigned long long msk, unsigned sh, unsigned long long acc, unsigned long long eps) {
     unsigned long long out;
-    asm("{\n\t.reg .b64 dx, dy, dz, ex, ey, ez, r2, u, ir2, q;\n\t.reg .f32 lo, hi;\n\t"
+    asm("{\n\t.reg .b64 dx, dy, dz, ex, ey, ez, r2, u, ir2, q, mm;\n\t.reg .f32 lo, hi;\n\t.reg .b32 m0, m1;\n\t"
         "sub.rn.f32x2 dx, %1, %10;\n\t"
         "sub.rn.f32x2 dy, %2, %11;\n\t"
         "sub.rn.f32x2 dz, %3, %12;\n\t"
@@ -964,7 +1067,7 @@ __device__ __forceinline__ unsigned long long bh_energy2_p6(
         "add.rn.f32x2 dx, dx, ex;\n\t"
         "add.rn.f32x2 dy, dy, ey;\n\t"
         "add.rn.f32x2 dz, dz, ez;\n\t"
-        "fma.rn.f32x2 r2, dz, dz, %18;\n\t"
+        "fma.rn.f32x2 r2, dz, dz, %20;\n\t"
         "fma.rn.f32x2 r2, dy, dy, r2;\n\t"
         "fma.rn.f32x2 r2, dx, dx, r2;\n\t"
         "mul.rn.f32x2 u, %7, dx;\n\t"
@@ -978,77 +1081,68 @@ __device__ __forceinline__ unsigned long long bh_energy2_p6(
         "mul.rn.f32x2 q, u, u;\n\t"
         "mul.rn.f32x2 u, q, q;\n\t"
         "mul.rn.f32x2 q, u, q;\n\t"
-        "fma.rn.f32x2 %0, q, %16, %17;\n\t}"
+        "mov.b64 {m0, m1}, %17;\n\t"
+        "shl.b32 m0, m0, %18;\n\t"
+        "shl.b32 m1, m1, %18;\n\t"
+        "shr.s32 m0, m0, 31;\n\t"
+        "shr.s32 m1, m1, 31;\n\t"
+        "mov.b64 mm, {m0, m1};\n\t"
+        "and.b64 q, q, mm;\n\t"
+        "fma.rn.f32x2 %0, q, %16, %19;\n\t}"
         : "=l"(out)
         : "l"(tx), "l"(ty), "l"(tz), "l"(ux), "l"(uy), "l"(uz), "l"(nx), "l"(ny), "l"(nz), "l"(sx), "l"(sy),
-          "l"(sz), "l"(lx), "l"(ly), "l"(lz), "l"(sa), "l"(acc), "l"(eps));
+          "l"(sz), "l"(lx), "l"(ly), "l"(lz), "l"(sa), "l"(msk), "r"(sh), "l"(acc), "l"(eps));
     return out;
 }
 
-// k_bh_energy_list for p = 6 with two list entries (or two leaf faces) per
-// packed instruction
+// Energy rows from the interaction lists for p = 6, staged batches of
+// source pairs (see above); FP32 terms per batch, Kahan across batches.
 __global__ void __launch_bounds__(128)
 k_bh_energy_list2(const float4* __restrict__ node4, const float4* __restrict__ nodelo, const float4* __restrict__ sa,
                   const float4* __restrict__ sb, const float4* __restrict__ sl, int nf, BhLists L,
                   const d4* __restrict__ f64a, const int* __restrict__ perm, double* __restrict__ rows,
                   unsigned long long* __restrict__ count) {
-    const int lane = threadIdx.x & 31;
-    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    __shared__ float4 sH[4][32], sD[4][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int g = blockIdx.x * 4 + w;
     if (g >= L.ngroups) return;
     const int i = g * BHL_GROUP + lane;
     const bool has = i < nf;
     const int ii = has ? i : 0;
-    const float4 A = sa[ii], B = sb[ii], Al = sl[ii];
+    const float4 A = sa[ii], N = sb[ii], Al = sl[ii];
     const unsigned long long TX = bp2(A.x, A.x), TY = bp2(A.y, A.y), TZ = bp2(A.z, A.z);
     const unsigned long long UX = bp2(Al.x, Al.x), UY = bp2(Al.y, Al.y), UZ = bp2(Al.z, Al.z);
-    const unsigned long long NX = bp2(B.x, B.x), NY = bp2(B.y, B.y), NZ = bp2(B.z, B.z);
-    const unsigned me = 1u << lane;
+    const unsigned long long NX = bp2(N.x, N.x), NY = bp2(N.y, N.y), NZ = bp2(N.z, N.z);
     const unsigned long long EPS = bp2(1e-18f, 1e-18f);
+    const unsigned sh = 31u - (unsigned)lane;
+    float4* H = sH[w];
+    float4* D = sD[w];
+    const ulonglong2* H2 = reinterpret_cast<const ulonglong2*>(H);
+    const ulonglong2* D2 = reinterpret_cast<const ulonglong2*>(D);
+    const BhBatches Bt(L, g, lane);
     KahanF sum;
-    const int f0 = (int)L.far_off[g], f1 = (int)L.far_off[g + 1];
-    unsigned long long acc = 0ull;
-    int run = 0;
-#pragma unroll 2
-    for (int e = f0; e < f1; e += 2) {
-        const int2 en0 = L.far[e];
-        const bool two = e + 1 < f1;
-        const int2 en1 = two ? L.far[e + 1] : make_int2(en0.x, 0);
-        const float4 c0 = node4[4 * en0.x], c1 = node4[4 * en1.x];
-        const float4 l0 = nodelo[en0.x], l1 = nodelo[en1.x];
-        const bool on0 = (unsigned)en0.y & me, on1 = (unsigned)en1.y & me;
-        acc = bh_energy2_p6(TX, TY, TZ, UX, UY, UZ, NX, NY, NZ, bp2(c0.x, c1.x), bp2(c0.y, c1.y), bp2(c0.z, c1.z),
-                            bp2(l0.x, l1.x), bp2(l0.y, l1.y), bp2(l0.z, l1.z),
-                            bp2(on0 ? c0.w : 0.f, on1 ? c1.w : 0.f), acc, EPS);
-        if (++run == 16) {
-            const float2 a = bu2(acc);
-            sum.add(a.x + a.y);
-            acc = 0ull;
-            run = 0;
-        }
-    }
-    {
-        const float2 a = bu2(acc);
-        sum.add(a.x + a.y);
-        acc = 0ull;
-    }
-    const int n0 = (int)L.near_off[g], n1 = (int)L.near_off[g + 1];
-    for (int e = n0; e < n1; ++e) {
-        const int2 en = L.near[e];
-        const int4 fc = reinterpret_cast<const int4*>(node4)[4 * en.x + 3];   // first, count, skip, leaf
-        const bool on = (unsigned)en.y & me;
-        const int j1 = fc.x + fc.y;
-        for (int j = fc.x; j < j1; j += 2) {
-            const bool two = j + 1 < j1;
-            const float4 s0 = sa[j], s1 = sa[two ? j + 1 : j];
-            const float4 q0 = sl[j], q1 = sl[two ? j + 1 : j];
-            const bool t0 = on && j != i, t1 = on && two && j + 1 != i;
-            acc = bh_energy2_p6(TX, TY, TZ, UX, UY, UZ, NX, NY, NZ, bp2(s0.x, s1.x), bp2(s0.y, s1.y),
-                                bp2(s0.z, s1.z), bp2(q0.x, q1.x), bp2(q0.y, q1.y), bp2(q0.z, q1.z),
-                                bp2(t0 ? s0.w : 0.f, t1 ? s1.w : 0.f), acc, EPS);
+    int2 en = Bt.entry(L, 0, lane);
+    BhSrc rec = bh_record(Bt, 0, en, L.leaf, nf, node4, nodelo, sa, sl);
+    bh_stage(H, D, rec, lane);
+    en = Bt.entry(L, 1, lane);
+    for (int b = 0; b < Bt.nb; ++b) {
+        const bool more = b + 1 < Bt.nb;
+        if (more) rec = bh_record(Bt, b + 1, en, L.leaf, nf, node4, nodelo, sa, sl);
+        const int2 en2 = Bt.entry(L, b + 2, lane);
+        __syncwarp();
+        const int np = (Bt.count(b, L.leaf) + 1) >> 1;
+        unsigned long long acc = 0ull;
+#pragma unroll 4
+        for (int q = 0; q < np; ++q) {
+            const ulonglong2 h0 = H2[2 * q], h1 = H2[2 * q + 1], d0 = D2[2 * q], d1 = D2[2 * q + 1];
+            acc = bh_energy2_p6(TX, TY, TZ, UX, UY, UZ, NX, NY, NZ, h0.x, h0.y, h1.x, d0.x, d0.y, d1.x, h1.y, d1.y,
+                                sh, acc, EPS);
         }
         const float2 a = bu2(acc);
         sum.add(a.x + a.y);
-        acc = 0ull;
+        __syncwarp();
+        if (more) bh_stage(H, D, rec, lane);
+        en = en2;
     }
     if (has) rows[perm[i]] = f64a[perm[i]].w * sum.value();
     if (count && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(count, L.interactions);
@@ -1373,7 +1467,7 @@ k_bh_diff_list(const float4* __restrict__ node4, const float4* __restrict__ node
     const int n0 = (int)L.near_off[g], n1 = (int)L.near_off[g + 1];
     for (int e = n0; e < n1; ++e) {
         const int2 en = L.near[e];
-        const int4 fc = reinterpret_cast<const int4*>(node4)[4 * en.x + 3];
+        const int2 fc = make_int2(en.x, min(L.leaf, nf - en.x));   // the leaf's first face, count
         const bool on = (unsigned)en.y & me;
         for (int j = fc.x; j < fc.x + fc.y; ++j) {
             const float4 s = sa[j];
@@ -1449,18 +1543,42 @@ __device__ __forceinline__ float warp_sum8(const float (&v)[8]) {
     return r;
 }
 
-// k_bh_diff_list for p = 6 with two list entries (or two leaf faces) per
-// packed instruction: the target side as in k_bh_diff_list, the source sides
-// of both entries summed over the warp together (warp_sum8) and added with
-// one FP64 atomic per entry and component
+// bit `lane` of each half of a packed mask pair, spread over the half
+// (all ones where set, zero where not): sh = 31 - lane
+__device__ __forceinline__ unsigned long long lane_bits2(float2 m, unsigned sh) {
+    unsigned long long r;
+    asm("{\n\t.reg .b32 m0, m1;\n\t"
+        "mov.b32 m0, %1;\n\tmov.b32 m1, %2;\n\t"
+        "shl.b32 m0, m0, %3;\n\tshl.b32 m1, m1, %3;\n\t"
+        "shr.s32 m0, m0, 31;\n\tshr.s32 m1, m1, 31;\n\t"
+        "mov.b64 %0, {m0, m1};\n\t}"
+        : "=l"(r) : "f"(m.x), "f"(m.y), "r"(sh));
+    return r;
+}
+__device__ __forceinline__ float2 q2and(float2 a, unsigned long long m) {
+    float2 d;
+    asm("{\n\t.reg .b64 ra;\n\tmov.b64 ra, {%2, %3};\n\tand.b64 ra, ra, %4;\n\tmov.b64 {%0, %1}, ra;\n\t}"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "l"(m));
+    return d;
+}
+
+// k_bh_diff_list for p = 6 over staged batches of source pairs (as the
+// energy): the target side as in k_bh_diff_list, two sources per packed
+// instruction; lanes outside an entry's mask get c = K = 0 by a bit mask.
+// FULL: the source sides of both sources of a pair are summed over the warp
+// together (warp_sum8) and added with one FP64 atomic per source and
+// component (node accumulators in far batches, face accumulators in near
+// batches).
 template <bool FULL>
 __global__ void __launch_bounds__(128)
 k_bh_diff_list2(const float4* __restrict__ node4, const float4* __restrict__ nodelo, const float4* __restrict__ sa,
                 const float4* __restrict__ sb, const float4* __restrict__ sl, int nf, BhLists L, float p,
                 double* __restrict__ tacc, double* __restrict__ nacc, double* __restrict__ facc,
                 unsigned long long* __restrict__ count) {
-    const int lane = threadIdx.x & 31;
-    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    __shared__ float4 sH[4][32], sD[4][32];
+    __shared__ int sI[4][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int g = blockIdx.x * 4 + w;
     if (g >= L.ngroups) return;
     const int i0 = g * BHL_GROUP + lane;
     const bool has = i0 < nf;
@@ -1470,98 +1588,74 @@ k_bh_diff_list2(const float4* __restrict__ node4, const float4* __restrict__ nod
     const float2 TX = q2(A.x), TY = q2(A.y), TZ = q2(A.z), UX = q2(Al.x), UY = q2(Al.y), UZ = q2(Al.z);
     const float2 NX = q2(B.x), NY = q2(B.y), NZ = q2(B.z), EPS2 = q2(1e-18f);
     const float2 S1 = q2(-aS * p), S2 = q2(2.f * aS * p), AS = q2(aS);
-    const unsigned me = 1u << lane;
+    const unsigned sh = 31u - (unsigned)lane;
+    float4* H = sH[w];
+    float4* D = sD[w];
+    int* I = sI[w];
     KahanF acc[8];
     float2 pt[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) pt[k] = make_float2(0.f, 0.f);
-    auto flush = [&]() {
+    const BhBatches Bt(L, g, lane);
+    int2 en = Bt.entry(L, 0, lane);
+    BhSrc rec = bh_record(Bt, 0, en, L.leaf, nf, node4, nodelo, sa, sl);
+    bh_stage(H, D, rec, lane);
+    I[lane] = rec.idx;
+    en = Bt.entry(L, 1, lane);
+    for (int b = 0; b < Bt.nb; ++b) {
+        const bool more = b + 1 < Bt.nb;
+        if (more) rec = bh_record(Bt, b + 1, en, L.leaf, nf, node4, nodelo, sa, sl);
+        const int2 en2 = Bt.entry(L, b + 2, lane);
+        double* sacc = b < Bt.nbf ? nacc : facc;
+        __syncwarp();
+        const int np = (Bt.count(b, L.leaf) + 1) >> 1;
+        for (int q = 0; q < np; ++q) {
+            const float4 h0 = H[2 * q], h1 = H[2 * q + 1], d0 = D[2 * q], d1 = D[2 * q + 1];
+            const unsigned long long mm = lane_bits2(make_float2(d1.z, d1.w), sh);
+            const float2 dx = q2add(q2sub(TX, make_float2(h0.x, h0.y)), q2sub(UX, make_float2(d0.x, d0.y)));
+            const float2 dy = q2add(q2sub(TY, make_float2(h0.z, h0.w)), q2sub(UY, make_float2(d0.z, d0.w)));
+            const float2 dz = q2add(q2sub(TZ, make_float2(h1.x, h1.y)), q2sub(UZ, make_float2(d1.x, d1.y)));
+            const float2 W = make_float2(h1.z, h1.w);
+            const float2 r2 = q2fma(dx, dx, q2fma(dy, dy, q2fma(dz, dz, EPS2)));
+            const float2 u = q2fma(NX, dx, q2fma(NY, dy, q2mul(NZ, dz)));
+            const float2 ir2 = make_float2(frcp(r2.x), frcp(r2.y));
+            const float2 ir4 = q2mul(ir2, ir2);
+            const float2 qq = q2mul(q2mul(u, u), ir4);
+            const float2 mq = q2mul(qq, qq);
+            const float2 K = q2and(q2mul(mq, qq), mm);
+            const float2 c = q2and(q2mul(q2mul(mq, u), ir4), mm);
+            const float2 wc = q2mul(W, c), wK = q2mul(W, K), wKd = q2mul(wK, ir2);
+            pt[0] = q2add(pt[0], wc);
+            pt[1] = q2fma(wc, dx, pt[1]);
+            pt[2] = q2fma(wc, dy, pt[2]);
+            pt[3] = q2fma(wc, dz, pt[3]);
+            pt[4] = q2fma(wKd, dx, pt[4]);
+            pt[5] = q2fma(wKd, dy, pt[5]);
+            pt[6] = q2fma(wKd, dz, pt[6]);
+            pt[7] = q2add(pt[7], wK);
+            if (FULL) {
+                const float2 s1 = q2mul(S1, wc), s2 = q2mul(S2, wKd);
+                const float2 G0 = q2fma(s2, dx, q2mul(s1, NX)), G1 = q2fma(s2, dy, q2mul(s1, NY)),
+                             G2 = q2fma(s2, dz, q2mul(s1, NZ));
+                const float2 Q = q2mul(AS, K);
+                const float v[8] = {G0.x, G1.x, G2.x, Q.x, G0.y, G1.y, G2.y, Q.y};
+                const float r = warp_sum8(v);
+                const int vi = lane >> 2;             // value: source vi >> 2 of the pair, component vi & 3
+                const int idx = I[2 * q + (vi >> 2)];
+                if ((lane & 3) == 0 && idx >= 0) atomicAdd(sacc + 4 * idx + (vi & 3), f2d_int(r));
+            }
+        }
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
             acc[k].add(pt[k].x + pt[k].y);
             pt[k] = make_float2(0.f, 0.f);
         }
-    };
-    // two interactions (lanes x, y of the float2 arguments): sources at
-    // (SX, SY, SZ) + low parts, weights W (zero where masked), on-flags for Q
-    auto interact2 = [&](float2 SX, float2 SY, float2 SZ, float2 LX, float2 LY, float2 LZ, float2 W, float2 ON,
-                         float (&v)[8]) {
-        const float2 dx = q2add(q2sub(TX, SX), q2sub(UX, LX));
-        const float2 dy = q2add(q2sub(TY, SY), q2sub(UY, LY));
-        const float2 dz = q2add(q2sub(TZ, SZ), q2sub(UZ, LZ));
-        const float2 r2 = q2fma(dx, dx, q2fma(dy, dy, q2fma(dz, dz, EPS2)));
-        const float2 u = q2fma(NX, dx, q2fma(NY, dy, q2mul(NZ, dz)));
-        const float2 ir2 = make_float2(frcp(r2.x), frcp(r2.y));
-        const float2 ir4 = q2mul(ir2, ir2);
-        const float2 q = q2mul(q2mul(u, u), ir4);
-        const float2 mq = q2mul(q, q);
-        const float2 K = q2mul(mq, q);
-        const float2 c = q2mul(q2mul(mq, u), ir4);
-        const float2 wc = q2mul(W, c), wK = q2mul(W, K), wKd = q2mul(wK, ir2);
-        pt[0] = q2add(pt[0], wc);
-        pt[1] = q2fma(wc, dx, pt[1]);
-        pt[2] = q2fma(wc, dy, pt[2]);
-        pt[3] = q2fma(wc, dz, pt[3]);
-        pt[4] = q2fma(wKd, dx, pt[4]);
-        pt[5] = q2fma(wKd, dy, pt[5]);
-        pt[6] = q2fma(wKd, dz, pt[6]);
-        pt[7] = q2add(pt[7], wK);
-        if (FULL) {
-            const float2 s1 = q2mul(S1, wc), s2 = q2mul(S2, wKd);
-            const float2 G0 = q2fma(s2, dx, q2mul(s1, NX)), G1 = q2fma(s2, dy, q2mul(s1, NY)),
-                         G2 = q2fma(s2, dz, q2mul(s1, NZ));
-            const float2 Q = q2mul(q2mul(AS, K), ON);
-            v[0] = G0.x; v[1] = G1.x; v[2] = G2.x; v[3] = Q.x;
-            v[4] = G0.y; v[5] = G1.y; v[6] = G2.y; v[7] = Q.y;
+        __syncwarp();
+        if (more) {
+            bh_stage(H, D, rec, lane);
+            I[lane] = rec.idx;
         }
-    };
-    const int f0 = (int)L.far_off[g], f1 = (int)L.far_off[g + 1];
-    int run = 0;
-    for (int e = f0; e < f1; e += 2) {
-        const int2 en0 = L.far[e];
-        const bool two = e + 1 < f1;
-        const int2 en1 = two ? L.far[e + 1] : make_int2(en0.x, 0);
-        const float4 c0 = node4[4 * en0.x], c1 = node4[4 * en1.x];
-        const float4 l0 = nodelo[en0.x], l1 = nodelo[en1.x];
-        const bool on0 = (unsigned)en0.y & me, on1 = (unsigned)en1.y & me;
-        float v[8];
-        interact2(make_float2(c0.x, c1.x), make_float2(c0.y, c1.y), make_float2(c0.z, c1.z),
-                  make_float2(l0.x, l1.x), make_float2(l0.y, l1.y), make_float2(l0.z, l1.z),
-                  make_float2(on0 ? c0.w : 0.f, on1 ? c1.w : 0.f), make_float2(on0 ? 1.f : 0.f, on1 ? 1.f : 0.f), v);
-        if (FULL) {
-            const float r = warp_sum8(v);
-            const int vi = lane >> 2;             // value: entry vi >> 2, component vi & 3
-            if ((lane & 3) == 0 && (vi < 4 || two))
-                atomicAdd(nacc + 4 * (vi < 4 ? en0.x : en1.x) + (vi & 3), f2d_int(r));
-        }
-        if (++run == 16) {
-            flush();
-            run = 0;
-        }
-    }
-    flush();
-    const int n0 = (int)L.near_off[g], n1 = (int)L.near_off[g + 1];
-    for (int e = n0; e < n1; ++e) {
-        const int2 en = L.near[e];
-        const int4 fc = reinterpret_cast<const int4*>(node4)[4 * en.x + 3];
-        const bool on = (unsigned)en.y & me;
-        const int j1 = fc.x + fc.y;
-        for (int j = fc.x; j < j1; j += 2) {
-            const bool two = j + 1 < j1;
-            const int jb = two ? j + 1 : j;
-            const float4 s0 = sa[j], s1 = sa[jb], q0 = sl[j], q1 = sl[jb];
-            const bool t0 = on && j != i0, t1 = on && two && jb != i0;
-            float v[8];
-            interact2(make_float2(s0.x, s1.x), make_float2(s0.y, s1.y), make_float2(s0.z, s1.z),
-                      make_float2(q0.x, q1.x), make_float2(q0.y, q1.y), make_float2(q0.z, q1.z),
-                      make_float2(t0 ? s0.w : 0.f, t1 ? s1.w : 0.f), make_float2(t0 ? 1.f : 0.f, t1 ? 1.f : 0.f), v);
-            if (FULL) {
-                const float r = warp_sum8(v);
-                const int vi = lane >> 2;
-                if ((lane & 3) == 0 && (vi < 4 || two)) atomicAdd(facc + 4 * (vi < 4 ? j : jb) + (vi & 3), f2d_int(r));
-            }
-        }
-        flush();
+        en = en2;
     }
     if (has)
         for (int k = 0; k < 8; ++k) tacc[(size_t)i0 * 8 + k] = acc[k].value();

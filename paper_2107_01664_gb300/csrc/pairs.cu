@@ -1790,8 +1790,40 @@ k_bh_apply(const BvhNode* __restrict__ node, const float4* __restrict__ nodelo, 
     if (count && nint) atomicAdd(count, (unsigned long long)nint);
 }
 
-// Barnes-Hut operator products from the interaction lists (one warp per
-// group of 32 sorted targets; lanes outside an entry's mask add nothing)
+// Barnes-Hut operator products from the interaction lists: one warp per
+// group of 32 sorted targets, streaming the group's far entries and then its
+// near leaves in batches of 32 sources (32 far nodes, or the faces of
+// 32 / leaf near leaves). The records of a batch (far: barycenter hi, low
+// part, the node's X and projector; near: the face's barycenter, low part,
+// normal and W) are copied global -> shared with cp.async, one 16-byte chunk
+// per lane and instruction, one batch ahead of their use (two buffers), so
+// the gathers of 32 sources are in flight together while the warp evaluates
+// the previous batch. Shared layout per warp and buffer: chunk-major
+// [chunk][32 sources] float4 (each copy instruction writes 512 contiguous
+// bytes; each read is a broadcast), plus the entries' lane masks and the
+// near faces' indices. A lane outside an entry's mask, and the self pair,
+// get a zero kernel value (the geometric factor h is selected to 0; the other
+// factors stay finite at d = 0 thanks to the |d|^2 offset).
+template <int OP, int KC> struct BhApplyStage {
+    using L = OpLayout<OP, KC>;
+    static constexpr bool LOW = (OP == TP_OP_A || OP == TP_OP_B0);
+    static constexpr int RF = 2 + L::NW4 + (LOW ? 2 : 0);   // far: c, lo, X[NW4], P[2]
+    static constexpr int RN = 2 + (LOW ? 1 : 0) + L::NW4;   // near: c, lo, normal, W[NW4]
+    static constexpr int R = RF > RN ? RF : RN;
+    static constexpr int BUF = R * 32;                      // float4 per warp and buffer
+    static constexpr size_t bytes = sizeof(float4) * 4 * 2 * BUF + sizeof(int) * 4 * 2 * 64;
+};
+
+__device__ __forceinline__ void cp_async16(void* sdst, const void* gsrc, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 template <int OP, int KC>
 __global__ void __launch_bounds__(128)
 k_bh_apply_list(const float4* __restrict__ node4, const float4* __restrict__ nodelo, const float4* __restrict__ sa,
@@ -1799,99 +1831,163 @@ k_bh_apply_list(const float4* __restrict__ node4, const float4* __restrict__ nod
                 const float4* __restrict__ Ws, const float4* __restrict__ nodeX, const float4* __restrict__ nodeP,
                 float s_exp, float l_exp, double* __restrict__ part, unsigned long long* __restrict__ count) {
     using L = OpLayout<OP, KC>;
-    constexpr bool LOW = (OP == TP_OP_A || OP == TP_OP_B0);
+    using SG = BhApplyStage<OP, KC>;
+    constexpr bool LOW = SG::LOW;
     constexpr int NP = L::NA / 2;
     constexpr int NW4 = L::NW4;
-    const int lane = threadIdx.x & 31;
-    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    extern __shared__ float4 bsm[];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int g = blockIdx.x * 4 + w;
     if (g >= Ls.ngroups) return;
+    float4* buf0 = bsm + (size_t)w * 2 * SG::BUF;
+    int* meta = reinterpret_cast<int*>(bsm + 4 * 2 * SG::BUF) + w * 128;   // [2][mask 32, idx 32]
     const int i = g * BHL_GROUP + lane;
     const bool has = i < nf;
     const int ii = has ? i : 0;
     const float4 A = sa[ii], B = sb[ii], Al = sl[ii];
-    const unsigned me = 1u << lane;
+    // batches: far first, then near (lb leaves of `leaf` faces per batch)
+    const int f0 = (int)Ls.far_off[g], f1 = (int)Ls.far_off[g + 1];
+    const int n0 = (int)Ls.near_off[g], n1 = (int)Ls.near_off[g + 1];
+    const int leaf = Ls.leaf, lb = 32 / leaf, kl = lane / leaf, fi = lane - kl * leaf;
+    const int nbf = (f1 - f0 + 31) >> 5, nb = nbf + (n1 - n0 + lb - 1) / lb;
+    auto entry = [&](int b) -> int2 {
+        if (b < nbf) {
+            const int e = f0 + 32 * b + lane;
+            return e < f1 ? Ls.far[e] : make_int2(-1, 0);
+        }
+        const int e = n0 + lb * (b - nbf) + kl;
+        return (kl < lb && e < n1) ? Ls.near[e] : make_int2(-1, 0);
+    };
+    // issue the copies of this lane's source of batch b into buffer b & 1
+    auto issue = [&](int b, int2 en) {
+        float4* dst = buf0 + (b & 1) * SG::BUF + lane;
+        int* mt = meta + (b & 1) * 64;
+        if (b < nbf) {
+            const bool v = en.x >= 0;
+            const int id = v ? en.x : 0;
+            cp_async16(dst, node4 + 4 * (size_t)id, v);
+            cp_async16(dst + 32, nodelo + id, v);
+#pragma unroll
+            for (int q = 0; q < NW4; ++q) cp_async16(dst + 32 * (2 + q), nodeX + (size_t)id * NW4 + q, v);
+            if (LOW) {
+                cp_async16(dst + 32 * (2 + NW4), nodeP + 2 * (size_t)id, v);
+                cp_async16(dst + 32 * (3 + NW4), nodeP + 2 * (size_t)id + 1, v);
+            }
+            mt[lane] = v ? en.y : 0;
+            mt[32 + lane] = -1;
+        } else {
+            const bool v = en.x >= 0 && fi < min(leaf, nf - en.x);
+            const int j = v ? en.x + fi : 0;
+            cp_async16(dst, sa + j, v);
+            cp_async16(dst + 32, sl + j, v);
+            if (LOW) cp_async16(dst + 64, sb + j, v);
+            constexpr int W0 = LOW ? 3 : 2;
+#pragma unroll
+            for (int q = 0; q < NW4; ++q) cp_async16(dst + 32 * (W0 + q), Ws + (size_t)j * NW4 + q, v);
+            mt[lane] = v ? en.y : 0;
+            mt[32 + lane] = v ? j : -1;
+        }
+        cp_async_commit();
+    };
+    const unsigned sh = 31u - (unsigned)lane;
     float2 pt[NP];
     Acc2<float> acc[NP];
 #pragma unroll
     for (int c = 0; c < NP; ++c) pt[c] = make_float2(0.f, 0.f);
-    const int f0 = (int)Ls.far_off[g], f1 = (int)Ls.far_off[g + 1];
-    int run = 0;
+    int2 en = entry(0);
+    if (nb > 0) issue(0, en);
+    en = entry(1);
+    for (int b = 0; b < nb; ++b) {
+        const bool more = b + 1 < nb;
+        if (more) issue(b + 1, en);
+        const int2 en2 = entry(b + 2);
+        if (more) cp_async_wait<1>();
+        else cp_async_wait<0>();
+        __syncwarp();
+        const float4* C = buf0 + (b & 1) * SG::BUF;
+        const int* mt = meta + (b & 1) * 64;
+        if (b < nbf) {
+            const int cnt = min(32, f1 - f0 - 32 * b);
 #pragma unroll 2
-    for (int e = f0; e < f1; ++e) {
-        const int2 en = Ls.far[e];
-        const int id = en.x;
-        const bool on = (unsigned)en.y & me;
-        const float4 c = node4[4 * id];
-        const float4 nl = nodelo[id];
-        const float dx = (A.x - c.x) + (Al.x - nl.x), dy = (A.y - c.y) + (Al.y - nl.y), dz = (A.z - c.z) + (Al.z - nl.z);
-        float2 x2[2 * NW4];
+            for (int k = 0; k < cnt; ++k) {
+                const bool on = ((unsigned)mt[k] << sh) >> 31;
+                const float4 c = C[k], nl = C[32 + k];
+                const float dx = (A.x - c.x) + (Al.x - nl.x), dy = (A.y - c.y) + (Al.y - nl.y),
+                            dz = (A.z - c.z) + (Al.z - nl.z);
+                float2 x2[2 * NW4];
 #pragma unroll
-        for (int q = 0; q < NW4; ++q) {
-            const float4 x = nodeX[(size_t)id * NW4 + q];
-            x2[2 * q] = make_float2(x.x, x.y);
-            x2[2 * q + 1] = make_float2(x.z, x.w);
-        }
-        const float r2 = r2_eps(dx, dy, dz);
-        if (OP == TP_OP_L) {
-            const float h = on ? pow_(r2, -l_exp) : 0.f;
+                for (int q = 0; q < NW4; ++q) {
+                    const float4 x = C[32 * (2 + q) + k];
+                    x2[2 * q] = make_float2(x.x, x.y);
+                    x2[2 * q + 1] = make_float2(x.z, x.w);
+                }
+                const float r2 = r2_eps(dx, dy, dz);
+                if (OP == TP_OP_L) {
+                    const float h = on ? pow_(r2, -l_exp) : 0.f;
 #pragma unroll
-            for (int k = 0; k < NP; ++k) pt[k] = pfma(h, x2[k], pt[k]);
+                    for (int q = 0; q < NP; ++q) pt[q] = pfma(h, x2[q], pt[q]);
+                } else {
+                    const float hB = on ? pow_(r2, -s_exp) : 0.f;
+#pragma unroll
+                    for (int q = 0; q < L::NH / 2; ++q) pt[q] = pfma(hB, x2[q], pt[q]);
+                    if (LOW) {
+                        const float4 p0 = C[32 * (2 + NW4) + k], p1 = C[32 * (3 + NW4) + k];
+                        const float ir2 = rcp_(r2);
+                        const float tS = (B.x * dx + B.y * dy + B.z * dz) * ir2;
+                        const float qx = p0.x * dx + p0.y * dy + p0.z * dz;
+                        const float qy = p0.y * dx + p0.w * dy + p1.x * dz;
+                        const float qz = p0.z * dx + p1.x * dy + p1.y * dz;
+                        const float tT2 = (qx * qx + qy * qy + qz * qz) * (ir2 * ir2);   // |P_I d|^2 / |d|^4
+                        const float h0 = 0.5f * fmaf(tS, tS, tT2) * hB;
+#pragma unroll
+                        for (int q = L::NH / 2; q < NP; ++q) pt[q] = pfma(h0, x2[q], pt[q]);
+                    }
+                }
+            }
         } else {
-            const float hB = on ? pow_(r2, -s_exp) : 0.f;
+            const int cnt = min(lb, n1 - n0 - lb * (b - nbf)) * leaf;
+            constexpr int W0 = LOW ? 3 : 2;
+#pragma unroll 2
+            for (int k = 0; k < cnt; ++k) {
+                const bool on = (((unsigned)mt[k] << sh) >> 31) && mt[32 + k] != i;
+                const float4 s = C[k], l = C[32 + k];
+                const float dx = (A.x - s.x) + (Al.x - l.x), dy = (A.y - s.y) + (Al.y - l.y),
+                            dz = (A.z - s.z) + (Al.z - l.z);
+                float2 x2[2 * NW4];
 #pragma unroll
-            for (int k = 0; k < L::NH / 2; ++k) pt[k] = pfma(hB, x2[k], pt[k]);
-            if (LOW) {
-                const float4 p0 = nodeP[2 * id], p1 = nodeP[2 * id + 1];
-                const float ir2 = rcp_(r2);
-                const float tS = (B.x * dx + B.y * dy + B.z * dz) * ir2;
-                const float qx = p0.x * dx + p0.y * dy + p0.z * dz;
-                const float qy = p0.y * dx + p0.w * dy + p1.x * dz;
-                const float qz = p0.z * dx + p1.x * dy + p1.y * dz;
-                const float tT2 = (qx * qx + qy * qy + qz * qz) * (ir2 * ir2);   // |P_I d|^2 / |d|^4
-                const float h0 = 0.5f * fmaf(tS, tS, tT2) * hB;
+                for (int q = 0; q < NW4; ++q) {
+                    const float4 x = C[32 * (W0 + q) + k];
+                    x2[2 * q] = make_float2(x.x, x.y);
+                    x2[2 * q + 1] = make_float2(x.z, x.w);
+                }
+                const float r2 = r2_eps(dx, dy, dz);
+                if (OP == TP_OP_L) {
+                    const float h = on ? pow_(r2, -l_exp) : 0.f;
 #pragma unroll
-                for (int k = L::NH / 2; k < NP; ++k) pt[k] = pfma(h0, x2[k], pt[k]);
+                    for (int q = 0; q < NP; ++q) pt[q] = pfma(h, x2[q], pt[q]);
+                } else {
+                    const float hB = on ? pow_(r2, -s_exp) : 0.f;
+#pragma unroll
+                    for (int q = 0; q < L::NH / 2; ++q) pt[q] = pfma(hB, x2[q], pt[q]);
+                    if (LOW) {
+                        const float4 m = C[64 + k];
+                        const float ir2 = rcp_(r2);
+                        const float tS = (B.x * dx + B.y * dy + B.z * dz) * ir2;
+                        const float tT = (m.x * dx + m.y * dy + m.z * dz) * ir2;
+                        const float h0 = 0.5f * fmaf(tS, tS, tT * tT) * hB;   // (k2(S;T) + k2(T;S)) / 2 |d|^{-2s}
+#pragma unroll
+                        for (int q = L::NH / 2; q < NP; ++q) pt[q] = pfma(h0, x2[q], pt[q]);
+                    }
+                }
             }
         }
-        if (++run == 32) {
 #pragma unroll
-            for (int k = 0; k < NP; ++k) {
-                acc[k].add(pt[k]);
-                pt[k] = make_float2(0.f, 0.f);
-            }
-            run = 0;
+        for (int q = 0; q < NP; ++q) {
+            acc[q].add(pt[q]);
+            pt[q] = make_float2(0.f, 0.f);
         }
-    }
-#pragma unroll
-    for (int k = 0; k < NP; ++k) {
-        acc[k].add(pt[k]);
-        pt[k] = make_float2(0.f, 0.f);
-    }
-    const int n0 = (int)Ls.near_off[g], n1 = (int)Ls.near_off[g + 1];
-    for (int e = n0; e < n1; ++e) {
-        const int2 en = Ls.near[e];
-        const int4 fc = reinterpret_cast<const int4*>(node4)[4 * en.x + 3];   // first, count, skip, leaf
-        const bool on = (unsigned)en.y & me;
-        for (int j = fc.x; j < fc.x + fc.y; ++j) {
-            const float4 s = sa[j], l = sl[j], mm = sb[j];
-            float2 x2[2 * NW4];
-            const bool t = on && j != i;
-#pragma unroll
-            for (int q = 0; q < NW4; ++q) {
-                const float4 x = t ? Ws[(size_t)j * NW4 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
-                x2[2 * q] = make_float2(x.x, x.y);
-                x2[2 * q + 1] = make_float2(x.z, x.w);
-            }
-            // the self pair and masked lanes: zero vectors, and d moved off 0
-            const float dx = t ? (A.x - s.x) + (Al.x - l.x) : 1.f, dy = (A.y - s.y) + (Al.y - l.y),
-                        dz = (A.z - s.z) + (Al.z - l.z);
-            apply_term<float, OP, false, KC>(dx, dy, dz, B.x, B.y, B.z, mm.x, mm.y, mm.z, x2, s_exp, l_exp, pt);
-        }
-#pragma unroll
-        for (int k = 0; k < NP; ++k) {
-            acc[k].add(pt[k]);
-            pt[k] = make_float2(0.f, 0.f);
-        }
+        __syncwarp();
+        en = en2;
     }
     if (has)   // sorted order: consecutive lanes write consecutive words
 #pragma unroll
@@ -1939,8 +2035,11 @@ static int launch_bh_apply_op(tp_mesh* m, const tp_params* p, const double* v, i
         {
             ProfScope ps(m, PK_BH_APPLY, 0.0, st);
             m->prof.cols[PK_BH_APPLY] += KC;
+            // (resident_per_sm raises the kernel's dynamic shared memory limit when it needs more than 48 KB)
+            if (lists && resident_per_sm((const void*)k_bh_apply_list<OP, KC>, 128, BhApplyStage<OP, KC>::bytes) < 1)
+                return fail(TP_ERR_CUDA, "Barnes-Hut apply: shared memory for the staged batches not available");
             if (lists)
-                k_bh_apply_list<OP, KC><<<(Ls.ngroups + 3) / 4, 128, 0, st>>>(
+                k_bh_apply_list<OP, KC><<<(Ls.ngroups + 3) / 4, 128, BhApplyStage<OP, KC>::bytes, st>>>(
                     reinterpret_cast<const float4*>(bv.node), bv.nodelo, bv.sa, bv.sb, bv.sl, nf, Ls, Ws, nodeX,
                     nodeP, (float)s, (float)l_exp, m->part.as<double>(), cnt);
             else

@@ -109,7 +109,8 @@ struct BhLists {
     const long long* far_off = nullptr;    // [ngroups + 1]
     const long long* near_off = nullptr;   // [ngroups + 1]
     const int2* far = nullptr;
-    const int2* near = nullptr;
+    const int2* near = nullptr;    // near entries: (first face of the leaf, lane mask)
+    int leaf = 0;                  // leaf size: a near leaf holds min(leaf, nf - first) faces
     unsigned long long interactions = 0;   // (target, node) plus (target, face) terms of one evaluation
 };
 

@@ -217,7 +217,8 @@ def _base_mesh(kind: str, a: int, b: int = 0):
 def make_requests(n: int, f_min: int, f_max: int, rate: float, seed: int) -> list[Request]:
     """n requests with Poisson arrivals at `rate` per second; each a perturbed
     icosphere or torus (50/50) whose face count is drawn log-uniformly in
-    [f_min, f_max] (icospheres take the nearest subdivision level), with
+    [f_min, f_max] (icospheres take the nearest subdivision level inside
+    that range), with
     seeded N(0, 0.01^2) noise per vertex coordinate. The constraint targets
     are left to the server (the mesh's own area and volume)."""
     from synth import gaussian_noise
@@ -228,8 +229,13 @@ def make_requests(n: int, f_min: int, f_max: int, rate: float, seed: int) -> lis
         t += rng.exponential(1.0 / rate)
         target = float(np.exp(rng.uniform(np.log(f_min), np.log(f_max))))
         if rng.random() < 0.5:
-            lvl = int(np.clip(round(np.log(target / 20.0) / np.log(4.0)), 1, 8))
-            V, F = _base_mesh("ico", lvl)
+            # the nearest level whose 20 * 4^l faces lie in [f_min, f_max]
+            # (the nearest level overall when none does)
+            lo = int(np.ceil(np.log(f_min / 20.0) / np.log(4.0) - 1e-9))
+            hi = int(np.floor(np.log(f_max / 20.0) / np.log(4.0) + 1e-9))
+            lvl = int(round(np.log(target / 20.0) / np.log(4.0)))
+            lvl = int(np.clip(lvl, lo, hi)) if lo <= hi else lvl
+            V, F = _base_mesh("ico", int(np.clip(lvl, 1, 8)))
         else:
             nm = max(8, int(round(np.sqrt(target / 2.0 * 4.0))))
             nn = max(4, int(round(target / 2.0 / nm)))
