@@ -1132,7 +1132,7 @@ k_bh_energy_list2(const float4* __restrict__ node4, const float4* __restrict__ n
         __syncwarp();
         const int np = (Bt.count(b, L.leaf) + 1) >> 1;
         unsigned long long acc = 0ull;
-#pragma unroll 4
+#pragma unroll 8
         for (int q = 0; q < np; ++q) {
             const ulonglong2 h0 = H2[2 * q], h1 = H2[2 * q + 1], d0 = D2[2 * q], d1 = D2[2 * q + 1];
             acc = bh_energy2_p6(TX, TY, TZ, UX, UY, UZ, NX, NY, NZ, h0.x, h0.y, h1.x, d0.x, d0.y, d1.x, h1.y, d1.y,
@@ -1570,7 +1570,7 @@ __device__ __forceinline__ float2 q2and(float2 a, unsigned long long m) {
 // component (node accumulators in far batches, face accumulators in near
 // batches).
 template <bool FULL>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 5)
 k_bh_diff_list2(const float4* __restrict__ node4, const float4* __restrict__ nodelo, const float4* __restrict__ sa,
                 const float4* __restrict__ sb, const float4* __restrict__ sl, int nf, BhLists L, float p,
                 double* __restrict__ tacc, double* __restrict__ nacc, double* __restrict__ facc,

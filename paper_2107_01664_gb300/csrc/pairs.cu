@@ -1908,7 +1908,7 @@ k_bh_apply_list(const float4* __restrict__ node4, const float4* __restrict__ nod
         const int* mt = meta + (b & 1) * 64;
         if (b < nbf) {
             const int cnt = min(32, f1 - f0 - 32 * b);
-#pragma unroll 2
+#pragma unroll 4
             for (int k = 0; k < cnt; ++k) {
                 const bool on = ((unsigned)mt[k] << sh) >> 31;
                 const float4 c = C[k], nl = C[32 + k];
@@ -1947,7 +1947,7 @@ k_bh_apply_list(const float4* __restrict__ node4, const float4* __restrict__ nod
         } else {
             const int cnt = min(lb, n1 - n0 - lb * (b - nbf)) * leaf;
             constexpr int W0 = LOW ? 3 : 2;
-#pragma unroll 2
+#pragma unroll 4
             for (int k = 0; k < cnt; ++k) {
                 const bool on = (((unsigned)mt[k] << sh) >> 31) && mt[32 + k] != i;
                 const float4 s = C[k], l = C[32 + k];
