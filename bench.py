@@ -58,8 +58,14 @@ FP32_LANES_PER_SM = 128
 
 
 def step_params(tp):
+    """The timed step: FP32 pair terms, flexible GMRES to 1e-5 on the exact
+    operator, the preconditioner's Poisson solves to 1e-4 (inside flexible
+    GMRES they are preconditioner applications: their accuracy moves the
+    iteration count, not the converged direction; 27 iterations on torus_20k
+    at 1e-4 as at 1e-6), and an Armijo line search whose first trial moves no
+    vertex by more than a quarter of the mean face size (tau0_disp = 0.25)."""
     return tp.params(theta=0.0, precision=tp.TP_PREC_FP32, krylov_tol=1e-5, krylov_max=60,
-                     gmres_restart=30, cg_tol=1e-6, cg_max=20000, proj_iters=1)
+                     gmres_restart=30, cg_tol=1e-4, cg_max=20000, proj_iters=1, tau0_disp=0.25)
 
 
 def bh_params(tp):
@@ -943,8 +949,8 @@ def serving(tp, dev, n=512, f_min=2000, f_max=200000, slots=4, fp64_n=16, fp64_f
     import numpy as np
     from paper_2107_01664_gb300 import serve
     t_start = time.perf_counter()
-    p32 = tp.params(precision=tp.TP_PREC_FP32, krylov_tol=1e-5, krylov_max=30, cg_tol=1e-6, tau0_disp=0.25)
-    p64 = tp.params(precision=tp.TP_PREC_FP64, krylov_tol=1e-5, krylov_max=30, cg_tol=1e-6, tau0_disp=0.25)
+    p32 = tp.params(precision=tp.TP_PREC_FP32, krylov_tol=1e-5, krylov_max=30, cg_tol=1e-4, tau0_disp=0.25)
+    p64 = tp.params(precision=tp.TP_PREC_FP64, krylov_tol=1e-5, krylov_max=30, cg_tol=1e-4, tau0_disp=0.25)
     reqs = serve.make_requests(n, f_min, f_max, rate=1.0, seed=404)
 
     def at_rate(rs, rate, seed):

@@ -264,7 +264,7 @@ int tp_mesh_destroy(tp_mesh* m) {
                   &m->f32c, &m->tilebox,
                   &m->f64a, &m->f64b, &m->fgrad, &m->rowptr, &m->col, &m->cotsrc, &m->diagpos, &m->val,
                   &m->dinv, &m->val32, &m->gval, &m->wm, &m->bvh_node, &m->bvh_perm, &m->bvh_keys, &m->bvh_tmp, &m->bvh_sortws,
-                  &m->bvh_f32a, &m->bvh_f32b, &m->bvh_f32c, &m->bh_apply_ws, &m->part, &m->part2, &m->scal, &m->corner,
+                  &m->bvh_f32a, &m->bvh_f32b, &m->bvh_f32c, &m->bh_apply_ws, &m->part, &m->part2, &m->tickets, &m->scal, &m->corner,
                   &m->wv64, &m->wv32, &m->io_in, &m->io_out, &m->adj, &m->erow, &m->tlist, &m->rowsum,
                   &m->kry, &m->gsdev};
     for (Buf* b : all) release(*b);

@@ -740,8 +740,10 @@ struct CoefList {
 // products at a time; the block sums fold across the warp (P-1 additions
 // for P values) and then across warps, always in the same order.
 __global__ void __launch_bounds__(DOT_T)
-k_multidot(PtrList xs, PtrList ys, int nvec, size_t n, double* __restrict__ part) {
+k_multidot(PtrList xs, PtrList ys, int nvec, size_t n, double* __restrict__ part, double* __restrict__ out,
+           unsigned* __restrict__ ticket) {
     __shared__ double wsum[DOT_CH][DOT_T / 32];
+    __shared__ bool last;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     for (int j0 = 0; j0 < nvec; j0 += DOT_CH) {
         double acc[DOT_CH];
@@ -782,15 +784,21 @@ k_multidot(PtrList xs, PtrList ys, int nvec, size_t n, double* __restrict__ part
         }
         __syncthreads();
     }
-}
-
-__global__ void k_multidot_final(const double* __restrict__ part, int nblk, int nvec,
-                                 double* __restrict__ out) {
-    int j = threadIdx.x;
-    if (j >= nvec) return;
-    double s = 0.0;
-    for (int b = 0; b < nblk; ++b) s += part[(size_t)b * nvec + j];
-    out[j] = s;
+    // the last block to finish adds the block sums in block order (the
+    // result does not depend on which block that is) and resets the ticket
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    for (int j = threadIdx.x; j < nvec; j += DOT_T) {
+        double s = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(part + (size_t)b * nvec + j);
+        out[j] = s;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
 }
 
 // out_host[j] = xs[j] . ys[j] (FP64, n elements each), one host sync
@@ -801,6 +809,8 @@ int dot_pairs(tp_mesh* m, const double* const* xs, const double* const* ys, int 
     if (nblk < 1) nblk = 1;
     TP_TRY(ensure(m->part2, sizeof(double) * ((size_t)nblk * DOT_MAXV + DOT_PAIRS_MAX)));
     double* part = m->part2.as<double>();
+    unsigned* tk = nullptr;
+    TP_TRY(mesh_tickets(m, &tk, st));
     double* out = part + (size_t)nblk * DOT_MAXV;
     for (int j0 = 0; j0 < nvec; j0 += DOT_MAXV) {
         const int nc = std::min(DOT_MAXV, nvec - j0);
@@ -809,9 +819,7 @@ int dot_pairs(tp_mesh* m, const double* const* xs, const double* const* ys, int 
             px.p[j] = xs[j0 + j];
             py.p[j] = ys[j0 + j];
         }
-        k_multidot<<<nblk, DOT_T, 0, st>>>(px, py, nc, n, part);
-        TP_LAUNCH_CHECK();
-        k_multidot_final<<<1, DOT_MAXV, 0, st>>>(part, nblk, nc, out + j0);
+        k_multidot<<<nblk, DOT_T, 0, st>>>(px, py, nc, n, part, out + j0, tk + TICKET_DOTS);
         TP_LAUNCH_CHECK();
     }
     TP_CUDA(cudaMemcpyAsync(out_host, out, sizeof(double) * nvec, cudaMemcpyDeviceToHost, st));
@@ -828,6 +836,8 @@ int dot_pairs_dev(tp_mesh* m, const double* const* xs, const double* const* ys, 
     if (nblk < 1) nblk = 1;
     TP_TRY(ensure(m->part2, sizeof(double) * ((size_t)nblk * DOT_MAXV + DOT_PAIRS_MAX)));
     double* part = m->part2.as<double>();
+    unsigned* tk = nullptr;
+    TP_TRY(mesh_tickets(m, &tk, st));
     for (int j0 = 0; j0 < nvec; j0 += DOT_MAXV) {
         const int nc = std::min(DOT_MAXV, nvec - j0);
         PtrList px, py;
@@ -835,9 +845,7 @@ int dot_pairs_dev(tp_mesh* m, const double* const* xs, const double* const* ys, 
             px.p[j] = xs[j0 + j];
             py.p[j] = ys[j0 + j];
         }
-        k_multidot<<<nblk, DOT_T, 0, st>>>(px, py, nc, n, part);
-        TP_LAUNCH_CHECK();
-        k_multidot_final<<<1, DOT_MAXV, 0, st>>>(part, nblk, nc, out_dev + j0);
+        k_multidot<<<nblk, DOT_T, 0, st>>>(px, py, nc, n, part, out_dev + j0, tk + TICKET_DOTS);
         TP_LAUNCH_CHECK();
     }
     return TP_OK;

@@ -783,14 +783,15 @@ __global__ void k_chol_check(const double* __restrict__ part, int nblk, int k, d
 }
 
 // per-component means of the k columns in a fixed order: block (c, s)
-// sums slice s of component c's vertex list (CH_MSPLIT slices), then one
-// block per component adds the slices in order
+// sums slice s of component c's vertex list (CH_MSPLIT slices), then the
+// last block to finish adds every component's slices in order
 constexpr int CH_MSPLIT = 16;
 
 __global__ void __launch_bounds__(256)
-k_comp_partial(const int* __restrict__ comp_ptr, const int* __restrict__ comp_verts, const double* __restrict__ x,
-               int k, double* __restrict__ part) {
+k_comp_mean(const int* __restrict__ comp_ptr, const int* __restrict__ comp_verts, const double* __restrict__ x,
+            int k, double* __restrict__ part, double* __restrict__ mean, unsigned* __restrict__ ticket) {
     __shared__ double sh[256 / 32][CH_KMAX];
+    __shared__ bool last;
     const int c = blockIdx.x, s = blockIdx.y;
     const int v0 = comp_ptr[c], v1 = comp_ptr[c + 1];
     const int len = (v1 - v0 + CH_MSPLIT - 1) / CH_MSPLIT;
@@ -817,15 +818,24 @@ k_comp_partial(const int* __restrict__ comp_ptr, const int* __restrict__ comp_ve
         for (int q = 0; q < 256 / 32; ++q) t += sh[q][threadIdx.x];
         part[((size_t)c * CH_MSPLIT + s) * k + threadIdx.x] = t;
     }
-}
-
-__global__ void k_comp_final(const int* __restrict__ comp_ptr, const double* __restrict__ part, int k,
-                             double* __restrict__ mean) {
-    const int c = blockIdx.x, j = threadIdx.x;
-    if (j >= k) return;
-    double t = 0.0;
-    for (int s = 0; s < CH_MSPLIT; ++s) t += part[((size_t)c * CH_MSPLIT + s) * k + j];
-    mean[(size_t)c * k + j] = t / (double)(comp_ptr[c + 1] - comp_ptr[c]);
+    // the last block to finish adds each component's slices in order and
+    // resets the ticket
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int ncomp = gridDim.x;
+    for (int e = threadIdx.x; e < ncomp * k; e += blockDim.x) {
+        const int cc = e / k, j = e - cc * k;
+        double t = 0.0;
+        for (int q = 0; q < CH_MSPLIT; ++q) t += __ldcg(part + ((size_t)cc * CH_MSPLIT + q) * k + j);
+        mean[(size_t)cc * k + j] = t / (double)(comp_ptr[cc + 1] - comp_ptr[cc]);
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
 }
 
 __global__ void k_comp_sub(const int* __restrict__ comp_of, const double* __restrict__ mean, int nv, int k,
@@ -1043,10 +1053,10 @@ static int comp_project(tp_mesh* m, const double* src, double* dst, int k, cudaS
     CholState* c = m->chol;
     double* mean = c->part.as<double>();                        // ncomp * 9 doubles
     double* slices = mean + (size_t)c->ncomp * CH_KMAX;          // ncomp * CH_MSPLIT * 9 doubles
-    k_comp_partial<<<dim3(c->ncomp, CH_MSPLIT), 256, 0, st>>>(c->comp_ptr.as<int>(), c->comp_verts.as<int>(), src,
-                                                              k, slices);
-    TP_LAUNCH_CHECK();
-    k_comp_final<<<c->ncomp, 32, 0, st>>>(c->comp_ptr.as<int>(), slices, k, mean);
+    unsigned* tk = nullptr;
+    TP_TRY(mesh_tickets(m, &tk, st));
+    k_comp_mean<<<dim3(c->ncomp, CH_MSPLIT), 256, 0, st>>>(c->comp_ptr.as<int>(), c->comp_verts.as<int>(), src, k,
+                                                           slices, mean, tk + TICKET_COMP);
     TP_LAUNCH_CHECK();
     const size_t n = (size_t)m->nv * k;
     k_comp_sub<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c->comp_of.as<int>(), mean, m->nv, k, src, dst);

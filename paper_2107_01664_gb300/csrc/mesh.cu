@@ -132,9 +132,14 @@ int copy_out(void* dst, const void* src, size_t bytes, int ptr_kind, cudaStream_
 
 static constexpr int kSumThreads = 256;
 
-__global__ void k_colsum_partial(const double* __restrict__ x, long n, int k, int rows_per_block,
-                                 double* __restrict__ part) {
+// Block b sums rows [b * rows_per_block, ...) of each column into
+// part[b][c]; the last block to finish (completion ticket) adds the block
+// sums in block order into out[c] (times scale) and puts the ticket back to
+// zero, so the result does not depend on which block finished last.
+__global__ void k_colsum(const double* __restrict__ x, long n, int k, int rows_per_block, double* __restrict__ part,
+                         double scale, double* __restrict__ out, unsigned* __restrict__ ticket) {
     __shared__ double sh[kSumThreads];
+    __shared__ bool last;
     long r0 = (long)blockIdx.x * rows_per_block;
     long r1 = r0 + rows_per_block < n ? r0 + rows_per_block : n;
     for (int c = 0; c < k; ++c) {
@@ -149,14 +154,17 @@ __global__ void k_colsum_partial(const double* __restrict__ x, long n, int k, in
         if (threadIdx.x == 0) part[(long)blockIdx.x * k + c] = sh[0];
         __syncthreads();
     }
-}
-
-__global__ void k_colsum_final(const double* __restrict__ part, int nblk, int k, double scale,
-                               double* __restrict__ out) {
-    __shared__ double sh[kSumThreads];
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int nblk = gridDim.x;
     for (int c = 0; c < k; ++c) {
         double s = 0.0;
-        for (int b = threadIdx.x; b < nblk; b += kSumThreads) s += part[(long)b * k + c];
+        for (int b = threadIdx.x; b < nblk; b += kSumThreads) s += __ldcg(part + (long)b * k + c);
         sh[threadIdx.x] = s;
         __syncthreads();
         for (int w = kSumThreads / 2; w > 0; w >>= 1) {
@@ -166,6 +174,18 @@ __global__ void k_colsum_final(const double* __restrict__ part, int nblk, int k,
         if (threadIdx.x == 0) out[c] = sh[0] * scale;
         __syncthreads();
     }
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// completion tickets of the fused reductions, zero between launches (the
+// last block of a launch puts its ticket back)
+int mesh_tickets(tp_mesh* m, unsigned** out, cudaStream_t st) {
+    if (!m->tickets.ptr) {
+        TP_TRY(ensure(m->tickets, TICKET_COUNT * sizeof(unsigned)));
+        TP_CUDA(cudaMemsetAsync(m->tickets.ptr, 0, TICKET_COUNT * sizeof(unsigned), st));
+    }
+    *out = m->tickets.as<unsigned>();
+    return TP_OK;
 }
 
 // column sums (times `scale`) of x [n][k] into out_dev [k]; uses m->part2
@@ -177,9 +197,9 @@ int colsum(tp_mesh* m, const double* x, long n, int k, double scale, double* out
     int rpb = (int)((n + nblk - 1) / nblk);
     if (rpb < 1) rpb = 1;
     TP_TRY(ensure(m->part2, sizeof(double) * (size_t)nblk * k));
-    k_colsum_partial<<<nblk, kSumThreads, 0, st>>>(x, n, k, rpb, m->part2.as<double>());
-    TP_LAUNCH_CHECK();
-    k_colsum_final<<<1, kSumThreads, 0, st>>>(m->part2.as<double>(), nblk, k, scale, out_dev);
+    unsigned* tk = nullptr;
+    TP_TRY(mesh_tickets(m, &tk, st));
+    k_colsum<<<nblk, kSumThreads, 0, st>>>(x, n, k, rpb, m->part2.as<double>(), scale, out_dev, tk + TICKET_COLSUM);
     TP_LAUNCH_CHECK();
     return TP_OK;
 }

@@ -791,34 +791,42 @@ __global__ void k_face_W(const double* __restrict__ v, int k, int col0, const in
                          int nf, const d4* __restrict__ f64a, const double* __restrict__ fgrad,
                          int op, double* __restrict__ W64, typename V4T<T>::type* __restrict__ Wp,
                          int nw4) {
-    int S = blockIdx.x * blockDim.x + threadIdx.x;
+    // one thread per face and group of (up to) three columns
+    constexpr int CG = KC < 3 ? KC : 3, NCG = (KC + CG - 1) / CG;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int S = t / NCG, g = t - S * NCG;
     if (S >= nf) return;
-    double a = f64a[S].w;
-    double val[3][KC];
+    const int c0 = g * CG;
+    const double a = f64a[S].w;
+    double val[3][CG];
     for (int cr = 0; cr < 3; ++cr) {
-        int vi = faces[3 * S + cr];
-        for (int c = 0; c < KC; ++c) val[cr][c] = (col0 + c < k) ? v[(size_t)vi * k + col0 + c] : 0.0;
+        const int vi = faces[3 * S + cr];
+        for (int c = 0; c < CG; ++c)
+            val[cr][c] = (c0 + c < KC && col0 + c0 + c < k) ? v[(size_t)vi * k + col0 + c0 + c] : 0.0;
     }
-    double w[4 * KC];
-    for (int q = 0; q < 3; ++q)
-        for (int c = 0; c < KC; ++c) {
-            double g = 0.0;
-            for (int cr = 0; cr < 3; ++cr) g += val[cr][c] * fgrad[9 * S + 3 * cr + q];
-            w[q * KC + c] = a * g;
-        }
-    for (int c = 0; c < KC; ++c) w[3 * KC + c] = a * (val[0][c] + val[1][c] + val[2][c]) / 3.0;
-    for (int i = 0; i < 4 * KC; ++i) W64[4 * KC * (size_t)S + i] = w[i];
+    double gr[9];
+    for (int i = 0; i < 9; ++i) gr[i] = fgrad[9 * S + i];
+    double* w64 = W64 + 4 * KC * (size_t)S;
     T* out = reinterpret_cast<T*>(Wp) + (size_t)S * 4 * nw4;
-    int n = 0;
-    if (op == TP_OP_A || op == TP_OP_B) {
-        out[n++] = (T)a;
-        for (int i = 0; i < 3 * KC; ++i) out[n++] = (T)w[i];
+    const bool hi = (op == TP_OP_A || op == TP_OP_B), lo = op != TP_OP_B;
+    const int ou = hi ? 1 + 3 * KC : 0;   // start of the low-order block in out
+    for (int c = 0; c < CG && c0 + c < KC; ++c) {
+        for (int q = 0; q < 3; ++q) {
+            double gq = 0.0;
+            for (int cr = 0; cr < 3; ++cr) gq += val[cr][c] * gr[3 * cr + q];
+            const double wv = a * gq;
+            w64[q * KC + c0 + c] = wv;
+            if (hi) out[1 + q * KC + c0 + c] = (T)wv;
+        }
+        const double wu = a * (val[0][c] + val[1][c] + val[2][c]) * (1.0 / 3.0);
+        w64[3 * KC + c0 + c] = wu;
+        if (lo) out[ou + 1 + c0 + c] = (T)wu;
     }
-    if (op != TP_OP_B) {
-        out[n++] = (T)a;
-        for (int c = 0; c < KC; ++c) out[n++] = (T)w[3 * KC + c];
+    if (g == 0) {
+        if (hi) out[0] = (T)a;
+        if (lo) out[ou] = (T)a;
+        for (int n = ou + (lo ? 1 + KC : 0); n < 4 * nw4; ++n) out[n] = T(0);
     }
-    while (n < 4 * nw4) out[n++] = T(0);
 }
 
 // ---- pairs of accumulators ------------------------------------------------
@@ -1490,7 +1498,7 @@ static int launch_apply_op(tp_mesh* m, const tp_params* p, const double* v, int 
     const V4* fa = (const V4*)(sizeof(T) == 4 ? m->f32a.ptr : m->f64a.ptr);
     const V4* fb = (const V4*)(sizeof(T) == 4 ? m->f32b.ptr : m->f64b.ptr);
     for (int col0 = 0; col0 < k; col0 += KC) {
-        k_face_W<T, KC><<<(nf + 255) / 256, 256, 0, st>>>(v, k, col0, m->faces.as<int>(), nf,
+        k_face_W<T, KC><<<(nf * ((KC + 2) / 3) + 255) / 256, 256, 0, st>>>(v, k, col0, m->faces.as<int>(), nf,
                                                           m->f64a.as<d4>(), m->fgrad.as<double>(), OP,
                                                           m->wv64.as<double>(), m->wv32.as<V4>(), L::NW4);
         TP_LAUNCH_CHECK();
@@ -1538,7 +1546,7 @@ static int launch_apply_wide(tp_mesh* m, const tp_params* p, const double* v, in
     const float4* fa = m->f32a.as<float4>();
     const float4* fb = m->f32b.as<float4>();
     for (int col0 = 0; col0 < k; col0 += 9) {
-        k_face_W<float, 9><<<(nf + 255) / 256, 256, 0, st>>>(v, k, col0, m->faces.as<int>(), nf, m->f64a.as<d4>(),
+        k_face_W<float, 9><<<(nf * 3 + 255) / 256, 256, 0, st>>>(v, k, col0, m->faces.as<int>(), nf, m->f64a.as<d4>(),
                                                              m->fgrad.as<double>(), OP, m->wv64.as<double>(),
                                                              m->wv32.as<float4>(), L::NW4);
         TP_LAUNCH_CHECK();
@@ -2020,7 +2028,7 @@ static int launch_bh_apply_op(tp_mesh* m, const tp_params* p, const double* v, i
     bool lists = false;
     TP_TRY(bh_lists(m, p, st, &Ls, &lists));
     for (int col0 = 0; col0 < k; col0 += KC) {
-        k_face_W<float, KC><<<(nf + 255) / 256, 256, 0, st>>>(v, k, col0, m->faces.as<int>(), nf,
+        k_face_W<float, KC><<<(nf * ((KC + 2) / 3) + 255) / 256, 256, 0, st>>>(v, k, col0, m->faces.as<int>(), nf,
                                                               m->f64a.as<d4>(), m->fgrad.as<double>(), OP,
                                                               m->wv64.as<double>(), m->wv32.as<float4>(), NW4);
         TP_LAUNCH_CHECK();

@@ -227,6 +227,7 @@ struct tp_mesh {
     tp::Buf io_in, io_out, adj, erow, tlist, rowsum;
     tp::Buf kry;        // FGMRES bases V and Z
     tp::Buf gsdev;      // FGMRES: first-pass Gram-Schmidt coefficients on the device
+    tp::Buf tickets;    // completion tickets of the fused reductions (tp::TICKET_*)
     tp::Buf stepv[8];   // vectors of the constrained step
     tp::Buf prec[3];    // preconditioner temporaries
     tp::Buf bhcount;    // device counter of Barnes-Hut interactions
@@ -257,6 +258,10 @@ int copy_in(void* dst, const void* src, size_t bytes, int ptr_kind, cudaStream_t
 int copy_out(void* dst, const void* src, size_t bytes, int ptr_kind, cudaStream_t st);
 int sum_f64(const double* x, int n, double* out_dev, tp_mesh* m, cudaStream_t st);
 int colsum(tp_mesh* m, const double* x, long n, int k, double scale, double* out_dev, cudaStream_t st);
+// completion tickets of the fused (single-launch) reductions: one slot per
+// reduction kind, zero between launches
+enum { TICKET_COLSUM = 0, TICKET_DOTS = 1, TICKET_COMP = 2, TICKET_COUNT = 8 };
+int mesh_tickets(tp_mesh* m, unsigned** out, cudaStream_t st);
 const char* last_error();
 // profiling: wrap a launch (or a group of launches) of kernel class `key`
 // processing `units` of algorithmic work

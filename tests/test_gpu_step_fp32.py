@@ -1,7 +1,7 @@
 """Parity of the benchmarked constrained step: FP32 pair terms (E, dE, A and
-L^{2-s} in the Krylov loop), Cholesky Poisson solves at cg_tol = 1e-6 and
-flexible GMRES at krylov_tol = 1e-5 -- exactly the parameters bench.py times --
-against the FP64 oracle.
+L^{2-s} in the Krylov loop), the preconditioner's Cholesky Poisson solves at
+cg_tol = 1e-4 and flexible GMRES at krylov_tol = 1e-5 -- exactly the
+parameters bench.py times (bench.step_params) -- against the FP64 oracle.
 
 What the step promises (§3.3, Eq. 14; §5.3, Eq. 17-18). The direction x
 solves the saddle problem [A dPhi^T; dPhi 0][x; lambda] = [-dE; 0] (with the
