@@ -47,7 +47,8 @@ def _bench_step_direction(lib, V, F, tau):
     import torch
     A0, V0 = O.total_area(V, F), O.total_volume(V, F)
     p = bench.step_params(lib)
-    p.fixed_tau, p.tau0, p.proj_iters = 1, tau, 0
+    # exactly tau: no line search, no displacement bound on the step, no projection
+    p.fixed_tau, p.tau0, p.tau0_disp, p.proj_iters = 1, tau, 0.0, 0
     c = lib.tp_constraints(flags=lib.TP_CONSTRAINT_AREA | lib.TP_CONSTRAINT_VOLUME, A0=A0, V0=V0)
     with lib.Mesh(dev(V, torch.float64), dev(F, torch.int32)) as m:
         rep = lib.precond_step(m, c, p)
