@@ -880,23 +880,46 @@ int lincomb(double* y, const double* const* xs, const double* coef, int nvec, si
     return TP_OK;
 }
 
-// y = beta y + scale * sum_j coef_dev[j] xs[j], the coefficients read from
-// device memory
-__global__ void k_lincomb_dev(double* __restrict__ y, PtrList xs, const double* __restrict__ coef, double scale,
-                              int nvec, size_t n, double beta) {
-    size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+constexpr int LC_MAXS = 4;
+struct LcSys {
+    double* out[LC_MAXS];
+    const double* y[LC_MAXS];
+    double scale[LC_MAXS];
+};
+
+// blockIdx.y = system; the same operation order as k_lincomb (beta y first,
+// then the vectors in order), then the scale
+__global__ void k_lincomb_sys(PtrList xs, CoefList cf, const double* __restrict__ coef_dev, LcSys L, int nvec,
+                              size_t n, double beta) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int s = blockIdx.y;
     if (i >= n) return;
-    double s = beta == 0.0 ? 0.0 : beta * y[i];
-    for (int j = 0; j < nvec; ++j) s += scale * coef[j] * xs.p[j][i];
-    y[i] = s;
+    double acc = beta == 0.0 ? 0.0 : beta * L.y[s][i];
+    for (int l = 0; l < nvec; ++l) {
+        const double c = coef_dev ? -coef_dev[s * nvec + l] : cf.c[s * nvec + l];
+        acc += c * xs.p[s * nvec + l][i];
+    }
+    L.out[s][i] = L.scale[s] == 1.0 ? acc : L.scale[s] * acc;
 }
 
-int lincomb_dev(double* y, const double* const* xs, const double* coef_dev, double scale, int nvec, size_t n,
-                double beta, cudaStream_t st) {
-    if (nvec < 0 || nvec > DOT_MAXV) return fail(TP_ERR_INVALID_ARG, "lincomb: too many vectors");
+int lincomb_sys(int ns, double* const* out, const double* const* y, const double* const* xs, int nvec,
+                const double* coef_dev, const double* coef_host, const double* scale, double beta, size_t n,
+                cudaStream_t st) {
+    if (ns < 1 || ns > LC_MAXS || nvec < 0 || ns * nvec > DOT_MAXV)
+        return fail(TP_ERR_INVALID_ARG, "lincomb_sys: too many vectors");
     PtrList pl;
-    for (int j = 0; j < nvec; ++j) pl.p[j] = xs[j];
-    k_lincomb_dev<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(y, pl, coef_dev, scale, nvec, n, beta);
+    CoefList cl;
+    LcSys L;
+    for (int j = 0; j < ns * nvec; ++j) {
+        pl.p[j] = xs[j];
+        cl.c[j] = coef_host ? coef_host[j] : 0.0;
+    }
+    for (int s = 0; s < ns; ++s) {
+        L.out[s] = out[s];
+        L.y[s] = y[s];
+        L.scale[s] = scale ? scale[s] : 1.0;
+    }
+    k_lincomb_sys<<<dim3((unsigned)((n + 255) / 256), ns), 256, 0, st>>>(pl, cl, coef_dev, L, nvec, n, beta);
     TP_LAUNCH_CHECK();
     return TP_OK;
 }

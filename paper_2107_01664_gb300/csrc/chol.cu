@@ -654,7 +654,9 @@ k_chol_sweep(SweepArgs A) {
     }
     __syncthreads();
     if (!s_last) return;
-    // the last block: convergence test (same rule as k_chol_check), reset
+    // the last block: convergence test (every column at |r|^2 <= tol^2 |b|^2;
+    // a column that has not lost three quarters of |r|^2 in the sweep means
+    // the FP32 factor is too coarse: stalled), reset
     __threadfence();
     __shared__ double s_rr[K];
     {
@@ -695,31 +697,31 @@ k_chol_sweep(SweepArgs A) {
     }
 }
 
-// r = bp - C x (FP64), per-block partial sums of r.r per column
+// The start of a solve in one launch: bp = b minus its per-component means
+// (mean, from k_comp_mean), x = 0, r = bp, per-block partials of |bp|^2;
+// the last block to finish (completion ticket) adds the partials in block
+// order, records |b|^2 per column (done when every column is zero), then
+// puts the ticket back.
 template <int K>
 __global__ void __launch_bounds__(CHR_T)
-k_chol_resid(const int* __restrict__ rowptr, const int* __restrict__ col, const double* __restrict__ val, int nv,
-             const double* __restrict__ bp, const double* __restrict__ x, double* __restrict__ r,
-             double* __restrict__ part, const CholCtl* __restrict__ ctl) {
-    if (ctl->done) return;
+k_chol_start(const double* __restrict__ b, const double* __restrict__ mean, const int* __restrict__ comp_of, int nv,
+             double* __restrict__ bp, double* __restrict__ x, double* __restrict__ r, double* __restrict__ part,
+             unsigned* __restrict__ ticket, CholCtl* __restrict__ ctl) {
     __shared__ double sh[CHR_T / 32][K];
+    __shared__ bool last;
     double acc[K];
 #pragma unroll
     for (int c = 0; c < K; ++c) acc[c] = 0.0;
     for (int v = blockIdx.x * CHR_T + threadIdx.x; v < nv; v += gridDim.x * CHR_T) {
-        double s[K];
-#pragma unroll
-        for (int c = 0; c < K; ++c) s[c] = bp[(size_t)v * K + c];
-        for (int e = rowptr[v]; e < rowptr[v + 1]; ++e) {
-            const double w = val[e];
-            const double* xr = x + (size_t)col[e] * K;
-#pragma unroll
-            for (int c = 0; c < K; ++c) s[c] -= w * xr[c];
-        }
+        const double* mc = mean + (size_t)comp_of[v] * K;
 #pragma unroll
         for (int c = 0; c < K; ++c) {
-            r[(size_t)v * K + c] = s[c];
-            acc[c] += s[c] * s[c];
+            const size_t o = (size_t)v * K + c;
+            const double s = b[o] - mc[c];
+            bp[o] = s;
+            x[o] = 0.0;
+            r[o] = s;
+            acc[c] += s * s;
         }
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -735,61 +737,45 @@ k_chol_resid(const int* __restrict__ rowptr, const int* __restrict__ col, const 
         for (int i = 0; i < CHR_T / 32; ++i) s += sh[i][threadIdx.x];
         part[(size_t)blockIdx.x * K + threadIdx.x] = s;
     }
-}
-
-// mode 0: |b|^2 from the partials; mode 1: convergence test after a sweep
-__global__ void k_chol_check(const double* __restrict__ part, int nblk, int k, double tol2, int cap, int mode,
-                             CholCtl* __restrict__ ctl) {
-    if (mode == 1 && ctl->done) return;
-    __shared__ double s_rr[CH_KMAX];
-    const int lane = threadIdx.x & 31, c = threadIdx.x >> 5;   // one warp per column
-    if (c < k) {
-        double s = 0.0;
-        for (int b = lane; b < nblk; b += 32) s += part[(size_t)b * k + c];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) s_rr[c] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    if (mode == 0) {
+    if (!last) return;
+    __threadfence();
+    __shared__ double s_bb[K];
+    for (int c = w; c < K; c += CHR_T / 32) {   // one warp per column
+        double t = 0.0;
+        for (unsigned q = lane; q < gridDim.x; q += 32) t += __ldcg(part + (size_t)q * K + c);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) s_bb[c] = t;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
         int all = 1;
-        for (int j = 0; j < k; ++j) {
-            ctl->bb[j] = s_rr[j];
-            ctl->rr[j] = s_rr[j];
-            all &= s_rr[j] == 0.0;
+        for (int j = 0; j < K; ++j) {
+            ctl->bb[j] = s_bb[j];
+            ctl->rr[j] = s_bb[j];
+            all &= s_bb[j] == 0.0;
         }
         ctl->done = all;
         ctl->iters = 0;
-        return;
-    }
-    int conv = 1, worse = 0;
-    for (int j = 0; j < k; ++j) {
-        const double rr = s_rr[j];
-        if (!(rr <= tol2 * ctl->bb[j])) {
-            conv = 0;
-            // a sweep that does not halve the residual norm means the FP32
-            // factor is too coarse for this matrix
-            if (!(rr <= 0.25 * ctl->rr[j])) worse = 1;
-        }
-        ctl->rr[j] = rr;
-    }
-    ctl->iters += 1;
-    if (conv) {
-        ctl->done = 1;
-    } else if (worse || ctl->bad_pivot || ctl->iters >= cap) {
-        ctl->done = 1;
-        ctl->stalled = 1;
+        *ticket = 0u;
     }
 }
 
 // per-component means of the k columns in a fixed order: block (c, s)
 // sums slice s of component c's vertex list (CH_MSPLIT slices), then the
-// last block to finish adds every component's slices in order
+// last block to finish adds every component's slices in order (and, given
+// dflags, records the state of the deferred solve that produced x)
 constexpr int CH_MSPLIT = 16;
 
 __global__ void __launch_bounds__(256)
 k_comp_mean(const int* __restrict__ comp_ptr, const int* __restrict__ comp_verts, const double* __restrict__ x,
-            int k, double* __restrict__ part, double* __restrict__ mean, unsigned* __restrict__ ticket) {
+            int k, double* __restrict__ part, double* __restrict__ mean, unsigned* __restrict__ ticket,
+            const CholCtl* __restrict__ ctl, int* __restrict__ dflags) {
     __shared__ double sh[256 / 32][CH_KMAX];
     __shared__ bool last;
     const int c = blockIdx.x, s = blockIdx.y;
@@ -835,7 +821,15 @@ k_comp_mean(const int* __restrict__ comp_ptr, const int* __restrict__ comp_verts
         for (int q = 0; q < CH_MSPLIT; ++q) t += __ldcg(part + ((size_t)cc * CH_MSPLIT + q) * k + j);
         mean[(size_t)cc * k + j] = t / (double)(comp_ptr[cc + 1] - comp_ptr[cc]);
     }
-    if (threadIdx.x == 0) *ticket = 0u;
+    if (threadIdx.x == 0) {
+        *ticket = 0u;
+        if (dflags) {
+            // after the sweeps of a deferred solve: its wait error, and whether
+            // it stopped short of the tolerance
+            if (ctl->err) dflags[0] = 1;
+            if (!ctl->done || ctl->stalled) dflags[1] = 1;
+        }
+    }
 }
 
 __global__ void k_comp_sub(const int* __restrict__ comp_of, const double* __restrict__ mean, int nv, int k,
@@ -869,15 +863,6 @@ void chol_invalidate(tp_mesh* m) {
     if (m->chol) {
         m->chol->factored = false;
         m->chol->pivot_known = false;
-    }
-}
-
-// after the sweeps of a deferred solve: accumulate its wait error and
-// whether it stopped short of the tolerance
-__global__ void k_chol_defer_flags(const CholCtl* __restrict__ ctl, int* __restrict__ flags) {
-    if (threadIdx.x == 0) {
-        if (ctl->err) flags[0] = 1;
-        if (!ctl->done || ctl->stalled) flags[1] = 1;
     }
 }
 
@@ -1049,23 +1034,30 @@ static int chol_factor(tp_mesh* m, cudaStream_t st) {
 }
 
 // dst = src minus its per-component mean (k columns)
-static int comp_project(tp_mesh* m, const double* src, double* dst, int k, cudaStream_t st) {
+// per-component means of src into c->part (and the deferred flags, see k_comp_mean)
+static int comp_means(tp_mesh* m, const double* src, int k, int* dflags, cudaStream_t st) {
     CholState* c = m->chol;
     double* mean = c->part.as<double>();                        // ncomp * 9 doubles
     double* slices = mean + (size_t)c->ncomp * CH_KMAX;          // ncomp * CH_MSPLIT * 9 doubles
     unsigned* tk = nullptr;
     TP_TRY(mesh_tickets(m, &tk, st));
     k_comp_mean<<<dim3(c->ncomp, CH_MSPLIT), 256, 0, st>>>(c->comp_ptr.as<int>(), c->comp_verts.as<int>(), src, k,
-                                                           slices, mean, tk + TICKET_COMP);
+                                                           slices, mean, tk + TICKET_COMP, c->ctl.as<CholCtl>(),
+                                                           dflags);
     TP_LAUNCH_CHECK();
+    return TP_OK;
+}
+
+static int comp_project(tp_mesh* m, const double* src, double* dst, int k, cudaStream_t st, int* dflags = nullptr) {
+    CholState* c = m->chol;
+    double* mean = c->part.as<double>();
+    TP_TRY(comp_means(m, src, k, dflags, st));
     const size_t n = (size_t)m->nv * k;
     k_comp_sub<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c->comp_of.as<int>(), mean, m->nv, k, src, dst);
     TP_LAUNCH_CHECK();
     return TP_OK;
 }
 
-// kernels of `nsweep` refinement sweeps on stream st (recorded into a graph
-// by the caller); *nk counts them
 // `nsweep` refinement sweeps on stream st (recorded into a graph by the
 // caller); *nk counts the kernels
 template <int K>
@@ -1183,18 +1175,20 @@ static int chol_run(tp_mesh* m, const tp_params* p, const double* b, double* z_o
     const size_t head = (size_t)c->ncomp * CH_KMAX * (1 + CH_MSPLIT);   // means and their slices
     TP_TRY(ensure(c->part, sizeof(double) * (head + nparts * CH_KMAX) + 64));
     double* partr = c->part.as<double>() + head;
-    TP_TRY(comp_project(m, b, c->bp.as<double>(), K, st));
-    TP_CUDA(cudaMemsetAsync(c->x.ptr, 0, sizeof(double) * n, st));
     // clear done .. arrive; bad_pivot (from the factorisation) and the epoch stay
     TP_CUDA(cudaMemsetAsync(c->ctl.ptr, 0, offsetof(CholCtl, bad_pivot), st));
-    k_chol_resid<K><<<rgrid, CHR_T, 0, st>>>(m->rowptr.as<int>(), m->col.as<int>(), m->val.as<double>(), nv,
-                                            c->bp.as<double>(), c->x.as<double>(), c->r.as<double>(), partr,
-                                            c->ctl.as<CholCtl>());
-    TP_LAUNCH_CHECK();
+    // b minus its component means, x = 0, r = b, |b|^2 (two launches)
+    TP_TRY(comp_means(m, b, K, nullptr, st));
+    {
+        unsigned* tk = nullptr;
+        TP_TRY(mesh_tickets(m, &tk, st));
+        k_chol_start<K><<<rgrid, CHR_T, 0, st>>>(b, c->part.as<double>(), c->comp_of.as<int>(), nv, c->bp.as<double>(),
+                                                c->x.as<double>(), c->r.as<double>(), partr, tk + TICKET_CHOL,
+                                                c->ctl.as<CholCtl>());
+        TP_LAUNCH_CHECK();
+    }
     const double tol2 = p->cg_tol * p->cg_tol;
     const int cap = std::max(1, std::min(p->cg_max, 40));
-    k_chol_check<<<1, 32 * CH_KMAX, 0, st>>>(partr, rgrid, K, tol2, cap, 0, c->ctl.as<CholCtl>());
-    TP_LAUNCH_CHECK();
     CholState::SweepGraph* g = nullptr;
     TP_TRY(sweep_graph<K>(m, rgrid, partr, tol2, cap, &g));
     if (deferred) {
@@ -1211,10 +1205,8 @@ static int chol_run(tp_mesh* m, const tp_params* p, const double* b, double* z_o
             TP_CUDA(cudaGraphLaunch(g->exec, st));
             count_launches(g->kernels);
         }
-        k_chol_defer_flags<<<1, 32, 0, st>>>(c->ctl.as<CholCtl>(), c->dflags.as<int>());
-        TP_LAUNCH_CHECK();
         if (iters) *iters = graphs * CH_SWEEPS_PER_GRAPH;
-        TP_TRY(comp_project(m, c->x.as<double>(), z_out, K, st));
+        TP_TRY(comp_project(m, c->x.as<double>(), z_out, K, st, c->dflags.as<int>()));
         return TP_OK;
     }
     CholCtl h{};

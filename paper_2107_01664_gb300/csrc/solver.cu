@@ -252,45 +252,68 @@ static int fgmres_multi(tp_mesh* m, const tp_params* p, int ns, const double* co
             TP_TRY(ensure(m->gsdev, sizeof(double) * 1024));
             double* h1dev = m->gsdev.as<double>();
             TP_TRY(dot_pairs_dev(m, dx.data(), dy.data(), (int)dx.size(), n, h1dev, st));
-            for (size_t ii = 0; ii < cyc.size(); ++ii) {
-                GmSys& q = S[cyc[ii]];
-                std::vector<const double*> basis(j + 1);
-                for (int l = 0; l <= j; ++l) basis[l] = Vj(q, l);
-                TP_TRY(lincomb_dev(q.w, basis.data(), h1dev + ii * (j + 1), -1.0, j + 1, n, 1.0, st));
+            std::vector<double*> ws;
+            std::vector<const double*> wc, basis_all;
+            for (int i : cyc) {
+                ws.push_back(S[i].w);
+                wc.push_back(S[i].w);
+                for (int l = 0; l <= j; ++l) basis_all.push_back(Vj(S[i], l));
             }
+            // w -= V h1 for every system of the cycle, one launch
+            TP_TRY(lincomb_sys(na, ws.data(), wc.data(), basis_all.data(), j + 1, h1dev, nullptr, nullptr, 1.0, n,
+                               st));
             TP_CUDA(cudaMemcpyAsync(h1.data(), h1dev, sizeof(double) * h1.size(), cudaMemcpyDeviceToHost, st));
             for (int i : cyc) {
                 dx.push_back(S[i].w);
                 dy.push_back(S[i].w);
             }
             TP_TRY(dot_pairs(m, dx.data(), dy.data(), (int)dx.size(), n, h2.data(), st));
+            // pass 2 and the normalisation V_{j+1} = (w - V h2) / |w - V h2| of every system in
+            // one launch, |w''|^2 from the dots; a system near breakdown measures |w''| directly
+            std::vector<double> hn_of(na, 0.0), neg_all((size_t)na * (j + 1)), sc_all(na, 1.0);
+            std::vector<char> near_bd(na, 0);
+            bool direct = false;
+            for (int ii = 0; ii < na; ++ii) {
+                const double* hh = h2.data() + ii * (j + 1);
+                double hh2 = 0.0;
+                for (int l = 0; l <= j; ++l) {
+                    neg_all[(size_t)ii * (j + 1) + l] = -hh[l];
+                    hh2 += hh[l] * hh[l];
+                }
+                const double ww = h2[(size_t)na * (j + 1) + ii];
+                hn_of[ii] = ww - hh2;
+                if (!(hn_of[ii] > 1e-6 * ww)) near_bd[ii] = 1, direct = true;
+            }
+            std::vector<double*> vnext;
+            for (int i : cyc) vnext.push_back(Vj(S[i], j + 1));
+            if (direct) {
+                // w'' stored first, then |w''|^2 measured for the systems near breakdown
+                TP_TRY(lincomb_sys(na, ws.data(), wc.data(), basis_all.data(), j + 1, nullptr, neg_all.data(),
+                                   nullptr, 1.0, n, st));
+                for (int ii = 0; ii < na; ++ii)
+                    if (near_bd[ii]) {
+                        const double* xs[1] = {S[cyc[ii]].w};
+                        TP_TRY(dots(m, xs, S[cyc[ii]].w, 1, n, &hn_of[ii], st));
+                    }
+            }
+            for (int ii = 0; ii < na; ++ii) {
+                const double hn = std::sqrt(std::max(0.0, hn_of[ii]));
+                hn_of[ii] = hn;
+                sc_all[ii] = hn > 0.0 ? 1.0 / hn : 0.0;
+            }
+            if (direct)
+                TP_TRY(lincomb_sys(na, vnext.data(), wc.data(), basis_all.data(), 0, nullptr, nullptr, sc_all.data(),
+                                   1.0, n, st));
+            else
+                TP_TRY(lincomb_sys(na, vnext.data(), wc.data(), basis_all.data(), j + 1, nullptr, neg_all.data(),
+                                   sc_all.data(), 1.0, n, st));
             for (size_t ii = 0; ii < cyc.size(); ++ii) {
                 const int i = cyc[ii];
                 GmSys& q = S[i];
                 const double* hh = h2.data() + ii * (j + 1);
-                std::vector<const double*> basis(j + 1);
-                std::vector<double> neg(j + 1);
-                double hh2 = 0.0;
-                for (int l = 0; l <= j; ++l) {
-                    basis[l] = Vj(q, l);
-                    neg[l] = -hh[l];
-                    hh2 += hh[l] * hh[l];
-                }
-                TP_TRY(lincomb(q.w, basis.data(), neg.data(), j + 1, n, 1.0, st));
                 for (int l = 0; l <= j; ++l) q.H[l * mr + j] = h1[ii * (j + 1) + l] + hh[l];
-                const double ww = h2[(size_t)cyc.size() * (j + 1) + ii];
-                double hn2 = ww - hh2;
-                if (!(hn2 > 1e-6 * ww)) {   // near breakdown: measure |w''| directly
-                    const double* xs[1] = {q.w};
-                    TP_TRY(dots(m, xs, q.w, 1, n, &hn2, st));
-                }
-                double hn = std::sqrt(std::max(0.0, hn2));
+                const double hn = hn_of[ii];
                 q.H[(j + 1) * mr + j] = hn;
-                if (hn > 0.0) {
-                    double sc = 1.0 / hn;
-                    const double* xs[1] = {q.w};
-                    TP_TRY(lincomb(Vj(q, j + 1), xs, &sc, 1, n, 0.0, st));
-                }
                 for (int l = 0; l < j; ++l) {  // Givens rotations
                     double a = q.H[l * mr + j], c = q.H[(l + 1) * mr + j];
                     q.H[l * mr + j] = q.cs[l] * a + q.sn[l] * c;

@@ -260,7 +260,7 @@ int sum_f64(const double* x, int n, double* out_dev, tp_mesh* m, cudaStream_t st
 int colsum(tp_mesh* m, const double* x, long n, int k, double scale, double* out_dev, cudaStream_t st);
 // completion tickets of the fused (single-launch) reductions: one slot per
 // reduction kind, zero between launches
-enum { TICKET_COLSUM = 0, TICKET_DOTS = 1, TICKET_COMP = 2, TICKET_COUNT = 8 };
+enum { TICKET_COLSUM = 0, TICKET_DOTS = 1, TICKET_COMP = 2, TICKET_CHOL = 3, TICKET_COUNT = 8 };
 int mesh_tickets(tp_mesh* m, unsigned** out, cudaStream_t st);
 const char* last_error();
 // profiling: wrap a launch (or a group of launches) of kernel class `key`
@@ -342,14 +342,19 @@ int dots(tp_mesh* m, const double* const* xs, const double* y, int nvec, size_t 
 int dot_pairs(tp_mesh* m, const double* const* xs, const double* const* ys, int nvec, size_t n,
               double* out_host, cudaStream_t st);   // out_host[j] = xs[j] . ys[j], nvec <= 512
 int axpy(double* y, const double* x, double a, size_t n, cudaStream_t st);
-// device-resident variants (no host synchronisation): dot products into
-// device memory, and a linear combination with coefficients read from it
+// device-resident variant (no host synchronisation): dot products into
+// device memory (lincomb_sys reads them as coefficients)
 int dot_pairs_dev(tp_mesh* m, const double* const* xs, const double* const* ys, int nvec, size_t n,
                   double* out_dev, cudaStream_t st);
-int lincomb_dev(double* y, const double* const* xs, const double* coef_dev, double scale, int nvec, size_t n,
-                double beta, cudaStream_t st);
 int lincomb(double* y, const double* const* xs, const double* coef_host, int nvec, size_t n,
             double beta, cudaStream_t st);
+// one launch for ns <= 4 systems with nvec vectors each: out[s] = scale[s] *
+// (beta y[s] + sum_l c[s * nvec + l] xs[s * nvec + l]), with c = coef_host, or
+// c = -coef_dev read from device memory (the Gram-Schmidt update w -= V h);
+// ns * nvec <= 128
+int lincomb_sys(int ns, double* const* out, const double* const* y, const double* const* xs, int nvec,
+                const double* coef_dev, const double* coef_host, const double* scale, double beta, size_t n,
+                cudaStream_t st);
 
 // -------- obstacle.cu ------------------------------------------------------
 int obstacle_attach(tp_mesh* m, tp_mesh* obstacle, double weight, cudaStream_t st);  // m owns it
