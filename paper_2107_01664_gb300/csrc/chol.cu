@@ -1192,20 +1192,30 @@ static int chol_run(tp_mesh* m, const tp_params* p, const double* b, double* z_o
     CholState::SweepGraph* g = nullptr;
     TP_TRY(sweep_graph<K>(m, rgrid, partr, tol2, cap, &g));
     if (deferred) {
-        // no host read: the sweeps that cg_tol needs at about three digits
-        // per sweep, then the flags; the caller reads them once per step
+        // no host read: the sweeps that cg_tol needs, then the flags; the
+        // caller reads them once per step. Measured digits of |r|/|b| (9
+        // columns): at least four after the first sweep (torus_20k,
+        // linked_tori_50k, icosphere_l3), about three more per sweep after it.
         if (!c->dflags.ptr) {
             TP_TRY(ensure(c->dflags, 4 * sizeof(int)));
             TP_CUDA(cudaMemsetAsync(c->dflags.ptr, 0, 4 * sizeof(int), st));   // fresh memory holds garbage
         }
-        const int sweeps = std::min(cap, std::max(1, (int)std::ceil(-std::log10(std::max(p->cg_tol, 1e-300)) / 3.0)));
-        const int graphs = (sweeps + CH_SWEEPS_PER_GRAPH - 1) / CH_SWEEPS_PER_GRAPH;
+        const double digits = -std::log10(std::max(p->cg_tol, 1e-300));
+        const int sweeps = std::min(cap, 1 + std::max(0, (int)std::ceil((digits - 4.0) / 3.0)));
+        const int graphs = sweeps / CH_SWEEPS_PER_GRAPH;
         for (int gi = 0; gi < graphs; ++gi) {
             ProfScope ps(m, PK_CHOL_SOLVE, c->solve_bytes * CH_SWEEPS_PER_GRAPH, st);
             TP_CUDA(cudaGraphLaunch(g->exec, st));
             count_launches(g->kernels);
         }
-        if (iters) *iters = graphs * CH_SWEEPS_PER_GRAPH;
+        if (sweeps % CH_SWEEPS_PER_GRAPH) {
+            // the odd sweep, launched directly
+            ProfScope ps(m, PK_CHOL_SOLVE, c->solve_bytes, st);
+            int nk = 0;
+            TP_TRY(chol_sweep_kernels<K>(m, sweeps % CH_SWEEPS_PER_GRAPH, rgrid, partr, tol2, cap, st, &nk));
+            count_launches(nk);
+        }
+        if (iters) *iters = sweeps;
         TP_TRY(comp_project(m, c->x.as<double>(), z_out, K, st, c->dflags.as<int>()));
         return TP_OK;
     }

@@ -154,6 +154,39 @@ static int apply_A_packed(tp_mesh* m, const tp_params* p, const double* v, int k
     return project_space(m, y, k, st);
 }
 
+// dst_s[v][c] = y[v][3 s + c] - mean[3 s + c] (the mean-zero projection of a
+// one-component mesh fused with the unpacking of the lockstep systems)
+__global__ void k_sub_mean_unpack(const double* __restrict__ y, const double* __restrict__ mean, int ns, int nv,
+                                  SysPtrs dst) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int w = 3 * ns;
+    if (i >= (size_t)nv * w) return;
+    const size_t v = i / w;
+    const int r = (int)(i % w), sI = r / 3, c = r % 3;
+    dst.p[sI][v * 3 + c] = y[i] - mean[r];
+}
+
+// apply_A_packed, its result unpacked into the systems' vectors (y is scratch)
+static int apply_A_unpacked(tp_mesh* m, const tp_params* p, const double* v, int ns, double* y,
+                            const std::vector<double*>& dst, cudaStream_t st) {
+    const int k = 3 * ns;
+    if (m->npins != 0 || m->ncomp != 1) {
+        TP_TRY(apply_A_packed(m, p, v, k, y, st));
+        return unpack(y, m->nv, dst, st);
+    }
+    TP_TRY(apply_op(m, p, TP_OP_A, v, k, y, st));
+    if (m->willmore_w > 0.0) TP_TRY(willmore_operator_add(m, v, k, y, m->willmore_w, st));
+    TP_TRY(ensure(m->tmpv[6], sizeof(double) * 64));
+    double* mean = m->tmpv[6].as<double>();
+    TP_TRY(colsum(m, y, m->nv, k, 1.0 / m->nv, mean, st));
+    SysPtrs sp{};
+    for (size_t i = 0; i < dst.size(); ++i) sp.p[i] = dst[i];
+    const size_t n = (size_t)m->nv * k;
+    k_sub_mean_unpack<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(y, mean, ns, m->nv, sp);
+    TP_LAUNCH_CHECK();
+    return TP_OK;
+}
+
 struct GmSys {
     double* b;
     double* x;
@@ -233,8 +266,7 @@ static int fgmres_multi(tp_mesh* m, const tp_params* p, int ns, const double* co
             TP_TRY(pack(vin, nv, P0, st));
             TP_TRY(precond_apply_dev(m, p, P0, 3 * na, P1, st, &ks->cg_iters, false));
             TP_TRY(unpack(P1, nv, zout, st));
-            TP_TRY(apply_A_packed(m, p, P1, 3 * na, P2, st));
-            TP_TRY(unpack(P2, nv, wout, st));
+            TP_TRY(apply_A_unpacked(m, p, P1, na, P2, wout, st));
             ++total;
             std::vector<int> still;
             // classical Gram-Schmidt, twice, for all systems of the cycle at
@@ -364,8 +396,7 @@ static int fgmres_multi(tp_mesh* m, const tp_params* p, int ns, const double* co
             rout.push_back(S[i].w);
         }
         TP_TRY(pack(xin, nv, P0, st));
-        TP_TRY(apply_A_packed(m, p, P0, 3 * (int)rest.size(), P2, st));
-        TP_TRY(unpack(P2, nv, rout, st));
+        TP_TRY(apply_A_unpacked(m, p, P0, (int)rest.size(), P2, rout, st));
         for (int i : rest) {
             GmSys& q = S[i];
             const double* xs[2] = {q.b, q.w};
