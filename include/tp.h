@@ -105,6 +105,10 @@ typedef struct tp_params {
     double tau0_disp;     /* > 0: the line search starts from min(tau0, tau0_disp h / max_v |x_v|),
                              h = sqrt(total area / nf), so that the first trial moves no vertex by
                              more than tau0_disp face sizes; 0 (default) = start from tau0 */
+    int    tensor_cores;  /* direct FP32 A applies on 4-9 columns: 1 = the accumulation of the kernel
+                             values times the source vectors on tcgen05 tensor cores (split TF32
+                             products, FP32 accumulators drained into compensated sums every 128
+                             sources); 0 (default) = CUDA cores (packed FP32) */
 } tp_params;
 
 typedef struct tp_constraints {

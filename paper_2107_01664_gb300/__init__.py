@@ -59,6 +59,7 @@ class tp_params(ctypes.Structure):
         ("armijo_shrink", ctypes.c_double), ("tau0", ctypes.c_double), ("ls_max", ctypes.c_int),
         ("fixed_tau", ctypes.c_int), ("proj_iters", ctypes.c_int), ("poisson_solver", ctypes.c_int),
         ("bvh_refit", ctypes.c_int), ("prec_self_weight", ctypes.c_double), ("tau0_disp", ctypes.c_double),
+        ("tensor_cores", ctypes.c_int),
     ]
 
 

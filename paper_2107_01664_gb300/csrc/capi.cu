@@ -49,6 +49,7 @@ int check_params(const tp_params* p) {
         return fail(TP_ERR_INVALID_ARG, "prec_self_weight must be finite and >= 0");
     if (!(p->tau0_disp >= 0.0) || !std::isfinite(p->tau0_disp))
         return fail(TP_ERR_INVALID_ARG, "tau0_disp must be finite and >= 0");
+    if (p->tensor_cores != 0 && p->tensor_cores != 1) return fail(TP_ERR_INVALID_ARG, "tensor_cores must be 0 or 1");
     return TP_OK;
 }
 
@@ -103,6 +104,7 @@ void tp_params_default(tp_params* p) {
     p->bvh_refit = 0;
     p->prec_self_weight = 24.0;
     p->tau0_disp = 0.0;
+    p->tensor_cores = 0;
 }
 
 const char* tp_last_error(void) { return tp::last_error(); }
@@ -264,7 +266,7 @@ int tp_mesh_destroy(tp_mesh* m) {
                   &m->f32c, &m->tilebox,
                   &m->f64a, &m->f64b, &m->fgrad, &m->rowptr, &m->col, &m->cotsrc, &m->diagpos, &m->val,
                   &m->dinv, &m->val32, &m->gval, &m->wm, &m->bvh_node, &m->bvh_perm, &m->bvh_keys, &m->bvh_tmp, &m->bvh_sortws,
-                  &m->bvh_f32a, &m->bvh_f32b, &m->bvh_f32c, &m->bh_apply_ws, &m->part, &m->part2, &m->tickets, &m->scal, &m->corner,
+                  &m->bvh_f32a, &m->bvh_f32b, &m->bvh_f32c, &m->bh_apply_ws, &m->part, &m->part2, &m->tickets, &m->tcbuf, &m->tcerr, &m->scal, &m->corner,
                   &m->wv64, &m->wv32, &m->io_in, &m->io_out, &m->adj, &m->erow, &m->tlist, &m->rowsum,
                   &m->kry, &m->gsdev};
     for (Buf* b : all) release(*b);

@@ -1525,6 +1525,379 @@ static int launch_apply_op(tp_mesh* m, const tp_params* p, const double* v, int 
 }
 
 // FP32, 9 columns: the two-targets-per-thread kernel (k_apply_wide)
+// ---------------------------------------------------------------------------
+// 9-column A apply with the accumulation on tcgen05 tensor cores
+// ---------------------------------------------------------------------------
+//
+// For a block of 128 targets and a tile of 16 sources the CUDA cores form the
+// kernel values h_B(S,T) and h_0(S,T) of the A operator (as apply_term); the
+// tensor cores then add H_B X_high and H_0 X_low into accumulators in tensor
+// memory (X_high = [a, W_V] (28 columns, padded to N = 32), X_low = [a, W_U]
+// (10 columns, padded to N = 16)). FP32 accuracy from TF32 operands by the
+// split product H X = Hh Xh + Hh Xl + Hl Xh (hi = the value rounded to TF32,
+// lo = the rest; the dropped lo x lo term is 2^-22 of the product). Every
+// 128 sources (8 tiles) the FP32 accumulators are read back and added into
+// Kahan pairs, as the CUDA-core kernel does per 128-source chunk; two sets of
+// accumulators alternate so that the read-back overlaps the next chunk's
+// products. Operands are K-major in shared memory without swizzle: core
+// matrices of 8 rows x 16 bytes (4 TF32 along K), adjacent along K at 128
+// bytes (leading byte offset), row groups at 512 bytes (stride byte offset).
+// Source tiles (X split into hi and lo in that layout, plus the sources'
+// barycenter hi, lo and normal) are packed once per apply by k_tc_pack and
+// copied into a ring of three shared buffers with cp.async.bulk, one tile
+// ahead. One thread issues the MMAs; mbarriers order the copies, the MMAs and
+// the reuse of the buffers; every wait is bounded by one second (an exhausted
+// wait stops all further work of the block, sets *err and writes NaN
+// partials).
+
+constexpr int TC_KT = 16;                      // sources per tile (two K = 8 steps)
+constexpr int TC_T = 256;                      // threads: target tid & 127, source half tid >> 7
+constexpr int TC_TILE_BYTES = 6912;            // packed source tile (see k_tc_pack)
+constexpr int TC_XH = 0, TC_XHL = 2048, TC_XL = 4096, TC_XLL = 5120, TC_SHI = 6144, TC_SLO = 6400, TC_SN = 6656;
+constexpr int TC_HMAT = 8192;                  // one 128 x 16 FP32 operand
+constexpr int TC_HBUF = 4 * TC_HMAT;           // H_B hi, H_B lo, H_0 hi, H_0 lo
+constexpr int TC_NX = 3;                       // source tile buffers
+constexpr size_t TC_SMEM = 2 * (size_t)TC_HBUF + TC_NX * (size_t)TC_TILE_BYTES;
+constexpr int TC_TMEM_COLS = 128;              // two accumulator sets of 64 columns (32 high + 16 low used)
+constexpr unsigned long long TC_WAIT_NS = 1000000000ull;   // bound of each mbarrier wait (1 s)
+
+// byte offset of element (row, k) of a [rows][16] K-major operand
+__device__ __forceinline__ int tc_cm(int row, int k) {
+    return (((row >> 3) * 4 + (k >> 2)) << 7) + ((row & 7) << 4) + ((k & 3) << 2);
+}
+__device__ __forceinline__ float tc_tf32(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+__device__ __forceinline__ unsigned tc_smem(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long tc_desc(unsigned addr) {
+    // start >> 4, leading byte offset 128 >> 4, stride byte offset 512 >> 4, version 1, no swizzle
+    return (unsigned long long)((addr >> 4) & 0x3fffu) | (8ull << 16) | (32ull << 32) | (1ull << 46);
+}
+__device__ __forceinline__ void tc_mma(unsigned d, unsigned long long a, unsigned long long b, unsigned idesc,
+                                       int acc) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
+                 ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+// bounded wait for the completion of the mbarrier phase with the given parity;
+// false when the wait gave up (or an earlier one did: *abort)
+__device__ __forceinline__ unsigned long long tc_now() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned parity, volatile int* abort) {
+    if (*abort) return false;
+    const unsigned long long t0 = tc_now();
+    for (;;) {
+        unsigned done;
+        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+        if (*abort) return false;
+        if (tc_now() - t0 > TC_WAIT_NS) {
+            *abort = 1;
+            return false;
+        }
+    }
+}
+
+// one thread per (source, column group of 4): the packed tiles of X (hi, lo)
+// and the sources' geometry; sources past nf: X = 0, geometry parked far away
+__global__ void k_tc_pack(const float4* __restrict__ Wp, const float4* __restrict__ fa, const float4* __restrict__ flo,
+                          const float4* __restrict__ fb, int nf, int ntile, unsigned char* __restrict__ tiles) {
+    constexpr int NW4 = OpLayout<TP_OP_A, 9>::NW4;   // 10 float4: [a, W_V (27), a, W_U (9), 0, 0]
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = idx / (NW4 + 1), q = idx - j * (NW4 + 1);
+    if (j >= ntile * TC_KT) return;
+    unsigned char* T = tiles + (size_t)(j / TC_KT) * TC_TILE_BYTES;
+    const int k = j % TC_KT;
+    const bool ok = j < nf;
+    if (q == NW4) {   // geometry
+        const float4 far = make_float4(1e15f, 1e15f, 1e15f, 0.f), z = make_float4(0.f, 0.f, 0.f, 0.f);
+        reinterpret_cast<float4*>(T + TC_SHI)[k] = ok ? fa[j] : far;
+        reinterpret_cast<float4*>(T + TC_SLO)[k] = ok ? flo[j] : z;
+        reinterpret_cast<float4*>(T + TC_SN)[k] = ok ? fb[j] : z;
+        return;
+    }
+    const float4 w = ok ? Wp[(size_t)j * NW4 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float v[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int a = 4 * q + e;   // accumulator index in [a, W_V, a, W_U]
+        if (a >= 38) continue;
+        const float hi = tc_tf32(v[e]), lo = v[e] - hi;
+        if (a < 28) {
+            *reinterpret_cast<float*>(T + TC_XH + tc_cm(a, k)) = hi;
+            *reinterpret_cast<float*>(T + TC_XHL + tc_cm(a, k)) = lo;
+        } else {
+            *reinterpret_cast<float*>(T + TC_XL + tc_cm(a - 28, k)) = hi;
+            *reinterpret_cast<float*>(T + TC_XLL + tc_cm(a - 28, k)) = lo;
+        }
+    }
+    if (q == 0) {   // the padding rows: high 28..31, low 10..15
+        for (int a = 28; a < 32; ++a) {
+            *reinterpret_cast<float*>(T + TC_XH + tc_cm(a, k)) = 0.f;
+            *reinterpret_cast<float*>(T + TC_XHL + tc_cm(a, k)) = 0.f;
+        }
+        for (int a = 10; a < 16; ++a) {
+            *reinterpret_cast<float*>(T + TC_XL + tc_cm(a, k)) = 0.f;
+            *reinterpret_cast<float*>(T + TC_XLL + tc_cm(a, k)) = 0.f;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(TC_T, 2)
+k_apply_tc(const float4* __restrict__ fa, const float4* __restrict__ fb, const float4* __restrict__ flo,
+           const unsigned char* __restrict__ tiles, int nf, int ntile, int tiles_per_split, float s_exp,
+           float2* __restrict__ part, int* __restrict__ err) {
+    constexpr int NA = OpLayout<TP_OP_A, 9>::NA;   // 38
+    extern __shared__ __align__(1024) unsigned char tsm[];
+    __shared__ __align__(8) unsigned long long mbar[2 + TC_NX];   // MMA done per H buffer, tile arrived per X buffer
+    __shared__ unsigned s_taddr;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, t = tid & 127, half = tid >> 7;
+    const int tg = blockIdx.x * 128 + t;
+    const int q0 = blockIdx.y * tiles_per_split, q1 = min(ntile, q0 + tiles_per_split), nt = max(0, q1 - q0);
+    unsigned char* Hb = tsm;                    // 2 x TC_HBUF
+    unsigned char* Xb = tsm + 2 * TC_HBUF;     // TC_NX x TC_TILE_BYTES
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(&s_taddr)),
+                     "r"(TC_TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int i = 0; i < 2 + TC_NX; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&mbar[i])));
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned taddr = s_taddr;
+    volatile int* abort = &s_abort;
+    auto issue_copy = [&](int q) {   // thread 0: tile q0 + q into buffer q % TC_NX
+        const unsigned mb = tc_smem(&mbar[2 + q % TC_NX]);
+        const unsigned dst = tc_smem(Xb + (q % TC_NX) * TC_TILE_BYTES);
+        const unsigned char* src = tiles + (size_t)(q0 + q) * TC_TILE_BYTES;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(TC_TILE_BYTES) : "memory");
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(dst), "l"(src), "r"(TC_TILE_BYTES), "r"(mb) : "memory");
+    };
+    if (tid == 0 && nt > 0) issue_copy(0);
+    // targets
+    const bool tv = tg < nf;
+    const float4 T = tv ? fa[tg] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 Tl = tv ? flo[tg] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 Tn = tv ? fb[tg] : make_float4(0.f, 0.f, 0.f, 0.f);
+    // accumulator columns of this thread: half 0 -> high 0..23; half 1 -> high 24..27, low 0..9
+    float ks[24], kc[24];
+#pragma unroll
+    for (int i = 0; i < 24; ++i) ks[i] = kc[i] = 0.f;
+    const unsigned idH = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+    const unsigned idL = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+    auto drain = [&](int set) {
+        const unsigned base = taddr + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)(set * 64);
+        unsigned r[24];
+        if (half == 0) {
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                           "=r"(r[15])
+                         : "r"(base));
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+                           "=r"(r[23])
+                         : "r"(base + 16));
+        } else {
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                         : "r"(base + 24));
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                           "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+                           "=r"(r[22]), "=r"(r[23])
+                         : "r"(base + 32));
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int i = 0; i < 24; ++i) {   // Kahan
+            const float y = __uint_as_float(r[i]) - kc[i];
+            const float s = ks[i] + y;
+            kc[i] = (s - ks[i]) - y;
+            ks[i] = s;
+        }
+    };
+    // every thread runs every iteration (the block barriers stay matched);
+    // after an exhausted wait the waits return at once and no work is issued
+    for (int q = 0; q < nt; ++q) {
+        const int hb = q & 1;
+        // (a) the H buffer and the tile buffer of tile q - 2 are free
+        if (q >= 2) tc_wait(tc_smem(&mbar[hb]), ((q - 2) >> 1) & 1, abort);
+        // (b) the next tile
+        if (tid == 0 && q + 1 < nt && !*abort) issue_copy(q + 1);
+        // (c) this tile
+        tc_wait(tc_smem(&mbar[2 + q % TC_NX]), (q / TC_NX) & 1, abort);
+        const unsigned char* X = Xb + (q % TC_NX) * TC_TILE_BYTES;
+        unsigned char* H = Hb + hb * TC_HBUF;
+        // (d) kernel values of target t against sources 8 half .. 8 half + 7 of the tile
+        float hB[8], h0[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int k = 8 * half + i;
+            const int sg = (q0 + q) * TC_KT + k;
+            const float4 S = reinterpret_cast<const float4*>(X + TC_SHI)[k];
+            const float4 Sl = reinterpret_cast<const float4*>(X + TC_SLO)[k];
+            const float4 Sn = reinterpret_cast<const float4*>(X + TC_SN)[k];
+            const float dx = (T.x - S.x) + (Tl.x - Sl.x), dy = (T.y - S.y) + (Tl.y - Sl.y),
+                        dz = (T.z - S.z) + (Tl.z - Sl.z);
+            const float r2 = r2_eps(dx, dy, dz);
+            const float b = pow_(r2, -s_exp);
+            const float ir2 = rcp_(r2);
+            const float tS = (Tn.x * dx + Tn.y * dy + Tn.z * dz) * ir2;
+            const float tT = (Sn.x * dx + Sn.y * dy + Sn.z * dz) * ir2;
+            const bool on = tv && sg < nf && sg != tg;
+            hB[i] = on ? b : 0.f;
+            h0[i] = on ? 0.5f * fmaf(tS, tS, tT * tT) * b : 0.f;
+        }
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+            float4 bh, bl, zh, zl;
+            float* pbh = &bh.x; float* pbl = &bl.x; float* pzh = &zh.x; float* pzl = &zl.x;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float x = hB[4 * g + e], y = h0[4 * g + e];
+                pbh[e] = tc_tf32(x);
+                pbl[e] = x - pbh[e];
+                pzh[e] = tc_tf32(y);
+                pzl[e] = y - pzh[e];
+            }
+            const int off = tc_cm(t, 8 * half + 4 * g);
+            *reinterpret_cast<float4*>(H + 0 * TC_HMAT + off) = bh;
+            *reinterpret_cast<float4*>(H + 1 * TC_HMAT + off) = bl;
+            *reinterpret_cast<float4*>(H + 2 * TC_HMAT + off) = zh;
+            *reinterpret_cast<float4*>(H + 3 * TC_HMAT + off) = zl;
+        }
+        // (e) the operands are visible to the tensor cores
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // (f) the products of tile q into accumulator set (q / 8) & 1
+        if (tid == 0 && !*abort) {
+            const int set = (q >> 3) & 1;
+            const unsigned dH = taddr + (unsigned)(set * 64), dL = dH + 32;
+            const unsigned hbase = tc_smem(H), xbase = tc_smem(X);
+#pragma unroll
+            for (int kk = 0; kk < 2; ++kk) {
+                const unsigned o = kk * 256;
+                const int acc = ((q & 7) == 0 && kk == 0) ? 0 : 1;
+                tc_mma(dH, tc_desc(hbase + 0 * TC_HMAT + o), tc_desc(xbase + TC_XH + o), idH, acc);
+                tc_mma(dH, tc_desc(hbase + 0 * TC_HMAT + o), tc_desc(xbase + TC_XHL + o), idH, 1);
+                tc_mma(dH, tc_desc(hbase + 1 * TC_HMAT + o), tc_desc(xbase + TC_XH + o), idH, 1);
+                tc_mma(dL, tc_desc(hbase + 2 * TC_HMAT + o), tc_desc(xbase + TC_XL + o), idL, acc);
+                tc_mma(dL, tc_desc(hbase + 2 * TC_HMAT + o), tc_desc(xbase + TC_XLL + o), idL, 1);
+                tc_mma(dL, tc_desc(hbase + 3 * TC_HMAT + o), tc_desc(xbase + TC_XL + o), idL, 1);
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"(tc_smem(&mbar[hb])) : "memory");
+        }
+        // (g) the previous chunk's accumulators, while this chunk's products run
+        if ((q & 7) == 0 && q > 0) {
+            const bool ok = __all_sync(0xffffffffu, tc_wait(tc_smem(&mbar[(q - 1) & 1]), ((q - 1) >> 1) & 1, abort));
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (ok) drain(((q >> 3) - 1) & 1);
+        }
+    }
+    // the last chunk
+    if (nt > 0) {
+        const bool ok = __all_sync(0xffffffffu, tc_wait(tc_smem(&mbar[(nt - 1) & 1]), ((nt - 1) >> 1) & 1, abort));
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (ok) drain(((nt - 1) >> 3) & 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    const bool bad = *abort != 0;
+    if (bad && tid == 0) atomicExch(err, 1);
+    if (tv) {
+        const float qnan = __int_as_float(0x7fc00000);
+#pragma unroll
+        for (int i = 0; i < 24; ++i) {
+            const int a = half == 0 ? i : (i < 4 ? 24 + i : (i >= 8 && i < 18 ? 28 + (i - 8) : -1));
+            if (a < 0) continue;
+            part[((size_t)blockIdx.y * NA + a) * nf + tg] = bad ? make_float2(qnan, 0.f) : make_float2(ks[i], kc[i]);
+        }
+    }
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TC_TMEM_COLS));
+}
+
+// the A apply on 9 columns with tensor-core accumulation (see k_apply_tc)
+static int launch_apply_tc(tp_mesh* m, const tp_params* p, const double* v, int k, double* y, cudaStream_t st) {
+    using L = OpLayout<TP_OP_A, 9>;
+    const int nf = m->nf;
+    const double s = 2.0 - 2.0 / p->p;
+    const int per_sm = resident_per_sm((const void*)k_apply_tc, TC_T, TC_SMEM);
+    if (per_sm < 1) return fail(TP_ERR_CUDA, "k_apply_tc: shared memory per block not available");
+    const Grid g = make_grid(nf, nf, 1, per_sm);   // splits in 128-source chunks
+    const int ntile = (nf + TC_KT - 1) / TC_KT;
+    const int tps = g.tiles_per_split * (128 / TC_KT);
+    TP_TRY(ensure(m->part, sizeof(float2) * (size_t)g.nsplit * L::NA * nf + sizeof(double) * L::NA * (size_t)nf));
+    TP_TRY(ensure(m->wv64, sizeof(double) * 4 * 9 * (size_t)nf));
+    TP_TRY(ensure(m->wv32, sizeof(float4) * L::NW4 * (size_t)nf));
+    TP_TRY(ensure(m->corner, sizeof(double) * 3 * (size_t)nf * k));
+    TP_TRY(ensure(m->tcbuf, (size_t)ntile * TC_TILE_BYTES));
+    if (!m->tcerr.ptr) {
+        TP_TRY(ensure(m->tcerr, 16));
+        TP_CUDA(cudaMemsetAsync(m->tcerr.ptr, 0, 16, st));   // fresh memory holds garbage
+    }
+    int* err = m->tcerr.as<int>();
+    const float4* fa = m->f32a.as<float4>();
+    const float4* fb = m->f32b.as<float4>();
+    const float4* fl = m->f32c.as<float4>();
+    for (int col0 = 0; col0 < k; col0 += 9) {
+        k_face_W<float, 9><<<(nf * 3 + 255) / 256, 256, 0, st>>>(v, k, col0, m->faces.as<int>(), nf, m->f64a.as<d4>(),
+                                                             m->fgrad.as<double>(), TP_OP_A, m->wv64.as<double>(),
+                                                             m->wv32.as<float4>(), L::NW4);
+        TP_LAUNCH_CHECK();
+        const int npack = ntile * TC_KT * (L::NW4 + 1);
+        k_tc_pack<<<(npack + 255) / 256, 256, 0, st>>>(m->wv32.as<float4>(), fa, fl, fb, nf, ntile,
+                                                       m->tcbuf.as<unsigned char>());
+        TP_LAUNCH_CHECK();
+        {
+            const double units = (double)nf * (nf - 1);
+            m->pairs += units;
+            ProfScope ps(m, PK_APPLY_A, units, st);
+            m->prof.cols[PK_APPLY_A] += 9;
+            k_apply_tc<<<dim3(g.bx, g.nsplit), TC_T, TC_SMEM, st>>>(fa, fb, fl, m->tcbuf.as<unsigned char>(), nf,
+                                                                   ntile, tps, (float)s, m->part.as<float2>(), err);
+        }
+        TP_LAUNCH_CHECK();
+        double* sums = reinterpret_cast<double*>(m->part.as<float2>() + (size_t)g.nsplit * L::NA * nf);
+        k_split_sum2<<<(unsigned)(((size_t)L::NA * nf + 255) / 256), 256, 0, st>>>(m->part.as<float2>(), g.nsplit,
+                                                                                L::NA, nf, sums);
+        TP_LAUNCH_CHECK();
+        k_apply_combine2<TP_OP_A, 9><<<(nf + 127) / 128, 128, 0, st>>>(sums, nf, m->f64a.as<d4>(),
+                                                                       m->fgrad.as<double>(), m->wv64.as<double>(), k,
+                                                                       col0, m->corner.as<double>());
+        TP_LAUNCH_CHECK();
+    }
+    return corners_to_vertices(m, m->corner.as<double>(), k, y, st);
+}
+
+// the tensor-core wait flag of the mesh's A applies (0 when none gave up), and reset
+int apply_tc_error(tp_mesh* m, int* gave_up, cudaStream_t st) {
+    *gave_up = 0;
+    if (!m->tcerr.ptr) return TP_OK;
+    int* err = m->tcerr.as<int>();
+    TP_CUDA(cudaMemcpyAsync(gave_up, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TP_CUDA(cudaStreamSynchronize(st));
+    if (*gave_up) TP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    return TP_OK;
+}
+
 template <int OP>
 static int launch_apply_wide(tp_mesh* m, const tp_params* p, const double* v, int k, double* y, cudaStream_t st) {
     using L = OpLayout<OP, 9>;
@@ -1584,7 +1957,8 @@ static int launch_apply(tp_mesh* m, const tp_params* p, int op, const double* v,
     const bool wide = k > 3;
     if (sizeof(T) == 4 && wide) {
         switch (op) {
-            case TP_OP_A: return launch_apply_wide<TP_OP_A>(m, p, v, k, y, st);
+            case TP_OP_A: return p->tensor_cores ? launch_apply_tc(m, p, v, k, y, st)
+                                                 : launch_apply_wide<TP_OP_A>(m, p, v, k, y, st);
             case TP_OP_B: return launch_apply_wide<TP_OP_B>(m, p, v, k, y, st);
             case TP_OP_B0: return launch_apply_wide<TP_OP_B0>(m, p, v, k, y, st);
             case TP_OP_L: return launch_apply_wide<TP_OP_L>(m, p, v, k, y, st);

@@ -725,6 +725,9 @@ int precond_step_dev(tp_mesh* m, const tp_params* p, const tp_constraints* c, tp
         int derr = 0, dunc = 0;
         TP_TRY(chol_deferred_flags(m, st, &derr, &dunc, false));
         if (derr) return fail(TP_ERR_TIMEOUT, "precond_step: a wait of the factorised sweep gave up");
+        int tcerr = 0;
+        if (p->tensor_cores) TP_TRY(apply_tc_error(m, &tcerr, st));
+        if (tcerr) return fail(TP_ERR_TIMEOUT, "precond_step: a wait of the tensor-core A apply gave up");
     }
     unsigned long long bh1[BH_NCOUNT];
     TP_TRY(bh_counts_read(m, bh1, false, st));

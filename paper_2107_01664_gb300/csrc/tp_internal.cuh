@@ -228,6 +228,8 @@ struct tp_mesh {
     tp::Buf kry;        // FGMRES bases V and Z
     tp::Buf gsdev;      // FGMRES: first-pass Gram-Schmidt coefficients on the device
     tp::Buf tickets;    // completion tickets of the fused reductions (tp::TICKET_*)
+    tp::Buf tcbuf;      // tensor-core A apply: packed source tiles
+    tp::Buf tcerr;      // tensor-core A apply: a wait gave up (device int)
     tp::Buf stepv[8];   // vectors of the constrained step
     tp::Buf prec[3];    // preconditioner temporaries
     tp::Buf bhcount;    // device counter of Barnes-Hut interactions
@@ -291,6 +293,9 @@ int apply_direct(tp_mesh* m, const tp_params* p, int op, const double* v_dev, in
 // y = O v over the Barnes-Hut interaction lists (theta > 0, FP32)
 int apply_bh(tp_mesh* m, const tp_params* p, int op, const double* v_dev, int k, double* y_dev,
              cudaStream_t st);
+// whether a bounded wait of the tensor-core A apply gave up since the last
+// call (reads a device flag: synchronises the stream)
+int apply_tc_error(tp_mesh* m, int* gave_up, cudaStream_t st);
 // direct for theta = 0, Barnes-Hut otherwise
 int apply_op(tp_mesh* m, const tp_params* p, int op, const double* v_dev, int k, double* y_dev,
              cudaStream_t st);

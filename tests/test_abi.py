@@ -37,7 +37,7 @@ def test_params_default_and_host_logic():
     import paper_2107_01664_gb300 as tp
     p = tp.params()
     assert p.p == 6.0 and p.theta == 0.0 and p.leaf_size == 8 and p.precision == tp.TP_PREC_FP32
-    assert p.prec_self_weight == 24.0 and p.bvh_refit == 0 and p.tau0_disp == 0.0   # last fields: layouts agree
+    assert p.prec_self_weight == 24.0 and p.bvh_refit == 0 and p.tau0_disp == 0.0 and p.tensor_cores == 0   # last fields: layouts agree
     q = tp.params(theta=0.5, leaf_size=4)
     assert q.theta == 0.5 and q.leaf_size == 4
     with pytest.raises(AttributeError):
