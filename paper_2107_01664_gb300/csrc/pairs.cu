@@ -1550,20 +1550,27 @@ static int launch_apply_op(tp_mesh* m, const tp_params* p, const double* v, int 
 // wait stops all further work of the block, sets *err and writes NaN
 // partials).
 
-constexpr int TC_KT = 16;                      // sources per tile (two K = 8 steps)
-constexpr int TC_T = 256;                      // threads: target tid & 127, source half tid >> 7
-constexpr int TC_TILE_BYTES = 6912;            // packed source tile (see k_tc_pack)
-constexpr int TC_XH = 0, TC_XHL = 2048, TC_XL = 4096, TC_XLL = 5120, TC_SHI = 6144, TC_SLO = 6400, TC_SN = 6656;
-constexpr int TC_HMAT = 8192;                  // one 128 x 16 FP32 operand
+constexpr int TC_KT = 32;                      // sources per tile (four K = 8 steps)
+constexpr int TC_KC = TC_KT / 4;               // core matrices along K
+constexpr int TC_CHUNK = 128 / TC_KT;          // tiles per FP32 chunk (128 sources)
+constexpr int TC_CW = 16;                      // compute warps: target t = tid & 127, source quarter tid >> 7
+constexpr int TC_T = 32 * (TC_CW + 1);         // + one warp that loads tiles and issues the MMAs
+// packed source tile (bytes): X high hi / lo (32 x KT), X low hi / lo (16 x KT),
+// K-major operands; then the KT sources' barycenter (hi), its low part and
+// normal, one array per coordinate
+constexpr int TC_XH = 0, TC_XHL = 32 * TC_KT * 4, TC_XL = 2 * 32 * TC_KT * 4, TC_XLL = TC_XL + 16 * TC_KT * 4;
+constexpr int TC_G = TC_XLL + 16 * TC_KT * 4;
+constexpr int TC_TILE_BYTES = TC_G + 9 * TC_KT * 4;   // 13440
+constexpr int TC_HMAT = 128 * TC_KT * 4;       // one 128 x KT FP32 operand
 constexpr int TC_HBUF = 4 * TC_HMAT;           // H_B hi, H_B lo, H_0 hi, H_0 lo
 constexpr int TC_NX = 3;                       // source tile buffers
 constexpr size_t TC_SMEM = 2 * (size_t)TC_HBUF + TC_NX * (size_t)TC_TILE_BYTES;
 constexpr int TC_TMEM_COLS = 128;              // two accumulator sets of 64 columns (32 high + 16 low used)
 constexpr unsigned long long TC_WAIT_NS = 1000000000ull;   // bound of each mbarrier wait (1 s)
 
-// byte offset of element (row, k) of a [rows][16] K-major operand
+// byte offset of element (row, k) of a [rows][KT] K-major operand
 __device__ __forceinline__ int tc_cm(int row, int k) {
-    return (((row >> 3) * 4 + (k >> 2)) << 7) + ((row & 7) << 4) + ((k & 3) << 2);
+    return (((row >> 3) * TC_KC + (k >> 2)) << 7) + ((row & 7) << 4) + ((k & 3) << 2);
 }
 __device__ __forceinline__ float tc_tf32(float x) {
     unsigned r;
@@ -1572,8 +1579,9 @@ __device__ __forceinline__ float tc_tf32(float x) {
 }
 __device__ __forceinline__ unsigned tc_smem(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ unsigned long long tc_desc(unsigned addr) {
-    // start >> 4, leading byte offset 128 >> 4, stride byte offset 512 >> 4, version 1, no swizzle
-    return (unsigned long long)((addr >> 4) & 0x3fffu) | (8ull << 16) | (32ull << 32) | (1ull << 46);
+    // start >> 4, leading byte offset 128 >> 4, stride byte offset (128 TC_KC) >> 4, version 1, no swizzle
+    return (unsigned long long)((addr >> 4) & 0x3fffu) | (8ull << 16) | ((unsigned long long)(8 * TC_KC) << 32) |
+           (1ull << 46);
 }
 __device__ __forceinline__ void tc_mma(unsigned d, unsigned long long a, unsigned long long b, unsigned idesc,
                                        int acc) {
@@ -1581,13 +1589,13 @@ __device__ __forceinline__ void tc_mma(unsigned d, unsigned long long a, unsigne
                  "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
                  ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
 }
-// bounded wait for the completion of the mbarrier phase with the given parity;
-// false when the wait gave up (or an earlier one did: *abort)
 __device__ __forceinline__ unsigned long long tc_now() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
+// bounded wait for the completion of the mbarrier phase with the given
+// parity; false when it gave up, or when an earlier wait of the block did
 __device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned parity, volatile int* abort) {
     if (*abort) return false;
     const unsigned long long t0 = tc_now();
@@ -1605,8 +1613,8 @@ __device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned parity, volatile
     }
 }
 
-// one thread per (source, column group of 4): the packed tiles of X (hi, lo)
-// and the sources' geometry; sources past nf: X = 0, geometry parked far away
+// one thread per (source, column group of 4, or the geometry): the packed
+// tiles; sources past nf: X = 0, geometry parked far away
 __global__ void k_tc_pack(const float4* __restrict__ Wp, const float4* __restrict__ fa, const float4* __restrict__ flo,
                           const float4* __restrict__ fb, int nf, int ntile, unsigned char* __restrict__ tiles) {
     constexpr int NW4 = OpLayout<TP_OP_A, 9>::NW4;   // 10 float4: [a, W_V (27), a, W_U (9), 0, 0]
@@ -1616,11 +1624,14 @@ __global__ void k_tc_pack(const float4* __restrict__ Wp, const float4* __restric
     unsigned char* T = tiles + (size_t)(j / TC_KT) * TC_TILE_BYTES;
     const int k = j % TC_KT;
     const bool ok = j < nf;
-    if (q == NW4) {   // geometry
-        const float4 far = make_float4(1e15f, 1e15f, 1e15f, 0.f), z = make_float4(0.f, 0.f, 0.f, 0.f);
-        reinterpret_cast<float4*>(T + TC_SHI)[k] = ok ? fa[j] : far;
-        reinterpret_cast<float4*>(T + TC_SLO)[k] = ok ? flo[j] : z;
-        reinterpret_cast<float4*>(T + TC_SN)[k] = ok ? fb[j] : z;
+    if (q == NW4) {   // geometry, structure of arrays
+        const float4 S = ok ? fa[j] : make_float4(1e15f, 1e15f, 1e15f, 0.f);
+        const float4 Sl = ok ? flo[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 Sn = ok ? fb[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float* G = reinterpret_cast<float*>(T + TC_G);
+        G[0 * TC_KT + k] = S.x;  G[1 * TC_KT + k] = S.y;  G[2 * TC_KT + k] = S.z;
+        G[3 * TC_KT + k] = Sl.x; G[4 * TC_KT + k] = Sl.y; G[5 * TC_KT + k] = Sl.z;
+        G[6 * TC_KT + k] = Sn.x; G[7 * TC_KT + k] = Sn.y; G[8 * TC_KT + k] = Sn.z;
         return;
     }
     const float4 w = ok ? Wp[(size_t)j * NW4 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1650,27 +1661,40 @@ __global__ void k_tc_pack(const float4* __restrict__ Wp, const float4* __restric
     }
 }
 
-__global__ void __launch_bounds__(TC_T, 2)
+// Warp-specialised: warps 0..15 form the kernel values (four threads per
+// target row, eight sources each, two sources per packed f32x2 instruction)
+// into the H buffer of the tile and arrive on its "full" barrier; warp 16
+// (one lane) keeps the tile buffers filled with cp.async.bulk, issues the
+// 24 MMAs of each tile once its H buffer is full and commits them to the
+// buffer's "done" barrier, which frees the H buffer and the tile buffer.
+// Barriers: done[2] (per H buffer), full[2] (per H buffer, 16 arrivals),
+// tile[3] (per tile buffer, transaction bytes). One block per SM (17 warps);
+// a warp reads back the accumulator columns of its quarter of the rows.
+__global__ void __maxnreg__(96)
 k_apply_tc(const float4* __restrict__ fa, const float4* __restrict__ fb, const float4* __restrict__ flo,
            const unsigned char* __restrict__ tiles, int nf, int ntile, int tiles_per_split, float s_exp,
            float2* __restrict__ part, int* __restrict__ err) {
     constexpr int NA = OpLayout<TP_OP_A, 9>::NA;   // 38
     extern __shared__ __align__(1024) unsigned char tsm[];
-    __shared__ __align__(8) unsigned long long mbar[2 + TC_NX];   // MMA done per H buffer, tile arrived per X buffer
+    __shared__ __align__(8) unsigned long long mbar[2 + 2 + TC_NX];
     __shared__ unsigned s_taddr;
     __shared__ int s_abort;
-    const int tid = threadIdx.x, warp = tid >> 5, t = tid & 127, half = tid >> 7;
-    const int tg = blockIdx.x * 128 + t;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int q0 = blockIdx.y * tiles_per_split, q1 = min(ntile, q0 + tiles_per_split), nt = max(0, q1 - q0);
     unsigned char* Hb = tsm;                    // 2 x TC_HBUF
     unsigned char* Xb = tsm + 2 * TC_HBUF;     // TC_NX x TC_TILE_BYTES
-    if (warp == 0) {
+    const unsigned mb_done = tc_smem(&mbar[0]), mb_full = tc_smem(&mbar[2]), mb_tile = tc_smem(&mbar[4]);
+    if (warp == TC_CW) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(&s_taddr)),
                      "r"(TC_TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        for (int i = 0; i < 2 + TC_NX; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem(&mbar[i])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_done));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_done + 8));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb_full), "r"(TC_CW));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb_full + 8), "r"(TC_CW));
+        for (int i = 0; i < TC_NX; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_tile + 8 * i));
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -1679,159 +1703,171 @@ k_apply_tc(const float4* __restrict__ fa, const float4* __restrict__ fb, const f
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const unsigned taddr = s_taddr;
     volatile int* abort = &s_abort;
-    auto issue_copy = [&](int q) {   // thread 0: tile q0 + q into buffer q % TC_NX
-        const unsigned mb = tc_smem(&mbar[2 + q % TC_NX]);
-        const unsigned dst = tc_smem(Xb + (q % TC_NX) * TC_TILE_BYTES);
-        const unsigned char* src = tiles + (size_t)(q0 + q) * TC_TILE_BYTES;
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(TC_TILE_BYTES) : "memory");
-        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                     ::"r"(dst), "l"(src), "r"(TC_TILE_BYTES), "r"(mb) : "memory");
-    };
-    if (tid == 0 && nt > 0) issue_copy(0);
-    // targets
-    const bool tv = tg < nf;
-    const float4 T = tv ? fa[tg] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 Tl = tv ? flo[tg] : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float4 Tn = tv ? fb[tg] : make_float4(0.f, 0.f, 0.f, 0.f);
-    // accumulator columns of this thread: half 0 -> high 0..23; half 1 -> high 24..27, low 0..9
-    float ks[24], kc[24];
+
+    if (warp == TC_CW) {
+        // ---- loads and products
+        if (lane == 0) {
+            auto issue_copy = [&](int q) {   // tile q0 + q into buffer q % TC_NX
+                const unsigned mb = mb_tile + 8 * (q % TC_NX);
+                const unsigned dst = tc_smem(Xb + (q % TC_NX) * TC_TILE_BYTES);
+                const unsigned char* src = tiles + (size_t)(q0 + q) * TC_TILE_BYTES;
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb), "r"(TC_TILE_BYTES)
+                             : "memory");
+                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                             ::"r"(dst), "l"(src), "r"(TC_TILE_BYTES), "r"(mb) : "memory");
+            };
+            for (int q = 0; q < min(nt, TC_NX); ++q) issue_copy(q);
+            const unsigned idH = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+            const unsigned idL = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+            for (int q = 0; q < nt; ++q) {
+                const int hb = q & 1;
+                if (!tc_wait(mb_full + 8 * hb, (q >> 1) & 1, abort)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const int set = (q / TC_CHUNK) & 1;
+                const unsigned dH = taddr + (unsigned)(set * 64), dL = dH + 32;
+                const unsigned hbase = tc_smem(Hb + hb * TC_HBUF), xbase = tc_smem(Xb + (q % TC_NX) * TC_TILE_BYTES);
 #pragma unroll
-    for (int i = 0; i < 24; ++i) ks[i] = kc[i] = 0.f;
-    const unsigned idH = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
-    const unsigned idL = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
-    auto drain = [&](int set) {
-        const unsigned base = taddr + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)(set * 64);
-        unsigned r[24];
-        if (half == 0) {
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                           "=r"(r[15])
-                         : "r"(base));
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                         : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
-                           "=r"(r[23])
-                         : "r"(base + 16));
-        } else {
+                for (int kk = 0; kk < TC_KT / 8; ++kk) {
+                    const unsigned o = kk * 256;
+                    const int acc = ((q % TC_CHUNK) == 0 && kk == 0) ? 0 : 1;
+                    tc_mma(dH, tc_desc(hbase + 0 * TC_HMAT + o), tc_desc(xbase + TC_XH + o), idH, acc);
+                    tc_mma(dH, tc_desc(hbase + 0 * TC_HMAT + o), tc_desc(xbase + TC_XHL + o), idH, 1);
+                    tc_mma(dH, tc_desc(hbase + 1 * TC_HMAT + o), tc_desc(xbase + TC_XH + o), idH, 1);
+                    tc_mma(dL, tc_desc(hbase + 2 * TC_HMAT + o), tc_desc(xbase + TC_XL + o), idL, acc);
+                    tc_mma(dL, tc_desc(hbase + 2 * TC_HMAT + o), tc_desc(xbase + TC_XLL + o), idL, 1);
+                    tc_mma(dL, tc_desc(hbase + 3 * TC_HMAT + o), tc_desc(xbase + TC_XL + o), idL, 1);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                             ::"r"(mb_done + 8 * hb) : "memory");
+                // refill the buffer of tile q - 1 with tile q + 2 once its products are done
+                if (q >= 1 && q + 2 < nt) {
+                    if (!tc_wait(mb_done + 8 * ((q - 1) & 1), ((q - 1) >> 1) & 1, abort)) break;
+                    issue_copy(q + 2);
+                }
+            }
+        }
+    } else {
+        // ---- kernel values, read-back of the accumulators
+        const int t = tid & 127, sq = tid >> 7;   // row; source quarter of the tile and column group
+        const int tg = blockIdx.x * 128 + t;
+        const bool tv = tg < nf;
+        const float4 T = tv ? fa[tg] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 Tl = tv ? flo[tg] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 Tn = tv ? fb[tg] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float2 TX = q2(T.x), TY = q2(T.y), TZ = q2(T.z), LX = q2(Tl.x), LY = q2(Tl.y), LZ = q2(Tl.z);
+        const float2 NX = q2(Tn.x), NY = q2(Tn.y), NZ = q2(Tn.z), EPS = q2(1e-18f), HALF = q2(0.5f);
+        // accumulator columns 12 sq .. 12 sq + 11 of a set (high 0..31 then low 32..47)
+        float ks[12], kc[12];
+#pragma unroll
+        for (int i = 0; i < 12; ++i) ks[i] = kc[i] = 0.f;
+        auto drain = [&](int set) {
+            const unsigned base = taddr + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)(set * 64 + 12 * sq);
+            unsigned r[12];
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                         : "r"(base + 24));
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                         : "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                           "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-                           "=r"(r[22]), "=r"(r[23])
-                         : "r"(base + 32));
-        }
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                         : "r"(base));
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                         : "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11])
+                         : "r"(base + 8));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int i = 0; i < 24; ++i) {   // Kahan
-            const float y = __uint_as_float(r[i]) - kc[i];
-            const float s = ks[i] + y;
-            kc[i] = (s - ks[i]) - y;
-            ks[i] = s;
-        }
-    };
-    // every thread runs every iteration (the block barriers stay matched);
-    // after an exhausted wait the waits return at once and no work is issued
-    for (int q = 0; q < nt; ++q) {
-        const int hb = q & 1;
-        // (a) the H buffer and the tile buffer of tile q - 2 are free
-        if (q >= 2) tc_wait(tc_smem(&mbar[hb]), ((q - 2) >> 1) & 1, abort);
-        // (b) the next tile
-        if (tid == 0 && q + 1 < nt && !*abort) issue_copy(q + 1);
-        // (c) this tile
-        tc_wait(tc_smem(&mbar[2 + q % TC_NX]), (q / TC_NX) & 1, abort);
-        const unsigned char* X = Xb + (q % TC_NX) * TC_TILE_BYTES;
-        unsigned char* H = Hb + hb * TC_HBUF;
-        // (d) kernel values of target t against sources 8 half .. 8 half + 7 of the tile
-        float hB[8], h0[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const int k = 8 * half + i;
-            const int sg = (q0 + q) * TC_KT + k;
-            const float4 S = reinterpret_cast<const float4*>(X + TC_SHI)[k];
-            const float4 Sl = reinterpret_cast<const float4*>(X + TC_SLO)[k];
-            const float4 Sn = reinterpret_cast<const float4*>(X + TC_SN)[k];
-            const float dx = (T.x - S.x) + (Tl.x - Sl.x), dy = (T.y - S.y) + (Tl.y - Sl.y),
-                        dz = (T.z - S.z) + (Tl.z - Sl.z);
-            const float r2 = r2_eps(dx, dy, dz);
-            const float b = pow_(r2, -s_exp);
-            const float ir2 = rcp_(r2);
-            const float tS = (Tn.x * dx + Tn.y * dy + Tn.z * dz) * ir2;
-            const float tT = (Sn.x * dx + Sn.y * dy + Sn.z * dz) * ir2;
-            const bool on = tv && sg < nf && sg != tg;
-            hB[i] = on ? b : 0.f;
-            h0[i] = on ? 0.5f * fmaf(tS, tS, tT * tT) * b : 0.f;
-        }
-#pragma unroll
-        for (int g = 0; g < 2; ++g) {
-            float4 bh, bl, zh, zl;
-            float* pbh = &bh.x; float* pbl = &bl.x; float* pzh = &zh.x; float* pzl = &zl.x;
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float x = hB[4 * g + e], y = h0[4 * g + e];
-                pbh[e] = tc_tf32(x);
-                pbl[e] = x - pbh[e];
-                pzh[e] = tc_tf32(y);
-                pzl[e] = y - pzh[e];
+            for (int i = 0; i < 12; ++i) {   // Kahan
+                const float y = __uint_as_float(r[i]) - kc[i];
+                const float s = ks[i] + y;
+                kc[i] = (s - ks[i]) - y;
+                ks[i] = s;
             }
-            const int off = tc_cm(t, 8 * half + 4 * g);
-            *reinterpret_cast<float4*>(H + 0 * TC_HMAT + off) = bh;
-            *reinterpret_cast<float4*>(H + 1 * TC_HMAT + off) = bl;
-            *reinterpret_cast<float4*>(H + 2 * TC_HMAT + off) = zh;
-            *reinterpret_cast<float4*>(H + 3 * TC_HMAT + off) = zl;
-        }
-        // (e) the operands are visible to the tensor cores
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // (f) the products of tile q into accumulator set (q / 8) & 1
-        if (tid == 0 && !*abort) {
-            const int set = (q >> 3) & 1;
-            const unsigned dH = taddr + (unsigned)(set * 64), dL = dH + 32;
-            const unsigned hbase = tc_smem(H), xbase = tc_smem(X);
+        };
+        for (int q = 0; q < nt; ++q) {
+            const int hb = q & 1;
+            // this tile's sources, and the H buffer of tile q - 2 free
+            tc_wait(mb_tile + 8 * (q % TC_NX), (q / TC_NX) & 1, abort);
+            if (q >= 2) tc_wait(mb_done + 8 * hb, ((q - 2) >> 1) & 1, abort);
+            if (!*abort) {
+                const float* G = reinterpret_cast<const float*>(Xb + (q % TC_NX) * TC_TILE_BYTES + TC_G);
+                unsigned char* H = Hb + hb * TC_HBUF;
+                const int sg0 = (q0 + q) * TC_KT;
+                float hB[8], h0[8];
 #pragma unroll
-            for (int kk = 0; kk < 2; ++kk) {
-                const unsigned o = kk * 256;
-                const int acc = ((q & 7) == 0 && kk == 0) ? 0 : 1;
-                tc_mma(dH, tc_desc(hbase + 0 * TC_HMAT + o), tc_desc(xbase + TC_XH + o), idH, acc);
-                tc_mma(dH, tc_desc(hbase + 0 * TC_HMAT + o), tc_desc(xbase + TC_XHL + o), idH, 1);
-                tc_mma(dH, tc_desc(hbase + 1 * TC_HMAT + o), tc_desc(xbase + TC_XH + o), idH, 1);
-                tc_mma(dL, tc_desc(hbase + 2 * TC_HMAT + o), tc_desc(xbase + TC_XL + o), idL, acc);
-                tc_mma(dL, tc_desc(hbase + 2 * TC_HMAT + o), tc_desc(xbase + TC_XLL + o), idL, 1);
-                tc_mma(dL, tc_desc(hbase + 3 * TC_HMAT + o), tc_desc(xbase + TC_XL + o), idL, 1);
+                for (int i = 0; i < 4; ++i) {
+                    const int k = 8 * sq + 2 * i;   // sources k, k + 1 of the tile, packed
+                    const float2 SX = *reinterpret_cast<const float2*>(G + 0 * TC_KT + k);
+                    const float2 SY = *reinterpret_cast<const float2*>(G + 1 * TC_KT + k);
+                    const float2 SZ = *reinterpret_cast<const float2*>(G + 2 * TC_KT + k);
+                    const float2 SLX = *reinterpret_cast<const float2*>(G + 3 * TC_KT + k);
+                    const float2 SLY = *reinterpret_cast<const float2*>(G + 4 * TC_KT + k);
+                    const float2 SLZ = *reinterpret_cast<const float2*>(G + 5 * TC_KT + k);
+                    const float2 MX = *reinterpret_cast<const float2*>(G + 6 * TC_KT + k);
+                    const float2 MY = *reinterpret_cast<const float2*>(G + 7 * TC_KT + k);
+                    const float2 MZ = *reinterpret_cast<const float2*>(G + 8 * TC_KT + k);
+                    const float2 dx = q2add(q2sub(TX, SX), q2sub(LX, SLX));
+                    const float2 dy = q2add(q2sub(TY, SY), q2sub(LY, SLY));
+                    const float2 dz = q2add(q2sub(TZ, SZ), q2sub(LZ, SLZ));
+                    const float2 r2 = q2fma(dx, dx, q2fma(dy, dy, q2fma(dz, dz, EPS)));
+                    const float2 b = make_float2(pow_(r2.x, -s_exp), pow_(r2.y, -s_exp));
+                    const float2 ir2 = make_float2(rcp_(r2.x), rcp_(r2.y));
+                    const float2 tS = q2mul(q2fma(NX, dx, q2fma(NY, dy, q2mul(NZ, dz))), ir2);
+                    const float2 tT = q2mul(q2fma(MX, dx, q2fma(MY, dy, q2mul(MZ, dz))), ir2);
+                    const float2 z = q2mul(q2mul(HALF, q2fma(tS, tS, q2mul(tT, tT))), b);
+                    const int s0 = sg0 + k, s1 = s0 + 1;
+                    const bool on0 = tv && s0 < nf && s0 != tg, on1 = tv && s1 < nf && s1 != tg;
+                    hB[2 * i] = on0 ? b.x : 0.f;
+                    hB[2 * i + 1] = on1 ? b.y : 0.f;
+                    h0[2 * i] = on0 ? z.x : 0.f;
+                    h0[2 * i + 1] = on1 ? z.y : 0.f;
+                }
+#pragma unroll
+                for (int g = 0; g < 2; ++g) {
+                    float4 bh, bl, zh, zl;
+                    float* pbh = &bh.x; float* pbl = &bl.x; float* pzh = &zh.x; float* pzl = &zl.x;
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float x = hB[4 * g + e], y = h0[4 * g + e];
+                        pbh[e] = tc_tf32(x);
+                        pbl[e] = x - pbh[e];
+                        pzh[e] = tc_tf32(y);
+                        pzl[e] = y - pzh[e];
+                    }
+                    const int off = tc_cm(t, 8 * sq + 4 * g);
+                    *reinterpret_cast<float4*>(H + 0 * TC_HMAT + off) = bh;
+                    *reinterpret_cast<float4*>(H + 1 * TC_HMAT + off) = bl;
+                    *reinterpret_cast<float4*>(H + 2 * TC_HMAT + off) = zh;
+                    *reinterpret_cast<float4*>(H + 3 * TC_HMAT + off) = zl;
+                }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                         ::"r"(tc_smem(&mbar[hb])) : "memory");
+            // the warp's part of H(q) is written: visible to the tensor cores
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0 && !*abort) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mb_full + 8 * hb)
+                                                   : "memory");
+            // the previous chunk's accumulators, while this chunk's products run
+            if ((q % TC_CHUNK) == 0 && q > 0) {
+                const bool ok = __all_sync(0xffffffffu, tc_wait(mb_done + 8 * ((q - 1) & 1), ((q - 1) >> 1) & 1, abort));
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                if (ok) drain(((q / TC_CHUNK) - 1) & 1);
+            }
         }
-        // (g) the previous chunk's accumulators, while this chunk's products run
-        if ((q & 7) == 0 && q > 0) {
-            const bool ok = __all_sync(0xffffffffu, tc_wait(tc_smem(&mbar[(q - 1) & 1]), ((q - 1) >> 1) & 1, abort));
+        if (nt > 0) {
+            const bool ok = __all_sync(0xffffffffu, tc_wait(mb_done + 8 * ((nt - 1) & 1), ((nt - 1) >> 1) & 1, abort));
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (ok) drain(((q >> 3) - 1) & 1);
+            if (ok) drain(((nt - 1) / TC_CHUNK) & 1);
         }
-    }
-    // the last chunk
-    if (nt > 0) {
-        const bool ok = __all_sync(0xffffffffu, tc_wait(tc_smem(&mbar[(nt - 1) & 1]), ((nt - 1) >> 1) & 1, abort));
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (ok) drain(((nt - 1) >> 3) & 1);
+        const bool bad = *abort != 0;
+        if (tv) {
+            const float qnan = __int_as_float(0x7fc00000);
+#pragma unroll
+            for (int i = 0; i < 12; ++i) {
+                const int c = 12 * sq + i;   // column of the set
+                const int a = c < 28 ? c : (c >= 32 && c < 42 ? 28 + (c - 32) : -1);
+                if (a < 0) continue;
+                part[((size_t)blockIdx.y * NA + a) * nf + tg] = bad ? make_float2(qnan, 0.f) : make_float2(ks[i], kc[i]);
+            }
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
-    const bool bad = *abort != 0;
-    if (bad && tid == 0) atomicExch(err, 1);
-    if (tv) {
-        const float qnan = __int_as_float(0x7fc00000);
-#pragma unroll
-        for (int i = 0; i < 24; ++i) {
-            const int a = half == 0 ? i : (i < 4 ? 24 + i : (i >= 8 && i < 18 ? 28 + (i - 8) : -1));
-            if (a < 0) continue;
-            part[((size_t)blockIdx.y * NA + a) * nf + tg] = bad ? make_float2(qnan, 0.f) : make_float2(ks[i], kc[i]);
-        }
-    }
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TC_TMEM_COLS));
+    if (tid == 0 && *abort) atomicExch(err, 1);
+    if (warp == TC_CW) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TC_TMEM_COLS));
 }
 
 // the A apply on 9 columns with tensor-core accumulation (see k_apply_tc)
@@ -1839,11 +1875,36 @@ static int launch_apply_tc(tp_mesh* m, const tp_params* p, const double* v, int 
     using L = OpLayout<TP_OP_A, 9>;
     const int nf = m->nf;
     const double s = 2.0 - 2.0 / p->p;
+    static bool carveout_set[64] = {false};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && !carveout_set[dev]) {
+        // the whole shared-memory carveout: the kernel needs 172 KB per block
+        TP_CUDA(cudaFuncSetAttribute((const void*)k_apply_tc, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+        carveout_set[dev] = true;
+    }
     const int per_sm = resident_per_sm((const void*)k_apply_tc, TC_T, TC_SMEM);
     if (per_sm < 1) return fail(TP_ERR_CUDA, "k_apply_tc: shared memory per block not available");
-    const Grid g = make_grid(nf, nf, 1, per_sm);   // splits in 128-source chunks
+    // source splits: blocks = target blocks x splits run in waves of per_sm x SMs; the time goes
+    // like waves x (tiles per split + the fixed cost of a block, about 6 tiles)
     const int ntile = (nf + TC_KT - 1) / TC_KT;
-    const int tps = g.tiles_per_split * (128 / TC_KT);
+    Grid g;
+    g.bx = (nf + 127) / 128;
+    {
+        const long long slots = (long long)per_sm * sm_count();
+        long long best = -1;
+        for (int ns = 1; ns <= 64 && ns <= ntile; ++ns) {
+            const long long tps_ = (ntile + ns - 1) / ns;
+            const long long waves = ((long long)g.bx * ns + slots - 1) / slots;
+            const long long cost = waves * (tps_ + 6);
+            if (best < 0 || cost < best) {
+                best = cost;
+                g.nsplit = ns;
+                g.tiles_per_split = (int)tps_;
+            }
+        }
+    }
+    const int tps = g.tiles_per_split;
     TP_TRY(ensure(m->part, sizeof(float2) * (size_t)g.nsplit * L::NA * nf + sizeof(double) * L::NA * (size_t)nf));
     TP_TRY(ensure(m->wv64, sizeof(double) * 4 * 9 * (size_t)nf));
     TP_TRY(ensure(m->wv32, sizeof(float4) * L::NW4 * (size_t)nf));
