@@ -1556,16 +1556,18 @@ constexpr int TC_CHUNK = 128 / TC_KT;          // tiles per FP32 chunk (128 sour
 constexpr int TC_CW = 16;                      // compute warps: target t = tid & 127, source quarter tid >> 7
 constexpr int TC_T = 32 * (TC_CW + 1);         // + one warp that loads tiles and issues the MMAs
 // packed source tile (bytes): X high hi / lo (32 x KT), X low hi / lo (16 x KT),
-// K-major operands; then the KT sources' barycenter (hi), its low part and
-// normal, one array per coordinate
+// K-major operands; then the sources' geometry by pairs (2p, 2p + 1), five
+// float4 per pair: {x0 x1 y0 y1} {z0 z1 nx0 nx1} {ny0 ny1 nz0 nz1}
+// {lx0 lx1 ly0 ly1} {lz0 lz1 0 0} (barycenter hi, normal, barycenter lo)
 constexpr int TC_XH = 0, TC_XHL = 32 * TC_KT * 4, TC_XL = 2 * 32 * TC_KT * 4, TC_XLL = TC_XL + 16 * TC_KT * 4;
 constexpr int TC_G = TC_XLL + 16 * TC_KT * 4;
-constexpr int TC_TILE_BYTES = TC_G + 9 * TC_KT * 4;   // 13440
+constexpr int TC_BOX = TC_G + (TC_KT / 2) * 5 * 16;   // bounding box of the tile's 128-source chunk (2 float4)
+constexpr int TC_TILE_BYTES = TC_BOX + 32;            // 13600
 constexpr int TC_HMAT = 128 * TC_KT * 4;       // one 128 x KT FP32 operand
 constexpr int TC_HBUF = 4 * TC_HMAT;           // H_B hi, H_B lo, H_0 hi, H_0 lo
 constexpr int TC_NX = 3;                       // source tile buffers
 constexpr size_t TC_SMEM = 2 * (size_t)TC_HBUF + TC_NX * (size_t)TC_TILE_BYTES;
-constexpr int TC_TMEM_COLS = 128;              // two accumulator sets of 64 columns (32 high + 16 low used)
+constexpr int TC_TMEM_COLS = 512;              // two sets x three split products x 64 columns (32 high + 16 low)
 constexpr unsigned long long TC_WAIT_NS = 1000000000ull;   // bound of each mbarrier wait (1 s)
 
 // byte offset of element (row, k) of a [rows][KT] K-major operand
@@ -1596,16 +1598,24 @@ __device__ __forceinline__ unsigned long long tc_now() {
 }
 // bounded wait for the completion of the mbarrier phase with the given
 // parity; false when it gave up, or when an earlier wait of the block did
-__device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned parity, volatile int* abort) {
-    if (*abort) return false;
+__device__ __forceinline__ bool tc_try(unsigned mbar, unsigned parity) {
+    unsigned done;
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+    return done != 0;
+}
+// (a waiting warp sleeps between tries, up to max_ns, instead of taking the
+// issue slots of the warps it waits for)
+__device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned parity, volatile int* abort, unsigned max_ns = 64) {
+    if (tc_try(mbar, parity)) return true;   // the common case: no clock read
     const unsigned long long t0 = tc_now();
+    unsigned ns = 16;
     for (;;) {
-        unsigned done;
-        asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
-        if (done) return true;
+        __nanosleep(ns);
+        if (ns < max_ns) ns <<= 1;
         if (*abort) return false;
+        if (tc_try(mbar, parity)) return true;
         if (tc_now() - t0 > TC_WAIT_NS) {
             *abort = 1;
             return false;
@@ -1616,7 +1626,8 @@ __device__ __forceinline__ bool tc_wait(unsigned mbar, unsigned parity, volatile
 // one thread per (source, column group of 4, or the geometry): the packed
 // tiles; sources past nf: X = 0, geometry parked far away
 __global__ void k_tc_pack(const float4* __restrict__ Wp, const float4* __restrict__ fa, const float4* __restrict__ flo,
-                          const float4* __restrict__ fb, int nf, int ntile, unsigned char* __restrict__ tiles) {
+                          const float4* __restrict__ fb, const float4* __restrict__ tbox, int nf, int ntile,
+                          unsigned char* __restrict__ tiles) {
     constexpr int NW4 = OpLayout<TP_OP_A, 9>::NW4;   // 10 float4: [a, W_V (27), a, W_U (9), 0, 0]
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = idx / (NW4 + 1), q = idx - j * (NW4 + 1);
@@ -1624,14 +1635,23 @@ __global__ void k_tc_pack(const float4* __restrict__ Wp, const float4* __restric
     unsigned char* T = tiles + (size_t)(j / TC_KT) * TC_TILE_BYTES;
     const int k = j % TC_KT;
     const bool ok = j < nf;
-    if (q == NW4) {   // geometry, structure of arrays
+    if (q == NW4) {   // geometry, by pairs of sources
         const float4 S = ok ? fa[j] : make_float4(1e15f, 1e15f, 1e15f, 0.f);
         const float4 Sl = ok ? flo[j] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 Sn = ok ? fb[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float* G = reinterpret_cast<float*>(T + TC_G);
-        G[0 * TC_KT + k] = S.x;  G[1 * TC_KT + k] = S.y;  G[2 * TC_KT + k] = S.z;
-        G[3 * TC_KT + k] = Sl.x; G[4 * TC_KT + k] = Sl.y; G[5 * TC_KT + k] = Sl.z;
-        G[6 * TC_KT + k] = Sn.x; G[7 * TC_KT + k] = Sn.y; G[8 * TC_KT + k] = Sn.z;
+        float* P = reinterpret_cast<float*>(T + TC_G) + (k >> 1) * 20;
+        const int e = k & 1;
+        P[0 + e] = S.x;   P[2 + e] = S.y;
+        P[4 + e] = S.z;   P[6 + e] = Sn.x;
+        P[8 + e] = Sn.y;  P[10 + e] = Sn.z;
+        P[12 + e] = Sl.x; P[14 + e] = Sl.y;
+        P[16 + e] = Sl.z; P[18 + e] = 0.f;
+        if (k == 0) {   // the box of the 128-source chunk (k_tile_boxes), for the near-tile test
+            float4* B = reinterpret_cast<float4*>(T + TC_BOX);
+            const int ch = j >> 7;
+            B[0] = tbox[2 * ch];
+            B[1] = tbox[2 * ch + 1];
+        }
         return;
     }
     const float4 w = ok ? Wp[(size_t)j * NW4 + q] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1672,14 +1692,34 @@ __global__ void k_tc_pack(const float4* __restrict__ Wp, const float4* __restric
 // a warp reads back the accumulator columns of its quarter of the rows.
 __global__ void __maxnreg__(96)
 k_apply_tc(const float4* __restrict__ fa, const float4* __restrict__ fb, const float4* __restrict__ flo,
-           const unsigned char* __restrict__ tiles, int nf, int ntile, int tiles_per_split, float s_exp,
-           float2* __restrict__ part, int* __restrict__ err) {
+           const float4* __restrict__ tbox, const double* __restrict__ center, const unsigned char* __restrict__ tiles,
+           int nf, int ntile, int tiles_per_split, float s_exp, float2* __restrict__ part, int* __restrict__ err) {
     constexpr int NA = OpLayout<TP_OP_A, 9>::NA;   // 38
     extern __shared__ __align__(1024) unsigned char tsm[];
     __shared__ __align__(8) unsigned long long mbar[2 + 2 + TC_NX];
     __shared__ unsigned s_taddr;
     __shared__ int s_abort;
+    __shared__ float s_wb[4][6];   // bounding boxes of the block's targets, per warp of rows
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp < 4) {
+        const int tb = blockIdx.x * 128 + tid;
+        float4 A = tb < nf ? fa[tb] : make_float4(3e38f, 3e38f, 3e38f, 0.f);
+        float lx = A.x, ly = A.y, lz = A.z;
+        if (tb >= nf) A = make_float4(-3e38f, -3e38f, -3e38f, 0.f);
+        float hx = A.x, hy = A.y, hz = A.z;
+        for (int o = 16; o > 0; o >>= 1) {
+            lx = fminf(lx, __shfl_xor_sync(0xffffffffu, lx, o));
+            ly = fminf(ly, __shfl_xor_sync(0xffffffffu, ly, o));
+            lz = fminf(lz, __shfl_xor_sync(0xffffffffu, lz, o));
+            hx = fmaxf(hx, __shfl_xor_sync(0xffffffffu, hx, o));
+            hy = fmaxf(hy, __shfl_xor_sync(0xffffffffu, hy, o));
+            hz = fmaxf(hz, __shfl_xor_sync(0xffffffffu, hz, o));
+        }
+        if (lane == 0) {
+            s_wb[warp][0] = lx; s_wb[warp][1] = ly; s_wb[warp][2] = lz;
+            s_wb[warp][3] = hx; s_wb[warp][4] = hy; s_wb[warp][5] = hz;
+        }
+    }
     const int q0 = blockIdx.y * tiles_per_split, q1 = min(ntile, q0 + tiles_per_split), nt = max(0, q1 - q0);
     unsigned char* Hb = tsm;                    // 2 x TC_HBUF
     unsigned char* Xb = tsm + 2 * TC_HBUF;     // TC_NX x TC_TILE_BYTES
@@ -1721,21 +1761,22 @@ k_apply_tc(const float4* __restrict__ fa, const float4* __restrict__ fb, const f
             const unsigned idL = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
             for (int q = 0; q < nt; ++q) {
                 const int hb = q & 1;
-                if (!tc_wait(mb_full + 8 * hb, (q >> 1) & 1, abort)) break;
+                if (!tc_wait(mb_full + 8 * hb, (q >> 1) & 1, abort, 256)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                // the three split products accumulate separately (independent MMA chains)
                 const int set = (q / TC_CHUNK) & 1;
-                const unsigned dH = taddr + (unsigned)(set * 64), dL = dH + 32;
+                const unsigned d0 = taddr + (unsigned)(set * 192);
                 const unsigned hbase = tc_smem(Hb + hb * TC_HBUF), xbase = tc_smem(Xb + (q % TC_NX) * TC_TILE_BYTES);
 #pragma unroll
                 for (int kk = 0; kk < TC_KT / 8; ++kk) {
                     const unsigned o = kk * 256;
                     const int acc = ((q % TC_CHUNK) == 0 && kk == 0) ? 0 : 1;
-                    tc_mma(dH, tc_desc(hbase + 0 * TC_HMAT + o), tc_desc(xbase + TC_XH + o), idH, acc);
-                    tc_mma(dH, tc_desc(hbase + 0 * TC_HMAT + o), tc_desc(xbase + TC_XHL + o), idH, 1);
-                    tc_mma(dH, tc_desc(hbase + 1 * TC_HMAT + o), tc_desc(xbase + TC_XH + o), idH, 1);
-                    tc_mma(dL, tc_desc(hbase + 2 * TC_HMAT + o), tc_desc(xbase + TC_XL + o), idL, acc);
-                    tc_mma(dL, tc_desc(hbase + 2 * TC_HMAT + o), tc_desc(xbase + TC_XLL + o), idL, 1);
-                    tc_mma(dL, tc_desc(hbase + 3 * TC_HMAT + o), tc_desc(xbase + TC_XL + o), idL, 1);
+                    tc_mma(d0, tc_desc(hbase + 0 * TC_HMAT + o), tc_desc(xbase + TC_XH + o), idH, acc);
+                    tc_mma(d0 + 64, tc_desc(hbase + 0 * TC_HMAT + o), tc_desc(xbase + TC_XHL + o), idH, acc);
+                    tc_mma(d0 + 128, tc_desc(hbase + 1 * TC_HMAT + o), tc_desc(xbase + TC_XH + o), idH, acc);
+                    tc_mma(d0 + 32, tc_desc(hbase + 2 * TC_HMAT + o), tc_desc(xbase + TC_XL + o), idL, acc);
+                    tc_mma(d0 + 96, tc_desc(hbase + 2 * TC_HMAT + o), tc_desc(xbase + TC_XLL + o), idL, acc);
+                    tc_mma(d0 + 160, tc_desc(hbase + 3 * TC_HMAT + o), tc_desc(xbase + TC_XL + o), idL, acc);
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                              ::"r"(mb_done + 8 * hb) : "memory");
@@ -1754,25 +1795,39 @@ k_apply_tc(const float4* __restrict__ fa, const float4* __restrict__ fb, const f
         const float4 T = tv ? fa[tg] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 Tl = tv ? flo[tg] : make_float4(0.f, 0.f, 0.f, 0.f);
         const float4 Tn = tv ? fb[tg] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float2 TX = q2(T.x), TY = q2(T.y), TZ = q2(T.z), LX = q2(Tl.x), LY = q2(Tl.y), LZ = q2(Tl.z);
-        const float2 NX = q2(Tn.x), NY = q2(Tn.y), NZ = q2(Tn.z), EPS = q2(1e-18f), HALF = q2(0.5f);
+        const unsigned long long TX = pk2(T.x, T.x), TY = pk2(T.y, T.y), TZ = pk2(T.z, T.z);
+        const unsigned long long LX = pk2(Tl.x, Tl.x), LY = pk2(Tl.y, Tl.y), LZ = pk2(Tl.z, Tl.z);
+        const unsigned long long NX = pk2(Tn.x, Tn.x), NY = pk2(Tn.y, Tn.y), NZ = pk2(Tn.z, Tn.z);
+        const unsigned long long EPS = pk2(1e-18f, 1e-18f), NE = pk2(-s_exp, -s_exp), HALF = pk2(0.5f, 0.5f);
+        float sbox[6];
+        for (int c = 0; c < 3; ++c) {
+            sbox[c] = fminf(fminf(s_wb[0][c], s_wb[1][c]), fminf(s_wb[2][c], s_wb[3][c]));
+            sbox[3 + c] = fmaxf(fmaxf(s_wb[0][3 + c], s_wb[1][3 + c]), fmaxf(s_wb[2][3 + c], s_wb[3][3 + c]));
+        }
+        const float thr2 = (float)center[3];
         // accumulator columns 12 sq .. 12 sq + 11 of a set (high 0..31 then low 32..47)
         float ks[12], kc[12];
 #pragma unroll
         for (int i = 0; i < 12; ++i) ks[i] = kc[i] = 0.f;
         auto drain = [&](int set) {
-            const unsigned base = taddr + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)(set * 64 + 12 * sq);
-            unsigned r[12];
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                         : "r"(base));
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                         : "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11])
-                         : "r"(base + 8));
+            // the three split products of each column, added, then into the Kahan pairs
+            const unsigned base = taddr + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)(set * 192 + 12 * sq);
+            unsigned r[3][12];
+#pragma unroll
+            for (int pr = 0; pr < 3; ++pr) {
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                             : "=r"(r[pr][0]), "=r"(r[pr][1]), "=r"(r[pr][2]), "=r"(r[pr][3]), "=r"(r[pr][4]),
+                               "=r"(r[pr][5]), "=r"(r[pr][6]), "=r"(r[pr][7])
+                             : "r"(base + 64 * pr));
+                asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                             : "=r"(r[pr][8]), "=r"(r[pr][9]), "=r"(r[pr][10]), "=r"(r[pr][11])
+                             : "r"(base + 64 * pr + 8));
+            }
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int i = 0; i < 12; ++i) {   // Kahan
-                const float y = __uint_as_float(r[i]) - kc[i];
+                const float v = (__uint_as_float(r[0][i]) + __uint_as_float(r[1][i])) + __uint_as_float(r[2][i]);
+                const float y = v - kc[i];
                 const float s = ks[i] + y;
                 kc[i] = (s - ks[i]) - y;
                 ks[i] = s;
@@ -1784,55 +1839,52 @@ k_apply_tc(const float4* __restrict__ fa, const float4* __restrict__ fb, const f
             tc_wait(mb_tile + 8 * (q % TC_NX), (q / TC_NX) & 1, abort);
             if (q >= 2) tc_wait(mb_done + 8 * hb, ((q - 2) >> 1) & 1, abort);
             if (!*abort) {
-                const float* G = reinterpret_cast<const float*>(Xb + (q % TC_NX) * TC_TILE_BYTES + TC_G);
+                const ulonglong2* G = reinterpret_cast<const ulonglong2*>(Xb + (q % TC_NX) * TC_TILE_BYTES + TC_G);
                 unsigned char* H = Hb + hb * TC_HBUF;
                 const int sg0 = (q0 + q) * TC_KT;
-                float hB[8], h0[8];
+                // tiles on the block's own rows (self pairs) or past nf take the masked path; tiles near
+                // the block's targets take the compensated differences (as in k_apply_wide)
+                const bool special = (sg0 < (int)blockIdx.x * 128 + 128 && sg0 + TC_KT > (int)blockIdx.x * 128) ||
+                                     sg0 + TC_KT > nf;
+                const bool near = special || tile_near(reinterpret_cast<const float4*>(Xb + (q % TC_NX) * TC_TILE_BYTES + TC_BOX),
+                                                       0, sbox, thr2);
+                unsigned long long hBp[4], h0p[4];   // kernel values of sources (2i, 2i + 1) of this thread
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const int k = 8 * sq + 2 * i;   // sources k, k + 1 of the tile, packed
-                    const float2 SX = *reinterpret_cast<const float2*>(G + 0 * TC_KT + k);
-                    const float2 SY = *reinterpret_cast<const float2*>(G + 1 * TC_KT + k);
-                    const float2 SZ = *reinterpret_cast<const float2*>(G + 2 * TC_KT + k);
-                    const float2 SLX = *reinterpret_cast<const float2*>(G + 3 * TC_KT + k);
-                    const float2 SLY = *reinterpret_cast<const float2*>(G + 4 * TC_KT + k);
-                    const float2 SLZ = *reinterpret_cast<const float2*>(G + 5 * TC_KT + k);
-                    const float2 MX = *reinterpret_cast<const float2*>(G + 6 * TC_KT + k);
-                    const float2 MY = *reinterpret_cast<const float2*>(G + 7 * TC_KT + k);
-                    const float2 MZ = *reinterpret_cast<const float2*>(G + 8 * TC_KT + k);
-                    const float2 dx = q2add(q2sub(TX, SX), q2sub(LX, SLX));
-                    const float2 dy = q2add(q2sub(TY, SY), q2sub(LY, SLY));
-                    const float2 dz = q2add(q2sub(TZ, SZ), q2sub(LZ, SLZ));
-                    const float2 r2 = q2fma(dx, dx, q2fma(dy, dy, q2fma(dz, dz, EPS)));
-                    const float2 b = make_float2(pow_(r2.x, -s_exp), pow_(r2.y, -s_exp));
-                    const float2 ir2 = make_float2(rcp_(r2.x), rcp_(r2.y));
-                    const float2 tS = q2mul(q2fma(NX, dx, q2fma(NY, dy, q2mul(NZ, dz))), ir2);
-                    const float2 tT = q2mul(q2fma(MX, dx, q2fma(MY, dy, q2mul(MZ, dz))), ir2);
-                    const float2 z = q2mul(q2mul(HALF, q2fma(tS, tS, q2mul(tT, tT))), b);
-                    const int s0 = sg0 + k, s1 = s0 + 1;
-                    const bool on0 = tv && s0 < nf && s0 != tg, on1 = tv && s1 < nf && s1 != tg;
-                    hB[2 * i] = on0 ? b.x : 0.f;
-                    hB[2 * i + 1] = on1 ? b.y : 0.f;
-                    h0[2 * i] = on0 ? z.x : 0.f;
-                    h0[2 * i + 1] = on1 ? z.y : 0.f;
+                    const int pp = 4 * sq + i;   // sources 2 pp, 2 pp + 1 of the tile, packed
+                    const ulonglong2 Q0 = G[5 * pp], Q1 = G[5 * pp + 1], Q2 = G[5 * pp + 2];
+                    unsigned long long dx, dy, dz;
+                    if (near) {
+                        const ulonglong2 Q3 = G[5 * pp + 3], Q4 = G[5 * pp + 4];
+                        wide_diff2<true>(TX, TY, TZ, Q0.x, Q0.y, Q1.x, LX, LY, LZ, Q3.x, Q3.y, Q4.x, dx, dy, dz);
+                    } else {
+                        wide_diff2<false>(TX, TY, TZ, Q0.x, Q0.y, Q1.x, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, dx, dy, dz);
+                    }
+                    wide_kernel2<true>(dx, dy, dz, NX, NY, NZ, Q1.y, Q2.x, Q2.y, EPS, NE, HALF, hBp[i], h0p[i]);
+                    if (special) {
+                        const int s0 = sg0 + 2 * pp, s1 = s0 + 1;
+                        const bool on0 = tv && s0 < nf && s0 != tg, on1 = tv && s1 < nf && s1 != tg;
+                        const float2 b = upk2(hBp[i]), z = upk2(h0p[i]);
+                        hBp[i] = pk2(on0 ? b.x : 0.f, on1 ? b.y : 0.f);
+                        h0p[i] = pk2(on0 ? z.x : 0.f, on1 ? z.y : 0.f);
+                    }
                 }
+                // TF32 splits: hi = the value with the 13 mantissa bits below TF32 cleared, lo = value - hi
+                constexpr unsigned long long HI = 0xffffe000ffffe000ull;
 #pragma unroll
                 for (int g = 0; g < 2; ++g) {
-                    float4 bh, bl, zh, zl;
-                    float* pbh = &bh.x; float* pbl = &bl.x; float* pzh = &zh.x; float* pzl = &zl.x;
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float x = hB[4 * g + e], y = h0[4 * g + e];
-                        pbh[e] = tc_tf32(x);
-                        pbl[e] = x - pbh[e];
-                        pzh[e] = tc_tf32(y);
-                        pzl[e] = y - pzh[e];
-                    }
+                    const unsigned long long b0 = hBp[2 * g], b1 = hBp[2 * g + 1], z0 = h0p[2 * g], z1 = h0p[2 * g + 1];
+                    const unsigned long long bh0 = b0 & HI, bh1 = b1 & HI, zh0 = z0 & HI, zh1 = z1 & HI;
+                    unsigned long long bl0, bl1, zl0, zl1;
+                    asm("sub.rn.f32x2 %0, %4, %8;\n\tsub.rn.f32x2 %1, %5, %9;\n\t"
+                        "sub.rn.f32x2 %2, %6, %10;\n\tsub.rn.f32x2 %3, %7, %11;"
+                        : "=l"(bl0), "=l"(bl1), "=l"(zl0), "=l"(zl1)
+                        : "l"(b0), "l"(b1), "l"(z0), "l"(z1), "l"(bh0), "l"(bh1), "l"(zh0), "l"(zh1));
                     const int off = tc_cm(t, 8 * sq + 4 * g);
-                    *reinterpret_cast<float4*>(H + 0 * TC_HMAT + off) = bh;
-                    *reinterpret_cast<float4*>(H + 1 * TC_HMAT + off) = bl;
-                    *reinterpret_cast<float4*>(H + 2 * TC_HMAT + off) = zh;
-                    *reinterpret_cast<float4*>(H + 3 * TC_HMAT + off) = zl;
+                    *reinterpret_cast<ulonglong2*>(H + 0 * TC_HMAT + off) = make_ulonglong2(bh0, bh1);
+                    *reinterpret_cast<ulonglong2*>(H + 1 * TC_HMAT + off) = make_ulonglong2(bl0, bl1);
+                    *reinterpret_cast<ulonglong2*>(H + 2 * TC_HMAT + off) = make_ulonglong2(zh0, zh1);
+                    *reinterpret_cast<ulonglong2*>(H + 3 * TC_HMAT + off) = make_ulonglong2(zl0, zl1);
                 }
             }
             // the warp's part of H(q) is written: visible to the tensor cores
@@ -1924,16 +1976,17 @@ static int launch_apply_tc(tp_mesh* m, const tp_params* p, const double* v, int 
                                                              m->wv32.as<float4>(), L::NW4);
         TP_LAUNCH_CHECK();
         const int npack = ntile * TC_KT * (L::NW4 + 1);
-        k_tc_pack<<<(npack + 255) / 256, 256, 0, st>>>(m->wv32.as<float4>(), fa, fl, fb, nf, ntile,
-                                                       m->tcbuf.as<unsigned char>());
+        k_tc_pack<<<(npack + 255) / 256, 256, 0, st>>>(m->wv32.as<float4>(), fa, fl, fb, m->tilebox.as<float4>(), nf,
+                                                       ntile, m->tcbuf.as<unsigned char>());
         TP_LAUNCH_CHECK();
         {
             const double units = (double)nf * (nf - 1);
             m->pairs += units;
             ProfScope ps(m, PK_APPLY_A, units, st);
             m->prof.cols[PK_APPLY_A] += 9;
-            k_apply_tc<<<dim3(g.bx, g.nsplit), TC_T, TC_SMEM, st>>>(fa, fb, fl, m->tcbuf.as<unsigned char>(), nf,
-                                                                   ntile, tps, (float)s, m->part.as<float2>(), err);
+            k_apply_tc<<<dim3(g.bx, g.nsplit), TC_T, TC_SMEM, st>>>(fa, fb, fl, m->tilebox.as<float4>(),
+                                                                   m->center.as<double>(), m->tcbuf.as<unsigned char>(),
+                                                                   nf, ntile, tps, (float)s, m->part.as<float2>(), err);
         }
         TP_LAUNCH_CHECK();
         double* sums = reinterpret_cast<double*>(m->part.as<float2>() + (size_t)g.nsplit * L::NA * nf);
