@@ -1563,11 +1563,13 @@ constexpr int TC_XH = 0, TC_XHL = 32 * TC_KT * 4, TC_XL = 2 * 32 * TC_KT * 4, TC
 constexpr int TC_G = TC_XLL + 16 * TC_KT * 4;
 constexpr int TC_BOX = TC_G + (TC_KT / 2) * 5 * 16;   // bounding box of the tile's 128-source chunk (2 float4)
 constexpr int TC_TILE_BYTES = TC_BOX + 32;            // 13600
-constexpr int TC_HMAT = 128 * TC_KT * 4;       // one 128 x KT FP32 operand
-constexpr int TC_HBUF = 4 * TC_HMAT;           // H_B hi, H_B lo, H_0 hi, H_0 lo
 constexpr int TC_NX = 3;                       // source tile buffers
-constexpr size_t TC_SMEM = 2 * (size_t)TC_HBUF + TC_NX * (size_t)TC_TILE_BYTES;
-constexpr int TC_TMEM_COLS = 512;              // two sets x three split products x 64 columns (32 high + 16 low)
+constexpr size_t TC_SMEM = TC_NX * (size_t)TC_TILE_BYTES;
+// tensor memory: accumulator sets at columns [0, 64) and [64, 128) (32 high + 16 low used each);
+// the H operands of the two tile buffers at [128, 256) and [256, 384): H_B hi, H_B lo, H_0 hi, H_0 lo,
+// KT = 32 columns each, one row (lane) per target
+constexpr int TC_HCOL = 128;
+constexpr int TC_TMEM_COLS = 512;
 constexpr unsigned long long TC_WAIT_NS = 1000000000ull;   // bound of each mbarrier wait (1 s)
 
 // byte offset of element (row, k) of a [rows][KT] K-major operand
@@ -1590,6 +1592,12 @@ __device__ __forceinline__ void tc_mma(unsigned d, unsigned long long a, unsigne
     asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                  "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
                  ::"r"(d), "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+// the same with A in tensor memory (address a)
+__device__ __forceinline__ void tc_mma_t(unsigned d, unsigned a, unsigned long long b, unsigned idesc, int acc) {
+    asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}"
+                 ::"r"(d), "r"(a), "l"(b), "r"(idesc), "r"(acc));
 }
 __device__ __forceinline__ unsigned long long tc_now() {
     unsigned long long t;
@@ -1721,8 +1729,7 @@ k_apply_tc(const float4* __restrict__ fa, const float4* __restrict__ fb, const f
         }
     }
     const int q0 = blockIdx.y * tiles_per_split, q1 = min(ntile, q0 + tiles_per_split), nt = max(0, q1 - q0);
-    unsigned char* Hb = tsm;                    // 2 x TC_HBUF
-    unsigned char* Xb = tsm + 2 * TC_HBUF;     // TC_NX x TC_TILE_BYTES
+    unsigned char* Xb = tsm;                    // TC_NX x TC_TILE_BYTES
     const unsigned mb_done = tc_smem(&mbar[0]), mb_full = tc_smem(&mbar[2]), mb_tile = tc_smem(&mbar[4]);
     if (warp == TC_CW) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(&s_taddr)),
@@ -1763,20 +1770,21 @@ k_apply_tc(const float4* __restrict__ fa, const float4* __restrict__ fb, const f
                 const int hb = q & 1;
                 if (!tc_wait(mb_full + 8 * hb, (q >> 1) & 1, abort, 256)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                // the three split products accumulate separately (independent MMA chains)
                 const int set = (q / TC_CHUNK) & 1;
-                const unsigned d0 = taddr + (unsigned)(set * 192);
-                const unsigned hbase = tc_smem(Hb + hb * TC_HBUF), xbase = tc_smem(Xb + (q % TC_NX) * TC_TILE_BYTES);
+                const unsigned dH = taddr + (unsigned)(set * 64), dL = dH + 32;
+                const unsigned ha = taddr + (unsigned)(TC_HCOL + hb * 128);   // H operands in tensor memory
+                const unsigned xbase = tc_smem(Xb + (q % TC_NX) * TC_TILE_BYTES);
 #pragma unroll
                 for (int kk = 0; kk < TC_KT / 8; ++kk) {
                     const unsigned o = kk * 256;
                     const int acc = ((q % TC_CHUNK) == 0 && kk == 0) ? 0 : 1;
-                    tc_mma(d0, tc_desc(hbase + 0 * TC_HMAT + o), tc_desc(xbase + TC_XH + o), idH, acc);
-                    tc_mma(d0 + 64, tc_desc(hbase + 0 * TC_HMAT + o), tc_desc(xbase + TC_XHL + o), idH, acc);
-                    tc_mma(d0 + 128, tc_desc(hbase + 1 * TC_HMAT + o), tc_desc(xbase + TC_XH + o), idH, acc);
-                    tc_mma(d0 + 32, tc_desc(hbase + 2 * TC_HMAT + o), tc_desc(xbase + TC_XL + o), idL, acc);
-                    tc_mma(d0 + 96, tc_desc(hbase + 2 * TC_HMAT + o), tc_desc(xbase + TC_XLL + o), idL, acc);
-                    tc_mma(d0 + 160, tc_desc(hbase + 3 * TC_HMAT + o), tc_desc(xbase + TC_XL + o), idL, acc);
+                    const unsigned ka = kk * 8;   // K columns of this step
+                    tc_mma_t(dH, ha + 0 * 32 + ka, tc_desc(xbase + TC_XH + o), idH, acc);
+                    tc_mma_t(dH, ha + 0 * 32 + ka, tc_desc(xbase + TC_XHL + o), idH, 1);
+                    tc_mma_t(dH, ha + 1 * 32 + ka, tc_desc(xbase + TC_XH + o), idH, 1);
+                    tc_mma_t(dL, ha + 2 * 32 + ka, tc_desc(xbase + TC_XL + o), idL, acc);
+                    tc_mma_t(dL, ha + 2 * 32 + ka, tc_desc(xbase + TC_XLL + o), idL, 1);
+                    tc_mma_t(dL, ha + 3 * 32 + ka, tc_desc(xbase + TC_XL + o), idL, 1);
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                              ::"r"(mb_done + 8 * hb) : "memory");
@@ -1810,24 +1818,18 @@ k_apply_tc(const float4* __restrict__ fa, const float4* __restrict__ fb, const f
 #pragma unroll
         for (int i = 0; i < 12; ++i) ks[i] = kc[i] = 0.f;
         auto drain = [&](int set) {
-            // the three split products of each column, added, then into the Kahan pairs
-            const unsigned base = taddr + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)(set * 192 + 12 * sq);
-            unsigned r[3][12];
-#pragma unroll
-            for (int pr = 0; pr < 3; ++pr) {
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                             : "=r"(r[pr][0]), "=r"(r[pr][1]), "=r"(r[pr][2]), "=r"(r[pr][3]), "=r"(r[pr][4]),
-                               "=r"(r[pr][5]), "=r"(r[pr][6]), "=r"(r[pr][7])
-                             : "r"(base + 64 * pr));
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                             : "=r"(r[pr][8]), "=r"(r[pr][9]), "=r"(r[pr][10]), "=r"(r[pr][11])
-                             : "r"(base + 64 * pr + 8));
-            }
+            const unsigned base = taddr + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)(set * 64 + 12 * sq);
+            unsigned r[12];
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                         : "r"(base));
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                         : "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11])
+                         : "r"(base + 8));
             asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
             for (int i = 0; i < 12; ++i) {   // Kahan
-                const float v = (__uint_as_float(r[0][i]) + __uint_as_float(r[1][i])) + __uint_as_float(r[2][i]);
-                const float y = v - kc[i];
+                const float y = __uint_as_float(r[i]) - kc[i];
                 const float s = ks[i] + y;
                 kc[i] = (s - ks[i]) - y;
                 ks[i] = s;
@@ -1838,9 +1840,9 @@ k_apply_tc(const float4* __restrict__ fa, const float4* __restrict__ fb, const f
             // this tile's sources, and the H buffer of tile q - 2 free
             tc_wait(mb_tile + 8 * (q % TC_NX), (q / TC_NX) & 1, abort);
             if (q >= 2) tc_wait(mb_done + 8 * hb, ((q - 2) >> 1) & 1, abort);
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (!*abort) {
                 const ulonglong2* G = reinterpret_cast<const ulonglong2*>(Xb + (q % TC_NX) * TC_TILE_BYTES + TC_G);
-                unsigned char* H = Hb + hb * TC_HBUF;
                 const int sg0 = (q0 + q) * TC_KT;
                 // tiles on the block's own rows (self pairs) or past nf take the masked path; tiles near
                 // the block's targets take the compensated differences (as in k_apply_wide)
@@ -1869,26 +1871,31 @@ k_apply_tc(const float4* __restrict__ fa, const float4* __restrict__ fb, const f
                         h0p[i] = pk2(on0 ? z.x : 0.f, on1 ? z.y : 0.f);
                     }
                 }
-                // TF32 splits: hi = the value with the 13 mantissa bits below TF32 cleared, lo = value - hi
+                // TF32 splits: hi = the value with the 13 mantissa bits below TF32 cleared, lo = value - hi;
+                // the thread's 8 K-columns of each operand into its row of tensor memory
                 constexpr unsigned long long HI = 0xffffe000ffffe000ull;
+                unsigned long long m[4][4];   // [operand][pair]
 #pragma unroll
-                for (int g = 0; g < 2; ++g) {
-                    const unsigned long long b0 = hBp[2 * g], b1 = hBp[2 * g + 1], z0 = h0p[2 * g], z1 = h0p[2 * g + 1];
-                    const unsigned long long bh0 = b0 & HI, bh1 = b1 & HI, zh0 = z0 & HI, zh1 = z1 & HI;
-                    unsigned long long bl0, bl1, zl0, zl1;
-                    asm("sub.rn.f32x2 %0, %4, %8;\n\tsub.rn.f32x2 %1, %5, %9;\n\t"
-                        "sub.rn.f32x2 %2, %6, %10;\n\tsub.rn.f32x2 %3, %7, %11;"
-                        : "=l"(bl0), "=l"(bl1), "=l"(zl0), "=l"(zl1)
-                        : "l"(b0), "l"(b1), "l"(z0), "l"(z1), "l"(bh0), "l"(bh1), "l"(zh0), "l"(zh1));
-                    const int off = tc_cm(t, 8 * sq + 4 * g);
-                    *reinterpret_cast<ulonglong2*>(H + 0 * TC_HMAT + off) = make_ulonglong2(bh0, bh1);
-                    *reinterpret_cast<ulonglong2*>(H + 1 * TC_HMAT + off) = make_ulonglong2(bl0, bl1);
-                    *reinterpret_cast<ulonglong2*>(H + 2 * TC_HMAT + off) = make_ulonglong2(zh0, zh1);
-                    *reinterpret_cast<ulonglong2*>(H + 3 * TC_HMAT + off) = make_ulonglong2(zl0, zl1);
+                for (int i = 0; i < 4; ++i) {
+                    const unsigned long long bh = hBp[i] & HI, zh = h0p[i] & HI;
+                    unsigned long long bl, zl;
+                    asm("sub.rn.f32x2 %0, %2, %4;\n\tsub.rn.f32x2 %1, %3, %5;"
+                        : "=l"(bl), "=l"(zl) : "l"(hBp[i]), "l"(h0p[i]), "l"(bh), "l"(zh));
+                    m[0][i] = bh; m[1][i] = bl; m[2][i] = zh; m[3][i] = zl;
                 }
+                const unsigned hrow = taddr + ((unsigned)((warp & 3) * 32) << 16) + (unsigned)(TC_HCOL + hb * 128 + 8 * sq);
+#pragma unroll
+                for (int op = 0; op < 4; ++op) {
+                    asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                                 ::"r"(hrow + 32 * op), "r"((unsigned)m[op][0]), "r"((unsigned)(m[op][0] >> 32)),
+                                   "r"((unsigned)m[op][1]), "r"((unsigned)(m[op][1] >> 32)), "r"((unsigned)m[op][2]),
+                                   "r"((unsigned)(m[op][2] >> 32)), "r"((unsigned)m[op][3]), "r"((unsigned)(m[op][3] >> 32))
+                                 : "memory");
+                }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             }
-            // the warp's part of H(q) is written: visible to the tensor cores
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            // the warp's part of H(q) is in tensor memory: ordered before the MMAs
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
             if (lane == 0 && !*abort) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mb_full + 8 * hb)
                                                    : "memory");
