@@ -1563,11 +1563,12 @@ constexpr int TC_XH = 0, TC_XHL = 32 * TC_KT * 4, TC_XL = 2 * 32 * TC_KT * 4, TC
 constexpr int TC_G = TC_XLL + 16 * TC_KT * 4;
 constexpr int TC_BOX = TC_G + (TC_KT / 2) * 5 * 16;   // bounding box of the tile's 128-source chunk (2 float4)
 constexpr int TC_TILE_BYTES = TC_BOX + 32;            // 13600
-constexpr int TC_NX = 3;                       // source tile buffers
+constexpr int TC_NX = 4;                       // source tile buffers
+constexpr int TC_NH = 3;                       // H operand buffers (tensor memory)
 constexpr size_t TC_SMEM = TC_NX * (size_t)TC_TILE_BYTES;
 // tensor memory: accumulator sets at columns [0, 64) and [64, 128) (32 high + 16 low used each);
-// the H operands of the two tile buffers at [128, 256) and [256, 384): H_B hi, H_B lo, H_0 hi, H_0 lo,
-// KT = 32 columns each, one row (lane) per target
+// the H operands of the three tile buffers at [128, 256), [256, 384), [384, 512): H_B hi, H_B lo,
+// H_0 hi, H_0 lo, KT = 32 columns each, one row (lane) per target
 constexpr int TC_HCOL = 128;
 constexpr int TC_TMEM_COLS = 512;
 constexpr unsigned long long TC_WAIT_NS = 1000000000ull;   // bound of each mbarrier wait (1 s)
@@ -1704,7 +1705,7 @@ k_apply_tc(const float4* __restrict__ fa, const float4* __restrict__ fb, const f
            int nf, int ntile, int tiles_per_split, float s_exp, float2* __restrict__ part, int* __restrict__ err) {
     constexpr int NA = OpLayout<TP_OP_A, 9>::NA;   // 38
     extern __shared__ __align__(1024) unsigned char tsm[];
-    __shared__ __align__(8) unsigned long long mbar[2 + 2 + TC_NX];
+    __shared__ __align__(8) unsigned long long mbar[2 * TC_NH + TC_NX];
     __shared__ unsigned s_taddr;
     __shared__ int s_abort;
     __shared__ float s_wb[4][6];   // bounding boxes of the block's targets, per warp of rows
@@ -1730,17 +1731,17 @@ k_apply_tc(const float4* __restrict__ fa, const float4* __restrict__ fb, const f
     }
     const int q0 = blockIdx.y * tiles_per_split, q1 = min(ntile, q0 + tiles_per_split), nt = max(0, q1 - q0);
     unsigned char* Xb = tsm;                    // TC_NX x TC_TILE_BYTES
-    const unsigned mb_done = tc_smem(&mbar[0]), mb_full = tc_smem(&mbar[2]), mb_tile = tc_smem(&mbar[4]);
+    const unsigned mb_done = tc_smem(&mbar[0]), mb_full = tc_smem(&mbar[TC_NH]), mb_tile = tc_smem(&mbar[2 * TC_NH]);
     if (warp == TC_CW) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_smem(&s_taddr)),
                      "r"(TC_TMEM_COLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_done));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_done + 8));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb_full), "r"(TC_CW));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb_full + 8), "r"(TC_CW));
+        for (int i = 0; i < TC_NH; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_done + 8 * i));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb_full + 8 * i), "r"(TC_CW));
+        }
         for (int i = 0; i < TC_NX; ++i) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb_tile + 8 * i));
         s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -1767,8 +1768,8 @@ k_apply_tc(const float4* __restrict__ fa, const float4* __restrict__ fb, const f
             const unsigned idH = (1u << 4) | (2u << 7) | (2u << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
             const unsigned idL = (1u << 4) | (2u << 7) | (2u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
             for (int q = 0; q < nt; ++q) {
-                const int hb = q & 1;
-                if (!tc_wait(mb_full + 8 * hb, (q >> 1) & 1, abort, 256)) break;
+                const int hb = q % TC_NH;
+                if (!tc_wait(mb_full + 8 * hb, (q / TC_NH) & 1, abort)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const int set = (q / TC_CHUNK) & 1;
                 const unsigned dH = taddr + (unsigned)(set * 64), dL = dH + 32;
@@ -1788,10 +1789,10 @@ k_apply_tc(const float4* __restrict__ fa, const float4* __restrict__ fb, const f
                 }
                 asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                              ::"r"(mb_done + 8 * hb) : "memory");
-                // refill the buffer of tile q - 1 with tile q + 2 once its products are done
-                if (q >= 1 && q + 2 < nt) {
-                    if (!tc_wait(mb_done + 8 * ((q - 1) & 1), ((q - 1) >> 1) & 1, abort)) break;
-                    issue_copy(q + 2);
+                // refill the buffer of tile q - 1 with tile q + TC_NX - 1 once its products are done
+                if (q >= 1 && q + TC_NX - 1 < nt) {
+                    if (!tc_wait(mb_done + 8 * ((q - 1) % TC_NH), ((q - 1) / TC_NH) & 1, abort)) break;
+                    issue_copy(q + TC_NX - 1);
                 }
             }
         }
@@ -1835,11 +1836,12 @@ k_apply_tc(const float4* __restrict__ fa, const float4* __restrict__ fb, const f
                 ks[i] = s;
             }
         };
+        int drained = 0;   // chunks read back
         for (int q = 0; q < nt; ++q) {
-            const int hb = q & 1;
-            // this tile's sources, and the H buffer of tile q - 2 free
+            const int hb = q % TC_NH;
+            // this tile's sources, and the H buffer of tile q - TC_NH free
             tc_wait(mb_tile + 8 * (q % TC_NX), (q / TC_NX) & 1, abort);
-            if (q >= 2) tc_wait(mb_done + 8 * hb, ((q - 2) >> 1) & 1, abort);
+            if (q >= TC_NH) tc_wait(mb_done + 8 * hb, ((q - TC_NH) / TC_NH) & 1, abort);
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             if (!*abort) {
                 const ulonglong2* G = reinterpret_cast<const ulonglong2*>(Xb + (q % TC_NX) * TC_TILE_BYTES + TC_G);
@@ -1899,17 +1901,24 @@ k_apply_tc(const float4* __restrict__ fa, const float4* __restrict__ fb, const f
             __syncwarp();
             if (lane == 0 && !*abort) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mb_full + 8 * hb)
                                                    : "memory");
-            // the previous chunk's accumulators, while this chunk's products run
-            if ((q % TC_CHUNK) == 0 && q > 0) {
-                const bool ok = __all_sync(0xffffffffu, tc_wait(mb_done + 8 * ((q - 1) & 1), ((q - 1) >> 1) & 1, abort));
+            // the previous chunk's accumulators, one tile after its last product was issued: the wait is
+            // for tile q - 2, and no later product on that barrier can have completed yet (it needs
+            // this warp's arrival for tile q + 1), so its phase is the one waited for
+            if ((q % TC_CHUNK) == 1 && q > TC_CHUNK) {
+                const bool ok = __all_sync(0xffffffffu, tc_wait(mb_done + 8 * ((q - 2) % TC_NH), ((q - 2) / TC_NH) & 1, abort));
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                if (ok) drain(((q / TC_CHUNK) - 1) & 1);
+                if (ok) drain(drained & 1);
+                ++drained;
             }
         }
-        if (nt > 0) {
-            const bool ok = __all_sync(0xffffffffu, tc_wait(mb_done + 8 * ((nt - 1) & 1), ((nt - 1) >> 1) & 1, abort));
+        // the remaining chunks (their last tiles are among the last three, so no later product
+        // shares their barrier phases)
+        const int nchunk = (nt + TC_CHUNK - 1) / TC_CHUNK;
+        for (; drained < nchunk; ++drained) {
+            const int last = min(TC_CHUNK * drained + TC_CHUNK - 1, nt - 1);
+            const bool ok = __all_sync(0xffffffffu, tc_wait(mb_done + 8 * (last % TC_NH), (last / TC_NH) & 1, abort));
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            if (ok) drain(((nt - 1) / TC_CHUNK) & 1);
+            if (ok) drain(drained & 1);
         }
         const bool bad = *abort != 0;
         if (tv) {
