@@ -567,6 +567,42 @@ def willmore_steps(tp, dev, steps=2, weight=100.0):
             "E_before": reps[0]["E_before"], "E_after": reps[0]["E_after"], "status": [r["status"] for r in reps]}
 
 
+def tensor_core_apply(tp, dev, reps=5):
+    """The 9-column A apply on torus_20k with its accumulation on tcgen05
+    tensor cores (tensor_cores = 1: split TF32 products, FP32 accumulators in
+    tensor memory, compensated read-back every 128 sources) beside the
+    CUDA-core kernel (the step's default): kernel time per launch, the
+    algorithmic FP32 rate (102 flop per pair, as apply_A), and the relative
+    difference of the two results."""
+    import numpy as np
+    import torch
+    from synth import vertex_vectors, workload
+    V, F = workload(WORKLOAD)
+    out = {"workload": WORKLOAD, "columns": 9}
+    with tp.Mesh(torch.tensor(V, dtype=torch.float64, device=dev),
+                 torch.tensor(F, dtype=torch.int32, device=dev), device=dev.index or 0) as m:
+        u = torch.tensor(vertex_vectors(len(V), 9, 11), dtype=torch.float64, device=dev)
+        ys = {}
+        for name, tc in (("cuda_cores", 0), ("tensor_cores", 1)):
+            pp = tp.params(tensor_cores=tc)
+            ys[name] = tp.fractional_apply(m, "A", u, pp).cpu().numpy()
+            torch.cuda.synchronize()
+            tp.tp_profile_read(m)
+            tp.tp_profile_enable(m, True)
+            for _ in range(reps):
+                tp.fractional_apply(m, "A", u, pp)
+            torch.cuda.synchronize()
+            d = tp.tp_profile_read(m)["apply_A"]
+            tp.tp_profile_enable(m, False)
+            ms = d["ms"] / d["launches"]
+            pairs = d["units"] / d["launches"]
+            out[name] = {"ms_per_launch": ms,
+                         "tflops": APPLY_FLOPS["apply_A"](9) * pairs / (ms / 1e3) / 1e12}
+        a, b = ys["tensor_cores"], ys["cuda_cores"]
+        out["rel_difference"] = float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    return out
+
+
 def accuracy(tp, dev):
     """Errors on torus_20k against the FP64 oracle, from stored oracle values
     (tests/golden: the energy, and dE and A u (u = 3 seeded N(0,1) columns)
@@ -858,6 +894,7 @@ def gpu_arm(args):
     if not args.no_large:
         line["large_mesh"] = large_mesh(tp, dev)
         line["accuracy"] = accuracy(tp, dev)
+        line["tensor_core_apply"] = tensor_core_apply(tp, dev)
         line["serving"] = serving(tp, dev, n=args.serve_n, slots=args.serve_slots)
         line["obstacle"] = obstacle_scene(tp, dev)
         line["pins"] = pinned_steps(tp, dev)
@@ -1036,6 +1073,8 @@ def main():
                     help="report only the errors on torus_20k against stored oracle values instead")
     ap.add_argument("--willmore", action="store_true",
                     help="run only the Willmore steps (torus_20k, weight 100) instead")
+    ap.add_argument("--tensor-cores", action="store_true",
+                    help="run only the tensor-core A apply beside the CUDA-core one (torus_20k) instead")
     ap.add_argument("--serve-n", type=int, default=512)
     ap.add_argument("--serve-fmax", type=int, default=200000)
     ap.add_argument("--serve-slots", type=int, default=4)
@@ -1075,6 +1114,12 @@ def main():
         import paper_2107_01664_gb300 as tp
         torch.cuda.set_device(0)
         print(json.dumps({"willmore": willmore_steps(tp, torch.device("cuda", 0))}))
+        return
+    if args.tensor_cores:
+        import torch
+        import paper_2107_01664_gb300 as tp
+        torch.cuda.set_device(0)
+        print(json.dumps({"tensor_core_apply": tensor_core_apply(tp, torch.device("cuda", 0))}))
         return
     if args.impl == "reference":
         reference_arm(args)
