@@ -1486,33 +1486,6 @@ k_bh_diff_list(const float4* __restrict__ node4, const float4* __restrict__ node
 }
 
 
-// sums of eight values over the warp: lane l ends with the sum of value
-// l >> 2 (9 shuffles instead of 8 x 5)
-__device__ __forceinline__ float warp_sum8(const float (&v)[8]) {
-    const int lane = threadIdx.x & 31;
-    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
-    float k[4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float keep = b4 ? v[4 + i] : v[i], send = b4 ? v[i] : v[4 + i];
-        k[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-    }
-    float m[2];
-#pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const float keep = b3 ? k[2 + i] : k[i], send = b3 ? k[i] : k[2 + i];
-        m[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-    }
-    float r;
-    {
-        const float keep = b2 ? m[1] : m[0], send = b2 ? m[0] : m[1];
-        r = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-    }
-    r += __shfl_xor_sync(0xffffffffu, r, 2);
-    r += __shfl_xor_sync(0xffffffffu, r, 1);
-    return r;
-}
-
 // bit `lane` of each half of a packed mask pair, spread over the half
 // (all ones where set, zero where not): sh = 31 - lane
 __device__ __forceinline__ unsigned long long lane_bits2(float2 m, unsigned sh) {
@@ -1535,10 +1508,14 @@ __device__ __forceinline__ float2 q2and(float2 a, unsigned long long m) {
 // k_bh_diff_list for p = 6 over staged batches of source pairs (as the
 // energy): the target side as in k_bh_diff_list, two sources per packed
 // instruction; lanes outside an entry's mask get c = K = 0 by a bit mask.
-// FULL: the source sides of both sources of a pair are summed over the warp
-// together (warp_sum8) and added with one FP64 atomic per source and
-// component (node accumulators in far batches, face accumulators in near
-// batches).
+// FULL: every lane stores the source sides (G, Q) of both sources of a pair
+// in its own row of a per-warp table; after 8 pairs (16 sources) lane l sums
+// rows 2l and 2l + 1 of the table's columns over the 32 targets and adds them
+// with two FP64 atomics (node accumulators in far batches, face accumulators
+// in near batches): a transpose through shared memory instead of a shuffle
+// reduction per pair and one atomic per source and component.
+constexpr int BHD_CHUNK = 8;                     // source pairs per table flush
+constexpr int BHD_RS = 8 * BHD_CHUNK + 4;        // row stride in floats (16-byte rows, no bank conflicts)
 template <bool FULL>
 __global__ void __launch_bounds__(128, 5)
 k_bh_diff_list2(const float4* __restrict__ node4, const float4* __restrict__ nodelo, const float4* __restrict__ sa,
@@ -1547,6 +1524,7 @@ k_bh_diff_list2(const float4* __restrict__ node4, const float4* __restrict__ nod
                 unsigned long long* __restrict__ count) {
     __shared__ float4 sH[4][32], sD[4][32];
     __shared__ int sI[4][32];
+    __shared__ __align__(16) float sR[FULL ? 4 * 32 * BHD_RS : 4];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int g = blockIdx.x * 4 + w;
     if (g >= L.ngroups) return;
@@ -1558,6 +1536,7 @@ k_bh_diff_list2(const float4* __restrict__ node4, const float4* __restrict__ nod
     const float2 TX = q2(A.x), TY = q2(A.y), TZ = q2(A.z), UX = q2(Al.x), UY = q2(Al.y), UZ = q2(Al.z);
     const float2 NX = q2(B.x), NY = q2(B.y), NZ = q2(B.z), EPS2 = q2(1e-18f);
     const float2 S1 = q2(-aS * p), S2 = q2(2.f * aS * p), AS = q2(aS);
+    float* R = sR + (FULL ? w * 32 * BHD_RS : 0);
     const unsigned sh = 31u - (unsigned)lane;
     float4* H = sH[w];
     float4* D = sD[w];
@@ -1579,40 +1558,67 @@ k_bh_diff_list2(const float4* __restrict__ node4, const float4* __restrict__ nod
         double* sacc = b < Bt.nbf ? nacc : facc;
         __syncwarp();
         const int np = (Bt.count(b, L.leaf) + 1) >> 1;
-        for (int q = 0; q < np; ++q) {
-            const float4 h0 = H[2 * q], h1 = H[2 * q + 1], d0 = D[2 * q], d1 = D[2 * q + 1];
-            const unsigned long long mm = lane_bits2(make_float2(d1.z, d1.w), sh);
-            const float2 dx = q2add(q2sub(TX, make_float2(h0.x, h0.y)), q2sub(UX, make_float2(d0.x, d0.y)));
-            const float2 dy = q2add(q2sub(TY, make_float2(h0.z, h0.w)), q2sub(UY, make_float2(d0.z, d0.w)));
-            const float2 dz = q2add(q2sub(TZ, make_float2(h1.x, h1.y)), q2sub(UZ, make_float2(d1.x, d1.y)));
-            const float2 W = make_float2(h1.z, h1.w);
-            const float2 r2 = q2fma(dx, dx, q2fma(dy, dy, q2fma(dz, dz, EPS2)));
-            const float2 u = q2fma(NX, dx, q2fma(NY, dy, q2mul(NZ, dz)));
-            const float2 ir2 = make_float2(frcp(r2.x), frcp(r2.y));
-            const float2 ir4 = q2mul(ir2, ir2);
-            const float2 qq = q2mul(q2mul(u, u), ir4);
-            const float2 mq = q2mul(qq, qq);
-            const float2 K = q2and(q2mul(mq, qq), mm);
-            const float2 c = q2and(q2mul(q2mul(mq, u), ir4), mm);
-            const float2 wc = q2mul(W, c), wK = q2mul(W, K), wKd = q2mul(wK, ir2);
-            pt[0] = q2add(pt[0], wc);
-            pt[1] = q2fma(wc, dx, pt[1]);
-            pt[2] = q2fma(wc, dy, pt[2]);
-            pt[3] = q2fma(wc, dz, pt[3]);
-            pt[4] = q2fma(wKd, dx, pt[4]);
-            pt[5] = q2fma(wKd, dy, pt[5]);
-            pt[6] = q2fma(wKd, dz, pt[6]);
-            pt[7] = q2add(pt[7], wK);
+        for (int q0 = 0; q0 < np; q0 += BHD_CHUNK) {
+            const int nq = min(BHD_CHUNK, np - q0);
+            for (int t = 0; t < nq; ++t) {
+                const int q = q0 + t;
+                const float4 h0 = H[2 * q], h1 = H[2 * q + 1], d0 = D[2 * q], d1 = D[2 * q + 1];
+                const unsigned long long mm = lane_bits2(make_float2(d1.z, d1.w), sh);
+                const float2 dx = q2add(q2sub(TX, make_float2(h0.x, h0.y)), q2sub(UX, make_float2(d0.x, d0.y)));
+                const float2 dy = q2add(q2sub(TY, make_float2(h0.z, h0.w)), q2sub(UY, make_float2(d0.z, d0.w)));
+                const float2 dz = q2add(q2sub(TZ, make_float2(h1.x, h1.y)), q2sub(UZ, make_float2(d1.x, d1.y)));
+                const float2 W = make_float2(h1.z, h1.w);
+                const float2 r2 = q2fma(dx, dx, q2fma(dy, dy, q2fma(dz, dz, EPS2)));
+                const float2 u = q2fma(NX, dx, q2fma(NY, dy, q2mul(NZ, dz)));
+                const float2 ir2 = make_float2(frcp(r2.x), frcp(r2.y));
+                const float2 ir4 = q2mul(ir2, ir2);
+                const float2 qq = q2mul(q2mul(u, u), ir4);
+                const float2 mq = q2mul(qq, qq);
+                const float2 K = q2and(q2mul(mq, qq), mm);
+                const float2 c = q2and(q2mul(q2mul(mq, u), ir4), mm);
+                const float2 wc = q2mul(W, c), wK = q2mul(W, K), wKd = q2mul(wK, ir2);
+                pt[0] = q2add(pt[0], wc);
+                pt[1] = q2fma(wc, dx, pt[1]);
+                pt[2] = q2fma(wc, dy, pt[2]);
+                pt[3] = q2fma(wc, dz, pt[3]);
+                pt[4] = q2fma(wKd, dx, pt[4]);
+                pt[5] = q2fma(wKd, dy, pt[5]);
+                pt[6] = q2fma(wKd, dz, pt[6]);
+                pt[7] = q2add(pt[7], wK);
+                if (FULL) {
+                    const float2 s1 = q2mul(S1, wc), s2 = q2mul(S2, wKd);
+                    const float2 G0 = q2fma(s2, dx, q2mul(s1, NX)), G1 = q2fma(s2, dy, q2mul(s1, NY)),
+                                 G2 = q2fma(s2, dz, q2mul(s1, NZ));
+                    const float2 Q = q2mul(AS, K);
+                    // row `lane`, columns 8 t .. 8 t + 7: (G, Q) of sources 2 q and 2 q + 1
+                    float4* row = reinterpret_cast<float4*>(R + lane * BHD_RS + 8 * t);
+                    row[0] = make_float4(G0.x, G1.x, G2.x, Q.x);
+                    row[1] = make_float4(G0.y, G1.y, G2.y, Q.y);
+                }
+            }
             if (FULL) {
-                const float2 s1 = q2mul(S1, wc), s2 = q2mul(S2, wKd);
-                const float2 G0 = q2fma(s2, dx, q2mul(s1, NX)), G1 = q2fma(s2, dy, q2mul(s1, NY)),
-                             G2 = q2fma(s2, dz, q2mul(s1, NZ));
-                const float2 Q = q2mul(AS, K);
-                const float v[8] = {G0.x, G1.x, G2.x, Q.x, G0.y, G1.y, G2.y, Q.y};
-                const float r = warp_sum8(v);
-                const int vi = lane >> 2;             // value: source vi >> 2 of the pair, component vi & 3
-                const int idx = I[2 * q + (vi >> 2)];
-                if ((lane & 3) == 0 && idx >= 0) atomicAdd(sacc + 4 * idx + (vi & 3), f2d_int(r));
+                // column pair (2 lane, 2 lane + 1) = source 2 q0 + (lane >> 1),
+                // components 2 (lane & 1) and 2 (lane & 1) + 1, summed over the rows
+                __syncwarp();
+                const float2* col = reinterpret_cast<const float2*>(R) + lane;
+                float2 c0 = col[0], c1 = col[BHD_RS / 2], c2 = col[BHD_RS], c3 = col[3 * BHD_RS / 2];
+#pragma unroll
+                for (int k = 4; k < 32; k += 4) {
+                    const float2* ck = col + k * (BHD_RS / 2);
+                    c0 = q2add(c0, ck[0]);
+                    c1 = q2add(c1, ck[BHD_RS / 2]);
+                    c2 = q2add(c2, ck[BHD_RS]);
+                    c3 = q2add(c3, ck[3 * BHD_RS / 2]);
+                }
+                const float2 sum = q2add(q2add(c0, c1), q2add(c2, c3));
+                const int src = lane >> 1;
+                const int idx = src < 2 * nq ? I[2 * q0 + src] : -1;
+                if (idx >= 0) {
+                    double* dst = sacc + 4 * idx + 2 * (lane & 1);
+                    atomicAdd(dst, f2d_int(sum.x));
+                    atomicAdd(dst + 1, f2d_int(sum.y));
+                }
+                __syncwarp();
             }
         }
 #pragma unroll
@@ -1722,6 +1728,15 @@ int diff_adjoints_bh(tp_mesh* m, const tp_params* p, double* adj, double* erow, 
         const float pf = (float)p->p;
         const float4* n4 = reinterpret_cast<const float4*>(node);
         const int blocks = (L.ngroups + 3) / 4;
+        static bool carveout_set[64] = {false};
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (full && dev >= 0 && dev < 64 && !carveout_set[dev]) {
+            // five blocks of 39 KB (the source-side tables) per SM
+            TP_CUDA(cudaFuncSetAttribute((const void*)k_bh_diff_list2<true>,
+                                         cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+            carveout_set[dev] = true;
+        }
         if (p->p == 6.0) {
             if (full) k_bh_diff_list2<true><<<blocks, 128, 0, st>>>(n4, nodelo, sa, sb, sl, nf, L, pf, tacc, nacc, facc, cnt);
             else k_bh_diff_list2<false><<<blocks, 128, 0, st>>>(n4, nodelo, sa, sb, sl, nf, L, pf, tacc, nacc, facc, cnt);

@@ -727,6 +727,7 @@ constexpr int DOT_T = 256;
 constexpr int DOT_MAXV = 128;
 constexpr int DOT_CH = 8;   // dot products accumulated per pass over the elements
 constexpr int DOT_PAIRS_MAX = 512;
+constexpr int DOT_SL_MAX = 64;   // element slices of k_multidot
 
 struct PtrList {
     const double* p[DOT_MAXV];
@@ -735,9 +736,9 @@ struct CoefList {
     double c[DOT_MAXV];
 };
 
-// part[blockIdx.x][j] = sum over this block's elements of xs[j][i] * ys[j][i].
-// Each thread owns one element per grid stride and accumulates DOT_CH
-// products at a time; the block sums fold across the warp (P-1 additions
+// Block (b, e) takes the DOT_CH pairs j0 = b DOT_CH, ... over the elements of
+// slice e (gridDim.y slices): part[e][j] = sum over the slice of
+// xs[j][i] * ys[j][i]. The block sums fold across the warp (P-1 additions
 // for P values) and then across warps, always in the same order.
 __global__ void __launch_bounds__(DOT_T)
 k_multidot(PtrList xs, PtrList ys, int nvec, size_t n, double* __restrict__ part, double* __restrict__ out,
@@ -745,11 +746,16 @@ k_multidot(PtrList xs, PtrList ys, int nvec, size_t n, double* __restrict__ part
     __shared__ double wsum[DOT_CH][DOT_T / 32];
     __shared__ bool last;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int j0 = 0; j0 < nvec; j0 += DOT_CH) {
+    const int j0 = blockIdx.x * DOT_CH;
+    const int nsl = gridDim.y;
+    const size_t per = (n + nsl - 1) / nsl;
+    const size_t i0 = (size_t)blockIdx.y * per, i1 = i0 + per < n ? i0 + per : n;
+    {
         double acc[DOT_CH];
 #pragma unroll
         for (int c = 0; c < DOT_CH; ++c) acc[c] = 0.0;
-        for (size_t i = (size_t)blockIdx.x * DOT_T + threadIdx.x; i < n; i += (size_t)gridDim.x * DOT_T) {
+#pragma unroll 2
+        for (size_t i = i0 + threadIdx.x; i < i1; i += DOT_T) {
 #pragma unroll
             for (int c = 0; c < DOT_CH; ++c)
                 if (j0 + c < nvec) acc[c] += xs.p[j0 + c][i] * ys.p[j0 + c][i];
@@ -780,38 +786,58 @@ k_multidot(PtrList xs, PtrList ys, int nvec, size_t n, double* __restrict__ part
             double s = 0.0;
 #pragma unroll
             for (int q = 0; q < DOT_T / 32; ++q) s += wsum[threadIdx.x][q];
-            part[(size_t)blockIdx.x * nvec + j0 + threadIdx.x] = s;
+            part[(size_t)blockIdx.y * nvec + j0 + threadIdx.x] = s;
         }
-        __syncthreads();
     }
     // the last block to finish adds the block sums in block order (the
     // result does not depend on which block that is) and resets the ticket
+    __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
-        last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+        last = atomicAdd(ticket, 1u) == gridDim.x * gridDim.y - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
-    for (int j = threadIdx.x; j < nvec; j += DOT_T) {
+    // pair j's slices in four quarters of DOT_SL_MAX / 4 (one thread each,
+    // its loads issued before the first addition), then the quarters in order
+    __shared__ double fin[4 * DOT_MAXV];
+    constexpr int QS = DOT_SL_MAX / 4;
+    for (int id = threadIdx.x; id < 4 * nvec; id += DOT_T) {
+        const int j = id >> 2, e0 = (id & 3) * QS;
+        double v[QS];
+#pragma unroll
+        for (int e = 0; e < QS; ++e) v[e] = e0 + e < nsl ? __ldcg(part + (size_t)(e0 + e) * nvec + j) : 0.0;
         double s = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) s += __ldcg(part + (size_t)b * nvec + j);
-        out[j] = s;
+#pragma unroll
+        for (int e = 0; e < QS; ++e) s += v[e];
+        fin[id] = s;
     }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nvec; j += DOT_T)
+        out[j] = ((fin[4 * j] + fin[4 * j + 1]) + fin[4 * j + 2]) + fin[4 * j + 3];
     if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// element slices of the dot kernels: about 512 elements per block (two per
+// thread and pair, so that a thread's loads are in flight together), at most
+// eight blocks per SM over all pair chunks, at most DOT_SL_MAX
+static int dot_slices(size_t n, int nvec) {
+    const int chunks = (nvec + DOT_CH - 1) / DOT_CH;
+    const long want = (long)((n + 511) / 512);
+    const long cap = std::max(1L, std::min<long>(DOT_SL_MAX, 8L * sm_count() / chunks));
+    return (int)std::max(1L, std::min(want, cap));
 }
 
 // out_host[j] = xs[j] . ys[j] (FP64, n elements each), one host sync
 int dot_pairs(tp_mesh* m, const double* const* xs, const double* const* ys, int nvec, size_t n, double* out_host,
               cudaStream_t st) {
     if (nvec < 1 || nvec > DOT_PAIRS_MAX) return fail(TP_ERR_INVALID_ARG, "dots: too many vectors");
-    int nblk = (int)std::min<size_t>((n + DOT_T - 1) / DOT_T, (size_t)sm_count());
-    if (nblk < 1) nblk = 1;
-    TP_TRY(ensure(m->part2, sizeof(double) * ((size_t)nblk * DOT_MAXV + DOT_PAIRS_MAX)));
+    TP_TRY(ensure(m->part2, sizeof(double) * ((size_t)DOT_SL_MAX * DOT_MAXV + DOT_PAIRS_MAX)));
     double* part = m->part2.as<double>();
     unsigned* tk = nullptr;
     TP_TRY(mesh_tickets(m, &tk, st));
-    double* out = part + (size_t)nblk * DOT_MAXV;
+    double* out = part + (size_t)DOT_SL_MAX * DOT_MAXV;
     for (int j0 = 0; j0 < nvec; j0 += DOT_MAXV) {
         const int nc = std::min(DOT_MAXV, nvec - j0);
         PtrList px, py;
@@ -819,7 +845,8 @@ int dot_pairs(tp_mesh* m, const double* const* xs, const double* const* ys, int 
             px.p[j] = xs[j0 + j];
             py.p[j] = ys[j0 + j];
         }
-        k_multidot<<<nblk, DOT_T, 0, st>>>(px, py, nc, n, part, out + j0, tk + TICKET_DOTS);
+        const dim3 grid((nc + DOT_CH - 1) / DOT_CH, dot_slices(n, nc));
+        k_multidot<<<grid, DOT_T, 0, st>>>(px, py, nc, n, part, out + j0, tk + TICKET_DOTS);
         TP_LAUNCH_CHECK();
     }
     TP_CUDA(cudaMemcpyAsync(out_host, out, sizeof(double) * nvec, cudaMemcpyDeviceToHost, st));
@@ -832,9 +859,7 @@ int dot_pairs(tp_mesh* m, const double* const* xs, const double* const* ys, int 
 int dot_pairs_dev(tp_mesh* m, const double* const* xs, const double* const* ys, int nvec, size_t n, double* out_dev,
                   cudaStream_t st) {
     if (nvec < 1 || nvec > DOT_PAIRS_MAX) return fail(TP_ERR_INVALID_ARG, "dots: too many vectors");
-    int nblk = (int)std::min<size_t>((n + DOT_T - 1) / DOT_T, (size_t)sm_count());
-    if (nblk < 1) nblk = 1;
-    TP_TRY(ensure(m->part2, sizeof(double) * ((size_t)nblk * DOT_MAXV + DOT_PAIRS_MAX)));
+    TP_TRY(ensure(m->part2, sizeof(double) * ((size_t)DOT_SL_MAX * DOT_MAXV + DOT_PAIRS_MAX)));
     double* part = m->part2.as<double>();
     unsigned* tk = nullptr;
     TP_TRY(mesh_tickets(m, &tk, st));
@@ -845,7 +870,8 @@ int dot_pairs_dev(tp_mesh* m, const double* const* xs, const double* const* ys, 
             px.p[j] = xs[j0 + j];
             py.p[j] = ys[j0 + j];
         }
-        k_multidot<<<nblk, DOT_T, 0, st>>>(px, py, nc, n, part, out_dev + j0, tk + TICKET_DOTS);
+        const dim3 grid((nc + DOT_CH - 1) / DOT_CH, dot_slices(n, nc));
+        k_multidot<<<grid, DOT_T, 0, st>>>(px, py, nc, n, part, out_dev + j0, tk + TICKET_DOTS);
         TP_LAUNCH_CHECK();
     }
     return TP_OK;

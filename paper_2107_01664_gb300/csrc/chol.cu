@@ -697,6 +697,34 @@ k_chol_sweep(SweepArgs A) {
     }
 }
 
+// sums over the T threads of a block of K per-thread FP64 values, in a fixed
+// order through shared memory sh [K * T] (16 partial sums per column, then
+// their sum): thread j < K returns the sum of column j, the others 0. Fewer
+// FP64 additions than a shuffle tree per column (the FP64 pipe is narrow).
+template <int K, int T>
+__device__ __forceinline__ double block_colsum_f64(const double (&acc)[K], double* sh) {
+    constexpr int P = 16;
+    static_assert(K * P <= T, "one thread per partial sum");
+    const int t = threadIdx.x;
+#pragma unroll
+    for (int j = 0; j < K; ++j) sh[j * T + t] = acc[j];
+    __syncthreads();
+    double s = 0.0;
+    if (t < K * P) {
+        const int j = t / P, q = t - j * P;
+#pragma unroll
+        for (int i = q; i < T; i += P) s += sh[j * T + i];
+    }
+    __syncthreads();
+    if (t < K * P) sh[t] = s;
+    __syncthreads();
+    double v = 0.0;
+    if (t < K)
+#pragma unroll
+        for (int q = 0; q < P; ++q) v += sh[t * P + q];
+    return v;
+}
+
 // The start of a solve in one launch: bp = b minus its per-component means
 // (mean, from k_comp_mean), x = 0, r = bp, per-block partials of |bp|^2;
 // the last block to finish (completion ticket) adds the partials in block
@@ -707,7 +735,7 @@ __global__ void __launch_bounds__(CHR_T)
 k_chol_start(const double* __restrict__ b, const double* __restrict__ mean, const int* __restrict__ comp_of, int nv,
              double* __restrict__ bp, double* __restrict__ x, double* __restrict__ r, double* __restrict__ part,
              unsigned* __restrict__ ticket, CholCtl* __restrict__ ctl) {
-    __shared__ double sh[CHR_T / 32][K];
+    __shared__ double sh[K * CHR_T];
     __shared__ bool last;
     double acc[K];
 #pragma unroll
@@ -725,18 +753,8 @@ k_chol_start(const double* __restrict__ b, const double* __restrict__ mean, cons
         }
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int c = 0; c < K; ++c) {
-        double v = acc[c];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sh[w][c] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < K) {
-        double s = 0.0;
-        for (int i = 0; i < CHR_T / 32; ++i) s += sh[i][threadIdx.x];
-        part[(size_t)blockIdx.x * K + threadIdx.x] = s;
-    }
+    const double bs = block_colsum_f64<K, CHR_T>(acc, sh);
+    if (threadIdx.x < K) part[(size_t)blockIdx.x * K + threadIdx.x] = bs;
     __syncthreads();
     if (threadIdx.x == 0) {
         __threadfence();
@@ -770,13 +788,13 @@ k_chol_start(const double* __restrict__ b, const double* __restrict__ mean, cons
 // sums slice s of component c's vertex list (CH_MSPLIT slices), then the
 // last block to finish adds every component's slices in order (and, given
 // dflags, records the state of the deferred solve that produced x)
-constexpr int CH_MSPLIT = 16;
+constexpr int CH_MSPLIT = 48;   // about one vertex per thread on 10k-vertex meshes
 
 __global__ void __launch_bounds__(256)
 k_comp_mean(const int* __restrict__ comp_ptr, const int* __restrict__ comp_verts, const double* __restrict__ x,
             int k, double* __restrict__ part, double* __restrict__ mean, unsigned* __restrict__ ticket,
             const CholCtl* __restrict__ ctl, int* __restrict__ dflags) {
-    __shared__ double sh[256 / 32][CH_KMAX];
+    __shared__ double sh[CH_KMAX * 256];
     __shared__ bool last;
     const int c = blockIdx.x, s = blockIdx.y;
     const int v0 = comp_ptr[c], v1 = comp_ptr[c + 1];
@@ -792,18 +810,8 @@ k_comp_mean(const int* __restrict__ comp_ptr, const int* __restrict__ comp_verts
             if (j < k) acc[j] += xv[j];
     }
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-    for (int j = 0; j < CH_KMAX; ++j) {
-        double v = acc[j];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sh[w][j] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < k) {
-        double t = 0.0;
-        for (int q = 0; q < 256 / 32; ++q) t += sh[q][threadIdx.x];
-        part[((size_t)c * CH_MSPLIT + s) * k + threadIdx.x] = t;
-    }
+    const double bs = block_colsum_f64<CH_KMAX, 256>(acc, sh);
+    if (threadIdx.x < k) part[((size_t)c * CH_MSPLIT + s) * k + threadIdx.x] = bs;
     // the last block to finish adds each component's slices in order and
     // resets the ticket
     __syncthreads();
@@ -814,12 +822,15 @@ k_comp_mean(const int* __restrict__ comp_ptr, const int* __restrict__ comp_verts
     __syncthreads();
     if (!last) return;
     __threadfence();
+    // one warp per (component, column): lane l takes slices l, l + 32, then
+    // a fixed shuffle tree
     const int ncomp = gridDim.x;
-    for (int e = threadIdx.x; e < ncomp * k; e += blockDim.x) {
+    for (int e = w; e < ncomp * k; e += 256 / 32) {
         const int cc = e / k, j = e - cc * k;
         double t = 0.0;
-        for (int q = 0; q < CH_MSPLIT; ++q) t += __ldcg(part + ((size_t)cc * CH_MSPLIT + q) * k + j);
-        mean[(size_t)cc * k + j] = t / (double)(comp_ptr[cc + 1] - comp_ptr[cc]);
+        for (int q = lane; q < CH_MSPLIT; q += 32) t += __ldcg(part + ((size_t)cc * CH_MSPLIT + q) * k + j);
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) mean[(size_t)cc * k + j] = t / (double)(comp_ptr[cc + 1] - comp_ptr[cc]);
     }
     if (threadIdx.x == 0) {
         *ticket = 0u;

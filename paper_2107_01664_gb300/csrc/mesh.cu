@@ -132,49 +132,65 @@ int copy_out(void* dst, const void* src, size_t bytes, int ptr_kind, cudaStream_
 
 static constexpr int kSumThreads = 256;
 
-// Block b sums rows [b * rows_per_block, ...) of each column into
-// part[b][c]; the last block to finish (completion ticket) adds the block
-// sums in block order into out[c] (times scale) and puts the ticket back to
-// zero, so the result does not depend on which block finished last.
-__global__ void k_colsum(const double* __restrict__ x, long n, int k, int rows_per_block, double* __restrict__ part,
-                         double scale, double* __restrict__ out, unsigned* __restrict__ ticket) {
+// Block b sums rows [b * rows_per_block, ...) of every column into
+// part[b][c]: thread t < (256 / k) k reads the flat elements t, t + (256 / k) k,
+// ... of the block's rows (coalesced; all of one column), then eight partial
+// sums per column and their sum in a fixed order. The last block to finish
+// (completion ticket) adds the block sums the same way, in block order, into
+// out[c] (times scale) and puts the ticket back to zero, so the result does
+// not depend on which block finished last. k <= 64.
+__device__ __forceinline__ double colsum_fold(double* sh, int k, int per, double s) {
+    const int t = threadIdx.x;
+    const int np = per < 8 ? per : 8;          // partial sums per column
+    sh[t] = s;
+    __syncthreads();
+    double s1 = 0.0;
+    if (t < np * k) {
+        const int c = t % k, q = t / k;
+        for (int i = q; i < per; i += np) s1 += sh[i * k + c];
+    }
+    __syncthreads();
+    if (t < np * k) sh[t] = s1;
+    __syncthreads();
+    double v = 0.0;
+    if (t < k)
+        for (int q = 0; q < np; ++q) v += sh[q * k + t];
+    __syncthreads();
+    return v;
+}
+
+__global__ void __launch_bounds__(256)
+k_colsum(const double* __restrict__ x, long n, int k, int rows_per_block, double* __restrict__ part,
+         double scale, double* __restrict__ out, unsigned* __restrict__ ticket) {
     __shared__ double sh[kSumThreads];
     __shared__ bool last;
-    long r0 = (long)blockIdx.x * rows_per_block;
-    long r1 = r0 + rows_per_block < n ? r0 + rows_per_block : n;
-    for (int c = 0; c < k; ++c) {
-        double s = 0.0;
-        for (long r = r0 + threadIdx.x; r < r1; r += kSumThreads) s += x[r * k + c];
-        sh[threadIdx.x] = s;
-        __syncthreads();
-        for (int w = kSumThreads / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) part[(long)blockIdx.x * k + c] = sh[0];
-        __syncthreads();
+    const int t = threadIdx.x;
+    const int per = kSumThreads / k, tk = per * k;
+    const long r0 = (long)blockIdx.x * rows_per_block;
+    const long r1 = r0 + rows_per_block < n ? r0 + rows_per_block : n;
+    double s = 0.0;
+    if (t < tk) {
+        const long e1 = r1 * k;
+#pragma unroll 4
+        for (long e = r0 * k + t; e < e1; e += tk) s += x[e];
     }
-    if (threadIdx.x == 0) {
+    const double v = colsum_fold(sh, k, per, s);
+    if (t < k) part[(long)blockIdx.x * k + t] = v;
+    if (t == 0) {
         __threadfence();
         last = atomicAdd(ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!last) return;
     __threadfence();
+    // block sums: thread t < tk takes blocks t / k, t / k + per, ... of column t % k
     const int nblk = gridDim.x;
-    for (int c = 0; c < k; ++c) {
-        double s = 0.0;
-        for (int b = threadIdx.x; b < nblk; b += kSumThreads) s += __ldcg(part + (long)b * k + c);
-        sh[threadIdx.x] = s;
-        __syncthreads();
-        for (int w = kSumThreads / 2; w > 0; w >>= 1) {
-            if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) out[c] = sh[0] * scale;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *ticket = 0u;
+    double sb = 0.0;
+    if (t < tk)
+        for (int b = t / k; b < nblk; b += per) sb += __ldcg(part + (long)b * k + t % k);
+    const double tot = colsum_fold(sh, k, per, sb);
+    if (t < k) out[t] = tot * scale;
+    if (t == 0) *ticket = 0u;
 }
 
 // completion tickets of the fused reductions, zero between launches (the
@@ -191,9 +207,11 @@ int mesh_tickets(tp_mesh* m, unsigned** out, cudaStream_t st) {
 // column sums (times `scale`) of x [n][k] into out_dev [k]; uses m->part2
 int colsum(tp_mesh* m, const double* x, long n, int k, double scale, double* out_dev,
                   cudaStream_t st) {
-    int nblk = (int)((n + 4095) / 4096);
-    if (nblk < 1) nblk = 1;
-    if (nblk > 1024) nblk = 1024;
+    if (k < 1 || k > 64) return fail(TP_ERR_INVALID_ARG, "colsum: 1 to 64 columns");
+    // about 2,048 elements per block (8 per thread), at most two blocks per SM
+    long nb = (n * k + 2047) / 2048;
+    const long cap = 2L * sm_count();
+    int nblk = (int)(nb < 1 ? 1 : (nb > cap ? cap : nb));
     int rpb = (int)((n + nblk - 1) / nblk);
     if (rpb < 1) rpb = 1;
     TP_TRY(ensure(m->part2, sizeof(double) * (size_t)nblk * k));
@@ -427,20 +445,22 @@ int refresh_geometry(tp_mesh* m, cudaStream_t st) {
 // face corners -> vertices (deterministic CSR gather, no atomics)
 // ---------------------------------------------------------------------------
 
+// one thread per (vertex, column): the vertex's corners in CSR order (a fixed
+// order), the 9 threads of a vertex reading one corner row together
 __global__ void k_gather(const double* __restrict__ corner, const int* __restrict__ vf_ptr,
                          const int* __restrict__ vf_idx, int nv, int k, double* __restrict__ y) {
-    int v = blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= nv) return;
-    int e0 = vf_ptr[v], e1 = vf_ptr[v + 1];
-    for (int c = 0; c < k; ++c) {
-        double s = 0.0;
-        for (int e = e0; e < e1; ++e) s += corner[(long)vf_idx[e] * k + c];
-        y[(long)v * k + c] = s;
-    }
+    const long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long)nv * k) return;
+    const int v = (int)(t / k), c = (int)(t - (long)v * k);
+    const int e0 = vf_ptr[v], e1 = vf_ptr[v + 1];
+    double s = 0.0;
+    for (int e = e0; e < e1; ++e) s += corner[(long)vf_idx[e] * k + c];
+    y[t] = s;
 }
 
 int corners_to_vertices(tp_mesh* m, const double* corner, int k, double* y, cudaStream_t st) {
-    int nb = (m->nv + 255) / 256;
+    const long n = (long)m->nv * k;
+    const unsigned nb = (unsigned)((n + 255) / 256);
     k_gather<<<nb, 256, 0, st>>>(corner, m->vf_ptr.as<int>(), m->vf_idx.as<int>(), m->nv, k, y);
     TP_LAUNCH_CHECK();
     return TP_OK;

@@ -1404,39 +1404,48 @@ __global__ void k_split_sum2(const float2* __restrict__ part, int nsplit, int na
     out[idx] = (double)a - (double)ca;
 }
 
-// as k_apply_combine, from the split sums of k_split_sum2 (accumulator a of
-// face S at sums[a * nf + S])
+// The FP64 combine from the split sums of k_split_sum2 (accumulator a of face
+// S at sums[a * nf + S]): one thread per (face S, column c), a block per
+// SC_FACES faces. Thread (S, c) forms z = (r/a) W_S - (H W)_S for column c,
+// then the corner values of the transposed map: 2 a_S grad phi_cr . zV (B)
+// and 2 a_S zU / 3 (B0, L). 1/a_S is taken once per face, in shared memory.
+constexpr int SC_FACES = 32;
 template <int OP, int KC>
-__global__ void k_apply_combine2(const double* __restrict__ sums, int nf, const d4* __restrict__ f64a,
-                                 const double* __restrict__ fgrad, const double* __restrict__ W64, int k, int col0,
-                                 double* __restrict__ corner) {
+__global__ void __launch_bounds__(SC_FACES * KC)
+k_apply_combine2(const double* __restrict__ sums, int nf, const d4* __restrict__ f64a,
+                 const double* __restrict__ fgrad, const double* __restrict__ W64, int k, int col0,
+                 double* __restrict__ corner) {
     using L = OpLayout<OP, KC>;
-    const int S = blockIdx.x * blockDim.x + threadIdx.x;
-    if (S >= nf) return;
-    double s[L::NA];
-#pragma unroll
-    for (int i = 0; i < L::NA; ++i) s[i] = sums[(size_t)i * nf + S];
-    double a = f64a[S].w;
+    __shared__ double s_inv[SC_FACES], s_a[SC_FACES];
+    const int S0 = blockIdx.x * SC_FACES;
+    if (threadIdx.x < SC_FACES && S0 + threadIdx.x < nf) {
+        const double a = f64a[S0 + threadIdx.x].w;
+        s_a[threadIdx.x] = a;
+        s_inv[threadIdx.x] = 1.0 / a;
+    }
+    __syncthreads();
+    const int fl = threadIdx.x / KC, c = threadIdx.x - fl * KC;
+    const int S = S0 + fl;
+    if (S >= nf || col0 + c >= k) return;
+    const double* ps = sums + S;
+    const double a = s_a[fl], ia = s_inv[fl];
     const double* W = W64 + 4 * KC * (size_t)S;
-    double zV[3 * KC], zU[KC];
-    for (int i = 0; i < 3 * KC; ++i) zV[i] = 0.0;
-    for (int i = 0; i < KC; ++i) zU[i] = 0.0;
-    int o = 0;
+    double zV[3] = {0.0, 0.0, 0.0}, zU = 0.0;
     if (L::HIGH) {
-        double r = s[0] / a;
-        for (int i = 0; i < 3 * KC; ++i) zV[i] = r * W[i] - s[1 + i];
-        o = 1 + 3 * KC;
+        const double r = ps[0] * ia;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) zV[q] = r * W[q * KC + c] - ps[(size_t)(1 + q * KC + c) * nf];
     }
     if (L::USEU) {
-        double r = s[o] / a;
-        for (int c = 0; c < KC; ++c) zU[c] = r * W[3 * KC + c] - s[o + 1 + c];
+        const double r = ps[(size_t)L::NH * nf] * ia;
+        zU = r * W[3 * KC + c] - ps[(size_t)(L::NH + 1 + c) * nf];
     }
-    for (int cr = 0; cr < 3; ++cr)
-        for (int c = 0; c < KC && col0 + c < k; ++c) {
-            double g = 0.0;
-            for (int q = 0; q < 3; ++q) g += fgrad[9 * S + 3 * cr + q] * zV[q * KC + c];
-            corner[((size_t)S * 3 + cr) * k + col0 + c] = 2.0 * a * (g + zU[c] / 3.0);
-        }
+    const double* gr = fgrad + 9 * (size_t)S;
+#pragma unroll
+    for (int cr = 0; cr < 3; ++cr) {
+        const double g = gr[3 * cr] * zV[0] + gr[3 * cr + 1] * zV[1] + gr[3 * cr + 2] * zV[2];
+        corner[((size_t)S * 3 + cr) * k + col0 + c] = 2.0 * a * (g + zU * (1.0 / 3.0));
+    }
 }
 
 // per face: z = (r/a) W_S - (H W)_S in FP64, then the corner values of the
@@ -1477,7 +1486,7 @@ __global__ void k_apply_combine(const double* __restrict__ part, int nsplit, int
         for (int c = 0; c < KC && col0 + c < k; ++c) {
             double g = 0.0;
             for (int q = 0; q < 3; ++q) g += fgrad[9 * S + 3 * cr + q] * zV[q * KC + c];
-            corner[((size_t)S * 3 + cr) * k + col0 + c] = 2.0 * a * (g + zU[c] / 3.0);
+            corner[((size_t)S * 3 + cr) * k + col0 + c] = 2.0 * a * (g + zU[c] * (1.0 / 3.0));
         }
 }
 
@@ -2009,9 +2018,8 @@ static int launch_apply_tc(tp_mesh* m, const tp_params* p, const double* v, int 
         k_split_sum2<<<(unsigned)(((size_t)L::NA * nf + 255) / 256), 256, 0, st>>>(m->part.as<float2>(), g.nsplit,
                                                                                 L::NA, nf, sums);
         TP_LAUNCH_CHECK();
-        k_apply_combine2<TP_OP_A, 9><<<(nf + 127) / 128, 128, 0, st>>>(sums, nf, m->f64a.as<d4>(),
-                                                                       m->fgrad.as<double>(), m->wv64.as<double>(), k,
-                                                                       col0, m->corner.as<double>());
+        k_apply_combine2<TP_OP_A, 9><<<(nf + SC_FACES - 1) / SC_FACES, SC_FACES * 9, 0, st>>>(
+            sums, nf, m->f64a.as<d4>(), m->fgrad.as<double>(), m->wv64.as<double>(), k, col0, m->corner.as<double>());
         TP_LAUNCH_CHECK();
     }
     return corners_to_vertices(m, m->corner.as<double>(), k, y, st);
@@ -2071,9 +2079,8 @@ static int launch_apply_wide(tp_mesh* m, const tp_params* p, const double* v, in
         k_split_sum2<<<(unsigned)(((size_t)L::NA * nf + 255) / 256), 256, 0, st>>>(m->part.as<float2>(), g.nsplit,
                                                                                 L::NA, nf, sums);
         TP_LAUNCH_CHECK();
-        k_apply_combine2<OP, 9><<<(nf + 127) / 128, 128, 0, st>>>(sums, nf, m->f64a.as<d4>(), m->fgrad.as<double>(),
-                                                                  m->wv64.as<double>(), k, col0,
-                                                                  m->corner.as<double>());
+        k_apply_combine2<OP, 9><<<(nf + SC_FACES - 1) / SC_FACES, SC_FACES * 9, 0, st>>>(
+            sums, nf, m->f64a.as<d4>(), m->fgrad.as<double>(), m->wv64.as<double>(), k, col0, m->corner.as<double>());
         TP_LAUNCH_CHECK();
     }
     return corners_to_vertices(m, m->corner.as<double>(), k, y, st);
