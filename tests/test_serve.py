@@ -106,3 +106,23 @@ def test_results_are_the_same_alone_and_in_the_mix(lib):
         assert a.report["E_after"] == pytest.approx(b.report["E_after"], rel=1e-12)
     s = serve.summarize(res_mix, mix.wall)
     assert s["completed"] == 8 and s["latency_ms"]["p99"] >= s["latency_ms"]["p50"]
+
+
+def test_request_sizes_stay_in_the_configured_range():
+    # icospheres take a subdivision level whose 20 * 4^l faces lie in
+    # [f_min, f_max]; tori round the drawn face count; arrivals increase
+    f_min, f_max = 2000, 200000
+    reqs = serve.make_requests(40, f_min, f_max, rate=10.0, seed=5)
+    t = [r.arrival for r in reqs]
+    assert all(b > a for a, b in zip(t, t[1:]))
+    kinds = set()
+    for r in reqs:
+        nf = len(r.F)
+        is_ico = len(r.V) == nf // 2 + 2 and nf % 20 == 0 and (nf // 20) & (nf // 20 - 1) == 0
+        kinds.add(is_ico)
+        if is_ico:
+            assert f_min <= nf <= f_max, nf
+        else:
+            assert 0.9 * f_min <= nf <= 1.1 * f_max, nf
+        assert r.F.min() >= 0 and r.F.max() < len(r.V)
+    assert kinds == {True, False}
